@@ -1,0 +1,55 @@
+"""Seeded synthetic dense-LP generators (inputs only; no simplex arithmetic).
+
+These stand in for the paper's random instances (Sec. 4 generates dense LPs
+of sizes 256..8192 with an Octave routine whose text is garbled and whose
+random stream is not reproducible here).  Both the CUDA library's tests and
+the CPU oracle take their inputs from this module.
+
+Dense workload (one LP):
+  A_ij  iid uniform integers in [1, 1000]     (row-major, drawn first)
+  b_i   iid uniform integers in [1000, 100000] (drawn second)
+  c_j   iid uniform integers in [1, 100]       (drawn third)
+all from ``numpy.random.default_rng(seed)`` and stored as float64.  Every
+value is an integer below 2**24, so it is exact in FP32 as well.  A > 0 and
+b > 0 make the LP max c'x, Ax <= b, x >= 0 feasible (x = 0) and bounded.
+"""
+import numpy as np
+
+
+def dense_lp(m: int, n: int, seed: int = 0):
+    """(A, b, c) of one dense LP, float64, C-contiguous."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(1, 1001, size=(m, n)).astype(np.float64)
+    b = rng.integers(1000, 100001, size=m).astype(np.float64)
+    c = rng.integers(1, 101, size=n).astype(np.float64)
+    return A, b, c
+
+
+def dual_of(A, b, c):
+    """Data of the dual LP  min b'y  s.t.  A'y >= c, y >= 0  as (A', c, b).
+
+    Feed the result to the dual-form entry point (min c'x, Ax >= b)."""
+    return np.ascontiguousarray(np.asarray(A).T), np.asarray(c).copy(), np.asarray(b).copy()
+
+
+def log_uniform_shapes(count: int, lo: int, hi: int, seed: int = 0):
+    """`count` (m, n) pairs, each drawn log-uniformly in [lo, hi] (integers)."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(np.log(lo), np.log(hi), size=(count, 2))
+    s = np.clip(np.rint(np.exp(u)).astype(np.int64), lo, hi)
+    return [(int(a), int(b)) for a, b in s]
+
+
+def batch_lps(count: int, lo: int, hi: int, seed: int = 0):
+    """`count` dense LPs with log-uniform shapes; LP k uses seed (seed, k)."""
+    shapes = log_uniform_shapes(count, lo, hi, seed)
+    out = []
+    for k, (m, n) in enumerate(shapes):
+        out.append(dense_lp(m, n, seed=np.random.SeedSequence([seed, k]).generate_state(1)[0]))
+    return out
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int = 0):
+    """Arrival times (seconds from 0) of a Poisson stream with the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
