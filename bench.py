@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Throughput of the dense tableau simplex on GB300: pivots/s and tableau GB/s.
+
+Workload (one step): four seeded synthetic dense LPs shaped like the paper's
+Sec. 4 problems, all FP64 and solved to optimality --
+  2048 x 2048 primal form (max c'x, Ax <= b),
+  2048 x 2048 dual form (min b'y, A'y >= c, by the dual simplex),
+  512 x 4096 and 4096 x 512 primal form (more variables than constraints and
+  the reverse).
+A entries uniform integers in [1, 1000], b in [1000, 100000], c in [1, 100].
+
+`value` is pivots per second over the whole job, device-timed with CUDA
+events on the library's stream, inputs resident in HBM before the timed
+region (lp_load copies them device to device and builds the tableau inside
+it).  L2 is flushed (256 MiB write) between steps, outside the step's events.
+`e2e` is the same metric through the C ABI from pinned host buffers:
+lp_load from host memory, lp_solve, lp_result into host memory, wall clock.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD_NAME = ("dense LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + 4096x512, "
+                 "FP64, Dantzig pricing")
+FP64_DFMA_PER_CLK_SM = 2          # GB300 FP64 rate: 1.25 TFLOP/s nominal = 2 DFMA/clk/SM
+SMS, SM_MAX_MHZ = 152, 2070.0
+ALU_PEAK_TFLOPS = 2 * FP64_DFMA_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+MAX_LE, MIN_GE = 0, 1
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pivot_kernel_fp64_traffic.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pivot.cu")
+
+
+def workload(seed):
+    from paper_1804_04737_gb300 import lpgen
+    out = []
+    A, b, c = lpgen.dense_lp(2048, 2048, seed)
+    out.append(("2048x2048 primal", A, b, c, MAX_LE))
+    out.append(("2048x2048 dual form", *lpgen.dual_of(A, b, c), MIN_GE))
+    out.append(("512x4096 primal", *lpgen.dense_lp(512, 4096, seed), MAX_LE))
+    out.append(("4096x512 primal", *lpgen.dense_lp(4096, 512, seed), MAX_LE))
+    return out
+
+
+def tableau_bytes(m, n, w=8):
+    """Algorithmic bytes of one pivot: the rank-1 update reads and writes the
+    whole (m+1) x (n+m+1) tableau once (Sec. 2 Step 5)."""
+    return 2 * (m + 1) * (n + m + 1) * w
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """dram bytes per pivot-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    import hashlib
+    try:
+        rec = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        if rec.get("kernel_source_sha256_16") != sha:
+            return None
+        return float(rec["dram_bytes_per_step_scaled"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "gbs_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"error": "nvidia-smi unavailable"}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"error": "no samples"}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_oracle_run(lps, threads):
+    import oracle
+    oracle.set_threads(threads)
+    pivots = 0
+    t0 = time.perf_counter()
+    for _, A, b, c, sense in lps:
+        r = oracle.solve(A, b, c, sense=sense)
+        assert r.status == oracle.OPTIMAL
+        pivots += r.iters
+    return pivots, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle (the paper's method as plain C, OpenMP over the rows of
+    Step 5) on the host cores, same workload, metric and units."""
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    lps = workload(0)
+    for _ in range(args.warmup):
+        cpu_oracle_run(lps, cores)
+    piv = 0
+    sec = 0.0
+    for _ in range(args.steps):
+        p, t = cpu_oracle_run(lps, cores)
+        piv += p
+        sec += t
+    v = piv / sec
+    line = {"impl": "reference", "metric": "pivots/s", "value": v, "unit": "pivots/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "seed": 0},
+            "cpu_baseline": {"value": v, "unit": "pivots/s", "cores": cores, "kind": "oracle",
+                             "sample": "the whole workload (4 LPs) per step"},
+            "e2e": {"value": v, "unit": "pivots/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_04737_gb300 import capi
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    lps = workload(rank)
+    dev_in = [(name, *(torch.from_numpy(v).cuda() for v in (A, b, c)), sense)
+              for name, A, b, c, sense in lps]
+    handles = [capi.lp_create(capi.lp_options_default(cuda_stream=stream, device=local))
+               for _ in lps]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def device_step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for h, (_, A, b, c, sense) in zip(handles, dev_in):
+                capi.lp_load(h, A, b, c, sense)
+                capi.lp_solve_async(h)
+            ev1.record(stream)
+        stats = []
+        for h in handles:
+            obj, st, it = capi.lp_result(h)
+            if st != capi.LP_OPTIMAL:
+                raise RuntimeError("solve ended with status %s" % capi.STATUS_NAMES[st])
+            kms, _ = capi.lp_kernel_time(h)
+            stats.append((it, kms, obj))
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), stats
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms, pivots, kernel_ms, alg_bytes = [], 0, 0.0, 0.0
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            ms, stats = device_step()
+            step_ms.append(ms)
+            for (it, kms, _), (_, A, _b, _c, _s) in zip(stats, lps):
+                pivots += it
+                kernel_ms += kms
+                alg_bytes += it * tableau_bytes(A.shape[0], A.shape[1])
+    torch.cuda.synchronize()
+    total_ms = sum(step_ms)
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pv = torch.tensor([pivots], dtype=torch.float64, device="cuda")
+        dist.all_reduce(pv)
+        all_pivots = int(pv.item())
+    else:
+        all_pivots = pivots
+
+    # end to end from pinned host buffers through the C ABI
+    host_in = []
+    for _, A, b, c, sense in lps:
+        pin = [torch.from_numpy(v).pin_memory() for v in (A, b, c)]
+        m, n = A.shape
+        host_in.append((pin, torch.empty(n, dtype=torch.float64).pin_memory(),
+                        torch.empty(m, dtype=torch.float64).pin_memory(), sense))
+    h2d = sum(8 * (A.size + b.size + c.size) for _, A, b, c, _ in lps)
+    d2h = sum(8 * (A.shape[0] + A.shape[1] + 1) for _, A, _, _, _ in lps)
+
+    def e2e_step():
+        piv = 0
+        for h, (pin, x, y, sense) in zip(handles, host_in):
+            capi.lp_load(h, pin[0].numpy(), pin[1].numpy(), pin[2].numpy(), sense)
+            capi.lp_solve(h)
+            _, st, it = capi.lp_result(h, x.numpy(), y.numpy())
+            piv += it
+        return piv
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_piv = 0
+    for _ in range(args.steps):
+        e2e_piv += e2e_step()
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    e2e_val = e2e_piv / e2e_sec
+    if dist:
+        t = torch.tensor([e2e_sec], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        pv = torch.tensor([e2e_piv], dtype=torch.float64, device="cuda")
+        dist.all_reduce(pv)
+        e2e_val = float(pv.item()) / float(t.item())
+
+    for h in handles:
+        capi.lp_destroy(h)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm_peak, peak_kind = peaks()
+    gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    flops = alg_bytes / 16 * 2  # one FMA (2 flops) per 16 bytes of FP64 read + write
+    tflops = flops / (kernel_ms * 1e-3) / 1e12
+    traffic = kernel_traffic()
+    hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(gbs / hbm_peak, 4), "peak_kind": peak_kind}
+    alu = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(ALU_PEAK_TFLOPS, 4),
+           "unit": "TFLOP/s", "frac": round(tflops / ALU_PEAK_TFLOPS, 4),
+           "peak_kind": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+    roof = dict(max((hbm, alu), key=lambda r: r["frac"]))
+    roof["traffic"] = traffic
+    roof["kernel"] = "pivot_kernel<double> (persistent, one launch per solve)"
+    roof["secondary"] = alu if roof["bound"] == "hbm" else hbm
+    line = {
+        "metric": "pivots/s", "value": all_pivots / (total_ms * 1e-3), "unit": "pivots/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "seed": "rank", "lps": [n for n, *_ in lps],
+                   "pivots_per_step": pivots // args.steps,
+                   "l2": "flushed between steps (256 MiB write), outside the step events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "tableau_gbs": round(gbs, 1),
+        "e2e": {"value": e2e_val, "unit": "pivots/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "gpu_launches": 5 * len(lps) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        p, t = cpu_oracle_run(lps, cores)
+        line["cpu_baseline"] = {"value": p / t, "unit": "pivots/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "the whole workload (4 LPs) once, %.1f s" % t}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * gbsimplex -- dense tableau simplex on one GB300 (sm_103a), C ABI.
+ *
+ * The method is the standard tableau simplex of Coutinho et al., "A Scalable
+ * Shared-Memory Parallel Simplex for Large-Scale Linear Programming"
+ * (arXiv:1804.04737), Sec. 2 (Steps 1-5) and its parallel scheme of Sec. 3
+ * (Steps I-VI), re-laid for a GPU: one persistent grid runs whole pivot
+ * sequences; each pivot is Dantzig pricing (Sec. 2 Step 2), the ratio test
+ * (Step 3) and the rank-1 tableau update (Steps 4-5).
+ *
+ * Problem forms (Sec. 2, Eq. 1 with m <= constraints and slack variables):
+ *   LP_MAX_LE  max c'x  s.t. Ax <= b, x >= 0   (needs b >= 0: the slack basis
+ *              is feasible; solved by the primal simplex)
+ *   LP_MIN_GE  min c'x  s.t. Ax >= b, x >= 0   (needs c >= 0: the slack basis
+ *              is dual feasible; solved by the dual simplex).  Loading
+ *              (A', c, b) of a LP_MAX_LE problem in this form solves its LP
+ *              dual, the "dual formulation" runs of Sec. 4.
+ *
+ * Arithmetic contract (FP64 mode), identical in the library and its test
+ * oracle, so that pivot sequences agree bit for bit:
+ *   pricing   candidate j < n+m with z_j < -eps_d; most negative wins, ties
+ *             smallest j (Bland mode: smallest candidate j);
+ *   ratio     rows with a_iq > eps_p; (rhs > 0 ? rhs : 0) / a_iq by one IEEE
+ *             division; smallest wins, ties smallest row (Bland mode:
+ *             smallest basic-variable index); none => LP_UNBOUNDED;
+ *   pivot     prow_j = T[p][j] / T[p][q] (IEEE division), other rows
+ *             T[i][j] = fma(-T[i][q], prow_j, T[i][j]), objective row too;
+ *   Bland     after `bland_after` consecutive pivots whose chosen ratio is
+ *             exactly 0, Bland's rule until the next nonzero ratio;
+ *   dual      leaving row: most negative rhs below -eps_r (ties smallest
+ *             row; Bland mode: smallest basic index); entering column: the
+ *             smallest (z_j > 0 ? z_j : 0) / (-T[r][j]) over T[r][j] < -eps_p,
+ *             ties smallest j; none => LP_INFEASIBLE.
+ *
+ * Conventions
+ *   - Every call returns an lp_err; nothing throws across the ABI.  The
+ *     message of the last error of a handle is lp_last_error(handle).
+ *   - Solve outcomes (unbounded, iteration limit, ...) are lp_status values,
+ *     not errors.
+ *   - Pointer arguments may be host or device memory (CUDA unified
+ *     addressing tells them apart); the library copies inputs and writes
+ *     outputs into caller buffers.  The caller keeps ownership of both.
+ *   - The library owns the device memory of a handle (tableau, scratch) and
+ *     frees it in lp_destroy.
+ *   - A handle is used by one host thread at a time.  Server handles are
+ *     thread-safe for submit / poll.
+ *   - Matrices are row-major, doubles.
+ */
+#ifndef GBSIMPLEX_H
+#define GBSIMPLEX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_handle lp_handle;
+
+typedef enum {
+    LP_OK = 0,
+    LP_ERR_INVALID_ARG = 1,      /* bad size, NULL pointer, NaN/Inf input      */
+    LP_ERR_OOM = 2,              /* device allocation failed or over budget     */
+    LP_ERR_CUDA = 3,             /* a CUDA call failed (message in last_error)  */
+    LP_ERR_INFEASIBLE_START = 4, /* LP_MAX_LE with some b_i < 0, or LP_MIN_GE
+                                    with some c_j < 0: needs a Phase I          */
+    LP_ERR_STATE = 5,            /* call order (solve before load, ...)         */
+    LP_ERR_BUSY = 6              /* server: no free slot / budget right now     */
+} lp_err;
+
+typedef enum {
+    LP_OPTIMAL = 0,
+    LP_UNBOUNDED = 1,   /* Sec. 2 Step 3: entering column has no a_iq > eps_p */
+    LP_ITER_LIMIT = 2,  /* max_iters pivots made in this call; lp_solve resumes */
+    LP_INFEASIBLE = 3,  /* dual simplex: violated row with no T[r][j] < -eps_p */
+    LP_NUMERICAL = 4,   /* FP32 mode: FP64 check still fails after reinversions */
+    LP_TIMEOUT = 5,     /* a device-side wait exceeded spin_timeout_cycles     */
+    LP_NOT_SOLVED = 6
+} lp_status;
+
+typedef enum { LP_MAX_LE = 0, LP_MIN_GE = 1 } lp_sense;
+typedef enum { LP_FP64 = 0, LP_FP32_REINV = 1 } lp_precision;
+
+typedef struct {
+    int precision;           /* lp_precision                                     */
+    int reinv_k;             /* FP32 mode: FP64 reinversion every reinv_k pivots  */
+    long long max_iters;     /* pivots per lp_solve call (then LP_ITER_LIMIT)     */
+    double eps_d;            /* <= 0: 1e-9 * max(1, max|c|)                       */
+    double eps_p;            /* <= 0: 1e-9 * max(1, max|A|)                       */
+    double eps_r;            /* <= 0: 1e-9 * max(1, max|b|)                       */
+    int bland_after;         /* consecutive zero-ratio pivots before Bland's rule */
+    int threads;             /* threads per CTA of the pivot kernel, 0 = auto     */
+    long long spin_timeout_cycles; /* device wait limit (SM clock cycles)        */
+    void *cuda_stream;       /* cudaStream_t to run on; NULL = library's own      */
+    int device;              /* CUDA device ordinal                               */
+    int ctas;                /* CTAs of the persistent grid, 0 = auto             */
+    long long trace_cap;     /* record (row, column) of the first trace_cap pivots */
+} lp_options;
+
+/* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
+ * by formula, bland_after 32, auto launch shape, spin timeout 4e9 cycles,
+ * library stream, device 0, no trace. */
+void lp_options_default(lp_options *opt);
+
+/* Create a handle on opt->device (opt may be NULL for the defaults).
+ * *out receives the handle, or NULL on error. */
+lp_err lp_create(lp_handle **out, const lp_options *opt);
+
+/* Copy one LP into the handle and build its initial tableau (Sec. 2 Step 1:
+ * rows [A | I | b], objective row [-c | 0 | 0]; for LP_MIN_GE rows
+ * [-A | I | -b] and objective row [c | 0 | 0]).  A is m x n row-major, b has
+ * m entries, c has n entries; each may be host or device memory.  m, n >= 1.
+ * Replaces any LP loaded before.  Errors: LP_ERR_INVALID_ARG (size, NULL,
+ * non-finite value), LP_ERR_INFEASIBLE_START, LP_ERR_OOM, LP_ERR_CUDA. */
+lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b,
+               const double *c, lp_sense sense);
+
+/* Pivot until optimal, unbounded / infeasible, or max_iters pivots in this
+ * call; blocking.  After LP_ITER_LIMIT another call continues from the same
+ * tableau.  Errors: LP_ERR_STATE (nothing loaded), LP_ERR_CUDA. */
+lp_err lp_solve(lp_handle *h);
+
+/* Enqueue the same work on the handle's stream and return without waiting;
+ * lp_result (or a stream synchronisation) completes it. */
+lp_err lp_solve_async(lp_handle *h);
+
+/* Read the result of the last solve (waits for the handle's stream).
+ * x (n entries): primal values, x_j = rhs of the row where j is basic, else 0.
+ * y (m entries): dual values, the objective-row entries of the slack columns.
+ * obj: c'x.  Any output pointer may be NULL; x, y may be host or device. */
+lp_err lp_result(lp_handle *h, double *x, double *y, double *obj,
+                 lp_status *status, long long *iters);
+
+/* Diagnostics for tests: the (row, column) of pivots 0..cap-1 of this load
+ * (count = pivots recorded), the basic variable of each row, and the
+ * (m+1) x (n+m+1) tableau converted to FP64 (host or device buffer). */
+lp_err lp_get_trace(lp_handle *h, int *rows, int *cols, long long cap, long long *count);
+lp_err lp_get_basis(lp_handle *h, int *basis);
+lp_err lp_get_tableau(lp_handle *h, double *T);
+
+/* Device time in milliseconds of the pivot kernel of the last solve, from
+ * CUDA events recorded around its launch on the handle's stream (waits for
+ * the stream).  *launches receives the number of pivot-kernel launches of
+ * that solve (1 in FP64 mode). */
+lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches);
+
+/* Free the handle and its device memory.  NULL is allowed. */
+void lp_destroy(lp_handle *h);
+
+/* Message of the last error on h ("" if none); h may be NULL for errors of
+ * lp_create and the batch call. */
+const char *lp_last_error(const lp_handle *h);
+
+/* Library version string. */
+const char *lp_version(void);
+
+/* sizeof(lp_options) as compiled into the library, for bindings that lay the
+ * struct out themselves. */
+size_t lp_options_size(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSIMPLEX_H */

@@ -1,0 +1,239 @@
+"""ctypes binding of the C ABI in ``include/gbsimplex.h`` (argument marshalling only).
+
+Every function keeps the C name.  Arrays may be numpy arrays (host memory) or
+torch tensors (host or CUDA memory); they are passed as raw pointers, so they
+must be C-contiguous float64 (int32 for index outputs).  Errors raise
+:class:`LpError` carrying the C error code and the library's message.
+
+The CUDA library must have been built (``paper_1804_04737_gb300.build``); a
+missing library raises instead of falling back to anything else.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgbsimplex.so")
+
+LP_OK, LP_ERR_INVALID_ARG, LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_INFEASIBLE_START, LP_ERR_STATE, \
+    LP_ERR_BUSY = range(7)
+LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT, LP_INFEASIBLE, LP_NUMERICAL, LP_TIMEOUT, \
+    LP_NOT_SOLVED = range(7)
+STATUS_NAMES = ["optimal", "unbounded", "iter_limit", "infeasible", "numerical", "timeout",
+                "not_solved"]
+LP_MAX_LE, LP_MIN_GE = 0, 1
+LP_FP64, LP_FP32_REINV = 0, 1
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class lp_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("reinv_k", ctypes.c_int),
+        ("max_iters", ctypes.c_longlong),
+        ("eps_d", ctypes.c_double),
+        ("eps_p", ctypes.c_double),
+        ("eps_r", ctypes.c_double),
+        ("bland_after", ctypes.c_int),
+        ("threads", ctypes.c_int),
+        ("spin_timeout_cycles", ctypes.c_longlong),
+        ("cuda_stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+        ("ctas", ctypes.c_int),
+        ("trace_cap", ctypes.c_longlong),
+    ]
+
+
+class LpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gbsimplex error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point of include/gbsimplex.h
+_SIGS = [
+    ("lp_options_default", None, [ctypes.POINTER(lp_options)]),
+    ("lp_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(lp_options)]),
+    ("lp_load", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("lp_solve", ctypes.c_int, [ctypes.c_void_p]),
+    ("lp_solve_async", ctypes.c_int, [ctypes.c_void_p]),
+    ("lp_result", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 _c_double_p, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_longlong)]),
+    ("lp_get_trace", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    ("lp_get_basis", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("lp_get_tableau", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("lp_kernel_time", ctypes.c_int, [ctypes.c_void_p, _c_double_p,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    ("lp_destroy", None, [ctypes.c_void_p]),
+    ("lp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("lp_version", ctypes.c_char_p, []),
+    ("lp_options_size", ctypes.c_size_t, []),
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (once) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("gbsimplex CUDA library not built (%s); run "
+                           "paper_1804_04737_gb300.build.build_library()" % path)
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.lp_options_size() != ctypes.sizeof(lp_options):
+        raise RuntimeError("lp_options layout mismatch between binding and library")
+    _lib = lib
+    return lib
+
+
+def _check(code, h=None):
+    if code != LP_OK:
+        msg = load_library().lp_last_error(h)
+        raise LpError(code, msg.decode() if msg else "")
+
+
+def _ptr(a, dtype=np.float64):
+    """Raw pointer of a contiguous numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):  # torch.Tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(a.dtype) != {np.float64: "torch.float64", np.int32: "torch.int32"}[dtype]:
+            raise ValueError("tensor dtype must be %s" % np.dtype(dtype).name)
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be a C-contiguous %s numpy array" % np.dtype(dtype).name)
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def lp_options_default(**overrides) -> lp_options:
+    o = lp_options()
+    load_library().lp_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream  # torch.cuda.Stream
+        setattr(o, k, v)
+    return o
+
+
+def lp_create(opt: Optional[lp_options] = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().lp_create(ctypes.byref(h), ctypes.byref(opt) if opt else None))
+    return h
+
+
+def lp_load(h, A, b, c, sense=LP_MAX_LE) -> None:
+    m, n = int(A.shape[0]), int(A.shape[1])
+    if tuple(b.shape) != (m,) or tuple(c.shape) != (n,):
+        raise ValueError("shapes: A %s, b %s, c %s" % (tuple(A.shape), tuple(b.shape),
+                                                       tuple(c.shape)))
+    _check(load_library().lp_load(h, m, n, _ptr(A), _ptr(b), _ptr(c), int(sense)), h)
+
+
+def lp_solve(h) -> None:
+    _check(load_library().lp_solve(h), h)
+
+
+def lp_solve_async(h) -> None:
+    _check(load_library().lp_solve_async(h), h)
+
+
+def lp_result(h, x=None, y=None):
+    """(obj, status, iters); fills x and y when given."""
+    obj = ctypes.c_double()
+    st = ctypes.c_int()
+    it = ctypes.c_longlong()
+    _check(load_library().lp_result(h, _ptr(x), _ptr(y), ctypes.byref(obj), ctypes.byref(st),
+                                    ctypes.byref(it)), h)
+    return obj.value, st.value, it.value
+
+
+def lp_get_trace(h, cap: int):
+    rows = np.full(max(cap, 1), -1, dtype=np.int32)
+    cols = np.full(max(cap, 1), -1, dtype=np.int32)
+    cnt = ctypes.c_longlong()
+    _check(load_library().lp_get_trace(h, _ptr(rows, np.int32), _ptr(cols, np.int32), cap,
+                                       ctypes.byref(cnt)), h)
+    return rows[:cnt.value], cols[:cnt.value]
+
+
+def lp_get_basis(h, m: int):
+    basis = np.empty(m, dtype=np.int32)
+    _check(load_library().lp_get_basis(h, _ptr(basis, np.int32)), h)
+    return basis
+
+
+def lp_get_tableau(h, m: int, n: int):
+    T = np.empty((m + 1, n + m + 1), dtype=np.float64)
+    _check(load_library().lp_get_tableau(h, _ptr(T)), h)
+    return T
+
+
+def lp_kernel_time(h):
+    """(milliseconds, launches) of the pivot kernel of the last solve."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(load_library().lp_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)), h)
+    return ms.value, n.value
+
+
+def lp_destroy(h) -> None:
+    if h is not None:
+        load_library().lp_destroy(h)
+
+
+def lp_last_error(h=None) -> str:
+    msg = load_library().lp_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def lp_version() -> str:
+    return load_library().lp_version().decode()
+
+
+@dataclass
+class Result:
+    status: int
+    obj: float
+    x: np.ndarray
+    y: np.ndarray
+    iters: int
+    trace_p: Optional[np.ndarray] = None
+    trace_q: Optional[np.ndarray] = None
+
+    @property
+    def status_name(self) -> str:
+        return STATUS_NAMES[self.status]
+
+
+def solve(A, b, c, sense=LP_MAX_LE, trace_cap=0, **opts) -> Result:
+    """lp_create + lp_load + lp_solve + lp_result (+ lp_get_trace) + lp_destroy."""
+    o = lp_options_default(trace_cap=trace_cap, **opts)
+    h = lp_create(o)
+    try:
+        lp_load(h, A, b, c, sense)
+        lp_solve(h)
+        m, n = int(A.shape[0]), int(A.shape[1])
+        x = np.empty(n, dtype=np.float64)
+        y = np.empty(m, dtype=np.float64)
+        obj, st, it = lp_result(h, x, y)
+        tp = tq = None
+        if trace_cap:
+            tp, tq = lp_get_trace(h, trace_cap)
+        return Result(st, obj, x, y, it, tp, tq)
+    finally:
+        lp_destroy(h)

@@ -1,0 +1,466 @@
+// C ABI of the tableau simplex library (declared in include/gbsimplex.h).
+//
+// A handle owns, on its device: the input copies (A, b, c in FP64), the
+// pitched tableau, the basis, the staged pivot column, the per-CTA partials,
+// the barrier words, the pivot trace and a small descriptor/state block.  All
+// of it is allocated on lp_load (reused when the next LP fits) and freed on
+// lp_destroy.
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "gbs_internal.h"
+#include "gbsimplex.h"
+
+using namespace gbs;
+
+struct lp_handle {
+    lp_options opt;
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char err[512] = {0};
+
+    // problem
+    bool loaded = false;
+    bool solved = false;
+    int m = 0, n = 0, M = 0, N = 0, sense = 0, prec = PREC_FP64;
+    long long P = 0;
+    double eps_d = 0, eps_p = 0, eps_r = 0;
+
+    // device memory
+    double *dA = nullptr, *db = nullptr, *dc = nullptr;
+    size_t cap_A = 0, cap_b = 0, cap_c = 0;  // element capacities
+    void *dT = nullptr;
+    size_t cap_T = 0;                           // bytes
+    int *dbasis = nullptr;
+    size_t cap_basis = 0;
+    void *dcol = nullptr;
+    size_t cap_col = 0;                         // bytes
+    Cand *dpart = nullptr;                      // 2 * max_ctas
+    int max_ctas = 0;
+    unsigned *dbar = nullptr;                   // 64 words + err flag
+    int *dtrace = nullptr;
+    long long cap_trace = 0;
+    LpDesc *ddesc = nullptr;
+    InputStats *dstats = nullptr;
+    double *dx = nullptr, *dy = nullptr, *dobj = nullptr;
+    size_t cap_x = 0, cap_y = 0;
+
+    // descriptor as written by lp_load, and a pinned mirror of the device copy
+    // read back after each solve
+    LpDesc desc{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pivot kernel
+    LpDesc *pdesc = nullptr;
+    double *pobj = nullptr;
+    PivotShape shape{};
+};
+
+namespace {
+
+thread_local char g_err[512];
+
+void set_err(lp_handle *h, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h ? h->err : g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+#define CUDA_TRY(h, call)                                                           \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            set_err((h), "%s failed: %s", #call, cudaGetErrorString(e_));           \
+            return e_ == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA;      \
+        }                                                                           \
+    } while (0)
+
+template <typename P>
+cudaError_t grow(P **ptr, size_t *cap, size_t need_elems) {
+    if (*ptr && *cap >= need_elems) return cudaSuccess;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void **)ptr, std::max<size_t>(need_elems, 1) * sizeof(P));
+    if (e == cudaSuccess) *cap = need_elems;
+    return e;
+}
+
+cudaError_t grow_bytes(void **ptr, size_t *cap, size_t bytes) {
+    if (*ptr && *cap >= bytes) return cudaSuccess;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) *cap = bytes;
+    return e;
+}
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_options_default(lp_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = LP_FP64;
+    o->reinv_k = 50;
+    o->max_iters = 1000000000000ll;
+    o->eps_d = 0.0;
+    o->eps_p = 0.0;
+    o->eps_r = 0.0;
+    o->bland_after = 32;
+    o->threads = 0;
+    o->spin_timeout_cycles = 4000000000ll;
+    o->cuda_stream = nullptr;
+    o->device = 0;
+    o->ctas = 0;
+    o->trace_cap = 0;
+}
+
+const char *lp_version(void) { return "gbsimplex 0.1 (sm_103a)"; }
+
+size_t lp_options_size(void) { return sizeof(lp_options); }
+
+const char *lp_last_error(const lp_handle *h) { return h ? h->err : g_err; }
+
+lp_err lp_create(lp_handle **out, const lp_options *opt) {
+    if (!out) {
+        set_err(nullptr, "lp_create: out is NULL");
+        return LP_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    lp_options o;
+    if (opt) o = *opt; else lp_options_default(&o);
+    if (o.precision != LP_FP64 && o.precision != LP_FP32_REINV) {
+        set_err(nullptr, "lp_create: unknown precision %d", o.precision);
+        return LP_ERR_INVALID_ARG;
+    }
+    if (o.precision == LP_FP32_REINV) {
+        set_err(nullptr, "lp_create: FP32 tableau mode is not available in this build");
+        return LP_ERR_INVALID_ARG;
+    }
+    if (o.max_iters < 0 || o.bland_after < 0 || o.trace_cap < 0 || o.spin_timeout_cycles <= 0 ||
+        o.threads < 0 || o.threads > 1024 || o.ctas < 0 || o.reinv_k < 1) {
+        set_err(nullptr, "lp_create: option out of range");
+        return LP_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev <= 0) {
+        set_err(nullptr, "lp_create: no CUDA device (%s)", cudaGetErrorString(e));
+        return LP_ERR_CUDA;
+    }
+    if (o.device < 0 || o.device >= ndev) {
+        set_err(nullptr, "lp_create: device %d out of range (%d devices)", o.device, ndev);
+        return LP_ERR_INVALID_ARG;
+    }
+    lp_handle *h = new (std::nothrow) lp_handle();
+    if (!h) {
+        set_err(nullptr, "lp_create: host allocation failed");
+        return LP_ERR_OOM;
+    }
+    h->opt = o;
+    h->device = o.device;
+    h->prec = o.precision == LP_FP64 ? PREC_FP64 : PREC_FP32;
+    e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) {
+        if (o.cuda_stream) {
+            h->stream = (cudaStream_t)o.cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            h->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->ddesc, sizeof(LpDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(InputStats));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, 64 * sizeof(unsigned) + 64);
+    if (e == cudaSuccess) e = cudaMalloc(&h->dobj, sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pdesc, sizeof(LpDesc));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pobj, sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "lp_create: %s", cudaGetErrorString(e));
+        lp_destroy(h);
+        return e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA;
+    }
+    *out = h;
+    return LP_OK;
+}
+
+void lp_destroy(lp_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dbasis, h->dcol, h->dpart, h->dbar,
+                    h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (h->pdesc) cudaFreeHost(h->pdesc);
+    if (h->pobj) cudaFreeHost(h->pobj);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, const double *c,
+               lp_sense sense) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    h->err[0] = 0;
+    if (m < 1 || n < 1 || !A || !b || !c) {
+        set_err(h, "lp_load: need m, n >= 1 and non-NULL A, b, c (m=%d n=%d)", m, n);
+        return LP_ERR_INVALID_ARG;
+    }
+    if (sense != LP_MAX_LE && sense != LP_MIN_GE) {
+        set_err(h, "lp_load: unknown sense %d", (int)sense);
+        return LP_ERR_INVALID_ARG;
+    }
+    if ((long long)n + m + 1 > 0x7fffffffll - 64) {
+        set_err(h, "lp_load: n + m too large");
+        return LP_ERR_INVALID_ARG;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    h->loaded = false;
+    h->solved = false;
+    const int M = m + 1, N = n + m + 1;
+    const long long P = pitch_for(N);
+    const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
+    const PivotShape sh = choose_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas);
+
+    CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
+    CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
+    CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
+    CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
+    CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
+    CUDA_TRY(h, grow_bytes(&h->dcol, &h->cap_col, (size_t)M * esz));
+    if (h->max_ctas < sh.ctas) {
+        if (h->dpart) cudaFree(h->dpart);
+        h->dpart = nullptr;
+        h->max_ctas = 0;
+        CUDA_TRY(h, cudaMalloc(&h->dpart, 2 * (size_t)sh.ctas * sizeof(Cand)));
+        h->max_ctas = sh.ctas;
+    }
+    if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
+        if (h->dtrace) cudaFree(h->dtrace);
+        h->dtrace = nullptr;
+        h->cap_trace = 0;
+        CUDA_TRY(h, cudaMalloc(&h->dtrace, 2 * (size_t)h->opt.trace_cap * sizeof(int)));
+        h->cap_trace = h->opt.trace_cap;
+    }
+    CUDA_TRY(h, grow(&h->dx, &h->cap_x, (size_t)n));
+    CUDA_TRY(h, grow(&h->dy, &h->cap_y, (size_t)m));
+
+    cudaStream_t s = h->stream;
+    CUDA_TRY(h, cudaMemcpyAsync(h->dA, A, sizeof(double) * (size_t)m * n, cudaMemcpyDefault, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->db, b, sizeof(double) * (size_t)m, cudaMemcpyDefault, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->dc, c, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CUDA_TRY(h, launch_inspect(h->dA, h->db, h->dc, m, n, h->dstats, s));
+    InputStats st;
+    CUDA_TRY(h, cudaMemcpyAsync(&st, h->dstats, sizeof st, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (st.flags & 4) {
+        set_err(h, "lp_load: A, b or c holds a NaN or infinity");
+        return LP_ERR_INVALID_ARG;
+    }
+    if (sense == LP_MAX_LE && (st.flags & 1)) {
+        set_err(h, "lp_load: max form needs b >= 0 (the slack basis must be feasible)");
+        return LP_ERR_INFEASIBLE_START;
+    }
+    if (sense == LP_MIN_GE && (st.flags & 2)) {
+        set_err(h, "lp_load: min form needs c >= 0 (the slack basis must be dual feasible)");
+        return LP_ERR_INFEASIBLE_START;
+    }
+    const double amax = bits_to_double(st.amax_bits), bmax = bits_to_double(st.bmax_bits),
+                 cmax = bits_to_double(st.cmax_bits);
+    h->eps_d = h->opt.eps_d > 0 ? h->opt.eps_d : 1e-9 * std::max(1.0, cmax);
+    h->eps_p = h->opt.eps_p > 0 ? h->opt.eps_p : 1e-9 * std::max(1.0, amax);
+    h->eps_r = h->opt.eps_r > 0 ? h->opt.eps_r : 1e-9 * std::max(1.0, bmax);
+
+    CUDA_TRY(h, launch_build(h->prec, h->dA, h->db, h->dc, m, n, (int)sense, h->dT, P, h->dbasis, s));
+
+    LpDesc d{};
+    d.T = h->dT;
+    d.basis = h->dbasis;
+    d.colbuf = h->dcol;
+    d.part_sel = h->dpart;
+    d.part_ratio = h->dpart + sh.ctas;
+    d.bar = h->dbar;
+    d.err = (int *)(h->dbar + 64);
+    d.trace = h->dtrace;
+    d.trace_cap = h->opt.trace_cap > 0 ? h->opt.trace_cap : 0;
+    d.P = P;
+    d.m = m;
+    d.n = n;
+    d.M = M;
+    d.N = N;
+    d.sense = (int)sense;
+    d.bland_after = h->opt.bland_after;
+    d.eps_d = h->eps_d;
+    d.eps_p = h->eps_p;
+    d.eps_r = h->eps_r;
+    d.iters = 0;
+    d.iter_limit = 0;
+    d.deg = 0;
+    d.status = -1;
+    d.last_p = d.last_q = -1;
+    CUDA_TRY(h, cudaMemcpyAsync(h->ddesc, &d, sizeof d, cudaMemcpyHostToDevice, s));
+    *h->pdesc = d;
+    h->desc = d;
+    h->shape = sh;
+    h->m = m;
+    h->n = n;
+    h->M = M;
+    h->N = N;
+    h->P = P;
+    h->sense = (int)sense;
+    h->loaded = true;
+    return LP_OK;
+}
+
+lp_err lp_solve_async(lp_handle *h) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    if (!h->loaded) {
+        set_err(h, "lp_solve: no LP loaded");
+        return LP_ERR_STATE;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    // The pivot state (iterations, degeneracy counter) lives in the device
+    // descriptor, so consecutive calls resume without a host round trip.
+    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, 64 * sizeof(unsigned) + 64, s));
+    CUDA_TRY(h, cudaEventRecord(h->ev0, s));
+    CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape, h->opt.spin_timeout_cycles,
+                             h->opt.max_iters, s));
+    CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+    CUDA_TRY(h, launch_extract(h->prec, h->ddesc, h->dT, h->dbasis, h->m, h->n, h->P, h->sense,
+                               h->dx, h->dy, h->dobj, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->pdesc, h->ddesc, sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->pobj, h->dobj, sizeof(double), cudaMemcpyDeviceToHost, s));
+    h->solved = true;
+    return LP_OK;
+}
+
+lp_err lp_solve(lp_handle *h) {
+    lp_err e = lp_solve_async(h);
+    if (e != LP_OK) return e;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+lp_err lp_result(lp_handle *h, double *x, double *y, double *obj, lp_status *status,
+                 long long *iters) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    if (!h->solved) {
+        set_err(h, "lp_result: nothing solved");
+        return LP_ERR_STATE;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    if (x) CUDA_TRY(h, cudaMemcpyAsync(x, h->dx, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    if (y) CUDA_TRY(h, cudaMemcpyAsync(y, h->dy, sizeof(double) * h->m, cudaMemcpyDefault, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (obj) *obj = *h->pobj;
+    if (status) *status = (lp_status)h->pdesc->status;
+    if (iters) *iters = h->pdesc->iters;
+    return LP_OK;
+}
+
+lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    if (!h->solved) {
+        set_err(h, "lp_kernel_time: nothing solved");
+        return LP_ERR_STATE;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    CUDA_TRY(h, cudaEventSynchronize(h->ev1));
+    float t = 0.0f;
+    CUDA_TRY(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
+    if (ms) *ms = (double)t;
+    if (launches) *launches = 1;
+    return LP_OK;
+}
+
+lp_err lp_get_trace(lp_handle *h, int *rows, int *cols, long long cap, long long *count) {
+    if (!h || cap < 0) return LP_ERR_INVALID_ARG;
+    if (!h->loaded) {
+        set_err(h, "lp_get_trace: no LP loaded");
+        return LP_ERR_STATE;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    long long k = std::min(std::min(h->pdesc->iters, h->pdesc->trace_cap), cap);
+    if (count) *count = k;
+    if (k <= 0) return LP_OK;
+    int *tmp = new (std::nothrow) int[2 * k];
+    if (!tmp) return LP_ERR_OOM;
+    cudaError_t e = cudaMemcpy(tmp, h->dtrace, sizeof(int) * 2 * k, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] tmp;
+        set_err(h, "lp_get_trace: %s", cudaGetErrorString(e));
+        return LP_ERR_CUDA;
+    }
+    for (long long i = 0; i < k; ++i) {
+        if (rows) rows[i] = tmp[2 * i];
+        if (cols) cols[i] = tmp[2 * i + 1];
+    }
+    delete[] tmp;
+    return LP_OK;
+}
+
+lp_err lp_get_basis(lp_handle *h, int *basis) {
+    if (!h || !basis) return LP_ERR_INVALID_ARG;
+    if (!h->loaded) {
+        set_err(h, "lp_get_basis: no LP loaded");
+        return LP_ERR_STATE;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    CUDA_TRY(h, cudaMemcpyAsync(basis, h->dbasis, sizeof(int) * h->m, cudaMemcpyDefault, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LP_OK;
+}
+
+lp_err lp_get_tableau(lp_handle *h, double *T) {
+    if (!h || !T) return LP_ERR_INVALID_ARG;
+    if (!h->loaded) {
+        set_err(h, "lp_get_tableau: no LP loaded");
+        return LP_ERR_STATE;
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    if (h->prec == PREC_FP64) {
+        CUDA_TRY(h, cudaMemcpy2DAsync(T, sizeof(double) * h->N, h->dT, sizeof(double) * h->P,
+                                      sizeof(double) * h->N, h->M, cudaMemcpyDefault, s));
+    } else {
+        double *tmp = nullptr;
+        CUDA_TRY(h, cudaMalloc(&tmp, sizeof(double) * (size_t)h->M * h->N));
+        cudaError_t e = launch_to_fp64((const float *)h->dT, h->P, h->M, h->N, tmp, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(T, tmp, sizeof(double) * (size_t)h->M * h->N, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        if (e != cudaSuccess) {
+            set_err(h, "lp_get_tableau: %s", cudaGetErrorString(e));
+            return LP_ERR_CUDA;
+        }
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    return LP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Internal interface between the C ABI (gbs_capi.cu) and the kernels
+// (gbs_pivot.cu).  Not part of the public header.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbs {
+
+enum : int {
+    ST_RUNNING = -1,
+    ST_OPTIMAL = 0,
+    ST_UNBOUNDED = 1,
+    ST_ITER_LIMIT = 2,
+    ST_INFEASIBLE = 3,
+    ST_NUMERICAL = 4,
+    ST_TIMEOUT = 5,
+};
+
+// A selection candidate: lexicographic minimum on (v, key); idx is the row or
+// column it names, -1 for "no candidate".  Keys are unique within one
+// selection, so the minimum is unique and independent of reduction order.
+struct Cand {
+    double v;
+    int key;
+    int idx;
+};
+
+// Device-resident description and state of one LP tableau.  Written by the
+// host before a launch, updated by the pivot kernel, read back after it.
+struct LpDesc {
+    void *T;             // M x P tableau (double or float), row-major, pitch P
+    int *basis;          // basic variable of each constraint row (m)
+    void *colbuf;        // staged pre-update pivot column (M), element type of T
+    Cand *part_sel;      // per-CTA selection partials (pricing / leaving row)
+    Cand *part_ratio;    // per-CTA ratio-test partials
+    unsigned *bar;       // grid barrier: [0] arrivals, [32] generation
+    int *err;            // set to 1 by a wait that timed out
+    int *trace;          // 2 * trace_cap ints: (row, column) per pivot
+    long long trace_cap;
+    long long P;         // row pitch in elements (multiple of 32)
+    int m, n, M, N;      // M = m + 1 rows, N = n + m + 1 columns
+    int sense;           // 0: primal simplex (max, <=); 1: dual simplex (min, >=)
+    int bland_after;
+    double eps_d, eps_p, eps_r;
+    // state carried across launches
+    long long iters;
+    long long iter_limit;  // last launch stopped (ITER_LIMIT) once iters reached this
+    int deg;               // consecutive zero-ratio pivots
+    int status;
+    int last_p, last_q;
+    int pad_;
+};
+
+// Launch shape of the persistent pivot kernel for one LP.
+struct PivotShape {
+    int ctas;     // grid size (= number of column strips)
+    int threads;  // CTA size
+    int strip;    // columns per strip (multiple of 32 bytes of elements)
+};
+
+struct InputStats {
+    unsigned long long amax_bits, bmax_bits, cmax_bits;  // bit patterns of max |.|
+    int flags;  // 1: some b < 0, 2: some c < 0, 4: a non-finite value
+    int pad_;
+};
+
+enum : int { PREC_FP64 = 0, PREC_FP32 = 1 };
+
+inline long long pitch_for(int N) { return ((long long)N + 31) / 32 * 32; }
+
+// Kernel launchers (gbs_pivot.cu).  All enqueue on `s` and return the launch
+// status.
+cudaError_t launch_inspect(const double *A, const double *b, const double *c, int m, int n,
+                           InputStats *out, cudaStream_t s);
+cudaError_t launch_build(int prec, const double *A, const double *b, const double *c, int m,
+                         int n, int sense, void *T, long long P, int *basis, cudaStream_t s);
+PivotShape choose_shape(int prec, int M, long long P, int sms, int threads, int ctas);
+cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long long spin_limit,
+                         long long budget, cudaStream_t s);
+cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,
+                           int m, int n, long long P, int sense, double *x, double *y,
+                           double *obj, cudaStream_t s);
+cudaError_t launch_to_fp64(const float *T, long long P, int M, int N, double *out,
+                           cudaStream_t s);
+
+}  // namespace gbs

@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point its header declares
+(no GPU needed: only symbol lookup and pure host calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1804_04737_gb300 import capi
+from paper_1804_04737_gb300.build import build_library
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    hdr_dir = os.path.join(ROOT, "include")
+    for f in os.listdir(hdr_dir):
+        if f.endswith(".h"):
+            src = open(os.path.join(hdr_dir, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lp_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_library()
+    return capi.load_library()
+
+
+def test_every_declared_symbol_exported(lib):
+    names = _declared()
+    assert {"lp_create", "lp_load", "lp_solve", "lp_result", "lp_destroy"} <= names
+    raw = ctypes.CDLL(capi.LIB_PATH)
+    for name in sorted(names):
+        assert hasattr(raw, name), name
+
+
+def test_binding_covers_header(lib):
+    bound = {s[0] for s in capi._SIGS}
+    assert _declared() <= bound, _declared() - bound
+
+
+def test_options_layout_and_defaults(lib):
+    assert lib.lp_options_size() == ctypes.sizeof(capi.lp_options)
+    o = capi.lp_options_default()
+    assert o.precision == capi.LP_FP64 and o.bland_after == 32 and o.reinv_k == 50
+    assert o.max_iters >= 10 ** 12 and o.spin_timeout_cycles > 0 and o.trace_cap == 0
+    assert capi.lp_version().startswith("gbsimplex")
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    assert lib.lp_create(None, None) == capi.LP_ERR_INVALID_ARG
+    assert lib.lp_load(None, 1, 1, None, None, None, 0) == capi.LP_ERR_INVALID_ARG
+    assert lib.lp_solve(None) == capi.LP_ERR_INVALID_ARG
+    lib.lp_destroy(None)
+    assert "NULL" in capi.lp_last_error(None)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.load_library(str(tmp_path / "nope.so"))
