@@ -41,11 +41,11 @@ struct lp_handle {
     size_t cap_T = 0;                           // bytes
     int *dbasis = nullptr;
     size_t cap_basis = 0;
-    void *dcol = nullptr;
-    size_t cap_col = 0;                         // bytes
+    void *dscratch = nullptr;
+    size_t cap_scratch = 0;                     // bytes
     Cand *dpart = nullptr;                      // 2 * max_ctas
     int max_ctas = 0;
-    unsigned *dbar = nullptr;                   // 64 words + err flag
+    unsigned *dbar = nullptr;                   // 128 words: barrier, readers, err
     int *dtrace = nullptr;
     long long cap_trace = 0;
     LpDesc *ddesc = nullptr;
@@ -188,7 +188,7 @@ lp_err lp_create(lp_handle **out, const lp_options *opt) {
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->ddesc, sizeof(LpDesc));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(InputStats));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, 64 * sizeof(unsigned) + 64);
+    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, 128 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&h->dobj, sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&h->pdesc, sizeof(LpDesc));
     if (e == cudaSuccess) e = cudaMallocHost(&h->pobj, sizeof(double));
@@ -207,7 +207,7 @@ void lp_destroy(lp_handle *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dbasis, h->dcol, h->dpart, h->dbar,
+    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dbasis, h->dscratch, h->dpart, h->dbar,
                     h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -241,14 +241,17 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    const PivotShape sh = choose_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas);
+    const PivotShape sh = choose_shape(h->prec, (int)sense, M, N, P, h->sms, h->opt.threads,
+                                       h->opt.ctas);
 
     CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
     CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
     CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
     CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
     CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
-    CUDA_TRY(h, grow_bytes(&h->dcol, &h->cap_col, (size_t)M * esz));
+    if (!sh.use_smem)
+        CUDA_TRY(h, grow_bytes(&h->dscratch, &h->cap_scratch,
+                               (size_t)sh.ctas * (size_t)sh.scratch_stride));
     if (h->max_ctas < sh.ctas) {
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
@@ -297,11 +300,11 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     LpDesc d{};
     d.T = h->dT;
     d.basis = h->dbasis;
-    d.colbuf = h->dcol;
+    d.scratch = h->dscratch;
+    d.scratch_stride = sh.scratch_stride;
     d.part_sel = h->dpart;
-    d.part_ratio = h->dpart + sh.ctas;
     d.bar = h->dbar;
-    d.err = (int *)(h->dbar + 64);
+    d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;
     d.trace_cap = h->opt.trace_cap > 0 ? h->opt.trace_cap : 0;
     d.P = P;
@@ -343,7 +346,7 @@ lp_err lp_solve_async(lp_handle *h) {
     cudaStream_t s = h->stream;
     // The pivot state (iterations, degeneracy counter) lives in the device
     // descriptor, so consecutive calls resume without a host round trip.
-    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, 64 * sizeof(unsigned) + 64, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, 128 * sizeof(unsigned), s));
     CUDA_TRY(h, cudaEventRecord(h->ev0, s));
     CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape, h->opt.spin_timeout_cycles,
                              h->opt.max_iters, s));

@@ -17,11 +17,12 @@ enum : int {
     ST_TIMEOUT = 5,
 };
 
-// A selection candidate: lexicographic minimum on (v, key); idx is the row or
+// A selection candidate: lexicographic minimum on (vk, key), where vk is an
+// order-preserving integer image of the value compared; idx is the row or
 // column it names, -1 for "no candidate".  Keys are unique within one
 // selection, so the minimum is unique and independent of reduction order.
 struct Cand {
-    double v;
+    unsigned long long vk;
     int key;
     int idx;
 };
@@ -29,18 +30,18 @@ struct Cand {
 // Device-resident description and state of one LP tableau.  Written by the
 // host before a launch, updated by the pivot kernel, read back after it.
 struct LpDesc {
-    void *T;             // M x P tableau (double or float), row-major, pitch P
-    int *basis;          // basic variable of each constraint row (m)
-    void *colbuf;        // staged pre-update pivot column (M), element type of T
-    Cand *part_sel;      // per-CTA selection partials (pricing / leaving row)
-    Cand *part_ratio;    // per-CTA ratio-test partials
-    unsigned *bar;       // grid barrier: [0] arrivals, [32] generation
-    int *err;            // set to 1 by a wait that timed out
-    int *trace;          // 2 * trace_cap ints: (row, column) per pivot
+    void *T;                   // M x P tableau (double or float), row-major, pitch P
+    int *basis;                // basic variable of each constraint row (m)
+    void *scratch;             // per-CTA selection scratch when shared memory is too small
+    long long scratch_stride;  // bytes of scratch per CTA
+    Cand *part_sel;            // 2 x G selection partials (pricing / leaving row), by parity
+    unsigned *bar;             // [0] arrivals, [32] generation, [64] readers counter
+    int *err;                  // set to 1 by a wait that timed out
+    int *trace;                // 2 * trace_cap ints: (row, column) per pivot
     long long trace_cap;
-    long long P;         // row pitch in elements (multiple of 32)
-    int m, n, M, N;      // M = m + 1 rows, N = n + m + 1 columns
-    int sense;           // 0: primal simplex (max, <=); 1: dual simplex (min, >=)
+    long long P;               // row pitch in elements (multiple of 32)
+    int m, n, M, N;            // M = m + 1 rows, N = n + m + 1 columns
+    int sense;                 // 0: primal simplex (max, <=); 1: dual simplex (min, >=)
     int bland_after;
     double eps_d, eps_p, eps_r;
     // state carried across launches
@@ -49,14 +50,17 @@ struct LpDesc {
     int deg;               // consecutive zero-ratio pivots
     int status;
     int last_p, last_q;
-    int pad_;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
 struct PivotShape {
-    int ctas;     // grid size (= number of column strips)
-    int threads;  // CTA size
-    int strip;    // columns per strip (multiple of 32 bytes of elements)
+    int ctas;                  // grid size (= number of column strips)
+    int threads;               // CTA size
+    int strip;                 // columns per strip (multiple of 32 bytes of elements)
+    int use_smem;              // selection scratch in shared memory (else global)
+    int dual;                  // dual simplex kernel (else primal)
+    size_t smem_bytes;         // dynamic shared memory per CTA
+    long long scratch_stride;  // global scratch bytes per CTA when !use_smem
 };
 
 struct InputStats {
@@ -75,7 +79,8 @@ cudaError_t launch_inspect(const double *A, const double *b, const double *c, in
                            InputStats *out, cudaStream_t s);
 cudaError_t launch_build(int prec, const double *A, const double *b, const double *c, int m,
                          int n, int sense, void *T, long long P, int *basis, cudaStream_t s);
-PivotShape choose_shape(int prec, int M, long long P, int sms, int threads, int ctas);
+PivotShape choose_shape(int prec, int sense, int M, int N, long long P, int sms, int threads,
+                        int ctas);
 cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long long spin_limit,
                          long long budget, cudaStream_t s);
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,

@@ -4,33 +4,37 @@
 // thread team alive for the whole solve, Sec. 3; here the team is a grid of
 // CTAs, one per SM, that never returns to the host between pivots).
 //
-// Work split.  CTA g owns the column strip [g*W, g*W + W) of every row.  A
-// pivot is two phases separated by a grid barrier:
+// Work split.  CTA g owns the column strip [g*W, g*W + W) of every row.  One
+// pivot is one phase between two grid barriers:
 //
-//   S (select)  every CTA reduces the selection partials of the previous
-//               phase to the entering column q (primal, Sec. 2 Step 2) or the
-//               leaving row r (dual simplex); then
-//                 primal: ratio test of Step 3 over the CTA's block of rows,
-//                         writing per-CTA partials;
-//                 dual:   the entering-column ratio over row r, computed
-//                         redundantly by every CTA (the row is short);
-//               and copies its block of rows of the pivot column into colbuf.
-//   U (update)  every CTA reduces the ratio partials to the pivot row p,
-//               divides its strip of row p by the pivot (Step 4) into shared
-//               memory, and applies T[i][j] = fma(-col[i], prow[j], T[i][j])
-//               to its strip of every other row, objective row included
-//               (Step 5).  The objective row (primal) or the rhs column
-//               (dual) is inspected on the fly, giving the selection partials
-//               of the next pivot -- the paper's Step VI fuses the objective
-//               row update with the next pricing in the same way.
+//   1. Selection, computed redundantly by every CTA (no second barrier):
+//      the per-CTA partials of the previous phase give the entering column q
+//      (primal, Sec. 2 Step 2) or the leaving row r (dual simplex); then the
+//      ratio test over all rows (primal, Step 3) or over all columns of row r
+//      (dual), staging the pre-update pivot column in shared memory.  The
+//      ratios are screened with a single-precision reciprocal and only the
+//      rows within 2^-19 of the smallest screened ratio get the exact IEEE
+//      division, so the selection equals the exact one.
+//   2. Step 4 on the CTA's strip of the pivot row (IEEE division), into
+//      shared memory.
+//   3. Step 5 on the strip, T[i][j] = fma(-col[i], prow[j], T[i][j]) for every
+//      row but the pivot row, objective row included, 128-bit vectors.  The
+//      objective row (primal) or the rhs column (dual) is inspected as it is
+//      written, giving this CTA's partial for the next selection -- the
+//      paper's Step VI fuses the objective-row update with the next pricing
+//      the same way.
 //
-// Race freedom: in phase U a CTA reads and writes only its own strip, plus
-// colbuf and the partials, which nobody writes in U.  Row p of the strip is
-// read into shared memory before any thread of the CTA writes it.  In phase S
-// nothing writes the tableau.  Partials are double-buffered by phase.
+// Race freedom.  A CTA writes only its own strip.  The data other CTAs read
+// during selection -- primal: the pivot column and the rhs column; dual: the
+// pivot column, row r and the objective row -- is written last: every CTA
+// bumps a counter once its selection reads are done, and a strip's protected
+// part is written only after the counter shows all CTAs arrived (by then it
+// normally has, so this wait costs nothing).  Partials are double-buffered
+// by pivot parity.
 //
-// Waits are bounded: a barrier that does not complete within the spin limit
-// sets the error flag and the kernel returns with status TIMEOUT.
+// Waits are bounded: a barrier or counter wait that does not complete within
+// the spin limit sets the error flag and the kernel returns with status
+// TIMEOUT.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -43,22 +47,40 @@ namespace gbs {
 namespace {
 
 constexpr int kMaxThreads = 1024;
+constexpr size_t kMaxDynSmem = 200 * 1024;  // below the 227 KB opt-in limit, leaving room for statics
+
+// ---------------------------------------------------------------------------
+// Ordered keys.  GB300 runs FP64 compares and min/max on its narrow FP64 pipe
+// (the same two operations per SM per clock as an FP64 FMA), so selection
+// compares doubles through order-preserving integer keys instead: for any two
+// non-NaN values, x < y exactly when okey(x) < okey(y).
+
+constexpr unsigned long long kSign = 0x8000000000000000ull;
+
+__device__ __forceinline__ unsigned long long okey(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u & kSign) ? ~u : (u | kSign);
+}
+__device__ __forceinline__ unsigned long long okey(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? (unsigned long long)(~u) : (unsigned long long)(u | 0x80000000u);
+}
 
 __device__ __forceinline__ Cand cand_empty() {
     Cand c;
-    c.v = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    c.vk = ~0ull;
     c.key = 0x7fffffff;
     c.idx = -1;
     return c;
 }
 
 __device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
-    return a.v < b.v || (a.v == b.v && a.key < b.key);
+    return a.vk < b.vk || (a.vk == b.vk && a.key < b.key);
 }
 
-__device__ __forceinline__ void cand_take(Cand &best, double v, int key, int idx) {
-    if (v < best.v || (v == best.v && key < best.key)) {
-        best.v = v;
+__device__ __forceinline__ void cand_take(Cand &best, unsigned long long vk, int key, int idx) {
+    if (vk < best.vk || (vk == best.vk && key < best.key)) {
+        best.vk = vk;
         best.key = key;
         best.idx = idx;
     }
@@ -68,7 +90,7 @@ __device__ __forceinline__ Cand warp_min(Cand c) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         Cand d;
-        d.v = __shfl_xor_sync(0xffffffffu, c.v, o);
+        d.vk = __shfl_xor_sync(0xffffffffu, c.vk, o);
         d.key = __shfl_xor_sync(0xffffffffu, c.key, o);
         d.idx = __shfl_xor_sync(0xffffffffu, c.idx, o);
         if (cand_less(d, c)) c = d;
@@ -76,34 +98,46 @@ __device__ __forceinline__ Cand warp_min(Cand c) {
     return c;
 }
 
-// Minimum over the CTA; every thread gets the result.  Uses red[0..32].
-__device__ Cand block_min(Cand c, Cand *red) {
+// Block-wide candidate minimum; every thread gets the result.  `buf` (32
+// entries) belongs to one call site; one __syncthreads.
+__device__ __forceinline__ Cand block_min_c(Cand c, Cand *buf) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
     c = warp_min(c);
-    __syncthreads();  // red may still be read from a previous call
-    if (lane == 0) red[wid] = c;
+    if (lane == 0) buf[wid] = c;
     __syncthreads();
-    if (wid == 0) {
-        Cand d = lane < nw ? red[lane] : cand_empty();
-        d = warp_min(d);
-        if (lane == 0) red[32] = d;
-    }
-    __syncthreads();
-    return red[32];
+    Cand r = buf[0];
+    for (int k = 1; k < nw; ++k)
+        if (cand_less(buf[k], r)) r = buf[k];
+    return r;
 }
 
-// Minimum of the G partials written by the previous phase (read from L2).
-__device__ Cand reduce_partials(const Cand *part, int G, Cand *red) {
+__device__ __forceinline__ unsigned long long block_min_u(unsigned long long v,
+                                                          unsigned long long *buf) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    if (lane == 0) buf[wid] = v;
+    __syncthreads();
+    unsigned long long r = buf[0];
+    for (int k = 1; k < nw; ++k) r = buf[k] < r ? buf[k] : r;
+    return r;
+}
+
+__device__ __forceinline__ Cand load_partials_min(const Cand *part, int G, Cand *buf) {
     Cand c = cand_empty();
     for (int k = threadIdx.x; k < G; k += blockDim.x) {
-        Cand d;
-        d.v = __ldcg(&part[k].v);
-        d.key = __ldcg(&part[k].key);
-        d.idx = __ldcg(&part[k].idx);
-        if (cand_less(d, c)) c = d;
+        Cand e;
+        e.vk = __ldcg(&part[k].vk);
+        e.key = __ldcg(&part[k].key);
+        e.idx = __ldcg(&part[k].idx);
+        if (cand_less(e, c)) c = e;
     }
-    return block_min(c, red);
+    return block_min_c(c, buf);
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
@@ -123,6 +157,10 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
                  : "l"(p), "r"(v)
                  : "memory");
     return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Grid barrier with a bounded wait.  Returns false (in every thread of the
@@ -159,6 +197,26 @@ __device__ bool grid_sync(unsigned *bar, int *err, int G, long long spin_limit, 
     return *s_flag != 0;
 }
 
+// Wait (thread 0, bounded) until *ctr has reached target.  False when the
+// wait ran out or another CTA reported a timeout.
+__device__ bool wait_count(unsigned *ctr, unsigned target, int *err, long long spin_limit,
+                           int *s_flag) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while ((int)(ld_acquire(ctr) - target) < 0) {
+            if (clock64() - t0 > spin_limit || *(volatile int *)err) {
+                atomicExch(err, 1);
+                ok = 0;
+                break;
+            }
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 template <typename T>
 struct Vec;
 template <>
@@ -182,111 +240,207 @@ __device__ __forceinline__ float getc(const float4 &v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-// t <- fma(a, pr, t) componentwise (a = -col[i]).
-__device__ __forceinline__ void vfma(double2 &t, double a, const double2 &pr) {
-    t.x = fma(a, pr.x, t.x);
-    t.y = fma(a, pr.y, t.y);
+// t <- fma(-c, pr, t) componentwise (Sec. 2 Step 5 on one vector).
+__device__ __forceinline__ void vfma(double2 &t, double c, const double2 &pr) {
+    t.x = fma(-c, pr.x, t.x);
+    t.y = fma(-c, pr.y, t.y);
 }
-__device__ __forceinline__ void vfma(float4 &t, float a, const float4 &pr) {
-    t.x = fmaf(a, pr.x, t.x);
-    t.y = fmaf(a, pr.y, t.y);
-    t.z = fmaf(a, pr.z, t.z);
-    t.w = fmaf(a, pr.w, t.w);
+__device__ __forceinline__ void vfma(float4 &t, float c, const float4 &pr) {
+    t.x = fmaf(-c, pr.x, t.x);
+    t.y = fmaf(-c, pr.y, t.y);
+    t.z = fmaf(-c, pr.z, t.z);
+    t.w = fmaf(-c, pr.w, t.w);
+}
+
+// (x > 0 ? x : 0) and -x through the sign bit, off the FP64 pipe.
+__device__ __forceinline__ double pos_part(double x) {
+    return __double_as_longlong(x) > 0 ? x : 0.0;
+}
+__device__ __forceinline__ float pos_part(float x) { return __float_as_int(x) > 0 ? x : 0.0f; }
+__device__ __forceinline__ double neg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)kSign);
+}
+__device__ __forceinline__ float neg(float x) { return __int_as_float(__float_as_int(x) ^ 0x80000000); }
+
+// Screening key of num / den (num >= +0, den > 0): okey of a value within a
+// relative 2^-20 of the exact quotient.  In range it is one single-precision
+// division of the truncated operands (integer ops convert in both
+// directions); outside it, the exact division.  Every row whose exactly
+// rounded quotient could be the minimum has a screening value within
+// kScreen of the smallest screening value, so screening never drops the row
+// the exact ratios select (ties included).
+__device__ __forceinline__ float trunc_to_float(long long b) {  // positive, exponent in range
+    const int e = (int)(b >> 52) - 1023 + 127;
+    return __int_as_float((e << 23) | (int)((b >> 29) & 0x7fffff));
+}
+__device__ __forceinline__ unsigned long long screen_key(double num, double den) {
+    const long long nb = __double_as_longlong(num), db = __double_as_longlong(den);
+    if (nb == 0) return okey(0.0);
+    const int ne = (int)(nb >> 52), de = (int)(db >> 52);
+    if (ne >= 1023 - 60 && ne <= 1023 + 60 && de >= 1023 - 60 && de <= 1023 + 60) {
+        const float q = __fdividef(trunc_to_float(nb), trunc_to_float(db));
+        const unsigned qb = __float_as_uint(q);  // positive normal: quotient in [2^-121, 2^121]
+        const unsigned long long r =
+            ((unsigned long long)(((qb >> 23) & 0xffu) - 127u + 1023u) << 52) |
+            ((unsigned long long)(qb & 0x7fffffu) << 29);
+        return r | kSign;
+    }
+    return okey(num / den);
+}
+__device__ __forceinline__ unsigned long long screen_key(float num, float den) {
+    const int nb = __float_as_int(num), db = __float_as_int(den);
+    if (nb == 0) return okey(0.0f);
+    const int ne = nb >> 23, de = db >> 23;
+    if (ne >= 127 - 60 && ne <= 127 + 60 && de >= 127 - 60 && de <= 127 + 60)
+        return okey(__fdividef(num, den));
+    return okey(num / den);
+}
+// Screening threshold: okey(rstar * kScreen) for a screening key rstar.
+constexpr double kScreen = 1.0 + 1.0 / 65536.0;  // 1 + 2^-16
+__device__ __forceinline__ unsigned long long screen_thr(unsigned long long rk, double) {
+    const double r = __longlong_as_double((long long)(rk & ~kSign));
+    return okey(r * kScreen);
+}
+__device__ __forceinline__ unsigned long long screen_thr(unsigned long long rk, float) {
+    const float r = __uint_as_float((unsigned)(rk & 0x7fffffffu));
+    return okey(r * (float)kScreen);
 }
 
 // Per-thread running candidate of the next selection, fed with freshly
 // updated values: the objective row (primal pricing, Sec. 2 Step 2) or the
 // rhs column (dual simplex leaving row).
+struct Watch {
+    unsigned long long lim_d, lim_r, zero;  // okey(-eps_d), okey(-eps_r), okey(0)
+    int sense, m, N, bland, p, q;
+    const int *basis;
+};
+
 template <typename T, typename V>
-__device__ __forceinline__ void watch_row(Cand &best, int sense, int i, int m, int N, int col0,
-                                          const V &t, int rhs_lane, double eps_d, double eps_r,
-                                          int bland, int p, int q, const int *basis) {
+__device__ __forceinline__ void watch_row(Cand &best, const Watch &w, int i, int col0, const V &t,
+                                          int rhs_lane) {
     constexpr int VW = Vec<T>::W;
-    if (sense == 0) {
-        if (i == m) {
+    if (w.sense == 0) {
+        if (i == w.m) {
 #pragma unroll
             for (int k = 0; k < VW; ++k) {
                 const int j = col0 + k;
-                const double z = (double)getc(t, k);
-                if (j < N - 1 && z < -eps_d) cand_take(best, bland ? 0.0 : z, j, j);
+                const unsigned long long zk = okey(getc(t, k));
+                if (j < w.N - 1 && zk < w.lim_d) cand_take(best, w.bland ? w.zero : zk, j, j);
             }
         }
-    } else if (rhs_lane >= 0 && i < m) {
-        const double v = (double)getc(t, rhs_lane);
-        if (v < -eps_r) {
-            const int key = bland ? (i == p ? q : __ldcg(basis + i)) : i;
-            cand_take(best, bland ? 0.0 : v, key, i);
+    } else if (rhs_lane >= 0 && i < w.m) {
+        const unsigned long long vk = okey(getc(t, rhs_lane));
+        if (vk < w.lim_r) {
+            const int key = w.bland ? (i == w.p ? w.q : __ldcg(w.basis + i)) : i;
+            cand_take(best, w.bland ? w.zero : vk, key, i);
         }
     }
 }
 
-template <typename T>
+// One 16-byte vector of row i: Step 4 for the pivot row, Step 5 otherwise.
+template <typename T, typename V>
+__device__ __forceinline__ V pivot_vec(const V &t, int i, int p, T col_i, const V &pr) {
+    if (i == p) return pr;
+    V r = t;
+    vfma(r, col_i, pr);
+    return r;
+}
+
+// SMEM: the selection scratch lives in shared memory (else in this CTA's
+// slice of global scratch); DUAL: dual simplex (else primal).  Template
+// parameters, so that the update loop carries no per-row tests for them.
+template <typename T, bool SMEM, bool DUAL>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
+    constexpr int sense = DUAL ? 1 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sprow = reinterpret_cast<T *>(smem_raw);
-    __shared__ Cand red[33];
+    __shared__ Cand rbuf[4][32];
+    __shared__ unsigned long long ubuf[32];
     __shared__ int s_flag;
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
-
     T *__restrict__ Tab = reinterpret_cast<T *>(d->T);
-    T *__restrict__ colbuf = reinterpret_cast<T *>(d->colbuf);
     int *__restrict__ basis = d->basis;
-    Cand *part_sel = d->part_sel;
-    Cand *part_ratio = d->part_ratio;
     const long long P = d->P;
-    const int m = d->m, M = d->M, N = d->N, sense = d->sense;
-    const double eps_d = d->eps_d, eps_p = d->eps_p, eps_r = d->eps_r;
+    const int m = d->m, M = d->M, N = d->N;
     const int bland_after = d->bland_after;
+    const unsigned long long lim_p = okey((T)d->eps_p);       // a_iq >  eps_p
+    const unsigned long long lim_np = okey((T)(-d->eps_p));   // a_rj < -eps_p
+    const unsigned long long zero_k = okey((T)0);
     long long iters = d->iters;
     const long long iter_limit =
         iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
     int deg = d->deg;
     int status = ST_RUNNING;
+    unsigned *readers = d->bar + 64;
+    Watch w;
+    w.lim_d = okey((T)(-d->eps_d));
+    w.lim_r = okey((T)(-d->eps_r));
+    w.zero = zero_k;
+    w.sense = sense;
+    w.m = m;
+    w.N = N;
+    w.basis = basis;
 
-    // Column strip of this CTA and its row block for the ratio test.
+    // Per-CTA scratch: the strip of the normalised pivot row, the pre-update
+    // pivot column and the screening keys (shared memory, or this CTA's slice
+    // of a global scratch buffer when they do not fit).
+    const size_t sprow_bytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
+    const size_t scol_bytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
+    T *sprow = reinterpret_cast<T *>(smem_raw);
+    T *scol;
+    unsigned long long *sr;
+    if (SMEM) {
+        scol = reinterpret_cast<T *>(smem_raw + sprow_bytes);
+        sr = reinterpret_cast<unsigned long long *>(smem_raw + sprow_bytes + scol_bytes);
+    } else {
+        unsigned char *base = reinterpret_cast<unsigned char *>(d->scratch) +
+                              (size_t)g * (size_t)d->scratch_stride;
+        scol = reinterpret_cast<T *>(base);
+        sr = reinterpret_cast<unsigned long long *>(base + scol_bytes);
+    }
+
+    // Column strip of this CTA and the thread -> (row lane, vector) map.
     const int c0 = g * W;  // < P: the host launches ceil(P / W) CTAs
     const int c1 = (int)min((long long)c0 + W, P);
     const int vpr = (c1 - c0) / VW;
-    const int rpp = vpr > 0 ? B / vpr : 0;
-    const int lr = vpr > 0 ? tid / vpr : 0;
-    const int lv = vpr > 0 ? tid - lr * vpr : 0;
-    const bool active = vpr > 0 && lr < rpp;
+    const int rpp = B / vpr;  // >= 1: the host keeps W <= B * VW
+    const int lr = tid / vpr;
+    const int lv = tid - lr * vpr;
+    const bool active = lr < rpp;
     const int col0 = c0 + lv * VW;
-    const int rhs_lane = (active && N - 1 >= col0 && N - 1 < col0 + VW) ? (N - 1 - col0) : -1;
-    const int RPC = (M + G - 1) / G;
-    const int r0 = min(M, g * RPC), r1 = min(M, r0 + RPC);
+    // the vector of this strip holding the rhs column, or -1
+    const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
 
-    // Selection partials of the current tableau.
+    // Selection partials of the current tableau (parity buffer 0).
     {
         const int bland = deg >= bland_after;
         Cand c = cand_empty();
-        if (sense == 0) {
+        if (!DUAL) {
             const T *z = Tab + (long long)m * P;
             for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
-                const double v = (double)lds(z + j);
-                if (v < -eps_d) cand_take(c, bland ? 0.0 : v, j, j);
+                const unsigned long long zk = okey(lds(z + j));
+                if (zk < w.lim_d) cand_take(c, bland ? zero_k : zk, j, j);
             }
-        } else if (N - 1 >= c0 && N - 1 < c1) {
+        } else if (rv >= 0) {
             for (int i = tid; i < m; i += B) {
-                const double v = (double)lds(Tab + (long long)i * P + (N - 1));
-                if (v < -eps_r) cand_take(c, bland ? 0.0 : v, bland ? __ldcg(basis + i) : i, i);
+                const unsigned long long vk = okey(lds(Tab + (long long)i * P + (N - 1)));
+                if (vk < w.lim_r) cand_take(c, bland ? zero_k : vk, bland ? __ldcg(basis + i) : i, i);
             }
         }
-        c = block_min(c, red);
-        if (tid == 0) part_sel[g] = c;
+        c = block_min_c(c, rbuf[3]);
+        if (tid == 0) d->part_sel[g] = c;
     }
     if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
 
+    unsigned rd_target = 0;
+    int lk = 0;  // pivots made in this launch: selects the partials' parity buffer
     while (status == ST_RUNNING) {
-        // ---------------- phase S: select ----------------
+        // ------------- selection, computed redundantly by every CTA -------------
         const int bland = deg >= bland_after;
-        const Cand sel = reduce_partials(part_sel, G, red);
-        int q = -1, p_dual = -1;
-        double rmin_dual = 0.0;
+        const Cand sel = load_partials_min(d->part_sel + (lk & 1) * G, G, rbuf[0]);
         if (sel.idx < 0) {
             status = ST_OPTIMAL;
             break;
@@ -295,63 +449,153 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             status = ST_ITER_LIMIT;
             break;
         }
-        if (sense == 0) {
+        int p, q;
+        unsigned long long rmin;
+        if (!DUAL) {
+            // Sec. 2 Step 3 over all rows: stage the pivot column, screen.
             q = sel.idx;
-            Cand c = cand_empty();
-            for (int i = r0 + tid; i < r1; i += B) {
+            unsigned long long lmin = ~0ull;
+            for (int i = tid; i < M; i += B) {
                 const T a = lds(Tab + (long long)i * P + q);
-                colbuf[i] = a;
-                if (i < m && (double)a > eps_p) {
-                    const T rhs = lds(Tab + (long long)i * P + (N - 1));
-                    const T r = (rhs > (T)0 ? rhs : (T)0) / a;
-                    cand_take(c, (double)r, bland ? __ldcg(basis + i) : i, i);
+                const T rhs = lds(Tab + (long long)i * P + (N - 1));
+                scol[i] = a;
+                if (i < m) {
+                    const unsigned long long rk = okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
+                    sr[i] = rk;
+                    lmin = rk < lmin ? rk : lmin;
                 }
             }
-            c = block_min(c, red);
-            if (tid == 0) part_ratio[g] = c;
-        } else {
-            p_dual = sel.idx;
-            const T *rowr = Tab + (long long)p_dual * P;
-            const T *z = Tab + (long long)m * P;
-            Cand c = cand_empty();
-            for (int j = tid; j < N - 1; j += B) {
-                const T a = lds(rowr + j);
-                if ((double)a < -eps_p) {
-                    const T zj = lds(z + j);
-                    const T t = (zj > (T)0 ? zj : (T)0) / (-a);
-                    cand_take(c, (double)t, j, j);
-                }
-            }
-            c = block_min(c, red);
-            if (c.idx < 0) {
-                status = ST_INFEASIBLE;
-                break;
-            }
-            q = c.idx;
-            rmin_dual = c.v;
-            for (int i = r0 + tid; i < r1; i += B) colbuf[i] = lds(Tab + (long long)i * P + q);
-        }
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
-        }
-
-        // ---------------- phase U: update ----------------
-        int p;
-        double rmin;
-        if (sense == 0) {
-            const Cand rc = reduce_partials(part_ratio, G, red);
-            if (rc.idx < 0) {
+            const unsigned long long rstar = block_min_u(lmin, ubuf);
+            if (rstar == ~0ull) {
                 status = ST_UNBOUNDED;
                 break;
             }
-            p = rc.idx;
-            rmin = rc.v;
+            const unsigned long long thr = screen_thr(rstar, (T)0);
+            Cand c = cand_empty();
+            for (int i = tid; i < m; i += B) {
+                if (sr[i] <= thr) {
+                    const T f = pos_part(lds(Tab + (long long)i * P + (N - 1))) / scol[i];
+                    cand_take(c, okey(f), bland ? __ldcg(basis + i) : i, i);
+                }
+            }
+            c = block_min_c(c, rbuf[1]);
+            p = c.idx;
+            rmin = c.vk;
         } else {
-            p = p_dual;
-            rmin = rmin_dual;
+            // Dual simplex: leaving row from the partials, entering column by
+            // the ratio over row r, then stage the pivot column.
+            p = sel.idx;
+            const T *rowr = Tab + (long long)p * P;
+            const T *z = Tab + (long long)m * P;
+            unsigned long long lmin = ~0ull;
+            for (int j = tid; j < N - 1; j += B) {
+                const T a = lds(rowr + j);
+                const T zj = lds(z + j);
+                const unsigned long long rk = okey(a) < lim_np ? screen_key(pos_part(zj), neg(a)) : ~0ull;
+                sr[j] = rk;
+                lmin = rk < lmin ? rk : lmin;
+            }
+            const unsigned long long rstar = block_min_u(lmin, ubuf);
+            if (rstar == ~0ull) {
+                status = ST_INFEASIBLE;
+                break;
+            }
+            const unsigned long long thr = screen_thr(rstar, (T)0);
+            Cand c = cand_empty();
+            for (int j = tid; j < N - 1; j += B) {
+                if (sr[j] <= thr) {
+                    const T t = pos_part(lds(z + j)) / neg(lds(rowr + j));
+                    cand_take(c, okey(t), j, j);
+                }
+            }
+            c = block_min_c(c, rbuf[1]);
+            q = c.idx;
+            rmin = c.vk;
+            for (int i = tid; i < M; i += B) scol[i] = lds(Tab + (long long)i * P + q);
         }
-        deg = (rmin == 0.0) ? deg + 1 : 0;
+        // Every read of another CTA's columns for this pivot is done: arrive.
+        __syncthreads();
+        if (tid == 0) red_add_release(readers, 1u);
+        rd_target += (unsigned)G;
+        deg = (rmin == zero_k) ? deg + 1 : 0;
+        w.bland = deg >= bland_after;  // rule of the next selection
+        w.p = p;
+        w.q = q;
+
+        // ------------- Step 4: this CTA's strip of the pivot row -------------
+        const T piv = scol[p];
+        const T *rowp = Tab + (long long)p * P;
+        for (int j = c0 + tid; j < c1; j += B) sprow[j - c0] = lds(rowp + j) / piv;
+        __syncthreads();
+
+        // ------------- Step 5, bulk of the strip -------------
+        // Left for the pass below: the vector holding column q and the one
+        // holding the rhs (other CTAs read them during selection; the rhs
+        // vector also feeds the dual's next selection), the objective row
+        // (it feeds the primal's next selection; the dual's selection reads
+        // it) and, in the dual, row r.
+        const int qv = (q >= c0 && q < c1) ? (q - c0) / VW : -1;
+        if (active && lv != qv && lv != rv) {
+            const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
+            T *base = Tab + col0;
+            int i = lr;
+            for (; i + 3 * rpp < m; i += 4 * rpp) {
+                const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                V *p0 = reinterpret_cast<V *>(base + (long long)i * P);
+                V *p1 = reinterpret_cast<V *>(base + (long long)i1 * P);
+                V *p2 = reinterpret_cast<V *>(base + (long long)i2 * P);
+                V *p3 = reinterpret_cast<V *>(base + (long long)i3 * P);
+                const V t0 = ldv(p0), t1 = ldv(p1), t2 = ldv(p2), t3 = ldv(p3);
+                const T a0 = scol[i], a1 = scol[i1], a2 = scol[i2], a3 = scol[i3];
+                const V u0 = pivot_vec<T>(t0, i, p, a0, pr);
+                const V u1 = pivot_vec<T>(t1, i1, p, a1, pr);
+                const V u2 = pivot_vec<T>(t2, i2, p, a2, pr);
+                const V u3 = pivot_vec<T>(t3, i3, p, a3, pr);
+                if (!DUAL || i != p) *p0 = u0;
+                if (!DUAL || i1 != p) *p1 = u1;
+                if (!DUAL || i2 != p) *p2 = u2;
+                if (!DUAL || i3 != p) *p3 = u3;
+            }
+            for (; i < m; i += rpp) {
+                if (DUAL && i == p) continue;
+                V *p0 = reinterpret_cast<V *>(base + (long long)i * P);
+                *p0 = pivot_vec<T>(ldv(p0), i, p, scol[i], pr);
+            }
+        }
+        if (!wait_count(readers, rd_target, d->err, spin_limit, &s_flag)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+        // ------------- Step 5, the rest, with the next selection's partials -----
+        Cand watch = cand_empty();
+        // (a) the q and rhs vectors, every row, spread over all threads
+        for (int k = 0; k < 2; ++k) {
+            const int v = k == 0 ? qv : (rv != qv ? rv : -1);
+            if (v < 0) continue;
+            const int vcol0 = c0 + v * VW;
+            const int vrhs = (N - 1 >= vcol0 && N - 1 < vcol0 + VW) ? (N - 1 - vcol0) : -1;
+            const V vpr_ = *reinterpret_cast<const V *>(sprow + v * VW);
+            T *vbase = Tab + vcol0;
+#pragma unroll 4
+            for (int i = tid; i < M; i += B) {
+                V *p0 = reinterpret_cast<V *>(vbase + (long long)i * P);
+                const V u0 = pivot_vec<T>(ldv(p0), i, p, scol[i], vpr_);
+                *p0 = u0;
+                watch_row<T>(watch, w, i, vcol0, u0, vrhs);
+            }
+        }
+        // (b) the objective row and, in the dual, row r, for the other vectors
+        for (int k = tid; k < (DUAL ? 2 : 1) * vpr; k += B) {
+            const int v = k % vpr;
+            if (v == qv || v == rv) continue;
+            const int i = k < vpr ? m : p;
+            const int vcol0 = c0 + v * VW;
+            V *p0 = reinterpret_cast<V *>(Tab + vcol0 + (long long)i * P);
+            const V u0 = pivot_vec<T>(ldv(p0), i, p, scol[i],
+                                      *reinterpret_cast<const V *>(sprow + v * VW));
+            *p0 = u0;
+            watch_row<T>(watch, w, i, vcol0, u0, -1);
+        }
         if (g == 0 && tid == 0) {
             if (iters < d->trace_cap) {
                 d->trace[2 * iters] = p;
@@ -361,51 +605,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             d->last_p = p;
             d->last_q = q;
         }
-        const T piv = lds(colbuf + p);
-        const T *rowp = Tab + (long long)p * P;
-        for (int j = c0 + tid; j < c1; j += B) sprow[j - c0] = lds(rowp + j) / piv;
-        __syncthreads();
-
-        const int nbland = deg >= bland_after;  // rule of the next selection
-        Cand watch = cand_empty();
-        if (active) {
-            const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
-            T *base = Tab + col0;
-            int i = lr;
-            for (; i + 3 * rpp < M; i += 4 * rpp) {
-                const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                V *p0 = reinterpret_cast<V *>(base + (long long)i * P);
-                V *p1 = reinterpret_cast<V *>(base + (long long)i1 * P);
-                V *p2 = reinterpret_cast<V *>(base + (long long)i2 * P);
-                V *p3 = reinterpret_cast<V *>(base + (long long)i3 * P);
-                V t0 = ldv(p0), t1 = ldv(p1), t2 = ldv(p2), t3 = ldv(p3);
-                const T a0 = -lds(colbuf + i), a1 = -lds(colbuf + i1);
-                const T a2 = -lds(colbuf + i2), a3 = -lds(colbuf + i3);
-                if (i == p) t0 = pr; else vfma(t0, a0, pr);
-                if (i1 == p) t1 = pr; else vfma(t1, a1, pr);
-                if (i2 == p) t2 = pr; else vfma(t2, a2, pr);
-                if (i3 == p) t3 = pr; else vfma(t3, a3, pr);
-                *p0 = t0;
-                *p1 = t1;
-                *p2 = t2;
-                *p3 = t3;
-                watch_row<T>(watch, sense, i, m, N, col0, t0, rhs_lane, eps_d, eps_r, nbland, p, q, basis);
-                watch_row<T>(watch, sense, i1, m, N, col0, t1, rhs_lane, eps_d, eps_r, nbland, p, q, basis);
-                watch_row<T>(watch, sense, i2, m, N, col0, t2, rhs_lane, eps_d, eps_r, nbland, p, q, basis);
-                watch_row<T>(watch, sense, i3, m, N, col0, t3, rhs_lane, eps_d, eps_r, nbland, p, q, basis);
-            }
-            for (; i < M; i += rpp) {
-                V *p0 = reinterpret_cast<V *>(base + (long long)i * P);
-                V t0 = ldv(p0);
-                const T a0 = -lds(colbuf + i);
-                if (i == p) t0 = pr; else vfma(t0, a0, pr);
-                *p0 = t0;
-                watch_row<T>(watch, sense, i, m, N, col0, t0, rhs_lane, eps_d, eps_r, nbland, p, q, basis);
-            }
-        }
-        watch = block_min(watch, red);
-        if (tid == 0) part_sel[g] = watch;
+        watch = block_min_c(watch, rbuf[2]);
+        if (tid == 0) d->part_sel[((lk + 1) & 1) * G + g] = watch;
         ++iters;
+        ++lk;
         if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
             status = ST_TIMEOUT;
             break;
@@ -422,44 +625,64 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void atomic_max_bits(unsigned long long *p, double v) {
-    atomicMax(p, (unsigned long long)__double_as_longlong(fabs(v)));
+__device__ __forceinline__ double block_max(double v, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;  // valid in thread 0
 }
 
 // max |A|, max |b|, max |c| (as bit patterns of non-negative doubles, whose
-// unsigned order is the numeric order), sign and finiteness flags.
-__global__ void inspect_kernel(const double *__restrict__ A, const double *__restrict__ b,
-                               const double *__restrict__ c, int m, int n, InputStats *out) {
+// unsigned order is the numeric order), sign and finiteness flags.  One
+// atomic per CTA and quantity.
+__global__ void __launch_bounds__(256) inspect_kernel(const double *__restrict__ A,
+                                                      const double *__restrict__ b,
+                                                      const double *__restrict__ c, int m, int n,
+                                                      InputStats *out) {
+    __shared__ double red[32];
+    __shared__ int sflags;
     const long long total = (long long)m * n;
     double amax = 0.0, bmax = 0.0, cmax = 0.0;
     int flags = 0;
+    if (threadIdx.x == 0) sflags = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += stride) {
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long k = t0; k < total; k += stride) {
         const double v = A[k];
         if (!isfinite(v)) flags |= 4;
-        amax = fmax(amax, fabs(v));
+        else amax = fmax(amax, fabs(v));
     }
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += stride) {
+    for (long long k = t0; k < m; k += stride) {
         const double v = b[k];
         if (!isfinite(v)) flags |= 4;
+        else bmax = fmax(bmax, fabs(v));
         if (v < 0.0) flags |= 1;
-        bmax = fmax(bmax, fabs(v));
     }
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
+    for (long long k = t0; k < n; k += stride) {
         const double v = c[k];
         if (!isfinite(v)) flags |= 4;
+        else cmax = fmax(cmax, fabs(v));
         if (v < 0.0) flags |= 2;
-        cmax = fmax(cmax, fabs(v));
     }
-    if (flags & 4) {  // keep the maxima meaningful even with NaN around
-        amax = isfinite(amax) ? amax : 0.0;
-        bmax = isfinite(bmax) ? bmax : 0.0;
-        cmax = isfinite(cmax) ? cmax : 0.0;
+    __syncthreads();
+    if (flags) atomicOr(&sflags, flags);
+    amax = block_max(amax, red);
+    bmax = block_max(bmax, red);
+    cmax = block_max(cmax, red);
+    if (threadIdx.x == 0) {
+        if (amax > 0.0) atomicMax(&out->amax_bits, (unsigned long long)__double_as_longlong(amax));
+        if (bmax > 0.0) atomicMax(&out->bmax_bits, (unsigned long long)__double_as_longlong(bmax));
+        if (cmax > 0.0) atomicMax(&out->cmax_bits, (unsigned long long)__double_as_longlong(cmax));
+        if (sflags) atomicOr(&out->flags, sflags);
     }
-    if (amax > 0.0) atomic_max_bits(&out->amax_bits, amax);
-    if (bmax > 0.0) atomic_max_bits(&out->bmax_bits, bmax);
-    if (cmax > 0.0) atomic_max_bits(&out->cmax_bits, cmax);
-    if (flags) atomicOr(&out->flags, flags);
 }
 
 // Sec. 2 Step 1: the initial tableau (rows [A | I | b], objective row
@@ -542,7 +765,7 @@ cudaError_t launch_inspect(const double *A, const double *b, const double *c, in
                            InputStats *out, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(InputStats), s);
     if (e != cudaSuccess) return e;
-    const long long work = (long long)m * n;
+    const long long work = (long long)m * n / 8;  // ~8 elements per thread
     inspect_kernel<<<grid_for(work, 256), 256, 0, s>>>(A, b, c, m, n, out);
     return cudaGetLastError();
 }
@@ -559,10 +782,12 @@ cudaError_t launch_build(int prec, const double *A, const double *b, const doubl
     return cudaGetLastError();
 }
 
-PivotShape choose_shape(int prec, int M, long long P, int sms, int threads, int ctas) {
+PivotShape choose_shape(int prec, int sense, int M, int N, long long P, int sms, int threads,
+                        int ctas) {
     PivotShape sh;
     const int vw = prec == PREC_FP64 ? 2 : 4;       // elements per 16-byte vector
     const int sector = prec == PREC_FP64 ? 4 : 8;   // elements per 32-byte sector
+    const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
     sh.threads = threads > 0 ? threads : kMaxThreads;
     if (sh.threads > kMaxThreads) sh.threads = kMaxThreads;
     if (sh.threads < 64) sh.threads = 64;
@@ -583,25 +808,50 @@ PivotShape choose_shape(int prec, int M, long long P, int sms, int threads, int 
     w = (w + sector - 1) / sector * sector;
     sh.strip = (int)w;
     sh.ctas = (int)((P + w - 1) / w);
+    sh.dual = sense;
+    const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
+    const size_t scol = ((size_t)M * esz + 15) & ~(size_t)15;
+    const size_t sr = (size_t)(sense == 0 ? M : N) * sizeof(double);
+    if (sprow + scol + sr <= kMaxDynSmem) {
+        sh.use_smem = 1;
+        sh.smem_bytes = sprow + scol + sr;
+        sh.scratch_stride = 0;
+    } else {
+        sh.use_smem = 0;
+        sh.smem_bytes = sprow;
+        sh.scratch_stride = (long long)((scol + sr + 255) & ~(size_t)255);
+    }
     return sh;
 }
 
 cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long long spin_limit,
                          long long budget, cudaStream_t s) {
-    const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    size_t smem = (size_t)sh.strip * esz;
     int W = sh.strip;
     void *args[] = {&d_desc, &W, &spin_limit, &budget};
-    const void *fn = prec == PREC_FP64 ? (const void *)pivot_kernel<double>
-                                       : (const void *)pivot_kernel<float>;
-    if (smem > 48 * 1024) {
+    const void *fn;
+    if (prec == PREC_FP64) {
+        if (sh.dual)
+            fn = sh.use_smem ? (const void *)pivot_kernel<double, true, true>
+                             : (const void *)pivot_kernel<double, false, true>;
+        else
+            fn = sh.use_smem ? (const void *)pivot_kernel<double, true, false>
+                             : (const void *)pivot_kernel<double, false, false>;
+    } else {
+        if (sh.dual)
+            fn = sh.use_smem ? (const void *)pivot_kernel<float, true, true>
+                             : (const void *)pivot_kernel<float, false, true>;
+        else
+            fn = sh.use_smem ? (const void *)pivot_kernel<float, true, false>
+                             : (const void *)pivot_kernel<float, false, false>;
+    }
+    if (sh.smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+                                             (int)sh.smem_bytes);
         if (e != cudaSuccess) return e;
     }
     // A cooperative launch fails instead of running when the grid cannot be
     // co-resident, which the grid barrier needs.
-    return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
 }
 
 cudaError_t launch_extract(int prec, const LpDesc *, const void *T, const int *basis, int m,
