@@ -77,7 +77,7 @@ def kernel_traffic():
         sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
         if rec.get("kernel_source_sha256_16") != sha:
             return None
-        return float(rec["dram_bytes_per_step_scaled"])
+        return float(rec["dram_bytes_per_launch"])
     except Exception:
         return None
 
