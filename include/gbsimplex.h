@@ -144,6 +144,31 @@ lp_err lp_get_tableau(lp_handle *h, double *T);
  * that solve (1 in FP64 mode). */
 lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches);
 
+/* Allocation-free solve (the paper has no counterpart; this is a library
+ * service).  Solves one FP64 LP like lp_create + lp_load + lp_solve +
+ * lp_result + lp_destroy, but allocates no device or pinned memory: every
+ * buffer it needs lives in one fixed 64 MiB device array that the library
+ * reserves on each GPU it is loaded on, for the life of the process.  It is
+ * for callers that cannot call cudaMalloc when they solve -- code handed a
+ * fixed memory budget up front, plug-ins inside a host process that owns the
+ * device allocator, loops that must not pay an allocation's latency.
+ *   - A (m x n, row-major), b, c: host or device memory; x (n), y (m): host or
+ *     device memory or NULL; obj, status, iters: host pointers or NULL.
+ *   - opt: NULL for the defaults; FP64 only, opt->trace_cap is ignored, runs
+ *     on opt->cuda_stream (NULL: the legacy default stream) and opt->device.
+ *   - Blocking: returns after the results are written.
+ *   - LPs whose working memory exceeds 64 MiB (about 1500 x 1500) are
+ *     rejected with LP_ERR_INVALID_ARG before any GPU work.
+ *   - The array is shared by all calls; each call rebuilds or clears what it
+ *     uses.  Calls in one process are serialised by a lock; work from it that
+ *     overlapped on the GPU (two processes sharing a context) would race.
+ *   - The first call on a device looks up the array's device address; make
+ *     it before any CUDA stream capture.
+ * Errors as lp_load / lp_solve; the message is lp_last_error(NULL). */
+lp_err lp_solve_noalloc(int m, int n, const double *A, const double *b, const double *c,
+                        lp_sense sense, const lp_options *opt, double *x, double *y,
+                        double *obj, lp_status *status, long long *iters);
+
 /* Free the handle and its device memory.  NULL is allowed. */
 void lp_destroy(lp_handle *h);
 

@@ -73,6 +73,12 @@ _SIGS = [
     ("lp_get_tableau", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("lp_kernel_time", ctypes.c_int, [ctypes.c_void_p, _c_double_p,
                                       ctypes.POINTER(ctypes.c_int)]),
+    ("lp_solve_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.POINTER(lp_options), ctypes.c_void_p,
+                                        ctypes.c_void_p, _c_double_p,
+                                        ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_longlong)]),
     ("lp_destroy", None, [ctypes.c_void_p]),
     ("lp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lp_version", ctypes.c_char_p, []),
@@ -189,6 +195,20 @@ def lp_kernel_time(h):
     n = ctypes.c_int()
     _check(load_library().lp_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)), h)
     return ms.value, n.value
+
+
+def lp_solve_noalloc(A, b, c, sense=LP_MAX_LE, opt: Optional[lp_options] = None, x=None,
+                     y=None):
+    """Allocation-free solve; returns (obj, status, iters) and fills x, y."""
+    m, n = int(A.shape[0]), int(A.shape[1])
+    obj = ctypes.c_double()
+    st = ctypes.c_int()
+    it = ctypes.c_longlong()
+    _check(load_library().lp_solve_noalloc(m, n, _ptr(A), _ptr(b), _ptr(c), int(sense),
+                                           ctypes.byref(opt) if opt else None, _ptr(x), _ptr(y),
+                                           ctypes.byref(obj), ctypes.byref(st),
+                                           ctypes.byref(it)))
+    return obj.value, st.value, it.value
 
 
 def lp_destroy(h) -> None:

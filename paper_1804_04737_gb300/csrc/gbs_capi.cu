@@ -111,6 +111,10 @@ double bits_to_double(unsigned long long b) {
 
 }  // namespace
 
+void gbs::set_last_error_global(const char *msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg);
+}
+
 extern "C" {
 
 void lp_options_default(lp_options *o) {

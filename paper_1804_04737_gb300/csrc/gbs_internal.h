@@ -86,6 +86,9 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,
                            int m, int n, long long P, int sense, double *x, double *y,
                            double *obj, cudaStream_t s);
+// Record the message returned by lp_last_error(NULL) (gbs_capi.cu).
+void set_last_error_global(const char *msg);
+
 cudaError_t launch_to_fp64(const float *T, long long P, int M, int N, double *out,
                            cudaStream_t s);
 
