@@ -32,6 +32,19 @@
  *             smallest (z_j > 0 ? z_j : 0) / (-T[r][j]) over T[r][j] < -eps_p,
  *             ties smallest j; none => LP_INFEASIBLE.
  *
+ * FP32 mode (LP_FP32_REINV; not in the paper): the tableau is FP32, which
+ * halves the bytes of the rank-1 update.  Every reinv_k pivots and at
+ * termination the library reinverts in FP64 from the original data: for the
+ * current basis B it computes x_B = B^-1 b, the duals and the objective row
+ * (c_B' B^-1 [A I] - [c 0]) and the objective, rounds them into the FP32
+ * tableau's rhs column and objective row, and reports the FP64 values as the
+ * solution.  An FP32 optimum is accepted only when these FP64 values are
+ * primal and dual feasible within the FP64 tolerances; otherwise pivoting
+ * continues (dual simplex from a dual-feasible basis, primal simplex from a
+ * primal-feasible one), and LP_NUMERICAL ends a run that does not converge.
+ * The body B^-1 A of the tableau stays FP32; its pivot sequence need not
+ * equal the FP64 one.
+ *
  * Conventions
  *   - Every call returns an lp_err; nothing throws across the ABI.  The
  *     message of the last error of a handle is lp_last_error(handle).
@@ -121,7 +134,8 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b,
 lp_err lp_solve(lp_handle *h);
 
 /* Enqueue the same work on the handle's stream and return without waiting;
- * lp_result (or a stream synchronisation) completes it. */
+ * lp_result (or a stream synchronisation) completes it.  In FP32 mode the
+ * host steers the reinversions, so this call waits like lp_solve. */
 lp_err lp_solve_async(lp_handle *h);
 
 /* Read the result of the last solve (waits for the handle's stream).
@@ -141,7 +155,8 @@ lp_err lp_get_tableau(lp_handle *h, double *T);
 /* Device time in milliseconds of the pivot kernel of the last solve, from
  * CUDA events recorded around its launch on the handle's stream (waits for
  * the stream).  *launches receives the number of pivot-kernel launches of
- * that solve (1 in FP64 mode). */
+ * that solve (1 in FP64 mode; one per reinversion period in FP32 mode, whose
+ * time is summed over them). */
 lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches);
 
 /* Allocation-free solve (the paper has no counterpart; this is a library

@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -60,6 +61,15 @@ struct lp_handle {
     LpDesc *pdesc = nullptr;
     double *pobj = nullptr;
     PivotShape shape{};
+    PivotShape shape_alt{};  // the other pivot rule (FP32 recovery), same strips
+
+    // FP32 mode: FP64 reinversion buffers and per-solve accounting
+    ReinvBufs rb{};
+    size_t cap_W = 0;       // doubles in rb.W
+    size_t cap_rb = 0;      // rows the index/vector buffers hold
+    double fp32_kernel_ms = 0.0, reinv_ms = 0.0;
+    int fp32_launches = 0, reinversions = 0;
+    double eps32_d = 0, eps32_p = 0, eps32_r = 0;
 };
 
 namespace {
@@ -153,10 +163,6 @@ lp_err lp_create(lp_handle **out, const lp_options *opt) {
         set_err(nullptr, "lp_create: unknown precision %d", o.precision);
         return LP_ERR_INVALID_ARG;
     }
-    if (o.precision == LP_FP32_REINV) {
-        set_err(nullptr, "lp_create: FP32 tableau mode is not available in this build");
-        return LP_ERR_INVALID_ARG;
-    }
     if (o.max_iters < 0 || o.bland_after < 0 || o.trace_cap < 0 || o.spin_timeout_cycles <= 0 ||
         o.threads < 0 || o.threads > 1024 || o.ctas < 0 || o.reinv_k < 1) {
         set_err(nullptr, "lp_create: option out of range");
@@ -211,6 +217,11 @@ void lp_destroy(lp_handle *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    void *rbufs[] = {h->rb.Lflag, h->rb.S, h->rb.R, h->rb.posS, h->rb.posR, h->rb.counts,
+                     h->rb.pivrow, h->rb.W, h->rb.xS, h->rb.yR, h->rb.zrow, h->rb.rhs, h->rb.chk,
+                     h->rb.bar};
+    for (void *p : rbufs)
+        if (p) cudaFree(p);
     void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dbasis, h->dscratch, h->dpart, h->dbar,
                     h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
     for (void *p : bufs)
@@ -247,15 +258,20 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
     const PivotShape sh = choose_shape(h->prec, (int)sense, M, N, P, h->sms, h->opt.threads,
                                        h->opt.ctas);
+    const PivotShape sh_alt = choose_shape(h->prec, 1 - (int)sense, M, N, P, h->sms,
+                                           h->opt.threads, h->opt.ctas);
 
     CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
     CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
     CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
     CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
     CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
-    if (!sh.use_smem)
-        CUDA_TRY(h, grow_bytes(&h->dscratch, &h->cap_scratch,
-                               (size_t)sh.ctas * (size_t)sh.scratch_stride));
+    {
+        size_t need = sh.use_smem ? 0 : (size_t)sh.ctas * (size_t)sh.scratch_stride;
+        if (h->prec == PREC_FP32 && !sh_alt.use_smem)
+            need = std::max(need, (size_t)sh_alt.ctas * (size_t)sh_alt.scratch_stride);
+        if (need) CUDA_TRY(h, grow_bytes(&h->dscratch, &h->cap_scratch, need));
+    }
     if (h->max_ctas < sh.ctas) {
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
@@ -299,6 +315,35 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     h->eps_p = h->opt.eps_p > 0 ? h->opt.eps_p : 1e-9 * std::max(1.0, amax);
     h->eps_r = h->opt.eps_r > 0 ? h->opt.eps_r : 1e-9 * std::max(1.0, bmax);
 
+    // FP32 tableau: the same tolerances as FP64.  A coarser pivot tolerance is
+    // wrong here: entries of the basis-inverse (slack) columns scale like
+    // 1/|A|, so a tolerance scaled by max|A| at FP32 resolution (1e-6) drops
+    // legitimate pivot rows and leads the FP32 run to an infeasible basis.
+    h->eps32_d = h->eps_d;
+    h->eps32_p = h->eps_p;
+    h->eps32_r = h->eps_r;
+    if (h->prec == PREC_FP32 && h->cap_rb < (size_t)(m > n ? m : n) + m) {
+        const size_t cap = (size_t)(m > n ? m : n) + m;
+        void **ints[] = {(void **)&h->rb.Lflag, (void **)&h->rb.S, (void **)&h->rb.R,
+                         (void **)&h->rb.posS, (void **)&h->rb.posR, (void **)&h->rb.pivrow};
+        for (void **q : ints) {
+            if (*q) cudaFree(*q);
+            *q = nullptr;
+            CUDA_TRY(h, cudaMalloc(q, cap * sizeof(int)));
+        }
+        void **dbl[] = {(void **)&h->rb.xS, (void **)&h->rb.yR, (void **)&h->rb.zrow,
+                        (void **)&h->rb.rhs};
+        for (void **q : dbl) {
+            if (*q) cudaFree(*q);
+            *q = nullptr;
+            CUDA_TRY(h, cudaMalloc(q, cap * sizeof(double)));
+        }
+        if (!h->rb.counts) CUDA_TRY(h, cudaMalloc(&h->rb.counts, 4 * sizeof(int)));
+        if (!h->rb.chk) CUDA_TRY(h, cudaMalloc(&h->rb.chk, sizeof(ReinvCheck)));
+        if (!h->rb.bar) CUDA_TRY(h, cudaMalloc(&h->rb.bar, 128 * sizeof(unsigned)));
+        h->cap_rb = cap;
+    }
+
     CUDA_TRY(h, launch_build(h->prec, h->dA, h->db, h->dc, m, n, (int)sense, h->dT, P, h->dbasis, s));
 
     LpDesc d{};
@@ -318,9 +363,9 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.N = N;
     d.sense = (int)sense;
     d.bland_after = h->opt.bland_after;
-    d.eps_d = h->eps_d;
-    d.eps_p = h->eps_p;
-    d.eps_r = h->eps_r;
+    d.eps_d = h->prec == PREC_FP64 ? h->eps_d : h->eps32_d;
+    d.eps_p = h->prec == PREC_FP64 ? h->eps_p : h->eps32_p;
+    d.eps_r = h->prec == PREC_FP64 ? h->eps_r : h->eps32_r;
     d.iters = 0;
     d.iter_limit = 0;
     d.deg = 0;
@@ -330,6 +375,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     *h->pdesc = d;
     h->desc = d;
     h->shape = sh;
+    h->shape_alt = sh_alt;
     h->m = m;
     h->n = n;
     h->M = M;
@@ -340,6 +386,163 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     return LP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+double okey_to_double(unsigned long long k) {
+    const unsigned long long bits = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    return d;
+}
+
+// FP64 reinversion of the current basis (gbs_reinv.cu); *zmin and *rmin
+// receive the smallest FP64 objective-row entry and rhs.
+lp_err reinvert(lp_handle *h, bool *singular, double *zmin, double *rmin) {
+    cudaStream_t s = h->stream;
+    const int m = h->m, n = h->n;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    CUDA_TRY(h, cudaEventRecord(e0, s));
+    CUDA_TRY(h, launch_reinv_lists(h->dbasis, m, n, h->rb, s));
+    int counts[2] = {0, 0};
+    CUDA_TRY(h, cudaMemcpyAsync(counts, h->rb.counts, sizeof counts, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    const int ns = counts[0];
+    if (counts[1] != ns) {
+        set_err(h, "reinversion: inconsistent basis (%d structural, %d free rows)", counts[0],
+                counts[1]);
+        return LP_ERR_STATE;
+    }
+    h->rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
+    const size_t need = (size_t)ns * (size_t)h->rb.Wp;
+    if (need > h->cap_W) {
+        if (h->rb.W) cudaFree(h->rb.W);
+        h->rb.W = nullptr;
+        h->cap_W = 0;
+        CUDA_TRY(h, cudaMalloc(&h->rb.W, std::max<size_t>(need, 1) * sizeof(double)));
+        h->cap_W = need;
+    }
+    CUDA_TRY(h, launch_reinv_solve(h->prec, h->dA, h->db, h->dc, h->sense, m, n, h->dbasis, h->rb,
+                                   ns, h->dT, h->P, h->dx, h->dy, h->dobj, h->sms,
+                                   h->opt.spin_timeout_cycles, s));
+    ReinvCheck chk;
+    CUDA_TRY(h, cudaMemcpyAsync(&chk, h->rb.chk, sizeof chk, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaEventRecord(e1, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->reinv_ms += t;
+    h->reinversions += 1;
+    *singular = chk.singular != 0;
+    *zmin = okey_to_double(chk.zmin_key);
+    *rmin = okey_to_double(chk.rhsmin_key);
+    return LP_OK;
+}
+
+// FP32 tableau with FP64 reinversion: pivot reinv_k pivots at a time in FP32,
+// reinvert in FP64 after each batch and at termination; an FP32 optimum is
+// accepted only when the FP64 values show it primal and dual feasible.
+lp_err solve_fp32(lp_handle *h) {
+    cudaStream_t s = h->stream;
+    long long remaining = h->opt.max_iters;
+    // Guard against FP32 runs that stop making progress: at most this many
+    // pivots per solve call before LP_NUMERICAL.
+    long long guard = 20ll * (h->m + h->n) + 1000;
+    int failed_checks = 0;
+    int rule = h->sense;  // 0: primal simplex, 1: dual simplex
+    lp_status final = LP_NOT_SOLVED;
+    h->fp32_kernel_ms = 0.0;
+    h->fp32_launches = 0;
+    h->reinv_ms = 0.0;
+    h->reinversions = 0;
+    for (;;) {
+        const PivotShape &sh = rule == h->sense ? h->shape : h->shape_alt;
+        const long long budget = std::min<long long>(remaining, (long long)h->opt.reinv_k);
+        const long long before = h->pdesc->iters;
+        const long long stride = sh.scratch_stride;
+        CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, scratch_stride), &stride,
+                                    sizeof stride, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, 128 * sizeof(unsigned), s));
+        CUDA_TRY(h, cudaEventRecord(h->ev0, s));
+        CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, sh, h->opt.spin_timeout_cycles, budget, s));
+        CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+        CUDA_TRY(h, cudaMemcpyAsync(h->pdesc, h->ddesc, sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, h->ev0, h->ev1);
+        h->fp32_kernel_ms += t;
+        h->fp32_launches += 1;
+        remaining -= h->pdesc->iters - before;
+        guard -= h->pdesc->iters - before;
+        const int st = h->pdesc->status;
+        if (st == LP_TIMEOUT) {
+            final = LP_TIMEOUT;
+            break;
+        }
+        bool singular = false;
+        double zmin = 0.0, rmin = 0.0;
+        lp_err e = reinvert(h, &singular, &zmin, &rmin);
+        if (e != LP_OK) return e;
+        if (singular) {
+            final = LP_NUMERICAL;
+            break;
+        }
+        const bool pfeas = rmin >= -h->eps_r, dfeas = zmin >= -h->eps_d;
+        if (st == LP_OPTIMAL) {
+            if (pfeas && dfeas) {
+                final = LP_OPTIMAL;
+                break;
+            }
+            if ((!pfeas && !dfeas) || ++failed_checks > 4) {
+                final = LP_NUMERICAL;
+                break;
+            }
+            // The FP32 run stopped at a basis the FP64 values reject.  From a
+            // dual-feasible basis the dual simplex restores primal
+            // feasibility, from a primal-feasible one the primal simplex
+            // restores optimality; price with the FP64 tolerances on the
+            // refreshed rhs and objective row.
+            rule = pfeas ? 0 : 1;
+            const double eps[3] = {h->eps_d, h->eps_p, h->eps_r};
+            CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, eps_d), eps,
+                                        sizeof eps, cudaMemcpyHostToDevice, s));
+            continue;
+        }
+        if (st == LP_UNBOUNDED || st == LP_INFEASIBLE) {
+            final = (lp_status)st;
+            break;
+        }
+        if (remaining <= 0) {  // ITER_LIMIT
+            final = LP_ITER_LIMIT;
+            break;
+        }
+        if (guard <= 0) {
+            final = LP_NUMERICAL;
+            break;
+        }
+        // periodic reinversion: when the FP64 values show the current rule's
+        // invariant lost (primal simplex: feasible rhs; dual simplex:
+        // nonnegative reduced costs) and the other rule's invariant holding,
+        // continue with the other rule
+        if (rule == 0 && !pfeas && dfeas) rule = 1;
+        else if (rule == 1 && !dfeas && pfeas) rule = 0;
+    }
+    h->pdesc->status = final;
+    CUDA_TRY(h, cudaMemcpyAsync(h->pobj, h->dobj, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    h->solved = true;
+    return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 lp_err lp_solve_async(lp_handle *h) {
     if (!h) return LP_ERR_INVALID_ARG;
     if (!h->loaded) {
@@ -347,6 +550,7 @@ lp_err lp_solve_async(lp_handle *h) {
         return LP_ERR_STATE;
     }
     CUDA_TRY(h, cudaSetDevice(h->device));
+    if (h->prec == PREC_FP32) return solve_fp32(h);
     cudaStream_t s = h->stream;
     // The pivot state (iterations, degeneracy counter) lives in the device
     // descriptor, so consecutive calls resume without a host round trip.
@@ -395,6 +599,11 @@ lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches) {
         return LP_ERR_STATE;
     }
     CUDA_TRY(h, cudaSetDevice(h->device));
+    if (h->prec == PREC_FP32) {
+        if (ms) *ms = h->fp32_kernel_ms;
+        if (launches) *launches = h->fp32_launches;
+        return LP_OK;
+    }
     CUDA_TRY(h, cudaEventSynchronize(h->ev1));
     float t = 0.0f;
     CUDA_TRY(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));

@@ -86,6 +86,32 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,
                            int m, int n, long long P, int sense, double *x, double *y,
                            double *obj, cudaStream_t s);
+// Buffers of the FP64 reinversion (gbs_reinv.cu), owned by the handle.
+struct ReinvCheck {
+    unsigned long long zmin_key;    // okey of the smallest objective-row entry
+    unsigned long long rhsmin_key;  // okey of the smallest rhs
+    int singular;                   // the basis matrix had no pivot in some column
+    int pad_;
+};
+struct ReinvBufs {
+    int *Lflag, *S, *R, *posS, *posR, *counts, *pivrow;
+    double *W;          // s x Wp Gauss-Jordan system [A_RS | b_R | I]
+    long long Wp;
+    double *xS, *yR, *zrow, *rhs;
+    ReinvCheck *chk;
+    unsigned *bar;      // barrier words for the Gauss-Jordan grid
+};
+
+cudaError_t launch_reinv_lists(const int *basis, int m, int n, const ReinvBufs &rb,
+                               cudaStream_t s);
+// Everything after the lists, for ns structural basics (W sized for ns).
+// Writes the FP64 solution (x, y, obj), the refreshed rhs column and
+// objective row of T and the check minima.
+cudaError_t launch_reinv_solve(int prec, const double *A, const double *b, const double *c,
+                               int sense, int m, int n, const int *basis, const ReinvBufs &rb,
+                               int ns, void *T, long long P, double *x, double *y, double *obj,
+                               int sms, long long spin_limit, cudaStream_t s);
+
 // Record the message returned by lp_last_error(NULL) (gbs_capi.cu).
 void set_last_error_global(const char *msg);
 
