@@ -108,6 +108,8 @@ typedef struct {
     int device;              /* CUDA device ordinal                               */
     int ctas;                /* CTAs of the persistent grid, 0 = auto             */
     long long trace_cap;     /* record (row, column) of the first trace_cap pivots */
+    long long group_elems;   /* batched solves: tableau elements per CTA of an LP's
+                                group, 0 = 262144 (see lp_solve_batch)            */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
@@ -158,6 +160,30 @@ lp_err lp_get_tableau(lp_handle *h, double *T);
  * that solve (1 in FP64 mode; one per reinversion period in FP32 mode, whose
  * time is summed over them). */
 lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches);
+
+/* Batched solve of `count` independent LPs in one persistent launch (the
+ * paper solves one LP at a time; batching many uneven LPs is a library
+ * service).  LP k is m[k] x n[k] with inputs A[k] (row-major), b[k], c[k]
+ * (all host or all device memory) and form sense[k] (NULL: all LP_MAX_LE).
+ * Each LP is pivoted by a group of CTAs sized to its tableau
+ * (opt->group_elems elements per CTA); CTAs take (LP, rank) work items from a
+ * queue, largest LPs first.  Per-LP arithmetic is the single-LP path's, so
+ * each result equals solving that LP alone bit for bit.  Outputs per LP:
+ * obj[k], status[k], iters[k] and, when x / y and x[k] / y[k] are non-NULL,
+ * the primal and dual vectors (host memory).  FP64 only; opt->threads caps
+ * the CTA size at 512; device memory is pooled per device between calls.
+ * Blocking.  Errors as lp_load (the message names the LP), in
+ * lp_last_error(NULL). */
+lp_err lp_solve_batch(int count, const int *m, const int *n, const double *const *A,
+                      const double *const *b, const double *const *c, const int *sense,
+                      const lp_options *opt, double *obj, lp_status *status, long long *iters,
+                      double *const *x, double *const *y);
+
+/* Figures of the last lp_solve_batch in this process: device time of the
+ * batched pivot kernel, total pivots, CTAs launched, CTA size and the largest
+ * group. */
+lp_err lp_batch_stats(double *kernel_ms, long long *pivots, int *ctas, int *threads,
+                      int *max_group);
 
 /* Allocation-free solve (the paper has no counterpart; this is a library
  * service).  Solves one FP64 LP like lp_create + lp_load + lp_solve +

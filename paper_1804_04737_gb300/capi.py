@@ -45,6 +45,7 @@ class lp_options(ctypes.Structure):
         ("device", ctypes.c_int),
         ("ctas", ctypes.c_int),
         ("trace_cap", ctypes.c_longlong),
+        ("group_elems", ctypes.c_longlong),
     ]
 
 
@@ -79,6 +80,14 @@ _SIGS = [
                                         ctypes.c_void_p, _c_double_p,
                                         ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_longlong)]),
+    ("lp_solve_batch", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.POINTER(lp_options),
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    ("lp_batch_stats", ctypes.c_int, [_c_double_p, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
     ("lp_destroy", None, [ctypes.c_void_p]),
     ("lp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lp_version", ctypes.c_char_p, []),
@@ -209,6 +218,45 @@ def lp_solve_noalloc(A, b, c, sense=LP_MAX_LE, opt: Optional[lp_options] = None,
                                            ctypes.byref(obj), ctypes.byref(st),
                                            ctypes.byref(it)))
     return obj.value, st.value, it.value
+
+
+def lp_solve_batch(lps, opt: Optional[lp_options] = None, want_xy=False):
+    """Solve a list of (A, b, c, sense) in one batched launch.
+
+    A, b, c may be numpy arrays or (all) CUDA tensors.  Returns (obj, status,
+    iters) arrays and, with want_xy, lists of x and y arrays."""
+    k = len(lps)
+    m = np.array([int(L[0].shape[0]) for L in lps], dtype=np.int32)
+    n = np.array([int(L[0].shape[1]) for L in lps], dtype=np.int32)
+    ptrs = [(_ptr(L[0]), _ptr(L[1]), _ptr(L[2])) for L in lps]
+    Ap = (ctypes.c_void_p * k)(*[p[0].value for p in ptrs])
+    bp = (ctypes.c_void_p * k)(*[p[1].value for p in ptrs])
+    cp = (ctypes.c_void_p * k)(*[p[2].value for p in ptrs])
+    sense = np.array([int(L[3]) if len(L) > 3 else LP_MAX_LE for L in lps], dtype=np.int32)
+    obj = np.empty(k)
+    st = np.empty(k, dtype=np.int32)
+    it = np.empty(k, dtype=np.int64)
+    xs = ys = None
+    xp = yp = None
+    if want_xy:
+        xs = [np.empty(int(v)) for v in n]
+        ys = [np.empty(int(v)) for v in m]
+        xp = (ctypes.c_void_p * k)(*[a.ctypes.data for a in xs])
+        yp = (ctypes.c_void_p * k)(*[a.ctypes.data for a in ys])
+    _check(load_library().lp_solve_batch(k, m.ctypes.data, n.ctypes.data, Ap, bp, cp,
+                                         sense.ctypes.data, ctypes.byref(opt) if opt else None,
+                                         obj.ctypes.data, st.ctypes.data, it.ctypes.data, xp, yp))
+    return (obj, st, it, xs, ys) if want_xy else (obj, st, it)
+
+
+def lp_batch_stats():
+    """(kernel_ms, pivots, ctas, threads, max_group) of the last batched solve."""
+    ms = ctypes.c_double()
+    pv = ctypes.c_longlong()
+    ct, th, mg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().lp_batch_stats(ctypes.byref(ms), ctypes.byref(pv), ctypes.byref(ct),
+                                         ctypes.byref(th), ctypes.byref(mg)))
+    return ms.value, pv.value, ct.value, th.value, mg.value
 
 
 def lp_destroy(h) -> None:

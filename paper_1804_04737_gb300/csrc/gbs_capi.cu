@@ -143,6 +143,7 @@ void lp_options_default(lp_options *o) {
     o->device = 0;
     o->ctas = 0;
     o->trace_cap = 0;
+    o->group_elems = 0;
 }
 
 const char *lp_version(void) { return "gbsimplex 0.1 (sm_103a)"; }

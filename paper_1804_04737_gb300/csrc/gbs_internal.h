@@ -50,6 +50,8 @@ struct LpDesc {
     int deg;               // consecutive zero-ratio pivots
     int status;
     int last_p, last_q;
+    // batched launches: CTAs per LP and their column strip width
+    int group, strip;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
@@ -83,6 +85,11 @@ PivotShape choose_shape(int prec, int sense, int M, int N, long long P, int sms,
                         int ctas);
 cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long long spin_limit,
                          long long budget, cudaStream_t s);
+// Batched persistent launch over nitems (lp, rank) work items (gbs_pivot.cu).
+cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems, unsigned *queue,
+                         int ctas, int threads, size_t smem, int use_smem, long long spin_limit,
+                         long long budget, cudaStream_t s);
+int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, int sms);
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,
                            int m, int n, long long P, int sense, double *x, double *y,
                            double *obj, cudaStream_t s);

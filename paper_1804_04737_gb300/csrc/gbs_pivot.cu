@@ -95,18 +95,24 @@ __device__ __forceinline__ V pivot_vec(const V &t, int i, int p, T col_i, const 
 // SMEM: the selection scratch lives in shared memory (else in this CTA's
 // slice of global scratch); DUAL: dual simplex (else primal).  Template
 // parameters, so that the update loop carries no per-row tests for them.
+//
+// solve_lp runs the pivots of one LP on a group of G co-resident CTAs (this
+// CTA is rank g of the group); the group's barrier words, reader counter,
+// partials and timeout flag live in the LP's descriptor.  The single-LP
+// kernel below is one group spanning the grid; the batched kernel forms groups
+// from a work queue.
 template <typename T, bool SMEM, bool DUAL>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+__device__ __forceinline__ void solve_lp(LpDesc *__restrict__ d, int G, int g, int W,
+                                         long long spin_limit, long long budget,
+                                         unsigned char *smem_raw) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
     constexpr int sense = DUAL ? 1 : 0;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Cand rbuf[4][32];
     __shared__ unsigned long long ubuf[32];
     __shared__ int s_flag;
 
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+    const int tid = threadIdx.x, B = blockDim.x;
     T *__restrict__ Tab = reinterpret_cast<T *>(d->T);
     int *__restrict__ basis = d->basis;
     const long long P = d->P;
@@ -369,6 +375,42 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
 }
 
+template <typename T, bool SMEM, bool DUAL>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    pivot_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    solve_lp<T, SMEM, DUAL>(d, gridDim.x, blockIdx.x, W, spin_limit, budget, smem_raw);
+}
+
+// Many LPs in one persistent launch.  items[] lists (lp, rank) pairs, the
+// ranks of one LP consecutive, largest LPs first; CTAs pop items in order
+// from *queue, and the d->group CTAs that pop the ranks of one LP solve it
+// together.  A group waits only on CTAs that hold earlier items, whose groups
+// are complete, so every group forms (the launch has at least max(group)
+// co-resident CTAs); all waits are bounded anyway.
+constexpr int kBatchThreads = 512;  // register room for both pivot rules in one kernel
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(kBatchThreads)
+    batch_kernel(LpDesc *__restrict__ descs, const int2 *__restrict__ items, int nitems,
+                 unsigned *queue, long long spin_limit, long long budget) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 w = items[it];
+        LpDesc *d = descs + w.x;
+        if (d->sense)
+            solve_lp<T, SMEM, true>(d, d->group, w.y, d->strip, spin_limit, budget, smem_raw);
+        else
+            solve_lp<T, SMEM, false>(d, d->group, w.y, d->strip, spin_limit, budget, smem_raw);
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double block_max(double v, double *red) {
@@ -598,6 +640,37 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
     // A cooperative launch fails instead of running when the grid cannot be
     // co-resident, which the grid barrier needs.
     return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
+}
+
+cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems, unsigned *queue,
+                         int ctas, int threads, size_t smem, int use_smem, long long spin_limit,
+                         long long budget, cudaStream_t s) {
+    void *args[] = {&descs, &items, &nitems, &queue, &spin_limit, &budget};
+    const void *fn;
+    if (prec == PREC_FP64)
+        fn = use_smem ? (const void *)batch_kernel<double, true> : (const void *)batch_kernel<double, false>;
+    else
+        fn = use_smem ? (const void *)batch_kernel<float, true> : (const void *)batch_kernel<float, false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
+}
+
+int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, int sms) {
+    const void *fn;
+    if (prec == PREC_FP64)
+        fn = use_smem ? (const void *)batch_kernel<double, true> : (const void *)batch_kernel<double, false>;
+    else
+        fn = use_smem ? (const void *)batch_kernel<float, true> : (const void *)batch_kernel<float, false>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
 }
 
 cudaError_t launch_extract(int prec, const LpDesc *, const void *T, const int *basis, int m,
