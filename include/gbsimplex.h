@@ -179,6 +179,46 @@ lp_err lp_solve_batch(int count, const int *m, const int *n, const double *const
                       const lp_options *opt, double *obj, lp_status *status, long long *iters,
                       double *const *x, double *const *y);
 
+/* Autotuner for lp_solve_batch: times every candidate launch shape
+ * (group_elems in {16K, 64K, 256K, 1M} x threads in {256, 512}) on this
+ * batch, best of two solves each, and returns in *best a copy of *opt (NULL:
+ * defaults) with the fastest group_elems and threads.  With a non-NULL
+ * cache_path the choice is looked up in / appended to that text file, keyed
+ * by the batch size and a hash of its sorted shapes. */
+lp_err lp_batch_autotune(int count, const int *m, const int *n, const double *const *A,
+                         const double *const *b, const double *const *c, const int *sense,
+                         const lp_options *opt, const char *cache_path, lp_options *best);
+
+/* Serving with continuous batching (a library service; the paper solves one
+ * LP at a time).  A server owns an HBM budget (one arena, first-fit
+ * allocation) and up to max_slots LPs in flight.  Requests are admitted in
+ * arrival order as slots and memory free up; admitted LPs are built, pivoted
+ * and read off by a persistent kernel that takes new LPs while others are
+ * running, so their work overlaps on the GPU.  Each LP runs on a group of
+ * CTAs with the single-LP pivot code, so its result equals solving it alone
+ * bit for bit.  FP64; m, n <= 4096; inputs and outputs in host memory.
+ * submit copies the inputs and returns a ticket at once; poll / wait return
+ * the result and the submit-to-completion latency in milliseconds (wait
+ * returns LP_ERR_BUSY on timeout).  A request whose inputs fail the checks of
+ * lp_load completes with that error.  create / destroy are not thread-safe;
+ * submit, poll, wait and stats may be called from any thread. */
+typedef struct lp_server lp_server;
+lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budget_bytes,
+                        int max_slots);
+lp_err lp_server_submit(lp_server *srv, int m, int n, const double *A, const double *b,
+                        const double *c, lp_sense sense, unsigned long long *ticket);
+lp_err lp_server_poll(lp_server *srv, unsigned long long ticket, int *done, double *x, double *y,
+                      double *obj, lp_status *status, long long *iters, double *latency_ms);
+lp_err lp_server_wait(lp_server *srv, unsigned long long ticket, double timeout_s, double *x,
+                      double *y, double *obj, lp_status *status, long long *iters,
+                      double *latency_ms);
+/* Requests completed, kernel launches so far, HBM bytes in use, requests
+ * waiting for admission. */
+lp_err lp_server_stats(lp_server *srv, long long *completed, long long *launches,
+                       size_t *hbm_used, int *queued);
+/* Finishes the requests in flight, then frees everything.  NULL allowed. */
+void lp_server_destroy(lp_server *srv);
+
 /* Figures of the last lp_solve_batch in this process: device time of the
  * batched pivot kernel, total pivots, CTAs launched, CTA size and the largest
  * group. */

@@ -88,6 +88,29 @@ _SIGS = [
     ("lp_batch_stats", ctypes.c_int, [_c_double_p, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
+    ("lp_batch_autotune", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(lp_options),
+                                         ctypes.c_char_p, ctypes.POINTER(lp_options)]),
+    ("lp_server_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(lp_options), ctypes.c_size_t,
+                                        ctypes.c_int]),
+    ("lp_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]),
+    ("lp_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                                      ctypes.c_void_p, _c_double_p, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_longlong), _c_double_p]),
+    ("lp_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_double,
+                                      ctypes.c_void_p, ctypes.c_void_p, _c_double_p,
+                                      ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_longlong), _c_double_p]),
+    ("lp_server_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_int)]),
+    ("lp_server_destroy", None, [ctypes.c_void_p]),
     ("lp_destroy", None, [ctypes.c_void_p]),
     ("lp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lp_version", ctypes.c_char_p, []),
@@ -249,6 +272,25 @@ def lp_solve_batch(lps, opt: Optional[lp_options] = None, want_xy=False):
     return (obj, st, it, xs, ys) if want_xy else (obj, st, it)
 
 
+def lp_batch_autotune(lps, opt: Optional[lp_options] = None, cache_path=None) -> lp_options:
+    """Fastest batched launch shape for this batch (see the C declaration)."""
+    k = len(lps)
+    m = np.array([int(L[0].shape[0]) for L in lps], dtype=np.int32)
+    n = np.array([int(L[0].shape[1]) for L in lps], dtype=np.int32)
+    ptrs = [(_ptr(L[0]), _ptr(L[1]), _ptr(L[2])) for L in lps]
+    Ap = (ctypes.c_void_p * k)(*[p[0].value for p in ptrs])
+    bp = (ctypes.c_void_p * k)(*[p[1].value for p in ptrs])
+    cp = (ctypes.c_void_p * k)(*[p[2].value for p in ptrs])
+    sense = np.array([int(L[3]) if len(L) > 3 else LP_MAX_LE for L in lps], dtype=np.int32)
+    best = lp_options()
+    _check(load_library().lp_batch_autotune(k, m.ctypes.data, n.ctypes.data, Ap, bp, cp,
+                                            sense.ctypes.data,
+                                            ctypes.byref(opt) if opt else None,
+                                            cache_path.encode() if cache_path else None,
+                                            ctypes.byref(best)))
+    return best
+
+
 def lp_batch_stats():
     """(kernel_ms, pivots, ctas, threads, max_group) of the last batched solve."""
     ms = ctypes.c_double()
@@ -257,6 +299,60 @@ def lp_batch_stats():
     _check(load_library().lp_batch_stats(ctypes.byref(ms), ctypes.byref(pv), ctypes.byref(ct),
                                          ctypes.byref(th), ctypes.byref(mg)))
     return ms.value, pv.value, ct.value, th.value, mg.value
+
+
+def lp_server_create(opt: Optional[lp_options] = None, hbm_budget_bytes=60 << 30,
+                     max_slots=256):
+    srv = ctypes.c_void_p()
+    _check(load_library().lp_server_create(ctypes.byref(srv), ctypes.byref(opt) if opt else None,
+                                           int(hbm_budget_bytes), int(max_slots)))
+    return srv
+
+
+def lp_server_submit(srv, A, b, c, sense=LP_MAX_LE) -> int:
+    """Queue one LP (host arrays); returns its ticket."""
+    t = ctypes.c_ulonglong()
+    _check(load_library().lp_server_submit(srv, int(A.shape[0]), int(A.shape[1]), _ptr(A),
+                                           _ptr(b), _ptr(c), int(sense), ctypes.byref(t)))
+    return t.value
+
+
+def _server_out(m, n):
+    return (np.empty(n), np.empty(m), ctypes.c_double(), ctypes.c_int(), ctypes.c_longlong(),
+            ctypes.c_double())
+
+
+def lp_server_wait(srv, ticket, m, n, timeout_s=60.0):
+    """(obj, status, iters, x, y, latency_ms) of a ticket, waiting for it."""
+    x, y, obj, st, it, lat = _server_out(m, n)
+    _check(load_library().lp_server_wait(srv, ticket, float(timeout_s), _ptr(x), _ptr(y),
+                                         ctypes.byref(obj), ctypes.byref(st), ctypes.byref(it),
+                                         ctypes.byref(lat)))
+    return obj.value, st.value, it.value, x, y, lat.value
+
+
+def lp_server_poll(srv, ticket, m, n):
+    """None while pending, else (obj, status, iters, x, y, latency_ms)."""
+    x, y, obj, st, it, lat = _server_out(m, n)
+    done = ctypes.c_int()
+    _check(load_library().lp_server_poll(srv, ticket, ctypes.byref(done), _ptr(x), _ptr(y),
+                                         ctypes.byref(obj), ctypes.byref(st), ctypes.byref(it),
+                                         ctypes.byref(lat)))
+    return (obj.value, st.value, it.value, x, y, lat.value) if done.value else None
+
+
+def lp_server_stats(srv):
+    """(completed, kernel launches, HBM bytes in use, requests queued)."""
+    c, l, q = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+    u = ctypes.c_size_t()
+    _check(load_library().lp_server_stats(srv, ctypes.byref(c), ctypes.byref(l), ctypes.byref(u),
+                                          ctypes.byref(q)))
+    return c.value, l.value, u.value, q.value
+
+
+def lp_server_destroy(srv) -> None:
+    if srv is not None:
+        load_library().lp_server_destroy(srv)
 
 
 def lp_destroy(h) -> None:

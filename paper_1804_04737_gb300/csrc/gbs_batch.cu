@@ -528,3 +528,103 @@ extern "C" lp_err lp_batch_stats(double *kernel_ms, long long *pivots, int *ctas
     if (max_group) *max_group = g_last.max_group;
     return LP_OK;
 }
+
+// ------------------------------------------------------------- autotuner --
+//
+// Picks the batched launch shape (tableau elements per CTA of a group, CTA
+// size) for a batch by timing every candidate on the batch itself (the best
+// of two solves each, batched pivot kernel time).  Results are cached in a
+// text file, one line "key group_elems threads kernel_ms" per batch
+// signature (count and a hash of the sorted shapes), so a serving process
+// tunes once per workload mix.
+
+namespace {
+
+unsigned long long shape_signature(int count, const int *m, const int *n) {
+    std::vector<unsigned long long> v(count);
+    for (int k = 0; k < count; ++k) v[k] = ((unsigned long long)m[k] << 32) | (unsigned)n[k];
+    std::sort(v.begin(), v.end());
+    unsigned long long h = 1469598103934665603ull;  // FNV-1a
+    for (unsigned long long x : v)
+        for (int i = 0; i < 8; ++i) {
+            h ^= (x >> (8 * i)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    return h;
+}
+
+bool cache_lookup(const char *path, const char *key, long long *ge, int *th) {
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[128];
+    long long g;
+    int t;
+    double ms;
+    bool hit = false;
+    while (fscanf(f, "%127s %lld %d %lf", k, &g, &t, &ms) == 4)
+        if (!strcmp(k, key)) {
+            *ge = g;
+            *th = t;
+            hit = true;
+        }
+    fclose(f);
+    return hit;
+}
+
+}  // namespace
+
+extern "C" lp_err lp_batch_autotune(int count, const int *m, const int *n,
+                                    const double *const *A, const double *const *b,
+                                    const double *const *c, const int *sense,
+                                    const lp_options *opt, const char *cache_path,
+                                    lp_options *best) {
+    if (!best) return bfail(LP_ERR_INVALID_ARG, "lp_batch_autotune: best is NULL");
+    lp_options o;
+    if (opt) o = *opt; else lp_options_default(&o);
+    if (count < 1 || !m || !n) return bfail(LP_ERR_INVALID_ARG, "lp_batch_autotune: empty batch");
+    char key[128];
+    snprintf(key, sizeof key, "fp64-c%d-%016llx", count, shape_signature(count, m, n));
+    long long ge = 0;
+    int th = 0;
+    if (cache_lookup(cache_path, key, &ge, &th)) {
+        *best = o;
+        best->group_elems = ge;
+        best->threads = th;
+        return LP_OK;
+    }
+    static const long long kElems[] = {16384, 65536, 262144, 1048576};
+    static const int kThreads[] = {256, 512};
+    double best_ms = 1e300;
+    for (long long e : kElems)
+        for (int t : kThreads) {
+            lp_options trial = o;
+            trial.group_elems = e;
+            trial.threads = t;
+            double ms = 1e300;
+            for (int rep = 0; rep < 2; ++rep) {
+                lp_err r = lp_solve_batch(count, m, n, A, b, c, sense, &trial, nullptr, nullptr,
+                                          nullptr, nullptr, nullptr);
+                if (r != LP_OK) return r;
+                double k_ms = 0.0;
+                lp_batch_stats(&k_ms, nullptr, nullptr, nullptr, nullptr);
+                ms = std::min(ms, k_ms);
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                ge = e;
+                th = t;
+            }
+        }
+    *best = o;
+    best->group_elems = ge;
+    best->threads = th;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s %lld %d %.4f\n", key, ge, th, best_ms);
+            fclose(f);
+        }
+    }
+    return LP_OK;
+}

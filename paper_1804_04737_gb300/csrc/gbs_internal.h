@@ -119,6 +119,41 @@ cudaError_t launch_reinv_solve(int prec, const double *A, const double *b, const
                                int ns, void *T, long long P, double *x, double *y, double *obj,
                                int sms, long long spin_limit, cudaStream_t s);
 
+// ------------------------------------------------------------- serving --
+// One admitted LP of the server (device memory, written by the host before
+// the slot is marked ready).
+struct ServeSlot {
+    LpDesc d;                    // T, basis, partials, barrier words, sizes, group, strip
+    const double *A, *b, *c;     // inputs copied to the device
+    double *x, *y, *obj;         // outputs (device)
+    InputStats *stats;           // zeroed by the host
+    double opt_eps_d, opt_eps_p, opt_eps_r;  // > 0: caller's tolerances
+    long long budget;            // pivot limit
+};
+constexpr int kServeQueue = 1 << 16;  // work-item ring
+// Device-side control block of the server kernel.
+struct ServeCtl {
+    unsigned head;       // worker tickets taken
+    unsigned tail;       // items published by the dispatcher
+    int in_flight;       // slots dispatched and not yet completed
+    int err;             // a bounded wait ran out
+    int2 items[kServeQueue];
+    unsigned seq[kServeQueue];  // item t is published when seq[t % Q] == t + 1
+};
+// Host-device ring in mapped pinned host memory.
+constexpr int kServeMaxSlots = 4096;
+struct ServeRing {
+    int rq[kServeMaxSlots];    // slots made ready by the host, in order
+    int rq_tail;               // host: entries of rq written
+    int rq_head;               // dispatcher: entries of rq consumed
+    int done[kServeMaxSlots];  // device: 1 = slot finished; host: back to 0
+    int shutdown;              // host: exit as soon as idle
+};
+cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing *ring_dev,
+                          int ctas, int threads, size_t smem, long long spin_limit,
+                          long long idle_limit, cudaStream_t s);
+int max_coresident_server_ctas(int threads, size_t smem, int sms);
+
 // Record the message returned by lp_last_error(NULL) (gbs_capi.cu).
 void set_last_error_global(const char *msg);
 

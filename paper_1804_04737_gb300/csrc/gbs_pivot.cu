@@ -390,6 +390,244 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // co-resident CTAs); all waits are bounded anyway.
 constexpr int kBatchThreads = 512;  // register room for both pivot rules in one kernel
 
+// ---------------------------------------------------------------------------
+// Serving: continuous batching in one persistent kernel.
+//
+// CTA 0 dispatches: it reads the slots the host made ready from a ring in
+// mapped host memory and publishes, for each, `group` consecutive work items
+// (slot, rank) into a device ring.  The other CTAs are workers: each takes a
+// ticket, waits until the item of that ticket is published, and runs that
+// rank of the slot's group; the group computes the input statistics and
+// tolerances, builds the tableau (Sec. 2 Step 1), pivots with the same code
+// as every other path, reads the solution off and marks the slot done in the
+// host ring.  Requests that arrive while others are on the GPU are dispatched
+// as soon as the host has a slot and memory for them, so their pivots overlap
+// with the ones in flight.  When nothing arrives for idle_limit cycles and no
+// slot is in flight, the dispatcher hands every worker an exit item and the
+// kernel ends; the host relaunches it on the next request.  While busy but
+// without new requests it hands waiting workers no-op items every idle_limit/2
+// cycles, so no worker's bounded wait runs out during a long solve.
+
+__device__ __forceinline__ int ld_acq_sys(const int *p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel_sys(int *p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ void serve_dispatch(ServeSlot *slots, ServeCtl *ctl, ServeRing *ring, int workers,
+                               long long idle_limit) {
+    if (threadIdx.x != 0) return;
+    const long long keepalive = idle_limit / 2;
+    long long idle0 = clock64(), alive0 = idle0;
+    unsigned tail = ctl->tail;
+    auto publish = [&](int slot, int rank) {
+        ctl->items[tail % kServeQueue] = make_int2(slot, rank);
+        __threadfence();
+        st_release(&ctl->seq[tail % kServeQueue], tail + 1u);
+        ++tail;
+    };
+    for (;;) {
+        const int rq_tail = ld_acq_sys(&ring->rq_tail);
+        int rq_head = *(volatile int *)&ring->rq_head;
+        bool any = false;
+        while (rq_head != rq_tail) {
+            const int s = *(volatile int *)&ring->rq[rq_head % kServeMaxSlots];
+            const int G = *(volatile int *)&slots[s].d.group;
+            atomicAdd(&ctl->in_flight, 1);
+            for (int r = 0; r < G; ++r) publish(s, r);
+            ++rq_head;
+            st_rel_sys(&ring->rq_head, rq_head);
+            any = true;
+        }
+        const long long now = clock64();
+        if (any) {
+            idle0 = alive0 = now;
+        } else if (*(volatile int *)&ctl->err ||
+                   (*(volatile int *)&ctl->in_flight == 0 &&
+                    (ld_acq_sys(&ring->shutdown) || now - idle0 > idle_limit))) {
+            break;
+        } else {
+            if (now - alive0 > keepalive) {
+                // hand every worker waiting on a ticket a no-op item, which
+                // restarts its bounded wait
+                const unsigned head = *(volatile unsigned *)&ctl->head;
+                while ((int)(head - tail) > 0) publish(-2, 0);
+                alive0 = now;
+            }
+            __nanosleep(200);
+        }
+    }
+    for (int k = 0; k < workers; ++k) publish(-1, 0);
+    ctl->tail = tail;
+}
+
+__device__ __forceinline__ double block_max_dev(double v, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmax(r, red[k]);
+    return r;
+}
+
+__device__ void serve_slot(ServeSlot *S, int slot, int rank, ServeCtl *ctl, ServeRing *ring,
+                           long long spin_limit, unsigned char *smem_raw) {
+    __shared__ double red[32];
+    __shared__ int s_flag, s_fl;
+    LpDesc *d = &S->d;
+    const int G = d->group, m = d->m, n = d->n, M = d->M, N = d->N, tid = threadIdx.x,
+              B = blockDim.x;
+    const long long P = d->P;
+    const int sense = d->sense;
+    // input statistics over this rank's slice
+    {
+        double amax = 0.0, bmax = 0.0, cmax = 0.0;
+        int fl = 0;
+        const long long L = (long long)m * n;
+        const long long a0 = L * rank / G, a1 = L * (rank + 1) / G;
+        for (long long e = a0 + tid; e < a1; e += B) {
+            const double v = S->A[e];
+            if (!isfinite(v)) fl |= 4; else amax = fmax(amax, fabs(v));
+        }
+        for (int i = (int)((long long)m * rank / G) + tid; i < (int)((long long)m * (rank + 1) / G); i += B) {
+            const double v = S->b[i];
+            if (!isfinite(v)) fl |= 4; else bmax = fmax(bmax, fabs(v));
+            if (v < 0.0) fl |= 1;
+        }
+        for (int j = (int)((long long)n * rank / G) + tid; j < (int)((long long)n * (rank + 1) / G); j += B) {
+            const double v = S->c[j];
+            if (!isfinite(v)) fl |= 4; else cmax = fmax(cmax, fabs(v));
+            if (v < 0.0) fl |= 2;
+        }
+        if (tid == 0) s_fl = 0;
+        __syncthreads();
+        if (fl) atomicOr(&s_fl, fl);
+        amax = block_max_dev(amax, red);
+        bmax = block_max_dev(bmax, red);
+        cmax = block_max_dev(cmax, red);
+        if (tid == 0) {
+            if (amax > 0.0) atomicMax(&S->stats->amax_bits, (unsigned long long)__double_as_longlong(amax));
+            if (bmax > 0.0) atomicMax(&S->stats->bmax_bits, (unsigned long long)__double_as_longlong(bmax));
+            if (cmax > 0.0) atomicMax(&S->stats->cmax_bits, (unsigned long long)__double_as_longlong(cmax));
+            if (s_fl) atomicOr(&S->stats->flags, s_fl);
+        }
+    }
+    bool ok = grid_sync(d->bar, d->err, G, spin_limit, &s_flag);
+    const int flags = __ldcg(&S->stats->flags);
+    const bool bad = (flags & 4) || (sense == 0 && (flags & 1)) || (sense == 1 && (flags & 2));
+    if (rank == 0 && tid == 0) {
+        const double amax = __longlong_as_double((long long)__ldcg(&S->stats->amax_bits));
+        const double bmax = __longlong_as_double((long long)__ldcg(&S->stats->bmax_bits));
+        const double cmax = __longlong_as_double((long long)__ldcg(&S->stats->cmax_bits));
+        d->eps_d = S->opt_eps_d > 0 ? S->opt_eps_d : 1e-9 * fmax(1.0, cmax);
+        d->eps_p = S->opt_eps_p > 0 ? S->opt_eps_p : 1e-9 * fmax(1.0, amax);
+        d->eps_r = S->opt_eps_r > 0 ? S->opt_eps_r : 1e-9 * fmax(1.0, bmax);
+    }
+    // Sec. 2 Step 1 on this rank's rows
+    if (ok && !bad) {
+        const double sg = sense == 0 ? 1.0 : -1.0;
+        double *Tab = reinterpret_cast<double *>(d->T);
+        const long long e0 = (long long)M * P * rank / G, e1 = (long long)M * P * (rank + 1) / G;
+        for (long long e = e0 + tid; e < e1; e += B) {
+            const int i = (int)(e / P);
+            const int j = (int)(e - (long long)i * P);
+            double v = 0.0;
+            if (i < m) {
+                if (j < n) v = sg * S->A[(long long)i * n + j];
+                else if (j == n + i) v = 1.0;
+                else if (j == N - 1) v = sg * S->b[i];
+            } else if (j < n) {
+                v = -sg * S->c[j];
+            }
+            Tab[e] = v;
+        }
+        for (int i = (int)((long long)m * rank / G) + tid; i < (int)((long long)m * (rank + 1) / G); i += B)
+            d->basis[i] = n + i;
+    }
+    if (ok) ok = grid_sync(d->bar, d->err, G, spin_limit, &s_flag);
+    if (ok && !bad) {
+        if (sense)
+            solve_lp<double, true, true>(d, G, rank, d->strip, spin_limit, S->budget, smem_raw);
+        else
+            solve_lp<double, true, false>(d, G, rank, d->strip, spin_limit, S->budget, smem_raw);
+    }
+    if (rank != 0) return;
+    __syncthreads();
+    if (!ok || *(volatile int *)d->err) {
+        // a group wait ran out: report it and stop the server taking work
+        if (tid == 0) {
+            d->status = ST_TIMEOUT;
+            atomicExch(&ctl->err, 1);
+        }
+    } else if (bad) {
+        if (tid == 0) d->status = (flags & 4) ? -2 : -3;  // invalid input / infeasible start
+    } else {
+        const double *Tab = reinterpret_cast<const double *>(d->T);
+        const double *z = Tab + (long long)m * P;
+        for (int j = tid; j < n; j += B) S->x[j] = 0.0;
+        for (int i = tid; i < m; i += B) S->y[i] = __ldcg(z + n + i);
+        __syncthreads();
+        for (int i = tid; i < m; i += B) {
+            const int j = __ldcg(d->basis + i);
+            if (j < n) S->x[j] = __ldcg(Tab + (long long)i * P + (N - 1));
+        }
+        if (tid == 0) {
+            const double zv = __ldcg(z + N - 1);
+            *S->obj = sense == 0 ? zv : -zv;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence_system();
+        atomicSub(&ctl->in_flight, 1);
+        st_rel_sys(&ring->done[slot], 1);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads)
+    server_kernel(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing *ring,
+                  long long spin_limit, long long idle_limit) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (blockIdx.x == 0) {
+        serve_dispatch(slots, ctl, ring, gridDim.x - 1, idle_limit);
+        return;
+    }
+    __shared__ int2 s_item;
+    __shared__ int s_ok;
+    const long long wait_limit = idle_limit + spin_limit;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned t = atomicAdd(&ctl->head, 1u);
+            int ok = 1;
+            const long long t0 = clock64();
+            while (ld_acquire(&ctl->seq[t % kServeQueue]) != t + 1u) {
+                if (clock64() - t0 > wait_limit) {
+                    atomicExch(&ctl->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+            s_ok = ok;
+            if (ok) {
+                s_item.x = __ldcg(&ctl->items[t % kServeQueue].x);
+                s_item.y = __ldcg(&ctl->items[t % kServeQueue].y);
+            }
+        }
+        __syncthreads();
+        if (!s_ok || s_item.x == -1) break;
+        if (s_item.x < 0) continue;  // keep-alive
+        serve_slot(slots + s_item.x, s_item.x, s_item.y, ctl, ring, spin_limit, smem_raw);
+    }
+}
+
 template <typename T, bool SMEM>
 __global__ void __launch_bounds__(kBatchThreads)
     batch_kernel(LpDesc *__restrict__ descs, const int2 *__restrict__ items, int nitems,
@@ -640,6 +878,29 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
     // A cooperative launch fails instead of running when the grid cannot be
     // co-resident, which the grid barrier needs.
     return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
+}
+
+cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing *ring_dev,
+                          int ctas, int threads, size_t smem, long long spin_limit,
+                          long long idle_limit, cudaStream_t s) {
+    void *args[] = {&slots, &nslots, &ctl, &ring_dev, &spin_limit, &idle_limit};
+    const void *fn = (const void *)server_kernel;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
+}
+
+int max_coresident_server_ctas(int threads, size_t smem, int sms) {
+    const void *fn = (const void *)server_kernel;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
 }
 
 cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems, unsigned *queue,

@@ -1,0 +1,530 @@
+// Serving engine (lp_server_*): continuous batching of LP requests.
+//
+// Host side, one engine thread per server:
+//   admission   requests wait in FIFO order until a slot and enough of the
+//               HBM budget are free; the engine copies their inputs to the
+//               device on a copy stream (overlapping the running kernel),
+//               writes the slot descriptor and appends the slot to the ring;
+//   completion  slots the kernel marked done have their results copied back,
+//               their memory returned to the budget and their ticket
+//               completed with submit-to-done latency;
+//   the kernel  is (re)launched whenever requests are waiting and the last
+//               launch has ended (it ends by itself after an idle period).
+// Device memory for tableaus comes from one arena of the budget's size,
+// managed by a first-fit allocator with coalescing.
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gbs_internal.h"
+#include "gbsimplex.h"
+
+using namespace gbs;
+
+namespace {
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, size) with coalescing of free neighbours.
+class Arena {
+  public:
+    void reset(size_t size) {
+        free_.clear();
+        free_[0] = size;
+        size_ = size;
+        used_ = 0;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = up256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = up256(bytes);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t used() const { return used_; }
+    size_t size() const { return size_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0, used_ = 0;
+};
+
+enum TicketState { QUEUED, ADMITTED, DONE };
+
+struct Request {
+    int m = 0, n = 0, sense = 0;
+    std::vector<double> in;  // A, b, c packed
+    TicketState state = QUEUED;
+    int slot = -1;
+    size_t off = 0, bytes = 0;
+    int group = 1, strip = 0;
+    // results
+    std::vector<double> x, y;
+    double obj = 0.0;
+    int status = LP_NOT_SOLVED;
+    long long iters = 0;
+    lp_err err = LP_OK;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+};
+
+}  // namespace
+
+struct lp_server {
+    lp_options opt;
+    int device = 0, sms = 0, threads = 512, ctas = 0, workers = 0;
+    size_t smem = 0;
+    int max_slots = 0;
+    static constexpr int kMaxDim = 4096;
+    cudaStream_t kstream = nullptr, cstream = nullptr;
+    unsigned char *arena_dev = nullptr;
+    Arena arena;
+    ServeSlot *d_slots = nullptr;
+    ServeCtl *d_ctl = nullptr;
+    ServeRing *h_ring = nullptr, *d_ring = nullptr;
+    std::vector<int> free_slots;
+    std::vector<unsigned long long> slot_ticket;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::unordered_map<unsigned long long, Request> reqs;
+    std::deque<unsigned long long> queue;
+    unsigned long long next_ticket = 1;
+    std::thread engine;
+    std::atomic<bool> stop{false};
+    bool kernel_running = false;
+    cudaEvent_t kdone = nullptr;
+    long long launches = 0, completed = 0;
+    lp_err fatal = LP_OK;
+    char fatal_msg[256] = {0};
+};
+
+namespace {
+
+lp_err sfail(lp_err code, const char *fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    set_last_error_global(msg);
+    return code;
+}
+
+struct SlotLayout {
+    size_t T, in, basis, part, bar, out, stats, total;
+};
+
+SlotLayout slot_layout(int m, int n, long long P, int G) {
+    SlotLayout L;
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t at = off; off += up256(b); return at; };
+    L.T = take((size_t)(m + 1) * (size_t)P * sizeof(double));
+    L.in = take(((size_t)m * n + m + n) * sizeof(double));
+    L.basis = take((size_t)m * sizeof(int));
+    L.part = take(2 * (size_t)G * sizeof(Cand));
+    L.bar = take(512);
+    L.out = take(((size_t)n + m + 1) * sizeof(double));
+    L.stats = take(sizeof(InputStats));
+    L.total = off;
+    return L;
+}
+
+void group_shape(const lp_server *sv, int m, int n, int *G, int *W) {
+    const long long M = m + 1, P = pitch_for(n + m + 1);
+    const long long ge = sv->opt.group_elems > 0 ? sv->opt.group_elems : 262144;
+    const long long gmin = (P + (long long)sv->threads * 2 - 1) / ((long long)sv->threads * 2);
+    long long g = (M * P + ge - 1) / ge;
+    g = std::min<long long>(g, std::min<long long>(sv->workers, P / 4));
+    g = std::max<long long>(g, gmin);
+    long long w = (P + g - 1) / g;
+    w = (w + 3) / 4 * 4;
+    *W = (int)w;
+    *G = (int)((P + w - 1) / w);
+}
+
+// Copy results of finished slots back and release their resources.
+bool engine_complete(lp_server *sv) {
+    std::vector<int> fin;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (int s = 0; s < sv->max_slots; ++s)
+            if (sv->slot_ticket[s] && *(volatile int *)&sv->h_ring->done[s] == 1) fin.push_back(s);
+    }
+    if (fin.empty()) return false;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    for (int s : fin) {
+        Request *r;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r = &sv->reqs[sv->slot_ticket[s]];
+        }
+        const long long P = pitch_for(r->n + r->m + 1);
+        const SlotLayout L = slot_layout(r->m, r->n, P, r->group);
+        LpDesc d;
+        r->x.resize(r->n);
+        r->y.resize(r->m);
+        const double *out = reinterpret_cast<const double *>(sv->arena_dev + r->off + L.out);
+        cudaMemcpyAsync(&d, &sv->d_slots[s].d, sizeof d, cudaMemcpyDeviceToHost, sv->cstream);
+        cudaMemcpyAsync(r->x.data(), out, sizeof(double) * r->n, cudaMemcpyDeviceToHost, sv->cstream);
+        cudaMemcpyAsync(r->y.data(), out + r->n, sizeof(double) * r->m, cudaMemcpyDeviceToHost,
+                        sv->cstream);
+        cudaMemcpyAsync(&r->obj, out + r->n + r->m, sizeof(double), cudaMemcpyDeviceToHost,
+                        sv->cstream);
+        cudaStreamSynchronize(sv->cstream);
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->iters = d.iters;
+        if (d.status == -2) { r->err = LP_ERR_INVALID_ARG; r->status = LP_NOT_SOLVED; }
+        else if (d.status == -3) { r->err = LP_ERR_INFEASIBLE_START; r->status = LP_NOT_SOLVED; }
+        else r->status = d.status;
+        r->state = DONE;
+        r->t_done = now_ms();
+        sv->arena.release(r->off, r->bytes);
+        sv->slot_ticket[s] = 0;
+        sv->free_slots.push_back(s);
+        *(volatile int *)&sv->h_ring->done[s] = 0;
+        ++sv->completed;
+    }
+    sv->cv.notify_all();
+    return true;
+}
+
+// Move waiting requests into free slots while the budget allows (FIFO).
+bool engine_admit(lp_server *sv) {
+    struct Adm { int s; unsigned long long t; Request *r; };
+    std::vector<Adm> adm;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        while (!sv->queue.empty() && !sv->free_slots.empty()) {
+            const unsigned long long t = sv->queue.front();
+            Request &r = sv->reqs[t];
+            group_shape(sv, r.m, r.n, &r.group, &r.strip);
+            const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group);
+            size_t off;
+            if (!sv->arena.alloc(L.total, &off)) break;
+            r.off = off;
+            r.bytes = L.total;
+            r.slot = sv->free_slots.back();
+            sv->free_slots.pop_back();
+            sv->slot_ticket[r.slot] = t;
+            r.state = ADMITTED;
+            r.t_admit = now_ms();
+            sv->queue.pop_front();
+            adm.push_back({r.slot, t, &r});
+        }
+    }
+    if (adm.empty()) return false;
+    std::vector<ServeSlot> hs(adm.size());
+    for (size_t k = 0; k < adm.size(); ++k) {
+        Request &r = *adm[k].r;
+        const int m = r.m, n = r.n;
+        const long long P = pitch_for(n + m + 1);
+        const SlotLayout L = slot_layout(m, n, P, r.group);
+        unsigned char *base = sv->arena_dev + r.off;
+        cudaMemcpyAsync(base + L.in, r.in.data(), r.in.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, sv->cstream);
+        cudaMemsetAsync(base + L.bar, 0, 512, sv->cstream);
+        cudaMemsetAsync(base + L.stats, 0, sizeof(InputStats), sv->cstream);
+        ServeSlot &S = hs[k];
+        memset(&S, 0, sizeof S);
+        LpDesc &d = S.d;
+        d.T = base + L.T;
+        d.basis = reinterpret_cast<int *>(base + L.basis);
+        d.part_sel = reinterpret_cast<Cand *>(base + L.part);
+        d.bar = reinterpret_cast<unsigned *>(base + L.bar);
+        d.err = reinterpret_cast<int *>(d.bar + 96);
+        d.P = P;
+        d.m = m;
+        d.n = n;
+        d.M = m + 1;
+        d.N = n + m + 1;
+        d.sense = r.sense;
+        d.bland_after = sv->opt.bland_after;
+        d.status = -1;
+        d.last_p = d.last_q = -1;
+        d.group = r.group;
+        d.strip = r.strip;
+        const double *in = reinterpret_cast<const double *>(base + L.in);
+        S.A = in;
+        S.b = in + (size_t)m * n;
+        S.c = S.b + m;
+        double *out = reinterpret_cast<double *>(base + L.out);
+        S.x = out;
+        S.y = out + n;
+        S.obj = out + n + m;
+        S.stats = reinterpret_cast<InputStats *>(base + L.stats);
+        S.opt_eps_d = sv->opt.eps_d;
+        S.opt_eps_p = sv->opt.eps_p;
+        S.opt_eps_r = sv->opt.eps_r;
+        S.budget = sv->opt.max_iters;
+        cudaMemcpyAsync(&sv->d_slots[adm[k].s], &S, sizeof S, cudaMemcpyHostToDevice, sv->cstream);
+    }
+    cudaStreamSynchronize(sv->cstream);
+    int tail = *(volatile int *)&sv->h_ring->rq_tail;
+    for (const Adm &a : adm) sv->h_ring->rq[tail++ % kServeMaxSlots] = a.s;
+    std::atomic_thread_fence(std::memory_order_release);
+    *(volatile int *)&sv->h_ring->rq_tail = tail;
+    return true;
+}
+
+void engine_kernel(lp_server *sv) {
+    if (sv->kernel_running && cudaEventQuery(sv->kdone) == cudaSuccess) {
+        sv->kernel_running = false;
+        int err = 0;
+        cudaMemcpy(&err, &sv->d_ctl->err, sizeof err, cudaMemcpyDeviceToHost);
+        if (err) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->fatal = LP_ERR_CUDA;
+            snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "server kernel: a device wait timed out");
+            sv->cv.notify_all();
+        }
+    }
+    bool pending;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        pending = sv->fatal == LP_OK &&
+                  *(volatile int *)&sv->h_ring->rq_head != *(volatile int *)&sv->h_ring->rq_tail;
+        for (int s = 0; !pending && s < sv->max_slots; ++s)
+            if (sv->slot_ticket[s] && *(volatile int *)&sv->h_ring->done[s] == 0) pending = true;
+    }
+    if (!pending || sv->kernel_running) return;
+    cudaMemsetAsync(sv->d_ctl, 0, sizeof(ServeCtl), sv->kstream);
+    const long long idle = 100000000ll;  // ~50 ms of SM clock with no work
+    cudaError_t e = launch_server(sv->d_slots, sv->max_slots, sv->d_ctl, sv->d_ring, sv->ctas,
+                                  sv->threads, sv->smem, sv->opt.spin_timeout_cycles, idle,
+                                  sv->kstream);
+    if (e == cudaSuccess) e = cudaEventRecord(sv->kdone, sv->kstream);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->fatal = LP_ERR_CUDA;
+        snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "server launch: %s", cudaGetErrorString(e));
+        sv->cv.notify_all();
+        return;
+    }
+    sv->kernel_running = true;
+    ++sv->launches;
+}
+
+void engine_main(lp_server *sv) {
+    cudaSetDevice(sv->device);
+    while (!sv->stop.load()) {
+        bool progress = engine_complete(sv);
+        progress |= engine_admit(sv);
+        engine_kernel(sv);
+        if (!progress) {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budget_bytes,
+                        int max_slots) {
+    if (!out) return sfail(LP_ERR_INVALID_ARG, "lp_server_create: out is NULL");
+    *out = nullptr;
+    lp_options o;
+    if (opt) o = *opt; else lp_options_default(&o);
+    if (o.precision != LP_FP64)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_create: FP64 only");
+    if (max_slots < 1 || max_slots > kServeMaxSlots || hbm_budget_bytes < (1u << 20))
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_create: need 1 <= max_slots <= %d and a "
+                     "budget of at least 1 MiB", kServeMaxSlots);
+    if (o.max_iters < 0 || o.bland_after < 0 || o.spin_timeout_cycles <= 0 || o.device < 0)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_create: option out of range");
+    lp_server *sv = new (std::nothrow) lp_server();
+    if (!sv) return sfail(LP_ERR_OOM, "lp_server_create: host allocation failed");
+    sv->opt = o;
+    sv->device = o.device;
+    sv->max_slots = max_slots;
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
+    const int M = lp_server::kMaxDim + 1, N = 2 * lp_server::kMaxDim + 1;
+    sv->smem = (size_t)sv->threads * 2 * sizeof(double) + (((size_t)M * sizeof(double) + 15) & ~(size_t)15) +
+               (size_t)std::max(M, N) * sizeof(double);
+    if (e == cudaSuccess) {
+        sv->ctas = max_coresident_server_ctas(sv->threads, sv->smem, sv->sms);
+        sv->workers = sv->ctas - 1;
+        if (sv->workers < 1) e = cudaErrorInvalidConfiguration;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->kstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->cstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->kdone, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->arena_dev, hbm_budget_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_slots, sizeof(ServeSlot) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&sv->d_ctl, sizeof(ServeCtl));
+    if (e == cudaSuccess) e = cudaHostAlloc(&sv->h_ring, sizeof(ServeRing), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&sv->d_ring, sv->h_ring, 0);
+    if (e != cudaSuccess) {
+        sfail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA, "lp_server_create: %s",
+              cudaGetErrorString(e));
+        lp_server_destroy(sv);
+        return e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA;
+    }
+    memset(sv->h_ring, 0, sizeof(ServeRing));
+    sv->arena.reset(hbm_budget_bytes);
+    sv->slot_ticket.assign(max_slots, 0);
+    for (int s = max_slots - 1; s >= 0; --s) sv->free_slots.push_back(s);
+    sv->engine = std::thread(engine_main, sv);
+    *out = sv;
+    return LP_OK;
+}
+
+lp_err lp_server_submit(lp_server *sv, int m, int n, const double *A, const double *b,
+                        const double *c, lp_sense sense, unsigned long long *ticket) {
+    if (!sv || !A || !b || !c || !ticket)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_submit: NULL argument");
+    if (m < 1 || n < 1 || m > lp_server::kMaxDim || n > lp_server::kMaxDim)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_submit: need 1 <= m, n <= %d",
+                     lp_server::kMaxDim);
+    if (sense != LP_MAX_LE && sense != LP_MIN_GE)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_submit: unknown sense");
+    Request r;
+    r.m = m;
+    r.n = n;
+    r.sense = (int)sense;
+    r.in.resize((size_t)m * n + m + n);
+    memcpy(r.in.data(), A, sizeof(double) * (size_t)m * n);
+    memcpy(r.in.data() + (size_t)m * n, b, sizeof(double) * m);
+    memcpy(r.in.data() + (size_t)m * n + m, c, sizeof(double) * n);
+    int G, W;
+    group_shape(sv, m, n, &G, &W);
+    if (slot_layout(m, n, pitch_for(n + m + 1), G).total > sv->arena.size())
+        return sfail(LP_ERR_OOM, "lp_server_submit: an LP of %d x %d exceeds the HBM budget", m, n);
+    r.t_submit = now_ms();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->fatal != LP_OK) return sfail(sv->fatal, "lp_server_submit: %s", sv->fatal_msg);
+    const unsigned long long t = sv->next_ticket++;
+    sv->reqs.emplace(t, std::move(r));
+    sv->queue.push_back(t);
+    *ticket = t;
+    sv->cv.notify_all();
+    return LP_OK;
+}
+
+static lp_err take_result(lp_server *sv, std::unordered_map<unsigned long long, Request>::iterator it,
+                          double *x, double *y, double *obj, lp_status *status, long long *iters,
+                          double *latency_ms) {
+    Request &r = it->second;
+    if (x) memcpy(x, r.x.data(), sizeof(double) * r.n);
+    if (y) memcpy(y, r.y.data(), sizeof(double) * r.m);
+    if (obj) *obj = r.obj;
+    if (status) *status = (lp_status)r.status;
+    if (iters) *iters = r.iters;
+    if (latency_ms) *latency_ms = r.t_done - r.t_submit;
+    const lp_err e = r.err;
+    sv->reqs.erase(it);
+    if (e != LP_OK) return sfail(e, "lp_server: request rejected by the input check");
+    return LP_OK;
+}
+
+lp_err lp_server_poll(lp_server *sv, unsigned long long ticket, int *done, double *x, double *y,
+                      double *obj, lp_status *status, long long *iters, double *latency_ms) {
+    if (!sv || !done) return sfail(LP_ERR_INVALID_ARG, "lp_server_poll: NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return sfail(LP_ERR_INVALID_ARG, "lp_server_poll: unknown ticket");
+    if (it->second.state != DONE) {
+        *done = 0;
+        if (sv->fatal != LP_OK) return sfail(sv->fatal, "lp_server_poll: %s", sv->fatal_msg);
+        return LP_OK;
+    }
+    *done = 1;
+    return take_result(sv, it, x, y, obj, status, iters, latency_ms);
+}
+
+lp_err lp_server_wait(lp_server *sv, unsigned long long ticket, double timeout_s, double *x,
+                      double *y, double *obj, lp_status *status, long long *iters,
+                      double *latency_ms) {
+    if (!sv) return sfail(LP_ERR_INVALID_ARG, "lp_server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return sfail(LP_ERR_INVALID_ARG, "lp_server_wait: unknown ticket");
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::microseconds((long long)(timeout_s * 1e6));
+    while (it->second.state != DONE) {
+        if (sv->fatal != LP_OK) return sfail(sv->fatal, "lp_server_wait: %s", sv->fatal_msg);
+        if (sv->cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+            it->second.state != DONE)
+            return sfail(LP_ERR_BUSY, "lp_server_wait: timed out");
+        it = sv->reqs.find(ticket);
+    }
+    return take_result(sv, it, x, y, obj, status, iters, latency_ms);
+}
+
+lp_err lp_server_stats(lp_server *sv, long long *completed, long long *launches,
+                       size_t *hbm_used, int *queued) {
+    if (!sv) return sfail(LP_ERR_INVALID_ARG, "lp_server_stats: NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (completed) *completed = sv->completed;
+    if (launches) *launches = sv->launches;
+    if (hbm_used) *hbm_used = sv->arena.used();
+    if (queued) *queued = (int)sv->queue.size();
+    return LP_OK;
+}
+
+void lp_server_destroy(lp_server *sv) {
+    if (!sv) return;
+    if (sv->engine.joinable()) {
+        sv->stop.store(true);
+        sv->cv.notify_all();
+        sv->engine.join();
+    }
+    cudaSetDevice(sv->device);
+    if (sv->h_ring) *(volatile int *)&sv->h_ring->shutdown = 1;
+    if (sv->kstream) cudaStreamSynchronize(sv->kstream);  // the kernel exits once idle
+    if (sv->cstream) cudaStreamSynchronize(sv->cstream);
+    if (sv->arena_dev) cudaFree(sv->arena_dev);
+    if (sv->d_slots) cudaFree(sv->d_slots);
+    if (sv->d_ctl) cudaFree(sv->d_ctl);
+    if (sv->h_ring) cudaFreeHost(sv->h_ring);
+    if (sv->kdone) cudaEventDestroy(sv->kdone);
+    if (sv->kstream) cudaStreamDestroy(sv->kstream);
+    if (sv->cstream) cudaStreamDestroy(sv->cstream);
+    delete sv;
+}
+
+}  // extern "C"

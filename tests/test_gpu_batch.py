@@ -100,3 +100,14 @@ def test_batch_errors_name_the_lp():
     with pytest.raises(capi.LpError) as e:
         capi.lp_solve_batch(lps)
     assert e.value.code == capi.LP_ERR_INFEASIBLE_START and "LP 3" in str(e.value)
+
+
+def test_batch_autotune_and_cache(tmp_path):
+    lps = _mixed(32, 16, 400, seed=6)
+    cache = str(tmp_path / "tune.txt")
+    best = capi.lp_batch_autotune(lps, cache_path=cache)
+    assert best.group_elems in (16384, 65536, 262144, 1048576) and best.threads in (256, 512)
+    again = capi.lp_batch_autotune(lps, cache_path=cache)  # cache hit
+    assert (again.group_elems, again.threads) == (best.group_elems, best.threads)
+    assert len(open(cache).read().strip().splitlines()) == 1
+    _check_against_oracle(lps, capi.lp_solve_batch(lps, best, want_xy=True))

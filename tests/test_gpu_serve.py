@@ -1,0 +1,111 @@
+"""Serving with continuous batching, through the C ABI.
+
+Requests are submitted while others are on the GPU; every result must equal
+the FP64 oracle's for that LP alone, bit for bit (each LP runs the single-LP
+pivot code on its own group of CTAs), whatever else is in the mix, under a
+budget that forces requests to wait for memory, and across kernel relaunches.
+"""
+import os
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_04737_gb300 import capi, lpgen
+from paper_1804_04737_gb300.build import build_library
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_library()
+    capi.load_library()
+    oracle.set_threads(os.cpu_count() or 1)
+    yield
+    oracle.set_threads(1)
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.uint64)
+
+
+def _mix(count, lo, hi, seed):
+    out = []
+    for k, (m, n) in enumerate(lpgen.log_uniform_shapes(count, lo, hi, seed)):
+        A, b, c = lpgen.dense_lp(m, n, seed=7000 * seed + k)
+        out.append((*lpgen.dual_of(A, b, c), capi.LP_MIN_GE) if k % 4 == 3
+                   else (A, b, c, capi.LP_MAX_LE))
+    return out
+
+
+def _check(lp, res):
+    A, b, c, sense = lp
+    obj, st, it, x, y, lat = res
+    o = oracle.solve(A, b, c, sense=sense)
+    assert st == o.status and it == o.iters
+    assert _bits([obj])[0] == _bits([o.obj])[0]
+    assert np.array_equal(_bits(x), _bits(o.x)) and np.array_equal(_bits(y), _bits(o.y))
+    assert lat > 0.0
+
+
+def test_serve_stream_matches_oracle():
+    lps = _mix(60, 8, 600, seed=1)
+    srv = capi.lp_server_create(hbm_budget_bytes=2 << 30, max_slots=64)
+    try:
+        tickets = []
+        for k, lp in enumerate(lps):  # staggered arrivals: new requests join running ones
+            tickets.append(capi.lp_server_submit(srv, *lp))
+            if k % 7 == 0:
+                time.sleep(0.002)
+        for lp, t in zip(lps, tickets):
+            _check(lp, capi.lp_server_wait(srv, t, lp[0].shape[0], lp[0].shape[1]))
+        assert capi.lp_server_stats(srv)[0] == len(lps)
+    finally:
+        capi.lp_server_destroy(srv)
+
+
+def test_serve_small_budget_admission_and_threads():
+    """A budget that holds only a few tableaus: requests wait for memory."""
+    lps = _mix(24, 100, 400, seed=2)
+    srv = capi.lp_server_create(hbm_budget_bytes=12 << 20, max_slots=8)
+    results = {}
+    try:
+        def client(idx):
+            for k in idx:
+                t = capi.lp_server_submit(srv, *lps[k])
+                results[k] = capi.lp_server_wait(srv, t, lps[k][0].shape[0], lps[k][0].shape[1])
+        ths = [threading.Thread(target=client, args=(range(j, len(lps), 4),)) for j in range(4)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        for k, lp in enumerate(lps):
+            _check(lp, results[k])
+        _, _, used, queued = capi.lp_server_stats(srv)
+        assert used == 0 and queued == 0
+    finally:
+        capi.lp_server_destroy(srv)
+
+
+def test_serve_idle_relaunch_and_rejected_request():
+    srv = capi.lp_server_create(hbm_budget_bytes=1 << 30, max_slots=16)
+    try:
+        lp = _mix(1, 50, 60, seed=3)[0]
+        _check(lp, capi.lp_server_wait(srv, capi.lp_server_submit(srv, *lp), lp[0].shape[0], lp[0].shape[1]))
+        time.sleep(0.3)  # the kernel ends after its idle period
+        A, b, c, _ = _mix(1, 20, 30, seed=4)[0]
+        bad = b.copy()
+        bad[2] = -5.0
+        tb = capi.lp_server_submit(srv, A, bad, c)
+        lp2 = _mix(1, 70, 80, seed=5)[0]
+        t2 = capi.lp_server_submit(srv, *lp2)
+        with pytest.raises(capi.LpError) as e:
+            capi.lp_server_wait(srv, tb, A.shape[0], A.shape[1])
+        assert e.value.code == capi.LP_ERR_INFEASIBLE_START
+        _check(lp2, capi.lp_server_wait(srv, t2, lp2[0].shape[0], lp2[0].shape[1]))
+        assert capi.lp_server_stats(srv)[1] >= 2  # relaunched after the idle exit
+    finally:
+        capi.lp_server_destroy(srv)
