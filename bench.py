@@ -130,6 +130,21 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
+def reduce_over_ranks(dist, maxes, sums, device="cpu"):
+    """Max of `maxes` and sum of `sums` over the ranks of the default process
+    group (identity without one).  Replicas: every rank runs its own solves,
+    so whole-job throughput is the units of all ranks over the slowest rank's
+    time."""
+    if dist is None:
+        return list(maxes), list(sums)
+    import torch
+    a = torch.tensor(list(maxes), dtype=torch.float64, device=device)
+    b = torch.tensor(list(sums), dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
+
+
 def cpu_oracle_run(lps, threads):
     import oracle
     oracle.set_threads(threads)
@@ -170,6 +185,127 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_lp8192(args, capi, torch):
+    """8192 x 8192 dense LP: FP64 against the FP32 tableau with FP64
+    reinversion every k in {50, 200} pivots.  The FP64 path is bit-identical
+    to the FP64 oracle at this size (tests/test_gpu_parity.py), so FP32
+    objective errors are measured against it."""
+    from paper_1804_04737_gb300 import lpgen
+    A, b, c = lpgen.dense_lp(8192, 8192, 0)
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    torch.cuda.synchronize()
+    out = []
+    ref = None
+    for prec, k in ((capi.LP_FP64, 0), (capi.LP_FP32_REINV, 50), (capi.LP_FP32_REINV, 200)):
+        h = capi.lp_create(capi.lp_options_default(precision=prec, reinv_k=max(k, 1)))
+        best = None
+        for rep in range(1 + max(1, args.steps // 5)):
+            t0 = time.perf_counter()
+            capi.lp_load(h, dA, db, dc)
+            capi.lp_solve(h)
+            obj, st, it = capi.lp_result(h)
+            wall = time.perf_counter() - t0
+            kms, launches = capi.lp_kernel_time(h)
+            if rep and (best is None or wall < best[0]):
+                best = (wall, kms, launches, obj, st, it)
+        capi.lp_destroy(h)
+        wall, kms, launches, obj, st, it = best
+        w = 8 if prec == capi.LP_FP64 else 4
+        if ref is None:
+            ref = obj
+        out.append({"mode": "fp64" if prec == capi.LP_FP64 else "fp32+reinv k=%d" % k,
+                    "status": capi.STATUS_NAMES[st], "pivots": it,
+                    "solve_ms": round(1e3 * wall, 2), "pivot_kernel_ms": round(kms, 2),
+                    "pivot_kernel_launches": launches,
+                    "pivots_per_s": round(it / wall, 1),
+                    "tableau_gbs_kernel": round(it * tableau_bytes(8192, 8192, w) / kms / 1e6, 1),
+                    "obj": obj, "obj_rel_err_vs_fp64": abs(obj - ref) / abs(ref)})
+    print(json.dumps({"workload": "dense LP 8192x8192, FP64 vs FP32 tableau + FP64 reinversion",
+                      "results": out, "hbm_peak_gbs": peaks()[0]}), flush=True)
+
+
+def run_batch(args, capi, torch):
+    """1024 dense LPs, m and n log-uniform in [32, 1024], one batched launch
+    (autotuned launch shape) against one LP per launch."""
+    import numpy as np
+    from paper_1804_04737_gb300 import lpgen
+    lps = [(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda(), torch.from_numpy(c).cuda(),
+            capi.LP_MAX_LE) for A, b, c in lpgen.batch_lps(1024, 32, 1024, seed=0)]
+    torch.cuda.synchronize()
+    best = capi.lp_batch_autotune(lps, cache_path="/tmp/gbs_batch_tune.txt")
+    for _ in range(args.warmup):
+        capi.lp_solve_batch(lps, best)
+    walls, kms = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        obj, st, it = capi.lp_solve_batch(lps, best)
+        walls.append(time.perf_counter() - t0)
+        kms.append(capi.lp_batch_stats()[0])
+    pivots = int(np.sum(it))
+    alg = sum(int(it[k]) * tableau_bytes(int(L[0].shape[0]), int(L[0].shape[1]))
+              for k, L in enumerate(lps))
+    h = capi.lp_create()
+    t0 = time.perf_counter()
+    for A, b, c, s in lps[:128]:
+        capi.lp_load(h, A, b, c, s)
+        capi.lp_solve(h)
+        capi.lp_result(h)
+    single = 128 / (time.perf_counter() - t0)
+    capi.lp_destroy(h)
+    wall = float(np.median(walls))
+    print(json.dumps({"workload": "batch of 1024 dense LPs, m,n log-uniform [32,1024], FP64",
+                      "lps_per_s": round(1024 / wall, 1), "wall_ms": round(1e3 * wall, 2),
+                      "kernel_ms": round(float(np.median(kms)), 2), "pivots": pivots,
+                      "pivots_per_s": round(pivots / wall, 1),
+                      "tableau_gbs_kernel": round(alg / float(np.median(kms)) / 1e6, 1),
+                      "all_optimal": bool(np.all(st == capi.LP_OPTIMAL)),
+                      "launch_shape": {"group_elems": best.group_elems, "threads": best.threads},
+                      "one_lp_per_launch_lps_per_s": round(single, 1)}), flush=True)
+
+
+def run_serve(args, capi, torch):
+    """Poisson stream of dense LPs (m, n log-uniform in [64, 4096]; a pool of
+    distinct LPs reused round robin) into a server with a 60 GB HBM budget;
+    arrival rate swept up by 1.5x until throughput stops rising."""
+    import numpy as np
+    from paper_1804_04737_gb300 import lpgen
+    rng = np.random.default_rng(0)
+    pool = [lpgen.dense_lp(m, n, seed=k) for k, (m, n) in
+            enumerate(lpgen.log_uniform_shapes(96, 64, 4096, seed=0))]
+    srv = capi.lp_server_create(hbm_budget_bytes=60 << 30, max_slots=512)
+    per_point = max(200, 40 * args.steps)
+    points = []
+    rate = 50.0
+    try:
+        for _ in range(10):
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=per_point))
+            tickets = []
+            t0 = time.perf_counter()
+            for k, ta in enumerate(arrivals):
+                d = t0 + ta - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                A, b, c = pool[k % len(pool)]
+                tickets.append((capi.lp_server_submit(srv, A, b, c), A.shape))
+            lat = []
+            for t, (m, n) in tickets:
+                lat.append(capi.lp_server_wait(srv, t, m, n, timeout_s=600)[5])
+            span = time.perf_counter() - t0
+            thr = per_point / span
+            points.append({"offered_per_s": round(rate, 1), "lps_per_s": round(thr, 1),
+                           "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 2)})
+            if len(points) > 1 and thr < 1.05 * points[-2]["lps_per_s"]:
+                break
+            rate *= 1.5
+    finally:
+        capi.lp_server_destroy(srv)
+    best = max(points, key=lambda p: p["lps_per_s"])
+    print(json.dumps({"workload": "serving: Poisson stream of dense LPs, m,n log-uniform "
+                      "[64,4096], 60 GB HBM budget, FP64", "requests_per_point": per_point,
+                      "saturation": best, "sweep": points}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,6 +313,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="lp2048set",
+                    choices=["lp2048set", "lp8192", "batch1024", "serve"],
+                    help="lp2048set is the headline line; the others report their own figures")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -191,6 +330,9 @@ def main():
     from paper_1804_04737_gb300 import capi
 
     torch.cuda.set_device(local)
+    if args.workload != "lp2048set":
+        return {"lp8192": run_lp8192, "batch1024": run_batch,
+                "serve": run_serve}[args.workload](args, capi, torch)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -239,17 +381,10 @@ def main():
                 kernel_ms += kms
                 alg_bytes += it * tableau_bytes(A.shape[0], A.shape[1])
     torch.cuda.synchronize()
-    total_ms = sum(step_ms)
     if dist:
         dist.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pv = torch.tensor([pivots], dtype=torch.float64, device="cuda")
-        dist.all_reduce(pv)
-        all_pivots = int(pv.item())
-    else:
-        all_pivots = pivots
+    (total_ms,), (all_pivots,) = reduce_over_ranks(dist, [sum(step_ms)], [pivots], "cuda")
+    all_pivots = int(all_pivots)
 
     # end to end from pinned host buffers through the C ABI
     host_in = []
@@ -278,13 +413,8 @@ def main():
         e2e_piv += e2e_step()
     torch.cuda.synchronize()
     e2e_sec = time.perf_counter() - t0
-    e2e_val = e2e_piv / e2e_sec
-    if dist:
-        t = torch.tensor([e2e_sec], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        pv = torch.tensor([e2e_piv], dtype=torch.float64, device="cuda")
-        dist.all_reduce(pv)
-        e2e_val = float(pv.item()) / float(t.item())
+    (e2e_sec_max,), (e2e_piv_all,) = reduce_over_ranks(dist, [e2e_sec], [e2e_piv], "cuda")
+    e2e_val = e2e_piv_all / e2e_sec_max
 
     for h in handles:
         capi.lp_destroy(h)
