@@ -110,11 +110,16 @@ typedef struct {
     long long trace_cap;     /* record (row, column) of the first trace_cap pivots */
     long long group_elems;   /* batched solves: tableau elements per CTA of an LP's
                                 group, 0 = 262144 (see lp_solve_batch)            */
+    int pipeline;            /* single-LP primal simplex: 1 = pipelined kernel
+                                (two tableau buffers; the next pivot's selection
+                                overlaps this pivot's update), 0 = in-place
+                                kernel (one buffer, selection then update).
+                                Same pivots and bits either way.                  */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
  * by formula, bland_after 32, auto launch shape, spin timeout 4e9 cycles,
- * library stream, device 0, no trace. */
+ * library stream, device 0, no trace, pipelined primal kernel. */
 void lp_options_default(lp_options *opt);
 
 /* Create a handle on opt->device (opt may be NULL for the defaults).

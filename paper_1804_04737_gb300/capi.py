@@ -46,6 +46,7 @@ class lp_options(ctypes.Structure):
         ("ctas", ctypes.c_int),
         ("trace_cap", ctypes.c_longlong),
         ("group_elems", ctypes.c_longlong),
+        ("pipeline", ctypes.c_int),
     ]
 
 

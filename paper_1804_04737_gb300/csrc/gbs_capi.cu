@@ -38,15 +38,19 @@ struct lp_handle {
     // device memory
     double *dA = nullptr, *db = nullptr, *dc = nullptr;
     size_t cap_A = 0, cap_b = 0, cap_c = 0;  // element capacities
-    void *dT = nullptr;
+    void *dT = nullptr;                         // the current tableau
     size_t cap_T = 0;                           // bytes
+    void *dT2 = nullptr;                        // pipelined kernel: the other buffer
+    size_t cap_T2 = 0;
+    void *dcol = nullptr;                       // pipelined kernel: 2 pivot columns
+    size_t cap_col = 0;
     int *dbasis = nullptr;
     size_t cap_basis = 0;
     void *dscratch = nullptr;
     size_t cap_scratch = 0;                     // bytes
-    Cand *dpart = nullptr;                      // 2 * max_ctas
+    Cand *dpart = nullptr;                      // 3 * max_ctas (selection, ratio)
     int max_ctas = 0;
-    unsigned *dbar = nullptr;                   // 128 words: barrier, readers, err
+    unsigned *dbar = nullptr;                   // kBarWords: barrier, counters, err
     int *dtrace = nullptr;
     long long cap_trace = 0;
     LpDesc *ddesc = nullptr;
@@ -144,6 +148,7 @@ void lp_options_default(lp_options *o) {
     o->ctas = 0;
     o->trace_cap = 0;
     o->group_elems = 0;
+    o->pipeline = 1;
 }
 
 const char *lp_version(void) { return "gbsimplex 0.1 (sm_103a)"; }
@@ -199,7 +204,7 @@ lp_err lp_create(lp_handle **out, const lp_options *opt) {
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->ddesc, sizeof(LpDesc));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(InputStats));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, 128 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, kBarWords * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&h->dobj, sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&h->pdesc, sizeof(LpDesc));
     if (e == cudaSuccess) e = cudaMallocHost(&h->pobj, sizeof(double));
@@ -223,7 +228,7 @@ void lp_destroy(lp_handle *h) {
                      h->rb.bar};
     for (void *p : rbufs)
         if (p) cudaFree(p);
-    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dbasis, h->dscratch, h->dpart, h->dbar,
+    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dcol, h->dbasis, h->dscratch, h->dpart, h->dbar,
                     h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -257,15 +262,29 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    const PivotShape sh = choose_shape(h->prec, (int)sense, M, N, P, h->sms, h->opt.threads,
-                                       h->opt.ctas);
-    const PivotShape sh_alt = choose_shape(h->prec, 1 - (int)sense, M, N, P, h->sms,
-                                           h->opt.threads, h->opt.ctas);
+    // the primal rule runs on the pipelined kernel where it can take the LP
+    auto shape_for = [&](int rule) {
+        if (rule == 0 && h->opt.pipeline) {
+            const PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads,
+                                                    h->opt.ctas);
+            if (ps.pipe) return ps;
+        }
+        return choose_shape(h->prec, rule, M, N, P, h->sms, h->opt.threads, h->opt.ctas);
+    };
+    const PivotShape sh = shape_for((int)sense);
+    // the other rule (FP32 recovery)
+    const PivotShape sh_alt = shape_for(1 - (int)sense);
+    const bool pipe = sh.pipe || (h->prec == PREC_FP32 && sh_alt.pipe);
+    const int ctas_max = h->prec == PREC_FP32 ? std::max(sh.ctas, sh_alt.ctas) : sh.ctas;
 
     CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
     CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
     CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
     CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
+    if (pipe) {
+        CUDA_TRY(h, grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz));
+        CUDA_TRY(h, grow_bytes(&h->dcol, &h->cap_col, 2 * (size_t)M * esz));
+    }
     CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
     {
         size_t need = sh.use_smem ? 0 : (size_t)sh.ctas * (size_t)sh.scratch_stride;
@@ -273,12 +292,12 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
             need = std::max(need, (size_t)sh_alt.ctas * (size_t)sh_alt.scratch_stride);
         if (need) CUDA_TRY(h, grow_bytes(&h->dscratch, &h->cap_scratch, need));
     }
-    if (h->max_ctas < sh.ctas) {
+    if (h->max_ctas < ctas_max) {
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
         h->max_ctas = 0;
-        CUDA_TRY(h, cudaMalloc(&h->dpart, 2 * (size_t)sh.ctas * sizeof(Cand)));
-        h->max_ctas = sh.ctas;
+        CUDA_TRY(h, cudaMalloc(&h->dpart, 3 * (size_t)ctas_max * sizeof(Cand)));
+        h->max_ctas = ctas_max;
     }
     if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
         if (h->dtrace) cudaFree(h->dtrace);
@@ -353,6 +372,10 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.scratch = h->dscratch;
     d.scratch_stride = sh.scratch_stride;
     d.part_sel = h->dpart;
+    d.part_ratio = h->dpart + 2 * (size_t)h->max_ctas;
+    d.T2 = pipe ? h->dT2 : nullptr;
+    d.colbuf = pipe ? h->dcol : nullptr;
+    d.cur = 0;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;
@@ -390,6 +413,17 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
 }  // extern "C"
 
 namespace {
+
+// The pipelined kernel leaves its last tableau in either buffer and names it
+// in the descriptor; once the descriptor is read back, make it h->dT.
+void adopt_tableau(lp_handle *h) {
+    if (h->pdesc->T != h->dT && h->pdesc->T == h->dT2) {
+        std::swap(h->dT, h->dT2);
+        std::swap(h->cap_T, h->cap_T2);
+    }
+    h->desc.T = h->dT;
+    h->desc.T2 = h->dT2;
+}
 
 double okey_to_double(unsigned long long k) {
     const unsigned long long bits = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
@@ -468,12 +502,13 @@ lp_err solve_fp32(lp_handle *h) {
         const long long stride = sh.scratch_stride;
         CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, scratch_stride), &stride,
                                     sizeof stride, cudaMemcpyHostToDevice, s));
-        CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, 128 * sizeof(unsigned), s));
+        CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, kBarWords * sizeof(unsigned), s));
         CUDA_TRY(h, cudaEventRecord(h->ev0, s));
         CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, sh, h->opt.spin_timeout_cycles, budget, s));
         CUDA_TRY(h, cudaEventRecord(h->ev1, s));
         CUDA_TRY(h, cudaMemcpyAsync(h->pdesc, h->ddesc, sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(h, cudaStreamSynchronize(s));
+        adopt_tableau(h);
         float t = 0.0f;
         cudaEventElapsedTime(&t, h->ev0, h->ev1);
         h->fp32_kernel_ms += t;
@@ -555,7 +590,7 @@ lp_err lp_solve_async(lp_handle *h) {
     cudaStream_t s = h->stream;
     // The pivot state (iterations, degeneracy counter) lives in the device
     // descriptor, so consecutive calls resume without a host round trip.
-    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, 128 * sizeof(unsigned), s));
+    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, kBarWords * sizeof(unsigned), s));
     CUDA_TRY(h, cudaEventRecord(h->ev0, s));
     CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape, h->opt.spin_timeout_cycles,
                              h->opt.max_iters, s));
@@ -660,6 +695,8 @@ lp_err lp_get_tableau(lp_handle *h, double *T) {
     }
     CUDA_TRY(h, cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (h->solved) adopt_tableau(h);
     if (h->prec == PREC_FP64) {
         CUDA_TRY(h, cudaMemcpy2DAsync(T, sizeof(double) * h->N, h->dT, sizeof(double) * h->P,
                                       sizeof(double) * h->N, h->M, cudaMemcpyDefault, s));

@@ -52,18 +52,33 @@ struct LpDesc {
     int last_p, last_q;
     // batched launches: CTAs per LP and their column strip width
     int group, strip;
+    // pipelined primal kernel: second tableau buffer, the pivot column of the
+    // next pivot (2 x M, by parity), ratio-test partials, and which buffer
+    // holds the current tableau (0: T, 1: T2)
+    void *T2;
+    void *colbuf;
+    Cand *part_ratio;
+    int cur;
+    int pad2_;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
 struct PivotShape {
-    int ctas;                  // grid size (= number of column strips)
-    int threads;               // CTA size
-    int strip;                 // columns per strip (multiple of 32 bytes of elements)
-    int use_smem;              // selection scratch in shared memory (else global)
-    int dual;                  // dual simplex kernel (else primal)
-    size_t smem_bytes;         // dynamic shared memory per CTA
-    long long scratch_stride;  // global scratch bytes per CTA when !use_smem
+    int ctas = 0;                  // grid size (= number of column strips)
+    int threads = 0;               // CTA size
+    int strip = 0;                 // columns per strip (multiple of 32 bytes of elements)
+    int use_smem = 0;              // selection scratch in shared memory (else global)
+    int dual = 0;                  // dual simplex kernel (else primal)
+    int pipe = 0;                  // pipelined primal kernel (double-buffered tableau)
+    size_t smem_bytes = 0;         // dynamic shared memory per CTA
+    long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };
+
+// Words of a pivot launch's synchronisation block (zeroed before each launch):
+// [0] grid-barrier count, [32] its generation, [64] readers counter (in-place
+// kernel) or pricing-partials counter (pipelined kernel), [96] error flag,
+// [128] ratio-partials counter (pipelined kernel); 128-byte apart.
+constexpr int kBarWords = 256;
 
 struct InputStats {
     unsigned long long amax_bits, bmax_bits, cmax_bits;  // bit patterns of max |.|
@@ -90,6 +105,12 @@ cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems,
                          int ctas, int threads, size_t smem, int use_smem, long long spin_limit,
                          long long budget, cudaStream_t s);
 int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, int sms);
+// Pipelined primal kernel (double-buffered tableau, selection overlapped).
+// The returned shape has pipe == 0 when the kernel cannot take the LP (a grid
+// larger than one CTA per SM, or too much shared memory).
+PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas);
+cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
+                              long long spin_limit, long long budget, cudaStream_t s);
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,
                            int m, int n, long long P, int sense, double *x, double *y,
                            double *obj, cudaStream_t s);

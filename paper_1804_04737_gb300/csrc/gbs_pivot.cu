@@ -38,6 +38,8 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "gbs_device.cuh"
@@ -388,6 +390,359 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // together.  A group waits only on CTAs that hold earlier items, whose groups
 // are complete, so every group forms (the launch has at least max(group)
 // co-resident CTAs); all waits are bounded anyway.
+// ---------------------------------------------------------------------------
+// Pipelined primal simplex for one LP (FP64 or FP32 tableau).
+//
+// Two tableau buffers: pivot k reads buffer `cur` and writes buffer cur^1, so
+// nothing a CTA reads during pivot k is written during pivot k.  In every CTA
+// the last warp selects pivot k+1 while the other warps stream pivot k's
+// update:
+//   update warps     divide the CTA's strip of the pivot row (Step 4), update
+//                    the strip of the objective row first and publish its
+//                    pricing partial (pricing counter), then update the rest
+//                    of the strip (Step 5);
+//   selection warp   once all pricing partials are in, reduces them to the
+//                    entering column q' (Step 2), forms its block of rows of
+//                    column q' and of the rhs of tableau k+1 from buffer `cur`
+//                    with the very fma the update uses (so the values are bit
+//                    for bit those the update writes), runs the screened
+//                    ratio test on them (Step 3), publishes its partial
+//                    (ratio counter) and the block of the next pivot column,
+//                    and reduces the ratio partials to the pivot row p'.
+// One grid barrier ends the pivot.  Selection thus overlaps the update
+// instead of preceding it.  The first pivot's selection runs alone.
+
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ Cand warp_partials_min(const Cand *part, int G) {
+    Cand c = cand_empty();
+    for (int k = threadIdx.x & 31; k < G; k += 32) {
+        Cand e;
+        e.vk = __ldcg(&part[k].vk);
+        e.key = __ldcg(&part[k].key);
+        e.idx = __ldcg(&part[k].idx);
+        if (cand_less(e, c)) c = e;
+    }
+    return warp_min(c);
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Lane 0 waits (bounded) until *ctr reaches target; the warp learns the outcome.
+__device__ __forceinline__ bool warp_wait(unsigned *ctr, unsigned target, int *err,
+                                          long long spin_limit) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        const long long t0 = clock64();
+        while ((int)(ld_acquire(ctr) - target) < 0) {
+            if (clock64() - t0 > spin_limit || *(volatile int *)err) {
+                atomicExch(err, 1);
+                ok = 0;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    pivot_pipe_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    typedef typename Vec<T>::type V;
+    constexpr int VW = Vec<T>::W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Cand rbuf[3][32];
+    __shared__ unsigned long long ubuf[32];
+    __shared__ Cand wpart[32];
+    __shared__ int s_flag, s_p, s_q, s_status;
+    __shared__ unsigned long long s_rmin;
+
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+    const int NU = B - 32;  // update threads; the last warp selects
+    const int lane = tid & 31;
+    const bool selw = tid >= NU;
+    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
+    const long long P = d->P;
+    const int m = d->m, M = d->M, N = d->N;
+    T *colb[2] = {reinterpret_cast<T *>(d->colbuf), reinterpret_cast<T *>(d->colbuf) + M};
+    int *__restrict__ basis = d->basis;
+    const int bland_after = d->bland_after;
+    const unsigned long long lim_p = okey((T)d->eps_p);
+    const unsigned long long lim_d = okey((T)(-d->eps_d));
+    const unsigned long long zero_k = okey((T)0);
+    long long iters = d->iters;
+    const long long iter_limit =
+        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
+    int deg = d->deg;
+    int cur = d->cur;
+    int status = ST_RUNNING;
+    unsigned *pcnt = d->bar + 64, *rcnt = d->bar + 128;
+
+    // strip and thread map of the update threads
+    const int c0 = g * W;
+    const int c1 = (int)min((long long)c0 + W, P);
+    const int vpr = (c1 - c0) / VW;
+    const int rpp = NU / vpr;  // >= 1: the host keeps W <= NU * VW
+    const int lr = tid / vpr, lv = tid - lr * vpr;
+    const bool active = !selw && lr < rpp;
+    const int col0 = c0 + lv * VW;
+    // the selection warp's block of rows, and its scratch
+    const int RPC = (M + G - 1) / G;
+    const int r0 = min(M, g * RPC), r1 = min(M, r0 + RPC);
+    T *sprow = reinterpret_cast<T *>(smem_raw);
+    unsigned char *sel_raw = smem_raw + (((size_t)W * sizeof(T) + 15) & ~(size_t)15);
+    unsigned long long *s_rk = reinterpret_cast<unsigned long long *>(sel_raw);
+    T *s_num = reinterpret_cast<T *>(s_rk + RPC);
+    T *s_a = s_num + RPC;
+
+    // ---- selection of the first pivot from the current tableau (all threads) ----
+    int p = -1, q = -1;
+    {
+        const T *A = bufs[cur];
+        const int bland = deg >= bland_after;
+        Cand c = cand_empty();
+        const T *z = A + (long long)m * P;
+        for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
+            const unsigned long long zk = okey(lds(z + j));
+            if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
+        }
+        c = block_min_c(c, rbuf[0]);
+        if (tid == 0) d->part_sel[g] = c;
+        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
+        if (status == ST_RUNNING) {
+            const Cand sel = load_partials_min(d->part_sel, G, rbuf[1]);
+            if (sel.idx < 0) status = ST_OPTIMAL;
+            else if (iters >= iter_limit) status = ST_ITER_LIMIT;
+            else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: see the loop's checks
+            else q = sel.idx;
+        }
+        if (status == ST_RUNNING) {
+            unsigned long long lmin = ~0ull;
+            for (int i = r0 + tid; i < r1; i += B) {
+                const T a = lds(A + (long long)i * P + q);
+                const T rhs = lds(A + (long long)i * P + (N - 1));
+                colb[0][i] = a;
+                unsigned long long rk = ~0ull;
+                if (i < m && okey(a) > lim_p) rk = screen_key(pos_part(rhs), a);
+                s_rk[i - r0] = rk;
+                s_num[i - r0] = pos_part(rhs);
+                s_a[i - r0] = a;
+                lmin = rk < lmin ? rk : lmin;
+            }
+            const unsigned long long rstar = block_min_u(lmin, ubuf);
+            Cand rc = cand_empty();
+            if (rstar != ~0ull) {
+                const unsigned long long thr = screen_thr(rstar, (T)0);
+                for (int i = r0 + tid; i < r1; i += B)
+                    if (s_rk[i - r0] <= thr)
+                        cand_take(rc, okey(s_num[i - r0] / s_a[i - r0]),
+                                  bland ? __ldcg(basis + i) : i, i);
+            }
+            rc = block_min_c(rc, rbuf[2]);
+            if (tid == 0) d->part_ratio[g] = rc;
+            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
+        }
+        if (status == ST_RUNNING) {
+            const Cand rc = load_partials_min(d->part_ratio, G, rbuf[0]);
+            if (rc.idx < 0) {
+                status = ST_UNBOUNDED;
+            } else if (rc.idx >= m) {
+                status = ST_TIMEOUT;
+            } else {
+                p = rc.idx;
+                deg = (rc.vk == zero_k) ? deg + 1 : 0;
+            }
+        }
+    }
+
+    int lk = 0;  // pivots made in this launch (parity of partials and pivot-column buffers)
+    while (status == ST_RUNNING) {
+        T *A = bufs[cur], *Bn = bufs[cur ^ 1];
+        const T *col = colb[lk & 1];
+        T *ncol = colb[(lk + 1) & 1];
+        if (g == 0 && tid == 0) {
+            if (iters < d->trace_cap) {
+                d->trace[2 * iters] = p;
+                d->trace[2 * iters + 1] = q;
+            }
+            basis[p] = q;
+            d->last_p = p;
+            d->last_q = q;
+        }
+        const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
+        const T piv = lds(col + p);
+        if (!selw) {
+            // Step 4 on this CTA's strip of the pivot row
+            for (int j = c0 + tid; j < c1; j += NU)
+                sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
+            named_sync(1, NU);
+            // the objective row first: it feeds pivot k+1's pricing
+            Cand c = cand_empty();
+            const T colm = lds(col + m);
+            for (int v = tid; v < vpr; v += NU) {
+                const int j0 = c0 + v * VW;
+                const V pr = *reinterpret_cast<const V *>(sprow + v * VW);
+                V t = ldv(reinterpret_cast<const V *>(A + (long long)m * P + j0));
+                vfma(t, colm, pr);
+                *reinterpret_cast<V *>(Bn + (long long)m * P + j0) = t;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    const int j = j0 + k;
+                    const unsigned long long zk = okey(getc(t, k));
+                    if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
+                }
+            }
+            c = warp_min(c);
+            if (lane == 0) wpart[tid >> 5] = c;
+            named_sync(1, NU);
+            if (tid == 0) {
+                Cand r = wpart[0];
+                for (int w = 1; w < NU / 32; ++w)
+                    if (cand_less(wpart[w], r)) r = wpart[w];
+                d->part_sel[((lk + 1) & 1) * G + g] = r;
+                __threadfence();
+                red_add_release(pcnt, 1u);
+            }
+            // Step 5 on the constraint rows of the strip
+            if (active) {
+                const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
+                const T *abase = A + col0;
+                T *bbase = Bn + col0;
+                int i = lr;
+                for (; i + 3 * rpp < m; i += 4 * rpp) {
+                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                    const T a0 = lds(col + i), a1 = lds(col + i1), a2 = lds(col + i2),
+                            a3 = lds(col + i3);
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p, a0, pr);
+                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p, a1, pr);
+                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p, a2, pr);
+                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p, a3, pr);
+                }
+                for (; i < m; i += rpp) {
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) =
+                        pivot_vec<T>(t0, i, p, lds(col + i), pr);
+                }
+            }
+        } else {
+            // selection of pivot k+1, overlapping the update of pivot k
+            int st = ST_RUNNING, np = -1, nq = -1;
+            unsigned long long nrmin = 0ull;
+            if (!warp_wait(pcnt, (unsigned)G * (unsigned)(lk + 1), d->err, spin_limit)) {
+                st = ST_TIMEOUT;
+            } else {
+                const Cand sel = warp_partials_min(d->part_sel + ((lk + 1) & 1) * G, G);
+                if (sel.idx < 0) st = ST_OPTIMAL;
+                else if (iters + 1 >= iter_limit) st = ST_ITER_LIMIT;
+                else nq = sel.idx;
+                if (st == ST_RUNNING && nq >= N - 1) {  // never: a partial from outside the row
+                    if (lane == 0) atomicExch(d->err, 1);
+                    st = ST_TIMEOUT;
+                }
+            }
+            if (st == ST_RUNNING) {
+                const T prq = lds(A + (long long)p * P + nq) / piv;
+                const T prr = lds(A + (long long)p * P + (N - 1)) / piv;
+                unsigned long long lmin = ~0ull;
+                for (int i = r0 + lane; i < r1; i += 32) {
+                    const T ci = lds(col + i);
+                    const T a0 = lds(A + (long long)i * P + nq);
+                    const T h0 = lds(A + (long long)i * P + (N - 1));
+                    const T a = (i == p) ? prq : tfma(-ci, prq, a0);
+                    const T rhs = (i == p) ? prr : tfma(-ci, prr, h0);
+                    ncol[i] = a;
+                    unsigned long long rk = ~0ull;
+                    if (i < m && okey(a) > lim_p) rk = screen_key(pos_part(rhs), a);
+                    s_rk[i - r0] = rk;
+                    s_num[i - r0] = pos_part(rhs);
+                    s_a[i - r0] = a;
+                    lmin = rk < lmin ? rk : lmin;
+                }
+                __syncwarp();
+                const unsigned long long rstar = warp_min_u(lmin);
+                Cand rc = cand_empty();
+                if (rstar != ~0ull) {
+                    const unsigned long long thr = screen_thr(rstar, (T)0);
+                    for (int i = r0 + lane; i < r1; i += 32)
+                        if (s_rk[i - r0] <= thr) {
+                            const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
+                            cand_take(rc, okey(s_num[i - r0] / s_a[i - r0]), key, i);
+                        }
+                }
+                rc = warp_min(rc);
+                if (lane == 0) {
+                    d->part_ratio[g] = rc;
+                    __threadfence();
+                    red_add_release(rcnt, 1u);
+                }
+                if (!warp_wait(rcnt, (unsigned)G * (unsigned)(lk + 1), d->err, spin_limit)) {
+                    st = ST_TIMEOUT;
+                } else {
+                    const Cand r = warp_partials_min(d->part_ratio, G);
+                    if (r.idx < 0) {
+                        st = ST_UNBOUNDED;
+                    } else if (r.idx >= m) {  // never: a partial from outside the column
+                        if (lane == 0) atomicExch(d->err, 1);
+                        st = ST_TIMEOUT;
+                    } else {
+                        np = r.idx;
+                        nrmin = r.vk;
+                    }
+                }
+            }
+            if (lane == 0) {
+                s_status = st;
+                s_p = np;
+                s_q = nq;
+                s_rmin = nrmin;
+            }
+        }
+        __syncthreads();
+        ++iters;
+        ++lk;
+        cur ^= 1;
+        status = s_status;
+        if (status == ST_RUNNING) {
+            p = s_p;
+            q = s_q;
+            deg = (s_rmin == zero_k) ? deg + 1 : 0;
+        }
+        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+    }
+
+    if (g == 0 && tid == 0) {
+        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
+        d->iters = iters;
+        d->iter_limit = iter_limit;
+        d->deg = deg;
+        // hand over the buffer holding the last tableau as the current one
+        d->T = bufs[cur];
+        d->T2 = bufs[cur ^ 1];
+        d->cur = 0;
+    }
+}
+
 constexpr int kBatchThreads = 512;  // register room for both pivot rules in one kernel
 
 // ---------------------------------------------------------------------------
@@ -741,8 +1096,9 @@ __global__ void build_kernel(const double *__restrict__ A, const double *__restr
 
 // Solution read-off, part 1: zero x, duals from the objective row, objective.
 template <typename T>
-__global__ void extract_kernel1(const T *__restrict__ Tab, int m, int n, long long P, int sense,
-                                double *x, double *y, double *obj) {
+__global__ void extract_kernel1(const LpDesc *__restrict__ d, const T *Tab, int m, int n,
+                                long long P, int sense, double *x, double *y, double *obj) {
+    if (d) Tab = reinterpret_cast<const T *>(d->T);  // the pivot kernel's current buffer
     const int N = n + m + 1;
     const T *z = Tab + (long long)m * P;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -758,8 +1114,10 @@ __global__ void extract_kernel1(const T *__restrict__ Tab, int m, int n, long lo
 
 // Part 2: x_j = rhs of the row where j is basic.
 template <typename T>
-__global__ void extract_kernel2(const T *__restrict__ Tab, const int *__restrict__ basis, int m,
-                                int n, long long P, double *x) {
+__global__ void extract_kernel2(const LpDesc *__restrict__ d, const T *Tab,
+                                const int *__restrict__ basis, int m, int n, long long P,
+                                double *x) {
+    if (d) Tab = reinterpret_cast<const T *>(d->T);
     const int N = n + m + 1;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride) {
@@ -852,6 +1210,7 @@ PivotShape choose_shape(int prec, int sense, int M, int N, long long P, int sms,
 
 cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long long spin_limit,
                          long long budget, cudaStream_t s) {
+    if (sh.pipe) return launch_pivot_pipe(prec, d_desc, sh, spin_limit, budget, s);
     int W = sh.strip;
     void *args[] = {&d_desc, &W, &spin_limit, &budget};
     const void *fn;
@@ -878,6 +1237,50 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
     // A cooperative launch fails instead of running when the grid cannot be
     // co-resident, which the grid barrier needs.
     return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
+}
+
+cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
+                              long long spin_limit, long long budget, cudaStream_t s) {
+    int W = sh.strip;
+    void *args[] = {&d_desc, &W, &spin_limit, &budget};
+    const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_kernel<double>
+                                       : (const void *)pivot_pipe_kernel<float>;
+    if (sh.smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sh.smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
+}
+
+// Launch shape of the pipelined kernel: strips sized for the update threads
+// (all but the last warp), shared memory for the strip and the selection
+// warp's block of rows.
+PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas) {
+    PivotShape sh;
+    const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
+    const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
+    sh.threads = threads > 0 ? threads : kMaxThreads;
+    sh.threads = std::min(kMaxThreads, std::max(128, (sh.threads + 31) / 32 * 32));
+    const int nu = sh.threads - 32;
+    long long g = ctas > 0 ? ctas : std::min<long long>(sms, ((long long)M * P + 32767) / 32768);
+    const long long gmin = (P + (long long)nu * vw - 1) / ((long long)nu * vw);
+    g = std::max<long long>(std::max<long long>(g, gmin), 1);
+    long long w = (P + g - 1) / g;
+    w = (w + sector - 1) / sector * sector;
+    if (w > (long long)nu * vw) w = (long long)nu * vw / sector * sector;
+    sh.strip = (int)w;
+    sh.ctas = (int)((P + w - 1) / w);
+    const long long rpc = (M + sh.ctas - 1) / sh.ctas;
+    sh.smem_bytes = (((size_t)w * esz + 15) & ~(size_t)15) + (size_t)rpc * (8 + 2 * esz) + 16;
+    sh.use_smem = 1;
+    sh.scratch_stride = 0;
+    sh.dual = 0;
+    // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
+    // launch), the strip one pass of the update threads
+    sh.pipe = sh.ctas <= sms && sh.smem_bytes <= kMaxDynSmem &&
+              (long long)sh.strip <= (long long)nu * vw;
+    return sh;
 }
 
 cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing *ring_dev,
@@ -934,20 +1337,20 @@ int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, 
     return per_sm * sms;
 }
 
-cudaError_t launch_extract(int prec, const LpDesc *, const void *T, const int *basis, int m,
-                           int n, long long P, int sense, double *x, double *y, double *obj,
-                           cudaStream_t s) {
+cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,
+                           int m, int n, long long P, int sense, double *x, double *y,
+                           double *obj, cudaStream_t s) {
     const long long work = (long long)(m > n ? m : n);
     if (prec == PREC_FP64) {
-        extract_kernel1<double><<<grid_for(work, 256), 256, 0, s>>>((const double *)T, m, n, P,
-                                                                    sense, x, y, obj);
-        extract_kernel2<double><<<grid_for(m, 256), 256, 0, s>>>((const double *)T, basis, m, n,
-                                                                 P, x);
+        extract_kernel1<double><<<grid_for(work, 256), 256, 0, s>>>(
+            d_desc, (const double *)T, m, n, P, sense, x, y, obj);
+        extract_kernel2<double><<<grid_for(m, 256), 256, 0, s>>>(d_desc, (const double *)T,
+                                                                 basis, m, n, P, x);
     } else {
-        extract_kernel1<float><<<grid_for(work, 256), 256, 0, s>>>((const float *)T, m, n, P,
-                                                                   sense, x, y, obj);
-        extract_kernel2<float><<<grid_for(m, 256), 256, 0, s>>>((const float *)T, basis, m, n,
-                                                                P, x);
+        extract_kernel1<float><<<grid_for(work, 256), 256, 0, s>>>(
+            d_desc, (const float *)T, m, n, P, sense, x, y, obj);
+        extract_kernel2<float><<<grid_for(m, 256), 256, 0, s>>>(d_desc, (const float *)T, basis,
+                                                                m, n, P, x);
     }
     return cudaGetLastError();
 }

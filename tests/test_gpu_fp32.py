@@ -65,10 +65,11 @@ def test_fp32_objective_vs_fp64_oracle(m, n, sense):
 
 
 @pytest.mark.parametrize("k", [1, 7, 50, 200])
-def test_fp32_reinversion_period(k):
+@pytest.mark.parametrize("pipeline", [0, 1])
+def test_fp32_reinversion_period(k, pipeline):
     A, b, c = lpgen.dense_lp(400, 500, seed=3)
     o = oracle.solve(A, b, c)
-    obj, st, it, x, y, _ = _fp32(A, b, c, reinv_k=k)
+    obj, st, it, x, y, _ = _fp32(A, b, c, reinv_k=k, pipeline=pipeline)
     assert st == capi.LP_OPTIMAL and _rel(obj, o.obj) <= OBJ_TOL
 
 
