@@ -110,11 +110,18 @@ typedef struct {
     long long trace_cap;     /* record (row, column) of the first trace_cap pivots */
     long long group_elems;   /* batched solves: tableau elements per CTA of an LP's
                                 group, 0 = 262144 (see lp_solve_batch)            */
-    int pipeline;            /* single-LP primal simplex: 1 = pipelined kernel
-                                (two tableau buffers; the next pivot's selection
-                                overlaps this pivot's update), 0 = in-place
-                                kernel (one buffer, selection then update).
-                                Same pivots and bits either way.                  */
+    int pipeline;            /* single-LP primal simplex kernel:
+                                0 = selection, then update (one launch-wide
+                                    grid barrier per pivot);
+                                1 = auto (default): 2 when the tableau fits the
+                                    L2 cache, else 3, else 0 when the second
+                                    buffer cannot be allocated;
+                                2 = pipelined in place: the next pivot's
+                                    selection overlaps this pivot's update, no
+                                    grid barrier;
+                                3 = pipelined, double-buffered tableau (twice
+                                    the memory), a grid barrier per pivot.
+                                Same pivots and bits in every mode.              */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances

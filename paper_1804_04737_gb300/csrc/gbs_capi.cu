@@ -20,6 +20,11 @@
 
 using namespace gbs;
 
+// Tableaus up to this size stay resident in the 129 MB L2 cache across
+// pivots when updated in place; the pipelined kernel runs in place below it
+// and double-buffered above it.
+constexpr size_t kL2FitBytes = 96ull << 20;
+
 struct lp_handle {
     lp_options opt;
     int device = 0;
@@ -40,7 +45,7 @@ struct lp_handle {
     size_t cap_A = 0, cap_b = 0, cap_c = 0;  // element capacities
     void *dT = nullptr;                         // the current tableau
     size_t cap_T = 0;                           // bytes
-    void *dT2 = nullptr;                        // pipelined kernel: the other buffer
+    void *dT2 = nullptr;                        // double-buffered pipelined kernel
     size_t cap_T2 = 0;
     void *dcol = nullptr;                       // pipelined kernel: 2 pivot columns
     size_t cap_col = 0;
@@ -48,7 +53,7 @@ struct lp_handle {
     size_t cap_basis = 0;
     void *dscratch = nullptr;
     size_t cap_scratch = 0;                     // bytes
-    Cand *dpart = nullptr;                      // 3 * max_ctas (selection, ratio)
+    Cand *dpart = nullptr;                      // 8 * max_ctas (records)
     int max_ctas = 0;
     unsigned *dbar = nullptr;                   // kBarWords: barrier, counters, err
     int *dtrace = nullptr;
@@ -262,9 +267,26 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    // the primal rule runs on the pipelined kernel where it can take the LP
+    // the primal rule runs on the pipelined kernel where it can take the LP;
+    // double-buffered for tableaus larger than the L2 cache
+    // (the primal rule runs for LP_MAX_LE, and in FP32 mode for either sense)
+    const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
+    int pmode = primal ? h->opt.pipeline : 0;
+    if (pmode == 1) pmode = (size_t)M * P * esz <= kL2FitBytes ? 2 : 3;
+    if (pmode == 3 && grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz) != cudaSuccess) {
+        cudaGetLastError();
+        pmode = h->opt.pipeline == 1 ? 0 : -1;
+    }
+    if (pmode < 0) {
+        set_err(h, "lp_load: no device memory for the second tableau buffer (pipeline 3)");
+        return LP_ERR_OOM;
+    }
+    if (pmode != 0 && pmode != 2 && pmode != 3) {
+        set_err(h, "lp_load: unknown pipeline mode %d", h->opt.pipeline);
+        return LP_ERR_INVALID_ARG;
+    }
     auto shape_for = [&](int rule) {
-        if (rule == 0 && h->opt.pipeline) {
+        if (rule == 0 && pmode) {
             const PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads,
                                                     h->opt.ctas);
             if (ps.pipe) return ps;
@@ -281,10 +303,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
     CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
     CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
-    if (pipe) {
-        CUDA_TRY(h, grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz));
-        CUDA_TRY(h, grow_bytes(&h->dcol, &h->cap_col, 2 * (size_t)M * esz));
-    }
+    if (pipe) CUDA_TRY(h, grow_bytes(&h->dcol, &h->cap_col, 2 * (size_t)M * esz));
     CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
     {
         size_t need = sh.use_smem ? 0 : (size_t)sh.ctas * (size_t)sh.scratch_stride;
@@ -296,7 +315,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
         h->max_ctas = 0;
-        CUDA_TRY(h, cudaMalloc(&h->dpart, 3 * (size_t)ctas_max * sizeof(Cand)));
+        CUDA_TRY(h, cudaMalloc(&h->dpart, 8 * (size_t)ctas_max * sizeof(Cand)));
         h->max_ctas = ctas_max;
     }
     if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
@@ -373,9 +392,9 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.scratch_stride = sh.scratch_stride;
     d.part_sel = h->dpart;
     d.part_ratio = h->dpart + 2 * (size_t)h->max_ctas;
-    d.T2 = pipe ? h->dT2 : nullptr;
+    d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 4 * (size_t)h->max_ctas);
+    d.T2 = pipe && pmode == 3 ? h->dT2 : nullptr;
     d.colbuf = pipe ? h->dcol : nullptr;
-    d.cur = 0;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;
@@ -414,15 +433,13 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
 
 namespace {
 
-// The pipelined kernel leaves its last tableau in either buffer and names it
-// in the descriptor; once the descriptor is read back, make it h->dT.
+// The double-buffered kernel leaves its last tableau in either buffer and
+// names it in the descriptor; once the descriptor is read back, make it h->dT.
 void adopt_tableau(lp_handle *h) {
     if (h->pdesc->T != h->dT && h->pdesc->T == h->dT2) {
         std::swap(h->dT, h->dT2);
         std::swap(h->cap_T, h->cap_T2);
     }
-    h->desc.T = h->dT;
-    h->desc.T2 = h->dT2;
 }
 
 double okey_to_double(unsigned long long k) {
@@ -696,7 +713,7 @@ lp_err lp_get_tableau(lp_handle *h, double *T) {
     CUDA_TRY(h, cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    if (h->solved) adopt_tableau(h);
+    adopt_tableau(h);
     if (h->prec == PREC_FP64) {
         CUDA_TRY(h, cudaMemcpy2DAsync(T, sizeof(double) * h->N, h->dT, sizeof(double) * h->P,
                                       sizeof(double) * h->N, h->M, cudaMemcpyDefault, s));

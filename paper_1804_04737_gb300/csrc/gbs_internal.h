@@ -52,14 +52,14 @@ struct LpDesc {
     int last_p, last_q;
     // batched launches: CTAs per LP and their column strip width
     int group, strip;
-    // pipelined primal kernel: second tableau buffer, the pivot column of the
-    // next pivot (2 x M, by parity), ratio-test partials, and which buffer
-    // holds the current tableau (0: T, 1: T2)
+    // pipelined primal kernel: the second tableau buffer (double-buffered
+    // mode; nullptr in place), the pivot columns of this and the next pivot
+    // (2 x M elements, by parity), the ratio records (2 x G, by parity) and
+    // the values that come with the pricing and ratio records (4 x G pairs)
     void *T2;
     void *colbuf;
     Cand *part_ratio;
-    int cur;
-    int pad2_;
+    unsigned long long *part_vals;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
@@ -69,7 +69,7 @@ struct PivotShape {
     int strip = 0;                 // columns per strip (multiple of 32 bytes of elements)
     int use_smem = 0;              // selection scratch in shared memory (else global)
     int dual = 0;                  // dual simplex kernel (else primal)
-    int pipe = 0;                  // pipelined primal kernel (double-buffered tableau)
+    int pipe = 0;                  // pipelined primal kernel
     size_t smem_bytes = 0;         // dynamic shared memory per CTA
     long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };
@@ -105,7 +105,7 @@ cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems,
                          int ctas, int threads, size_t smem, int use_smem, long long spin_limit,
                          long long budget, cudaStream_t s);
 int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, int sms);
-// Pipelined primal kernel (double-buffered tableau, selection overlapped).
+// Pipelined primal kernel (selection of pivot k+1 overlapped with pivot k's update).
 // The returned shape has pipe == 0 when the kernel cannot take the LP (a grid
 // larger than one CTA per SM, or too much shared memory).
 PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas);

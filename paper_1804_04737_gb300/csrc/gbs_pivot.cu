@@ -40,6 +40,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "gbs_device.cuh"
@@ -384,33 +385,39 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     solve_lp<T, SMEM, DUAL>(d, gridDim.x, blockIdx.x, W, spin_limit, budget, smem_raw);
 }
 
-// Many LPs in one persistent launch.  items[] lists (lp, rank) pairs, the
-// ranks of one LP consecutive, largest LPs first; CTAs pop items in order
-// from *queue, and the d->group CTAs that pop the ranks of one LP solve it
-// together.  A group waits only on CTAs that hold earlier items, whose groups
-// are complete, so every group forms (the launch has at least max(group)
-// co-resident CTAs); all waits are bounded anyway.
 // ---------------------------------------------------------------------------
-// Pipelined primal simplex for one LP (FP64 or FP32 tableau).
+// Pipelined primal simplex for one LP (FP64 or FP32 tableau), in place.
 //
-// Two tableau buffers: pivot k reads buffer `cur` and writes buffer cur^1, so
-// nothing a CTA reads during pivot k is written during pivot k.  In every CTA
-// the last warp selects pivot k+1 while the other warps stream pivot k's
-// update:
-//   update warps     divide the CTA's strip of the pivot row (Step 4), update
-//                    the strip of the objective row first and publish its
-//                    pricing partial (pricing counter), then update the rest
-//                    of the strip (Step 5);
-//   selection warp   once all pricing partials are in, reduces them to the
-//                    entering column q' (Step 2), forms its block of rows of
-//                    column q' and of the rhs of tableau k+1 from buffer `cur`
-//                    with the very fma the update uses (so the values are bit
-//                    for bit those the update writes), runs the screened
-//                    ratio test on them (Step 3), publishes its partial
-//                    (ratio counter) and the block of the next pivot column,
-//                    and reduces the ratio partials to the pivot row p'.
-// One grid barrier ends the pivot.  Selection thus overlaps the update
-// instead of preceding it.  The first pivot's selection runs alone.
+// In every CTA the last warp selects pivot k+1 while the other warps stream
+// pivot k's update of the CTA's column strip:
+//   update warps     divide the strip of the pivot row (Step 4), update the
+//                    strip of the objective row and publish the CTA's pricing
+//                    record (its best column, with the new pivot-row values at
+//                    that column and at the rhs), then update the rest of the
+//                    strip (Step 5) except two protected vectors: the one
+//                    holding the CTA's pricing winner and the one holding the
+//                    rhs.  Once every selection warp has finished reading
+//                    (ratio counter) they update the protected vectors.
+//   selection warp   reduces the pricing records to the entering column q'
+//                    (Step 2), forms its block of rows of column q' and of the
+//                    rhs of tableau k+1 with the very fma the update uses (so
+//                    the values are bit for bit those the update writes), runs
+//                    the screened ratio test on them (Step 3), publishes its
+//                    ratio record and its block of the next pivot column, and
+//                    reduces the ratio records to the pivot row p'.
+// The entering column is the pricing winner of the CTA that owns it, so the
+// columns the selection reads (q' and the rhs, of tableau k) are protected
+// vectors, unchanged while they are read.  There is no grid barrier per
+// pivot: a CTA publishes its pricing record only after finishing its previous
+// pivot, so the pricing counter also tells the selection warps that every
+// protected vector they read is up to date, and a CTA starts pivot k+1 only
+// after the ratio counter of pivot k is complete, so no CTA runs more than one
+// pivot ahead of another; records and pivot columns are double-buffered by
+// pivot parity.  The selection warp issues no floating-point division in the
+// common case (it competes for the FP64 pipe with the update): the pivot-row
+// values come with the pricing records, and the exact Step 3 quotient is
+// formed only when two screened ratios lie within the screening threshold.
+// The first pivot's selection runs alone, with grid barriers.
 
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
@@ -419,17 +426,8 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-__device__ __forceinline__ Cand warp_partials_min(const Cand *part, int G) {
-    Cand c = cand_empty();
-    for (int k = threadIdx.x & 31; k < G; k += 32) {
-        Cand e;
-        e.vk = __ldcg(&part[k].vk);
-        e.key = __ldcg(&part[k].key);
-        e.idx = __ldcg(&part[k].idx);
-        if (cand_less(e, c)) c = e;
-    }
-    return warp_min(c);
-}
+static_assert(sizeof(Cand) == 16 && offsetof(Cand, key) == 8 && offsetof(Cand, idx) == 12,
+              "Cand is read as one 16-byte vector");
 
 __device__ __forceinline__ unsigned long long warp_min_u(unsigned long long v) {
 #pragma unroll
@@ -459,6 +457,135 @@ __device__ __forceinline__ bool warp_wait(unsigned *ctr, unsigned target, int *e
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long tbits(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ unsigned long long tbits(float x) {
+    return (unsigned long long)__float_as_uint(x);
+}
+template <typename T>
+__device__ __forceinline__ T tfrom(unsigned long long u);
+template <>
+__device__ __forceinline__ double tfrom<double>(unsigned long long u) {
+    return __longlong_as_double((long long)u);
+}
+template <>
+__device__ __forceinline__ float tfrom<float>(unsigned long long u) {
+    return __uint_as_float((unsigned)u);
+}
+
+// Records of the pipelined kernel, one per CTA and pivot parity: a Cand and
+// two values.  A lane loads up to kRecPerLane of them in one round.
+constexpr int kRecPerLane = 5;  // grids of at most 160 CTAs
+constexpr int kMaxPipeCtas = 32 * kRecPerLane;
+
+__device__ __forceinline__ Cand unpack_cand(const ulonglong2 &v) {
+    Cand e;
+    e.vk = v.x;
+    e.key = (int)(unsigned)(v.y & 0xffffffffull);
+    e.idx = (int)(unsigned)(v.y >> 32);
+    return e;
+}
+
+// Entering column of pivot k+1 (every lane gets it): the minimum on (vk, key)
+// of the G pricing records, with the pivot-row value of that column that its
+// CTA published (vals[k].x).
+__device__ __forceinline__ Cand warp_price_min(const Cand *part, const ulonglong2 *vals, int G,
+                                               unsigned long long *prq) {
+    const int lane = threadIdx.x & 31;
+    ulonglong2 cv[kRecPerLane];
+    unsigned long long pv[kRecPerLane];
+#pragma unroll
+    for (int u = 0; u < kRecPerLane; ++u) {
+        const int k = lane + 32 * u;
+        cv[u] = k < G ? __ldcg(reinterpret_cast<const ulonglong2 *>(part) + k)
+                      : make_ulonglong2(~0ull, 0xffffffff7fffffffull);
+        pv[u] = k < G ? __ldcg(&vals[k].x) : 0ull;
+    }
+    Cand c = cand_empty();
+    unsigned long long bq = 0ull;
+#pragma unroll
+    for (int u = 0; u < kRecPerLane; ++u) {
+        const Cand e = unpack_cand(cv[u]);
+        if (cand_less(e, c)) {
+            c = e;
+            bq = pv[u];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Cand e;
+        e.vk = __shfl_xor_sync(0xffffffffu, c.vk, o);
+        e.key = __shfl_xor_sync(0xffffffffu, c.key, o);
+        e.idx = __shfl_xor_sync(0xffffffffu, c.idx, o);
+        const unsigned long long eq = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (cand_less(e, c)) {
+            c = e;
+            bq = eq;
+        }
+    }
+    *prq = bq;
+    return c;
+}
+
+// Pivot row of pivot k+1 from the G ratio records (every lane gets it).  A
+// record holds a CTA's exact winner: its screening key, tie key and row, and
+// (vals) the numerator and denominator of its Step 3 quotient.  The record
+// holding the exact minimum has a screening key within the threshold of the
+// smallest one, r*; when it is the only such record it is the answer,
+// otherwise the records within the threshold are compared by their exact
+// quotients, then by key.  *rzero: the selected quotient is +0.
+template <typename T>
+__device__ __forceinline__ int warp_ratio_min(const Cand *part, const ulonglong2 *vals, int G,
+                                              unsigned long long zero_k, bool *rzero) {
+    const int lane = threadIdx.x & 31;
+    ulonglong2 cv[kRecPerLane];
+#pragma unroll
+    for (int u = 0; u < kRecPerLane; ++u) {
+        const int k = lane + 32 * u;
+        cv[u] = k < G ? __ldcg(reinterpret_cast<const ulonglong2 *>(part) + k)
+                      : make_ulonglong2(~0ull, 0xffffffff7fffffffull);
+    }
+    unsigned long long r = ~0ull;
+#pragma unroll
+    for (int u = 0; u < kRecPerLane; ++u) r = cv[u].x < r ? cv[u].x : r;
+    r = warp_min_u(r);
+    *rzero = false;
+    if (r == ~0ull) return -1;
+    const unsigned long long thr = screen_thr(r, (T)0);
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < kRecPerLane; ++u) cnt += __popc(__ballot_sync(0xffffffffu, cv[u].x <= thr));
+    if (cnt == 1) {
+        int idx = -1;
+        unsigned long long rk = 0ull;
+#pragma unroll
+        for (int u = 0; u < kRecPerLane; ++u) {
+            const unsigned bal = __ballot_sync(0xffffffffu, cv[u].x <= thr);
+            if (bal) {
+                const int src = __ffs(bal) - 1;
+                idx = __shfl_sync(0xffffffffu, (int)(unsigned)(cv[u].y >> 32), src);
+                rk = __shfl_sync(0xffffffffu, cv[u].x, src);
+            }
+        }
+        *rzero = rk == zero_k;  // screening keys are +0 exactly for a +0 quotient
+        return idx;
+    }
+    Cand c = cand_empty();
+#pragma unroll
+    for (int u = 0; u < kRecPerLane; ++u) {
+        if (cv[u].x <= thr) {
+            const ulonglong2 nv = __ldcg(vals + lane + 32 * u);
+            const unsigned long long vk =
+                nv.x == 0ull ? zero_k : okey(tfrom<T>(nv.x) / tfrom<T>(nv.y));
+            cand_take(c, vk, (int)(unsigned)(cv[u].y & 0xffffffffull), (int)(unsigned)(cv[u].y >> 32));
+        }
+    }
+    c = warp_min(c);
+    *rzero = c.vk == zero_k;
+    return c.idx;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_pipe_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
@@ -468,14 +595,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand rbuf[3][32];
     __shared__ unsigned long long ubuf[32];
     __shared__ Cand wpart[32];
-    __shared__ int s_flag, s_p, s_q, s_status;
-    __shared__ unsigned long long s_rmin;
+    __shared__ int s_flag, s_p, s_q, s_status, s_jv, s_uok, s_rzero;
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     const int NU = B - 32;  // update threads; the last warp selects
     const int lane = tid & 31;
     const bool selw = tid >= NU;
-    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
+    // in place, or double-buffered (T2 set): pivot k reads bufs[cur] and
+    // writes bufs[cur ^ 1], with a grid barrier after each pivot
+    const bool db = d->T2 != nullptr;
+    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(db ? d->T2 : d->T)};
+    int cur = 0;
+    const T *Tab = bufs[0];
     const long long P = d->P;
     const int m = d->m, M = d->M, N = d->N;
     T *colb[2] = {reinterpret_cast<T *>(d->colbuf), reinterpret_cast<T *>(d->colbuf) + M};
@@ -488,18 +619,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const long long iter_limit =
         iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
     int deg = d->deg;
-    int cur = d->cur;
     int status = ST_RUNNING;
     unsigned *pcnt = d->bar + 64, *rcnt = d->bar + 128;
 
     // strip and thread map of the update threads
-    const int c0 = g * W;
+    const int c0 = g * W;  // < P: the host launches ceil(P / W) CTAs
     const int c1 = (int)min((long long)c0 + W, P);
     const int vpr = (c1 - c0) / VW;
     const int rpp = NU / vpr;  // >= 1: the host keeps W <= NU * VW
     const int lr = tid / vpr, lv = tid - lr * vpr;
     const bool active = !selw && lr < rpp;
     const int col0 = c0 + lv * VW;
+    // the vector of this strip holding the rhs column, or -1; protected from
+    // the in-place update until the selection has read it
+    const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
+    const int rvp = db ? -1 : rv;
     // the selection warp's block of rows, and its scratch
     const int RPC = (M + G - 1) / G;
     const int r0 = min(M, g * RPC), r1 = min(M, r0 + RPC);
@@ -512,10 +646,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // ---- selection of the first pivot from the current tableau (all threads) ----
     int p = -1, q = -1;
     {
-        const T *A = bufs[cur];
         const int bland = deg >= bland_after;
         Cand c = cand_empty();
-        const T *z = A + (long long)m * P;
+        const T *z = Tab + (long long)m * P;
         for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
             const unsigned long long zk = okey(lds(z + j));
             if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
@@ -533,8 +666,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (status == ST_RUNNING) {
             unsigned long long lmin = ~0ull;
             for (int i = r0 + tid; i < r1; i += B) {
-                const T a = lds(A + (long long)i * P + q);
-                const T rhs = lds(A + (long long)i * P + (N - 1));
+                const T a = lds(Tab + (long long)i * P + q);
+                const T rhs = lds(Tab + (long long)i * P + (N - 1));
                 colb[0][i] = a;
                 unsigned long long rk = ~0ull;
                 if (i < m && okey(a) > lim_p) rk = screen_key(pos_part(rhs), a);
@@ -569,11 +702,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         }
     }
 
-    int lk = 0;  // pivots made in this launch (parity of partials and pivot-column buffers)
+    int lk = 0;  // pivots made in this launch (parity of records and pivot-column buffers)
+    const int rowner = (N - 1) / W;  // the CTA whose strip holds the rhs column
     while (status == ST_RUNNING) {
-        T *A = bufs[cur], *Bn = bufs[cur ^ 1];
+        const T *A = bufs[cur];
+        T *Bn = bufs[cur ^ 1];
         const T *col = colb[lk & 1];
         T *ncol = colb[(lk + 1) & 1];
+        const int par = (lk + 1) & 1;  // records of the selection of pivot k+1
+        Cand *psel = d->part_sel + par * G;
+        ulonglong2 *pval = reinterpret_cast<ulonglong2 *>(d->part_vals) + par * G;
+        Cand *prat = d->part_ratio + par * G;
+        ulonglong2 *rval = reinterpret_cast<ulonglong2 *>(d->part_vals) + (2 + par) * G;
+        const unsigned target = (unsigned)G * (unsigned)(lk + 1);
         if (g == 0 && tid == 0) {
             if (iters < d->trace_cap) {
                 d->trace[2 * iters] = p;
@@ -584,25 +725,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             d->last_q = q;
         }
         const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
-        const T piv = lds(col + p);
         if (!selw) {
+            const T piv = lds(col + p);
             // Step 4 on this CTA's strip of the pivot row
             for (int j = c0 + tid; j < c1; j += NU)
                 sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
             named_sync(1, NU);
-            // the objective row first: it feeds pivot k+1's pricing
+            // the strip of the objective row, held back in registers, and the
+            // CTA's pricing candidate for pivot k+1
             Cand c = cand_empty();
-            const T colm = lds(col + m);
-            for (int v = tid; v < vpr; v += NU) {
-                const int j0 = c0 + v * VW;
-                const V pr = *reinterpret_cast<const V *>(sprow + v * VW);
-                V t = ldv(reinterpret_cast<const V *>(A + (long long)m * P + j0));
-                vfma(t, colm, pr);
-                *reinterpret_cast<V *>(Bn + (long long)m * P + j0) = t;
+            V zt;
+            const bool zown = tid < vpr;
+            if (zown) {
+                const T colm = lds(col + m);
+                const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
+                zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
+                vfma(zt, colm, pr);
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
-                    const int j = j0 + k;
-                    const unsigned long long zk = okey(getc(t, k));
+                    const int j = c0 + tid * VW + k;
+                    const unsigned long long zk = okey(getc(zt, k));
                     if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
                 }
             }
@@ -613,12 +755,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 Cand r = wpart[0];
                 for (int w = 1; w < NU / 32; ++w)
                     if (cand_less(wpart[w], r)) r = wpart[w];
-                d->part_sel[((lk + 1) & 1) * G + g] = r;
-                __threadfence();
+                psel[g] = r;
+                // with it, the new pivot-row values the selection needs from
+                // this strip: at the candidate column and at the rhs
+                pval[g] = make_ulonglong2(r.idx >= 0 ? tbits(sprow[r.idx - c0]) : 0ull,
+                                          rv >= 0 ? tbits(sprow[N - 1 - c0]) : 0ull);
                 red_add_release(pcnt, 1u);
+                s_jv = (r.idx >= 0 && !db) ? (r.idx - c0) / VW : -1;
             }
-            // Step 5 on the constraint rows of the strip
-            if (active) {
+            named_sync(1, NU);
+            const int jv = s_jv;  // protected: the vector of the CTA's candidate
+            if (zown && tid != jv && tid != rvp)
+                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
+            // Step 5 on the constraint rows of the strip, but the protected vectors
+            if (active && lv != jv && lv != rvp) {
                 const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
                 const T *abase = A + col0;
                 T *bbase = Bn + col0;
@@ -642,69 +792,130 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         pivot_vec<T>(t0, i, p, lds(col + i), pr);
                 }
             }
+            // every selection warp is done reading the protected vectors (in
+            // place; double-buffered, nothing this pivot writes is read)
+            if (db) {
+                if (tid == 0) s_uok = 1;
+            } else if (tid == 0) {
+                int ok = 1;
+                const long long t0 = clock64();
+                while ((int)(ld_acquire(rcnt) - target) < 0) {
+                    if (clock64() - t0 > spin_limit || *(volatile int *)d->err) {
+                        atomicExch(d->err, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+                s_uok = ok;
+            }
+            named_sync(1, NU);
+            if (s_uok) {
+                // the protected vectors, every row, spread over the update threads
+                for (int k = 0; k < 2; ++k) {
+                    const int v = k == 0 ? jv : (rvp != jv ? rvp : -1);
+                    if (v < 0) continue;
+                    const V vpr_ = *reinterpret_cast<const V *>(sprow + v * VW);
+                    T *vbase = Bn + c0 + v * VW;
+                    for (int i = tid; i < M; i += NU) {
+                        V *p0 = reinterpret_cast<V *>(vbase + (long long)i * P);
+                        *p0 = pivot_vec<T>(ldv(p0), i, p, lds(col + i), vpr_);
+                    }
+                }
+            }
         } else {
             // selection of pivot k+1, overlapping the update of pivot k
             int st = ST_RUNNING, np = -1, nq = -1;
-            unsigned long long nrmin = 0ull;
-            if (!warp_wait(pcnt, (unsigned)G * (unsigned)(lk + 1), d->err, spin_limit)) {
+            bool nzero = false;
+            // s_a holds this warp's rows of the pivot column of pivot k: the
+            // first selection or the previous pivot's selection left them there
+            if (!warp_wait(pcnt, target, d->err, spin_limit)) {
                 st = ST_TIMEOUT;
             } else {
-                const Cand sel = warp_partials_min(d->part_sel + ((lk + 1) & 1) * G, G);
+                // every CTA has finished pivot k-1 and published its records
+                const unsigned long long prr_b = __ldcg(&pval[rowner].y);
+                unsigned long long prq_b;
+                const Cand sel = warp_price_min(psel, pval, G, &prq_b);
                 if (sel.idx < 0) st = ST_OPTIMAL;
                 else if (iters + 1 >= iter_limit) st = ST_ITER_LIMIT;
                 else nq = sel.idx;
-                if (st == ST_RUNNING && nq >= N - 1) {  // never: a partial from outside the row
+                if (st == ST_RUNNING && nq >= N - 1) {  // never: a record from outside the row
                     if (lane == 0) atomicExch(d->err, 1);
                     st = ST_TIMEOUT;
                 }
-            }
-            if (st == ST_RUNNING) {
-                const T prq = lds(A + (long long)p * P + nq) / piv;
-                const T prr = lds(A + (long long)p * P + (N - 1)) / piv;
-                unsigned long long lmin = ~0ull;
-                for (int i = r0 + lane; i < r1; i += 32) {
-                    const T ci = lds(col + i);
-                    const T a0 = lds(A + (long long)i * P + nq);
-                    const T h0 = lds(A + (long long)i * P + (N - 1));
-                    const T a = (i == p) ? prq : tfma(-ci, prq, a0);
-                    const T rhs = (i == p) ? prr : tfma(-ci, prr, h0);
-                    ncol[i] = a;
-                    unsigned long long rk = ~0ull;
-                    if (i < m && okey(a) > lim_p) rk = screen_key(pos_part(rhs), a);
-                    s_rk[i - r0] = rk;
-                    s_num[i - r0] = pos_part(rhs);
-                    s_a[i - r0] = a;
-                    lmin = rk < lmin ? rk : lmin;
-                }
-                __syncwarp();
-                const unsigned long long rstar = warp_min_u(lmin);
-                Cand rc = cand_empty();
-                if (rstar != ~0ull) {
-                    const unsigned long long thr = screen_thr(rstar, (T)0);
-                    for (int i = r0 + lane; i < r1; i += 32)
-                        if (s_rk[i - r0] <= thr) {
-                            const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
-                            cand_take(rc, okey(s_num[i - r0] / s_a[i - r0]), key, i);
+                if (st == ST_RUNNING) {
+                    // rows of column q' and of the rhs of tableau k+1, and Step 3
+                    const T prq = tfrom<T>(prq_b), prr = tfrom<T>(prr_b);
+                    unsigned long long lmin = ~0ull;
+                    for (int i = r0 + lane; i < r1; i += 32) {
+                        const T a0 = lds(A + (long long)i * P + nq);
+                        const T h0 = lds(A + (long long)i * P + (N - 1));
+                        const T ci = s_a[i - r0];
+                        const T a = (i == p) ? prq : tfma(-ci, prq, a0);
+                        const T num = pos_part((i == p) ? prr : tfma(-ci, prr, h0));
+                        ncol[i] = a;
+                        s_a[i - r0] = a;
+                        s_num[i - r0] = num;
+                        unsigned long long rk = ~0ull;
+                        if (i < m && okey(a) > lim_p) rk = screen_key(num, a);
+                        s_rk[i - r0] = rk;
+                        lmin = rk < lmin ? rk : lmin;
+                    }
+                    __syncwarp();
+                    // this CTA's exact winner: the one row within the screening
+                    // threshold, else the exact minimum of those within it
+                    const unsigned long long rloc = warp_min_u(lmin);
+                    int w = -1;
+                    if (rloc != ~0ull) {
+                        const unsigned long long thr = screen_thr(rloc, (T)0);
+                        int cnt = 0;
+                        for (int b0 = r0; b0 < r1; b0 += 32) {
+                            const int i = b0 + lane;
+                            const unsigned bal =
+                                __ballot_sync(0xffffffffu, i < r1 && s_rk[i - r0] <= thr);
+                            if (bal && w < 0) w = b0 + __ffs(bal) - 1;
+                            cnt += __popc(bal);
                         }
+                        if (cnt > 1) {
+                            Cand e = cand_empty();
+                            for (int i = r0 + lane; i < r1; i += 32)
+                                if (s_rk[i - r0] <= thr) {
+                                    const T nm = s_num[i - r0];
+                                    const unsigned long long vk =
+                                        tbits(nm) == 0ull ? zero_k : okey(nm / s_a[i - r0]);
+                                    const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
+                                    cand_take(e, vk, key, i);
+                                }
+                            w = warp_min(e).idx;
+                        }
+                    }
+                    if (lane == 0) {
+                        Cand rc = cand_empty();
+                        ulonglong2 nv = make_ulonglong2(0ull, 0ull);
+                        if (w >= 0) {
+                            rc.vk = s_rk[w - r0];
+                            rc.key = nbland ? (w == p ? q : __ldcg(basis + w)) : w;
+                            rc.idx = w;
+                            nv = make_ulonglong2(tbits(s_num[w - r0]), tbits(s_a[w - r0]));
+                        }
+                        prat[g] = rc;
+                        rval[g] = nv;
+                    }
                 }
-                rc = warp_min(rc);
-                if (lane == 0) {
-                    d->part_ratio[g] = rc;
-                    __threadfence();
-                    red_add_release(rcnt, 1u);
-                }
-                if (!warp_wait(rcnt, (unsigned)G * (unsigned)(lk + 1), d->err, spin_limit)) {
+            }
+            // this warp's reads of the protected vectors are done: arrive
+            // (also when no ratio test ran: the update threads wait for it)
+            __syncwarp();
+            if (lane == 0 && st != ST_TIMEOUT) red_add_release(rcnt, 1u);
+            if (st == ST_RUNNING) {
+                if (!warp_wait(rcnt, target, d->err, spin_limit)) {
                     st = ST_TIMEOUT;
                 } else {
-                    const Cand r = warp_partials_min(d->part_ratio, G);
-                    if (r.idx < 0) {
+                    np = warp_ratio_min<T>(prat, rval, G, zero_k, &nzero);
+                    if (np < 0) {
                         st = ST_UNBOUNDED;
-                    } else if (r.idx >= m) {  // never: a partial from outside the column
+                    } else if (np >= m) {  // never: a record from outside the column
                         if (lane == 0) atomicExch(d->err, 1);
                         st = ST_TIMEOUT;
-                    } else {
-                        np = r.idx;
-                        nrmin = r.vk;
                     }
                 }
             }
@@ -712,22 +923,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 s_status = st;
                 s_p = np;
                 s_q = nq;
-                s_rmin = nrmin;
+                s_rzero = nzero ? 1 : 0;
             }
         }
+        // the CTA's update of pivot k and its selection of pivot k+1 are done;
+        // the records and counters order everything else between CTAs
         __syncthreads();
         ++iters;
         ++lk;
-        cur ^= 1;
         status = s_status;
+        if (!s_uok) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
             p = s_p;
             q = s_q;
-            deg = (s_rmin == zero_k) ? deg + 1 : 0;
+            deg = s_rzero ? deg + 1 : 0;
         }
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
+        if (db) {
+            cur ^= 1;
+            // keeps the CTAs in step: their row streams then share DRAM pages
+            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
+                status = ST_TIMEOUT;
+                break;
+            }
         }
     }
 
@@ -736,10 +953,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         d->iters = iters;
         d->iter_limit = iter_limit;
         d->deg = deg;
-        // hand over the buffer holding the last tableau as the current one
-        d->T = bufs[cur];
-        d->T2 = bufs[cur ^ 1];
-        d->cur = 0;
+        if (db) {  // hand over the buffer holding the last tableau as the current one
+            d->T = bufs[cur];
+            d->T2 = bufs[cur ^ 1];
+        }
     }
 }
 
@@ -983,6 +1200,12 @@ __global__ void __launch_bounds__(kBatchThreads)
     }
 }
 
+// Many LPs in one persistent launch.  items[] lists (lp, rank) pairs, the
+// ranks of one LP consecutive, largest LPs first; CTAs pop items in order
+// from *queue, and the d->group CTAs that pop the ranks of one LP solve it
+// together.  A group waits only on CTAs that hold earlier items, whose groups
+// are complete, so every group forms (the launch has at least max(group)
+// co-resident CTAs); all waits are bounded anyway.
 template <typename T, bool SMEM>
 __global__ void __launch_bounds__(kBatchThreads)
     batch_kernel(LpDesc *__restrict__ descs, const int2 *__restrict__ items, int nitems,
@@ -1098,7 +1321,7 @@ __global__ void build_kernel(const double *__restrict__ A, const double *__restr
 template <typename T>
 __global__ void extract_kernel1(const LpDesc *__restrict__ d, const T *Tab, int m, int n,
                                 long long P, int sense, double *x, double *y, double *obj) {
-    if (d) Tab = reinterpret_cast<const T *>(d->T);  // the pivot kernel's current buffer
+    if (d) Tab = reinterpret_cast<const T *>(d->T);  // the buffer the pivot kernel left current
     const int N = n + m + 1;
     const T *z = Tab + (long long)m * P;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1277,8 +1500,9 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     sh.scratch_stride = 0;
     sh.dual = 0;
     // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
-    // launch), the strip one pass of the update threads
-    sh.pipe = sh.ctas <= sms && sh.smem_bytes <= kMaxDynSmem &&
+    // launch) and the record reductions, the strip one pass of the update
+    // threads
+    sh.pipe = sh.ctas <= sms && sh.ctas <= kMaxPipeCtas && sh.smem_bytes <= kMaxDynSmem &&
               (long long)sh.strip <= (long long)nu * vw;
     return sh;
 }

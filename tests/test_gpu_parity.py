@@ -92,19 +92,18 @@ def test_launch_shapes_bitwise(ctas, threads):
     assert_same(Run(Ad, bd, cd, MIN_GE, ctas=ctas, threads=threads), od)
 
 
-@pytest.mark.parametrize("pipeline", [0, 1])
+@pytest.mark.parametrize("pipeline", [0, 2, 3])
 @pytest.mark.parametrize("m,n,ctas,threads", [(1, 1, 0, 0), (9, 1, 0, 0), (33, 17, 2, 128),
                                               (257, 100, 0, 0), (300, 1000, 5, 256),
                                               (1000, 300, 0, 1024), (200, 311, 40, 64)])
 def test_primal_kernels_bitwise(m, n, ctas, threads, pipeline):
-    """The pipelined primal kernel (two tableau buffers, selection of pivot
-    k+1 overlapping the update of pivot k) and the in-place kernel give the
-    oracle's pivots and bits."""
+    """Every primal kernel gives the oracle's pivots and bits: selection then
+    update (0), pipelined in place (2), pipelined double-buffered (3)."""
     A, b, c = lpgen.dense_lp(m, n, seed=7 * m + n)
     assert_same(Run(A, b, c, ctas=ctas, threads=threads, pipeline=pipeline), _oracle(A, b, c))
 
 
-@pytest.mark.parametrize("pipeline", [0, 1])
+@pytest.mark.parametrize("pipeline", [0, 2, 3])
 @pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
 def test_pivot_by_pivot_tableau(sense, pipeline):
     """One pivot per call: the tableau equals the oracle's after every pivot."""
