@@ -33,7 +33,7 @@ FP64_DFMA_PER_CLK_SM = 2          # GB300 FP64 rate: 1.25 TFLOP/s nominal = 2 DF
 SMS, SM_MAX_MHZ = 152, 2070.0
 ALU_PEAK_TFLOPS = 2 * FP64_DFMA_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
 MAX_LE, MIN_GE = 0, 1
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pivot_kernel_fp64_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pivot_pipe_kernel_fp64_traffic.txt")
 KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pivot.cu")
 
 
@@ -63,9 +63,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# The kernel each LP of the set runs on (default options): the primal LPs on
+# the pipelined kernel (in place up to 96 MB of tableau, double-buffered
+# above), the dual form on the dual simplex kernel.
+PRIMAL_KERNEL = "pivot_pipe_kernel<double>"
+DUAL_KERNEL = "pivot_kernel<double, SMEM, DUAL> (dual simplex)"
+
+
+def kernel_of(sense):
+    return PRIMAL_KERNEL if sense == MAX_LE else DUAL_KERNEL
+
+
 def kernel_traffic():
-    """dram bytes per pivot-kernel launch from the committed ncu summary, or
-    None when the kernel source changed since that capture."""
+    """Mean DRAM bytes per pipelined-kernel launch in one bench step, from the
+    committed ncu summary, or None when the kernel source changed since that
+    capture."""
     import hashlib
     try:
         rec = {}
@@ -372,14 +384,21 @@ def main():
     if dist:
         dist.barrier()
     step_ms, pivots, kernel_ms, alg_bytes = [], 0, 0.0, 0.0
+    per_kernel = {}  # name -> [launches, ms, algorithmic bytes, pivots]
     with Clocks(local) as clk:
         for _ in range(args.steps):
             ms, stats = device_step()
             step_ms.append(ms)
-            for (it, kms, _), (_, A, _b, _c, _s) in zip(stats, lps):
+            for (it, kms, _), (_, A, _b, _c, sense) in zip(stats, lps):
                 pivots += it
                 kernel_ms += kms
-                alg_bytes += it * tableau_bytes(A.shape[0], A.shape[1])
+                by = it * tableau_bytes(A.shape[0], A.shape[1])
+                alg_bytes += by
+                rec = per_kernel.setdefault(kernel_of(sense), [0, 0.0, 0.0, 0])
+                rec[0] += 1
+                rec[1] += kms
+                rec[2] += by
+                rec[3] += it
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -425,18 +444,33 @@ def main():
 
     hbm_peak, peak_kind = peaks()
     gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    flops = alg_bytes / 16 * 2  # one FMA (2 flops) per 16 bytes of FP64 read + write
-    tflops = flops / (kernel_ms * 1e-3) / 1e12
-    traffic = kernel_traffic()
-    hbm = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-           "frac": round(gbs / hbm_peak, 4), "peak_kind": peak_kind}
-    alu = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(ALU_PEAK_TFLOPS, 4),
-           "unit": "TFLOP/s", "frac": round(tflops / ALU_PEAK_TFLOPS, 4),
-           "peak_kind": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
-    roof = dict(max((hbm, alu), key=lambda r: r["frac"]))
-    roof["traffic"] = traffic
-    roof["kernel"] = "pivot_kernel<double> (persistent, one launch per solve)"
-    roof["secondary"] = alu if roof["bound"] == "hbm" else hbm
+
+    def roofline_of(name):
+        """HBM and FP64-ALU rooflines of one kernel: algorithmic bytes (or
+        flops) per launch over its mean CUDA-event launch duration."""
+        launches, ms, by, piv = per_kernel[name]
+        sec = ms * 1e-3
+        flops = by / 16 * 2  # one FMA (2 flops) per 16 bytes of FP64 read + write
+        hbm = {"bound": "hbm", "achieved": round(by / sec / 1e9, 1), "peak": hbm_peak,
+               "unit": "GB/s", "frac": round(by / sec / 1e9 / hbm_peak, 4),
+               "peak_kind": peak_kind}
+        alu = {"bound": "alu", "achieved": round(flops / sec / 1e12, 4),
+               "peak": round(ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+               "frac": round(flops / sec / 1e12 / ALU_PEAK_TFLOPS, 4),
+               "peak_kind": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+        r = dict(max((hbm, alu), key=lambda x: x["frac"]))
+        r["secondary"] = alu if r["bound"] == "hbm" else hbm
+        r["kernel"] = name
+        r["launches_per_step"] = launches // args.steps
+        r["mean_launch_ms"] = round(ms / launches, 4)
+        r["algorithmic_bytes_per_launch"] = round(by / launches)
+        r["share_of_pivot_kernel_time"] = round(ms / kernel_ms, 4)
+        return r
+
+    dominant = max(per_kernel, key=lambda k: per_kernel[k][1])
+    roof = roofline_of(dominant)
+    roof["traffic"] = kernel_traffic() if dominant == PRIMAL_KERNEL else None
+    roof["others"] = [roofline_of(k) for k in per_kernel if k != dominant]
     line = {
         "metric": "pivots/s", "value": all_pivots / (total_ms * 1e-3), "unit": "pivots/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -454,11 +488,15 @@ def main():
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
+        # the whole workload, repeated until about 10 s of oracle time
         cores = len(os.sched_getaffinity(0))
-        p, t = cpu_oracle_run(lps, cores)
+        p, t, reps = 0, 0.0, 0
+        while t < 10.0 and reps < 1000:
+            dp, dt = cpu_oracle_run(lps, cores)
+            p, t, reps = p + dp, t + dt, reps + 1
         line["cpu_baseline"] = {"value": p / t, "unit": "pivots/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": "the whole workload (4 LPs) once, %.1f s" % t}
+                                "sample": "the whole workload (4 LPs) %d times, %.1f s" % (reps, t)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
