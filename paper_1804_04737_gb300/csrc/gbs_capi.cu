@@ -47,13 +47,11 @@ struct lp_handle {
     size_t cap_T = 0;                           // bytes
     void *dT2 = nullptr;                        // double-buffered pipelined kernel
     size_t cap_T2 = 0;
-    void *dcol = nullptr;                       // pipelined kernel: 2 pivot columns
-    size_t cap_col = 0;
     int *dbasis = nullptr;
     size_t cap_basis = 0;
     void *dscratch = nullptr;
     size_t cap_scratch = 0;                     // bytes
-    Cand *dpart = nullptr;                      // 8 * max_ctas (records)
+    Cand *dpart = nullptr;                      // 4 * max_ctas (records, values)
     int max_ctas = 0;
     unsigned *dbar = nullptr;                   // kBarWords: barrier, counters, err
     int *dtrace = nullptr;
@@ -233,7 +231,7 @@ void lp_destroy(lp_handle *h) {
                      h->rb.bar};
     for (void *p : rbufs)
         if (p) cudaFree(p);
-    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dcol, h->dbasis, h->dscratch, h->dpart, h->dbar,
+    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dbasis, h->dscratch, h->dpart, h->dbar,
                     h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -287,9 +285,11 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     }
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
-            const PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads,
-                                                    h->opt.ctas);
-            if (ps.pipe) return ps;
+            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas);
+            if (ps.pipe) {
+                if (pmode == 3) ps.pipe = 2;  // double-buffered
+                return ps;
+            }
         }
         return choose_shape(h->prec, rule, M, N, P, h->sms, h->opt.threads, h->opt.ctas);
     };
@@ -303,7 +303,6 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
     CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
     CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
-    if (pipe) CUDA_TRY(h, grow_bytes(&h->dcol, &h->cap_col, 2 * (size_t)M * esz));
     CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
     {
         size_t need = sh.use_smem ? 0 : (size_t)sh.ctas * (size_t)sh.scratch_stride;
@@ -315,7 +314,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
         h->max_ctas = 0;
-        CUDA_TRY(h, cudaMalloc(&h->dpart, 8 * (size_t)ctas_max * sizeof(Cand)));
+        CUDA_TRY(h, cudaMalloc(&h->dpart, 4 * (size_t)ctas_max * sizeof(Cand)));
         h->max_ctas = ctas_max;
     }
     if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
@@ -391,10 +390,8 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.scratch = h->dscratch;
     d.scratch_stride = sh.scratch_stride;
     d.part_sel = h->dpart;
-    d.part_ratio = h->dpart + 2 * (size_t)h->max_ctas;
-    d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 4 * (size_t)h->max_ctas);
+    d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 2 * (size_t)h->max_ctas);
     d.T2 = pipe && pmode == 3 ? h->dT2 : nullptr;
-    d.colbuf = pipe ? h->dcol : nullptr;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;

@@ -47,16 +47,35 @@ __device__ __forceinline__ void cand_take(Cand &best, unsigned long long vk, int
     }
 }
 
+// Warp-wide minima on the redux unit: one instruction per 32-bit minimum.  A
+// five-step shuffle butterfly took several microseconds on GB300 while the
+// SM's load/store path was busy with the tableau stream.
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32);
+    const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? (unsigned)v : 0xffffffffu);
+    return ((unsigned long long)mhi << 32) | mlo;
+}
+
+// Lowest lane holding the lexicographic minimum of (vk, key), keys >= 0;
+// the minimum itself in *mvk, *mkey.
+__device__ __forceinline__ int warp_argmin(unsigned long long vk, int key, unsigned long long *mvk,
+                                           int *mkey) {
+    const unsigned long long m = warp_min_u64(vk);
+    const bool at = vk == m;
+    const unsigned k = __reduce_min_sync(0xffffffffu, at ? (unsigned)key : 0xffffffffu);
+    const unsigned bal = __ballot_sync(0xffffffffu, at && (unsigned)key == k);
+    *mvk = m;
+    *mkey = (int)k;
+    return __ffs(bal) - 1;
+}
+
+// Warp-wide candidate minimum; every lane gets it.
 __device__ __forceinline__ Cand warp_min(Cand c) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Cand d;
-        d.vk = __shfl_xor_sync(0xffffffffu, c.vk, o);
-        d.key = __shfl_xor_sync(0xffffffffu, c.key, o);
-        d.idx = __shfl_xor_sync(0xffffffffu, c.idx, o);
-        if (cand_less(d, c)) c = d;
-    }
-    return c;
+    Cand r;
+    const int src = warp_argmin(c.vk, c.key, &r.vk, &r.key);
+    r.idx = __shfl_sync(0xffffffffu, c.idx, src);
+    return r;
 }
 
 // Block-wide candidate minimum; every thread gets the result.  `buf` (32
@@ -77,11 +96,7 @@ __device__ __forceinline__ unsigned long long block_min_u(unsigned long long v,
                                                           unsigned long long *buf) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w < v ? w : v;
-    }
+    v = warp_min_u64(v);
     if (lane == 0) buf[wid] = v;
     __syncthreads();
     unsigned long long r = buf[0];

@@ -53,12 +53,10 @@ struct LpDesc {
     // batched launches: CTAs per LP and their column strip width
     int group, strip;
     // pipelined primal kernel: the second tableau buffer (double-buffered
-    // mode; nullptr in place), the pivot columns of this and the next pivot
-    // (2 x M elements, by parity), the ratio records (2 x G, by parity) and
-    // the values that come with the pricing and ratio records (4 x G pairs)
+    // mode; nullptr in place) and the values that come with the pricing
+    // records (2 x G pairs, by parity: the new pivot-row entries at the
+    // record's column and at the rhs)
     void *T2;
-    void *colbuf;
-    Cand *part_ratio;
     unsigned long long *part_vals;
 };
 
@@ -69,15 +67,15 @@ struct PivotShape {
     int strip = 0;                 // columns per strip (multiple of 32 bytes of elements)
     int use_smem = 0;              // selection scratch in shared memory (else global)
     int dual = 0;                  // dual simplex kernel (else primal)
-    int pipe = 0;                  // pipelined primal kernel
+    int pipe = 0;                  // pipelined primal kernel: 1 in place, 2 double-buffered
     size_t smem_bytes = 0;         // dynamic shared memory per CTA
     long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };
 
 // Words of a pivot launch's synchronisation block (zeroed before each launch):
 // [0] grid-barrier count, [32] its generation, [64] readers counter (in-place
-// kernel) or pricing-partials counter (pipelined kernel), [96] error flag,
-// [128] ratio-partials counter (pipelined kernel); 128-byte apart.
+// kernel) or pricing-records counter (pipelined kernel), [96] error flag,
+// [128] selections-done counter (pipelined kernel); 128-byte apart.
 constexpr int kBarWords = 256;
 
 struct InputStats {
@@ -107,7 +105,8 @@ cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems,
 int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, int sms);
 // Pipelined primal kernel (selection of pivot k+1 overlapped with pivot k's update).
 // The returned shape has pipe == 0 when the kernel cannot take the LP (a grid
-// larger than one CTA per SM, or too much shared memory).
+// larger than one CTA per SM); its scratch is in shared memory when it fits,
+// else a global slice of scratch_stride bytes per CTA.
 PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas);
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s);

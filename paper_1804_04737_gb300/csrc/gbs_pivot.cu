@@ -386,38 +386,41 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined primal simplex for one LP (FP64 or FP32 tableau), in place.
+// Pipelined primal simplex for one LP (FP64 or FP32 tableau).
 //
-// In every CTA the last warp selects pivot k+1 while the other warps stream
-// pivot k's update of the CTA's column strip:
+// In every CTA the last kSelWarps warps select pivot k+1 while the others
+// stream pivot k's update of the CTA's column strip:
 //   update warps     divide the strip of the pivot row (Step 4), update the
 //                    strip of the objective row and publish the CTA's pricing
 //                    record (its best column, with the new pivot-row values at
 //                    that column and at the rhs), then update the rest of the
-//                    strip (Step 5) except two protected vectors: the one
-//                    holding the CTA's pricing winner and the one holding the
-//                    rhs.  Once every selection warp has finished reading
-//                    (ratio counter) they update the protected vectors.
-//   selection warp   reduces the pricing records to the entering column q'
-//                    (Step 2), forms its block of rows of column q' and of the
-//                    rhs of tableau k+1 with the very fma the update uses (so
-//                    the values are bit for bit those the update writes), runs
-//                    the screened ratio test on them (Step 3), publishes its
-//                    ratio record and its block of the next pivot column, and
-//                    reduces the ratio records to the pivot row p'.
-// The entering column is the pricing winner of the CTA that owns it, so the
-// columns the selection reads (q' and the rhs, of tableau k) are protected
-// vectors, unchanged while they are read.  There is no grid barrier per
-// pivot: a CTA publishes its pricing record only after finishing its previous
-// pivot, so the pricing counter also tells the selection warps that every
-// protected vector they read is up to date, and a CTA starts pivot k+1 only
-// after the ratio counter of pivot k is complete, so no CTA runs more than one
-// pivot ahead of another; records and pivot columns are double-buffered by
-// pivot parity.  The selection warp issues no floating-point division in the
-// common case (it competes for the FP64 pipe with the update): the pivot-row
-// values come with the pricing records, and the exact Step 3 quotient is
-// formed only when two screened ratios lie within the screening threshold.
-// The first pivot's selection runs alone, with grid barriers.
+//                    strip (Step 5), reading the pivot column from this CTA's
+//                    scratch;
+//   selection warps  reduce the pricing records to the entering column q'
+//                    (Step 2), form the whole column q' and rhs of tableau k+1
+//                    from tableau k with the very fma the update uses (so the
+//                    values are bit for bit those the update writes) into the
+//                    CTA's scratch, and run the screened ratio test on them
+//                    (Step 3).  Every CTA does this redundantly, so the pivot
+//                    row needs no exchange between CTAs.
+// In place (tableaus that fit L2), the vectors the selection reads (each
+// CTA's own pricing winner, which is where the entering column always is, and
+// the rhs) are left out of the bulk update and updated once a counter shows
+// every CTA's selection done reading them.  There is no grid barrier: a CTA
+// publishes its pricing record only after finishing its previous pivot, so
+// the pricing counter also proves every vector the selection reads is current,
+// and no CTA runs more than one pivot ahead of another (records are
+// double-buffered by pivot parity).  Double-buffered (larger tableaus), pivot
+// k reads one buffer and writes the other, with a grid barrier per pivot to
+// keep the CTAs' row streams in step.  The selection divides only on
+// near-ties: it shares the FP64 pipe with the update warps.  The first pivot's
+// selection runs alone, with a grid barrier.
+
+// Selection warps per CTA: four in place (the selection is the critical path
+// of an L2-resident pivot), two double-buffered (the update is, and wants
+// the warps).  kSelThreadsMax sizes the launch shape for either.
+constexpr int kSelThreadsMax = 128;
+constexpr int kSelRows = 4;
 
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
@@ -428,34 +431,6 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 
 static_assert(sizeof(Cand) == 16 && offsetof(Cand, key) == 8 && offsetof(Cand, idx) == 12,
               "Cand is read as one 16-byte vector");
-
-__device__ __forceinline__ unsigned long long warp_min_u(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w < v ? w : v;
-    }
-    return v;
-}
-
-// Lane 0 waits (bounded) until *ctr reaches target; the warp learns the outcome.
-__device__ __forceinline__ bool warp_wait(unsigned *ctr, unsigned target, int *err,
-                                          long long spin_limit) {
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) {
-        const long long t0 = clock64();
-        while ((int)(ld_acquire(ctr) - target) < 0) {
-            if (clock64() - t0 > spin_limit || *(volatile int *)err) {
-                atomicExch(err, 1);
-                ok = 0;
-                break;
-            }
-        }
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    return ok != 0;
-}
 
 __device__ __forceinline__ unsigned long long tbits(double x) {
     return (unsigned long long)__double_as_longlong(x);
@@ -474,11 +449,6 @@ __device__ __forceinline__ float tfrom<float>(unsigned long long u) {
     return __uint_as_float((unsigned)u);
 }
 
-// Records of the pipelined kernel, one per CTA and pivot parity: a Cand and
-// two values.  A lane loads up to kRecPerLane of them in one round.
-constexpr int kRecPerLane = 5;  // grids of at most 160 CTAs
-constexpr int kMaxPipeCtas = 32 * kRecPerLane;
-
 __device__ __forceinline__ Cand unpack_cand(const ulonglong2 &v) {
     Cand e;
     e.vk = v.x;
@@ -487,120 +457,110 @@ __device__ __forceinline__ Cand unpack_cand(const ulonglong2 &v) {
     return e;
 }
 
-// Entering column of pivot k+1 (every lane gets it): the minimum on (vk, key)
-// of the G pricing records, with the pivot-row value of that column that its
-// CTA published (vals[k].x).
-__device__ __forceinline__ Cand warp_price_min(const Cand *part, const ulonglong2 *vals, int G,
-                                               unsigned long long *prq) {
-    const int lane = threadIdx.x & 31;
-    ulonglong2 cv[kRecPerLane];
-    unsigned long long pv[kRecPerLane];
-#pragma unroll
-    for (int u = 0; u < kRecPerLane; ++u) {
-        const int k = lane + 32 * u;
-        cv[u] = k < G ? __ldcg(reinterpret_cast<const ulonglong2 *>(part) + k)
-                      : make_ulonglong2(~0ull, 0xffffffff7fffffffull);
-        pv[u] = k < G ? __ldcg(&vals[k].x) : 0ull;
-    }
-    Cand c = cand_empty();
-    unsigned long long bq = 0ull;
-#pragma unroll
-    for (int u = 0; u < kRecPerLane; ++u) {
-        const Cand e = unpack_cand(cv[u]);
-        if (cand_less(e, c)) {
-            c = e;
-            bq = pv[u];
+// Bounded wait of one thread until *ctr reaches target; false when it ran out
+// or another CTA reported a timeout.
+__device__ __forceinline__ bool wait_ctr(unsigned *ctr, unsigned target, int *err,
+                                         long long spin_limit) {
+    const long long t0 = clock64();
+    while ((int)(ld_acquire(ctr) - target) < 0) {
+        if (clock64() - t0 > spin_limit || *(volatile int *)err) {
+            atomicExch(err, 1);
+            return false;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Cand e;
-        e.vk = __shfl_xor_sync(0xffffffffu, c.vk, o);
-        e.key = __shfl_xor_sync(0xffffffffu, c.key, o);
-        e.idx = __shfl_xor_sync(0xffffffffu, c.idx, o);
-        const unsigned long long eq = __shfl_xor_sync(0xffffffffu, bq, o);
-        if (cand_less(e, c)) {
-            c = e;
-            bq = eq;
-        }
-    }
-    *prq = bq;
-    return c;
+    return true;
 }
 
-// Pivot row of pivot k+1 from the G ratio records (every lane gets it).  A
-// record holds a CTA's exact winner: its screening key, tie key and row, and
-// (vals) the numerator and denominator of its Step 3 quotient.  The record
-// holding the exact minimum has a screening key within the threshold of the
-// smallest one, r*; when it is the only such record it is the answer,
-// otherwise the records within the threshold are compared by their exact
-// quotients, then by key.  *rzero: the selected quotient is +0.
-template <typename T>
-__device__ __forceinline__ int warp_ratio_min(const Cand *part, const ulonglong2 *vals, int G,
-                                              unsigned long long zero_k, bool *rzero) {
-    const int lane = threadIdx.x & 31;
-    ulonglong2 cv[kRecPerLane];
-#pragma unroll
-    for (int u = 0; u < kRecPerLane; ++u) {
-        const int k = lane + 32 * u;
-        cv[u] = k < G ? __ldcg(reinterpret_cast<const ulonglong2 *>(part) + k)
-                      : make_ulonglong2(~0ull, 0xffffffff7fffffffull);
+// Selection-group minimum of a candidate and its 64-bit payload: the warps'
+// minima go through sc[]/sq[] (kSelWarps entries) and a named barrier; every
+// selection thread gets the result.
+template <int SW>
+__device__ __forceinline__ Cand sel_min(Cand c, unsigned long long q, Cand *sc,
+                                        unsigned long long *sq, unsigned long long *pq) {
+    const int lane = threadIdx.x & 31, sw = (threadIdx.x >> 5) % SW;
+    Cand r;
+    const int src = warp_argmin(c.vk, c.key, &r.vk, &r.key);
+    r.idx = __shfl_sync(0xffffffffu, c.idx, src);
+    const unsigned long long rq = __shfl_sync(0xffffffffu, q, src);
+    if (lane == 0) {
+        sc[sw] = r;
+        sq[sw] = rq;
     }
-    unsigned long long r = ~0ull;
+    named_sync(2, 32 * SW);
+    Cand b = sc[0];
+    unsigned long long bq = sq[0];
 #pragma unroll
-    for (int u = 0; u < kRecPerLane; ++u) r = cv[u].x < r ? cv[u].x : r;
-    r = warp_min_u(r);
-    *rzero = false;
-    if (r == ~0ull) return -1;
-    const unsigned long long thr = screen_thr(r, (T)0);
-    int cnt = 0;
-#pragma unroll
-    for (int u = 0; u < kRecPerLane; ++u) cnt += __popc(__ballot_sync(0xffffffffu, cv[u].x <= thr));
-    if (cnt == 1) {
-        int idx = -1;
-        unsigned long long rk = 0ull;
-#pragma unroll
-        for (int u = 0; u < kRecPerLane; ++u) {
-            const unsigned bal = __ballot_sync(0xffffffffu, cv[u].x <= thr);
-            if (bal) {
-                const int src = __ffs(bal) - 1;
-                idx = __shfl_sync(0xffffffffu, (int)(unsigned)(cv[u].y >> 32), src);
-                rk = __shfl_sync(0xffffffffu, cv[u].x, src);
-            }
+    for (int w = 1; w < SW; ++w)
+        if (cand_less(sc[w], b)) {
+            b = sc[w];
+            bq = sq[w];
         }
-        *rzero = rk == zero_k;  // screening keys are +0 exactly for a +0 quotient
-        return idx;
-    }
-    Cand c = cand_empty();
-#pragma unroll
-    for (int u = 0; u < kRecPerLane; ++u) {
-        if (cv[u].x <= thr) {
-            const ulonglong2 nv = __ldcg(vals + lane + 32 * u);
-            const unsigned long long vk =
-                nv.x == 0ull ? zero_k : okey(tfrom<T>(nv.x) / tfrom<T>(nv.y));
-            cand_take(c, vk, (int)(unsigned)(cv[u].y & 0xffffffffull), (int)(unsigned)(cv[u].y >> 32));
-        }
-    }
-    c = warp_min(c);
-    *rzero = c.vk == zero_k;
-    return c.idx;
+    named_sync(2, 32 * SW);  // sc/sq free again
+    if (pq) *pq = bq;
+    return b;
 }
 
-template <typename T>
+// Selection-group minimum and sum of two 32-bit values (min of a, sum of b).
+template <int SW>
+__device__ __forceinline__ void sel_min_sum(unsigned a, unsigned b, unsigned *sa, unsigned *sb,
+                                            unsigned *ra, unsigned *rb) {
+    const int lane = threadIdx.x & 31, sw = (threadIdx.x >> 5) % SW;
+    a = __reduce_min_sync(0xffffffffu, a);
+    b = __reduce_add_sync(0xffffffffu, b);
+    if (lane == 0) {
+        sa[sw] = a;
+        sb[sw] = b;
+    }
+    named_sync(2, 32 * SW);
+    unsigned ma = sa[0], mb = sb[0];
+#pragma unroll
+    for (int w = 1; w < SW; ++w) {
+        ma = sa[w] < ma ? sa[w] : ma;
+        mb += sb[w];
+    }
+    named_sync(2, 32 * SW);
+    *ra = ma;
+    *rb = mb;
+}
+
+// Selection-group minimum of a 64-bit value.
+template <int SW>
+__device__ __forceinline__ unsigned long long sel_min_u64(unsigned long long v,
+                                                          unsigned long long *sq) {
+    const int lane = threadIdx.x & 31, sw = (threadIdx.x >> 5) % SW;
+    v = warp_min_u64(v);
+    if (lane == 0) sq[sw] = v;
+    named_sync(2, 32 * SW);
+    unsigned long long r = sq[0];
+#pragma unroll
+    for (int w = 1; w < SW; ++w) r = sq[w] < r ? sq[w] : r;
+    named_sync(2, 32 * SW);
+    return r;
+}
+
+// SW selection warps; SW == 2 runs the double-buffered mode, SW == 4 in place.
+template <typename T, int SW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_pipe_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
+    constexpr int kSelWarps = SW, kSelThreads = 32 * SW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Cand rbuf[3][32];
+    __shared__ Cand rbuf[2][32];
     __shared__ unsigned long long ubuf[32];
     __shared__ Cand wpart[32];
-    __shared__ int s_flag, s_p, s_q, s_status, s_jv, s_uok, s_rzero;
+    __shared__ Cand selc[SW];
+    __shared__ unsigned long long selq[SW];
+    __shared__ unsigned sela[SW], selb[SW];
+    __shared__ int s_flag, s_p, s_q, s_status, s_jv, s_uok, s_rzero, s_sok;
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
-    const int NU = B - 32;  // update threads; the last warp selects
+    // update threads; the last SW warps select (the launch reserves
+    // kSelThreadsMax threads for them, the rest of those update)
+    const int NU = B - kSelThreads;
     const int lane = tid & 31;
     const bool selw = tid >= NU;
+    const int stid = tid - NU;
     // in place, or double-buffered (T2 set): pivot k reads bufs[cur] and
     // writes bufs[cur ^ 1], with a grid barrier after each pivot
     const bool db = d->T2 != nullptr;
@@ -609,7 +569,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const T *Tab = bufs[0];
     const long long P = d->P;
     const int m = d->m, M = d->M, N = d->N;
-    T *colb[2] = {reinterpret_cast<T *>(d->colbuf), reinterpret_cast<T *>(d->colbuf) + M};
     int *__restrict__ basis = d->basis;
     const int bland_after = d->bland_after;
     const unsigned long long lim_p = okey((T)d->eps_p);
@@ -630,18 +589,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const int lr = tid / vpr, lv = tid - lr * vpr;
     const bool active = !selw && lr < rpp;
     const int col0 = c0 + lv * VW;
-    // the vector of this strip holding the rhs column, or -1; protected from
-    // the in-place update until the selection has read it
+    // the vector of this strip holding the rhs column, or -1; in place it is
+    // protected from the bulk update until every selection has read it
     const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
     const int rvp = db ? -1 : rv;
-    // the selection warp's block of rows, and its scratch
-    const int RPC = (M + G - 1) / G;
-    const int r0 = min(M, g * RPC), r1 = min(M, r0 + RPC);
+    // scratch: the strip of the pivot row in shared memory; the pivot columns
+    // of this and the next pivot, the ratio numerators and the screening keys
+    // in shared memory, or in this CTA's slice of global scratch
     T *sprow = reinterpret_cast<T *>(smem_raw);
-    unsigned char *sel_raw = smem_raw + (((size_t)W * sizeof(T) + 15) & ~(size_t)15);
-    unsigned long long *s_rk = reinterpret_cast<unsigned long long *>(sel_raw);
-    T *s_num = reinterpret_cast<T *>(s_rk + RPC);
-    T *s_a = s_num + RPC;
+    unsigned char *sc = d->scratch_stride > 0
+                            ? reinterpret_cast<unsigned char *>(d->scratch) +
+                                  (size_t)g * (size_t)d->scratch_stride
+                            : smem_raw + (((size_t)W * sizeof(T) + 15) & ~(size_t)15);
+    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
+    T *scol[2] = {reinterpret_cast<T *>(sc), reinterpret_cast<T *>(sc + cbytes)};
+    T *snum = reinterpret_cast<T *>(sc + 2 * cbytes);
+    unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 3 * cbytes);
 
     // ---- selection of the first pivot from the current tableau (all threads) ----
     int p = -1, q = -1;
@@ -660,42 +623,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             const Cand sel = load_partials_min(d->part_sel, G, rbuf[1]);
             if (sel.idx < 0) status = ST_OPTIMAL;
             else if (iters >= iter_limit) status = ST_ITER_LIMIT;
-            else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: see the loop's checks
+            else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: a partial from outside the row
             else q = sel.idx;
         }
         if (status == ST_RUNNING) {
+            // the whole pivot column and the ratio test, in every CTA
             unsigned long long lmin = ~0ull;
-            for (int i = r0 + tid; i < r1; i += B) {
+            for (int i = tid; i < M; i += B) {
                 const T a = lds(Tab + (long long)i * P + q);
-                const T rhs = lds(Tab + (long long)i * P + (N - 1));
-                colb[0][i] = a;
-                unsigned long long rk = ~0ull;
-                if (i < m && okey(a) > lim_p) rk = screen_key(pos_part(rhs), a);
-                s_rk[i - r0] = rk;
-                s_num[i - r0] = pos_part(rhs);
-                s_a[i - r0] = a;
-                lmin = rk < lmin ? rk : lmin;
+                scol[0][i] = a;
+                if (i < m) {
+                    const T num = pos_part(lds(Tab + (long long)i * P + (N - 1)));
+                    const unsigned long long rk = okey(a) > lim_p ? screen_key(num, a) : ~0ull;
+                    snum[i] = num;
+                    srk[i] = rk;
+                    lmin = rk < lmin ? rk : lmin;
+                }
             }
             const unsigned long long rstar = block_min_u(lmin, ubuf);
-            Cand rc = cand_empty();
-            if (rstar != ~0ull) {
-                const unsigned long long thr = screen_thr(rstar, (T)0);
-                for (int i = r0 + tid; i < r1; i += B)
-                    if (s_rk[i - r0] <= thr)
-                        cand_take(rc, okey(s_num[i - r0] / s_a[i - r0]),
-                                  bland ? __ldcg(basis + i) : i, i);
-            }
-            rc = block_min_c(rc, rbuf[2]);
-            if (tid == 0) d->part_ratio[g] = rc;
-            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
-        }
-        if (status == ST_RUNNING) {
-            const Cand rc = load_partials_min(d->part_ratio, G, rbuf[0]);
-            if (rc.idx < 0) {
+            if (rstar == ~0ull) {
                 status = ST_UNBOUNDED;
-            } else if (rc.idx >= m) {
-                status = ST_TIMEOUT;
             } else {
+                const unsigned long long thr = screen_thr(rstar, (T)0);
+                Cand rc = cand_empty();
+                for (int i = tid; i < m; i += B)
+                    if (srk[i] <= thr)
+                        cand_take(rc, okey(snum[i] / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
+                rc = block_min_c(rc, rbuf[0]);
                 p = rc.idx;
                 deg = (rc.vk == zero_k) ? deg + 1 : 0;
             }
@@ -707,26 +661,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     while (status == ST_RUNNING) {
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
-        const T *col = colb[lk & 1];
-        T *ncol = colb[(lk + 1) & 1];
+        const T *col = scol[lk & 1];
+        T *ncol = scol[(lk + 1) & 1];
         const int par = (lk + 1) & 1;  // records of the selection of pivot k+1
         Cand *psel = d->part_sel + par * G;
         ulonglong2 *pval = reinterpret_cast<ulonglong2 *>(d->part_vals) + par * G;
-        Cand *prat = d->part_ratio + par * G;
-        ulonglong2 *rval = reinterpret_cast<ulonglong2 *>(d->part_vals) + (2 + par) * G;
         const unsigned target = (unsigned)G * (unsigned)(lk + 1);
-        if (g == 0 && tid == 0) {
-            if (iters < d->trace_cap) {
-                d->trace[2 * iters] = p;
-                d->trace[2 * iters + 1] = q;
-            }
-            basis[p] = q;
-            d->last_p = p;
-            d->last_q = q;
-        }
         const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
         if (!selw) {
-            const T piv = lds(col + p);
+            const T piv = col[p];
             // Step 4 on this CTA's strip of the pivot row
             for (int j = c0 + tid; j < c1; j += NU)
                 sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
@@ -737,7 +680,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             V zt;
             const bool zown = tid < vpr;
             if (zown) {
-                const T colm = lds(col + m);
+                const T colm = col[m];
                 const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
                 zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
                 vfma(zt, colm, pr);
@@ -751,17 +694,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             c = warp_min(c);
             if (lane == 0) wpart[tid >> 5] = c;
             named_sync(1, NU);
-            if (tid == 0) {
-                Cand r = wpart[0];
-                for (int w = 1; w < NU / 32; ++w)
-                    if (cand_less(wpart[w], r)) r = wpart[w];
-                psel[g] = r;
-                // with it, the new pivot-row values the selection needs from
-                // this strip: at the candidate column and at the rhs
-                pval[g] = make_ulonglong2(r.idx >= 0 ? tbits(sprow[r.idx - c0]) : 0ull,
-                                          rv >= 0 ? tbits(sprow[N - 1 - c0]) : 0ull);
-                red_add_release(pcnt, 1u);
-                s_jv = (r.idx >= 0 && !db) ? (r.idx - c0) / VW : -1;
+            if (tid < 32) {  // warp 0 reduces the warps' candidates and publishes
+                const Cand e = tid < NU / 32 ? wpart[tid] : cand_empty();
+                const Cand r = warp_min(e);
+                if (tid == 0) {
+                    psel[g] = r;
+                    // with it, the new pivot-row values the selection needs
+                    // from this strip: at the candidate column and at the rhs
+                    pval[g] = make_ulonglong2(r.idx >= 0 ? tbits(sprow[r.idx - c0]) : 0ull,
+                                              rv >= 0 ? tbits(sprow[N - 1 - c0]) : 0ull);
+                    red_add_release(pcnt, 1u);
+                    s_jv = (r.idx >= 0 && !db) ? (r.idx - c0) / VW : -1;
+                }
             }
             named_sync(1, NU);
             const int jv = s_jv;  // protected: the vector of the CTA's candidate
@@ -779,8 +723,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
                     const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
                     const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    const T a0 = lds(col + i), a1 = lds(col + i1), a2 = lds(col + i2),
-                            a3 = lds(col + i3);
+                    const T a0 = col[i], a1 = col[i1], a2 = col[i2], a3 = col[i3];
                     *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p, a0, pr);
                     *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p, a1, pr);
                     *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p, a2, pr);
@@ -789,28 +732,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 for (; i < m; i += rpp) {
                     const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
                     *reinterpret_cast<V *>(bbase + (long long)i * P) =
-                        pivot_vec<T>(t0, i, p, lds(col + i), pr);
+                        pivot_vec<T>(t0, i, p, col[i], pr);
                 }
             }
-            // every selection warp is done reading the protected vectors (in
-            // place; double-buffered, nothing this pivot writes is read)
-            if (db) {
-                if (tid == 0) s_uok = 1;
-            } else if (tid == 0) {
-                int ok = 1;
-                const long long t0 = clock64();
-                while ((int)(ld_acquire(rcnt) - target) < 0) {
-                    if (clock64() - t0 > spin_limit || *(volatile int *)d->err) {
-                        atomicExch(d->err, 1);
-                        ok = 0;
-                        break;
-                    }
-                }
-                s_uok = ok;
-            }
+            // in place: every CTA's selection is done reading the protected
+            // vectors, then update them (double-buffered: nothing to protect)
+            if (tid == 0) s_uok = db ? 1 : (int)wait_ctr(rcnt, target, d->err, spin_limit);
             named_sync(1, NU);
-            if (s_uok) {
-                // the protected vectors, every row, spread over the update threads
+            if (s_uok && !db) {
                 for (int k = 0; k < 2; ++k) {
                     const int v = k == 0 ? jv : (rvp != jv ? rvp : -1);
                     if (v < 0) continue;
@@ -818,116 +747,134 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     T *vbase = Bn + c0 + v * VW;
                     for (int i = tid; i < M; i += NU) {
                         V *p0 = reinterpret_cast<V *>(vbase + (long long)i * P);
-                        *p0 = pivot_vec<T>(ldv(p0), i, p, lds(col + i), vpr_);
+                        *p0 = pivot_vec<T>(ldv(p0), i, p, col[i], vpr_);
                     }
                 }
             }
         } else {
             // selection of pivot k+1, overlapping the update of pivot k
-            int st = ST_RUNNING, np = -1, nq = -1;
-            bool nzero = false;
-            // s_a holds this warp's rows of the pivot column of pivot k: the
-            // first selection or the previous pivot's selection left them there
-            if (!warp_wait(pcnt, target, d->err, spin_limit)) {
+            int st = ST_RUNNING, np = -1, nq = -1, rzero = 0;
+            if (stid == 0) {
+                int ok = 1;
+                if (g == 0) {
+                    // the basis and trace of pivot k, once every CTA's selection
+                    // of pivot k is done reading the basis of pivot k-1
+                    ok = (int)wait_ctr(rcnt, target - (unsigned)G, d->err, spin_limit);
+                    if (ok) {
+                        if (iters < d->trace_cap) {
+                            d->trace[2 * iters] = p;
+                            d->trace[2 * iters + 1] = q;
+                        }
+                        basis[p] = q;
+                        d->last_p = p;
+                        d->last_q = q;
+                    }
+                }
+                // every CTA has finished pivot k-1 and published its record
+                if (ok) ok = (int)wait_ctr(pcnt, target, d->err, spin_limit);
+                s_sok = ok;
+            }
+            named_sync(2, kSelThreads);
+            if (!s_sok) {
                 st = ST_TIMEOUT;
             } else {
-                // every CTA has finished pivot k-1 and published its records
+                // Step 2: the entering column from the G pricing records
+                Cand e = cand_empty();
+                unsigned long long eq = 0ull;
+                for (int k = stid; k < G; k += kSelThreads) {
+                    const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(psel) + k));
+                    const unsigned long long rq = __ldcg(&pval[k].x);
+                    if (cand_less(r, e)) {
+                        e = r;
+                        eq = rq;
+                    }
+                }
                 const unsigned long long prr_b = __ldcg(&pval[rowner].y);
                 unsigned long long prq_b;
-                const Cand sel = warp_price_min(psel, pval, G, &prq_b);
+                const Cand sel = sel_min<SW>(e, eq, selc, selq, &prq_b);
                 if (sel.idx < 0) st = ST_OPTIMAL;
                 else if (iters + 1 >= iter_limit) st = ST_ITER_LIMIT;
+                else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never: a record from outside the row
                 else nq = sel.idx;
-                if (st == ST_RUNNING && nq >= N - 1) {  // never: a record from outside the row
-                    if (lane == 0) atomicExch(d->err, 1);
-                    st = ST_TIMEOUT;
-                }
+                if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
                 if (st == ST_RUNNING) {
-                    // rows of column q' and of the rhs of tableau k+1, and Step 3
+                    // column q' and rhs of tableau k+1, every row, and Step 3
                     const T prq = tfrom<T>(prq_b), prr = tfrom<T>(prr_b);
                     unsigned long long lmin = ~0ull;
-                    for (int i = r0 + lane; i < r1; i += 32) {
-                        const T a0 = lds(A + (long long)i * P + nq);
-                        const T h0 = lds(A + (long long)i * P + (N - 1));
-                        const T ci = s_a[i - r0];
-                        const T a = (i == p) ? prq : tfma(-ci, prq, a0);
-                        const T num = pos_part((i == p) ? prr : tfma(-ci, prr, h0));
-                        ncol[i] = a;
-                        s_a[i - r0] = a;
-                        s_num[i - r0] = num;
-                        unsigned long long rk = ~0ull;
-                        if (i < m && okey(a) > lim_p) rk = screen_key(num, a);
-                        s_rk[i - r0] = rk;
-                        lmin = rk < lmin ? rk : lmin;
-                    }
-                    __syncwarp();
-                    // this CTA's exact winner: the one row within the screening
-                    // threshold, else the exact minimum of those within it
-                    const unsigned long long rloc = warp_min_u(lmin);
-                    int w = -1;
-                    if (rloc != ~0ull) {
-                        const unsigned long long thr = screen_thr(rloc, (T)0);
-                        int cnt = 0;
-                        for (int b0 = r0; b0 < r1; b0 += 32) {
-                            const int i = b0 + lane;
-                            const unsigned bal =
-                                __ballot_sync(0xffffffffu, i < r1 && s_rk[i - r0] <= thr);
-                            if (bal && w < 0) w = b0 + __ffs(bal) - 1;
-                            cnt += __popc(bal);
+                    // kSelRows rows per thread in flight (the loads are L2 round trips)
+                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                        T av[kSelRows], hv[kSelRows];
+#pragma unroll
+                        for (int u = 0; u < kSelRows; ++u) {
+                            const int i = i0 + u * kSelThreads;
+                            av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
+                            hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
                         }
-                        if (cnt > 1) {
-                            Cand e = cand_empty();
-                            for (int i = r0 + lane; i < r1; i += 32)
-                                if (s_rk[i - r0] <= thr) {
-                                    const T nm = s_num[i - r0];
-                                    const unsigned long long vk =
-                                        tbits(nm) == 0ull ? zero_k : okey(nm / s_a[i - r0]);
-                                    const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
-                                    cand_take(e, vk, key, i);
-                                }
-                            w = warp_min(e).idx;
+#pragma unroll
+                        for (int u = 0; u < kSelRows; ++u) {
+                            const int i = i0 + u * kSelThreads;
+                            if (i >= M) break;
+                            const T ci = col[i];
+                            const T a = (i == p) ? prq : tfma(-ci, prq, av[u]);
+                            ncol[i] = a;
+                            if (i < m) {
+                                const T num = pos_part((i == p) ? prr : tfma(-ci, prr, hv[u]));
+                                const unsigned long long rk =
+                                    okey(a) > lim_p ? screen_key(num, a) : ~0ull;
+                                snum[i] = num;
+                                srk[i] = rk;
+                                lmin = rk < lmin ? rk : lmin;
+                            }
                         }
                     }
-                    if (lane == 0) {
-                        Cand rc = cand_empty();
-                        ulonglong2 nv = make_ulonglong2(0ull, 0ull);
-                        if (w >= 0) {
-                            rc.vk = s_rk[w - r0];
-                            rc.key = nbland ? (w == p ? q : __ldcg(basis + w)) : w;
-                            rc.idx = w;
-                            nv = make_ulonglong2(tbits(s_num[w - r0]), tbits(s_a[w - r0]));
-                        }
-                        prat[g] = rc;
-                        rval[g] = nv;
-                    }
-                }
-            }
-            // this warp's reads of the protected vectors are done: arrive
-            // (also when no ratio test ran: the update threads wait for it)
-            __syncwarp();
-            if (lane == 0 && st != ST_TIMEOUT) red_add_release(rcnt, 1u);
-            if (st == ST_RUNNING) {
-                if (!warp_wait(rcnt, target, d->err, spin_limit)) {
-                    st = ST_TIMEOUT;
-                } else {
-                    np = warp_ratio_min<T>(prat, rval, G, zero_k, &nzero);
-                    if (np < 0) {
+                    const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
+                    if (rstar == ~0ull) {
                         st = ST_UNBOUNDED;
-                    } else if (np >= m) {  // never: a record from outside the column
-                        if (lane == 0) atomicExch(d->err, 1);
-                        st = ST_TIMEOUT;
+                    } else {
+                        // the rows within the screening threshold: when there is
+                        // one it is the exact minimum, otherwise compare their
+                        // exact quotients, then keys
+                        const unsigned long long thr = screen_thr(rstar, (T)0);
+                        unsigned first = 0xffffffffu, cnt = 0;
+                        for (int i = stid; i < m; i += kSelThreads)
+                            if (srk[i] <= thr) {
+                                first = (unsigned)i < first ? (unsigned)i : first;
+                                ++cnt;
+                            }
+                        unsigned gfirst, gcnt;
+                        sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
+                        if (gcnt == 1) {
+                            np = (int)gfirst;
+                            rzero = srk[np] == zero_k;  // screening keys are exact at +0
+                        } else {
+                            Cand rc = cand_empty();
+                            for (int i = stid; i < m; i += kSelThreads)
+                                if (srk[i] <= thr) {
+                                    const T nm = snum[i];
+                                    const unsigned long long vk =
+                                        tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
+                                    const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
+                                    cand_take(rc, vk, key, i);
+                                }
+                            rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
+                            np = rc.idx;
+                            rzero = rc.vk == zero_k;
+                        }
                     }
                 }
             }
-            if (lane == 0) {
+            // every selection thread of this CTA is done reading tableau k: arrive
+            // (also when no ratio test ran: the owners of protected vectors wait)
+            named_sync(2, kSelThreads);
+            if (stid == 0) {
+                if (st != ST_TIMEOUT) red_add_release(rcnt, 1u);
                 s_status = st;
                 s_p = np;
                 s_q = nq;
-                s_rzero = nzero ? 1 : 0;
+                s_rzero = rzero;
             }
         }
-        // the CTA's update of pivot k and its selection of pivot k+1 are done;
-        // the records and counters order everything else between CTAs
+        // the CTA's update of pivot k and its selection of pivot k+1 are done
         __syncthreads();
         ++iters;
         ++lk;
@@ -1466,8 +1413,11 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s) {
     int W = sh.strip;
     void *args[] = {&d_desc, &W, &spin_limit, &budget};
-    const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_kernel<double>
-                                       : (const void *)pivot_pipe_kernel<float>;
+    const void *fn = prec == PREC_FP64
+                         ? (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<double, 2>
+                                         : (const void *)pivot_pipe_kernel<double, 4>)
+                         : (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<float, 2>
+                                         : (const void *)pivot_pipe_kernel<float, 4>);
     if (sh.smem_bytes > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sh.smem_bytes);
@@ -1484,8 +1434,8 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
     const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
     sh.threads = threads > 0 ? threads : kMaxThreads;
-    sh.threads = std::min(kMaxThreads, std::max(128, (sh.threads + 31) / 32 * 32));
-    const int nu = sh.threads - 32;
+    sh.threads = std::min(kMaxThreads, std::max(2 * kSelThreadsMax, (sh.threads + 31) / 32 * 32));
+    const int nu = sh.threads - kSelThreadsMax;
     long long g = ctas > 0 ? ctas : std::min<long long>(sms, ((long long)M * P + 32767) / 32768);
     const long long gmin = (P + (long long)nu * vw - 1) / ((long long)nu * vw);
     g = std::max<long long>(std::max<long long>(g, gmin), 1);
@@ -1494,16 +1444,23 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     if (w > (long long)nu * vw) w = (long long)nu * vw / sector * sector;
     sh.strip = (int)w;
     sh.ctas = (int)((P + w - 1) / w);
-    const long long rpc = (M + sh.ctas - 1) / sh.ctas;
-    sh.smem_bytes = (((size_t)w * esz + 15) & ~(size_t)15) + (size_t)rpc * (8 + 2 * esz) + 16;
-    sh.use_smem = 1;
-    sh.scratch_stride = 0;
+    // the pivot columns of two pivots, the ratio numerators and screening keys
+    const size_t cbytes = ((size_t)M * esz + 15) & ~(size_t)15;
+    const size_t scratch = 3 * cbytes + (size_t)M * sizeof(unsigned long long);
+    const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
+    if (sprow + scratch <= kMaxDynSmem) {
+        sh.use_smem = 1;
+        sh.smem_bytes = sprow + scratch;
+        sh.scratch_stride = 0;
+    } else {
+        sh.use_smem = 0;
+        sh.smem_bytes = sprow;
+        sh.scratch_stride = (long long)((scratch + 255) & ~(size_t)255);
+    }
     sh.dual = 0;
     // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
-    // launch) and the record reductions, the strip one pass of the update
-    // threads
-    sh.pipe = sh.ctas <= sms && sh.ctas <= kMaxPipeCtas && sh.smem_bytes <= kMaxDynSmem &&
-              (long long)sh.strip <= (long long)nu * vw;
+    // launch), the strip one pass of the update threads
+    sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw;
     return sh;
 }
 
