@@ -273,6 +273,22 @@ def run_batch(args, capi, torch):
                       "all_optimal": bool(np.all(st == capi.LP_OPTIMAL)),
                       "launch_shape": {"group_elems": best.group_elems, "threads": best.threads},
                       "one_lp_per_launch_lps_per_s": round(single, 1)}), flush=True)
+    # FP32 tableaus with FP64 reinversion every k pivots, the same batch; the
+    # FP64 batch (bit-identical to the FP64 oracle) is the reference objective
+    for k in (50, 200):
+        opt = capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=k)
+        capi.lp_solve_batch(lps, opt)
+        t0 = time.perf_counter()
+        o32, s32, i32 = capi.lp_solve_batch(lps, opt)
+        w32 = time.perf_counter() - t0
+        k32 = capi.lp_batch_stats()[0]
+        err = float(np.max(np.abs(o32 - obj) / np.maximum(1.0, np.abs(obj))))
+        print(json.dumps({"workload": "batch of 1024 dense LPs, m,n log-uniform [32,1024], "
+                                      "FP32 tableau + FP64 reinversion k=%d" % k,
+                          "lps_per_s": round(1024 / w32, 1), "wall_ms": round(1e3 * w32, 2),
+                          "pivot_kernel_ms": round(k32, 2), "pivots": int(np.sum(i32)),
+                          "all_optimal": bool(np.all(s32 == capi.LP_OPTIMAL)),
+                          "max_obj_rel_err_vs_fp64": err}), flush=True)
 
 
 def run_serve(args, capi, torch):

@@ -226,6 +226,199 @@ lp_err bfail(lp_err code, const char *fmt, ...) {
 
 using namespace gbs;
 
+namespace {
+
+// ------------------------------------------------- FP32 batches (A9 + A11) --
+
+double key_to_double(unsigned long long k) {
+    const unsigned long long bits = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    return d;
+}
+
+// What the FP32 rounds need of lp_solve_batch's layout.
+struct BatchFp32 {
+    int count;
+    const int *m, *n, *sv, *G, *order;
+    const long long *in_off, *t_off, *xy_off, *P;
+    const double *d_in;
+    unsigned char *d_T;
+    double *d_xy, *d_obj;
+    LpDesc *h_desc, *d_desc;
+    int2 *h_items, *d_items;
+    unsigned *d_queue;
+    unsigned char *d_bar;
+    int ctas, threads, use_smem, sms;
+    size_t smem;
+    const lp_options *opt;
+    cudaStream_t s;
+};
+
+// Device buffers of one FP64 reinversion, sized for the largest LP and reused
+// LP by LP.
+struct ReinvPool {
+    ReinvBufs rb{};
+    size_t cap_W = 0;
+    int *h_counts = nullptr;
+    ReinvCheck *h_chk = nullptr;
+    ~ReinvPool() {
+        void *bufs[] = {rb.Lflag, rb.S, rb.R, rb.posS, rb.posR, rb.counts, rb.pivrow, rb.W,
+                        rb.xS, rb.yR, rb.zrow, rb.rhs, rb.chk, rb.bar};
+        for (void *p : bufs)
+            if (p) cudaFree(p);
+        if (h_counts) cudaFreeHost(h_counts);
+        if (h_chk) cudaFreeHost(h_chk);
+    }
+    cudaError_t init(size_t cap) {
+        void **ints[] = {(void **)&rb.Lflag, (void **)&rb.S, (void **)&rb.R, (void **)&rb.posS,
+                         (void **)&rb.posR, (void **)&rb.pivrow};
+        for (void **q : ints) {
+            cudaError_t e = cudaMalloc(q, cap * sizeof(int));
+            if (e != cudaSuccess) return e;
+        }
+        void **dbl[] = {(void **)&rb.xS, (void **)&rb.yR, (void **)&rb.zrow, (void **)&rb.rhs};
+        for (void **q : dbl) {
+            cudaError_t e = cudaMalloc(q, cap * sizeof(double));
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaMalloc(&rb.counts, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&rb.chk, sizeof(ReinvCheck));
+        if (e == cudaSuccess) e = cudaMalloc(&rb.bar, 128 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMallocHost(&h_counts, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost(&h_chk, sizeof(ReinvCheck));
+        return e;
+    }
+};
+
+// FP32 batch: rounds of one batched launch (every unfinished LP pivots up to
+// reinv_k times in FP32), then, LP by LP, the FP64 reinversion of its basis
+// and the same decisions as the single-LP FP32 mode: accept an FP32 optimum
+// only when the FP64 values are primal and dual feasible, otherwise continue
+// with the rule whose invariant holds (primal simplex from a primal-feasible
+// basis, dual simplex from a dual-feasible one).  x, y and the objective are
+// the FP64 values of the last reinversion.
+lp_err solve_batch_fp32(const BatchFp32 &f, lp_status *fin, double *kernel_ms) {
+    const int count = f.count;
+    cudaStream_t s = f.s;
+    size_t cap = 0, capW = 0;
+    for (int k = 0; k < count; ++k) {
+        cap = std::max(cap, (size_t)std::max(f.m[k], f.n[k]) + f.m[k]);
+        const size_t ns = (size_t)std::min(f.m[k], f.n[k]);
+        capW = std::max(capW, ns * (((2 * ns + 1) + 31) / 32 * 32));
+    }
+    ReinvPool rp;
+    B_TRY(rp.init(cap));
+    B_TRY(cudaMalloc(&rp.rb.W, std::max<size_t>(capW, 1) * sizeof(double)));
+    rp.cap_W = capW;
+
+    std::vector<int> active(count, 1), rule(count), failed(count, 0);
+    std::vector<long long> remaining(count), guard(count), before(count);
+    for (int k = 0; k < count; ++k) {
+        rule[k] = f.sv[k];
+        remaining[k] = f.opt->max_iters;
+        guard[k] = 20ll * (f.m[k] + f.n[k]) + 1000;
+    }
+    cudaEvent_t e0, e1;
+    B_TRY(cudaEventCreate(&e0));
+    B_TRY(cudaEventCreate(&e1));
+    *kernel_ms = 0.0;
+    for (int round = 0;; ++round) {
+        // work items of the unfinished LPs, largest first
+        int nitems = 0;
+        long long budget = f.opt->reinv_k;
+        for (int o = 0; o < count; ++o) {
+            const int k = f.order[o];
+            if (!active[k]) continue;
+            budget = std::min(budget, remaining[k]);
+            for (int r = 0; r < f.G[k]; ++r) f.h_items[nitems++] = make_int2(k, r);
+            f.h_desc[k].sense = rule[k];
+            before[k] = f.h_desc[k].iters;
+        }
+        if (nitems == 0) break;
+        B_TRY(cudaMemcpyAsync(f.d_items, f.h_items, nitems * sizeof(int2), cudaMemcpyHostToDevice, s));
+        B_TRY(cudaMemcpyAsync(f.d_desc, f.h_desc, count * sizeof(LpDesc), cudaMemcpyHostToDevice, s));
+        B_TRY(cudaMemsetAsync(f.d_bar, 0, (size_t)count * 512, s));
+        B_TRY(cudaMemsetAsync(f.d_queue, 0, sizeof(unsigned), s));
+        B_TRY(cudaEventRecord(e0, s));
+        B_TRY(launch_batch(PREC_FP32, f.d_desc, f.d_items, nitems, f.d_queue, f.ctas, f.threads,
+                           f.smem, f.use_smem, f.opt->spin_timeout_cycles, budget, s));
+        B_TRY(cudaEventRecord(e1, s));
+        B_TRY(cudaMemcpyAsync(f.h_desc, f.d_desc, count * sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
+        B_TRY(cudaStreamSynchronize(s));
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        *kernel_ms += t;
+        for (int k = 0; k < count; ++k) {
+            if (!active[k]) continue;
+            LpDesc &d = f.h_desc[k];
+            const long long made = d.iters - before[k];
+            remaining[k] -= made;
+            guard[k] -= made;
+            const int st = d.status;
+            auto finish = [&](lp_status v) {
+                fin[k] = v;
+                active[k] = 0;
+            };
+            if (st == LP_TIMEOUT) {
+                finish(LP_TIMEOUT);
+                continue;
+            }
+            // FP64 reinversion of the basis reached
+            const int m = f.m[k], n = f.n[k];
+            const double *A = f.d_in + f.in_off[k], *b = A + (long long)m * n, *c = b + m;
+            B_TRY(launch_reinv_lists(d.basis, m, n, rp.rb, s));
+            B_TRY(cudaMemcpyAsync(rp.h_counts, rp.rb.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            B_TRY(cudaStreamSynchronize(s));
+            const int ns = rp.h_counts[0];
+            if (rp.h_counts[1] != ns)
+                return bfail(LP_ERR_STATE, "lp_solve_batch: LP %d: inconsistent basis", k);
+            rp.rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
+            double *x = f.d_xy + f.xy_off[k];
+            B_TRY(launch_reinv_solve(PREC_FP32, A, b, c, f.sv[k], m, n, d.basis, rp.rb, ns,
+                                     f.d_T + f.t_off[k], f.P[k], x, x + n, f.d_obj + k, f.sms,
+                                     f.opt->spin_timeout_cycles, s));
+            B_TRY(cudaMemcpyAsync(rp.h_chk, rp.rb.chk, sizeof(ReinvCheck), cudaMemcpyDeviceToHost, s));
+            B_TRY(cudaStreamSynchronize(s));
+            if (rp.h_chk->singular) {
+                finish(LP_NUMERICAL);
+                continue;
+            }
+            const bool pfeas = key_to_double(rp.h_chk->rhsmin_key) >= -d.eps_r;
+            const bool dfeas = key_to_double(rp.h_chk->zmin_key) >= -d.eps_d;
+            if (st == LP_OPTIMAL) {
+                if (pfeas && dfeas) {
+                    finish(LP_OPTIMAL);
+                } else if ((!pfeas && !dfeas) || ++failed[k] > 4) {
+                    finish(LP_NUMERICAL);
+                } else {
+                    rule[k] = pfeas ? 0 : 1;
+                }
+                continue;
+            }
+            if (st == LP_UNBOUNDED || st == LP_INFEASIBLE) {
+                finish((lp_status)st);
+                continue;
+            }
+            if (remaining[k] <= 0) {
+                finish(LP_ITER_LIMIT);
+                continue;
+            }
+            if (guard[k] <= 0) {
+                finish(LP_NUMERICAL);
+                continue;
+            }
+            if (rule[k] == 0 && !pfeas && dfeas) rule[k] = 1;
+            else if (rule[k] == 1 && !dfeas && pfeas) rule[k] = 0;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return LP_OK;
+}
+
+}  // namespace
+
 extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const double *const *A,
                                  const double *const *b, const double *const *c,
                                  const int *sense, const lp_options *opt, double *obj,
@@ -235,8 +428,10 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
         return bfail(LP_ERR_INVALID_ARG, "lp_solve_batch: need count >= 1 and non-NULL arrays");
     lp_options o;
     if (opt) o = *opt; else lp_options_default(&o);
-    if (o.precision != LP_FP64)
-        return bfail(LP_ERR_INVALID_ARG, "lp_solve_batch: FP64 only");
+    if (o.precision != LP_FP64 && o.precision != LP_FP32_REINV)
+        return bfail(LP_ERR_INVALID_ARG, "lp_solve_batch: unknown precision %d", o.precision);
+    if (o.precision == LP_FP32_REINV && o.reinv_k < 1)
+        return bfail(LP_ERR_INVALID_ARG, "lp_solve_batch: reinv_k must be >= 1");
     if (o.max_iters < 0 || o.bland_after < 0 || o.spin_timeout_cycles <= 0 || o.threads < 0 ||
         o.group_elems < 0 || o.device < 0 || o.device >= 64)
         return bfail(LP_ERR_INVALID_ARG, "lp_solve_batch: option out of range");
@@ -251,9 +446,13 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
     B_TRY(cudaSetDevice(o.device));
     int sms = 0;
     B_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device));
-    const int prec = PREC_FP64;
-    const size_t esz = sizeof(double);
-    const int vw = 2, sector = 4;
+    // FP32 tableaus pivot with the FP64 reinversion between rounds of
+    // reinv_k pivots; the pivot rule of an LP may switch, so its selection
+    // scratch is sized for either rule
+    const bool fp32 = o.precision == LP_FP32_REINV;
+    const int prec = fp32 ? PREC_FP32 : PREC_FP64;
+    const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+    const int vw = fp32 ? 4 : 2, sector = fp32 ? 8 : 4;
     int threads = o.threads > 0 ? std::min(o.threads, 512) : 512;
     threads = std::max(64, (threads + 31) / 32 * 32);
     const long long gelems = o.group_elems > 0 ? o.group_elems : 262144;
@@ -277,7 +476,7 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
         G[k] = (int)((P[k] + w - 1) / w);
         const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
         const size_t scol = ((size_t)M[k] * esz + 15) & ~(size_t)15;
-        const size_t sr = (size_t)(sv[k] == 0 ? M[k] : N[k]) * sizeof(double);
+        const size_t sr = (size_t)(sv[k] == 0 && !fp32 ? M[k] : N[k]) * sizeof(double);
         smem_max = std::max(smem_max, sprow + scol + sr);
         sprow_max = std::max(sprow_max, sprow);
     }
@@ -313,7 +512,7 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
         scr_off[k] = (long long)scr_total;
         if (!use_smem) {
             const size_t scol = ((size_t)M[k] * esz + 15) & ~(size_t)15;
-            const size_t sr = (size_t)(sv[k] == 0 ? M[k] : N[k]) * sizeof(double);
+            const size_t sr = (size_t)(sv[k] == 0 && !fp32 ? M[k] : N[k]) * sizeof(double);
             scr_total += (size_t)G[k] * up256(scol + sr);
         }
     }
@@ -444,7 +643,7 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
         d.scratch = use_smem ? nullptr : D + o_scr + scr_off[k];
         if (!use_smem) {
             const size_t scol = ((size_t)M[k] * esz + 15) & ~(size_t)15;
-            const size_t sr = (size_t)(sv[k] == 0 ? M[k] : N[k]) * sizeof(double);
+            const size_t sr = (size_t)(sv[k] == 0 && !fp32 ? M[k] : N[k]) * sizeof(double);
             d.scratch_stride = (long long)up256(scol + sr);
         }
         d.part_sel = reinterpret_cast<Cand *>(D + o_part + po);
@@ -472,9 +671,71 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
     B_TRY(cudaMemcpyAsync(d_desc, h_desc, count * sizeof(LpDesc), cudaMemcpyHostToDevice, s));
     B_TRY(cudaMemsetAsync(D + o_bar, 0, (size_t)count * 512, s));
     B_TRY(cudaMemsetAsync(D + o_queue, 0, sizeof(unsigned), s));
-    batch_build_kernel<double><<<dim3(16, count), 256, 0, s>>>(
-        ba, d_in, D + o_T, reinterpret_cast<int *const *>(D + o_bptr));
+    if (fp32)
+        batch_build_kernel<float><<<dim3(16, count), 256, 0, s>>>(
+            ba, d_in, D + o_T, reinterpret_cast<int *const *>(D + o_bptr));
+    else
+        batch_build_kernel<double><<<dim3(16, count), 256, 0, s>>>(
+            ba, d_in, D + o_T, reinterpret_cast<int *const *>(D + o_bptr));
     B_TRY(cudaGetLastError());
+    double *d_xy = reinterpret_cast<double *>(D + o_xy), *d_obj = reinterpret_cast<double *>(D + o_obj);
+    if (fp32) {
+        BatchFp32 f;
+        f.count = count;
+        f.m = m;
+        f.n = n;
+        f.sv = sv.data();
+        f.G = G.data();
+        f.order = order.data();
+        f.in_off = in_off.data();
+        f.t_off = t_off.data();
+        f.xy_off = xy_off.data();
+        f.P = P.data();
+        f.d_in = d_in;
+        f.d_T = D + o_T;
+        f.d_xy = d_xy;
+        f.d_obj = d_obj;
+        f.h_desc = h_desc;
+        f.d_desc = reinterpret_cast<LpDesc *>(D + o_desc);
+        f.h_items = reinterpret_cast<int2 *>(H + o_items);
+        f.d_items = reinterpret_cast<int2 *>(D + o_items);
+        f.d_queue = reinterpret_cast<unsigned *>(D + o_queue);
+        f.d_bar = D + o_bar;
+        f.ctas = ctas;
+        f.threads = threads;
+        f.smem = smem;
+        f.use_smem = use_smem;
+        f.sms = sms;
+        f.opt = &o;
+        f.s = s;
+        lp_status *fin = nullptr;
+        double kms = 0.0;
+        std::vector<lp_status> fstat(count, LP_NOT_SOLVED);
+        fin = fstat.data();
+        const lp_err fe = solve_batch_fp32(f, fin, &kms);
+        if (fe != LP_OK) return fe;
+        B_TRY(cudaMemcpyAsync(h_obj, d_obj, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (x || y)
+            B_TRY(cudaMemcpyAsync(h_xy, d_xy, xy_total * sizeof(double), cudaMemcpyDeviceToHost, s));
+        B_TRY(cudaStreamSynchronize(s));
+        long long piv = 0;
+        for (int k = 0; k < count; ++k) {
+            if (obj) obj[k] = h_obj[k];
+            if (status) status[k] = fin[k];
+            if (iters) iters[k] = h_desc[k].iters;
+            piv += h_desc[k].iters;
+            if (x && x[k]) memcpy(x[k], h_xy + xy_off[k], sizeof(double) * n[k]);
+            if (y && y[k]) memcpy(y[k], h_xy + xy_off[k] + n[k], sizeof(double) * m[k]);
+        }
+        std::lock_guard<std::mutex> sl(g_stats_mu);
+        g_last.kernel_ms = kms;
+        g_last.pivots = piv;
+        g_last.ctas = ctas;
+        g_last.threads = threads;
+        g_last.items = (int)items.size();
+        g_last.max_group = max_group;
+        return LP_OK;
+    }
     cudaEvent_t e0, e1;
     B_TRY(cudaEventCreate(&e0));
     B_TRY(cudaEventCreate(&e1));
@@ -483,7 +744,6 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
                        reinterpret_cast<unsigned *>(D + o_queue), ctas, threads, smem, use_smem,
                        o.spin_timeout_cycles, o.max_iters, s));
     B_TRY(cudaEventRecord(e1, s));
-    double *d_xy = reinterpret_cast<double *>(D + o_xy), *d_obj = reinterpret_cast<double *>(D + o_obj);
     batch_extract_kernel<double><<<count, 256, 0, s>>>(ba, D + o_T,
                                                        reinterpret_cast<int *const *>(D + o_bptr),
                                                        d_xy, d_obj);

@@ -111,3 +111,41 @@ def test_batch_autotune_and_cache(tmp_path):
     assert (again.group_elems, again.threads) == (best.group_elems, best.threads)
     assert len(open(cache).read().strip().splitlines()) == 1
     _check_against_oracle(lps, capi.lp_solve_batch(lps, best, want_xy=True))
+
+
+def _rel(a, b):
+    return abs(a - b) / max(1.0, abs(b))
+
+
+@pytest.mark.parametrize("k", [50, 200])
+def test_batch_fp32_objective_vs_fp64_oracle(k):
+    """FP32 tableaus with FP64 reinversion every k pivots, many LPs in one
+    batch: each objective within 1e-6 of the FP64 oracle, with an FP64
+    optimality certificate for the x, y returned."""
+    lps = _mixed(40, 16, 400, seed=7)
+    opt = capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=k)
+    obj, st, it, xs, ys = capi.lp_solve_batch(lps, opt, want_xy=True)
+    for j, (A, b, c, sense) in enumerate(lps):
+        o = oracle.solve(A, b, c, sense=sense)
+        assert st[j] == capi.LP_OPTIMAL, j
+        assert _rel(obj[j], o.obj) <= 1e-6, (j, obj[j], o.obj)
+        cert = oracle.certificate(A, b, c, xs[j], ys[j], obj[j], sense=sense)
+        scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
+        assert max(cert.values()) <= 1e-6 * scale, (j, cert)
+
+
+def test_batch_fp32_matches_solo_fp32():
+    """A batched FP32 LP pivots, reinverts and ends exactly as it does alone."""
+    lps = _mixed(12, 8, 200, seed=8)
+    opt = capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50)
+    obj, st, it = capi.lp_solve_batch(lps, opt)
+    for j, (A, b, c, sense) in enumerate(lps):
+        h = capi.lp_create(capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50))
+        try:
+            capi.lp_load(h, A, b, c, sense)
+            capi.lp_solve(h)
+            o1, s1, i1 = capi.lp_result(h)
+        finally:
+            capi.lp_destroy(h)
+        assert (st[j], it[j]) == (s1, i1), j
+        assert _bits([obj[j]])[0] == _bits([o1])[0], (j, obj[j], o1)
