@@ -64,10 +64,11 @@ def peaks():
 
 
 # The kernel each LP of the set runs on (default options): the primal LPs on
-# the pipelined kernel (in place up to 96 MB of tableau, double-buffered
-# above), the dual form on the dual simplex kernel.
+# the pipelined primal kernel (in place up to 96 MB of tableau,
+# double-buffered above), the dual form on the pipelined dual simplex kernel
+# (double-buffered).
 PRIMAL_KERNEL = "pivot_pipe_kernel<double>"
-DUAL_KERNEL = "pivot_kernel<double, SMEM, DUAL> (dual simplex)"
+DUAL_KERNEL = "pivot_pipe_dual_kernel<double> (dual simplex)"
 
 
 def kernel_of(sense):

@@ -265,29 +265,43 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    // the primal rule runs on the pipelined kernel where it can take the LP;
-    // double-buffered for tableaus larger than the L2 cache
-    // (the primal rule runs for LP_MAX_LE, and in FP32 mode for either sense)
-    const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
-    int pmode = primal ? h->opt.pipeline : 0;
-    if (pmode == 1) pmode = (size_t)M * P * esz <= kL2FitBytes ? 2 : 3;
-    if (pmode == 3 && grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz) != cudaSuccess) {
-        cudaGetLastError();
-        pmode = h->opt.pipeline == 1 ? 0 : -1;
-    }
-    if (pmode < 0) {
-        set_err(h, "lp_load: no device memory for the second tableau buffer (pipeline 3)");
-        return LP_ERR_OOM;
-    }
-    if (pmode != 0 && pmode != 2 && pmode != 3) {
+    // the pipelined kernels where they can take the LP: the primal rule in
+    // place for tableaus that fit L2 and double-buffered above, the dual rule
+    // double-buffered (the rule runs for its sense, and in FP32 mode for both)
+    if (h->opt.pipeline < 0 || h->opt.pipeline > 3) {
         set_err(h, "lp_load: unknown pipeline mode %d", h->opt.pipeline);
         return LP_ERR_INVALID_ARG;
     }
+    const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
+    const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32;
+    int pmode = primal ? h->opt.pipeline : 0;
+    if (pmode == 1) pmode = (size_t)M * P * esz <= kL2FitBytes ? 2 : 3;
+    const bool dwant = dualr && h->opt.pipeline != 0;
+    bool have_t2 = false;
+    if (pmode == 3 || dwant) {
+        have_t2 = grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz) == cudaSuccess;
+        if (!have_t2) cudaGetLastError();
+    }
+    if (pmode == 3 && !have_t2) {
+        if (h->opt.pipeline == 3) {
+            set_err(h, "lp_load: no device memory for the second tableau buffer (pipeline 3)");
+            return LP_ERR_OOM;
+        }
+        pmode = 0;
+    }
+    const bool dpipe = dwant && have_t2;
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
-            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas);
+            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas, 0);
             if (ps.pipe) {
                 if (pmode == 3) ps.pipe = 2;  // double-buffered
+                return ps;
+            }
+        }
+        if (rule == 1 && dpipe) {
+            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas, 1);
+            if (ps.pipe) {
+                ps.pipe = 2;
                 return ps;
             }
         }
@@ -296,7 +310,6 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const PivotShape sh = shape_for((int)sense);
     // the other rule (FP32 recovery)
     const PivotShape sh_alt = shape_for(1 - (int)sense);
-    const bool pipe = sh.pipe || (h->prec == PREC_FP32 && sh_alt.pipe);
     const int ctas_max = h->prec == PREC_FP32 ? std::max(sh.ctas, sh_alt.ctas) : sh.ctas;
 
     CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
@@ -391,7 +404,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.scratch_stride = sh.scratch_stride;
     d.part_sel = h->dpart;
     d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 2 * (size_t)h->max_ctas);
-    d.T2 = pipe && pmode == 3 ? h->dT2 : nullptr;
+    d.T2 = have_t2 ? h->dT2 : nullptr;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;

@@ -107,7 +107,9 @@ int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, 
 // The returned shape has pipe == 0 when the kernel cannot take the LP (a grid
 // larger than one CTA per SM); its scratch is in shared memory when it fits,
 // else a global slice of scratch_stride bytes per CTA.
-PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas);
+// dual: the dual simplex kernel (double-buffered only).
+PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas,
+                             int dual);
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s);
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,

@@ -541,7 +541,8 @@ __device__ __forceinline__ unsigned long long sel_min_u64(unsigned long long v,
 // SW selection warps; SW == 2 runs the double-buffered mode, SW == 4 in place.
 template <typename T, int SW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_pipe_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    pivot_pipe_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget,
+                      int dbm) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
     constexpr int kSelWarps = SW, kSelThreads = 32 * SW;
@@ -561,9 +562,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const int lane = tid & 31;
     const bool selw = tid >= NU;
     const int stid = tid - NU;
-    // in place, or double-buffered (T2 set): pivot k reads bufs[cur] and
-    // writes bufs[cur ^ 1], with a grid barrier after each pivot
-    const bool db = d->T2 != nullptr;
+    // in place, or double-buffered (dbm; T2 is the second buffer): pivot k
+    // reads bufs[cur] and writes bufs[cur ^ 1], with a grid barrier after
+    // each pivot
+    const bool db = dbm != 0 && d->T2 != nullptr;
     T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(db ? d->T2 : d->T)};
     int cur = 0;
     const T *Tab = bufs[0];
@@ -904,6 +906,316 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             d->T = bufs[cur];
             d->T2 = bufs[cur ^ 1];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined dual simplex for the dual form (sense LP_MIN_GE), double-buffered:
+// pivot k reads bufs[cur] and writes bufs[cur ^ 1], so the selection of pivot
+// k+1 reads tableau k while the update warps stream pivot k.
+//   update warps     divide the strip of the pivot row (Step 4), update the
+//                    strip of the objective row (kept for the selection) and
+//                    the rest of the strip (Step 5);
+//   selection warps  form the rhs of tableau k+1 over every row and take the
+//                    leaving row r' (the most negative rhs; every CTA does this
+//                    redundantly), then row r' of tableau k+1 on the CTA's own
+//                    strip and the dual ratio test on it, publish the strip's
+//                    winner with its pivot-row value, reduce the G records to
+//                    the entering column q', and form column q' of tableau k+1
+//                    (the next pivot column) in the CTA's scratch.
+// The values the selection forms are the very fma results the update writes.
+// A grid barrier ends each pivot.  The first pivot's selection runs alone.
+template <typename T, int SW>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    pivot_pipe_dual_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    typedef typename Vec<T>::type V;
+    constexpr int VW = Vec<T>::W;
+    constexpr int kSelThreads = 32 * SW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Cand rbuf[2][32];
+    __shared__ Cand selc[SW];
+    __shared__ unsigned long long selq[SW];
+    __shared__ int s_flag, s_p, s_q, s_status, s_rzero, s_sok;
+
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+    const int NU = B - kSelThreads;  // update threads; the last SW warps select
+    const bool selw = tid >= NU;
+    const int stid = tid - NU;
+    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
+    int cur = 0;
+    const long long P = d->P;
+    const int m = d->m, M = d->M, N = d->N;
+    int *__restrict__ basis = d->basis;
+    const int bland_after = d->bland_after;
+    const unsigned long long lim_np = okey((T)(-d->eps_p));
+    const unsigned long long lim_r = okey((T)(-d->eps_r));
+    const unsigned long long zero_k = okey((T)0);
+    long long iters = d->iters;
+    const long long iter_limit =
+        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
+    int deg = d->deg;
+    int status = ST_RUNNING;
+    unsigned *rcnt = d->bar + 128;
+
+    // strip and thread map of the update threads
+    const int c0 = g * W;  // < P: the host launches ceil(P / W) CTAs
+    const int c1 = (int)min((long long)c0 + W, P);
+    const int jend = min(c1, N - 1);  // the strip's columns that may enter
+    const int vpr = (c1 - c0) / VW;
+    const int rpp = NU / vpr;  // >= 1: the host keeps W <= NU * VW
+    const int lr = tid / vpr, lv = tid - lr * vpr;
+    const bool active = !selw && lr < rpp;
+    const int col0 = c0 + lv * VW;
+    // scratch: the strip of the pivot row in shared memory; the strip of the
+    // new objective row and the pivot columns of this and the next pivot in
+    // shared memory, or in this CTA's slice of global scratch
+    T *sprow = reinterpret_cast<T *>(smem_raw);
+    const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
+    unsigned char *sc = d->scratch_stride > 0
+                            ? reinterpret_cast<unsigned char *>(d->scratch) +
+                                  (size_t)g * (size_t)d->scratch_stride
+                            : smem_raw + wbytes;
+    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
+    T *sz = reinterpret_cast<T *>(sc);
+    T *scol[2] = {reinterpret_cast<T *>(sc + wbytes), reinterpret_cast<T *>(sc + wbytes + cbytes)};
+
+    // ---- selection of the first pivot from the current tableau (all threads) ----
+    int p = -1, q = -1;
+    {
+        const T *A = bufs[0];
+        const int bland = deg >= bland_after;
+        // leaving row, in every CTA over all rows
+        Cand c = cand_empty();
+        for (int i = tid; i < m; i += B) {
+            const unsigned long long vk = okey(lds(A + (long long)i * P + (N - 1)));
+            if (vk < lim_r) cand_take(c, bland ? zero_k : vk, bland ? __ldcg(basis + i) : i, i);
+        }
+        c = block_min_c(c, rbuf[0]);
+        if (c.idx < 0) status = ST_OPTIMAL;
+        else if (iters >= iter_limit) status = ST_ITER_LIMIT;
+        else p = c.idx;
+        if (status == ST_RUNNING) {
+            // entering column: the dual ratio test on this CTA's strip of row
+            // p, then over the CTAs' partials
+            const T *rowr = A + (long long)p * P, *z = A + (long long)m * P;
+            Cand e = cand_empty();
+            for (int j = c0 + tid; j < jend; j += B) {
+                const T a = lds(rowr + j);
+                if (okey(a) < lim_np) cand_take(e, okey(pos_part(lds(z + j)) / neg(a)), j, j);
+            }
+            e = block_min_c(e, rbuf[1]);
+            if (tid == 0) d->part_sel[g] = e;
+            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
+            if (status == ST_RUNNING) {
+                const Cand sel = load_partials_min(d->part_sel, G, rbuf[0]);
+                if (sel.idx < 0) {
+                    status = ST_INFEASIBLE;
+                } else if (sel.idx >= N - 1) {
+                    status = ST_TIMEOUT;  // never: a partial from outside the row
+                } else {
+                    q = sel.idx;
+                    deg = (sel.vk == zero_k) ? deg + 1 : 0;
+                    for (int i = tid; i < M; i += B) scol[0][i] = lds(A + (long long)i * P + q);
+                }
+            }
+        }
+    }
+    __syncthreads();  // the first pivot column is in scol[0]
+
+    int lk = 0;  // pivots made in this launch (parity of records and pivot columns)
+    while (status == ST_RUNNING) {
+        const T *A = bufs[cur];
+        T *Bn = bufs[cur ^ 1];
+        const T *col = scol[lk & 1];
+        T *ncol = scol[(lk + 1) & 1];
+        const int par = (lk + 1) & 1;  // records of the selection of pivot k+1
+        Cand *psel = d->part_sel + par * G;
+        ulonglong2 *pval = reinterpret_cast<ulonglong2 *>(d->part_vals) + par * G;
+        const unsigned target = (unsigned)G * (unsigned)(lk + 1);
+        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
+            if (iters < d->trace_cap) {
+                d->trace[2 * iters] = p;
+                d->trace[2 * iters + 1] = q;
+            }
+            basis[p] = q;
+            d->last_p = p;
+            d->last_q = q;
+        }
+        const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
+        const T piv = col[p];
+        if (!selw) {
+            // Step 4 on this CTA's strip of the pivot row
+            for (int j = c0 + tid; j < c1; j += NU)
+                sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
+            named_sync(1, NU);
+            // the strip of the objective row, also kept for the selection
+            if (tid < vpr) {
+                const T colm = col[m];
+                const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
+                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
+                vfma(zt, colm, pr);
+                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
+                *reinterpret_cast<V *>(sz + tid * VW) = zt;
+            }
+            named_sync(3, B);  // sprow and sz ready for the selection warps
+            // Step 5 on the constraint rows of the strip
+            if (active) {
+                const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
+                const T *abase = A + col0;
+                T *bbase = Bn + col0;
+                int i = lr;
+                for (; i + 3 * rpp < m; i += 4 * rpp) {
+                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                    const T a0 = col[i], a1 = col[i1], a2 = col[i2], a3 = col[i3];
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p, a0, pr);
+                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p, a1, pr);
+                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p, a2, pr);
+                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p, a3, pr);
+                }
+                for (; i < m; i += rpp) {
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) =
+                        pivot_vec<T>(t0, i, p, col[i], pr);
+                }
+            }
+        } else {
+            // selection of pivot k+1, overlapping the update of pivot k
+            int st = ST_RUNNING, np = -1, nq = -1, rzero = 0;
+            // leaving row: the rhs of tableau k+1 over every row
+            const T prr = lds(A + (long long)p * P + (N - 1)) / piv;
+            Cand c = cand_empty();
+            for (int i0 = stid; i0 < m; i0 += kSelRows * kSelThreads) {
+                T hv[kSelRows];
+#pragma unroll
+                for (int u = 0; u < kSelRows; ++u) {
+                    const int i = i0 + u * kSelThreads;
+                    hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < kSelRows; ++u) {
+                    const int i = i0 + u * kSelThreads;
+                    if (i >= m) break;
+                    const T rhs = (i == p) ? prr : tfma(-col[i], prr, hv[u]);
+                    const unsigned long long vk = okey(rhs);
+                    if (vk < lim_r)
+                        cand_take(c, nbland ? zero_k : vk,
+                                  nbland ? (i == p ? q : __ldcg(basis + i)) : i, i);
+                }
+            }
+            c = sel_min<SW>(c, 0ull, selc, selq, nullptr);
+            if (c.idx < 0) st = ST_OPTIMAL;
+            else if (iters + 1 >= iter_limit) st = ST_ITER_LIMIT;
+            else if (c.idx >= m) st = ST_TIMEOUT;  // never: a row outside the tableau
+            else np = c.idx;
+            if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+            named_sync(3, B);  // the update warps' sprow and sz
+            if (st == ST_RUNNING) {
+                // row r' of tableau k+1 on this strip and the dual ratio test
+                const T cr = col[np];
+                Cand e = cand_empty();
+                unsigned long long eq = 0ull;
+                for (int j = c0 + stid; j < jend; j += kSelThreads) {
+                    const T pr = sprow[j - c0];
+                    const T a = (np == p) ? pr : tfma(-cr, pr, lds(A + (long long)np * P + j));
+                    if (okey(a) < lim_np) {
+                        const unsigned long long vk = okey(pos_part(sz[j - c0]) / neg(a));
+                        if (vk < e.vk || (vk == e.vk && j < e.key)) {
+                            e.vk = vk;
+                            e.key = j;
+                            e.idx = j;
+                            eq = tbits(pr);
+                        }
+                    }
+                }
+                e = sel_min<SW>(e, eq, selc, selq, &eq);
+                if (stid == 0) {
+                    psel[g] = e;
+                    pval[g] = make_ulonglong2(eq, 0ull);
+                }
+            }
+            named_sync(2, kSelThreads);
+            if (stid == 0 && st != ST_TIMEOUT) red_add_release(rcnt, 1u);
+            if (st == ST_RUNNING) {
+                if (stid == 0) s_sok = (int)wait_ctr(rcnt, target, d->err, spin_limit);
+                named_sync(2, kSelThreads);
+                if (!s_sok) {
+                    st = ST_TIMEOUT;
+                } else {
+                    // entering column from the G records, with its pivot-row value
+                    Cand e = cand_empty();
+                    unsigned long long eq = 0ull;
+                    for (int k = stid; k < G; k += kSelThreads) {
+                        const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(psel) + k));
+                        const unsigned long long rq = __ldcg(&pval[k].x);
+                        if (cand_less(r, e)) {
+                            e = r;
+                            eq = rq;
+                        }
+                    }
+                    unsigned long long prq_b;
+                    const Cand sel = sel_min<SW>(e, eq, selc, selq, &prq_b);
+                    if (sel.idx < 0) {
+                        st = ST_INFEASIBLE;
+                    } else if (sel.idx >= N - 1) {  // never: a record from outside the row
+                        if (stid == 0) atomicExch(d->err, 1);
+                        st = ST_TIMEOUT;
+                    } else {
+                        nq = sel.idx;
+                        rzero = sel.vk == zero_k;
+                        // column q' of tableau k+1: the next pivot column
+                        const T prq = tfrom<T>(prq_b);
+                        for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                            T av[kSelRows];
+#pragma unroll
+                            for (int u = 0; u < kSelRows; ++u) {
+                                const int i = i0 + u * kSelThreads;
+                                av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < kSelRows; ++u) {
+                                const int i = i0 + u * kSelThreads;
+                                if (i >= M) break;
+                                ncol[i] = (i == p) ? prq : tfma(-col[i], prq, av[u]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (stid == 0) {
+                s_status = st;
+                s_p = np;
+                s_q = nq;
+                s_rzero = rzero;
+            }
+        }
+        // the CTA's update of pivot k and its selection of pivot k+1 are done
+        __syncthreads();
+        ++iters;
+        ++lk;
+        status = s_status;
+        if (status == ST_RUNNING) {
+            p = s_p;
+            q = s_q;
+            deg = s_rzero ? deg + 1 : 0;
+        }
+        cur ^= 1;
+        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+    }
+
+    if (g == 0 && tid == 0) {
+        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
+        d->iters = iters;
+        d->iter_limit = iter_limit;
+        d->deg = deg;
+        d->T = bufs[cur];  // hand over the buffer holding the last tableau
+        d->T2 = bufs[cur ^ 1];
     }
 }
 
@@ -1412,7 +1724,19 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s) {
     int W = sh.strip;
-    void *args[] = {&d_desc, &W, &spin_limit, &budget};
+    int dbm = sh.pipe == 2 ? 1 : 0;
+    void *args[] = {&d_desc, &W, &spin_limit, &budget, &dbm};
+    if (sh.dual) {
+        const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_dual_kernel<double, 4>
+                                           : (const void *)pivot_pipe_dual_kernel<float, 4>;
+        if (sh.smem_bytes > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sh.smem_bytes);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args,
+                                           sh.smem_bytes, s);
+    }
     const void *fn = prec == PREC_FP64
                          ? (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<double, 2>
                                          : (const void *)pivot_pipe_kernel<double, 4>)
@@ -1429,7 +1753,8 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
 // Launch shape of the pipelined kernel: strips sized for the update threads
 // (all but the last warp), shared memory for the strip and the selection
 // warp's block of rows.
-PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas) {
+PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas,
+                             int dual) {
     PivotShape sh;
     const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
     const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -1444,10 +1769,12 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     if (w > (long long)nu * vw) w = (long long)nu * vw / sector * sector;
     sh.strip = (int)w;
     sh.ctas = (int)((P + w - 1) / w);
-    // the pivot columns of two pivots, the ratio numerators and screening keys
+    // the pivot columns of two pivots and the ratio numerators and screening
+    // keys (primal), or the strip of the new objective row (dual)
     const size_t cbytes = ((size_t)M * esz + 15) & ~(size_t)15;
-    const size_t scratch = 3 * cbytes + (size_t)M * sizeof(unsigned long long);
     const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
+    const size_t scratch = dual ? sprow + 2 * cbytes
+                                : 3 * cbytes + (size_t)M * sizeof(unsigned long long);
     if (sprow + scratch <= kMaxDynSmem) {
         sh.use_smem = 1;
         sh.smem_bytes = sprow + scratch;
@@ -1457,7 +1784,7 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
         sh.smem_bytes = sprow;
         sh.scratch_stride = (long long)((scratch + 255) & ~(size_t)255);
     }
-    sh.dual = 0;
+    sh.dual = dual;
     // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
     // launch), the strip one pass of the update threads
     sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw;
