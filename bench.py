@@ -31,6 +31,7 @@ WORKLOAD_NAME = ("dense LP set: 2048x2048 primal + 2048x2048 dual form + 512x409
                  "FP64, Dantzig pricing")
 FP64_DFMA_PER_CLK_SM = 2          # GB300 FP64 rate: 1.25 TFLOP/s nominal = 2 DFMA/clk/SM
 SMS, SM_MAX_MHZ = 152, 2070.0
+HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal
 ALU_PEAK_TFLOPS = 2 * FP64_DFMA_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
 MAX_LE, MIN_GE = 0, 1
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pivot_pipe_kernel_fp64_traffic.txt")
@@ -470,7 +471,8 @@ def main():
         flops = by / 16 * 2  # one FMA (2 flops) per 16 bytes of FP64 read + write
         hbm = {"bound": "hbm", "achieved": round(by / sec / 1e9, 1), "peak": hbm_peak,
                "unit": "GB/s", "frac": round(by / sec / 1e9 / hbm_peak, 4),
-               "peak_kind": peak_kind}
+               "peak_kind": peak_kind,
+               "frac_of_nominal": round(by / sec / 1e9 / HBM_NOMINAL_GBS, 4)}
         alu = {"bound": "alu", "achieved": round(flops / sec / 1e12, 4),
                "peak": round(ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                "frac": round(flops / sec / 1e12 / ALU_PEAK_TFLOPS, 4),
@@ -511,9 +513,12 @@ def main():
         while t < 10.0 and reps < 1000:
             dp, dt = cpu_oracle_run(lps, cores)
             p, t, reps = p + dp, t + dt, reps + 1
+        p1, t1 = cpu_oracle_run(lps, 1)
         line["cpu_baseline"] = {"value": p / t, "unit": "pivots/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": "the whole workload (4 LPs) %d times, %.1f s" % (reps, t)}
+                                "sample": "the whole workload (4 LPs) %d times, %.1f s" % (reps, t),
+                                "single_thread": {"value": p1 / t1, "unit": "pivots/s",
+                                                  "sample": "the whole workload once, %.1f s" % t1}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
