@@ -233,6 +233,12 @@ def run_lp8192(args, capi, torch):
                     "pivot_kernel_launches": launches,
                     "pivots_per_s": round(it / wall, 1),
                     "tableau_gbs_kernel": round(it * tableau_bytes(8192, 8192, w) / kms / 1e6, 1),
+                    # two pivots per pass over the tableau at this size: the
+                    # tableau traffic is half the algorithmic bytes, and FP64 is
+                    # bound by the FMA rate (one FMA per element and pivot)
+                    "tflops_kernel": round(it * 2 * 8193 * 16385 / kms / 1e9, 4),
+                    "fp64_alu_frac": (round(it * 2 * 8193 * 16385 / kms / 1e9 / ALU_PEAK_TFLOPS, 4)
+                                      if prec == capi.LP_FP64 else None),
                     "obj": obj, "obj_rel_err_vs_fp64": abs(obj - ref) / abs(ref)})
     print(json.dumps({"workload": "dense LP 8192x8192, FP64 vs FP32 tableau + FP64 reinversion",
                       "results": out, "hbm_peak_gbs": peaks()[0]}), flush=True)

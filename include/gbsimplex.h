@@ -114,13 +114,16 @@ typedef struct {
                                 0 = selection, then update (one launch-wide
                                     grid barrier per pivot);
                                 1 = auto (default): 2 when the tableau fits the
-                                    L2 cache, else 3, else 0 when the second
-                                    buffer cannot be allocated;
+                                    L2 cache (up to 96 MB), 4 from 384 MB, 3
+                                    between; 0 when the second buffer cannot
+                                    be allocated;
                                 2 = pipelined in place: the next pivot's
                                     selection overlaps this pivot's update, no
                                     grid barrier;
                                 3 = pipelined, double-buffered tableau (twice
-                                    the memory), a grid barrier per pivot.
+                                    the memory), a grid barrier per pivot;
+                                4 = as 3, two pivots per pass over the tableau
+                                    (half the tableau traffic per pivot).
                                 Same pivots and bits in every mode.              */
 } lp_options;
 

@@ -24,6 +24,11 @@ using namespace gbs;
 // pivots when updated in place; the pipelined kernel runs in place below it
 // and double-buffered above it.
 constexpr size_t kL2FitBytes = 96ull << 20;
+// From this size on, a pass over the tableau is long enough to hide the
+// selection of two pivots, and the kernel applies two pivots per pass (half
+// the tableau traffic per pivot; measured at 8192^2 FP64: 249 against 370 us
+// per pivot, at 4096 x 512 (152 MB): 61 against 58).
+constexpr size_t kBlockBytes = 384ull << 20;
 
 struct lp_handle {
     lp_options opt;
@@ -51,7 +56,7 @@ struct lp_handle {
     size_t cap_basis = 0;
     void *dscratch = nullptr;
     size_t cap_scratch = 0;                     // bytes
-    Cand *dpart = nullptr;                      // 4 * max_ctas (records, values)
+    Cand *dpart = nullptr;                      // 20 * max_ctas (records, values)
     int max_ctas = 0;
     unsigned *dbar = nullptr;                   // kBarWords: barrier, counters, err
     int *dtrace = nullptr;
@@ -268,22 +273,25 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     // the pipelined kernels where they can take the LP: the primal rule in
     // place for tableaus that fit L2 and double-buffered above, the dual rule
     // double-buffered (the rule runs for its sense, and in FP32 mode for both)
-    if (h->opt.pipeline < 0 || h->opt.pipeline > 3) {
+    if (h->opt.pipeline < 0 || h->opt.pipeline > 4) {
         set_err(h, "lp_load: unknown pipeline mode %d", h->opt.pipeline);
         return LP_ERR_INVALID_ARG;
     }
     const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
     const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32;
     int pmode = primal ? h->opt.pipeline : 0;
-    if (pmode == 1) pmode = (size_t)M * P * esz <= kL2FitBytes ? 2 : 3;
+    if (pmode == 1) {
+        const size_t tb = (size_t)M * P * esz;
+        pmode = tb <= kL2FitBytes ? 2 : (tb < kBlockBytes ? 3 : 4);
+    }
     const bool dwant = dualr && h->opt.pipeline != 0;
     bool have_t2 = false;
-    if (pmode == 3 || dwant) {
+    if (pmode >= 3 || dwant) {
         have_t2 = grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz) == cudaSuccess;
         if (!have_t2) cudaGetLastError();
     }
-    if (pmode == 3 && !have_t2) {
-        if (h->opt.pipeline == 3) {
+    if (pmode >= 3 && !have_t2) {
+        if (h->opt.pipeline >= 3) {
             set_err(h, "lp_load: no device memory for the second tableau buffer (pipeline 3)");
             return LP_ERR_OOM;
         }
@@ -292,9 +300,11 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const bool dpipe = dwant && have_t2;
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
-            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas, 0);
+            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas,
+                                              pmode == 4 ? 2 : 0);
             if (ps.pipe) {
                 if (pmode == 3) ps.pipe = 2;  // double-buffered
+                if (pmode == 4) ps.pipe = 3;  // double-buffered, two pivots per pass
                 return ps;
             }
         }
@@ -327,7 +337,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
         h->max_ctas = 0;
-        CUDA_TRY(h, cudaMalloc(&h->dpart, 4 * (size_t)ctas_max * sizeof(Cand)));
+        CUDA_TRY(h, cudaMalloc(&h->dpart, 20 * (size_t)ctas_max * sizeof(Cand)));
         h->max_ctas = ctas_max;
     }
     if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
@@ -403,7 +413,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.scratch = h->dscratch;
     d.scratch_stride = sh.scratch_stride;
     d.part_sel = h->dpart;
-    d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 2 * (size_t)h->max_ctas);
+    d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 4 * (size_t)h->max_ctas);
     d.T2 = have_t2 ? h->dT2 : nullptr;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);

@@ -52,10 +52,10 @@ struct LpDesc {
     int last_p, last_q;
     // batched launches: CTAs per LP and their column strip width
     int group, strip;
-    // pipelined primal kernel: the second tableau buffer (double-buffered
-    // mode; nullptr in place) and the values that come with the pricing
-    // records (2 x G pairs, by parity: the new pivot-row entries at the
-    // record's column and at the rhs)
+    // pipelined kernels: the second tableau buffer (double-buffered mode;
+    // nullptr in place) and the values that come with the records (by
+    // parity: the new pivot-row entries at the record's column and at the
+    // rhs; 2 x G pairs, or 4 x G x 8 values for two pivots per pass)
     void *T2;
     unsigned long long *part_vals;
 };
@@ -67,7 +67,7 @@ struct PivotShape {
     int strip = 0;                 // columns per strip (multiple of 32 bytes of elements)
     int use_smem = 0;              // selection scratch in shared memory (else global)
     int dual = 0;                  // dual simplex kernel (else primal)
-    int pipe = 0;                  // pipelined primal kernel: 1 in place, 2 double-buffered
+    int pipe = 0;                  // pipelined kernel: 1 in place, 2 double-buffered, 3 two pivots per pass
     size_t smem_bytes = 0;         // dynamic shared memory per CTA
     long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };
@@ -107,7 +107,8 @@ int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, 
 // The returned shape has pipe == 0 when the kernel cannot take the LP (a grid
 // larger than one CTA per SM); its scratch is in shared memory when it fits,
 // else a global slice of scratch_stride bytes per CTA.
-// dual: the dual simplex kernel (double-buffered only).
+// dual: 1 the dual simplex kernel, 2 the two-pivot primal kernel (both
+// double-buffered only), 0 the primal kernel.
 PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas,
                              int dual);
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,

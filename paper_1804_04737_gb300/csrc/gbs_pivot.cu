@@ -1219,6 +1219,585 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two pivots per pass (multi-pivot blocking), primal, double-buffered.
+//
+// A pass reads tableau T0 from bufs[cur] once and writes T2 into bufs[cur^1],
+// applying the pass's pivots (p1, q1) and (p2, q2) to every element in the
+// order the one-pivot method applies them:
+//   t = i == p1 ? prow1[j] : fma(-col1[i], prow1[j], T0[i][j]);
+//   T2[i][j] = i == p2 ? prow2[j] : fma(-col2[i], prow2[j], t),
+// so the result is bit for bit that of two one-pivot passes, with half of
+// their tableau traffic.  prow1 = T0[p1][.] / col1[p1] and prow2 = T1[p2][.] /
+// col2[p2] are formed per strip at the start of the pass; col1 and col2 (the
+// columns q1 of T0 and q2 of T1) come from the previous pass's selection.
+//
+// While the update warps stream the pass, the selection warps select the
+// next two pivots from T0 and the pass's pivots (Steps 2-3 twice):
+//   a: pricing records (each CTA's best column of the objective row of T2,
+//      with the pass's pivot-row values there and at the rhs) -> q_a; the
+//      whole column q_a and rhs of T2 in every CTA -> ratio test -> p_a;
+//   b: row p_a of T2 on each CTA's strip divided by the pivot (the pivot row
+//      of pivot a) and the objective row after pivot a -> pricing records ->
+//      q_b; column q_b and rhs after pivot a in every CTA -> p_b.
+// A pass holds one pivot when the next pivot ends the solve (optimal,
+// unbounded, iteration limit); the first pass of a launch holds the first
+// pivot alone.  A grid barrier ends each pass.
+
+constexpr int kBlk = 2;       // pivots per pass
+constexpr int kBlkVals = 8;   // values per record: 3 at the record's column, 3 at the rhs, 2 unused
+
+// x after the pass's pivots 0..np-1, for row i (pv: their pivot-row values at
+// the column of x).
+template <typename T>
+__device__ __forceinline__ T blk_apply(T x, int i, int np, const int *pp, const T *const *pc,
+                                       const T *pv) {
+#pragma unroll
+    for (int k = 0; k < kBlk; ++k)
+        if (k < np) x = (i == pp[k]) ? pv[k] : tfma(-pc[k][i], pv[k], x);
+    return x;
+}
+
+template <typename T, int SW>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    pivot_block_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    typedef typename Vec<T>::type V;
+    constexpr int VW = Vec<T>::W;
+    constexpr int kSelThreads = 32 * SW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Cand rbuf[2][32];
+    __shared__ unsigned long long ubuf[32];
+    __shared__ Cand wpart[32];
+    __shared__ Cand selc[SW];
+    __shared__ unsigned long long selq[SW];
+    __shared__ unsigned sela[SW], selb[SW];
+    __shared__ int s_flag, s_status, s_sok, s_np, s_pend;
+    __shared__ volatile int s_zready;  // passes whose objective-row strip is in sz
+    __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
+
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+    const int NU = B - kSelThreads;
+    const int lane = tid & 31;
+    const bool selw = tid >= NU;
+    const int stid = tid - NU;
+    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
+    int cur = 0;
+    const long long P = d->P;
+    const int m = d->m, M = d->M, N = d->N;
+    int *__restrict__ basis = d->basis;
+    const int bland_after = d->bland_after;
+    const unsigned long long lim_p = okey((T)d->eps_p);
+    const unsigned long long lim_d = okey((T)(-d->eps_d));
+    const unsigned long long zero_k = okey((T)0);
+    long long iters = d->iters;
+    const long long iter_limit =
+        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
+    int deg = d->deg;
+    int status = ST_RUNNING;
+    unsigned *pcnt = d->bar + 64;
+
+    // strip and thread map of the update threads
+    const int c0 = g * W;
+    const int c1 = (int)min((long long)c0 + W, P);
+    const int vpr = (c1 - c0) / VW;
+    const int rpp = NU / vpr;
+    const int lr = tid / vpr, lv = tid - lr * vpr;
+    const bool active = !selw && lr < rpp;
+    const int col0 = c0 + lv * VW;
+    const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
+    const int rowner = (N - 1) / W;
+    // shared memory: the pass's pivot rows on the strip, the objective row of
+    // T2 on the strip, pivot a's row on the strip; scratch (shared or this
+    // CTA's global slice): four pivot columns (this pass's two, the next
+    // pass's two), ratio numerators, screening keys
+    const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
+    T *sprow[kBlk] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + wbytes)};
+    T *sz = reinterpret_cast<T *>(smem_raw + 2 * wbytes);
+    T *spa = reinterpret_cast<T *>(smem_raw + 3 * wbytes);
+    unsigned char *sc = d->scratch_stride > 0
+                            ? reinterpret_cast<unsigned char *>(d->scratch) +
+                                  (size_t)g * (size_t)d->scratch_stride
+                            : smem_raw + 4 * wbytes;
+    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
+    T *scol[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scol[k] = reinterpret_cast<T *>(sc + k * cbytes);
+    T *snum = reinterpret_cast<T *>(sc + 4 * cbytes);
+    unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 5 * cbytes);
+
+    // ---- selection of the first pivot from the current tableau (all threads) ----
+    int p = -1, q = -1;
+    {
+        const T *Tab = bufs[0];
+        const int bland = deg >= bland_after;
+        Cand c = cand_empty();
+        const T *z = Tab + (long long)m * P;
+        for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
+            const unsigned long long zk = okey(lds(z + j));
+            if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
+        }
+        c = block_min_c(c, rbuf[0]);
+        if (tid == 0) d->part_sel[g] = c;
+        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
+        if (status == ST_RUNNING) {
+            const Cand sel = load_partials_min(d->part_sel, G, rbuf[1]);
+            if (sel.idx < 0) status = ST_OPTIMAL;
+            else if (iters >= iter_limit) status = ST_ITER_LIMIT;
+            else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: a partial from outside the row
+            else q = sel.idx;
+        }
+        if (status == ST_RUNNING) {
+            unsigned long long lmin = ~0ull;
+            for (int i = tid; i < M; i += B) {
+                const T a = lds(Tab + (long long)i * P + q);
+                scol[0][i] = a;
+                if (i < m) {
+                    const T num = pos_part(lds(Tab + (long long)i * P + (N - 1)));
+                    const unsigned long long rk = okey(a) > lim_p ? screen_key(num, a) : ~0ull;
+                    snum[i] = num;
+                    srk[i] = rk;
+                    lmin = rk < lmin ? rk : lmin;
+                }
+            }
+            const unsigned long long rstar = block_min_u(lmin, ubuf);
+            if (rstar == ~0ull) {
+                status = ST_UNBOUNDED;
+            } else {
+                const unsigned long long thr = screen_thr(rstar, (T)0);
+                Cand rc = cand_empty();
+                for (int i = tid; i < m; i += B)
+                    if (srk[i] <= thr)
+                        cand_take(rc, okey(snum[i] / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
+                rc = block_min_c(rc, rbuf[0]);
+                p = rc.idx;
+                deg = (rc.vk == zero_k) ? deg + 1 : 0;
+            }
+        }
+    }
+
+    // the pass's pivots; pend: the status to report after this pass, when the
+    // selection during the previous pass already ended the solve
+    int np = 1, pend = ST_RUNNING;
+    int pp[kBlk] = {p, -1}, qq[kBlk] = {q, -1};
+    int cb = 0;          // the pass's pivot columns are scol[cb], scol[cb + 1] (mod 4)
+    unsigned lk = 0;     // passes made in this launch
+    if (tid == 0) s_zready = 0;
+    __syncthreads();
+    while (status == ST_RUNNING) {
+        const T *A = bufs[cur];
+        T *Bn = bufs[cur ^ 1];
+        const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
+        T *nc[kBlk] = {scol[(cb + 2) & 3], scol[(cb + 3) & 3]};
+        const int par = lk & 1;
+        Cand *recA = d->part_sel + (2 * par) * G, *recB = d->part_sel + (2 * par + 1) * G;
+        unsigned long long *valA = d->part_vals + (size_t)(2 * par) * G * kBlkVals;
+        unsigned long long *valB = d->part_vals + (size_t)(2 * par + 1) * G * kBlkVals;
+        const unsigned tA = (unsigned)G * (2u * lk + 1u), tB = (unsigned)G * (2u * lk + 2u);
+        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
+            for (int k = 0; k < np; ++k) {
+                if (iters + k < d->trace_cap) {
+                    d->trace[2 * (iters + k)] = pp[k];
+                    d->trace[2 * (iters + k) + 1] = qq[k];
+                }
+                basis[pp[k]] = qq[k];
+            }
+            d->last_p = pp[np - 1];
+            d->last_q = qq[np - 1];
+        }
+        const int nbland = deg >= bland_after;  // rule of pivot a's selection
+        const bool select = pend == ST_RUNNING;
+        if (!selw) {
+            // Step 4 for the pass's pivots on this CTA's strip
+            for (int j = c0 + tid; j < c1; j += NU) {
+                const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
+                sprow[0][j - c0] = r;
+                if (np > 1) {
+                    const T t = (pp[1] == pp[0]) ? r
+                                                 : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + j));
+                    sprow[1][j - c0] = t / pc[1][pp[1]];
+                }
+            }
+            named_sync(1, NU);
+            // the strip of the objective row of T2, and the CTA's pricing record a
+            Cand c = cand_empty();
+            if (tid < vpr) {
+                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
+#pragma unroll
+                for (int k = 0; k < kBlk; ++k)
+                    if (k < np) vfma(zt, pc[k][m], *reinterpret_cast<const V *>(sprow[k] + tid * VW));
+                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
+                *reinterpret_cast<V *>(sz + tid * VW) = zt;
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    const int j = c0 + tid * VW + k;
+                    const unsigned long long zk = okey(getc(zt, k));
+                    if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
+                }
+            }
+            c = warp_min(c);
+            if (lane == 0) wpart[tid >> 5] = c;
+            named_sync(1, NU);
+            if (tid < 32) {
+                const Cand e = tid < NU / 32 ? wpart[tid] : cand_empty();
+                const Cand r = warp_min(e);
+                if (tid == 0) {
+                    if (select) {
+                        recA[g] = r;
+                        unsigned long long *v = valA + (size_t)g * kBlkVals;
+                        for (int k = 0; k < np; ++k) {
+                            v[k] = r.idx >= 0 ? tbits(sprow[k][r.idx - c0]) : 0ull;
+                            v[3 + k] = rv >= 0 ? tbits(sprow[k][N - 1 - c0]) : 0ull;
+                        }
+                        red_add_release(pcnt, 1u);
+                    }
+                    __threadfence_block();
+                    s_zready = (int)(lk + 1);  // sz, sprow of this pass ready for the selection
+                }
+            }
+            // Step 5 for the pass's pivots on the constraint rows of the strip
+            if (active && np == 2) {
+                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
+                const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
+                const int p0 = pp[0], p1 = pp[1];
+                const T *__restrict__ c0p = pc[0];
+                const T *__restrict__ c1p = pc[1];
+                const T *abase = A + col0;
+                T *bbase = Bn + col0;
+                int i = lr;
+                for (; i + 3 * rpp < m; i += 4 * rpp) {
+                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                    V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                    V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                    t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
+                    t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
+                    t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
+                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p1, c1p[i1], pr1);
+                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p1, c1p[i2], pr1);
+                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p1, c1p[i3], pr1);
+                }
+                for (; i < m; i += rpp) {
+                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
+                }
+            } else if (active) {
+                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
+                const int p0 = pp[0];
+                const T *__restrict__ c0p = pc[0];
+                const T *abase = A + col0;
+                T *bbase = Bn + col0;
+                int i = lr;
+                for (; i + 3 * rpp < m; i += 4 * rpp) {
+                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
+                }
+                for (; i < m; i += rpp) {
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                }
+            }
+        } else {
+            // selection of the next pass's pivots a and b
+            int st = ST_RUNNING, nnp = 0, npend = ST_RUNNING;
+            int pa = -1, qa = -1, pb = -1, qb = -1, rza = 0, rzb = 0;
+            // the basic variable of row i after the pass's pivots
+            auto bkey = [&](int i) -> int {
+                if (np > 1 && i == pp[1]) return qq[1];
+                if (i == pp[0]) return qq[0];
+                return __ldcg(basis + i);
+            };
+            const T *colA = nc[0];
+            if (!select) {
+                st = pend;  // the previous pass's selection already ended the solve
+            } else {
+                // ---- pivot a (Step 2): the pricing records of this pass ----
+                if (stid == 0) s_sok = (int)wait_ctr(pcnt, tA, d->err, spin_limit);
+                named_sync(2, kSelThreads);
+                unsigned long long ka = 0ull;
+                if (!s_sok) {
+                    st = ST_TIMEOUT;
+                } else {
+                    Cand e = cand_empty();
+                    for (int k = stid; k < G; k += kSelThreads) {
+                        const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recA) + k));
+                        if (cand_less(r, e)) {
+                            e = r;
+                            ka = (unsigned long long)k;
+                        }
+                    }
+                    const Cand sel = sel_min<SW>(e, ka, selc, selq, &ka);
+                    if (sel.idx < 0) st = ST_OPTIMAL;
+                    else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
+                    else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never: a record from outside the row
+                    else qa = sel.idx;
+                    if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+                }
+                if (st == ST_RUNNING) {
+                    // the pass's pivot-row values at q_a and at the rhs
+                    T pvq[kBlk], pvr[kBlk];
+#pragma unroll
+                    for (int k = 0; k < kBlk; ++k) {
+                        pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
+                        pvr[k] = tfrom<T>(__ldcg(valA + (size_t)rowner * kBlkVals + 3 + k));
+                    }
+                    // column q_a and rhs of T2, every row (Step 3)
+                    T *ncol = nc[0];
+                    unsigned long long lmin = ~0ull;
+                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                        T av[kSelRows], hv[kSelRows];
+#pragma unroll
+                        for (int u = 0; u < kSelRows; ++u) {
+                            const int i = i0 + u * kSelThreads;
+                            av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
+                            hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < kSelRows; ++u) {
+                            const int i = i0 + u * kSelThreads;
+                            if (i >= M) break;
+                            const T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
+                            ncol[i] = a;
+                            if (i < m) {
+                                const T num = pos_part(blk_apply<T>(hv[u], i, np, pp, pc, pvr));
+                                const unsigned long long rk =
+                                    okey(a) > lim_p ? screen_key(num, a) : ~0ull;
+                                snum[i] = num;
+                                srk[i] = rk;
+                                lmin = rk < lmin ? rk : lmin;
+                            }
+                        }
+                    }
+                    const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
+                    if (rstar == ~0ull) {
+                        st = ST_UNBOUNDED;
+                    } else {
+                        const unsigned long long thr = screen_thr(rstar, (T)0);
+                        unsigned first = 0xffffffffu, cnt = 0;
+                        for (int i = stid; i < m; i += kSelThreads)
+                            if (srk[i] <= thr) {
+                                first = (unsigned)i < first ? (unsigned)i : first;
+                                ++cnt;
+                            }
+                        unsigned gfirst, gcnt;
+                        sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
+                        if (gcnt == 1) {
+                            pa = (int)gfirst;
+                            rza = srk[pa] == zero_k;
+                        } else {
+                            Cand rc = cand_empty();
+                            for (int i = stid; i < m; i += kSelThreads)
+                                if (srk[i] <= thr) {
+                                    const T nm = snum[i];
+                                    const unsigned long long vk =
+                                        tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
+                                    cand_take(rc, vk, nbland ? bkey(i) : i, i);
+                                }
+                            rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
+                            pa = rc.idx;
+                            rza = rc.vk == zero_k;
+                        }
+                    }
+                }
+                if (st == ST_RUNNING) {
+                    // ---- pivot b: pivot a's row on this strip, the objective row
+                    // after pivot a, the CTA's pricing record b ----
+                    const int nblandb = (rza ? deg + 1 : 0) >= bland_after;
+                    if (stid == 0) {  // this pass's sprow and sz (written by the update warps)
+                        const long long t0 = clock64();
+                        int ok = 1;
+                        while (s_zready < (int)(lk + 1)) {
+                            if (clock64() - t0 > spin_limit || *(volatile int *)d->err) {
+                                atomicExch(d->err, 1);
+                                ok = 0;
+                                break;
+                            }
+                        }
+                        s_sok = ok;
+                    }
+                    named_sync(2, kSelThreads);
+                    __threadfence_block();
+                    if (!s_sok) {
+                        st = ST_TIMEOUT;
+                    } else {
+                        const T piva = colA[pa];
+                        Cand e = cand_empty();
+                        for (int j = c0 + stid; j < c1; j += kSelThreads) {
+                            T r = lds(A + (long long)pa * P + j);
+#pragma unroll
+                            for (int k = 0; k < kBlk; ++k)
+                                if (k < np)
+                                    r = (pa == pp[k]) ? sprow[k][j - c0]
+                                                      : tfma(-pc[k][pa], sprow[k][j - c0], r);
+                            const T pra = r / piva;
+                            spa[j - c0] = pra;
+                            const unsigned long long zk = okey(tfma(-colA[m], pra, sz[j - c0]));
+                            if (j < N - 1 && zk < lim_d) cand_take(e, nblandb ? zero_k : zk, j, j);
+                        }
+                        e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
+                        if (stid == 0) {
+                            recB[g] = e;
+                            unsigned long long *v = valB + (size_t)g * kBlkVals;
+                            for (int k = 0; k <= np; ++k) {
+                                const T *row = k < np ? sprow[k] : spa;
+                                v[k] = e.idx >= 0 ? tbits(row[e.idx - c0]) : 0ull;
+                                v[3 + k] = rv >= 0 ? tbits(row[N - 1 - c0]) : 0ull;
+                            }
+                            red_add_release(pcnt, 1u);
+                        }
+                        // ---- pivot b (Step 2): the pricing records ----
+                        if (stid == 0) s_sok = (int)wait_ctr(pcnt, tB, d->err, spin_limit);
+                        named_sync(2, kSelThreads);
+                        unsigned long long kb = 0ull;
+                        if (!s_sok) {
+                            st = ST_TIMEOUT;
+                        } else {
+                            Cand f = cand_empty();
+                            for (int k = stid; k < G; k += kSelThreads) {
+                                const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recB) + k));
+                                if (cand_less(r, f)) {
+                                    f = r;
+                                    kb = (unsigned long long)k;
+                                }
+                            }
+                            const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
+                            nnp = 1;
+                            if (sel.idx < 0) npend = ST_OPTIMAL;
+                            else if (iters + np + 1 >= iter_limit) npend = ST_ITER_LIMIT;
+                            else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
+                            else qb = sel.idx;
+                            if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+                        }
+                        if (st == ST_RUNNING && qb >= 0) {
+                            T pvq[kBlk + 1], pvr[kBlk + 1];
+#pragma unroll
+                            for (int k = 0; k <= kBlk; ++k) {
+                                pvq[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
+                                pvr[k] = tfrom<T>(__ldcg(valB + (size_t)rowner * kBlkVals + 3 + k));
+                            }
+                            // column q_b and rhs after pivot a, every row (Step 3)
+                            T *ncol = nc[1];
+                            unsigned long long lmin = ~0ull;
+                            for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                                T av[kSelRows], hv[kSelRows];
+#pragma unroll
+                                for (int u = 0; u < kSelRows; ++u) {
+                                    const int i = i0 + u * kSelThreads;
+                                    av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
+                                    hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
+                                }
+#pragma unroll
+                                for (int u = 0; u < kSelRows; ++u) {
+                                    const int i = i0 + u * kSelThreads;
+                                    if (i >= M) break;
+                                    const T ca = colA[i];
+                                    T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
+                                    a = (i == pa) ? pvq[np] : tfma(-ca, pvq[np], a);
+                                    ncol[i] = a;
+                                    if (i < m) {
+                                        T h = blk_apply<T>(hv[u], i, np, pp, pc, pvr);
+                                        h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], h);
+                                        const T num = pos_part(h);
+                                        const unsigned long long rk =
+                                            okey(a) > lim_p ? screen_key(num, a) : ~0ull;
+                                        snum[i] = num;
+                                        srk[i] = rk;
+                                        lmin = rk < lmin ? rk : lmin;
+                                    }
+                                }
+                            }
+                            const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
+                            if (rstar == ~0ull) {
+                                npend = ST_UNBOUNDED;
+                            } else {
+                                const unsigned long long thr = screen_thr(rstar, (T)0);
+                                unsigned first = 0xffffffffu, cnt = 0;
+                                for (int i = stid; i < m; i += kSelThreads)
+                                    if (srk[i] <= thr) {
+                                        first = (unsigned)i < first ? (unsigned)i : first;
+                                        ++cnt;
+                                    }
+                                unsigned gfirst, gcnt;
+                                sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
+                                if (gcnt == 1) {
+                                    pb = (int)gfirst;
+                                    rzb = srk[pb] == zero_k;
+                                } else {
+                                    Cand rc = cand_empty();
+                                    for (int i = stid; i < m; i += kSelThreads)
+                                        if (srk[i] <= thr) {
+                                            const T nm = snum[i];
+                                            const unsigned long long vk =
+                                                tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
+                                            const int key = nblandb ? (i == pa ? qa : bkey(i)) : i;
+                                            cand_take(rc, vk, key, i);
+                                        }
+                                    rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
+                                    pb = rc.idx;
+                                    rzb = rc.vk == zero_k;
+                                }
+                                nnp = 2;
+                            }
+                        }
+                    }
+                }
+            }
+            named_sync(2, kSelThreads);
+            if (stid == 0) {
+                s_status = st;
+                s_np = nnp;
+                s_pend = npend;
+                s_p[0] = pa;
+                s_q[0] = qa;
+                s_p[1] = pb;
+                s_q[1] = qb;
+                s_rz[0] = rza;
+                s_rz[1] = rzb;
+            }
+        }
+        // the CTA's pass and its selection of the next pass are done
+        __syncthreads();
+        iters += np;
+        ++lk;
+        status = s_status;
+        if (status == ST_RUNNING) {
+            np = s_np;
+            pend = s_pend;
+            for (int k = 0; k < kBlk; ++k) {
+                pp[k] = s_p[k];
+                qq[k] = s_q[k];
+            }
+            deg = s_rz[0] ? deg + 1 : 0;
+            if (np > 1) deg = s_rz[1] ? deg + 1 : 0;
+            cb = (cb + 2) & 3;
+        }
+        cur ^= 1;
+        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+    }
+
+    if (g == 0 && tid == 0) {
+        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
+        d->iters = iters;
+        d->iter_limit = iter_limit;
+        d->deg = deg;
+        d->T = bufs[cur];  // hand over the buffer holding the last tableau
+        d->T2 = bufs[cur ^ 1];
+    }
+}
+
 constexpr int kBatchThreads = 512;  // register room for both pivot rules in one kernel
 
 // ---------------------------------------------------------------------------
@@ -1711,7 +2290,7 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
             fn = sh.use_smem ? (const void *)pivot_kernel<float, true, false>
                              : (const void *)pivot_kernel<float, false, false>;
     }
-    if (sh.smem_bytes > 48 * 1024) {
+    if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sh.smem_bytes);
         if (e != cudaSuccess) return e;
@@ -1726,10 +2305,22 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
     int W = sh.strip;
     int dbm = sh.pipe == 2 ? 1 : 0;
     void *args[] = {&d_desc, &W, &spin_limit, &budget, &dbm};
+    if (sh.pipe == 3) {  // two pivots per pass
+        void *bargs[] = {&d_desc, &W, &spin_limit, &budget};
+        const void *fn = prec == PREC_FP64 ? (const void *)pivot_block_kernel<double, 4>
+                                           : (const void *)pivot_block_kernel<float, 4>;
+        if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sh.smem_bytes);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), bargs,
+                                           sh.smem_bytes, s);
+    }
     if (sh.dual) {
         const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_dual_kernel<double, 4>
                                            : (const void *)pivot_pipe_dual_kernel<float, 4>;
-        if (sh.smem_bytes > 48 * 1024) {
+        if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sh.smem_bytes);
             if (e != cudaSuccess) return e;
@@ -1742,7 +2333,7 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                          : (const void *)pivot_pipe_kernel<double, 4>)
                          : (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<float, 2>
                                          : (const void *)pivot_pipe_kernel<float, 4>);
-    if (sh.smem_bytes > 48 * 1024) {
+    if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sh.smem_bytes);
         if (e != cudaSuccess) return e;
@@ -1773,18 +2364,21 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     // keys (primal), or the strip of the new objective row (dual)
     const size_t cbytes = ((size_t)M * esz + 15) & ~(size_t)15;
     const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
-    const size_t scratch = dual ? sprow + 2 * cbytes
-                                : 3 * cbytes + (size_t)M * sizeof(unsigned long long);
-    if (sprow + scratch <= kMaxDynSmem) {
+    // (dual == 2: the two-pivot kernel, four pivot rows and columns)
+    const size_t scratch = dual == 1   ? sprow + 2 * cbytes
+                           : dual == 2 ? 5 * cbytes + (size_t)M * sizeof(unsigned long long)
+                                       : 3 * cbytes + (size_t)M * sizeof(unsigned long long);
+    const size_t fixed = dual == 2 ? 4 * sprow : sprow;
+    if (fixed + scratch <= kMaxDynSmem) {
         sh.use_smem = 1;
-        sh.smem_bytes = sprow + scratch;
+        sh.smem_bytes = fixed + scratch;
         sh.scratch_stride = 0;
     } else {
         sh.use_smem = 0;
-        sh.smem_bytes = sprow;
+        sh.smem_bytes = fixed;
         sh.scratch_stride = (long long)((scratch + 255) & ~(size_t)255);
     }
-    sh.dual = dual;
+    sh.dual = dual == 1;
     // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
     // launch), the strip one pass of the update threads
     sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw;
@@ -1796,7 +2390,7 @@ cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing
                           long long idle_limit, cudaStream_t s) {
     void *args[] = {&slots, &nslots, &ctl, &ring_dev, &spin_limit, &idle_limit};
     const void *fn = (const void *)server_kernel;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {  // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
@@ -1806,8 +2400,7 @@ cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing
 
 int max_coresident_server_ctas(int threads, size_t smem, int sms) {
     const void *fn = (const void *)server_kernel;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
         return 0;
@@ -1823,7 +2416,7 @@ cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems,
         fn = use_smem ? (const void *)batch_kernel<double, true> : (const void *)batch_kernel<double, false>;
     else
         fn = use_smem ? (const void *)batch_kernel<float, true> : (const void *)batch_kernel<float, false>;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {  // static shared memory counts against the 48 KB default too
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
@@ -1837,8 +2430,7 @@ int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, 
         fn = use_smem ? (const void *)batch_kernel<double, true> : (const void *)batch_kernel<double, false>;
     else
         fn = use_smem ? (const void *)batch_kernel<float, true> : (const void *)batch_kernel<float, false>;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
         return 0;

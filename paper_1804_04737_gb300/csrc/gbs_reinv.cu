@@ -303,7 +303,7 @@ cudaError_t launch_reinv_solve(int prec, const double *A, const double *b, const
         G = (ncols + strip - 1) / strip;
         const size_t smem = sizeof(double) * ((size_t)ns + strip) + 4 * (((size_t)ns + 31) / 32);
         const void *fn = (const void *)gj_kernel;
-        if (smem > 48 * 1024) {
+        if (smem > 0) {  // static shared memory counts against the 48 KB default too
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }

@@ -92,18 +92,19 @@ def test_launch_shapes_bitwise(ctas, threads):
     assert_same(Run(Ad, bd, cd, MIN_GE, ctas=ctas, threads=threads), od)
 
 
-@pytest.mark.parametrize("pipeline", [0, 2, 3])
+@pytest.mark.parametrize("pipeline", [0, 2, 3, 4])
 @pytest.mark.parametrize("m,n,ctas,threads", [(1, 1, 0, 0), (9, 1, 0, 0), (33, 17, 2, 128),
                                               (257, 100, 0, 0), (300, 1000, 5, 256),
                                               (1000, 300, 0, 1024), (200, 311, 40, 64)])
 def test_primal_kernels_bitwise(m, n, ctas, threads, pipeline):
     """Every primal kernel gives the oracle's pivots and bits: selection then
-    update (0), pipelined in place (2), pipelined double-buffered (3)."""
+    update (0), pipelined in place (2), pipelined double-buffered (3), two
+    pivots per pass (4)."""
     A, b, c = lpgen.dense_lp(m, n, seed=7 * m + n)
     assert_same(Run(A, b, c, ctas=ctas, threads=threads, pipeline=pipeline), _oracle(A, b, c))
 
 
-@pytest.mark.parametrize("pipeline", [0, 2, 3])
+@pytest.mark.parametrize("pipeline", [0, 2, 3, 4])
 @pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
 def test_pivot_by_pivot_tableau(sense, pipeline):
     """One pivot per call: the tableau equals the oracle's after every pivot."""
@@ -132,10 +133,13 @@ def test_pivot_by_pivot_tableau(sense, pipeline):
         capi.lp_destroy(h)
 
 
-def test_resume_in_chunks():
+@pytest.mark.parametrize("chunk,pipeline", [(7, 1), (1, 4), (2, 4), (3, 4), (7, 4)])
+def test_resume_in_chunks(chunk, pipeline):
+    """Pivot limits that end a launch inside a two-pivot pass or between passes."""
     A, b, c = lpgen.dense_lp(150, 180, seed=13)
     o = _oracle(A, b, c)
-    h = capi.lp_create(capi.lp_options_default(max_iters=7, trace_cap=4096))
+    h = capi.lp_create(capi.lp_options_default(max_iters=chunk, trace_cap=4096,
+                                               pipeline=pipeline))
     try:
         capi.lp_load(h, A, b, c)
         calls = 0
@@ -145,7 +149,7 @@ def test_resume_in_chunks():
             obj, st, it = capi.lp_result(h)
             if st != capi.LP_ITER_LIMIT:
                 break
-            assert it == 7 * calls
+            assert it == chunk * calls
         tp, tq = capi.lp_get_trace(h, 4096)
         assert st == capi.LP_OPTIMAL and it == o.iters and obj == o.obj
         assert np.array_equal(tp, o.trace_p) and np.array_equal(tq, o.trace_q)
@@ -170,15 +174,16 @@ def test_klee_minty_on_gpu():
         assert_same(g, _oracle(A, b, c))
 
 
+@pytest.mark.parametrize("pipeline", [1, 4])
 @pytest.mark.parametrize("name", ["chvatal_cycling.txt", "beale_cycling.txt"])
-def test_cycling_examples_on_gpu(name):
+def test_cycling_examples_on_gpu(name, pipeline):
     g0 = read_lp(name)
     A, b, c = g0["A"], g0["b"], g0["c"]
-    g = Run(A, b, c, bland_after=10 ** 9, max_iters=60, cap=60)
+    g = Run(A, b, c, bland_after=10 ** 9, max_iters=60, cap=60, pipeline=pipeline)
     assert g.status == capi.LP_ITER_LIMIT and g.iters == 60
     assert_same(g, _oracle(A, b, c, bland_after=10 ** 9, max_iters=60, cap=60))
     for ba in (0, 1, 32):
-        g = Run(A, b, c, bland_after=ba)
+        g = Run(A, b, c, bland_after=ba, pipeline=pipeline)
         assert g.status == capi.LP_OPTIMAL and abs(g.obj - g0["z"]) <= 1e-12
         assert_same(g, _oracle(A, b, c, bland_after=ba))
 
@@ -205,7 +210,8 @@ def test_textbook_unbounded_infeasible_on_gpu():
     assert g.status == capi.LP_INFEASIBLE
 
 
-def test_degenerate_integer_instances():
+@pytest.mark.parametrize("pipeline", [1, 4])
+def test_degenerate_integer_instances(pipeline):
     """Integer data with zeros in b: ties and degenerate pivots."""
     for seed in range(40):
         rng = np.random.default_rng(seed)
@@ -217,7 +223,7 @@ def test_degenerate_integer_instances():
         b = rng.integers(0, 3, size=m).astype(float)
         c = rng.integers(-1, 4, size=n).astype(float)
         for ba in (0, 3, 32):
-            assert_same(Run(A, b, c, bland_after=ba, ctas=3, threads=64),
+            assert_same(Run(A, b, c, bland_after=ba, ctas=3, threads=64, pipeline=pipeline),
                         _oracle(A, b, c, bland_after=ba))
 
 
@@ -234,9 +240,16 @@ def test_full_size_bitwise(m, n, sense):
     assert_same(g, o)
 
 
-def test_8192_bitwise():
+@pytest.mark.parametrize("m,n", [(2048, 2048), (4096, 512)])
+def test_full_size_two_pivot_passes(m, n):
+    A, b, c = lpgen.dense_lp(m, n, seed=0)
+    assert_same(Run(A, b, c, pipeline=4), _oracle(A, b, c))
+
+
+@pytest.mark.parametrize("pipeline", [1, 4])
+def test_8192_bitwise(pipeline):
     A, b, c = lpgen.dense_lp(8192, 8192, seed=0)
-    g = Run(A, b, c)
+    g = Run(A, b, c, pipeline=pipeline)
     o = oracle.solve(A, b, c, trace_cap=4096)
     assert g.status == o.status == capi.LP_OPTIMAL
     assert g.iters == o.iters
