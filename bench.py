@@ -34,7 +34,6 @@ SMS, SM_MAX_MHZ = 152, 2070.0
 HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal
 ALU_PEAK_TFLOPS = 2 * FP64_DFMA_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
 MAX_LE, MIN_GE = 0, 1
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pivot_pipe_kernel_fp64_traffic.txt")
 KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pivot.cu")
 
 
@@ -64,26 +63,35 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# The kernel each LP of the set runs on (default options): the primal LPs on
-# the pipelined primal kernel (in place up to 96 MB of tableau,
-# double-buffered above), the dual form on the pipelined dual simplex kernel
-# (double-buffered).
-PRIMAL_KERNEL = "pivot_pipe_kernel<double>"
+# The kernel each LP of the set runs on (default options): primal LPs whose
+# tableau fits L2 (up to 96 MB) on the pipelined primal kernel in place,
+# larger ones on the two-pivots-per-pass kernel (double-buffered), the dual
+# form on the pipelined dual simplex kernel (double-buffered).
+INPLACE_KERNEL = "pivot_pipe_kernel<double> (in place)"
+BLOCK_KERNEL = "pivot_block_kernel<double> (two pivots per pass)"
 DUAL_KERNEL = "pivot_pipe_dual_kernel<double> (dual simplex)"
+TRAFFIC_FILES = {
+    INPLACE_KERNEL: os.path.join(ROOT, "profiles", "pivot_pipe_kernel_fp64_traffic.txt"),
+    BLOCK_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_kernel_fp64_traffic.txt"),
+    DUAL_KERNEL: os.path.join(ROOT, "profiles", "pivot_pipe_dual_kernel_fp64_traffic.txt"),
+}
 
 
-def kernel_of(sense):
-    return PRIMAL_KERNEL if sense == MAX_LE else DUAL_KERNEL
+def kernel_of(m, n, sense):
+    if sense != MAX_LE:
+        return DUAL_KERNEL
+    pitch = (n + m + 1 + 31) // 32 * 32
+    return INPLACE_KERNEL if (m + 1) * pitch * 8 <= 96 * 2 ** 20 else BLOCK_KERNEL
 
 
-def kernel_traffic():
-    """Mean DRAM bytes per pipelined-kernel launch in one bench step, from the
-    committed ncu summary, or None when the kernel source changed since that
-    capture."""
+def kernel_traffic(name):
+    """Mean DRAM bytes per launch of one kernel in one bench step, from the
+    committed ncu summary, or None when there is none or the kernel source
+    changed since that capture."""
     import hashlib
     try:
         rec = {}
-        with open(TRAFFIC_FILE) as f:
+        with open(TRAFFIC_FILES[name]) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
@@ -418,7 +426,8 @@ def main():
                 kernel_ms += kms
                 by = it * tableau_bytes(A.shape[0], A.shape[1])
                 alg_bytes += by
-                rec = per_kernel.setdefault(kernel_of(sense), [0, 0.0, 0.0, 0])
+                rec = per_kernel.setdefault(kernel_of(A.shape[0], A.shape[1], sense),
+                                            [0, 0.0, 0.0, 0])
                 rec[0] += 1
                 rec[1] += kms
                 rec[2] += by
@@ -494,8 +503,14 @@ def main():
 
     dominant = max(per_kernel, key=lambda k: per_kernel[k][1])
     roof = roofline_of(dominant)
-    roof["traffic"] = kernel_traffic() if dominant == PRIMAL_KERNEL else None
-    roof["others"] = [roofline_of(k) for k in per_kernel if k != dominant]
+    roof["traffic"] = kernel_traffic(dominant)
+    others = []
+    for k in per_kernel:
+        if k != dominant:
+            r = roofline_of(k)
+            r["traffic"] = kernel_traffic(k)
+            others.append(r)
+    roof["others"] = others
     line = {
         "metric": "pivots/s", "value": all_pivots / (total_ms * 1e-3), "unit": "pivots/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

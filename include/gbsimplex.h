@@ -114,9 +114,8 @@ typedef struct {
                                 0 = selection, then update (one launch-wide
                                     grid barrier per pivot);
                                 1 = auto (default): 2 when the tableau fits the
-                                    L2 cache (up to 96 MB), 4 from 384 MB, 3
-                                    between; 0 when the second buffer cannot
-                                    be allocated;
+                                    L2 cache (up to 96 MB), else 4; 0 when the
+                                    second buffer cannot be allocated;
                                 2 = pipelined in place: the next pivot's
                                     selection overlaps this pivot's update, no
                                     grid barrier;

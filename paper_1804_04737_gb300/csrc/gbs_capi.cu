@@ -24,10 +24,12 @@ using namespace gbs;
 // pivots when updated in place; the pipelined kernel runs in place below it
 // and double-buffered above it.
 constexpr size_t kL2FitBytes = 96ull << 20;
-// From this size on, a pass over the tableau is long enough to hide the
-// selection of two pivots, and the kernel applies two pivots per pass (half
-// the tableau traffic per pivot; measured at 8192^2 FP64: 249 against 370 us
-// per pivot, at 4096 x 512 (152 MB): 61 against 58).
+// Above kL2FitBytes the kernel applies two pivots per pass (half the tableau
+// traffic per pivot).  Below this size its selection of two pivots is the
+// longer chain and gets eight warps, from it on four (measured: 4096 x 512
+// (152 MB) 51.3 us per pivot with eight, 60.5 with four, 57.9 with one pivot
+// per pass; 8192^2 FP64 (1.07 GB) 249 with four, 253 with eight, 370 with
+// one pivot per pass).
 constexpr size_t kBlockBytes = 384ull << 20;
 
 struct lp_handle {
@@ -280,10 +282,8 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
     const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32;
     int pmode = primal ? h->opt.pipeline : 0;
-    if (pmode == 1) {
-        const size_t tb = (size_t)M * P * esz;
-        pmode = tb <= kL2FitBytes ? 2 : (tb < kBlockBytes ? 3 : 4);
-    }
+    const size_t tbytes = (size_t)M * P * esz;
+    if (pmode == 1) pmode = tbytes <= kL2FitBytes ? 2 : 4;
     const bool dwant = dualr && h->opt.pipeline != 0;
     bool have_t2 = false;
     if (pmode >= 3 || dwant) {
@@ -304,7 +304,10 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
                                               pmode == 4 ? 2 : 0);
             if (ps.pipe) {
                 if (pmode == 3) ps.pipe = 2;  // double-buffered
-                if (pmode == 4) ps.pipe = 3;  // double-buffered, two pivots per pass
+                if (pmode == 4) {  // double-buffered, two pivots per pass
+                    ps.pipe = 3;
+                    ps.sel_warps = tbytes < kBlockBytes ? 8 : 4;
+                }
                 return ps;
             }
         }

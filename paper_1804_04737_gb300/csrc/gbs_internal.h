@@ -68,6 +68,7 @@ struct PivotShape {
     int use_smem = 0;              // selection scratch in shared memory (else global)
     int dual = 0;                  // dual simplex kernel (else primal)
     int pipe = 0;                  // pipelined kernel: 1 in place, 2 double-buffered, 3 two pivots per pass
+    int sel_warps = 4;             // two pivots per pass: selection warps per CTA (4 or 8)
     size_t smem_bytes = 0;         // dynamic shared memory per CTA
     long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };

@@ -418,8 +418,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
 // Selection warps per CTA: four in place (the selection is the critical path
 // of an L2-resident pivot), two double-buffered (the update is, and wants
-// the warps).  kSelThreadsMax sizes the launch shape for either.
-constexpr int kSelThreadsMax = 128;
+// the warps); the two-pivot kernel takes four or eight.  kSelThreadsMax sizes
+// the launch shape for any of them.
+constexpr int kSelThreadsMax = 256;
 constexpr int kSelRows = 4;
 
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
@@ -2307,8 +2308,12 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
     void *args[] = {&d_desc, &W, &spin_limit, &budget, &dbm};
     if (sh.pipe == 3) {  // two pivots per pass
         void *bargs[] = {&d_desc, &W, &spin_limit, &budget};
-        const void *fn = prec == PREC_FP64 ? (const void *)pivot_block_kernel<double, 4>
-                                           : (const void *)pivot_block_kernel<float, 4>;
+        const bool w8 = sh.sel_warps == 8;
+        const void *fn = prec == PREC_FP64
+                             ? (w8 ? (const void *)pivot_block_kernel<double, 8>
+                                   : (const void *)pivot_block_kernel<double, 4>)
+                             : (w8 ? (const void *)pivot_block_kernel<float, 8>
+                                   : (const void *)pivot_block_kernel<float, 4>);
         if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sh.smem_bytes);
