@@ -123,6 +123,9 @@ typedef struct {
                                     the memory), a grid barrier per pivot;
                                 4 = as 3, two pivots per pass over the tableau
                                     (half the tableau traffic per pivot).
+                                The dual rule (LP_MIN_GE, and FP32 recovery)
+                                always runs double-buffered: one pivot per pass
+                                for 2 and 3, two for 1 and 4.
                                 Same pivots and bits in every mode.              */
 } lp_options;
 

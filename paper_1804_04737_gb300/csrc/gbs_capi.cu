@@ -312,9 +312,13 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
             }
         }
         if (rule == 1 && dpipe) {
-            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas, 1);
+            // the dual rule: two pivots per pass unless one is asked for (2, 3)
+            const bool two = h->opt.pipeline == 1 || h->opt.pipeline == 4;
+            PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas,
+                                              two ? 3 : 1);
             if (ps.pipe) {
-                ps.pipe = 2;
+                ps.pipe = two ? 3 : 2;
+                if (two) ps.sel_warps = tbytes < kBlockBytes ? 8 : 4;
                 return ps;
             }
         }

@@ -1799,6 +1799,500 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two pivots per pass for the dual form (dual simplex), double-buffered.
+//
+// The pass is the two-pivot primal kernel's (the same update warps' code:
+// Step 4 for both pivots on the strip, then both elementary operations per
+// element in order).  The selection warps choose the next two pivots from the
+// pass's source buffer: leaving row r_a from the rhs of T2 (every CTA, all
+// rows), row r_a of T2 on the CTA's strip and its dual ratio test, one
+// record per CTA (with the pass's pivot-row values at its column) for the
+// entering column q_a, column q_a of T2 (every CTA, all rows); then the rhs
+// after pivot a (from values already in scratch), leaving row r_b, row r_b
+// after pivot a on the strip, a second round of records for q_b, column q_b
+// after pivot a.
+template <typename T, int SW>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    pivot_block_dual_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    typedef typename Vec<T>::type V;
+    constexpr int VW = Vec<T>::W;
+    constexpr int kSelThreads = 32 * SW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Cand rbuf[2][32];
+    __shared__ Cand selc[SW];
+    __shared__ unsigned long long selq[SW];
+    __shared__ int s_flag, s_status, s_sok, s_np, s_pend;
+    __shared__ volatile int s_zready;
+    __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
+
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
+    const int NU = B - kSelThreads;
+    const int lane = tid & 31;
+    const bool selw = tid >= NU;
+    const int stid = tid - NU;
+    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
+    int cur = 0;
+    const long long P = d->P;
+    const int m = d->m, M = d->M, N = d->N;
+    int *__restrict__ basis = d->basis;
+    const int bland_after = d->bland_after;
+    const unsigned long long lim_np = okey((T)(-d->eps_p));
+    const unsigned long long lim_r = okey((T)(-d->eps_r));
+    const unsigned long long zero_k = okey((T)0);
+    long long iters = d->iters;
+    const long long iter_limit =
+        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
+    int deg = d->deg;
+    int status = ST_RUNNING;
+    unsigned *rcnt = d->bar + 128;
+
+    const int c0 = g * W;
+    const int c1 = (int)min((long long)c0 + W, P);
+    const int jend = min(c1, N - 1);
+    const int vpr = (c1 - c0) / VW;
+    const int rpp = NU / vpr;
+    const int lr = tid / vpr, lv = tid - lr * vpr;
+    const bool active = !selw && lr < rpp;
+    const int col0 = c0 + lv * VW;
+    // shared memory: the pass's pivot rows on the strip, the objective row of
+    // T2 on the strip, row r_a of T2 on the strip; scratch: four pivot
+    // columns, the rhs of T2
+    const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
+    T *sprow[kBlk] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + wbytes)};
+    T *sz = reinterpret_cast<T *>(smem_raw + 2 * wbytes);
+    T *sra = reinterpret_cast<T *>(smem_raw + 3 * wbytes);
+    unsigned char *sc = d->scratch_stride > 0
+                            ? reinterpret_cast<unsigned char *>(d->scratch) +
+                                  (size_t)g * (size_t)d->scratch_stride
+                            : smem_raw + 4 * wbytes;
+    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
+    T *scol[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scol[k] = reinterpret_cast<T *>(sc + k * cbytes);
+    T *srhs = reinterpret_cast<T *>(sc + 4 * cbytes);
+
+    // ---- the first pivot from the current tableau (all threads) ----
+    int p = -1, q = -1;
+    {
+        const T *A = bufs[0];
+        const int bland = deg >= bland_after;
+        Cand c = cand_empty();
+        for (int i = tid; i < m; i += B) {
+            const unsigned long long vk = okey(lds(A + (long long)i * P + (N - 1)));
+            if (vk < lim_r) cand_take(c, bland ? zero_k : vk, bland ? __ldcg(basis + i) : i, i);
+        }
+        c = block_min_c(c, rbuf[0]);
+        if (c.idx < 0) status = ST_OPTIMAL;
+        else if (iters >= iter_limit) status = ST_ITER_LIMIT;
+        else p = c.idx;
+        if (status == ST_RUNNING) {
+            const T *rowr = A + (long long)p * P, *z = A + (long long)m * P;
+            Cand e = cand_empty();
+            for (int j = c0 + tid; j < jend; j += B) {
+                const T a = lds(rowr + j);
+                if (okey(a) < lim_np) cand_take(e, okey(pos_part(lds(z + j)) / neg(a)), j, j);
+            }
+            e = block_min_c(e, rbuf[1]);
+            if (tid == 0) d->part_sel[g] = e;
+            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
+            if (status == ST_RUNNING) {
+                const Cand sel = load_partials_min(d->part_sel, G, rbuf[0]);
+                if (sel.idx < 0) {
+                    status = ST_INFEASIBLE;
+                } else if (sel.idx >= N - 1) {
+                    status = ST_TIMEOUT;  // never: a partial from outside the row
+                } else {
+                    q = sel.idx;
+                    deg = (sel.vk == zero_k) ? deg + 1 : 0;
+                    for (int i = tid; i < M; i += B) scol[0][i] = lds(A + (long long)i * P + q);
+                }
+            }
+        }
+    }
+    int np = 1, pend = ST_RUNNING;
+    int pp[kBlk] = {p, -1}, qq[kBlk] = {q, -1};
+    int cb = 0;
+    unsigned lk = 0;
+    if (tid == 0) s_zready = 0;
+    __syncthreads();
+
+    while (status == ST_RUNNING) {
+        const T *A = bufs[cur];
+        T *Bn = bufs[cur ^ 1];
+        const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
+        T *nc[kBlk] = {scol[(cb + 2) & 3], scol[(cb + 3) & 3]};
+        const int par = lk & 1;
+        Cand *recA = d->part_sel + (2 * par) * G, *recB = d->part_sel + (2 * par + 1) * G;
+        unsigned long long *valA = d->part_vals + (size_t)(2 * par) * G * kBlkVals;
+        unsigned long long *valB = d->part_vals + (size_t)(2 * par + 1) * G * kBlkVals;
+        const unsigned tA = (unsigned)G * (2u * lk + 1u), tB = (unsigned)G * (2u * lk + 2u);
+        (void)lane;
+        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
+            for (int k = 0; k < np; ++k) {
+                if (iters + k < d->trace_cap) {
+                    d->trace[2 * (iters + k)] = pp[k];
+                    d->trace[2 * (iters + k) + 1] = qq[k];
+                }
+                basis[pp[k]] = qq[k];
+            }
+            d->last_p = pp[np - 1];
+            d->last_q = qq[np - 1];
+        }
+        const int nbland = deg >= bland_after;  // rule of pivot a's selection
+        const bool select = pend == ST_RUNNING;
+        if (!selw) {
+            // Step 4 for the pass's pivots on this CTA's strip
+            for (int j = c0 + tid; j < c1; j += NU) {
+                const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
+                sprow[0][j - c0] = r;
+                if (np > 1) {
+                    const T t = (pp[1] == pp[0]) ? r
+                                                 : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + j));
+                    sprow[1][j - c0] = t / pc[1][pp[1]];
+                }
+            }
+            named_sync(1, NU);
+            // the strip of the objective row of T2, also for the selection
+            if (tid < vpr) {
+                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
+#pragma unroll
+                for (int k = 0; k < kBlk; ++k)
+                    if (k < np) vfma(zt, pc[k][m], *reinterpret_cast<const V *>(sprow[k] + tid * VW));
+                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
+                *reinterpret_cast<V *>(sz + tid * VW) = zt;
+            }
+            named_sync(1, NU);
+            if (tid == 0) {
+                __threadfence_block();
+                s_zready = (int)(lk + 1);  // sz, sprow of this pass ready for the selection
+            }
+            // Step 5 for the pass's pivots on the constraint rows of the strip
+            if (active && np == 2) {
+                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
+                const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
+                const int p0 = pp[0], p1 = pp[1];
+                const T *__restrict__ c0p = pc[0];
+                const T *__restrict__ c1p = pc[1];
+                const T *abase = A + col0;
+                T *bbase = Bn + col0;
+                int i = lr;
+                for (; i + 3 * rpp < m; i += 4 * rpp) {
+                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                    V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                    V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                    t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
+                    t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
+                    t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
+                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p1, c1p[i1], pr1);
+                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p1, c1p[i2], pr1);
+                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p1, c1p[i3], pr1);
+                }
+                for (; i < m; i += rpp) {
+                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
+                }
+            } else if (active) {
+                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
+                const int p0 = pp[0];
+                const T *__restrict__ c0p = pc[0];
+                const T *abase = A + col0;
+                T *bbase = Bn + col0;
+                int i = lr;
+                for (; i + 3 * rpp < m; i += 4 * rpp) {
+                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
+                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
+                }
+                for (; i < m; i += rpp) {
+                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                }
+            }
+        } else {
+            // selection of the next pass's pivots a and b (dual simplex)
+            int st = ST_RUNNING, nnp = 0, npend = ST_RUNNING;
+            int pa = -1, qa = -1, pb = -1, qb = -1, rza = 0, rzb = 0;
+            auto bkey = [&](int i) -> int {  // the basic variable of row i after the pass
+                if (np > 1 && i == pp[1]) return qq[1];
+                if (i == pp[0]) return qq[0];
+                return __ldcg(basis + i);
+            };
+            T *colA = nc[0];
+            if (!select) {
+                st = pend;  // the previous pass's selection already ended the solve
+            } else {
+                // the pass's pivot-row values at the rhs (the update warps' Step 4 values)
+                T pvr[kBlk];
+                {
+                    const T r = lds(A + (long long)pp[0] * P + (N - 1)) / pc[0][pp[0]];
+                    pvr[0] = r;
+                    pvr[1] = (T)0;
+                    if (np > 1) {
+                        const T t = (pp[1] == pp[0])
+                                        ? r
+                                        : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + (N - 1)));
+                        pvr[1] = t / pc[1][pp[1]];
+                    }
+                }
+                // ---- pivot a: the leaving row from the rhs of T2, every row ----
+                Cand c = cand_empty();
+                for (int i0 = stid; i0 < m; i0 += kSelRows * kSelThreads) {
+                    T hv[kSelRows];
+#pragma unroll
+                    for (int u = 0; u < kSelRows; ++u) {
+                        const int i = i0 + u * kSelThreads;
+                        hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSelRows; ++u) {
+                        const int i = i0 + u * kSelThreads;
+                        if (i >= m) break;
+                        const T h = blk_apply<T>(hv[u], i, np, pp, pc, pvr);
+                        srhs[i] = h;
+                        const unsigned long long vk = okey(h);
+                        if (vk < lim_r) cand_take(c, nbland ? zero_k : vk, nbland ? bkey(i) : i, i);
+                    }
+                }
+                c = sel_min<SW>(c, 0ull, selc, selq, nullptr);
+                if (c.idx < 0) st = ST_OPTIMAL;
+                else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
+                else if (c.idx >= m) st = ST_TIMEOUT;  // never: a row outside the tableau
+                else pa = c.idx;
+                if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+                if (st == ST_RUNNING) {
+                    // this pass's sprow and sz from the update warps
+                    if (stid == 0) {
+                        const long long t0 = clock64();
+                        int ok = 1;
+                        while (s_zready < (int)(lk + 1)) {
+                            if (clock64() - t0 > spin_limit || *(volatile int *)d->err) {
+                                atomicExch(d->err, 1);
+                                ok = 0;
+                                break;
+                            }
+                        }
+                        s_sok = ok;
+                    }
+                    named_sync(2, kSelThreads);
+                    __threadfence_block();
+                    if (!s_sok) st = ST_TIMEOUT;
+                }
+                unsigned long long ka = 0ull;
+                if (st == ST_RUNNING) {
+                    // row r_a of T2 on this strip and its dual ratio test; the record
+                    Cand e = cand_empty();
+                    for (int j = c0 + stid; j < c1; j += kSelThreads) {
+                        T x = lds(A + (long long)pa * P + j);
+#pragma unroll
+                        for (int k = 0; k < kBlk; ++k)
+                            if (k < np)
+                                x = (pa == pp[k]) ? sprow[k][j - c0] : tfma(-pc[k][pa], sprow[k][j - c0], x);
+                        sra[j - c0] = x;
+                        if (j < jend && okey(x) < lim_np)
+                            cand_take(e, okey(pos_part(sz[j - c0]) / neg(x)), j, j);
+                    }
+                    e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
+                    if (stid == 0) {
+                        recA[g] = e;
+                        unsigned long long *v = valA + (size_t)g * kBlkVals;
+                        for (int k = 0; k < np; ++k) v[k] = e.idx >= 0 ? tbits(sprow[k][e.idx - c0]) : 0ull;
+                        red_add_release(rcnt, 1u);
+                        s_sok = (int)wait_ctr(rcnt, tA, d->err, spin_limit);
+                    }
+                    named_sync(2, kSelThreads);
+                    if (!s_sok) {
+                        st = ST_TIMEOUT;
+                    } else {
+                        Cand f = cand_empty();
+                        for (int k = stid; k < G; k += kSelThreads) {
+                            const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recA) + k));
+                            if (cand_less(r, f)) {
+                                f = r;
+                                ka = (unsigned long long)k;
+                            }
+                        }
+                        const Cand sel = sel_min<SW>(f, ka, selc, selq, &ka);
+                        if (sel.idx < 0) st = ST_INFEASIBLE;
+                        else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
+                        else {
+                            qa = sel.idx;
+                            rza = sel.vk == zero_k;
+                        }
+                        if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+                    }
+                }
+                if (st == ST_RUNNING) {
+                    // column q_a of T2, every row: the next pass's first pivot column
+                    T pvq[kBlk];
+#pragma unroll
+                    for (int k = 0; k < kBlk; ++k) pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
+                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                        T av[kSelRows];
+#pragma unroll
+                        for (int u = 0; u < kSelRows; ++u) {
+                            const int i = i0 + u * kSelThreads;
+                            av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < kSelRows; ++u) {
+                            const int i = i0 + u * kSelThreads;
+                            if (i >= M) break;
+                            colA[i] = blk_apply<T>(av[u], i, np, pp, pc, pvq);
+                        }
+                    }
+                    named_sync(2, kSelThreads);
+                    // ---- pivot b: the rhs after pivot a and its leaving row ----
+                    const T piva = colA[pa];
+                    const T pra = srhs[pa] / piva;  // pivot a's row at the rhs
+                    const int nblandb = (rza ? deg + 1 : 0) >= bland_after;
+                    Cand cb2 = cand_empty();
+                    for (int i = stid; i < m; i += kSelThreads) {
+                        const T h = (i == pa) ? pra : tfma(-colA[i], pra, srhs[i]);
+                        const unsigned long long vk = okey(h);
+                        if (vk < lim_r)
+                            cand_take(cb2, nblandb ? zero_k : vk,
+                                      nblandb ? (i == pa ? qa : bkey(i)) : i, i);
+                    }
+                    cb2 = sel_min<SW>(cb2, 0ull, selc, selq, nullptr);
+                    nnp = 1;
+                    if (cb2.idx < 0) npend = ST_OPTIMAL;
+                    else if (iters + np + 1 >= iter_limit) npend = ST_ITER_LIMIT;
+                    else if (cb2.idx >= m) st = ST_TIMEOUT;  // never
+                    else pb = cb2.idx;
+                    if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+                    if (st == ST_RUNNING && pb >= 0) {
+                        // row r_b after pivot a on this strip, its dual ratio test;
+                        // the record carries the pivot-row values at its column
+                        Cand e = cand_empty();
+                        const T cab = colA[pb], cam = colA[m];
+                        for (int j = c0 + stid; j < c1; j += kSelThreads) {
+                            T x = lds(A + (long long)pb * P + j);
+#pragma unroll
+                            for (int k = 0; k < kBlk; ++k)
+                                if (k < np)
+                                    x = (pb == pp[k]) ? sprow[k][j - c0] : tfma(-pc[k][pb], sprow[k][j - c0], x);
+                            const T prj = sra[j - c0] / piva;  // pivot a's row at column j
+                            x = (pb == pa) ? prj : tfma(-cab, prj, x);
+                            if (j < jend && okey(x) < lim_np) {
+                                const T z3 = tfma(-cam, prj, sz[j - c0]);
+                                cand_take(e, okey(pos_part(z3) / neg(x)), j, j);
+                            }
+                        }
+                        e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
+                        if (stid == 0) {
+                            recB[g] = e;
+                            unsigned long long *v = valB + (size_t)g * kBlkVals;
+                            for (int k = 0; k < np; ++k) v[k] = e.idx >= 0 ? tbits(sprow[k][e.idx - c0]) : 0ull;
+                            v[np] = e.idx >= 0 ? tbits(sra[e.idx - c0] / piva) : 0ull;
+                            red_add_release(rcnt, 1u);
+                            s_sok = (int)wait_ctr(rcnt, tB, d->err, spin_limit);
+                        }
+                        named_sync(2, kSelThreads);
+                        unsigned long long kb = 0ull;
+                        if (!s_sok) {
+                            st = ST_TIMEOUT;
+                        } else {
+                            Cand f = cand_empty();
+                            for (int k = stid; k < G; k += kSelThreads) {
+                                const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recB) + k));
+                                if (cand_less(r, f)) {
+                                    f = r;
+                                    kb = (unsigned long long)k;
+                                }
+                            }
+                            const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
+                            if (sel.idx < 0) npend = ST_INFEASIBLE;
+                            else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
+                            else {
+                                qb = sel.idx;
+                                rzb = sel.vk == zero_k;
+                            }
+                            if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
+                        }
+                        if (st == ST_RUNNING && qb >= 0) {
+                            // column q_b after pivot a, every row
+                            T pvb[kBlk + 1];
+#pragma unroll
+                            for (int k = 0; k <= kBlk; ++k) pvb[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
+                            T *colB = nc[1];
+                            for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                                T av[kSelRows];
+#pragma unroll
+                                for (int u = 0; u < kSelRows; ++u) {
+                                    const int i = i0 + u * kSelThreads;
+                                    av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
+                                }
+#pragma unroll
+                                for (int u = 0; u < kSelRows; ++u) {
+                                    const int i = i0 + u * kSelThreads;
+                                    if (i >= M) break;
+                                    const T t = blk_apply<T>(av[u], i, np, pp, pc, pvb);
+                                    colB[i] = (i == pa) ? pvb[np] : tfma(-colA[i], pvb[np], t);
+                                }
+                            }
+                            nnp = 2;
+                        }
+                    }
+                }
+            }
+            named_sync(2, kSelThreads);
+            if (stid == 0) {
+                s_status = st;
+                s_np = nnp;
+                s_pend = npend;
+                s_p[0] = pa;
+                s_q[0] = qa;
+                s_p[1] = pb;
+                s_q[1] = qb;
+                s_rz[0] = rza;
+                s_rz[1] = rzb;
+            }
+        }
+        // the CTA's pass and its selection of the next pass are done
+        __syncthreads();
+        iters += np;
+        ++lk;
+        status = s_status;
+        if (status == ST_RUNNING) {
+            np = s_np;
+            pend = s_pend;
+            for (int k = 0; k < kBlk; ++k) {
+                pp[k] = s_p[k];
+                qq[k] = s_q[k];
+            }
+            deg = s_rz[0] ? deg + 1 : 0;
+            if (np > 1) deg = s_rz[1] ? deg + 1 : 0;
+            cb = (cb + 2) & 3;
+        }
+        cur ^= 1;
+        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
+            status = ST_TIMEOUT;
+            break;
+        }
+    }
+
+    if (g == 0 && tid == 0) {
+        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
+        d->iters = iters;
+        d->iter_limit = iter_limit;
+        d->deg = deg;
+        d->T = bufs[cur];  // hand over the buffer holding the last tableau
+        d->T2 = bufs[cur ^ 1];
+    }
+}
+
 constexpr int kBatchThreads = 512;  // register room for both pivot rules in one kernel
 
 // ---------------------------------------------------------------------------
@@ -2309,7 +2803,12 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
     if (sh.pipe == 3) {  // two pivots per pass
         void *bargs[] = {&d_desc, &W, &spin_limit, &budget};
         const bool w8 = sh.sel_warps == 8;
-        const void *fn = prec == PREC_FP64
+        const void *fn = sh.dual ? (prec == PREC_FP64
+                                        ? (w8 ? (const void *)pivot_block_dual_kernel<double, 8>
+                                              : (const void *)pivot_block_dual_kernel<double, 4>)
+                                        : (w8 ? (const void *)pivot_block_dual_kernel<float, 8>
+                                              : (const void *)pivot_block_dual_kernel<float, 4>))
+                         : prec == PREC_FP64
                              ? (w8 ? (const void *)pivot_block_kernel<double, 8>
                                    : (const void *)pivot_block_kernel<double, 4>)
                              : (w8 ? (const void *)pivot_block_kernel<float, 8>
@@ -2370,10 +2869,12 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     const size_t cbytes = ((size_t)M * esz + 15) & ~(size_t)15;
     const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
     // (dual == 2: the two-pivot kernel, four pivot rows and columns)
+    // (dual == 3: the two-pivot dual kernel, four pivot rows and columns and the rhs)
     const size_t scratch = dual == 1   ? sprow + 2 * cbytes
                            : dual == 2 ? 5 * cbytes + (size_t)M * sizeof(unsigned long long)
+                           : dual == 3 ? 5 * cbytes
                                        : 3 * cbytes + (size_t)M * sizeof(unsigned long long);
-    const size_t fixed = dual == 2 ? 4 * sprow : sprow;
+    const size_t fixed = dual >= 2 ? 4 * sprow : sprow;
     if (fixed + scratch <= kMaxDynSmem) {
         sh.use_smem = 1;
         sh.smem_bytes = fixed + scratch;
@@ -2383,7 +2884,7 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
         sh.smem_bytes = fixed;
         sh.scratch_stride = (long long)((scratch + 255) & ~(size_t)255);
     }
-    sh.dual = dual == 1;
+    sh.dual = dual == 1 || dual == 3;
     // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
     // launch), the strip one pass of the update threads
     sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw;

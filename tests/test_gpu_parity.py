@@ -133,15 +133,18 @@ def test_pivot_by_pivot_tableau(sense, pipeline):
         capi.lp_destroy(h)
 
 
-@pytest.mark.parametrize("chunk,pipeline", [(7, 1), (1, 4), (2, 4), (3, 4), (7, 4)])
-def test_resume_in_chunks(chunk, pipeline):
+@pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
+@pytest.mark.parametrize("chunk,pipeline", [(7, 1), (1, 4), (2, 4), (3, 4), (7, 4), (5, 3)])
+def test_resume_in_chunks(chunk, pipeline, sense):
     """Pivot limits that end a launch inside a two-pivot pass or between passes."""
     A, b, c = lpgen.dense_lp(150, 180, seed=13)
-    o = _oracle(A, b, c)
+    if sense == MIN_GE:
+        A, b, c = lpgen.dual_of(A, b, c)
+    o = _oracle(A, b, c, sense)
     h = capi.lp_create(capi.lp_options_default(max_iters=chunk, trace_cap=4096,
                                                pipeline=pipeline))
     try:
-        capi.lp_load(h, A, b, c)
+        capi.lp_load(h, A, b, c, sense)
         calls = 0
         while True:
             capi.lp_solve(h)
@@ -246,11 +249,13 @@ def test_full_size_two_pivot_passes(m, n):
     assert_same(Run(A, b, c, pipeline=4), _oracle(A, b, c))
 
 
-@pytest.mark.parametrize("pipeline", [1, 4])
-def test_8192_bitwise(pipeline):
+@pytest.mark.parametrize("pipeline,sense", [(1, MAX_LE), (3, MAX_LE), (1, MIN_GE)])
+def test_8192_bitwise(pipeline, sense):
     A, b, c = lpgen.dense_lp(8192, 8192, seed=0)
-    g = Run(A, b, c, pipeline=pipeline)
-    o = oracle.solve(A, b, c, trace_cap=4096)
+    if sense == MIN_GE:
+        A, b, c = lpgen.dual_of(A, b, c)
+    g = Run(A, b, c, sense, pipeline=pipeline)
+    o = oracle.solve(A, b, c, sense=sense, trace_cap=4096)
     assert g.status == o.status == capi.LP_OPTIMAL
     assert g.iters == o.iters
     assert np.array_equal(g.tp, o.trace_p) and np.array_equal(g.tq, o.trace_q)
