@@ -66,14 +66,14 @@ def peaks():
 # The kernel each LP of the set runs on (default options): primal LPs whose
 # tableau fits L2 (up to 96 MB) on the pipelined primal kernel in place,
 # larger ones on the two-pivots-per-pass kernel (double-buffered), the dual
-# form on the pipelined dual simplex kernel (double-buffered).
+# form on the two-pivots-per-pass dual simplex kernel (double-buffered).
 INPLACE_KERNEL = "pivot_pipe_kernel<double> (in place)"
 BLOCK_KERNEL = "pivot_block_kernel<double> (two pivots per pass)"
-DUAL_KERNEL = "pivot_pipe_dual_kernel<double> (dual simplex)"
+DUAL_KERNEL = "pivot_block_dual_kernel<double> (dual simplex, two pivots per pass)"
 TRAFFIC_FILES = {
     INPLACE_KERNEL: os.path.join(ROOT, "profiles", "pivot_pipe_kernel_fp64_traffic.txt"),
     BLOCK_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_kernel_fp64_traffic.txt"),
-    DUAL_KERNEL: os.path.join(ROOT, "profiles", "pivot_pipe_dual_kernel_fp64_traffic.txt"),
+    DUAL_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_dual_kernel_fp64_traffic.txt"),
 }
 
 
