@@ -34,7 +34,7 @@ SMS, SM_MAX_MHZ = 152, 2070.0
 HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal
 ALU_PEAK_TFLOPS = 2 * FP64_DFMA_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
 MAX_LE, MIN_GE = 0, 1
-KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pivot.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pipe.cu")
 
 
 def workload(seed):

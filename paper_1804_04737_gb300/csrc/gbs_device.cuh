@@ -282,5 +282,14 @@ __device__ __forceinline__ unsigned long long screen_thr(unsigned long long rk, 
     return okey(r * (float)kScreen);
 }
 
+// One 16-byte vector of row i: Step 4 for the pivot row, Step 5 otherwise.
+template <typename T, typename V>
+__device__ __forceinline__ V pivot_vec(const V &t, int i, int p, T col_i, const V &pr) {
+    if (i == p) return pr;
+    V r = t;
+    vfma(r, col_i, pr);
+    return r;
+}
+
 }  // namespace dev
 }  // namespace gbs

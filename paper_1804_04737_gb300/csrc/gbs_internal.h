@@ -87,6 +87,10 @@ struct InputStats {
 
 enum : int { PREC_FP64 = 0, PREC_FP32 = 1 };
 
+// Launch limits of the persistent pivot kernels.
+constexpr int kMaxThreads = 1024;
+constexpr size_t kMaxDynSmem = 200 * 1024;  // below the 227 KB opt-in limit, leaving room for statics
+
 inline long long pitch_for(int N) { return ((long long)N + 31) / 32 * 32; }
 
 // Kernel launchers (gbs_pivot.cu).  All enqueue on `s` and return the launch

@@ -1,4 +1,7 @@
-// Dense tableau simplex kernels for sm_103a.
+// Dense tableau simplex kernels for sm_103a: the in-place kernel (one grid
+// barrier per pivot; also run by batched and served solves), the batch and
+// server kernels, and the build, inspection and extraction kernels.  The
+// pipelined kernels are in gbs_pipe.cu.
 //
 // One persistent grid runs whole pivot sequences (the paper's Step I keeps its
 // thread team alive for the whole solve, Sec. 3; here the team is a grid of
@@ -52,8 +55,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int kMaxThreads = 1024;
-constexpr size_t kMaxDynSmem = 200 * 1024;  // below the 227 KB opt-in limit, leaving room for statics
 
 // Per-thread running candidate of the next selection, fed with freshly
 // updated values: the objective row (primal pricing, Sec. 2 Step 2) or the
@@ -84,15 +85,6 @@ __device__ __forceinline__ void watch_row(Cand &best, const Watch &w, int i, int
             cand_take(best, w.bland ? w.zero : vk, key, i);
         }
     }
-}
-
-// One 16-byte vector of row i: Step 4 for the pivot row, Step 5 otherwise.
-template <typename T, typename V>
-__device__ __forceinline__ V pivot_vec(const V &t, int i, int p, T col_i, const V &pr) {
-    if (i == p) return pr;
-    V r = t;
-    vfma(r, col_i, pr);
-    return r;
 }
 
 // SMEM: the selection scratch lives in shared memory (else in this CTA's
@@ -383,1914 +375,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     solve_lp<T, SMEM, DUAL>(d, gridDim.x, blockIdx.x, W, spin_limit, budget, smem_raw);
-}
-
-// ---------------------------------------------------------------------------
-// Pipelined primal simplex for one LP (FP64 or FP32 tableau).
-//
-// In every CTA the last kSelWarps warps select pivot k+1 while the others
-// stream pivot k's update of the CTA's column strip:
-//   update warps     divide the strip of the pivot row (Step 4), update the
-//                    strip of the objective row and publish the CTA's pricing
-//                    record (its best column, with the new pivot-row values at
-//                    that column and at the rhs), then update the rest of the
-//                    strip (Step 5), reading the pivot column from this CTA's
-//                    scratch;
-//   selection warps  reduce the pricing records to the entering column q'
-//                    (Step 2), form the whole column q' and rhs of tableau k+1
-//                    from tableau k with the very fma the update uses (so the
-//                    values are bit for bit those the update writes) into the
-//                    CTA's scratch, and run the screened ratio test on them
-//                    (Step 3).  Every CTA does this redundantly, so the pivot
-//                    row needs no exchange between CTAs.
-// In place (tableaus that fit L2), the vectors the selection reads (each
-// CTA's own pricing winner, which is where the entering column always is, and
-// the rhs) are left out of the bulk update and updated once a counter shows
-// every CTA's selection done reading them.  There is no grid barrier: a CTA
-// publishes its pricing record only after finishing its previous pivot, so
-// the pricing counter also proves every vector the selection reads is current,
-// and no CTA runs more than one pivot ahead of another (records are
-// double-buffered by pivot parity).  Double-buffered (larger tableaus), pivot
-// k reads one buffer and writes the other, with a grid barrier per pivot to
-// keep the CTAs' row streams in step.  The selection divides only on
-// near-ties: it shares the FP64 pipe with the update warps.  The first pivot's
-// selection runs alone, with a grid barrier.
-
-// Selection warps per CTA: four in place (the selection is the critical path
-// of an L2-resident pivot), two double-buffered (the update is, and wants
-// the warps); the two-pivot kernel takes four or eight.  kSelThreadsMax sizes
-// the launch shape for any of them.
-constexpr int kSelThreadsMax = 256;
-constexpr int kSelRows = 4;
-
-__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
-
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-static_assert(sizeof(Cand) == 16 && offsetof(Cand, key) == 8 && offsetof(Cand, idx) == 12,
-              "Cand is read as one 16-byte vector");
-
-__device__ __forceinline__ unsigned long long tbits(double x) {
-    return (unsigned long long)__double_as_longlong(x);
-}
-__device__ __forceinline__ unsigned long long tbits(float x) {
-    return (unsigned long long)__float_as_uint(x);
-}
-template <typename T>
-__device__ __forceinline__ T tfrom(unsigned long long u);
-template <>
-__device__ __forceinline__ double tfrom<double>(unsigned long long u) {
-    return __longlong_as_double((long long)u);
-}
-template <>
-__device__ __forceinline__ float tfrom<float>(unsigned long long u) {
-    return __uint_as_float((unsigned)u);
-}
-
-__device__ __forceinline__ Cand unpack_cand(const ulonglong2 &v) {
-    Cand e;
-    e.vk = v.x;
-    e.key = (int)(unsigned)(v.y & 0xffffffffull);
-    e.idx = (int)(unsigned)(v.y >> 32);
-    return e;
-}
-
-// Bounded wait of one thread until *ctr reaches target; false when it ran out
-// or another CTA reported a timeout.
-__device__ __forceinline__ bool wait_ctr(unsigned *ctr, unsigned target, int *err,
-                                         long long spin_limit) {
-    const long long t0 = clock64();
-    while ((int)(ld_acquire(ctr) - target) < 0) {
-        if (clock64() - t0 > spin_limit || *(volatile int *)err) {
-            atomicExch(err, 1);
-            return false;
-        }
-    }
-    return true;
-}
-
-// Selection-group minimum of a candidate and its 64-bit payload: the warps'
-// minima go through sc[]/sq[] (kSelWarps entries) and a named barrier; every
-// selection thread gets the result.
-template <int SW>
-__device__ __forceinline__ Cand sel_min(Cand c, unsigned long long q, Cand *sc,
-                                        unsigned long long *sq, unsigned long long *pq) {
-    const int lane = threadIdx.x & 31, sw = (threadIdx.x >> 5) % SW;
-    Cand r;
-    const int src = warp_argmin(c.vk, c.key, &r.vk, &r.key);
-    r.idx = __shfl_sync(0xffffffffu, c.idx, src);
-    const unsigned long long rq = __shfl_sync(0xffffffffu, q, src);
-    if (lane == 0) {
-        sc[sw] = r;
-        sq[sw] = rq;
-    }
-    named_sync(2, 32 * SW);
-    Cand b = sc[0];
-    unsigned long long bq = sq[0];
-#pragma unroll
-    for (int w = 1; w < SW; ++w)
-        if (cand_less(sc[w], b)) {
-            b = sc[w];
-            bq = sq[w];
-        }
-    named_sync(2, 32 * SW);  // sc/sq free again
-    if (pq) *pq = bq;
-    return b;
-}
-
-// Selection-group minimum and sum of two 32-bit values (min of a, sum of b).
-template <int SW>
-__device__ __forceinline__ void sel_min_sum(unsigned a, unsigned b, unsigned *sa, unsigned *sb,
-                                            unsigned *ra, unsigned *rb) {
-    const int lane = threadIdx.x & 31, sw = (threadIdx.x >> 5) % SW;
-    a = __reduce_min_sync(0xffffffffu, a);
-    b = __reduce_add_sync(0xffffffffu, b);
-    if (lane == 0) {
-        sa[sw] = a;
-        sb[sw] = b;
-    }
-    named_sync(2, 32 * SW);
-    unsigned ma = sa[0], mb = sb[0];
-#pragma unroll
-    for (int w = 1; w < SW; ++w) {
-        ma = sa[w] < ma ? sa[w] : ma;
-        mb += sb[w];
-    }
-    named_sync(2, 32 * SW);
-    *ra = ma;
-    *rb = mb;
-}
-
-// Selection-group minimum of a 64-bit value.
-template <int SW>
-__device__ __forceinline__ unsigned long long sel_min_u64(unsigned long long v,
-                                                          unsigned long long *sq) {
-    const int lane = threadIdx.x & 31, sw = (threadIdx.x >> 5) % SW;
-    v = warp_min_u64(v);
-    if (lane == 0) sq[sw] = v;
-    named_sync(2, 32 * SW);
-    unsigned long long r = sq[0];
-#pragma unroll
-    for (int w = 1; w < SW; ++w) r = sq[w] < r ? sq[w] : r;
-    named_sync(2, 32 * SW);
-    return r;
-}
-
-// SW selection warps; SW == 2 runs the double-buffered mode, SW == 4 in place.
-template <typename T, int SW>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_pipe_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget,
-                      int dbm) {
-    typedef typename Vec<T>::type V;
-    constexpr int VW = Vec<T>::W;
-    constexpr int kSelWarps = SW, kSelThreads = 32 * SW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Cand rbuf[2][32];
-    __shared__ unsigned long long ubuf[32];
-    __shared__ Cand wpart[32];
-    __shared__ Cand selc[SW];
-    __shared__ unsigned long long selq[SW];
-    __shared__ unsigned sela[SW], selb[SW];
-    __shared__ int s_flag, s_p, s_q, s_status, s_jv, s_uok, s_rzero, s_sok;
-
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
-    // update threads; the last SW warps select (the launch reserves
-    // kSelThreadsMax threads for them, the rest of those update)
-    const int NU = B - kSelThreads;
-    const int lane = tid & 31;
-    const bool selw = tid >= NU;
-    const int stid = tid - NU;
-    // in place, or double-buffered (dbm; T2 is the second buffer): pivot k
-    // reads bufs[cur] and writes bufs[cur ^ 1], with a grid barrier after
-    // each pivot
-    const bool db = dbm != 0 && d->T2 != nullptr;
-    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(db ? d->T2 : d->T)};
-    int cur = 0;
-    const T *Tab = bufs[0];
-    const long long P = d->P;
-    const int m = d->m, M = d->M, N = d->N;
-    int *__restrict__ basis = d->basis;
-    const int bland_after = d->bland_after;
-    const unsigned long long lim_p = okey((T)d->eps_p);
-    const unsigned long long lim_d = okey((T)(-d->eps_d));
-    const unsigned long long zero_k = okey((T)0);
-    long long iters = d->iters;
-    const long long iter_limit =
-        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
-    int deg = d->deg;
-    int status = ST_RUNNING;
-    unsigned *pcnt = d->bar + 64, *rcnt = d->bar + 128;
-
-    // strip and thread map of the update threads
-    const int c0 = g * W;  // < P: the host launches ceil(P / W) CTAs
-    const int c1 = (int)min((long long)c0 + W, P);
-    const int vpr = (c1 - c0) / VW;
-    const int rpp = NU / vpr;  // >= 1: the host keeps W <= NU * VW
-    const int lr = tid / vpr, lv = tid - lr * vpr;
-    const bool active = !selw && lr < rpp;
-    const int col0 = c0 + lv * VW;
-    // the vector of this strip holding the rhs column, or -1; in place it is
-    // protected from the bulk update until every selection has read it
-    const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
-    const int rvp = db ? -1 : rv;
-    // scratch: the strip of the pivot row in shared memory; the pivot columns
-    // of this and the next pivot, the ratio numerators and the screening keys
-    // in shared memory, or in this CTA's slice of global scratch
-    T *sprow = reinterpret_cast<T *>(smem_raw);
-    unsigned char *sc = d->scratch_stride > 0
-                            ? reinterpret_cast<unsigned char *>(d->scratch) +
-                                  (size_t)g * (size_t)d->scratch_stride
-                            : smem_raw + (((size_t)W * sizeof(T) + 15) & ~(size_t)15);
-    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
-    T *scol[2] = {reinterpret_cast<T *>(sc), reinterpret_cast<T *>(sc + cbytes)};
-    T *snum = reinterpret_cast<T *>(sc + 2 * cbytes);
-    unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 3 * cbytes);
-
-    // ---- selection of the first pivot from the current tableau (all threads) ----
-    int p = -1, q = -1;
-    {
-        const int bland = deg >= bland_after;
-        Cand c = cand_empty();
-        const T *z = Tab + (long long)m * P;
-        for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
-            const unsigned long long zk = okey(lds(z + j));
-            if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
-        }
-        c = block_min_c(c, rbuf[0]);
-        if (tid == 0) d->part_sel[g] = c;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
-        if (status == ST_RUNNING) {
-            const Cand sel = load_partials_min(d->part_sel, G, rbuf[1]);
-            if (sel.idx < 0) status = ST_OPTIMAL;
-            else if (iters >= iter_limit) status = ST_ITER_LIMIT;
-            else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: a partial from outside the row
-            else q = sel.idx;
-        }
-        if (status == ST_RUNNING) {
-            // the whole pivot column and the ratio test, in every CTA
-            unsigned long long lmin = ~0ull;
-            for (int i = tid; i < M; i += B) {
-                const T a = lds(Tab + (long long)i * P + q);
-                scol[0][i] = a;
-                if (i < m) {
-                    const T num = pos_part(lds(Tab + (long long)i * P + (N - 1)));
-                    const unsigned long long rk = okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                    snum[i] = num;
-                    srk[i] = rk;
-                    lmin = rk < lmin ? rk : lmin;
-                }
-            }
-            const unsigned long long rstar = block_min_u(lmin, ubuf);
-            if (rstar == ~0ull) {
-                status = ST_UNBOUNDED;
-            } else {
-                const unsigned long long thr = screen_thr(rstar, (T)0);
-                Cand rc = cand_empty();
-                for (int i = tid; i < m; i += B)
-                    if (srk[i] <= thr)
-                        cand_take(rc, okey(snum[i] / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
-                rc = block_min_c(rc, rbuf[0]);
-                p = rc.idx;
-                deg = (rc.vk == zero_k) ? deg + 1 : 0;
-            }
-        }
-    }
-
-    int lk = 0;  // pivots made in this launch (parity of records and pivot-column buffers)
-    const int rowner = (N - 1) / W;  // the CTA whose strip holds the rhs column
-    while (status == ST_RUNNING) {
-        const T *A = bufs[cur];
-        T *Bn = bufs[cur ^ 1];
-        const T *col = scol[lk & 1];
-        T *ncol = scol[(lk + 1) & 1];
-        const int par = (lk + 1) & 1;  // records of the selection of pivot k+1
-        Cand *psel = d->part_sel + par * G;
-        ulonglong2 *pval = reinterpret_cast<ulonglong2 *>(d->part_vals) + par * G;
-        const unsigned target = (unsigned)G * (unsigned)(lk + 1);
-        const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
-        if (!selw) {
-            const T piv = col[p];
-            // Step 4 on this CTA's strip of the pivot row
-            for (int j = c0 + tid; j < c1; j += NU)
-                sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
-            named_sync(1, NU);
-            // the strip of the objective row, held back in registers, and the
-            // CTA's pricing candidate for pivot k+1
-            Cand c = cand_empty();
-            V zt;
-            const bool zown = tid < vpr;
-            if (zown) {
-                const T colm = col[m];
-                const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
-                zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
-                vfma(zt, colm, pr);
-#pragma unroll
-                for (int k = 0; k < VW; ++k) {
-                    const int j = c0 + tid * VW + k;
-                    const unsigned long long zk = okey(getc(zt, k));
-                    if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
-                }
-            }
-            c = warp_min(c);
-            if (lane == 0) wpart[tid >> 5] = c;
-            named_sync(1, NU);
-            if (tid < 32) {  // warp 0 reduces the warps' candidates and publishes
-                const Cand e = tid < NU / 32 ? wpart[tid] : cand_empty();
-                const Cand r = warp_min(e);
-                if (tid == 0) {
-                    psel[g] = r;
-                    // with it, the new pivot-row values the selection needs
-                    // from this strip: at the candidate column and at the rhs
-                    pval[g] = make_ulonglong2(r.idx >= 0 ? tbits(sprow[r.idx - c0]) : 0ull,
-                                              rv >= 0 ? tbits(sprow[N - 1 - c0]) : 0ull);
-                    red_add_release(pcnt, 1u);
-                    s_jv = (r.idx >= 0 && !db) ? (r.idx - c0) / VW : -1;
-                }
-            }
-            named_sync(1, NU);
-            const int jv = s_jv;  // protected: the vector of the CTA's candidate
-            if (zown && tid != jv && tid != rvp)
-                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
-            // Step 5 on the constraint rows of the strip, but the protected vectors
-            if (active && lv != jv && lv != rvp) {
-                const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    const T a0 = col[i], a1 = col[i1], a2 = col[i2], a3 = col[i3];
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p, a0, pr);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p, a1, pr);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p, a2, pr);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p, a3, pr);
-                }
-                for (; i < m; i += rpp) {
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) =
-                        pivot_vec<T>(t0, i, p, col[i], pr);
-                }
-            }
-            // in place: every CTA's selection is done reading the protected
-            // vectors, then update them (double-buffered: nothing to protect)
-            if (tid == 0) s_uok = db ? 1 : (int)wait_ctr(rcnt, target, d->err, spin_limit);
-            named_sync(1, NU);
-            if (s_uok && !db) {
-                for (int k = 0; k < 2; ++k) {
-                    const int v = k == 0 ? jv : (rvp != jv ? rvp : -1);
-                    if (v < 0) continue;
-                    const V vpr_ = *reinterpret_cast<const V *>(sprow + v * VW);
-                    T *vbase = Bn + c0 + v * VW;
-                    for (int i = tid; i < M; i += NU) {
-                        V *p0 = reinterpret_cast<V *>(vbase + (long long)i * P);
-                        *p0 = pivot_vec<T>(ldv(p0), i, p, col[i], vpr_);
-                    }
-                }
-            }
-        } else {
-            // selection of pivot k+1, overlapping the update of pivot k
-            int st = ST_RUNNING, np = -1, nq = -1, rzero = 0;
-            if (stid == 0) {
-                int ok = 1;
-                if (g == 0) {
-                    // the basis and trace of pivot k, once every CTA's selection
-                    // of pivot k is done reading the basis of pivot k-1
-                    ok = (int)wait_ctr(rcnt, target - (unsigned)G, d->err, spin_limit);
-                    if (ok) {
-                        if (iters < d->trace_cap) {
-                            d->trace[2 * iters] = p;
-                            d->trace[2 * iters + 1] = q;
-                        }
-                        basis[p] = q;
-                        d->last_p = p;
-                        d->last_q = q;
-                    }
-                }
-                // every CTA has finished pivot k-1 and published its record
-                if (ok) ok = (int)wait_ctr(pcnt, target, d->err, spin_limit);
-                s_sok = ok;
-            }
-            named_sync(2, kSelThreads);
-            if (!s_sok) {
-                st = ST_TIMEOUT;
-            } else {
-                // Step 2: the entering column from the G pricing records
-                Cand e = cand_empty();
-                unsigned long long eq = 0ull;
-                for (int k = stid; k < G; k += kSelThreads) {
-                    const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(psel) + k));
-                    const unsigned long long rq = __ldcg(&pval[k].x);
-                    if (cand_less(r, e)) {
-                        e = r;
-                        eq = rq;
-                    }
-                }
-                const unsigned long long prr_b = __ldcg(&pval[rowner].y);
-                unsigned long long prq_b;
-                const Cand sel = sel_min<SW>(e, eq, selc, selq, &prq_b);
-                if (sel.idx < 0) st = ST_OPTIMAL;
-                else if (iters + 1 >= iter_limit) st = ST_ITER_LIMIT;
-                else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never: a record from outside the row
-                else nq = sel.idx;
-                if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                if (st == ST_RUNNING) {
-                    // column q' and rhs of tableau k+1, every row, and Step 3
-                    const T prq = tfrom<T>(prq_b), prr = tfrom<T>(prr_b);
-                    unsigned long long lmin = ~0ull;
-                    // kSelRows rows per thread in flight (the loads are L2 round trips)
-                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                        T av[kSelRows], hv[kSelRows];
-#pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
-                            const int i = i0 + u * kSelThreads;
-                            av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
-                            hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
-                        }
-#pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
-                            const int i = i0 + u * kSelThreads;
-                            if (i >= M) break;
-                            const T ci = col[i];
-                            const T a = (i == p) ? prq : tfma(-ci, prq, av[u]);
-                            ncol[i] = a;
-                            if (i < m) {
-                                const T num = pos_part((i == p) ? prr : tfma(-ci, prr, hv[u]));
-                                const unsigned long long rk =
-                                    okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                                snum[i] = num;
-                                srk[i] = rk;
-                                lmin = rk < lmin ? rk : lmin;
-                            }
-                        }
-                    }
-                    const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
-                    if (rstar == ~0ull) {
-                        st = ST_UNBOUNDED;
-                    } else {
-                        // the rows within the screening threshold: when there is
-                        // one it is the exact minimum, otherwise compare their
-                        // exact quotients, then keys
-                        const unsigned long long thr = screen_thr(rstar, (T)0);
-                        unsigned first = 0xffffffffu, cnt = 0;
-                        for (int i = stid; i < m; i += kSelThreads)
-                            if (srk[i] <= thr) {
-                                first = (unsigned)i < first ? (unsigned)i : first;
-                                ++cnt;
-                            }
-                        unsigned gfirst, gcnt;
-                        sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
-                        if (gcnt == 1) {
-                            np = (int)gfirst;
-                            rzero = srk[np] == zero_k;  // screening keys are exact at +0
-                        } else {
-                            Cand rc = cand_empty();
-                            for (int i = stid; i < m; i += kSelThreads)
-                                if (srk[i] <= thr) {
-                                    const T nm = snum[i];
-                                    const unsigned long long vk =
-                                        tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
-                                    const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
-                                    cand_take(rc, vk, key, i);
-                                }
-                            rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
-                            np = rc.idx;
-                            rzero = rc.vk == zero_k;
-                        }
-                    }
-                }
-            }
-            // every selection thread of this CTA is done reading tableau k: arrive
-            // (also when no ratio test ran: the owners of protected vectors wait)
-            named_sync(2, kSelThreads);
-            if (stid == 0) {
-                if (st != ST_TIMEOUT) red_add_release(rcnt, 1u);
-                s_status = st;
-                s_p = np;
-                s_q = nq;
-                s_rzero = rzero;
-            }
-        }
-        // the CTA's update of pivot k and its selection of pivot k+1 are done
-        __syncthreads();
-        ++iters;
-        ++lk;
-        status = s_status;
-        if (!s_uok) status = ST_TIMEOUT;
-        if (status == ST_RUNNING) {
-            p = s_p;
-            q = s_q;
-            deg = s_rzero ? deg + 1 : 0;
-        }
-        if (db) {
-            cur ^= 1;
-            // keeps the CTAs in step: their row streams then share DRAM pages
-            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-                status = ST_TIMEOUT;
-                break;
-            }
-        }
-    }
-
-    if (g == 0 && tid == 0) {
-        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
-        d->iters = iters;
-        d->iter_limit = iter_limit;
-        d->deg = deg;
-        if (db) {  // hand over the buffer holding the last tableau as the current one
-            d->T = bufs[cur];
-            d->T2 = bufs[cur ^ 1];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Pipelined dual simplex for the dual form (sense LP_MIN_GE), double-buffered:
-// pivot k reads bufs[cur] and writes bufs[cur ^ 1], so the selection of pivot
-// k+1 reads tableau k while the update warps stream pivot k.
-//   update warps     divide the strip of the pivot row (Step 4), update the
-//                    strip of the objective row (kept for the selection) and
-//                    the rest of the strip (Step 5);
-//   selection warps  form the rhs of tableau k+1 over every row and take the
-//                    leaving row r' (the most negative rhs; every CTA does this
-//                    redundantly), then row r' of tableau k+1 on the CTA's own
-//                    strip and the dual ratio test on it, publish the strip's
-//                    winner with its pivot-row value, reduce the G records to
-//                    the entering column q', and form column q' of tableau k+1
-//                    (the next pivot column) in the CTA's scratch.
-// The values the selection forms are the very fma results the update writes.
-// A grid barrier ends each pivot.  The first pivot's selection runs alone.
-template <typename T, int SW>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_pipe_dual_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
-    typedef typename Vec<T>::type V;
-    constexpr int VW = Vec<T>::W;
-    constexpr int kSelThreads = 32 * SW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Cand rbuf[2][32];
-    __shared__ Cand selc[SW];
-    __shared__ unsigned long long selq[SW];
-    __shared__ int s_flag, s_p, s_q, s_status, s_rzero, s_sok;
-
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
-    const int NU = B - kSelThreads;  // update threads; the last SW warps select
-    const bool selw = tid >= NU;
-    const int stid = tid - NU;
-    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
-    int cur = 0;
-    const long long P = d->P;
-    const int m = d->m, M = d->M, N = d->N;
-    int *__restrict__ basis = d->basis;
-    const int bland_after = d->bland_after;
-    const unsigned long long lim_np = okey((T)(-d->eps_p));
-    const unsigned long long lim_r = okey((T)(-d->eps_r));
-    const unsigned long long zero_k = okey((T)0);
-    long long iters = d->iters;
-    const long long iter_limit =
-        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
-    int deg = d->deg;
-    int status = ST_RUNNING;
-    unsigned *rcnt = d->bar + 128;
-
-    // strip and thread map of the update threads
-    const int c0 = g * W;  // < P: the host launches ceil(P / W) CTAs
-    const int c1 = (int)min((long long)c0 + W, P);
-    const int jend = min(c1, N - 1);  // the strip's columns that may enter
-    const int vpr = (c1 - c0) / VW;
-    const int rpp = NU / vpr;  // >= 1: the host keeps W <= NU * VW
-    const int lr = tid / vpr, lv = tid - lr * vpr;
-    const bool active = !selw && lr < rpp;
-    const int col0 = c0 + lv * VW;
-    // scratch: the strip of the pivot row in shared memory; the strip of the
-    // new objective row and the pivot columns of this and the next pivot in
-    // shared memory, or in this CTA's slice of global scratch
-    T *sprow = reinterpret_cast<T *>(smem_raw);
-    const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
-    unsigned char *sc = d->scratch_stride > 0
-                            ? reinterpret_cast<unsigned char *>(d->scratch) +
-                                  (size_t)g * (size_t)d->scratch_stride
-                            : smem_raw + wbytes;
-    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
-    T *sz = reinterpret_cast<T *>(sc);
-    T *scol[2] = {reinterpret_cast<T *>(sc + wbytes), reinterpret_cast<T *>(sc + wbytes + cbytes)};
-
-    // ---- selection of the first pivot from the current tableau (all threads) ----
-    int p = -1, q = -1;
-    {
-        const T *A = bufs[0];
-        const int bland = deg >= bland_after;
-        // leaving row, in every CTA over all rows
-        Cand c = cand_empty();
-        for (int i = tid; i < m; i += B) {
-            const unsigned long long vk = okey(lds(A + (long long)i * P + (N - 1)));
-            if (vk < lim_r) cand_take(c, bland ? zero_k : vk, bland ? __ldcg(basis + i) : i, i);
-        }
-        c = block_min_c(c, rbuf[0]);
-        if (c.idx < 0) status = ST_OPTIMAL;
-        else if (iters >= iter_limit) status = ST_ITER_LIMIT;
-        else p = c.idx;
-        if (status == ST_RUNNING) {
-            // entering column: the dual ratio test on this CTA's strip of row
-            // p, then over the CTAs' partials
-            const T *rowr = A + (long long)p * P, *z = A + (long long)m * P;
-            Cand e = cand_empty();
-            for (int j = c0 + tid; j < jend; j += B) {
-                const T a = lds(rowr + j);
-                if (okey(a) < lim_np) cand_take(e, okey(pos_part(lds(z + j)) / neg(a)), j, j);
-            }
-            e = block_min_c(e, rbuf[1]);
-            if (tid == 0) d->part_sel[g] = e;
-            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
-            if (status == ST_RUNNING) {
-                const Cand sel = load_partials_min(d->part_sel, G, rbuf[0]);
-                if (sel.idx < 0) {
-                    status = ST_INFEASIBLE;
-                } else if (sel.idx >= N - 1) {
-                    status = ST_TIMEOUT;  // never: a partial from outside the row
-                } else {
-                    q = sel.idx;
-                    deg = (sel.vk == zero_k) ? deg + 1 : 0;
-                    for (int i = tid; i < M; i += B) scol[0][i] = lds(A + (long long)i * P + q);
-                }
-            }
-        }
-    }
-    __syncthreads();  // the first pivot column is in scol[0]
-
-    int lk = 0;  // pivots made in this launch (parity of records and pivot columns)
-    while (status == ST_RUNNING) {
-        const T *A = bufs[cur];
-        T *Bn = bufs[cur ^ 1];
-        const T *col = scol[lk & 1];
-        T *ncol = scol[(lk + 1) & 1];
-        const int par = (lk + 1) & 1;  // records of the selection of pivot k+1
-        Cand *psel = d->part_sel + par * G;
-        ulonglong2 *pval = reinterpret_cast<ulonglong2 *>(d->part_vals) + par * G;
-        const unsigned target = (unsigned)G * (unsigned)(lk + 1);
-        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
-            if (iters < d->trace_cap) {
-                d->trace[2 * iters] = p;
-                d->trace[2 * iters + 1] = q;
-            }
-            basis[p] = q;
-            d->last_p = p;
-            d->last_q = q;
-        }
-        const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
-        const T piv = col[p];
-        if (!selw) {
-            // Step 4 on this CTA's strip of the pivot row
-            for (int j = c0 + tid; j < c1; j += NU)
-                sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
-            named_sync(1, NU);
-            // the strip of the objective row, also kept for the selection
-            if (tid < vpr) {
-                const T colm = col[m];
-                const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
-                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
-                vfma(zt, colm, pr);
-                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
-                *reinterpret_cast<V *>(sz + tid * VW) = zt;
-            }
-            named_sync(3, B);  // sprow and sz ready for the selection warps
-            // Step 5 on the constraint rows of the strip
-            if (active) {
-                const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    const T a0 = col[i], a1 = col[i1], a2 = col[i2], a3 = col[i3];
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p, a0, pr);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p, a1, pr);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p, a2, pr);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p, a3, pr);
-                }
-                for (; i < m; i += rpp) {
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) =
-                        pivot_vec<T>(t0, i, p, col[i], pr);
-                }
-            }
-        } else {
-            // selection of pivot k+1, overlapping the update of pivot k
-            int st = ST_RUNNING, np = -1, nq = -1, rzero = 0;
-            // leaving row: the rhs of tableau k+1 over every row
-            const T prr = lds(A + (long long)p * P + (N - 1)) / piv;
-            Cand c = cand_empty();
-            for (int i0 = stid; i0 < m; i0 += kSelRows * kSelThreads) {
-                T hv[kSelRows];
-#pragma unroll
-                for (int u = 0; u < kSelRows; ++u) {
-                    const int i = i0 + u * kSelThreads;
-                    hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
-                }
-#pragma unroll
-                for (int u = 0; u < kSelRows; ++u) {
-                    const int i = i0 + u * kSelThreads;
-                    if (i >= m) break;
-                    const T rhs = (i == p) ? prr : tfma(-col[i], prr, hv[u]);
-                    const unsigned long long vk = okey(rhs);
-                    if (vk < lim_r)
-                        cand_take(c, nbland ? zero_k : vk,
-                                  nbland ? (i == p ? q : __ldcg(basis + i)) : i, i);
-                }
-            }
-            c = sel_min<SW>(c, 0ull, selc, selq, nullptr);
-            if (c.idx < 0) st = ST_OPTIMAL;
-            else if (iters + 1 >= iter_limit) st = ST_ITER_LIMIT;
-            else if (c.idx >= m) st = ST_TIMEOUT;  // never: a row outside the tableau
-            else np = c.idx;
-            if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-            named_sync(3, B);  // the update warps' sprow and sz
-            if (st == ST_RUNNING) {
-                // row r' of tableau k+1 on this strip and the dual ratio test
-                const T cr = col[np];
-                Cand e = cand_empty();
-                unsigned long long eq = 0ull;
-                for (int j = c0 + stid; j < jend; j += kSelThreads) {
-                    const T pr = sprow[j - c0];
-                    const T a = (np == p) ? pr : tfma(-cr, pr, lds(A + (long long)np * P + j));
-                    if (okey(a) < lim_np) {
-                        const unsigned long long vk = okey(pos_part(sz[j - c0]) / neg(a));
-                        if (vk < e.vk || (vk == e.vk && j < e.key)) {
-                            e.vk = vk;
-                            e.key = j;
-                            e.idx = j;
-                            eq = tbits(pr);
-                        }
-                    }
-                }
-                e = sel_min<SW>(e, eq, selc, selq, &eq);
-                if (stid == 0) {
-                    psel[g] = e;
-                    pval[g] = make_ulonglong2(eq, 0ull);
-                }
-            }
-            named_sync(2, kSelThreads);
-            if (stid == 0 && st != ST_TIMEOUT) red_add_release(rcnt, 1u);
-            if (st == ST_RUNNING) {
-                if (stid == 0) s_sok = (int)wait_ctr(rcnt, target, d->err, spin_limit);
-                named_sync(2, kSelThreads);
-                if (!s_sok) {
-                    st = ST_TIMEOUT;
-                } else {
-                    // entering column from the G records, with its pivot-row value
-                    Cand e = cand_empty();
-                    unsigned long long eq = 0ull;
-                    for (int k = stid; k < G; k += kSelThreads) {
-                        const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(psel) + k));
-                        const unsigned long long rq = __ldcg(&pval[k].x);
-                        if (cand_less(r, e)) {
-                            e = r;
-                            eq = rq;
-                        }
-                    }
-                    unsigned long long prq_b;
-                    const Cand sel = sel_min<SW>(e, eq, selc, selq, &prq_b);
-                    if (sel.idx < 0) {
-                        st = ST_INFEASIBLE;
-                    } else if (sel.idx >= N - 1) {  // never: a record from outside the row
-                        if (stid == 0) atomicExch(d->err, 1);
-                        st = ST_TIMEOUT;
-                    } else {
-                        nq = sel.idx;
-                        rzero = sel.vk == zero_k;
-                        // column q' of tableau k+1: the next pivot column
-                        const T prq = tfrom<T>(prq_b);
-                        for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                            T av[kSelRows];
-#pragma unroll
-                            for (int u = 0; u < kSelRows; ++u) {
-                                const int i = i0 + u * kSelThreads;
-                                av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
-                            }
-#pragma unroll
-                            for (int u = 0; u < kSelRows; ++u) {
-                                const int i = i0 + u * kSelThreads;
-                                if (i >= M) break;
-                                ncol[i] = (i == p) ? prq : tfma(-col[i], prq, av[u]);
-                            }
-                        }
-                    }
-                }
-            }
-            if (stid == 0) {
-                s_status = st;
-                s_p = np;
-                s_q = nq;
-                s_rzero = rzero;
-            }
-        }
-        // the CTA's update of pivot k and its selection of pivot k+1 are done
-        __syncthreads();
-        ++iters;
-        ++lk;
-        status = s_status;
-        if (status == ST_RUNNING) {
-            p = s_p;
-            q = s_q;
-            deg = s_rzero ? deg + 1 : 0;
-        }
-        cur ^= 1;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
-        }
-    }
-
-    if (g == 0 && tid == 0) {
-        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
-        d->iters = iters;
-        d->iter_limit = iter_limit;
-        d->deg = deg;
-        d->T = bufs[cur];  // hand over the buffer holding the last tableau
-        d->T2 = bufs[cur ^ 1];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Two pivots per pass (multi-pivot blocking), primal, double-buffered.
-//
-// A pass reads tableau T0 from bufs[cur] once and writes T2 into bufs[cur^1],
-// applying the pass's pivots (p1, q1) and (p2, q2) to every element in the
-// order the one-pivot method applies them:
-//   t = i == p1 ? prow1[j] : fma(-col1[i], prow1[j], T0[i][j]);
-//   T2[i][j] = i == p2 ? prow2[j] : fma(-col2[i], prow2[j], t),
-// so the result is bit for bit that of two one-pivot passes, with half of
-// their tableau traffic.  prow1 = T0[p1][.] / col1[p1] and prow2 = T1[p2][.] /
-// col2[p2] are formed per strip at the start of the pass; col1 and col2 (the
-// columns q1 of T0 and q2 of T1) come from the previous pass's selection.
-//
-// While the update warps stream the pass, the selection warps select the
-// next two pivots from T0 and the pass's pivots (Steps 2-3 twice):
-//   a: pricing records (each CTA's best column of the objective row of T2,
-//      with the pass's pivot-row values there and at the rhs) -> q_a; the
-//      whole column q_a and rhs of T2 in every CTA -> ratio test -> p_a;
-//   b: row p_a of T2 on each CTA's strip divided by the pivot (the pivot row
-//      of pivot a) and the objective row after pivot a -> pricing records ->
-//      q_b; column q_b and rhs after pivot a in every CTA -> p_b.
-// A pass holds one pivot when the next pivot ends the solve (optimal,
-// unbounded, iteration limit); the first pass of a launch holds the first
-// pivot alone.  A grid barrier ends each pass.
-
-constexpr int kBlk = 2;       // pivots per pass
-constexpr int kBlkVals = 8;   // values per record: 3 at the record's column, 3 at the rhs, 2 unused
-
-// x after the pass's pivots 0..np-1, for row i (pv: their pivot-row values at
-// the column of x).
-template <typename T>
-__device__ __forceinline__ T blk_apply(T x, int i, int np, const int *pp, const T *const *pc,
-                                       const T *pv) {
-#pragma unroll
-    for (int k = 0; k < kBlk; ++k)
-        if (k < np) x = (i == pp[k]) ? pv[k] : tfma(-pc[k][i], pv[k], x);
-    return x;
-}
-
-template <typename T, int SW>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_block_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
-    typedef typename Vec<T>::type V;
-    constexpr int VW = Vec<T>::W;
-    constexpr int kSelThreads = 32 * SW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Cand rbuf[2][32];
-    __shared__ unsigned long long ubuf[32];
-    __shared__ Cand wpart[32];
-    __shared__ Cand selc[SW];
-    __shared__ unsigned long long selq[SW];
-    __shared__ unsigned sela[SW], selb[SW];
-    __shared__ int s_flag, s_status, s_sok, s_np, s_pend;
-    __shared__ volatile int s_zready;  // passes whose objective-row strip is in sz
-    __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
-
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
-    const int NU = B - kSelThreads;
-    const int lane = tid & 31;
-    const bool selw = tid >= NU;
-    const int stid = tid - NU;
-    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
-    int cur = 0;
-    const long long P = d->P;
-    const int m = d->m, M = d->M, N = d->N;
-    int *__restrict__ basis = d->basis;
-    const int bland_after = d->bland_after;
-    const unsigned long long lim_p = okey((T)d->eps_p);
-    const unsigned long long lim_d = okey((T)(-d->eps_d));
-    const unsigned long long zero_k = okey((T)0);
-    long long iters = d->iters;
-    const long long iter_limit =
-        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
-    int deg = d->deg;
-    int status = ST_RUNNING;
-    unsigned *pcnt = d->bar + 64;
-
-    // strip and thread map of the update threads
-    const int c0 = g * W;
-    const int c1 = (int)min((long long)c0 + W, P);
-    const int vpr = (c1 - c0) / VW;
-    const int rpp = NU / vpr;
-    const int lr = tid / vpr, lv = tid - lr * vpr;
-    const bool active = !selw && lr < rpp;
-    const int col0 = c0 + lv * VW;
-    const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
-    const int rowner = (N - 1) / W;
-    // shared memory: the pass's pivot rows on the strip, the objective row of
-    // T2 on the strip, pivot a's row on the strip; scratch (shared or this
-    // CTA's global slice): four pivot columns (this pass's two, the next
-    // pass's two), ratio numerators, screening keys
-    const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
-    T *sprow[kBlk] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + wbytes)};
-    T *sz = reinterpret_cast<T *>(smem_raw + 2 * wbytes);
-    T *spa = reinterpret_cast<T *>(smem_raw + 3 * wbytes);
-    unsigned char *sc = d->scratch_stride > 0
-                            ? reinterpret_cast<unsigned char *>(d->scratch) +
-                                  (size_t)g * (size_t)d->scratch_stride
-                            : smem_raw + 4 * wbytes;
-    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
-    T *scol[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) scol[k] = reinterpret_cast<T *>(sc + k * cbytes);
-    T *snum = reinterpret_cast<T *>(sc + 4 * cbytes);
-    unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 5 * cbytes);
-
-    // ---- selection of the first pivot from the current tableau (all threads) ----
-    int p = -1, q = -1;
-    {
-        const T *Tab = bufs[0];
-        const int bland = deg >= bland_after;
-        Cand c = cand_empty();
-        const T *z = Tab + (long long)m * P;
-        for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
-            const unsigned long long zk = okey(lds(z + j));
-            if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
-        }
-        c = block_min_c(c, rbuf[0]);
-        if (tid == 0) d->part_sel[g] = c;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
-        if (status == ST_RUNNING) {
-            const Cand sel = load_partials_min(d->part_sel, G, rbuf[1]);
-            if (sel.idx < 0) status = ST_OPTIMAL;
-            else if (iters >= iter_limit) status = ST_ITER_LIMIT;
-            else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: a partial from outside the row
-            else q = sel.idx;
-        }
-        if (status == ST_RUNNING) {
-            unsigned long long lmin = ~0ull;
-            for (int i = tid; i < M; i += B) {
-                const T a = lds(Tab + (long long)i * P + q);
-                scol[0][i] = a;
-                if (i < m) {
-                    const T num = pos_part(lds(Tab + (long long)i * P + (N - 1)));
-                    const unsigned long long rk = okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                    snum[i] = num;
-                    srk[i] = rk;
-                    lmin = rk < lmin ? rk : lmin;
-                }
-            }
-            const unsigned long long rstar = block_min_u(lmin, ubuf);
-            if (rstar == ~0ull) {
-                status = ST_UNBOUNDED;
-            } else {
-                const unsigned long long thr = screen_thr(rstar, (T)0);
-                Cand rc = cand_empty();
-                for (int i = tid; i < m; i += B)
-                    if (srk[i] <= thr)
-                        cand_take(rc, okey(snum[i] / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
-                rc = block_min_c(rc, rbuf[0]);
-                p = rc.idx;
-                deg = (rc.vk == zero_k) ? deg + 1 : 0;
-            }
-        }
-    }
-
-    // the pass's pivots; pend: the status to report after this pass, when the
-    // selection during the previous pass already ended the solve
-    int np = 1, pend = ST_RUNNING;
-    int pp[kBlk] = {p, -1}, qq[kBlk] = {q, -1};
-    int cb = 0;          // the pass's pivot columns are scol[cb], scol[cb + 1] (mod 4)
-    unsigned lk = 0;     // passes made in this launch
-    if (tid == 0) s_zready = 0;
-    __syncthreads();
-    while (status == ST_RUNNING) {
-        const T *A = bufs[cur];
-        T *Bn = bufs[cur ^ 1];
-        const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
-        T *nc[kBlk] = {scol[(cb + 2) & 3], scol[(cb + 3) & 3]};
-        const int par = lk & 1;
-        Cand *recA = d->part_sel + (2 * par) * G, *recB = d->part_sel + (2 * par + 1) * G;
-        unsigned long long *valA = d->part_vals + (size_t)(2 * par) * G * kBlkVals;
-        unsigned long long *valB = d->part_vals + (size_t)(2 * par + 1) * G * kBlkVals;
-        const unsigned tA = (unsigned)G * (2u * lk + 1u), tB = (unsigned)G * (2u * lk + 2u);
-        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
-            for (int k = 0; k < np; ++k) {
-                if (iters + k < d->trace_cap) {
-                    d->trace[2 * (iters + k)] = pp[k];
-                    d->trace[2 * (iters + k) + 1] = qq[k];
-                }
-                basis[pp[k]] = qq[k];
-            }
-            d->last_p = pp[np - 1];
-            d->last_q = qq[np - 1];
-        }
-        const int nbland = deg >= bland_after;  // rule of pivot a's selection
-        const bool select = pend == ST_RUNNING;
-        if (!selw) {
-            // Step 4 for the pass's pivots on this CTA's strip
-            for (int j = c0 + tid; j < c1; j += NU) {
-                const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
-                sprow[0][j - c0] = r;
-                if (np > 1) {
-                    const T t = (pp[1] == pp[0]) ? r
-                                                 : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + j));
-                    sprow[1][j - c0] = t / pc[1][pp[1]];
-                }
-            }
-            named_sync(1, NU);
-            // the strip of the objective row of T2, and the CTA's pricing record a
-            Cand c = cand_empty();
-            if (tid < vpr) {
-                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
-#pragma unroll
-                for (int k = 0; k < kBlk; ++k)
-                    if (k < np) vfma(zt, pc[k][m], *reinterpret_cast<const V *>(sprow[k] + tid * VW));
-                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
-                *reinterpret_cast<V *>(sz + tid * VW) = zt;
-#pragma unroll
-                for (int k = 0; k < VW; ++k) {
-                    const int j = c0 + tid * VW + k;
-                    const unsigned long long zk = okey(getc(zt, k));
-                    if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
-                }
-            }
-            c = warp_min(c);
-            if (lane == 0) wpart[tid >> 5] = c;
-            named_sync(1, NU);
-            if (tid < 32) {
-                const Cand e = tid < NU / 32 ? wpart[tid] : cand_empty();
-                const Cand r = warp_min(e);
-                if (tid == 0) {
-                    if (select) {
-                        recA[g] = r;
-                        unsigned long long *v = valA + (size_t)g * kBlkVals;
-                        for (int k = 0; k < np; ++k) {
-                            v[k] = r.idx >= 0 ? tbits(sprow[k][r.idx - c0]) : 0ull;
-                            v[3 + k] = rv >= 0 ? tbits(sprow[k][N - 1 - c0]) : 0ull;
-                        }
-                        red_add_release(pcnt, 1u);
-                    }
-                    __threadfence_block();
-                    s_zready = (int)(lk + 1);  // sz, sprow of this pass ready for the selection
-                }
-            }
-            // Step 5 for the pass's pivots on the constraint rows of the strip
-            if (active && np == 2) {
-                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
-                const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
-                const int p0 = pp[0], p1 = pp[1];
-                const T *__restrict__ c0p = pc[0];
-                const T *__restrict__ c1p = pc[1];
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
-                    t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
-                    t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p1, c1p[i1], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p1, c1p[i2], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p1, c1p[i3], pr1);
-                }
-                for (; i < m; i += rpp) {
-                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
-                }
-            } else if (active) {
-                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
-                const int p0 = pp[0];
-                const T *__restrict__ c0p = pc[0];
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
-                }
-                for (; i < m; i += rpp) {
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                }
-            }
-        } else {
-            // selection of the next pass's pivots a and b
-            int st = ST_RUNNING, nnp = 0, npend = ST_RUNNING;
-            int pa = -1, qa = -1, pb = -1, qb = -1, rza = 0, rzb = 0;
-            // the basic variable of row i after the pass's pivots
-            auto bkey = [&](int i) -> int {
-                if (np > 1 && i == pp[1]) return qq[1];
-                if (i == pp[0]) return qq[0];
-                return __ldcg(basis + i);
-            };
-            const T *colA = nc[0];
-            if (!select) {
-                st = pend;  // the previous pass's selection already ended the solve
-            } else {
-                // ---- pivot a (Step 2): the pricing records of this pass ----
-                if (stid == 0) s_sok = (int)wait_ctr(pcnt, tA, d->err, spin_limit);
-                named_sync(2, kSelThreads);
-                unsigned long long ka = 0ull;
-                if (!s_sok) {
-                    st = ST_TIMEOUT;
-                } else {
-                    Cand e = cand_empty();
-                    for (int k = stid; k < G; k += kSelThreads) {
-                        const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recA) + k));
-                        if (cand_less(r, e)) {
-                            e = r;
-                            ka = (unsigned long long)k;
-                        }
-                    }
-                    const Cand sel = sel_min<SW>(e, ka, selc, selq, &ka);
-                    if (sel.idx < 0) st = ST_OPTIMAL;
-                    else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
-                    else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never: a record from outside the row
-                    else qa = sel.idx;
-                    if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                }
-                if (st == ST_RUNNING) {
-                    // the pass's pivot-row values at q_a and at the rhs
-                    T pvq[kBlk], pvr[kBlk];
-#pragma unroll
-                    for (int k = 0; k < kBlk; ++k) {
-                        pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
-                        pvr[k] = tfrom<T>(__ldcg(valA + (size_t)rowner * kBlkVals + 3 + k));
-                    }
-                    // column q_a and rhs of T2, every row (Step 3)
-                    T *ncol = nc[0];
-                    unsigned long long lmin = ~0ull;
-                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                        T av[kSelRows], hv[kSelRows];
-#pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
-                            const int i = i0 + u * kSelThreads;
-                            av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
-                            hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
-                        }
-#pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
-                            const int i = i0 + u * kSelThreads;
-                            if (i >= M) break;
-                            const T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
-                            ncol[i] = a;
-                            if (i < m) {
-                                const T num = pos_part(blk_apply<T>(hv[u], i, np, pp, pc, pvr));
-                                const unsigned long long rk =
-                                    okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                                snum[i] = num;
-                                srk[i] = rk;
-                                lmin = rk < lmin ? rk : lmin;
-                            }
-                        }
-                    }
-                    const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
-                    if (rstar == ~0ull) {
-                        st = ST_UNBOUNDED;
-                    } else {
-                        const unsigned long long thr = screen_thr(rstar, (T)0);
-                        unsigned first = 0xffffffffu, cnt = 0;
-                        for (int i = stid; i < m; i += kSelThreads)
-                            if (srk[i] <= thr) {
-                                first = (unsigned)i < first ? (unsigned)i : first;
-                                ++cnt;
-                            }
-                        unsigned gfirst, gcnt;
-                        sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
-                        if (gcnt == 1) {
-                            pa = (int)gfirst;
-                            rza = srk[pa] == zero_k;
-                        } else {
-                            Cand rc = cand_empty();
-                            for (int i = stid; i < m; i += kSelThreads)
-                                if (srk[i] <= thr) {
-                                    const T nm = snum[i];
-                                    const unsigned long long vk =
-                                        tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
-                                    cand_take(rc, vk, nbland ? bkey(i) : i, i);
-                                }
-                            rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
-                            pa = rc.idx;
-                            rza = rc.vk == zero_k;
-                        }
-                    }
-                }
-                if (st == ST_RUNNING) {
-                    // ---- pivot b: pivot a's row on this strip, the objective row
-                    // after pivot a, the CTA's pricing record b ----
-                    const int nblandb = (rza ? deg + 1 : 0) >= bland_after;
-                    if (stid == 0) {  // this pass's sprow and sz (written by the update warps)
-                        const long long t0 = clock64();
-                        int ok = 1;
-                        while (s_zready < (int)(lk + 1)) {
-                            if (clock64() - t0 > spin_limit || *(volatile int *)d->err) {
-                                atomicExch(d->err, 1);
-                                ok = 0;
-                                break;
-                            }
-                        }
-                        s_sok = ok;
-                    }
-                    named_sync(2, kSelThreads);
-                    __threadfence_block();
-                    if (!s_sok) {
-                        st = ST_TIMEOUT;
-                    } else {
-                        const T piva = colA[pa];
-                        Cand e = cand_empty();
-                        for (int j = c0 + stid; j < c1; j += kSelThreads) {
-                            T r = lds(A + (long long)pa * P + j);
-#pragma unroll
-                            for (int k = 0; k < kBlk; ++k)
-                                if (k < np)
-                                    r = (pa == pp[k]) ? sprow[k][j - c0]
-                                                      : tfma(-pc[k][pa], sprow[k][j - c0], r);
-                            const T pra = r / piva;
-                            spa[j - c0] = pra;
-                            const unsigned long long zk = okey(tfma(-colA[m], pra, sz[j - c0]));
-                            if (j < N - 1 && zk < lim_d) cand_take(e, nblandb ? zero_k : zk, j, j);
-                        }
-                        e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
-                        if (stid == 0) {
-                            recB[g] = e;
-                            unsigned long long *v = valB + (size_t)g * kBlkVals;
-                            for (int k = 0; k <= np; ++k) {
-                                const T *row = k < np ? sprow[k] : spa;
-                                v[k] = e.idx >= 0 ? tbits(row[e.idx - c0]) : 0ull;
-                                v[3 + k] = rv >= 0 ? tbits(row[N - 1 - c0]) : 0ull;
-                            }
-                            red_add_release(pcnt, 1u);
-                        }
-                        // ---- pivot b (Step 2): the pricing records ----
-                        if (stid == 0) s_sok = (int)wait_ctr(pcnt, tB, d->err, spin_limit);
-                        named_sync(2, kSelThreads);
-                        unsigned long long kb = 0ull;
-                        if (!s_sok) {
-                            st = ST_TIMEOUT;
-                        } else {
-                            Cand f = cand_empty();
-                            for (int k = stid; k < G; k += kSelThreads) {
-                                const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recB) + k));
-                                if (cand_less(r, f)) {
-                                    f = r;
-                                    kb = (unsigned long long)k;
-                                }
-                            }
-                            const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
-                            nnp = 1;
-                            if (sel.idx < 0) npend = ST_OPTIMAL;
-                            else if (iters + np + 1 >= iter_limit) npend = ST_ITER_LIMIT;
-                            else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
-                            else qb = sel.idx;
-                            if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                        }
-                        if (st == ST_RUNNING && qb >= 0) {
-                            T pvq[kBlk + 1], pvr[kBlk + 1];
-#pragma unroll
-                            for (int k = 0; k <= kBlk; ++k) {
-                                pvq[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
-                                pvr[k] = tfrom<T>(__ldcg(valB + (size_t)rowner * kBlkVals + 3 + k));
-                            }
-                            // column q_b and rhs after pivot a, every row (Step 3)
-                            T *ncol = nc[1];
-                            unsigned long long lmin = ~0ull;
-                            for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                                T av[kSelRows], hv[kSelRows];
-#pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
-                                    const int i = i0 + u * kSelThreads;
-                                    av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
-                                    hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
-                                }
-#pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
-                                    const int i = i0 + u * kSelThreads;
-                                    if (i >= M) break;
-                                    const T ca = colA[i];
-                                    T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
-                                    a = (i == pa) ? pvq[np] : tfma(-ca, pvq[np], a);
-                                    ncol[i] = a;
-                                    if (i < m) {
-                                        T h = blk_apply<T>(hv[u], i, np, pp, pc, pvr);
-                                        h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], h);
-                                        const T num = pos_part(h);
-                                        const unsigned long long rk =
-                                            okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                                        snum[i] = num;
-                                        srk[i] = rk;
-                                        lmin = rk < lmin ? rk : lmin;
-                                    }
-                                }
-                            }
-                            const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
-                            if (rstar == ~0ull) {
-                                npend = ST_UNBOUNDED;
-                            } else {
-                                const unsigned long long thr = screen_thr(rstar, (T)0);
-                                unsigned first = 0xffffffffu, cnt = 0;
-                                for (int i = stid; i < m; i += kSelThreads)
-                                    if (srk[i] <= thr) {
-                                        first = (unsigned)i < first ? (unsigned)i : first;
-                                        ++cnt;
-                                    }
-                                unsigned gfirst, gcnt;
-                                sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
-                                if (gcnt == 1) {
-                                    pb = (int)gfirst;
-                                    rzb = srk[pb] == zero_k;
-                                } else {
-                                    Cand rc = cand_empty();
-                                    for (int i = stid; i < m; i += kSelThreads)
-                                        if (srk[i] <= thr) {
-                                            const T nm = snum[i];
-                                            const unsigned long long vk =
-                                                tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
-                                            const int key = nblandb ? (i == pa ? qa : bkey(i)) : i;
-                                            cand_take(rc, vk, key, i);
-                                        }
-                                    rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
-                                    pb = rc.idx;
-                                    rzb = rc.vk == zero_k;
-                                }
-                                nnp = 2;
-                            }
-                        }
-                    }
-                }
-            }
-            named_sync(2, kSelThreads);
-            if (stid == 0) {
-                s_status = st;
-                s_np = nnp;
-                s_pend = npend;
-                s_p[0] = pa;
-                s_q[0] = qa;
-                s_p[1] = pb;
-                s_q[1] = qb;
-                s_rz[0] = rza;
-                s_rz[1] = rzb;
-            }
-        }
-        // the CTA's pass and its selection of the next pass are done
-        __syncthreads();
-        iters += np;
-        ++lk;
-        status = s_status;
-        if (status == ST_RUNNING) {
-            np = s_np;
-            pend = s_pend;
-            for (int k = 0; k < kBlk; ++k) {
-                pp[k] = s_p[k];
-                qq[k] = s_q[k];
-            }
-            deg = s_rz[0] ? deg + 1 : 0;
-            if (np > 1) deg = s_rz[1] ? deg + 1 : 0;
-            cb = (cb + 2) & 3;
-        }
-        cur ^= 1;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
-        }
-    }
-
-    if (g == 0 && tid == 0) {
-        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
-        d->iters = iters;
-        d->iter_limit = iter_limit;
-        d->deg = deg;
-        d->T = bufs[cur];  // hand over the buffer holding the last tableau
-        d->T2 = bufs[cur ^ 1];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Two pivots per pass for the dual form (dual simplex), double-buffered.
-//
-// The pass is the two-pivot primal kernel's (the same update warps' code:
-// Step 4 for both pivots on the strip, then both elementary operations per
-// element in order).  The selection warps choose the next two pivots from the
-// pass's source buffer: leaving row r_a from the rhs of T2 (every CTA, all
-// rows), row r_a of T2 on the CTA's strip and its dual ratio test, one
-// record per CTA (with the pass's pivot-row values at its column) for the
-// entering column q_a, column q_a of T2 (every CTA, all rows); then the rhs
-// after pivot a (from values already in scratch), leaving row r_b, row r_b
-// after pivot a on the strip, a second round of records for q_b, column q_b
-// after pivot a.
-template <typename T, int SW>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_block_dual_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
-    typedef typename Vec<T>::type V;
-    constexpr int VW = Vec<T>::W;
-    constexpr int kSelThreads = 32 * SW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Cand rbuf[2][32];
-    __shared__ Cand selc[SW];
-    __shared__ unsigned long long selq[SW];
-    __shared__ int s_flag, s_status, s_sok, s_np, s_pend;
-    __shared__ volatile int s_zready;
-    __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
-
-    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
-    const int NU = B - kSelThreads;
-    const int lane = tid & 31;
-    const bool selw = tid >= NU;
-    const int stid = tid - NU;
-    T *bufs[2] = {reinterpret_cast<T *>(d->T), reinterpret_cast<T *>(d->T2)};
-    int cur = 0;
-    const long long P = d->P;
-    const int m = d->m, M = d->M, N = d->N;
-    int *__restrict__ basis = d->basis;
-    const int bland_after = d->bland_after;
-    const unsigned long long lim_np = okey((T)(-d->eps_p));
-    const unsigned long long lim_r = okey((T)(-d->eps_r));
-    const unsigned long long zero_k = okey((T)0);
-    long long iters = d->iters;
-    const long long iter_limit =
-        iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
-    int deg = d->deg;
-    int status = ST_RUNNING;
-    unsigned *rcnt = d->bar + 128;
-
-    const int c0 = g * W;
-    const int c1 = (int)min((long long)c0 + W, P);
-    const int jend = min(c1, N - 1);
-    const int vpr = (c1 - c0) / VW;
-    const int rpp = NU / vpr;
-    const int lr = tid / vpr, lv = tid - lr * vpr;
-    const bool active = !selw && lr < rpp;
-    const int col0 = c0 + lv * VW;
-    // shared memory: the pass's pivot rows on the strip, the objective row of
-    // T2 on the strip, row r_a of T2 on the strip; scratch: four pivot
-    // columns, the rhs of T2
-    const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
-    T *sprow[kBlk] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + wbytes)};
-    T *sz = reinterpret_cast<T *>(smem_raw + 2 * wbytes);
-    T *sra = reinterpret_cast<T *>(smem_raw + 3 * wbytes);
-    unsigned char *sc = d->scratch_stride > 0
-                            ? reinterpret_cast<unsigned char *>(d->scratch) +
-                                  (size_t)g * (size_t)d->scratch_stride
-                            : smem_raw + 4 * wbytes;
-    const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
-    T *scol[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) scol[k] = reinterpret_cast<T *>(sc + k * cbytes);
-    T *srhs = reinterpret_cast<T *>(sc + 4 * cbytes);
-
-    // ---- the first pivot from the current tableau (all threads) ----
-    int p = -1, q = -1;
-    {
-        const T *A = bufs[0];
-        const int bland = deg >= bland_after;
-        Cand c = cand_empty();
-        for (int i = tid; i < m; i += B) {
-            const unsigned long long vk = okey(lds(A + (long long)i * P + (N - 1)));
-            if (vk < lim_r) cand_take(c, bland ? zero_k : vk, bland ? __ldcg(basis + i) : i, i);
-        }
-        c = block_min_c(c, rbuf[0]);
-        if (c.idx < 0) status = ST_OPTIMAL;
-        else if (iters >= iter_limit) status = ST_ITER_LIMIT;
-        else p = c.idx;
-        if (status == ST_RUNNING) {
-            const T *rowr = A + (long long)p * P, *z = A + (long long)m * P;
-            Cand e = cand_empty();
-            for (int j = c0 + tid; j < jend; j += B) {
-                const T a = lds(rowr + j);
-                if (okey(a) < lim_np) cand_take(e, okey(pos_part(lds(z + j)) / neg(a)), j, j);
-            }
-            e = block_min_c(e, rbuf[1]);
-            if (tid == 0) d->part_sel[g] = e;
-            if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
-            if (status == ST_RUNNING) {
-                const Cand sel = load_partials_min(d->part_sel, G, rbuf[0]);
-                if (sel.idx < 0) {
-                    status = ST_INFEASIBLE;
-                } else if (sel.idx >= N - 1) {
-                    status = ST_TIMEOUT;  // never: a partial from outside the row
-                } else {
-                    q = sel.idx;
-                    deg = (sel.vk == zero_k) ? deg + 1 : 0;
-                    for (int i = tid; i < M; i += B) scol[0][i] = lds(A + (long long)i * P + q);
-                }
-            }
-        }
-    }
-    int np = 1, pend = ST_RUNNING;
-    int pp[kBlk] = {p, -1}, qq[kBlk] = {q, -1};
-    int cb = 0;
-    unsigned lk = 0;
-    if (tid == 0) s_zready = 0;
-    __syncthreads();
-
-    while (status == ST_RUNNING) {
-        const T *A = bufs[cur];
-        T *Bn = bufs[cur ^ 1];
-        const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
-        T *nc[kBlk] = {scol[(cb + 2) & 3], scol[(cb + 3) & 3]};
-        const int par = lk & 1;
-        Cand *recA = d->part_sel + (2 * par) * G, *recB = d->part_sel + (2 * par + 1) * G;
-        unsigned long long *valA = d->part_vals + (size_t)(2 * par) * G * kBlkVals;
-        unsigned long long *valB = d->part_vals + (size_t)(2 * par + 1) * G * kBlkVals;
-        const unsigned tA = (unsigned)G * (2u * lk + 1u), tB = (unsigned)G * (2u * lk + 2u);
-        (void)lane;
-        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
-            for (int k = 0; k < np; ++k) {
-                if (iters + k < d->trace_cap) {
-                    d->trace[2 * (iters + k)] = pp[k];
-                    d->trace[2 * (iters + k) + 1] = qq[k];
-                }
-                basis[pp[k]] = qq[k];
-            }
-            d->last_p = pp[np - 1];
-            d->last_q = qq[np - 1];
-        }
-        const int nbland = deg >= bland_after;  // rule of pivot a's selection
-        const bool select = pend == ST_RUNNING;
-        if (!selw) {
-            // Step 4 for the pass's pivots on this CTA's strip
-            for (int j = c0 + tid; j < c1; j += NU) {
-                const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
-                sprow[0][j - c0] = r;
-                if (np > 1) {
-                    const T t = (pp[1] == pp[0]) ? r
-                                                 : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + j));
-                    sprow[1][j - c0] = t / pc[1][pp[1]];
-                }
-            }
-            named_sync(1, NU);
-            // the strip of the objective row of T2, also for the selection
-            if (tid < vpr) {
-                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
-#pragma unroll
-                for (int k = 0; k < kBlk; ++k)
-                    if (k < np) vfma(zt, pc[k][m], *reinterpret_cast<const V *>(sprow[k] + tid * VW));
-                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
-                *reinterpret_cast<V *>(sz + tid * VW) = zt;
-            }
-            named_sync(1, NU);
-            if (tid == 0) {
-                __threadfence_block();
-                s_zready = (int)(lk + 1);  // sz, sprow of this pass ready for the selection
-            }
-            // Step 5 for the pass's pivots on the constraint rows of the strip
-            if (active && np == 2) {
-                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
-                const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
-                const int p0 = pp[0], p1 = pp[1];
-                const T *__restrict__ c0p = pc[0];
-                const T *__restrict__ c1p = pc[1];
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
-                    t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
-                    t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p1, c1p[i1], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p1, c1p[i2], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p1, c1p[i3], pr1);
-                }
-                for (; i < m; i += rpp) {
-                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
-                }
-            } else if (active) {
-                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
-                const int p0 = pp[0];
-                const T *__restrict__ c0p = pc[0];
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
-                }
-                for (; i < m; i += rpp) {
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                }
-            }
-        } else {
-            // selection of the next pass's pivots a and b (dual simplex)
-            int st = ST_RUNNING, nnp = 0, npend = ST_RUNNING;
-            int pa = -1, qa = -1, pb = -1, qb = -1, rza = 0, rzb = 0;
-            auto bkey = [&](int i) -> int {  // the basic variable of row i after the pass
-                if (np > 1 && i == pp[1]) return qq[1];
-                if (i == pp[0]) return qq[0];
-                return __ldcg(basis + i);
-            };
-            T *colA = nc[0];
-            if (!select) {
-                st = pend;  // the previous pass's selection already ended the solve
-            } else {
-                // the pass's pivot-row values at the rhs (the update warps' Step 4 values)
-                T pvr[kBlk];
-                {
-                    const T r = lds(A + (long long)pp[0] * P + (N - 1)) / pc[0][pp[0]];
-                    pvr[0] = r;
-                    pvr[1] = (T)0;
-                    if (np > 1) {
-                        const T t = (pp[1] == pp[0])
-                                        ? r
-                                        : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + (N - 1)));
-                        pvr[1] = t / pc[1][pp[1]];
-                    }
-                }
-                // ---- pivot a: the leaving row from the rhs of T2, every row ----
-                Cand c = cand_empty();
-                for (int i0 = stid; i0 < m; i0 += kSelRows * kSelThreads) {
-                    T hv[kSelRows];
-#pragma unroll
-                    for (int u = 0; u < kSelRows; ++u) {
-                        const int i = i0 + u * kSelThreads;
-                        hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kSelRows; ++u) {
-                        const int i = i0 + u * kSelThreads;
-                        if (i >= m) break;
-                        const T h = blk_apply<T>(hv[u], i, np, pp, pc, pvr);
-                        srhs[i] = h;
-                        const unsigned long long vk = okey(h);
-                        if (vk < lim_r) cand_take(c, nbland ? zero_k : vk, nbland ? bkey(i) : i, i);
-                    }
-                }
-                c = sel_min<SW>(c, 0ull, selc, selq, nullptr);
-                if (c.idx < 0) st = ST_OPTIMAL;
-                else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
-                else if (c.idx >= m) st = ST_TIMEOUT;  // never: a row outside the tableau
-                else pa = c.idx;
-                if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                if (st == ST_RUNNING) {
-                    // this pass's sprow and sz from the update warps
-                    if (stid == 0) {
-                        const long long t0 = clock64();
-                        int ok = 1;
-                        while (s_zready < (int)(lk + 1)) {
-                            if (clock64() - t0 > spin_limit || *(volatile int *)d->err) {
-                                atomicExch(d->err, 1);
-                                ok = 0;
-                                break;
-                            }
-                        }
-                        s_sok = ok;
-                    }
-                    named_sync(2, kSelThreads);
-                    __threadfence_block();
-                    if (!s_sok) st = ST_TIMEOUT;
-                }
-                unsigned long long ka = 0ull;
-                if (st == ST_RUNNING) {
-                    // row r_a of T2 on this strip and its dual ratio test; the record
-                    Cand e = cand_empty();
-                    for (int j = c0 + stid; j < c1; j += kSelThreads) {
-                        T x = lds(A + (long long)pa * P + j);
-#pragma unroll
-                        for (int k = 0; k < kBlk; ++k)
-                            if (k < np)
-                                x = (pa == pp[k]) ? sprow[k][j - c0] : tfma(-pc[k][pa], sprow[k][j - c0], x);
-                        sra[j - c0] = x;
-                        if (j < jend && okey(x) < lim_np)
-                            cand_take(e, okey(pos_part(sz[j - c0]) / neg(x)), j, j);
-                    }
-                    e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
-                    if (stid == 0) {
-                        recA[g] = e;
-                        unsigned long long *v = valA + (size_t)g * kBlkVals;
-                        for (int k = 0; k < np; ++k) v[k] = e.idx >= 0 ? tbits(sprow[k][e.idx - c0]) : 0ull;
-                        red_add_release(rcnt, 1u);
-                        s_sok = (int)wait_ctr(rcnt, tA, d->err, spin_limit);
-                    }
-                    named_sync(2, kSelThreads);
-                    if (!s_sok) {
-                        st = ST_TIMEOUT;
-                    } else {
-                        Cand f = cand_empty();
-                        for (int k = stid; k < G; k += kSelThreads) {
-                            const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recA) + k));
-                            if (cand_less(r, f)) {
-                                f = r;
-                                ka = (unsigned long long)k;
-                            }
-                        }
-                        const Cand sel = sel_min<SW>(f, ka, selc, selq, &ka);
-                        if (sel.idx < 0) st = ST_INFEASIBLE;
-                        else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
-                        else {
-                            qa = sel.idx;
-                            rza = sel.vk == zero_k;
-                        }
-                        if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                    }
-                }
-                if (st == ST_RUNNING) {
-                    // column q_a of T2, every row: the next pass's first pivot column
-                    T pvq[kBlk];
-#pragma unroll
-                    for (int k = 0; k < kBlk; ++k) pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
-                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                        T av[kSelRows];
-#pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
-                            const int i = i0 + u * kSelThreads;
-                            av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
-                        }
-#pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
-                            const int i = i0 + u * kSelThreads;
-                            if (i >= M) break;
-                            colA[i] = blk_apply<T>(av[u], i, np, pp, pc, pvq);
-                        }
-                    }
-                    named_sync(2, kSelThreads);
-                    // ---- pivot b: the rhs after pivot a and its leaving row ----
-                    const T piva = colA[pa];
-                    const T pra = srhs[pa] / piva;  // pivot a's row at the rhs
-                    const int nblandb = (rza ? deg + 1 : 0) >= bland_after;
-                    Cand cb2 = cand_empty();
-                    for (int i = stid; i < m; i += kSelThreads) {
-                        const T h = (i == pa) ? pra : tfma(-colA[i], pra, srhs[i]);
-                        const unsigned long long vk = okey(h);
-                        if (vk < lim_r)
-                            cand_take(cb2, nblandb ? zero_k : vk,
-                                      nblandb ? (i == pa ? qa : bkey(i)) : i, i);
-                    }
-                    cb2 = sel_min<SW>(cb2, 0ull, selc, selq, nullptr);
-                    nnp = 1;
-                    if (cb2.idx < 0) npend = ST_OPTIMAL;
-                    else if (iters + np + 1 >= iter_limit) npend = ST_ITER_LIMIT;
-                    else if (cb2.idx >= m) st = ST_TIMEOUT;  // never
-                    else pb = cb2.idx;
-                    if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                    if (st == ST_RUNNING && pb >= 0) {
-                        // row r_b after pivot a on this strip, its dual ratio test;
-                        // the record carries the pivot-row values at its column
-                        Cand e = cand_empty();
-                        const T cab = colA[pb], cam = colA[m];
-                        for (int j = c0 + stid; j < c1; j += kSelThreads) {
-                            T x = lds(A + (long long)pb * P + j);
-#pragma unroll
-                            for (int k = 0; k < kBlk; ++k)
-                                if (k < np)
-                                    x = (pb == pp[k]) ? sprow[k][j - c0] : tfma(-pc[k][pb], sprow[k][j - c0], x);
-                            const T prj = sra[j - c0] / piva;  // pivot a's row at column j
-                            x = (pb == pa) ? prj : tfma(-cab, prj, x);
-                            if (j < jend && okey(x) < lim_np) {
-                                const T z3 = tfma(-cam, prj, sz[j - c0]);
-                                cand_take(e, okey(pos_part(z3) / neg(x)), j, j);
-                            }
-                        }
-                        e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
-                        if (stid == 0) {
-                            recB[g] = e;
-                            unsigned long long *v = valB + (size_t)g * kBlkVals;
-                            for (int k = 0; k < np; ++k) v[k] = e.idx >= 0 ? tbits(sprow[k][e.idx - c0]) : 0ull;
-                            v[np] = e.idx >= 0 ? tbits(sra[e.idx - c0] / piva) : 0ull;
-                            red_add_release(rcnt, 1u);
-                            s_sok = (int)wait_ctr(rcnt, tB, d->err, spin_limit);
-                        }
-                        named_sync(2, kSelThreads);
-                        unsigned long long kb = 0ull;
-                        if (!s_sok) {
-                            st = ST_TIMEOUT;
-                        } else {
-                            Cand f = cand_empty();
-                            for (int k = stid; k < G; k += kSelThreads) {
-                                const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recB) + k));
-                                if (cand_less(r, f)) {
-                                    f = r;
-                                    kb = (unsigned long long)k;
-                                }
-                            }
-                            const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
-                            if (sel.idx < 0) npend = ST_INFEASIBLE;
-                            else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
-                            else {
-                                qb = sel.idx;
-                                rzb = sel.vk == zero_k;
-                            }
-                            if (st == ST_TIMEOUT && stid == 0) atomicExch(d->err, 1);
-                        }
-                        if (st == ST_RUNNING && qb >= 0) {
-                            // column q_b after pivot a, every row
-                            T pvb[kBlk + 1];
-#pragma unroll
-                            for (int k = 0; k <= kBlk; ++k) pvb[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
-                            T *colB = nc[1];
-                            for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                                T av[kSelRows];
-#pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
-                                    const int i = i0 + u * kSelThreads;
-                                    av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
-                                }
-#pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
-                                    const int i = i0 + u * kSelThreads;
-                                    if (i >= M) break;
-                                    const T t = blk_apply<T>(av[u], i, np, pp, pc, pvb);
-                                    colB[i] = (i == pa) ? pvb[np] : tfma(-colA[i], pvb[np], t);
-                                }
-                            }
-                            nnp = 2;
-                        }
-                    }
-                }
-            }
-            named_sync(2, kSelThreads);
-            if (stid == 0) {
-                s_status = st;
-                s_np = nnp;
-                s_pend = npend;
-                s_p[0] = pa;
-                s_q[0] = qa;
-                s_p[1] = pb;
-                s_q[1] = qb;
-                s_rz[0] = rza;
-                s_rz[1] = rzb;
-            }
-        }
-        // the CTA's pass and its selection of the next pass are done
-        __syncthreads();
-        iters += np;
-        ++lk;
-        status = s_status;
-        if (status == ST_RUNNING) {
-            np = s_np;
-            pend = s_pend;
-            for (int k = 0; k < kBlk; ++k) {
-                pp[k] = s_p[k];
-                qq[k] = s_q[k];
-            }
-            deg = s_rz[0] ? deg + 1 : 0;
-            if (np > 1) deg = s_rz[1] ? deg + 1 : 0;
-            cb = (cb + 2) & 3;
-        }
-        cur ^= 1;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
-        }
-    }
-
-    if (g == 0 && tid == 0) {
-        d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
-        d->iters = iters;
-        d->iter_limit = iter_limit;
-        d->deg = deg;
-        d->T = bufs[cur];  // hand over the buffer holding the last tableau
-        d->T2 = bufs[cur ^ 1];
-    }
 }
 
 constexpr int kBatchThreads = 512;  // register room for both pivot rules in one kernel
@@ -2793,102 +877,6 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
     // A cooperative launch fails instead of running when the grid cannot be
     // co-resident, which the grid barrier needs.
     return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
-}
-
-cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
-                              long long spin_limit, long long budget, cudaStream_t s) {
-    int W = sh.strip;
-    int dbm = sh.pipe == 2 ? 1 : 0;
-    void *args[] = {&d_desc, &W, &spin_limit, &budget, &dbm};
-    if (sh.pipe == 3) {  // two pivots per pass
-        void *bargs[] = {&d_desc, &W, &spin_limit, &budget};
-        const bool w8 = sh.sel_warps == 8;
-        const void *fn = sh.dual ? (prec == PREC_FP64
-                                        ? (w8 ? (const void *)pivot_block_dual_kernel<double, 8>
-                                              : (const void *)pivot_block_dual_kernel<double, 4>)
-                                        : (w8 ? (const void *)pivot_block_dual_kernel<float, 8>
-                                              : (const void *)pivot_block_dual_kernel<float, 4>))
-                         : prec == PREC_FP64
-                             ? (w8 ? (const void *)pivot_block_kernel<double, 8>
-                                   : (const void *)pivot_block_kernel<double, 4>)
-                             : (w8 ? (const void *)pivot_block_kernel<float, 8>
-                                   : (const void *)pivot_block_kernel<float, 4>);
-        if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sh.smem_bytes);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), bargs,
-                                           sh.smem_bytes, s);
-    }
-    if (sh.dual) {
-        const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_dual_kernel<double, 4>
-                                           : (const void *)pivot_pipe_dual_kernel<float, 4>;
-        if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sh.smem_bytes);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args,
-                                           sh.smem_bytes, s);
-    }
-    const void *fn = prec == PREC_FP64
-                         ? (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<double, 2>
-                                         : (const void *)pivot_pipe_kernel<double, 4>)
-                         : (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<float, 2>
-                                         : (const void *)pivot_pipe_kernel<float, 4>);
-    if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sh.smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);
-}
-
-// Launch shape of the pipelined kernel: strips sized for the update threads
-// (all but the last warp), shared memory for the strip and the selection
-// warp's block of rows.
-PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas,
-                             int dual) {
-    PivotShape sh;
-    const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
-    const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    sh.threads = threads > 0 ? threads : kMaxThreads;
-    sh.threads = std::min(kMaxThreads, std::max(2 * kSelThreadsMax, (sh.threads + 31) / 32 * 32));
-    const int nu = sh.threads - kSelThreadsMax;
-    long long g = ctas > 0 ? ctas : std::min<long long>(sms, ((long long)M * P + 32767) / 32768);
-    const long long gmin = (P + (long long)nu * vw - 1) / ((long long)nu * vw);
-    g = std::max<long long>(std::max<long long>(g, gmin), 1);
-    long long w = (P + g - 1) / g;
-    w = (w + sector - 1) / sector * sector;
-    if (w > (long long)nu * vw) w = (long long)nu * vw / sector * sector;
-    sh.strip = (int)w;
-    sh.ctas = (int)((P + w - 1) / w);
-    // the pivot columns of two pivots and the ratio numerators and screening
-    // keys (primal), or the strip of the new objective row (dual)
-    const size_t cbytes = ((size_t)M * esz + 15) & ~(size_t)15;
-    const size_t sprow = ((size_t)w * esz + 15) & ~(size_t)15;
-    // (dual == 2: the two-pivot kernel, four pivot rows and columns)
-    // (dual == 3: the two-pivot dual kernel, four pivot rows and columns and the rhs)
-    const size_t scratch = dual == 1   ? sprow + 2 * cbytes
-                           : dual == 2 ? 5 * cbytes + (size_t)M * sizeof(unsigned long long)
-                           : dual == 3 ? 5 * cbytes
-                                       : 3 * cbytes + (size_t)M * sizeof(unsigned long long);
-    const size_t fixed = dual >= 2 ? 4 * sprow : sprow;
-    if (fixed + scratch <= kMaxDynSmem) {
-        sh.use_smem = 1;
-        sh.smem_bytes = fixed + scratch;
-        sh.scratch_stride = 0;
-    } else {
-        sh.use_smem = 0;
-        sh.smem_bytes = fixed;
-        sh.scratch_stride = (long long)((scratch + 255) & ~(size_t)255);
-    }
-    sh.dual = dual == 1 || dual == 3;
-    // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
-    // launch), the strip one pass of the update threads
-    sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw;
-    return sh;
 }
 
 cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing *ring_dev,
