@@ -67,7 +67,8 @@ using namespace dev;
 // the warps); the two-pivot kernel takes four or eight.  kSelThreadsMax sizes
 // the launch shape for any of them.
 constexpr int kSelThreadsMax = 256;
-constexpr int kSelRows = 4;
+constexpr int kSelRows = 4;  // rows in flight per selection thread, two loads each
+constexpr int kColRows = 8;  // the same with one load per row
 
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
@@ -238,13 +239,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const int lr = tid / vpr, lv = tid - lr * vpr;
     const bool active = !selw && lr < rpp;
     const int col0 = c0 + lv * VW;
-    // the vector of this strip holding the rhs column, or -1; in place it is
-    // protected from the bulk update until every selection has read it
+    // the vector of this strip holding the rhs column, or -1
     const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
-    const int rvp = db ? -1 : rv;
     // scratch: the strip of the pivot row in shared memory; the pivot columns
-    // of this and the next pivot, the ratio numerators and the screening keys
-    // in shared memory, or in this CTA's slice of global scratch
+    // of this and the next pivot, the rhs column of the current tableau (kept
+    // here from pivot to pivot, so the selection never reads it from the
+    // tableau) and the screening keys in shared memory, or in this CTA's
+    // slice of global scratch
     T *sprow = reinterpret_cast<T *>(smem_raw);
     unsigned char *sc = d->scratch_stride > 0
                             ? reinterpret_cast<unsigned char *>(d->scratch) +
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             : smem_raw + (((size_t)W * sizeof(T) + 15) & ~(size_t)15);
     const size_t cbytes = ((size_t)M * sizeof(T) + 15) & ~(size_t)15;
     T *scol[2] = {reinterpret_cast<T *>(sc), reinterpret_cast<T *>(sc + cbytes)};
-    T *snum = reinterpret_cast<T *>(sc + 2 * cbytes);
+    T *srhs = reinterpret_cast<T *>(sc + 2 * cbytes);
     unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 3 * cbytes);
 
     // ---- selection of the first pivot from the current tableau (all threads) ----
@@ -282,9 +283,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 const T a = lds(Tab + (long long)i * P + q);
                 scol[0][i] = a;
                 if (i < m) {
-                    const T num = pos_part(lds(Tab + (long long)i * P + (N - 1)));
-                    const unsigned long long rk = okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                    snum[i] = num;
+                    const T rhs = lds(Tab + (long long)i * P + (N - 1));
+                    const unsigned long long rk =
+                        okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
+                    srhs[i] = rhs;
                     srk[i] = rk;
                     lmin = rk < lmin ? rk : lmin;
                 }
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 Cand rc = cand_empty();
                 for (int i = tid; i < m; i += B)
                     if (srk[i] <= thr)
-                        cand_take(rc, okey(snum[i] / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
+                        cand_take(rc, okey(pos_part(srhs[i]) / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
                 rc = block_min_c(rc, rbuf[0]);
                 p = rc.idx;
                 deg = (rc.vk == zero_k) ? deg + 1 : 0;
@@ -358,10 +360,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
             named_sync(1, NU);
             const int jv = s_jv;  // protected: the vector of the CTA's candidate
-            if (zown && tid != jv && tid != rvp)
+            if (zown && tid != jv)
                 *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
             // Step 5 on the constraint rows of the strip, but the protected vectors
-            if (active && lv != jv && lv != rvp) {
+            if (active && lv != jv) {
                 const V pr = *reinterpret_cast<const V *>(sprow + lv * VW);
                 const T *abase = A + col0;
                 T *bbase = Bn + col0;
@@ -385,19 +387,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 }
             }
             // in place: every CTA's selection is done reading the protected
-            // vectors, then update them (double-buffered: nothing to protect)
+            // vector, then update it (double-buffered: nothing to protect)
             if (tid == 0) s_uok = db ? 1 : (int)wait_ctr(rcnt, target, d->err, spin_limit);
             named_sync(1, NU);
-            if (s_uok && !db) {
-                for (int k = 0; k < 2; ++k) {
-                    const int v = k == 0 ? jv : (rvp != jv ? rvp : -1);
-                    if (v < 0) continue;
-                    const V vpr_ = *reinterpret_cast<const V *>(sprow + v * VW);
-                    T *vbase = Bn + c0 + v * VW;
-                    for (int i = tid; i < M; i += NU) {
-                        V *p0 = reinterpret_cast<V *>(vbase + (long long)i * P);
-                        *p0 = pivot_vec<T>(ldv(p0), i, p, col[i], vpr_);
-                    }
+            if (s_uok && !db && jv >= 0) {
+                const V vpr_ = *reinterpret_cast<const V *>(sprow + jv * VW);
+                T *vbase = Bn + c0 + jv * VW;
+                for (int i = tid; i < M; i += NU) {
+                    V *p0 = reinterpret_cast<V *>(vbase + (long long)i * P);
+                    *p0 = pivot_vec<T>(ldv(p0), i, p, col[i], vpr_);
                 }
             }
         } else {
@@ -450,27 +448,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     // column q' and rhs of tableau k+1, every row, and Step 3
                     const T prq = tfrom<T>(prq_b), prr = tfrom<T>(prr_b);
                     unsigned long long lmin = ~0ull;
-                    // kSelRows rows per thread in flight (the loads are L2 round trips)
-                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                        T av[kSelRows], hv[kSelRows];
+                    // kColRows rows per thread in flight (the loads are L2 round trips)
+                    for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                        T av[kColRows];
 #pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
+                        for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
                             av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
-                            hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
                         }
 #pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
+                        for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
                             if (i >= M) break;
                             const T ci = col[i];
                             const T a = (i == p) ? prq : tfma(-ci, prq, av[u]);
                             ncol[i] = a;
                             if (i < m) {
-                                const T num = pos_part((i == p) ? prr : tfma(-ci, prr, hv[u]));
+                                const T rhs = (i == p) ? prr : tfma(-ci, prr, srhs[i]);
+                                srhs[i] = rhs;
                                 const unsigned long long rk =
-                                    okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                                snum[i] = num;
+                                    okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
                                 srk[i] = rk;
                                 lmin = rk < lmin ? rk : lmin;
                             }
@@ -499,7 +496,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             Cand rc = cand_empty();
                             for (int i = stid; i < m; i += kSelThreads)
                                 if (srk[i] <= thr) {
-                                    const T nm = snum[i];
+                                    const T nm = pos_part(srhs[i]);
                                     const unsigned long long vk =
                                         tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
                                     const int key = nbland ? (i == p ? q : __ldcg(basis + i)) : i;
@@ -956,7 +953,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // shared memory: the pass's pivot rows on the strip, the objective row of
     // T2 on the strip, pivot a's row on the strip; scratch (shared or this
     // CTA's global slice): four pivot columns (this pass's two, the next
-    // pass's two), ratio numerators, screening keys
+    // pass's two), the rhs column of the pass's source tableau (kept from
+    // pass to pass, so the selection never reads it from the tableau),
+    // screening keys
     const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
     T *sprow[kBlk] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + wbytes)};
     T *sz = reinterpret_cast<T *>(smem_raw + 2 * wbytes);
@@ -969,7 +968,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     T *scol[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) scol[k] = reinterpret_cast<T *>(sc + k * cbytes);
-    T *snum = reinterpret_cast<T *>(sc + 4 * cbytes);
+    T *srhs = reinterpret_cast<T *>(sc + 4 * cbytes);
     unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 5 * cbytes);
 
     // ---- selection of the first pivot from the current tableau (all threads) ----
@@ -999,9 +998,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 const T a = lds(Tab + (long long)i * P + q);
                 scol[0][i] = a;
                 if (i < m) {
-                    const T num = pos_part(lds(Tab + (long long)i * P + (N - 1)));
-                    const unsigned long long rk = okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                    snum[i] = num;
+                    const T rhs = lds(Tab + (long long)i * P + (N - 1));
+                    const unsigned long long rk =
+                        okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
+                    srhs[i] = rhs;
                     srk[i] = rk;
                     lmin = rk < lmin ? rk : lmin;
                 }
@@ -1014,7 +1014,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 Cand rc = cand_empty();
                 for (int i = tid; i < m; i += B)
                     if (srk[i] <= thr)
-                        cand_take(rc, okey(snum[i] / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
+                        cand_take(rc, okey(pos_part(srhs[i]) / scol[0][i]), bland ? __ldcg(basis + i) : i, i);
                 rc = block_min_c(rc, rbuf[0]);
                 p = rc.idx;
                 deg = (rc.vk == zero_k) ? deg + 1 : 0;
@@ -1198,28 +1198,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
                         pvr[k] = tfrom<T>(__ldcg(valA + (size_t)rowner * kBlkVals + 3 + k));
                     }
-                    // column q_a and rhs of T2, every row (Step 3)
+                    // column q_a and rhs of T2, every row (Step 3); the rhs from
+                    // the one of T0 kept in scratch, which becomes T2's
                     T *ncol = nc[0];
                     unsigned long long lmin = ~0ull;
-                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                        T av[kSelRows], hv[kSelRows];
+                    for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                        T av[kColRows];
 #pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
+                        for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
                             av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
-                            hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
                         }
 #pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
+                        for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
                             if (i >= M) break;
                             const T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
                             ncol[i] = a;
                             if (i < m) {
-                                const T num = pos_part(blk_apply<T>(hv[u], i, np, pp, pc, pvr));
+                                const T rhs = blk_apply<T>(srhs[i], i, np, pp, pc, pvr);
+                                srhs[i] = rhs;
                                 const unsigned long long rk =
-                                    okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                                snum[i] = num;
+                                    okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
                                 srk[i] = rk;
                                 lmin = rk < lmin ? rk : lmin;
                             }
@@ -1245,7 +1245,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             Cand rc = cand_empty();
                             for (int i = stid; i < m; i += kSelThreads)
                                 if (srk[i] <= thr) {
-                                    const T nm = snum[i];
+                                    const T nm = pos_part(srhs[i]);
                                     const unsigned long long vk =
                                         tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
                                     cand_take(rc, vk, nbland ? bkey(i) : i, i);
@@ -1332,19 +1332,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                 pvq[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
                                 pvr[k] = tfrom<T>(__ldcg(valB + (size_t)rowner * kBlkVals + 3 + k));
                             }
-                            // column q_b and rhs after pivot a, every row (Step 3)
+                            // column q_b and rhs after pivot a, every row (Step 3);
+                            // scratch keeps T2's rhs for the next pass
                             T *ncol = nc[1];
                             unsigned long long lmin = ~0ull;
-                            for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                                T av[kSelRows], hv[kSelRows];
+                            for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                                T av[kColRows];
 #pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
+                                for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
                                     av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
-                                    hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
                                 }
 #pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
+                                for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
                                     if (i >= M) break;
                                     const T ca = colA[i];
@@ -1352,12 +1352,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                     a = (i == pa) ? pvq[np] : tfma(-ca, pvq[np], a);
                                     ncol[i] = a;
                                     if (i < m) {
-                                        T h = blk_apply<T>(hv[u], i, np, pp, pc, pvr);
-                                        h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], h);
-                                        const T num = pos_part(h);
+                                        const T h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], srhs[i]);
                                         const unsigned long long rk =
-                                            okey(a) > lim_p ? screen_key(num, a) : ~0ull;
-                                        snum[i] = num;
+                                            okey(a) > lim_p ? screen_key(pos_part(h), a) : ~0ull;
                                         srk[i] = rk;
                                         lmin = rk < lmin ? rk : lmin;
                                     }
@@ -1383,7 +1380,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                     Cand rc = cand_empty();
                                     for (int i = stid; i < m; i += kSelThreads)
                                         if (srk[i] <= thr) {
-                                            const T nm = snum[i];
+                                            const T nm = pos_part((i == pa) ? pvr[np]
+                                                                            : tfma(-colA[i], pvr[np], srhs[i]));
                                             const unsigned long long vk =
                                                 tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
                                             const int key = nblandb ? (i == pa ? qa : bkey(i)) : i;
@@ -1503,7 +1501,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const int col0 = c0 + lv * VW;
     // shared memory: the pass's pivot rows on the strip, the objective row of
     // T2 on the strip, row r_a of T2 on the strip; scratch: four pivot
-    // columns, the rhs of T2
+    // columns, the rhs column of the pass's source tableau (kept from pass to
+    // pass, so the selection never reads it from the tableau)
     const size_t wbytes = ((size_t)W * sizeof(T) + 15) & ~(size_t)15;
     T *sprow[kBlk] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw + wbytes)};
     T *sz = reinterpret_cast<T *>(smem_raw + 2 * wbytes);
@@ -1525,7 +1524,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int bland = deg >= bland_after;
         Cand c = cand_empty();
         for (int i = tid; i < m; i += B) {
-            const unsigned long long vk = okey(lds(A + (long long)i * P + (N - 1)));
+            const T rhs = lds(A + (long long)i * P + (N - 1));
+            srhs[i] = rhs;
+            const unsigned long long vk = okey(rhs);
             if (vk < lim_r) cand_take(c, bland ? zero_k : vk, bland ? __ldcg(basis + i) : i, i);
         }
         c = block_min_c(c, rbuf[0]);
@@ -1692,24 +1693,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         pvr[1] = t / pc[1][pp[1]];
                     }
                 }
-                // ---- pivot a: the leaving row from the rhs of T2, every row ----
+                // ---- pivot a: the leaving row from the rhs of T2, every row
+                // (from the rhs of T0 kept in scratch, which becomes T2's) ----
                 Cand c = cand_empty();
-                for (int i0 = stid; i0 < m; i0 += kSelRows * kSelThreads) {
-                    T hv[kSelRows];
-#pragma unroll
-                    for (int u = 0; u < kSelRows; ++u) {
-                        const int i = i0 + u * kSelThreads;
-                        hv[u] = i < m ? lds(A + (long long)i * P + (N - 1)) : (T)0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kSelRows; ++u) {
-                        const int i = i0 + u * kSelThreads;
-                        if (i >= m) break;
-                        const T h = blk_apply<T>(hv[u], i, np, pp, pc, pvr);
-                        srhs[i] = h;
-                        const unsigned long long vk = okey(h);
-                        if (vk < lim_r) cand_take(c, nbland ? zero_k : vk, nbland ? bkey(i) : i, i);
-                    }
+                for (int i = stid; i < m; i += kSelThreads) {
+                    const T h = blk_apply<T>(srhs[i], i, np, pp, pc, pvr);
+                    srhs[i] = h;
+                    const unsigned long long vk = okey(h);
+                    if (vk < lim_r) cand_take(c, nbland ? zero_k : vk, nbland ? bkey(i) : i, i);
                 }
                 c = sel_min<SW>(c, 0ull, selc, selq, nullptr);
                 if (c.idx < 0) st = ST_OPTIMAL;
@@ -1784,15 +1775,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     T pvq[kBlk];
 #pragma unroll
                     for (int k = 0; k < kBlk; ++k) pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
-                    for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                        T av[kSelRows];
+                    for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                        T av[kColRows];
 #pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
+                        for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
                             av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
                         }
 #pragma unroll
-                        for (int u = 0; u < kSelRows; ++u) {
+                        for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
                             if (i >= M) break;
                             colA[i] = blk_apply<T>(av[u], i, np, pp, pc, pvq);
@@ -1873,15 +1864,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
                             for (int k = 0; k <= kBlk; ++k) pvb[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
                             T *colB = nc[1];
-                            for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
-                                T av[kSelRows];
+                            for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                                T av[kColRows];
 #pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
+                                for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
                                     av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
                                 }
 #pragma unroll
-                                for (int u = 0; u < kSelRows; ++u) {
+                                for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
                                     if (i >= M) break;
                                     const T t = blk_apply<T>(av[u], i, np, pp, pc, pvb);
