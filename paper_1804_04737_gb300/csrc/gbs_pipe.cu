@@ -44,17 +44,19 @@ using namespace dev;
 //                    scratch;
 //   selection warps  reduce the pricing records to the entering column q'
 //                    (Step 2), form the whole column q' and rhs of tableau k+1
-//                    from tableau k with the very fma the update uses (so the
-//                    values are bit for bit those the update writes) into the
-//                    CTA's scratch, and run the screened ratio test on them
-//                    (Step 3).  Every CTA does this redundantly, so the pivot
-//                    row needs no exchange between CTAs.
-// In place (tableaus that fit L2), the vectors the selection reads (each
-// CTA's own pricing winner, which is where the entering column always is, and
-// the rhs) are left out of the bulk update and updated once a counter shows
-// every CTA's selection done reading them.  There is no grid barrier: a CTA
-// publishes its pricing record only after finishing its previous pivot, so
-// the pricing counter also proves every vector the selection reads is current,
+//                    with the very fma the update uses (so the values are bit
+//                    for bit those the update writes) into the CTA's scratch,
+//                    and run the screened ratio test on them (Step 3).  Every
+//                    CTA does this redundantly, so the pivot row needs no
+//                    exchange between CTAs.  The column comes from tableau k;
+//                    the rhs from the CTA's own copy of the rhs column, which
+//                    it carries in scratch from pivot to pivot.
+// In place (tableaus that fit L2), the vector the selection reads (each CTA's
+// own pricing winner, which is where the entering column always is) is left
+// out of the bulk update and updated once a counter shows every CTA's
+// selection done reading it.  There is no grid barrier: a CTA publishes its
+// pricing record only after finishing its previous pivot, so the pricing
+// counter also proves every vector the selection reads is current,
 // and no CTA runs more than one pivot ahead of another (records are
 // double-buffered by pivot parity).  Double-buffered (larger tableaus), pivot
 // k reads one buffer and writes the other, with a grid barrier per pivot to
