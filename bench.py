@@ -63,10 +63,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# The kernel each LP of the set runs on (default options): primal LPs whose
-# tableau fits L2 (up to 96 MB) on the pipelined primal kernel in place,
-# larger ones on the two-pivots-per-pass kernel (double-buffered), the dual
-# form on the two-pivots-per-pass dual simplex kernel (double-buffered).
+# The kernel each LP of the set runs on (default options): primal LPs below
+# 2^19 tableau elements on the pipelined primal kernel in place, larger ones
+# on the two-pivots-per-pass kernel (double-buffered), the dual form on the
+# two-pivots-per-pass dual simplex kernel (double-buffered).
 INPLACE_KERNEL = "pivot_pipe_kernel<double> (in place)"
 BLOCK_KERNEL = "pivot_block_kernel<double> (two pivots per pass)"
 DUAL_KERNEL = "pivot_block_dual_kernel<double> (dual simplex, two pivots per pass)"
@@ -81,7 +81,7 @@ def kernel_of(m, n, sense):
     if sense != MAX_LE:
         return DUAL_KERNEL
     pitch = (n + m + 1 + 31) // 32 * 32
-    return INPLACE_KERNEL if (m + 1) * pitch * 8 <= 96 * 2 ** 20 else BLOCK_KERNEL
+    return INPLACE_KERNEL if (m + 1) * pitch < 2 ** 19 else BLOCK_KERNEL
 
 
 def kernel_traffic(name):

@@ -113,16 +113,18 @@ typedef struct {
     int pipeline;            /* single-LP primal simplex kernel:
                                 0 = selection, then update (one launch-wide
                                     grid barrier per pivot);
-                                1 = auto (default): 2 when the tableau fits the
-                                    L2 cache (up to 96 MB), else 4; 0 when the
-                                    second buffer cannot be allocated;
+                                1 = auto (default): 2 below 2^19 tableau
+                                    elements ((m+1) x row pitch), else 4; 2
+                                    when the second buffer cannot be
+                                    allocated;
                                 2 = pipelined in place: the next pivot's
                                     selection overlaps this pivot's update, no
                                     grid barrier;
                                 3 = pipelined, double-buffered tableau (twice
                                     the memory), a grid barrier per pivot;
-                                4 = as 3, two pivots per pass over the tableau
-                                    (half the tableau traffic per pivot).
+                                4 = double-buffered, two pivots per pass over
+                                    the tableau (half the tableau traffic per
+                                    pivot), no grid barrier between passes.
                                 The dual rule (LP_MIN_GE, and FP32 recovery)
                                 always runs double-buffered: one pivot per pass
                                 for 2 and 3, two for 1 and 4.

@@ -20,16 +20,17 @@
 
 using namespace gbs;
 
-// Tableaus up to this size stay resident in the 129 MB L2 cache across
-// pivots when updated in place; the pipelined kernel runs in place below it
-// and double-buffered above it.
-constexpr size_t kL2FitBytes = 96ull << 20;
-// Above kL2FitBytes the kernel applies two pivots per pass (half the tableau
-// traffic per pivot).  Below this size its selection of two pivots is the
-// longer chain and gets eight warps, from it on four (measured: 4096 x 512
-// (152 MB) 51.3 us per pivot with eight, 60.5 with four, 57.9 with one pivot
-// per pass; 8192^2 FP64 (1.07 GB) 249 with four, 253 with eight, 370 with
-// one pivot per pass).
+// From this many tableau elements on, the primal simplex applies two pivots
+// per pass (double-buffered, half the tableau traffic per pivot); below it
+// the pipelined kernel runs in place, whose shorter chain wins on small
+// tableaus.  Measured per pivot, FP64, one pivot per pass in place / two per
+// pass: 256^2 9.3 / 9.4 us, 512^2 10.4 / 10.3, 1024^2 14.2 / 13.3, 2048^2
+// 27.5 / 24.3, 3000^2 65.6 / 41.4 (the in-place tableau no longer fits L2).
+constexpr long long kBlockElems = 1ll << 19;
+// Below this size the two-pivot selection is the longer chain and gets eight
+// warps, from it on four (measured: 4096 x 512 (152 MB) 51.3 us per pivot
+// with eight, 60.5 with four, 57.9 with one pivot per pass; 8192^2 FP64
+// (1.07 GB) 249 with four, 253 with eight, 370 with one pivot per pass).
 constexpr size_t kBlockBytes = 384ull << 20;
 
 struct lp_handle {
@@ -273,7 +274,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
     // the pipelined kernels where they can take the LP: the primal rule in
-    // place for tableaus that fit L2 and double-buffered above, the dual rule
+    // place for small tableaus and two pivots per pass above, the dual rule
     // double-buffered (the rule runs for its sense, and in FP32 mode for both)
     if (h->opt.pipeline < 0 || h->opt.pipeline > 4) {
         set_err(h, "lp_load: unknown pipeline mode %d", h->opt.pipeline);
@@ -283,7 +284,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32;
     int pmode = primal ? h->opt.pipeline : 0;
     const size_t tbytes = (size_t)M * P * esz;
-    if (pmode == 1) pmode = tbytes <= kL2FitBytes ? 2 : 4;
+    if (pmode == 1) pmode = (long long)M * P >= kBlockElems ? 4 : 2;
     const bool dwant = dualr && h->opt.pipeline != 0;
     bool have_t2 = false;
     if (pmode >= 3 || dwant) {
@@ -295,7 +296,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
             set_err(h, "lp_load: no device memory for the second tableau buffer (pipeline 3)");
             return LP_ERR_OOM;
         }
-        pmode = 0;
+        pmode = 2;  // automatic mode without room for a second buffer: in place
     }
     const bool dpipe = dwant && have_t2;
     auto shape_for = [&](int rule) {

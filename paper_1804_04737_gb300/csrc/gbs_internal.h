@@ -76,7 +76,9 @@ struct PivotShape {
 // Words of a pivot launch's synchronisation block (zeroed before each launch):
 // [0] grid-barrier count, [32] its generation, [64] readers counter (in-place
 // kernel) or pricing-records counter (pipelined kernel), [96] error flag,
-// [128] selections-done counter (pipelined kernel); 128-byte apart.
+// [128] selections-done counter (one-pivot pipelined kernels) or records
+// counter (two-pivot dual kernel), [160] selections-done counter (two-pivot
+// kernels); 128-byte apart.
 constexpr int kBarWords = 256;
 
 struct InputStats {

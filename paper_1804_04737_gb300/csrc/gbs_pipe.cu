@@ -34,7 +34,7 @@ using namespace dev;
 // ---------------------------------------------------------------------------
 // Pipelined primal simplex for one LP (FP64 or FP32 tableau).
 //
-// In every CTA the last kSelWarps warps select pivot k+1 while the others
+// In every CTA the last SW warps select pivot k+1 while the others
 // stream pivot k's update of the CTA's column strip:
 //   update warps     divide the strip of the pivot row (Step 4), update the
 //                    strip of the objective row and publish the CTA's pricing
@@ -107,6 +107,40 @@ __device__ __forceinline__ Cand unpack_cand(const ulonglong2 &v) {
     return e;
 }
 
+// This selection thread's minimum over the G records stid, stid + NT, ...,
+// with a tag of its winner: vals[k].x when vals is given, else the record
+// index k.  The records of one thread are loaded in one batch (up to 256
+// records in all), so the scan is one memory round trip, not one per record.
+template <int NT>
+__device__ __forceinline__ Cand scan_records(const Cand *rec, const ulonglong2 *vals, int G,
+                                             int stid, unsigned long long *tag) {
+    constexpr int R = NT >= 256 ? 1 : 256 / NT;
+    Cand e = cand_empty();
+    unsigned long long et = 0ull;
+    for (int k0 = stid; k0 < G; k0 += R * NT) {
+        ulonglong2 rb[R];
+        unsigned long long vb[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int k = k0 + u * NT;
+            rb[u] = k < G ? __ldcg(reinterpret_cast<const ulonglong2 *>(rec) + k)
+                          : make_ulonglong2(~0ull, ~0ull);
+            vb[u] = vals != nullptr && k < G ? __ldcg(&vals[k].x) : (unsigned long long)k;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (k0 + u * NT >= G) break;
+            const Cand r = unpack_cand(rb[u]);
+            if (cand_less(r, e)) {
+                e = r;
+                et = vb[u];
+            }
+        }
+    }
+    *tag = et;
+    return e;
+}
+
 // Bounded wait of one thread until *ctr reaches target; false when it ran out
 // or another CTA reported a timeout.
 __device__ __forceinline__ bool wait_ctr(unsigned *ctr, unsigned target, int *err,
@@ -122,7 +156,7 @@ __device__ __forceinline__ bool wait_ctr(unsigned *ctr, unsigned target, int *er
 }
 
 // Selection-group minimum of a candidate and its 64-bit payload: the warps'
-// minima go through sc[]/sq[] (kSelWarps entries) and a named barrier; every
+// minima go through sc[]/sq[] (SW entries) and a named barrier; every
 // selection thread gets the result.
 template <int SW>
 __device__ __forceinline__ Cand sel_min(Cand c, unsigned long long q, Cand *sc,
@@ -195,7 +229,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                       int dbm) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
-    constexpr int kSelWarps = SW, kSelThreads = 32 * SW;
+    constexpr int kSelThreads = 32 * SW;  // the last SW warps select
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Cand rbuf[2][32];
     __shared__ unsigned long long ubuf[32];
@@ -323,19 +357,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
         if (!selw) {
             const T piv = col[p];
+            // the strip of the objective row is loaded with the pivot row's:
+            // both head the chain to the next pricing record
+            V zt;
+            const bool zown = tid < vpr;
+            if (zown) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
             // Step 4 on this CTA's strip of the pivot row
             for (int j = c0 + tid; j < c1; j += NU)
                 sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
             named_sync(1, NU);
-            // the strip of the objective row, held back in registers, and the
-            // CTA's pricing candidate for pivot k+1
+            // the new strip of the objective row, held back in registers, and
+            // the CTA's pricing candidate for pivot k+1
             Cand c = cand_empty();
-            V zt;
-            const bool zown = tid < vpr;
             if (zown) {
                 const T colm = col[m];
                 const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
-                zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
                 vfma(zt, colm, pr);
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
@@ -428,16 +464,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 st = ST_TIMEOUT;
             } else {
                 // Step 2: the entering column from the G pricing records
-                Cand e = cand_empty();
-                unsigned long long eq = 0ull;
-                for (int k = stid; k < G; k += kSelThreads) {
-                    const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(psel) + k));
-                    const unsigned long long rq = __ldcg(&pval[k].x);
-                    if (cand_less(r, e)) {
-                        e = r;
-                        eq = rq;
-                    }
-                }
+                unsigned long long eq;
+                const Cand e = scan_records<kSelThreads>(psel, pval, G, stid, &eq);
                 const unsigned long long prr_b = __ldcg(&pval[rowner].y);
                 unsigned long long prq_b;
                 const Cand sel = sel_min<SW>(e, eq, selc, selq, &prq_b);
@@ -450,31 +478,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     // column q' and rhs of tableau k+1, every row, and Step 3
                     const T prq = tfrom<T>(prq_b), prr = tfrom<T>(prr_b);
                     unsigned long long lmin = ~0ull;
-                    // kColRows rows per thread in flight (the loads are L2 round trips)
-                    for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                    // kColRows constraint rows per thread in flight (the loads
+                    // are L2 round trips); the objective row's entry rides
+                    // with the first batch, so that m = 2^k rows take 2^k /
+                    // (kColRows * kSelThreads) batches, not one more
+                    const T am = stid == 0 ? lds(A + (long long)m * P + nq) : (T)0;
+                    for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
                         T av[kColRows];
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
+                            av[u] = i < m ? lds(A + (long long)i * P + nq) : (T)0;
                         }
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            if (i >= M) break;
+                            if (i >= m) break;
                             const T ci = col[i];
                             const T a = (i == p) ? prq : tfma(-ci, prq, av[u]);
                             ncol[i] = a;
-                            if (i < m) {
-                                const T rhs = (i == p) ? prr : tfma(-ci, prr, srhs[i]);
-                                srhs[i] = rhs;
-                                const unsigned long long rk =
-                                    okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
-                                srk[i] = rk;
-                                lmin = rk < lmin ? rk : lmin;
-                            }
+                            const T rhs = (i == p) ? prr : tfma(-ci, prr, srhs[i]);
+                            srhs[i] = rhs;
+                            const unsigned long long rk =
+                                okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
+                            srk[i] = rk;
+                            lmin = rk < lmin ? rk : lmin;
                         }
                     }
+                    if (stid == 0) ncol[m] = tfma(-col[m], prq, am);  // p < m
                     const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
                     if (rstar == ~0ull) {
                         st = ST_UNBOUNDED;
@@ -690,15 +721,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int nbland = deg >= bland_after;  // rule of pivot k+1's selection
         const T piv = col[p];
         if (!selw) {
+            // the strip of the objective row is loaded with the pivot row's
+            V zt;
+            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
             // Step 4 on this CTA's strip of the pivot row
             for (int j = c0 + tid; j < c1; j += NU)
                 sprow[j - c0] = lds(A + (long long)p * P + j) / piv;
             named_sync(1, NU);
-            // the strip of the objective row, also kept for the selection
+            // the new strip of the objective row, also kept for the selection
             if (tid < vpr) {
                 const T colm = col[m];
                 const V pr = *reinterpret_cast<const V *>(sprow + tid * VW);
-                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
                 vfma(zt, colm, pr);
                 *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
                 *reinterpret_cast<V *>(sz + tid * VW) = zt;
@@ -792,16 +825,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     st = ST_TIMEOUT;
                 } else {
                     // entering column from the G records, with its pivot-row value
-                    Cand e = cand_empty();
-                    unsigned long long eq = 0ull;
-                    for (int k = stid; k < G; k += kSelThreads) {
-                        const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(psel) + k));
-                        const unsigned long long rq = __ldcg(&pval[k].x);
-                        if (cand_less(r, e)) {
-                            e = r;
-                            eq = rq;
-                        }
-                    }
+                    unsigned long long eq;
+                    const Cand e = scan_records<kSelThreads>(psel, pval, G, stid, &eq);
                     unsigned long long prq_b;
                     const Cand sel = sel_min<SW>(e, eq, selc, selq, &prq_b);
                     if (sel.idx < 0) {
@@ -814,20 +839,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         rzero = sel.vk == zero_k;
                         // column q' of tableau k+1: the next pivot column
                         const T prq = tfrom<T>(prq_b);
-                        for (int i0 = stid; i0 < M; i0 += kSelRows * kSelThreads) {
+                        // the objective row's entry rides with the first batch
+                        const T am = stid == 0 ? lds(A + (long long)m * P + nq) : (T)0;
+                        for (int i0 = stid; i0 < m; i0 += kSelRows * kSelThreads) {
                             T av[kSelRows];
 #pragma unroll
                             for (int u = 0; u < kSelRows; ++u) {
                                 const int i = i0 + u * kSelThreads;
-                                av[u] = i < M ? lds(A + (long long)i * P + nq) : (T)0;
+                                av[u] = i < m ? lds(A + (long long)i * P + nq) : (T)0;
                             }
 #pragma unroll
                             for (int u = 0; u < kSelRows; ++u) {
                                 const int i = i0 + u * kSelThreads;
-                                if (i >= M) break;
+                                if (i >= m) break;
                                 ncol[i] = (i == p) ? prq : tfma(-col[i], prq, av[u]);
                             }
                         }
+                        if (stid == 0) ncol[m] = tfma(-col[m], prq, am);  // p < m
                     }
                 }
             }
@@ -888,10 +916,60 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 //      q_b; column q_b and rhs after pivot a in every CTA -> p_b.
 // A pass holds one pivot when the next pivot ends the solve (optimal,
 // unbounded, iteration limit); the first pass of a launch holds the first
-// pivot alone.  A grid barrier ends each pass.
+// pivot alone.
+//
+// No grid barrier separates the passes: a CTA starts pass k+1 when its own
+// pass k is done.  Its pass-k+1 pricing record proves to every reader that
+// its strip of T2 is written; before it writes into bufs[cur] again (pass k+1
+// writes what pass k read), it waits until every CTA's selection of pass k
+// has counted itself done.  That wait overlaps its own start of pass k+1
+// (pivot rows, objective row, record), so pass k+1's selection starts
+// without waiting for the slowest CTA of pass k.
 
 constexpr int kBlk = 2;       // pivots per pass
 constexpr int kBlkVals = 8;   // values per record: 3 at the record's column, 3 at the rhs, 2 unused
+constexpr int kMaxRecs = 256; // CTAs of a two-pivot launch (records copied to shared memory)
+
+// scan_records over one round of two-pivot records, which also copies the
+// first NV values of every record (vals + k * kBlkVals) to tab[k * NV + v] in
+// shared memory, loaded in the same batch as the records: after the selection
+// group's next barrier every thread reads the winner's values from there,
+// without another round trip to memory (a round trip costs several
+// microseconds while the update streams the tableau).
+template <int NT, int NV>
+__device__ __forceinline__ Cand scan_records_tab(const Cand *rec, const unsigned long long *vals,
+                                                 int G, int stid, unsigned long long *tag,
+                                                 unsigned long long *tab) {
+    constexpr int R = NT >= 256 ? 1 : 256 / NT;
+    Cand e = cand_empty();
+    unsigned long long et = 0ull;
+    for (int k0 = stid; k0 < G; k0 += R * NT) {
+        ulonglong2 rb[R];
+        unsigned long long vb[R][NV];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int k = k0 + u * NT;
+            rb[u] = k < G ? __ldcg(reinterpret_cast<const ulonglong2 *>(rec) + k)
+                          : make_ulonglong2(~0ull, ~0ull);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) vb[u][v] = k < G ? __ldcg(vals + (size_t)k * kBlkVals + v) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int k = k0 + u * NT;
+            if (k >= G) break;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tab[k * NV + v] = vb[u][v];
+            const Cand r = unpack_cand(rb[u]);
+            if (cand_less(r, e)) {
+                e = r;
+                et = (unsigned long long)k;
+            }
+        }
+    }
+    *tag = et;
+    return e;
+}
 
 // x after the pass's pivots 0..np-1, for row i (pv: their pivot-row values at
 // the column of x).
@@ -917,9 +995,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand selc[SW];
     __shared__ unsigned long long selq[SW];
     __shared__ unsigned sela[SW], selb[SW];
-    __shared__ int s_flag, s_status, s_sok, s_np, s_pend;
+    __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend;
     __shared__ volatile int s_zready;  // passes whose objective-row strip is in sz
     __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
+    __shared__ unsigned long long s_tab[kMaxRecs * (kBlk + 1)];  // the records' values
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     const int NU = B - kSelThreads;
@@ -940,7 +1019,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
     int deg = d->deg;
     int status = ST_RUNNING;
-    unsigned *pcnt = d->bar + 64;
+    // pcnt counts pricing records; scnt counts selections done (the first
+    // selection, then one per pass), after which the CTA reads no more of the
+    // pass's source tableau
+    unsigned *pcnt = d->bar + 64, *scnt = d->bar + 160;
 
     // strip and thread map of the update threads
     const int c0 = g * W;
@@ -985,10 +1067,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
         }
         c = block_min_c(c, rbuf[0]);
-        if (tid == 0) d->part_sel[g] = c;
+        // in the slots of pass 1's first records: pass 0 writes its records
+        // while slower CTAs may still read these, pass 1 only after every
+        // CTA's pass-0 selection, which follows this one
+        if (tid == 0) d->part_sel[2 * G + g] = c;
         if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
-            const Cand sel = load_partials_min(d->part_sel, G, rbuf[1]);
+            const Cand sel = load_partials_min(d->part_sel + 2 * G, G, rbuf[1]);
             if (sel.idx < 0) status = ST_OPTIMAL;
             else if (iters >= iter_limit) status = ST_ITER_LIMIT;
             else if (sel.idx >= N - 1) status = ST_TIMEOUT;  // never: a partial from outside the row
@@ -1032,6 +1117,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     unsigned lk = 0;     // passes made in this launch
     if (tid == 0) s_zready = 0;
     __syncthreads();
+    if (tid == 0 && status != ST_TIMEOUT) red_add_release(scnt, 1u);  // the first selection
     while (status == ST_RUNNING) {
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
@@ -1042,20 +1128,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         unsigned long long *valA = d->part_vals + (size_t)(2 * par) * G * kBlkVals;
         unsigned long long *valB = d->part_vals + (size_t)(2 * par + 1) * G * kBlkVals;
         const unsigned tA = (unsigned)G * (2u * lk + 1u), tB = (unsigned)G * (2u * lk + 2u);
-        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
-            for (int k = 0; k < np; ++k) {
-                if (iters + k < d->trace_cap) {
-                    d->trace[2 * (iters + k)] = pp[k];
-                    d->trace[2 * (iters + k) + 1] = qq[k];
-                }
-                basis[pp[k]] = qq[k];
-            }
-            d->last_p = pp[np - 1];
-            d->last_q = qq[np - 1];
-        }
         const int nbland = deg >= bland_after;  // rule of pivot a's selection
         const bool select = pend == ST_RUNNING;
         if (!selw) {
+            // the strip of the objective row is loaded with the pivot rows'
+            V zt;
+            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
             // Step 4 for the pass's pivots on this CTA's strip
             for (int j = c0 + tid; j < c1; j += NU) {
                 const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
@@ -1067,14 +1145,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 }
             }
             named_sync(1, NU);
-            // the strip of the objective row of T2, and the CTA's pricing record a
+            // the new strip of the objective row of T2, and the CTA's pricing record a
             Cand c = cand_empty();
             if (tid < vpr) {
-                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
 #pragma unroll
                 for (int k = 0; k < kBlk; ++k)
                     if (k < np) vfma(zt, pc[k][m], *reinterpret_cast<const V *>(sprow[k] + tid * VW));
-                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
                 *reinterpret_cast<V *>(sz + tid * VW) = zt;
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
@@ -1101,10 +1177,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     }
                     __threadfence_block();
                     s_zready = (int)(lk + 1);  // sz, sprow of this pass ready for the selection
+                    // This pass writes the previous pass's source: every CTA's
+                    // selections so far must be done reading it (and the
+                    // basis, whose entries for this pass's pivots CTA 0 writes
+                    // now: this pass's selection never reads them, the next
+                    // pass's reads them after this CTA's next record).  The
+                    // wait overlaps the selection of this pass, which needs
+                    // only the records.
+                    const int ok = (int)wait_ctr(scnt, (unsigned)G * (lk + 1u), d->err, spin_limit);
+                    if (ok && g == 0) {
+                        for (int k = 0; k < np; ++k) {
+                            if (iters + k < d->trace_cap) {
+                                d->trace[2 * (iters + k)] = pp[k];
+                                d->trace[2 * (iters + k) + 1] = qq[k];
+                            }
+                            basis[pp[k]] = qq[k];
+                        }
+                        d->last_p = pp[np - 1];
+                        d->last_q = qq[np - 1];
+                    }
+                    s_uok = ok;
                 }
             }
+            named_sync(1, NU);
+            const bool upd = active && s_uok;
+            if (s_uok && tid < vpr) *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
             // Step 5 for the pass's pivots on the constraint rows of the strip
-            if (active && np == 2) {
+            if (upd && np == 2) {
                 const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
                 const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
                 const int p0 = pp[0], p1 = pp[1];
@@ -1133,7 +1232,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
                     *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
                 }
-            } else if (active) {
+            } else if (upd) {
                 const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
                 const int p0 = pp[0];
                 const T *__restrict__ c0p = pc[0];
@@ -1174,17 +1273,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 if (stid == 0) s_sok = (int)wait_ctr(pcnt, tA, d->err, spin_limit);
                 named_sync(2, kSelThreads);
                 unsigned long long ka = 0ull;
+                unsigned long long rvb[kBlk];  // the rhs owner's values, loaded with the records
                 if (!s_sok) {
                     st = ST_TIMEOUT;
                 } else {
-                    Cand e = cand_empty();
-                    for (int k = stid; k < G; k += kSelThreads) {
-                        const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recA) + k));
-                        if (cand_less(r, e)) {
-                            e = r;
-                            ka = (unsigned long long)k;
-                        }
-                    }
+#pragma unroll
+                    for (int k = 0; k < kBlk; ++k) rvb[k] = __ldcg(valA + (size_t)rowner * kBlkVals + 3 + k);
+                    const Cand e = scan_records_tab<kSelThreads, kBlk>(recA, valA, G, stid, &ka, s_tab);
                     const Cand sel = sel_min<SW>(e, ka, selc, selq, &ka);
                     if (sel.idx < 0) st = ST_OPTIMAL;
                     else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
@@ -1197,36 +1292,37 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     T pvq[kBlk], pvr[kBlk];
 #pragma unroll
                     for (int k = 0; k < kBlk; ++k) {
-                        pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
-                        pvr[k] = tfrom<T>(__ldcg(valA + (size_t)rowner * kBlkVals + 3 + k));
+                        pvq[k] = tfrom<T>(s_tab[ka * kBlk + k]);
+                        pvr[k] = tfrom<T>(rvb[k]);
                     }
                     // column q_a and rhs of T2, every row (Step 3); the rhs from
                     // the one of T0 kept in scratch, which becomes T2's
                     T *ncol = nc[0];
                     unsigned long long lmin = ~0ull;
-                    for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                    // the objective row's entry rides with the first batch
+                    const T am = stid == 0 ? lds(A + (long long)m * P + qa) : (T)0;
+                    for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
                         T av[kColRows];
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
+                            av[u] = i < m ? lds(A + (long long)i * P + qa) : (T)0;
                         }
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            if (i >= M) break;
+                            if (i >= m) break;
                             const T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
                             ncol[i] = a;
-                            if (i < m) {
-                                const T rhs = blk_apply<T>(srhs[i], i, np, pp, pc, pvr);
-                                srhs[i] = rhs;
-                                const unsigned long long rk =
-                                    okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
-                                srk[i] = rk;
-                                lmin = rk < lmin ? rk : lmin;
-                            }
+                            const T rhs = blk_apply<T>(srhs[i], i, np, pp, pc, pvr);
+                            srhs[i] = rhs;
+                            const unsigned long long rk =
+                                okey(a) > lim_p ? screen_key(pos_part(rhs), a) : ~0ull;
+                            srk[i] = rk;
+                            lmin = rk < lmin ? rk : lmin;
                         }
                     }
+                    if (stid == 0) ncol[m] = blk_apply<T>(am, m, np, pp, pc, pvq);
                     const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
                     if (rstar == ~0ull) {
                         st = ST_UNBOUNDED;
@@ -1308,17 +1404,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         if (stid == 0) s_sok = (int)wait_ctr(pcnt, tB, d->err, spin_limit);
                         named_sync(2, kSelThreads);
                         unsigned long long kb = 0ull;
+                        unsigned long long rvb[kBlk + 1];  // the rhs owner's values
                         if (!s_sok) {
                             st = ST_TIMEOUT;
                         } else {
-                            Cand f = cand_empty();
-                            for (int k = stid; k < G; k += kSelThreads) {
-                                const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recB) + k));
-                                if (cand_less(r, f)) {
-                                    f = r;
-                                    kb = (unsigned long long)k;
-                                }
-                            }
+#pragma unroll
+                            for (int k = 0; k <= kBlk; ++k)
+                                rvb[k] = __ldcg(valB + (size_t)rowner * kBlkVals + 3 + k);
+                            const Cand f = scan_records_tab<kSelThreads, kBlk + 1>(recB, valB, G, stid, &kb, s_tab);
                             const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
                             nnp = 1;
                             if (sel.idx < 0) npend = ST_OPTIMAL;
@@ -1331,37 +1424,38 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             T pvq[kBlk + 1], pvr[kBlk + 1];
 #pragma unroll
                             for (int k = 0; k <= kBlk; ++k) {
-                                pvq[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
-                                pvr[k] = tfrom<T>(__ldcg(valB + (size_t)rowner * kBlkVals + 3 + k));
+                                pvq[k] = tfrom<T>(s_tab[kb * (kBlk + 1) + k]);
+                                pvr[k] = tfrom<T>(rvb[k]);
                             }
                             // column q_b and rhs after pivot a, every row (Step 3);
                             // scratch keeps T2's rhs for the next pass
                             T *ncol = nc[1];
                             unsigned long long lmin = ~0ull;
-                            for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                            const T am = stid == 0 ? lds(A + (long long)m * P + qb) : (T)0;
+                            for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
                                 T av[kColRows];
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
+                                    av[u] = i < m ? lds(A + (long long)i * P + qb) : (T)0;
                                 }
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    if (i >= M) break;
+                                    if (i >= m) break;
                                     const T ca = colA[i];
                                     T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
                                     a = (i == pa) ? pvq[np] : tfma(-ca, pvq[np], a);
                                     ncol[i] = a;
-                                    if (i < m) {
-                                        const T h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], srhs[i]);
-                                        const unsigned long long rk =
-                                            okey(a) > lim_p ? screen_key(pos_part(h), a) : ~0ull;
-                                        srk[i] = rk;
-                                        lmin = rk < lmin ? rk : lmin;
-                                    }
+                                    const T h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], srhs[i]);
+                                    const unsigned long long rk =
+                                        okey(a) > lim_p ? screen_key(pos_part(h), a) : ~0ull;
+                                    srk[i] = rk;
+                                    lmin = rk < lmin ? rk : lmin;
                                 }
                             }
+                            if (stid == 0)  // pa < m
+                                ncol[m] = tfma(-colA[m], pvq[np], blk_apply<T>(am, m, np, pp, pc, pvq));
                             const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
                             if (rstar == ~0ull) {
                                 npend = ST_UNBOUNDED;
@@ -1399,8 +1493,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     }
                 }
             }
+            // every selection thread is done reading this pass's source
             named_sync(2, kSelThreads);
             if (stid == 0) {
+                if (st != ST_TIMEOUT) red_add_release(scnt, 1u);
                 s_status = st;
                 s_np = nnp;
                 s_pend = npend;
@@ -1417,6 +1513,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         iters += np;
         ++lk;
         status = s_status;
+        if (!s_uok) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
             np = s_np;
             pend = s_pend;
@@ -1429,13 +1526,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             cb = (cb + 2) & 3;
         }
         cur ^= 1;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
-        }
+        // no grid barrier: a CTA starts the next pass as soon as its own is
+        // done; the counters order everything that crosses CTAs
     }
 
     if (g == 0 && tid == 0) {
+        // every CTA's last selection is done, and with it its last wait
+        wait_ctr(scnt, (unsigned)G * (lk + 1u), d->err, spin_limit);
         d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
         d->iters = iters;
         d->iter_limit = iter_limit;
@@ -1457,7 +1554,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // entering column q_a, column q_a of T2 (every CTA, all rows); then the rhs
 // after pivot a (from values already in scratch), leaving row r_b, row r_b
 // after pivot a on the strip, a second round of records for q_b, column q_b
-// after pivot a.
+// after pivot a.  As in the primal kernel, no grid barrier separates the
+// passes: a counter of selections done guards the rewrite of the source.
 template <typename T, int SW>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_block_dual_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
@@ -1468,9 +1566,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand rbuf[2][32];
     __shared__ Cand selc[SW];
     __shared__ unsigned long long selq[SW];
-    __shared__ int s_flag, s_status, s_sok, s_np, s_pend;
+    __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend;
     __shared__ volatile int s_zready;
     __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
+    __shared__ unsigned long long s_tab[kMaxRecs * (kBlk + 1)];  // the records' values
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     const int NU = B - kSelThreads;
@@ -1491,7 +1590,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         iters > 0x3fffffffffffffffll - budget ? 0x3fffffffffffffffll : iters + budget;
     int deg = d->deg;
     int status = ST_RUNNING;
-    unsigned *rcnt = d->bar + 128;
+    // rcnt counts the records; scnt the selections done (the first, then one
+    // per pass), as in the primal kernel
+    unsigned *rcnt = d->bar + 128, *scnt = d->bar + 160;
 
     const int c0 = g * W;
     const int c1 = (int)min((long long)c0 + W, P);
@@ -1543,10 +1644,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 if (okey(a) < lim_np) cand_take(e, okey(pos_part(lds(z + j)) / neg(a)), j, j);
             }
             e = block_min_c(e, rbuf[1]);
-            if (tid == 0) d->part_sel[g] = e;
+            if (tid == 0) d->part_sel[2 * G + g] = e;
             if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) status = ST_TIMEOUT;
             if (status == ST_RUNNING) {
-                const Cand sel = load_partials_min(d->part_sel, G, rbuf[0]);
+                const Cand sel = load_partials_min(d->part_sel + 2 * G, G, rbuf[0]);
                 if (sel.idx < 0) {
                     status = ST_INFEASIBLE;
                 } else if (sel.idx >= N - 1) {
@@ -1565,6 +1666,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     unsigned lk = 0;
     if (tid == 0) s_zready = 0;
     __syncthreads();
+    if (tid == 0 && status != ST_TIMEOUT) red_add_release(scnt, 1u);  // the first selection
 
     while (status == ST_RUNNING) {
         const T *A = bufs[cur];
@@ -1577,20 +1679,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         unsigned long long *valB = d->part_vals + (size_t)(2 * par + 1) * G * kBlkVals;
         const unsigned tA = (unsigned)G * (2u * lk + 1u), tB = (unsigned)G * (2u * lk + 2u);
         (void)lane;
-        if (g == 0 && tid == 0) {  // grid barriers order this against every reader
-            for (int k = 0; k < np; ++k) {
-                if (iters + k < d->trace_cap) {
-                    d->trace[2 * (iters + k)] = pp[k];
-                    d->trace[2 * (iters + k) + 1] = qq[k];
-                }
-                basis[pp[k]] = qq[k];
-            }
-            d->last_p = pp[np - 1];
-            d->last_q = qq[np - 1];
-        }
         const int nbland = deg >= bland_after;  // rule of pivot a's selection
         const bool select = pend == ST_RUNNING;
         if (!selw) {
+            // the strip of the objective row is loaded with the pivot rows'
+            V zt;
+            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
             // Step 4 for the pass's pivots on this CTA's strip
             for (int j = c0 + tid; j < c1; j += NU) {
                 const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
@@ -1602,22 +1696,40 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 }
             }
             named_sync(1, NU);
-            // the strip of the objective row of T2, also for the selection
+            // the new strip of the objective row of T2, also for the selection
             if (tid < vpr) {
-                V zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
 #pragma unroll
                 for (int k = 0; k < kBlk; ++k)
                     if (k < np) vfma(zt, pc[k][m], *reinterpret_cast<const V *>(sprow[k] + tid * VW));
-                *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
                 *reinterpret_cast<V *>(sz + tid * VW) = zt;
             }
             named_sync(1, NU);
             if (tid == 0) {
                 __threadfence_block();
                 s_zready = (int)(lk + 1);  // sz, sprow of this pass ready for the selection
+                // this pass writes the previous pass's source, and CTA 0 the
+                // basis entries of this pass's pivots: wait until every CTA's
+                // selections so far are done reading both (as in the primal
+                // kernel)
+                const int ok = (int)wait_ctr(scnt, (unsigned)G * (lk + 1u), d->err, spin_limit);
+                if (ok && g == 0) {
+                    for (int k = 0; k < np; ++k) {
+                        if (iters + k < d->trace_cap) {
+                            d->trace[2 * (iters + k)] = pp[k];
+                            d->trace[2 * (iters + k) + 1] = qq[k];
+                        }
+                        basis[pp[k]] = qq[k];
+                    }
+                    d->last_p = pp[np - 1];
+                    d->last_q = qq[np - 1];
+                }
+                s_uok = ok;
             }
+            named_sync(1, NU);
+            const bool upd = active && s_uok;
+            if (s_uok && tid < vpr) *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
             // Step 5 for the pass's pivots on the constraint rows of the strip
-            if (active && np == 2) {
+            if (upd && np == 2) {
                 const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
                 const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
                 const int p0 = pp[0], p1 = pp[1];
@@ -1646,7 +1758,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
                     *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
                 }
-            } else if (active) {
+            } else if (upd) {
                 const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
                 const int p0 = pp[0];
                 const T *__restrict__ c0p = pc[0];
@@ -1754,14 +1866,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     if (!s_sok) {
                         st = ST_TIMEOUT;
                     } else {
-                        Cand f = cand_empty();
-                        for (int k = stid; k < G; k += kSelThreads) {
-                            const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recA) + k));
-                            if (cand_less(r, f)) {
-                                f = r;
-                                ka = (unsigned long long)k;
-                            }
-                        }
+                        const Cand f = scan_records_tab<kSelThreads, kBlk>(recA, valA, G, stid, &ka, s_tab);
                         const Cand sel = sel_min<SW>(f, ka, selc, selq, &ka);
                         if (sel.idx < 0) st = ST_INFEASIBLE;
                         else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
@@ -1776,21 +1881,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     // column q_a of T2, every row: the next pass's first pivot column
                     T pvq[kBlk];
 #pragma unroll
-                    for (int k = 0; k < kBlk; ++k) pvq[k] = tfrom<T>(__ldcg(valA + ka * kBlkVals + k));
-                    for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                    for (int k = 0; k < kBlk; ++k) pvq[k] = tfrom<T>(s_tab[ka * kBlk + k]);
+                    // the objective row's entry rides with the first batch
+                    const T am = stid == 0 ? lds(A + (long long)m * P + qa) : (T)0;
+                    for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
                         T av[kColRows];
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            av[u] = i < M ? lds(A + (long long)i * P + qa) : (T)0;
+                            av[u] = i < m ? lds(A + (long long)i * P + qa) : (T)0;
                         }
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            if (i >= M) break;
+                            if (i >= m) break;
                             colA[i] = blk_apply<T>(av[u], i, np, pp, pc, pvq);
                         }
                     }
+                    if (stid == 0) colA[m] = blk_apply<T>(am, m, np, pp, pc, pvq);
                     named_sync(2, kSelThreads);
                     // ---- pivot b: the rhs after pivot a and its leaving row ----
                     const T piva = colA[pa];
@@ -1843,14 +1951,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         if (!s_sok) {
                             st = ST_TIMEOUT;
                         } else {
-                            Cand f = cand_empty();
-                            for (int k = stid; k < G; k += kSelThreads) {
-                                const Cand r = unpack_cand(__ldcg(reinterpret_cast<const ulonglong2 *>(recB) + k));
-                                if (cand_less(r, f)) {
-                                    f = r;
-                                    kb = (unsigned long long)k;
-                                }
-                            }
+                            const Cand f = scan_records_tab<kSelThreads, kBlk + 1>(recB, valB, G, stid, &kb, s_tab);
                             const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
                             if (sel.idx < 0) npend = ST_INFEASIBLE;
                             else if (sel.idx >= N - 1) st = ST_TIMEOUT;  // never
@@ -1864,30 +1965,35 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             // column q_b after pivot a, every row
                             T pvb[kBlk + 1];
 #pragma unroll
-                            for (int k = 0; k <= kBlk; ++k) pvb[k] = tfrom<T>(__ldcg(valB + kb * kBlkVals + k));
+                            for (int k = 0; k <= kBlk; ++k) pvb[k] = tfrom<T>(s_tab[kb * (kBlk + 1) + k]);
                             T *colB = nc[1];
-                            for (int i0 = stid; i0 < M; i0 += kColRows * kSelThreads) {
+                            const T am = stid == 0 ? lds(A + (long long)m * P + qb) : (T)0;
+                            for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
                                 T av[kColRows];
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    av[u] = i < M ? lds(A + (long long)i * P + qb) : (T)0;
+                                    av[u] = i < m ? lds(A + (long long)i * P + qb) : (T)0;
                                 }
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    if (i >= M) break;
+                                    if (i >= m) break;
                                     const T t = blk_apply<T>(av[u], i, np, pp, pc, pvb);
                                     colB[i] = (i == pa) ? pvb[np] : tfma(-colA[i], pvb[np], t);
                                 }
                             }
+                            if (stid == 0)  // pa < m
+                                colB[m] = tfma(-colA[m], pvb[np], blk_apply<T>(am, m, np, pp, pc, pvb));
                             nnp = 2;
                         }
                     }
                 }
             }
+            // every selection thread is done reading this pass's source
             named_sync(2, kSelThreads);
             if (stid == 0) {
+                if (st != ST_TIMEOUT) red_add_release(scnt, 1u);
                 s_status = st;
                 s_np = nnp;
                 s_pend = npend;
@@ -1904,6 +2010,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         iters += np;
         ++lk;
         status = s_status;
+        if (!s_uok) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
             np = s_np;
             pend = s_pend;
@@ -1916,13 +2023,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             cb = (cb + 2) & 3;
         }
         cur ^= 1;
-        if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {
-            status = ST_TIMEOUT;
-            break;
-        }
+        // no grid barrier between passes (as in the primal kernel)
     }
 
     if (g == 0 && tid == 0) {
+        // every CTA's last selection is done, and with it its last wait
+        wait_ctr(scnt, (unsigned)G * (lk + 1u), d->err, spin_limit);
         d->status = (*(volatile int *)d->err) ? ST_TIMEOUT : status;
         d->iters = iters;
         d->iter_limit = iter_limit;
@@ -1995,7 +2101,13 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     sh.threads = threads > 0 ? threads : kMaxThreads;
     sh.threads = std::min(kMaxThreads, std::max(2 * kSelThreadsMax, (sh.threads + 31) / 32 * 32));
     const int nu = sh.threads - kSelThreadsMax;
-    long long g = ctas > 0 ? ctas : std::min<long long>(sms, ((long long)M * P + 32767) / 32768);
+    // Default grid: every SM.  A pivot costs the selection chain plus the
+    // update of one strip, and a narrower strip shortens the update while the
+    // extra pricing records add little (512 x 4096: 11.7 us per pivot on 152
+    // CTAs, 14.5 on 73).  Below half a million tableau elements the records
+    // weigh more than the update saved, and half the SMs does as well.
+    const long long g_auto = (long long)M * P >= (1ll << 19) ? sms : (sms + 1) / 2;
+    long long g = ctas > 0 ? ctas : g_auto;
     const long long gmin = (P + (long long)nu * vw - 1) / ((long long)nu * vw);
     g = std::max<long long>(std::max<long long>(g, gmin), 1);
     long long w = (P + g - 1) / g;
@@ -2026,7 +2138,8 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     sh.dual = dual == 1 || dual == 3;
     // one CTA per SM at 1024 threads: the grid must fit the SMs (cooperative
     // launch), the strip one pass of the update threads
-    sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw;
+    sh.pipe = sh.ctas <= sms && (long long)sh.strip <= (long long)nu * vw &&
+              (dual < 2 || sh.ctas <= kMaxRecs);
     return sh;
 }
 
