@@ -70,8 +70,8 @@ def peaks():
 INPLACE_KERNEL = "pivot_pipe_kernel<double> (in place)"
 BLOCK_KERNEL = "pivot_block_kernel<double> (two pivots per pass)"
 DUAL_KERNEL = "pivot_block_dual_kernel<double> (dual simplex, two pivots per pass)"
+# (the in-place kernel runs no LP of the default set, so it has no record)
 TRAFFIC_FILES = {
-    INPLACE_KERNEL: os.path.join(ROOT, "profiles", "pivot_pipe_kernel_fp64_traffic.txt"),
     BLOCK_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_kernel_fp64_traffic.txt"),
     DUAL_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_dual_kernel_fp64_traffic.txt"),
 }
