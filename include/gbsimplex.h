@@ -124,10 +124,14 @@ typedef struct {
                                     the memory), a grid barrier per pivot;
                                 4 = double-buffered, two pivots per pass over
                                     the tableau (half the tableau traffic per
-                                    pivot), no grid barrier between passes.
+                                    pivot), no grid barrier between passes;
+                                    from m > 4 x 32 x selection warps on, each
+                                    CTA forms the new pivot columns on its own
+                                    rows and the ratio test is distributed;
+                                5 = as 4, the ratio test always distributed.
                                 The dual rule (LP_MIN_GE, and FP32 recovery)
                                 always runs double-buffered: one pivot per pass
-                                for 2 and 3, two for 1 and 4.
+                                for 2 and 3, two for 1, 4 and 5.
                                 Same pivots and bits in every mode.              */
 } lp_options;
 

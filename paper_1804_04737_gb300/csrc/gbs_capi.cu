@@ -32,6 +32,13 @@ constexpr long long kBlockElems = 1ll << 19;
 // with eight, 60.5 with four, 57.9 with one pivot per pass; 8192^2 FP64
 // (1.07 GB) 249 with four, 253 with eight, 370 with one pivot per pass).
 constexpr size_t kBlockBytes = 384ull << 20;
+// The two-pivot primal kernel distributes its ratio test over the CTAs (one
+// more record exchange per pivot, a slice of the column's rows per CTA) when
+// every selection thread would otherwise form more than this many rows of
+// each new column (measured per pivot, redundant / distributed: 512 x 4096
+// (2 rows a thread) 11.4 / 13.5 us, 2048^2 (8) 24.3 / 23.7, 4096 x 512 (16)
+// 46.6 / 40.5, 8192^2 (64) 243 / 239).
+constexpr int kDistRows = 4;
 
 struct lp_handle {
     lp_options opt;
@@ -55,11 +62,13 @@ struct lp_handle {
     size_t cap_T = 0;                           // bytes
     void *dT2 = nullptr;                        // double-buffered pipelined kernel
     size_t cap_T2 = 0;
+    void *dcolx = nullptr;                      // two-pivot kernel: four pivot-column slots
+    size_t cap_colx = 0;
     int *dbasis = nullptr;
     size_t cap_basis = 0;
     void *dscratch = nullptr;
     size_t cap_scratch = 0;                     // bytes
-    Cand *dpart = nullptr;                      // 20 * max_ctas (records, values)
+    Cand *dpart = nullptr;                      // 38 * max_ctas (records, values)
     int max_ctas = 0;
     unsigned *dbar = nullptr;                   // kBarWords: barrier, counters, err
     int *dtrace = nullptr;
@@ -239,8 +248,8 @@ void lp_destroy(lp_handle *h) {
                      h->rb.bar};
     for (void *p : rbufs)
         if (p) cudaFree(p);
-    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dbasis, h->dscratch, h->dpart, h->dbar,
-                    h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
+    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dcolx, h->dbasis, h->dscratch, h->dpart,
+                    h->dbar, h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->pdesc) cudaFreeHost(h->pdesc);
@@ -276,13 +285,15 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     // the pipelined kernels where they can take the LP: the primal rule in
     // place for small tableaus and two pivots per pass above, the dual rule
     // double-buffered (the rule runs for its sense, and in FP32 mode for both)
-    if (h->opt.pipeline < 0 || h->opt.pipeline > 4) {
+    if (h->opt.pipeline < 0 || h->opt.pipeline > 5) {
         set_err(h, "lp_load: unknown pipeline mode %d", h->opt.pipeline);
         return LP_ERR_INVALID_ARG;
     }
     const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
     const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32;
     int pmode = primal ? h->opt.pipeline : 0;
+    const bool force_dist = pmode == 5;  // 5: as 4, the ratio test always distributed
+    if (pmode == 5) pmode = 4;
     const size_t tbytes = (size_t)M * P * esz;
     if (pmode == 1) pmode = (long long)M * P >= kBlockElems ? 4 : 2;
     const bool dwant = dualr && h->opt.pipeline != 0;
@@ -298,6 +309,8 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         }
         pmode = 2;  // automatic mode without room for a second buffer: in place
     }
+    if (pmode == 4)  // the two-pivot kernel's pivot-column slots
+        CUDA_TRY(h, grow_bytes(&h->dcolx, &h->cap_colx, 4 * (((size_t)M * esz + 15) & ~(size_t)15)));
     const bool dpipe = dwant && have_t2;
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
@@ -308,13 +321,17 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
                 if (pmode == 4) {  // double-buffered, two pivots per pass
                     ps.pipe = 3;
                     ps.sel_warps = tbytes < kBlockBytes ? 8 : 4;
+                    // each CTA forms the new columns on its own rows once the
+                    // whole columns would take a selection thread more than
+                    // kDistRows rows
+                    ps.dist = force_dist || m > kDistRows * 32 * ps.sel_warps;
                 }
                 return ps;
             }
         }
         if (rule == 1 && dpipe) {
             // the dual rule: two pivots per pass unless one is asked for (2, 3)
-            const bool two = h->opt.pipeline == 1 || h->opt.pipeline == 4;
+            const bool two = h->opt.pipeline == 1 || h->opt.pipeline >= 4;
             PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas,
                                               two ? 3 : 1);
             if (ps.pipe) {
@@ -345,7 +362,10 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         if (h->dpart) cudaFree(h->dpart);
         h->dpart = nullptr;
         h->max_ctas = 0;
-        CUDA_TRY(h, cudaMalloc(&h->dpart, 20 * (size_t)ctas_max * sizeof(Cand)));
+        // records: 4 x G pricing candidates, then (in 8-byte words) 32 x G
+        // record values, 16 x G ratio records, 4 x G exact candidates and
+        // 16 x G exact values
+        CUDA_TRY(h, cudaMalloc(&h->dpart, 38 * (size_t)ctas_max * sizeof(Cand)));
         h->max_ctas = ctas_max;
     }
     if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
@@ -423,6 +443,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.part_sel = h->dpart;
     d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 4 * (size_t)h->max_ctas);
     d.T2 = have_t2 ? h->dT2 : nullptr;
+    d.colx = h->dcolx;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;

@@ -58,6 +58,10 @@ struct LpDesc {
     // rhs; 2 x G pairs, or 4 x G x 8 values for two pivots per pass)
     void *T2;
     unsigned long long *part_vals;
+    // two-pivot primal kernel: the global slots of its four pivot columns
+    // (4 x the column bytes rounded up to 16; the distributed ratio test
+    // assembles each new column there)
+    void *colx;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
@@ -69,6 +73,7 @@ struct PivotShape {
     int dual = 0;                  // dual simplex kernel (else primal)
     int pipe = 0;                  // pipelined kernel: 1 in place, 2 double-buffered, 3 two pivots per pass
     int sel_warps = 4;             // two pivots per pass: selection warps per CTA (4 or 8)
+    int dist = 0;                  // two pivots per pass, primal: ratio test distributed over the CTAs
     size_t smem_bytes = 0;         // dynamic shared memory per CTA
     long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };
@@ -78,7 +83,8 @@ struct PivotShape {
 // kernel) or pricing-records counter (pipelined kernel), [96] error flag,
 // [128] selections-done counter (one-pivot pipelined kernels) or records
 // counter (two-pivot dual kernel), [160] selections-done counter (two-pivot
-// kernels); 128-byte apart.
+// kernels), [192] ratio-records counter and [224] exact-rounds counter
+// (two-pivot primal kernel); 128-byte apart.
 constexpr int kBarWords = 256;
 
 struct InputStats {

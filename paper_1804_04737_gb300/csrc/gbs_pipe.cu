@@ -971,6 +971,152 @@ __device__ __forceinline__ Cand scan_records_tab(const Cand *rec, const unsigned
     return e;
 }
 
+// Copy a whole pivot column (cbytes, a multiple of 16, from its global slot)
+// into this CTA's scratch: into shared memory asynchronously (cp.async, 16
+// bytes per copy; fill_wait completes this thread's copies), into a global
+// scratch slice with plain loads.  Rows the CTA formed itself get the bits
+// they already hold.
+template <typename T>
+__device__ __forceinline__ void fill_column(T *dst, const T *src, size_t cbytes, int stid, int nt,
+                                            bool smem) {
+    const int n16 = (int)(cbytes / 16);
+    if (smem) {
+        const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+        const char *gsrc = reinterpret_cast<const char *>(src);
+        for (int c = stid; c < n16; c += nt)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16u * (unsigned)c),
+                         "l"(gsrc + 16 * (size_t)c)
+                         : "memory");
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    } else {
+        const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
+        ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst);
+        for (int c = stid; c < n16; c += nt) d2[c] = __ldcg(s2 + c);
+    }
+}
+__device__ __forceinline__ void fill_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---- the distributed ratio test of the two-pivot primal kernel ----
+//
+// Every CTA forms the new pivot column, the rhs and the screening keys only on
+// its own slice of rows [r0, r1) (rows g*rs .. g*rs + rs - 1), writes its part
+// of the column to a global slot, and publishes one ratio record per round:
+// {smallest key of the slice, (count << 32 | first row) of its rows within the
+// screening threshold of that key, the column's entry at that row}.  From all
+// records every CTA takes the same decision: with rstar the smallest key and
+// thr its threshold, the slices whose key is within thr hold every row within
+// thr, each at least one, and a slice's count covers its rows within thr
+// (its own threshold is at least thr); so the sum of their counts is 1
+// exactly when one row in all is within thr, which is then the leaving row,
+// as in the one-CTA test.  Otherwise (near ties) the slices' exact quotients
+// go through a second exchange.  Either way the row and its keys are those of
+// the screened test over all rows.
+struct RatioPick {
+    int status;               // ST_RUNNING, ST_UNBOUNDED or ST_TIMEOUT
+    int row;                  // the leaving row, or -1: near ties, exact round needed
+    unsigned long long key;   // the smallest screening key (rstar)
+    unsigned long long val;   // bits of the new column's entry at row
+};
+
+template <typename T, int SW>
+__device__ RatioPick ratio_slices(unsigned long long lmin, const unsigned long long *srk,
+                                  const T *ncol, int r0, int r1, int rs, unsigned long long *recs,
+                                  unsigned *cnt, unsigned target, int *err, long long spin_limit,
+                                  int G, int g, int stid, unsigned long long *selq, unsigned *sela,
+                                  unsigned *selb, unsigned long long *vtab, volatile int *s_ok) {
+    constexpr int NT = 32 * SW;
+    constexpr int R = NT >= 256 ? 1 : 256 / NT;  // G <= 256
+    RatioPick out{ST_RUNNING, -1, ~0ull, 0ull};
+    // this slice's record
+    const unsigned long long kmin = sel_min_u64<SW>(lmin, selq);
+    unsigned first = 0xffffffffu, cnt_g = 0;
+    if (kmin != ~0ull) {
+        const unsigned long long thr = screen_thr(kmin, (T)0);
+        for (int i = r0 + stid; i < r1; i += NT)
+            if (srk[i] <= thr) {
+                first = (unsigned)i < first ? (unsigned)i : first;
+                ++cnt_g;
+            }
+    }
+    unsigned sfirst, scnt;
+    sel_min_sum<SW>(first, cnt_g, sela, selb, &sfirst, &scnt);
+    if (stid == 0) {
+        unsigned long long *r = recs + (size_t)g * 4;
+        r[0] = kmin;
+        r[1] = ((unsigned long long)scnt << 32) | sfirst;
+        r[2] = scnt ? tbits(ncol[sfirst]) : 0ull;
+        red_add_release(cnt, 1u);
+        *s_ok = (int)wait_ctr(cnt, target, err, spin_limit);
+    }
+    named_sync(2, NT);
+    if (!*s_ok) {
+        out.status = ST_TIMEOUT;
+        return out;
+    }
+    // every slice's record, in one batch of loads
+    unsigned long long kk[R], fc[R];
+    unsigned long long lk = ~0ull;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int k = stid + u * NT;
+        kk[u] = k < G ? __ldcg(recs + (size_t)k * 4) : ~0ull;
+        fc[u] = k < G ? __ldcg(recs + (size_t)k * 4 + 1) : 0ull;
+        if (k < G) vtab[k] = __ldcg(recs + (size_t)k * 4 + 2);
+        lk = kk[u] < lk ? kk[u] : lk;
+    }
+    const unsigned long long rstar = sel_min_u64<SW>(lk, selq);
+    if (rstar == ~0ull) {
+        out.status = ST_UNBOUNDED;
+        return out;
+    }
+    const unsigned long long thr = screen_thr(rstar, (T)0);
+    unsigned a = 0xffffffffu, b = 0;
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+        if (kk[u] <= thr) {
+            const unsigned f = (unsigned)(fc[u] & 0xffffffffull);
+            a = f < a ? f : a;
+            b += (unsigned)(fc[u] >> 32);
+        }
+    unsigned wfirst, wcnt;
+    sel_min_sum<SW>(a, b, sela, selb, &wfirst, &wcnt);  // its barriers also publish vtab
+    out.key = rstar;
+    if (wcnt == 1) {
+        out.row = (int)wfirst;
+        out.val = vtab[wfirst / (unsigned)rs];
+    }
+    return out;
+}
+
+// The exact round after near ties: each CTA's best exact candidate (rc, with
+// the new column's entry at its row) goes through one more exchange; every CTA
+// gets the winner and its entry.  slot: this round's records (xsel + G) and
+// values (xval + G * kBlkVals).
+template <typename T, int SW>
+__device__ Cand ratio_exact(Cand rc, unsigned long long rcval, Cand *xsel, unsigned long long *xval,
+                            unsigned *cnt, unsigned target, int *err, long long spin_limit, int G,
+                            int g, int stid, Cand *selc, unsigned long long *selq,
+                            unsigned long long *tab, volatile int *s_ok, unsigned long long *val,
+                            int *status) {
+    constexpr int NT = 32 * SW;
+    if (stid == 0) {
+        xsel[g] = rc;
+        xval[(size_t)g * kBlkVals] = rcval;
+        red_add_release(cnt, 1u);
+        *s_ok = (int)wait_ctr(cnt, target, err, spin_limit);
+    }
+    named_sync(2, NT);
+    if (!*s_ok) {
+        *status = ST_TIMEOUT;
+        return cand_empty();
+    }
+    unsigned long long k;
+    const Cand e = scan_records_tab<NT, 1>(xsel, xval, G, stid, &k, tab);
+    const Cand w = sel_min<SW>(e, k, selc, selq, &k);
+    *val = tab[k];
+    return w;
+}
+
 // x after the pass's pivots 0..np-1, for row i (pv: their pivot-row values at
 // the column of x).
 template <typename T>
@@ -982,7 +1128,7 @@ __device__ __forceinline__ T blk_apply(T x, int i, int np, const int *pp, const 
     return x;
 }
 
-template <typename T, int SW>
+template <typename T, int SW, bool DIST>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_block_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
     typedef typename Vec<T>::type V;
@@ -1054,6 +1200,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     for (int k = 0; k < 4; ++k) scol[k] = reinterpret_cast<T *>(sc + k * cbytes);
     T *srhs = reinterpret_cast<T *>(sc + 4 * cbytes);
     unsigned long long *srk = reinterpret_cast<unsigned long long *>(sc + 5 * cbytes);
+    // the distributed ratio test: this CTA's rows [r0, r1), the global slots
+    // of the four pivot columns (as scol), the ratio records and the records
+    // of the exact rounds (by parity of their counts), and their counters
+    const int rsl = m > 0 ? (m + G - 1) / G : 1;
+    const int r0 = min(m, g * rsl), r1 = min(m, r0 + rsl);
+    const int ra0 = DIST ? r0 : 0, ra1 = DIST ? r1 : m;  // the rows this CTA forms
+    T *gcs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        gcs[k] = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(d->colx) + k * cbytes);
+    unsigned long long *rrec = d->part_vals + (size_t)32 * G;  // 2 x G x 4
+    Cand *xsel = reinterpret_cast<Cand *>(d->part_vals + (size_t)48 * G);  // 2 x G
+    unsigned long long *xval = d->part_vals + (size_t)52 * G;  // 2 x G x kBlkVals
+    unsigned *rrcnt = d->bar + 192, *xcnt = d->bar + 224;
+    unsigned nrr = 0, nx = 0;  // ratio rounds and exact rounds so far (the same in every CTA)
+    const bool smem_scr = d->scratch_stride == 0;
 
     // ---- selection of the first pivot from the current tableau (all threads) ----
     int p = -1, q = -1;
@@ -1123,6 +1285,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         T *Bn = bufs[cur ^ 1];
         const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
         T *nc[kBlk] = {scol[(cb + 2) & 3], scol[(cb + 3) & 3]};
+        T *gnc[kBlk] = {gcs[(cb + 2) & 3], gcs[(cb + 3) & 3]};
         const int par = lk & 1;
         Cand *recA = d->part_sel + (2 * par) * G, *recB = d->part_sel + (2 * par + 1) * G;
         unsigned long long *valA = d->part_vals + (size_t)(2 * par) * G * kBlkVals;
@@ -1259,6 +1422,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             // selection of the next pass's pivots a and b
             int st = ST_RUNNING, nnp = 0, npend = ST_RUNNING;
             int pa = -1, qa = -1, pb = -1, qb = -1, rza = 0, rzb = 0;
+            T piva = (T)0;  // pivot a's entry of its column
             // the basic variable of row i after the pass's pivots
             auto bkey = [&](int i) -> int {
                 if (np > 1 && i == pp[1]) return qq[1];
@@ -1295,25 +1459,27 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         pvq[k] = tfrom<T>(s_tab[ka * kBlk + k]);
                         pvr[k] = tfrom<T>(rvb[k]);
                     }
-                    // column q_a and rhs of T2, every row (Step 3); the rhs from
-                    // the one of T0 kept in scratch, which becomes T2's
+                    // column q_a and rhs of T2 on this CTA's rows (Step 3,
+                    // distributed); the rhs from the one of T0 kept in scratch,
+                    // which becomes T2's
                     T *ncol = nc[0];
                     unsigned long long lmin = ~0ull;
                     // the objective row's entry rides with the first batch
                     const T am = stid == 0 ? lds(A + (long long)m * P + qa) : (T)0;
-                    for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
+                    for (int i0 = ra0 + stid; i0 < ra1; i0 += kColRows * kSelThreads) {
                         T av[kColRows];
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            av[u] = i < m ? lds(A + (long long)i * P + qa) : (T)0;
+                            av[u] = i < ra1 ? lds(A + (long long)i * P + qa) : (T)0;
                         }
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            if (i >= m) break;
+                            if (i >= ra1) break;
                             const T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
                             ncol[i] = a;
+                            if (DIST) gnc[0][i] = a;
                             const T rhs = blk_apply<T>(srhs[i], i, np, pp, pc, pvr);
                             srhs[i] = rhs;
                             const unsigned long long rk =
@@ -1322,36 +1488,81 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             lmin = rk < lmin ? rk : lmin;
                         }
                     }
-                    if (stid == 0) ncol[m] = blk_apply<T>(am, m, np, pp, pc, pvq);
-                    const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
-                    if (rstar == ~0ull) {
-                        st = ST_UNBOUNDED;
-                    } else {
-                        const unsigned long long thr = screen_thr(rstar, (T)0);
-                        unsigned first = 0xffffffffu, cnt = 0;
-                        for (int i = stid; i < m; i += kSelThreads)
-                            if (srk[i] <= thr) {
-                                first = (unsigned)i < first ? (unsigned)i : first;
-                                ++cnt;
-                            }
-                        unsigned gfirst, gcnt;
-                        sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
-                        if (gcnt == 1) {
-                            pa = (int)gfirst;
-                            rza = srk[pa] == zero_k;
+                    if (stid == 0) {  // every CTA forms the objective row's entry itself
+                        ncol[m] = blk_apply<T>(am, m, np, pp, pc, pvq);
+                        if (DIST && g == 0) gnc[0][m] = ncol[m];
+                    }
+                    if constexpr (!DIST) {
+                        // every row in this CTA: the screened test, exact on near ties
+                        const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
+                        if (rstar == ~0ull) {
+                            st = ST_UNBOUNDED;
                         } else {
-                            Cand rc = cand_empty();
+                            const unsigned long long thr = screen_thr(rstar, (T)0);
+                            unsigned first = 0xffffffffu, cnt = 0;
                             for (int i = stid; i < m; i += kSelThreads)
                                 if (srk[i] <= thr) {
-                                    const T nm = pos_part(srhs[i]);
-                                    const unsigned long long vk =
-                                        tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
-                                    cand_take(rc, vk, nbland ? bkey(i) : i, i);
+                                    first = (unsigned)i < first ? (unsigned)i : first;
+                                    ++cnt;
                                 }
-                            rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
-                            pa = rc.idx;
-                            rza = rc.vk == zero_k;
+                            unsigned gfirst, gcnt;
+                            sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
+                            if (gcnt == 1) {
+                                pa = (int)gfirst;
+                                rza = srk[pa] == zero_k;
+                            } else {
+                                Cand rc = cand_empty();
+                                for (int i = stid; i < m; i += kSelThreads)
+                                    if (srk[i] <= thr) {
+                                        const T nm = pos_part(srhs[i]);
+                                        const unsigned long long vk =
+                                            tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
+                                        cand_take(rc, vk, nbland ? bkey(i) : i, i);
+                                    }
+                                rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
+                                pa = rc.idx;
+                                rza = rc.vk == zero_k;
+                            }
+                            piva = ncol[pa];
                         }
+                    } else {
+                    const RatioPick rp = ratio_slices<T, SW>(
+                        lmin, srk, ncol, r0, r1, rsl, rrec + (size_t)(nrr & 1) * G * 4, rrcnt,
+                        (unsigned)G * (nrr + 1u), d->err, spin_limit, G, g, stid, selq, sela, selb,
+                        s_tab, &s_sok);
+                    ++nrr;
+                    if (rp.status != ST_RUNNING) {
+                        st = rp.status;
+                    } else if (rp.row >= 0) {
+                        pa = rp.row;
+                        piva = tfrom<T>(rp.val);
+                        rza = rp.key == zero_k;
+                    } else {
+                        // near ties: the exact quotients of the rows within the
+                        // threshold, one more exchange
+                        const unsigned long long thr = screen_thr(rp.key, (T)0);
+                        Cand rc = cand_empty();
+                        for (int i = r0 + stid; i < r1; i += kSelThreads)
+                            if (srk[i] <= thr) {
+                                const T nm = pos_part(srhs[i]);
+                                const unsigned long long vk =
+                                    tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
+                                cand_take(rc, vk, nbland ? bkey(i) : i, i);
+                            }
+                        rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
+                        unsigned long long v;
+                        const Cand w = ratio_exact<T, SW>(
+                            rc, rc.idx >= 0 ? tbits(ncol[rc.idx]) : 0ull, xsel + (size_t)(nx & 1) * G,
+                            xval + (size_t)(nx & 1) * G * kBlkVals, xcnt, (unsigned)G * (nx + 1u),
+                            d->err, spin_limit, G, g, stid, selc, selq, s_tab, &s_sok, &v, &st);
+                        ++nx;
+                        pa = w.idx;
+                        piva = tfrom<T>(v);
+                        rza = w.vk == zero_k;
+                    }
+                    // the whole column q_a for the next pass's update, copied
+                    // while pivot b is selected
+                    if (st == ST_RUNNING) fill_column(ncol, gnc[0], cbytes, stid, kSelThreads, smem_scr);
                     }
                 }
                 if (st == ST_RUNNING) {
@@ -1375,7 +1586,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     if (!s_sok) {
                         st = ST_TIMEOUT;
                     } else {
-                        const T piva = colA[pa];
                         Cand e = cand_empty();
                         for (int j = c0 + stid; j < c1; j += kSelThreads) {
                             T r = lds(A + (long long)pa * P + j);
@@ -1427,26 +1637,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                 pvq[k] = tfrom<T>(s_tab[kb * (kBlk + 1) + k]);
                                 pvr[k] = tfrom<T>(rvb[k]);
                             }
-                            // column q_b and rhs after pivot a, every row (Step 3);
-                            // scratch keeps T2's rhs for the next pass
+                            // column q_b and rhs after pivot a on this CTA's rows
+                            // (Step 3, distributed); scratch keeps T2's rhs for the
+                            // next pass
                             T *ncol = nc[1];
                             unsigned long long lmin = ~0ull;
                             const T am = stid == 0 ? lds(A + (long long)m * P + qb) : (T)0;
-                            for (int i0 = stid; i0 < m; i0 += kColRows * kSelThreads) {
+                            for (int i0 = ra0 + stid; i0 < ra1; i0 += kColRows * kSelThreads) {
                                 T av[kColRows];
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    av[u] = i < m ? lds(A + (long long)i * P + qb) : (T)0;
+                                    av[u] = i < ra1 ? lds(A + (long long)i * P + qb) : (T)0;
                                 }
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    if (i >= m) break;
+                                    if (i >= ra1) break;
                                     const T ca = colA[i];
                                     T a = blk_apply<T>(av[u], i, np, pp, pc, pvq);
                                     a = (i == pa) ? pvq[np] : tfma(-ca, pvq[np], a);
                                     ncol[i] = a;
+                                    if (DIST) gnc[1][i] = a;
                                     const T h = (i == pa) ? pvr[np] : tfma(-ca, pvr[np], srhs[i]);
                                     const unsigned long long rk =
                                         okey(a) > lim_p ? screen_key(pos_part(h), a) : ~0ull;
@@ -1454,27 +1666,62 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                     lmin = rk < lmin ? rk : lmin;
                                 }
                             }
-                            if (stid == 0)  // pa < m
+                            if (stid == 0) {  // pa < m
                                 ncol[m] = tfma(-colA[m], pvq[np], blk_apply<T>(am, m, np, pp, pc, pvq));
-                            const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
-                            if (rstar == ~0ull) {
+                                if (DIST && g == 0) gnc[1][m] = ncol[m];
+                            }
+                            if constexpr (!DIST) {
+                                const unsigned long long rstar = sel_min_u64<SW>(lmin, selq);
+                                if (rstar == ~0ull) {
+                                    npend = ST_UNBOUNDED;
+                                } else {
+                                    const unsigned long long thr = screen_thr(rstar, (T)0);
+                                    unsigned first = 0xffffffffu, cnt = 0;
+                                    for (int i = stid; i < m; i += kSelThreads)
+                                        if (srk[i] <= thr) {
+                                            first = (unsigned)i < first ? (unsigned)i : first;
+                                            ++cnt;
+                                        }
+                                    unsigned gfirst, gcnt;
+                                    sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
+                                    if (gcnt == 1) {
+                                        pb = (int)gfirst;
+                                        rzb = srk[pb] == zero_k;
+                                    } else {
+                                        Cand rc = cand_empty();
+                                        for (int i = stid; i < m; i += kSelThreads)
+                                            if (srk[i] <= thr) {
+                                                const T nm = pos_part((i == pa) ? pvr[np]
+                                                                                : tfma(-colA[i], pvr[np], srhs[i]));
+                                                const unsigned long long vk =
+                                                    tbits(nm) == 0ull ? zero_k : okey(nm / ncol[i]);
+                                                const int key = nblandb ? (i == pa ? qa : bkey(i)) : i;
+                                                cand_take(rc, vk, key, i);
+                                            }
+                                        rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
+                                        pb = rc.idx;
+                                        rzb = rc.vk == zero_k;
+                                    }
+                                    nnp = 2;
+                                }
+                            } else {
+                            const RatioPick rp = ratio_slices<T, SW>(
+                                lmin, srk, ncol, r0, r1, rsl, rrec + (size_t)(nrr & 1) * G * 4, rrcnt,
+                                (unsigned)G * (nrr + 1u), d->err, spin_limit, G, g, stid, selq, sela,
+                                selb, s_tab, &s_sok);
+                            ++nrr;
+                            if (rp.status == ST_TIMEOUT) {
+                                st = ST_TIMEOUT;
+                            } else if (rp.status == ST_UNBOUNDED) {
                                 npend = ST_UNBOUNDED;
                             } else {
-                                const unsigned long long thr = screen_thr(rstar, (T)0);
-                                unsigned first = 0xffffffffu, cnt = 0;
-                                for (int i = stid; i < m; i += kSelThreads)
-                                    if (srk[i] <= thr) {
-                                        first = (unsigned)i < first ? (unsigned)i : first;
-                                        ++cnt;
-                                    }
-                                unsigned gfirst, gcnt;
-                                sel_min_sum<SW>(first, cnt, sela, selb, &gfirst, &gcnt);
-                                if (gcnt == 1) {
-                                    pb = (int)gfirst;
-                                    rzb = srk[pb] == zero_k;
+                                if (rp.row >= 0) {
+                                    pb = rp.row;
+                                    rzb = rp.key == zero_k;
                                 } else {
+                                    const unsigned long long thr = screen_thr(rp.key, (T)0);
                                     Cand rc = cand_empty();
-                                    for (int i = stid; i < m; i += kSelThreads)
+                                    for (int i = r0 + stid; i < r1; i += kSelThreads)
                                         if (srk[i] <= thr) {
                                             const T nm = pos_part((i == pa) ? pvr[np]
                                                                             : tfma(-colA[i], pvr[np], srhs[i]));
@@ -1484,15 +1731,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                             cand_take(rc, vk, key, i);
                                         }
                                     rc = sel_min<SW>(rc, 0ull, selc, selq, nullptr);
-                                    pb = rc.idx;
-                                    rzb = rc.vk == zero_k;
+                                    unsigned long long v;
+                                    const Cand w = ratio_exact<T, SW>(
+                                        rc, rc.idx >= 0 ? tbits(ncol[rc.idx]) : 0ull,
+                                        xsel + (size_t)(nx & 1) * G, xval + (size_t)(nx & 1) * G * kBlkVals,
+                                        xcnt, (unsigned)G * (nx + 1u), d->err, spin_limit, G, g, stid,
+                                        selc, selq, s_tab, &s_sok, &v, &st);
+                                    ++nx;
+                                    pb = w.idx;
+                                    rzb = w.vk == zero_k;
                                 }
-                                nnp = 2;
+                                if (st == ST_RUNNING) {
+                                    fill_column(ncol, gnc[1], cbytes, stid, kSelThreads, smem_scr);
+                                    nnp = 2;
+                                }
+                            }
                             }
                         }
                     }
                 }
             }
+            // the pass's pivot columns are copied in full before the next pass
+            fill_wait();
             // every selection thread is done reading this pass's source
             named_sync(2, kSelThreads);
             if (stid == 0) {
@@ -2054,10 +2314,14 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                         : (w8 ? (const void *)pivot_block_dual_kernel<float, 8>
                                               : (const void *)pivot_block_dual_kernel<float, 4>))
                          : prec == PREC_FP64
-                             ? (w8 ? (const void *)pivot_block_kernel<double, 8>
-                                   : (const void *)pivot_block_kernel<double, 4>)
-                             : (w8 ? (const void *)pivot_block_kernel<float, 8>
-                                   : (const void *)pivot_block_kernel<float, 4>);
+                             ? (w8 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true>
+                                              : (const void *)pivot_block_kernel<double, 8, false>)
+                                   : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true>
+                                              : (const void *)pivot_block_kernel<double, 4, false>))
+                             : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<float, 8, true>
+                                              : (const void *)pivot_block_kernel<float, 8, false>)
+                                   : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true>
+                                              : (const void *)pivot_block_kernel<float, 4, false>));
         if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sh.smem_bytes);

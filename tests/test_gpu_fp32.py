@@ -65,7 +65,7 @@ def test_fp32_objective_vs_fp64_oracle(m, n, sense):
 
 
 @pytest.mark.parametrize("k", [1, 7, 50, 200])
-@pytest.mark.parametrize("pipeline", [0, 2, 3, 4])
+@pytest.mark.parametrize("pipeline", [0, 2, 3, 4, 5])
 def test_fp32_reinversion_period(k, pipeline):
     A, b, c = lpgen.dense_lp(400, 500, seed=3)
     o = oracle.solve(A, b, c)

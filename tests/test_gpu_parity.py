@@ -92,19 +92,20 @@ def test_launch_shapes_bitwise(ctas, threads):
     assert_same(Run(Ad, bd, cd, MIN_GE, ctas=ctas, threads=threads), od)
 
 
-@pytest.mark.parametrize("pipeline", [0, 2, 3, 4])
+@pytest.mark.parametrize("pipeline", [0, 2, 3, 4, 5])
 @pytest.mark.parametrize("m,n,ctas,threads", [(1, 1, 0, 0), (9, 1, 0, 0), (33, 17, 2, 128),
                                               (257, 100, 0, 0), (300, 1000, 5, 256),
                                               (1000, 300, 0, 1024), (200, 311, 40, 64)])
 def test_primal_kernels_bitwise(m, n, ctas, threads, pipeline):
     """Every primal kernel gives the oracle's pivots and bits: selection then
     update (0), pipelined in place (2), pipelined double-buffered (3), two
-    pivots per pass (4)."""
+    pivots per pass (4), two pivots per pass with the ratio test distributed
+    over the CTAs (5)."""
     A, b, c = lpgen.dense_lp(m, n, seed=7 * m + n)
     assert_same(Run(A, b, c, ctas=ctas, threads=threads, pipeline=pipeline), _oracle(A, b, c))
 
 
-@pytest.mark.parametrize("pipeline", [0, 2, 3, 4])
+@pytest.mark.parametrize("pipeline", [0, 2, 3, 4, 5])
 @pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
 def test_pivot_by_pivot_tableau(sense, pipeline):
     """One pivot per call: the tableau equals the oracle's after every pivot."""
@@ -134,7 +135,7 @@ def test_pivot_by_pivot_tableau(sense, pipeline):
 
 
 @pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
-@pytest.mark.parametrize("chunk,pipeline", [(7, 1), (1, 4), (2, 4), (3, 4), (7, 4), (5, 3)])
+@pytest.mark.parametrize("chunk,pipeline", [(7, 1), (1, 4), (2, 4), (3, 4), (7, 4), (5, 3), (1, 5), (3, 5)])
 def test_resume_in_chunks(chunk, pipeline, sense):
     """Pivot limits that end a launch inside a two-pivot pass or between passes."""
     A, b, c = lpgen.dense_lp(150, 180, seed=13)
@@ -177,7 +178,7 @@ def test_klee_minty_on_gpu():
         assert_same(g, _oracle(A, b, c))
 
 
-@pytest.mark.parametrize("pipeline", [1, 4])
+@pytest.mark.parametrize("pipeline", [1, 4, 5])
 @pytest.mark.parametrize("name", ["chvatal_cycling.txt", "beale_cycling.txt"])
 def test_cycling_examples_on_gpu(name, pipeline):
     g0 = read_lp(name)
@@ -213,7 +214,7 @@ def test_textbook_unbounded_infeasible_on_gpu():
     assert g.status == capi.LP_INFEASIBLE
 
 
-@pytest.mark.parametrize("pipeline", [1, 4])
+@pytest.mark.parametrize("pipeline", [1, 4, 5])
 def test_degenerate_integer_instances(pipeline):
     """Integer data with zeros in b: ties and degenerate pivots."""
     for seed in range(40):
@@ -243,10 +244,12 @@ def test_full_size_bitwise(m, n, sense):
     assert_same(g, o)
 
 
-@pytest.mark.parametrize("m,n", [(2048, 2048), (4096, 512)])
-def test_full_size_two_pivot_passes(m, n):
+@pytest.mark.parametrize("m,n,pipeline", [(2048, 2048, 4), (4096, 512, 4), (512, 4096, 5)])
+def test_full_size_two_pivot_passes(m, n, pipeline):
+    """Two pivots per pass at full size; 4 takes the distributed ratio test
+    for 2048 and 4096 rows and the per-CTA one for 512, 5 forces it."""
     A, b, c = lpgen.dense_lp(m, n, seed=0)
-    assert_same(Run(A, b, c, pipeline=4), _oracle(A, b, c))
+    assert_same(Run(A, b, c, pipeline=pipeline), _oracle(A, b, c))
 
 
 @pytest.mark.parametrize("pipeline,sense", [(1, MAX_LE), (3, MAX_LE), (1, MIN_GE)])
