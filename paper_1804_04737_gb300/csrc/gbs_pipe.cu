@@ -910,10 +910,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // next two pivots from T0 and the pass's pivots (Steps 2-3 twice):
 //   a: pricing records (each CTA's best column of the objective row of T2,
 //      with the pass's pivot-row values there and at the rhs) -> q_a; the
-//      whole column q_a and rhs of T2 in every CTA -> ratio test -> p_a;
+//      column q_a and rhs of T2 -> ratio test -> p_a;
 //   b: row p_a of T2 on each CTA's strip divided by the pivot (the pivot row
 //      of pivot a) and the objective row after pivot a -> pricing records ->
-//      q_b; column q_b and rhs after pivot a in every CTA -> p_b.
+//      q_b; column q_b and rhs after pivot a -> p_b.
+// The columns and the ratio test are either formed whole in every CTA, or
+// (DIST, tall tableaus) on each CTA's slice of rows with one ratio record per
+// CTA (ratio_slices), the whole columns then copied from global slots.
 // A pass holds one pivot when the next pivot ends the solve (optimal,
 // unbounded, iteration limit); the first pass of a launch holds the first
 // pivot alone.
