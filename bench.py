@@ -29,6 +29,10 @@ if ROOT not in sys.path:
 
 WORKLOAD_NAME = ("dense LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + 4096x512, "
                  "FP64, Dantzig pricing")
+# the same shapes from the paper's own random family (Sec. 4): density 0.9,
+# real-valued data, about 25 times the pivots of the integer family
+PAPER_WORKLOAD_NAME = ("paper-family LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + "
+                       "4096x512, density 0.9, FP64, Dantzig pricing")
 FP64_DFMA_PER_CLK_SM = 2          # GB300 FP64 rate: 1.25 TFLOP/s nominal = 2 DFMA/clk/SM
 SMS, SM_MAX_MHZ = 152, 2070.0
 HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal
@@ -37,14 +41,15 @@ MAX_LE, MIN_GE = 0, 1
 KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pipe.cu")
 
 
-def workload(seed):
+def workload(seed, family="dense"):
     from paper_1804_04737_gb300 import lpgen
+    gen = lpgen.dense_lp if family == "dense" else lpgen.paper_lp
     out = []
-    A, b, c = lpgen.dense_lp(2048, 2048, seed)
+    A, b, c = gen(2048, 2048, seed)
     out.append(("2048x2048 primal", A, b, c, MAX_LE))
     out.append(("2048x2048 dual form", *lpgen.dual_of(A, b, c), MIN_GE))
-    out.append(("512x4096 primal", *lpgen.dense_lp(512, 4096, seed), MAX_LE))
-    out.append(("4096x512 primal", *lpgen.dense_lp(4096, 512, seed), MAX_LE))
+    out.append(("512x4096 primal", *gen(512, 4096, seed), MAX_LE))
+    out.append(("4096x512 primal", *gen(4096, 512, seed), MAX_LE))
     return out
 
 
@@ -167,14 +172,16 @@ def reduce_over_ranks(dist, maxes, sums, device="cpu"):
     return a.tolist(), b.tolist()
 
 
-def cpu_oracle_run(lps, threads):
+def cpu_oracle_run(lps, threads, cap=None):
+    """Pivots and seconds of the oracle on the whole workload, each LP stopped
+    after `cap` pivots when given."""
     import oracle
     oracle.set_threads(threads)
     pivots = 0
     t0 = time.perf_counter()
     for _, A, b, c, sense in lps:
-        r = oracle.solve(A, b, c, sense=sense)
-        assert r.status == oracle.OPTIMAL
+        r = oracle.solve(A, b, c, sense=sense, max_iters=cap if cap else 10 ** 12)
+        assert r.status == (oracle.ITER_LIMIT if cap and r.iters == cap else oracle.OPTIMAL)
         pivots += r.iters
     return pivots, time.perf_counter() - t0
 
@@ -358,7 +365,7 @@ def main():
     ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="lp2048set",
-                    choices=["lp2048set", "lp8192", "batch1024", "serve"],
+                    choices=["lp2048set", "paperset", "lp8192", "batch1024", "serve"],
                     help="lp2048set is the headline line; the others report their own figures")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -374,7 +381,9 @@ def main():
     from paper_1804_04737_gb300 import capi
 
     torch.cuda.set_device(local)
-    if args.workload != "lp2048set":
+    family = "paper" if args.workload == "paperset" else "dense"
+    wname = PAPER_WORKLOAD_NAME if family == "paper" else WORKLOAD_NAME
+    if args.workload not in ("lp2048set", "paperset"):
         return {"lp8192": run_lp8192, "batch1024": run_batch,
                 "serve": run_serve}[args.workload](args, capi, torch)
     dist = None
@@ -382,7 +391,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
-    lps = workload(rank)
+    lps = workload(rank, family)
     dev_in = [(name, *(torch.from_numpy(v).cuda() for v in (A, b, c)), sense)
               for name, A, b, c, sense in lps]
     handles = [capi.lp_create(capi.lp_options_default(cuda_stream=stream, device=local))
@@ -503,12 +512,13 @@ def main():
 
     dominant = max(per_kernel, key=lambda k: per_kernel[k][1])
     roof = roofline_of(dominant)
-    roof["traffic"] = kernel_traffic(dominant)
+    # (the DRAM records are of the integer family's step)
+    roof["traffic"] = kernel_traffic(dominant) if family == "dense" else None
     others = []
     for k in per_kernel:
         if k != dominant:
             r = roofline_of(k)
-            r["traffic"] = kernel_traffic(k)
+            r["traffic"] = kernel_traffic(k) if family == "dense" else None
             others.append(r)
     roof["others"] = others
     line = {
@@ -516,7 +526,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "seed": "rank", "lps": [n for n, *_ in lps],
+        "config": {"workload": wname, "seed": "rank", "lps": [n for n, *_ in lps],
                    "pivots_per_step": pivots // args.steps,
                    "l2": "flushed between steps (256 MiB write), outside the step events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -530,16 +540,21 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         # the whole workload, repeated until about 10 s of oracle time
         cores = len(os.sched_getaffinity(0))
+        # the paper family's LPs take thousands of pivots: the sample stops
+        # each LP after a fixed number of them
+        cap, cap1 = (200, 20) if family == "paper" else (None, None)
         p, t, reps = 0, 0.0, 0
         while t < 10.0 and reps < 1000:
-            dp, dt = cpu_oracle_run(lps, cores)
+            dp, dt = cpu_oracle_run(lps, cores, cap)
             p, t, reps = p + dp, t + dt, reps + 1
-        p1, t1 = cpu_oracle_run(lps, 1)
+        p1, t1 = cpu_oracle_run(lps, 1, cap1)
+        what = "the whole workload (4 LPs)" if cap is None else "the first %d pivots of each LP" % cap
+        what1 = "the whole workload" if cap1 is None else "the first %d pivots of each LP" % cap1
         line["cpu_baseline"] = {"value": p / t, "unit": "pivots/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": "the whole workload (4 LPs) %d times, %.1f s" % (reps, t),
+                                "sample": "%s %d times, %.1f s" % (what, reps, t),
                                 "single_thread": {"value": p1 / t1, "unit": "pivots/s",
-                                                  "sample": "the whole workload once, %.1f s" % t1}}
+                                                  "sample": "%s once, %.1f s" % (what1, t1)}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -2,8 +2,10 @@
 
 These stand in for the paper's random instances (Sec. 4 generates dense LPs
 of sizes 256..8192 with an Octave routine whose text is garbled and whose
-random stream is not reproducible here).  Both the CUDA library's tests and
-the CPU oracle take their inputs from this module.
+random stream is not reproducible here): ``dense_lp`` is the main family
+(integer data, exact in FP32), ``paper_lp`` follows the paper's own
+distribution.  Both the CUDA library's tests and the CPU oracle take their
+inputs from this module.
 
 Dense workload (one LP):
   A_ij  iid uniform integers in [1, 1000]     (row-major, drawn first)
@@ -23,6 +25,35 @@ def dense_lp(m: int, n: int, seed: int = 0):
     b = rng.integers(1000, 100001, size=m).astype(np.float64)
     c = rng.integers(1, 101, size=n).astype(np.float64)
     return A, b, c
+
+
+def paper_lp(m: int, n: int, seed: int = 0, density: float = 0.9):
+    """(A, b, c) of one LP of the paper's own random family (Sec. 4), float64.
+
+    The paper draws A with a given density (0.9 in its runs) and nonzeros
+    uniform on (0, 50), a point x0 with entries uniform on [0, 10), b = A x0
+    (so x0 is feasible and b >= 0), and an objective row A'u for a random
+    vector u, redrawn until that row has a negative entry.  The listing that
+    states this is garbled (its objective assignment reads "c=A'"); the reading
+    taken here is objective row = A'u with u_i = [r1 > r2] (r3 - r4) for
+    uniform r's, as its other lines define u.  In the form max c'x, Ax <= b
+    used here the objective row is -c, so c = -A'u.
+
+    Draw order (``numpy.random.default_rng(seed)``), repeated until c has a
+    positive entry: A's values, A's mask, x0, then r1, r2, r3, r4 (m each).
+    Unlike ``dense_lp`` the values are not integers: FP32 holds them rounded."""
+    rng = np.random.default_rng(seed)
+    while True:
+        vals = 50.0 * rng.random((m, n))
+        mask = rng.random((m, n)) < density
+        A = np.where(mask, vals, 0.0)
+        x0 = 10.0 * rng.random(n)
+        b = A @ x0
+        r1, r2, r3, r4 = (rng.random(m) for _ in range(4))
+        u = np.where(r1 > r2, r3 - r4, 0.0)
+        c = -(A.T @ u)
+        if np.any(c > 0):
+            return (np.ascontiguousarray(A), np.ascontiguousarray(b), np.ascontiguousarray(c))
 
 
 def dual_of(A, b, c):

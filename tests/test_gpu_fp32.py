@@ -120,3 +120,20 @@ def test_fp32_unbounded():
     obj, st, *_ = _fp32(np.array([[1.0, -1.0], [2.0, 0.0]]), np.array([4.0, 6.0]),
                         np.array([1.0, 3.0]))
     assert st == capi.LP_UNBOUNDED
+
+
+@pytest.mark.parametrize("m,n,sense", [(512, 512, MAX_LE), (1024, 1024, MAX_LE), (1024, 1024, MIN_GE)])
+def test_fp32_paper_family_objective(m, n, sense):
+    """The paper's random family (real-valued data, which FP32 rounds; about
+    1400 pivots at 1024^2): FP32 pivoting with FP64 reinversion still ends at
+    the FP64 optimum within the tolerance, with an FP64 certificate."""
+    A, b, c = lpgen.paper_lp(m, n, seed=2)
+    if sense == MIN_GE:
+        A, b, c = lpgen.dual_of(A, b, c)
+    o = oracle.solve(A, b, c, sense=sense)
+    obj, st, it, x, y, _ = _fp32(A, b, c, sense)
+    assert st == capi.LP_OPTIMAL
+    assert _rel(obj, o.obj) <= OBJ_TOL, (obj, o.obj)
+    cert = oracle.certificate(A, b, c, x, y, obj, sense=sense)
+    scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
+    assert max(cert.values()) <= 1e-9 * scale * 1e3, cert

@@ -333,3 +333,38 @@ def test_bounded_wait_times_out_and_context_survives():
     assert capi.LP_TIMEOUT in seen
     g = Run(A, b, c)
     assert g.status == capi.LP_OPTIMAL and g.obj == o.obj
+
+
+_PAPER_ORACLE = {}
+
+
+def _paper_case(m, n, sense, seed=1):
+    """An LP of the paper's own random family and its oracle run (cached: the
+    pivot-mode cases share them)."""
+    A, b, c = lpgen.paper_lp(m, n, seed=seed)
+    if sense == MIN_GE:
+        A, b, c = lpgen.dual_of(A, b, c)
+    key = (m, n, sense, seed)
+    if key not in _PAPER_ORACLE:
+        _PAPER_ORACLE[key] = _oracle(A, b, c, sense)
+    return A, b, c, _PAPER_ORACLE[key]
+
+
+@pytest.mark.parametrize("pipeline", [1, 2, 4, 5])
+@pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
+@pytest.mark.parametrize("m,n", [(40, 61), (257, 100), (100, 300), (512, 512), (1024, 1024)])
+def test_paper_family_bitwise(m, n, sense, pipeline):
+    """LPs of the paper's own random family (density 0.9, real-valued data;
+    1445 pivots at 1024^2, against 40 for the integer family): every pivot and
+    every bit as the oracle, in each primal kernel mode."""
+    A, b, c, o = _paper_case(m, n, sense)
+    assert o.status == oracle.OPTIMAL
+    assert_same(Run(A, b, c, sense, pipeline=pipeline), o)
+
+
+@pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
+def test_paper_family_2048_bitwise(sense):
+    """2048^2 of the paper's family (2172 pivots), default launch."""
+    A, b, c, o = _paper_case(2048, 2048, sense)
+    assert o.status == oracle.OPTIMAL and o.iters > 2000
+    assert_same(Run(A, b, c, sense), o)

@@ -192,11 +192,12 @@ def test_zero_and_trivial_sizes():
     assert r.status == oracle.OPTIMAL and r.obj == 1.5 and r.iters == 1
 
 
+@pytest.mark.parametrize("gen", ["dense_lp", "paper_lp"])
 @pytest.mark.parametrize("m,n", [(64, 64), (96, 200), (200, 96)])
-def test_generator_instances_certificate_and_linprog(m, n):
-    """Dense generator LPs: optimality certificate, and the optimum of a
-    library LP solver (HiGHS via scipy)."""
-    A, b, c = lpgen.dense_lp(m, n, seed=3)
+def test_generator_instances_certificate_and_linprog(m, n, gen):
+    """Generator LPs (both families): optimality certificate, and the optimum
+    of a library LP solver (HiGHS via scipy)."""
+    A, b, c = getattr(lpgen, gen)(m, n, seed=3)
     r = oracle.solve(A, b, c)
     assert r.status == oracle.OPTIMAL
     cert = oracle.certificate(A, b, c, r.x, r.y, r.obj)
@@ -208,11 +209,12 @@ def test_generator_instances_certificate_and_linprog(m, n):
     assert _rel(r.obj, -res.fun) <= 1e-9
 
 
+@pytest.mark.parametrize("gen", ["dense_lp", "paper_lp"])
 @pytest.mark.parametrize("m,n", [(64, 64), (50, 120), (120, 50)])
-def test_dual_form_matches_primal(m, n):
+def test_dual_form_matches_primal(m, n, gen):
     """Sec. 4 solves each problem in primal and dual formulation: the same
     optimum, x of one is y of the other."""
-    A, b, c = lpgen.dense_lp(m, n, seed=5)
+    A, b, c = getattr(lpgen, gen)(m, n, seed=5)
     rp = oracle.solve(A, b, c)
     Ad, bd, cd = lpgen.dual_of(A, b, c)
     rd = oracle.solve(Ad, bd, cd, sense=oracle.MIN_GE)
@@ -280,3 +282,20 @@ def test_input_validation():
         oracle.solve(np.ones((2, 2)), np.array([1.0, -1.0]), np.ones(2))
     with pytest.raises(ValueError):
         oracle.solve(np.ones((2, 2)), np.ones(2), np.array([1.0, -1.0]), sense=oracle.MIN_GE)
+
+
+def test_paper_family_generator():
+    """The paper's random family (Sec. 4): density 0.9, nonzeros in (0, 50),
+    b = A x0 >= 0 for some x0 >= 0 (so x0 is feasible), an objective with an
+    improving column; the same seed gives the same LP."""
+    A, b, c = lpgen.paper_lp(300, 400, seed=7)
+    assert A.shape == (300, 400) and b.shape == (300,) and c.shape == (400,)
+    assert abs(float(np.mean(A > 0)) - 0.9) < 0.01
+    assert float(A.min()) >= 0.0 and float(A.max()) < 50.0
+    assert np.all(b >= 0) and np.any(c > 0)
+    # b lies in the cone of A's columns: a nonnegative x with A x = b exists
+    sp = pytest.importorskip("scipy.optimize")
+    x, res = sp.nnls(A, b)
+    assert res <= 1e-9 * float(np.linalg.norm(b))
+    A2, b2, c2 = lpgen.paper_lp(300, 400, seed=7)
+    assert np.array_equal(A, A2) and np.array_equal(b, b2) and np.array_equal(c, c2)
