@@ -9,8 +9,9 @@
  * (Step 3) and the rank-1 tableau update (Steps 4-5).
  *
  * Problem forms (Sec. 2, Eq. 1 with m <= constraints and slack variables):
- *   LP_MAX_LE  max c'x  s.t. Ax <= b, x >= 0   (needs b >= 0: the slack basis
- *              is feasible; solved by the primal simplex)
+ *   LP_MAX_LE  max c'x  s.t. Ax <= b, x >= 0   (solved by the primal simplex
+ *              from the slack basis, which b >= 0 makes feasible; with some
+ *              b_i < 0, single FP64 solves go through Phase I, below)
  *   LP_MIN_GE  min c'x  s.t. Ax >= b, x >= 0   (needs c >= 0: the slack basis
  *              is dual feasible; solved by the dual simplex).  Loading
  *              (A', c, b) of a LP_MAX_LE problem in this form solves its LP
@@ -30,7 +31,18 @@
  *   dual      leaving row: most negative rhs below -eps_r (ties smallest
  *             row; Bland mode: smallest basic index); entering column: the
  *             smallest (z_j > 0 ? z_j : 0) / (-T[r][j]) over T[r][j] < -eps_p,
- *             ties smallest j; none => LP_INFEASIBLE.
+ *             ties smallest j; none => LP_INFEASIBLE;
+ *   Phase I   (not in the paper; LP_MAX_LE with some b_i < 0, lp_load and
+ *             lp_solve in FP64) Phase 1 builds the objective row
+ *             [max(-c, 0) | 0 | 0], dual feasible in the slack basis, and
+ *             runs the dual rule until no rhs is below -eps_r (LP_INFEASIBLE
+ *             when a violated row has no entering column); Phase 2 sets the
+ *             objective row to z_j = -c_j + sum_i c_B(i) T[i][j] (c_j = 0 for
+ *             slacks, the rhs column included), summed over the rows in
+ *             increasing order with one fma per row whose basic variable is
+ *             structural, restarts the Bland count and runs the primal rule.
+ *             Pivots are counted and traced across both phases.  lp_solve
+ *             waits for Phase 1 to end before it launches Phase 2.
  *
  * FP32 mode (LP_FP32_REINV; not in the paper): the tableau is FP32, which
  * halves the bytes of the rank-1 update.  Every reinv_k pivots and at
@@ -75,8 +87,9 @@ typedef enum {
     LP_ERR_INVALID_ARG = 1,      /* bad size, NULL pointer, NaN/Inf input      */
     LP_ERR_OOM = 2,              /* device allocation failed or over budget     */
     LP_ERR_CUDA = 3,             /* a CUDA call failed (message in last_error)  */
-    LP_ERR_INFEASIBLE_START = 4, /* LP_MAX_LE with some b_i < 0, or LP_MIN_GE
-                                    with some c_j < 0: needs a Phase I          */
+    LP_ERR_INFEASIBLE_START = 4, /* LP_MIN_GE with some c_j < 0, or LP_MAX_LE
+                                    with some b_i < 0 where no Phase I runs
+                                    (FP32 mode, batches, serving, noalloc)     */
     LP_ERR_STATE = 5,            /* call order (solve before load, ...)         */
     LP_ERR_BUSY = 6              /* server: no free slot / budget right now     */
 } lp_err;
@@ -148,8 +161,11 @@ lp_err lp_create(lp_handle **out, const lp_options *opt);
  * rows [A | I | b], objective row [-c | 0 | 0]; for LP_MIN_GE rows
  * [-A | I | -b] and objective row [c | 0 | 0]).  A is m x n row-major, b has
  * m entries, c has n entries; each may be host or device memory.  m, n >= 1.
- * Replaces any LP loaded before.  Errors: LP_ERR_INVALID_ARG (size, NULL,
- * non-finite value), LP_ERR_INFEASIBLE_START, LP_ERR_OOM, LP_ERR_CUDA. */
+ * Replaces any LP loaded before.  LP_MAX_LE with some b_i < 0 is taken in
+ * FP64 mode, with Phase I (the header's top).  Errors: LP_ERR_INVALID_ARG
+ * (size, NULL, non-finite value), LP_ERR_INFEASIBLE_START (LP_MIN_GE with
+ * some c_j < 0; LP_MAX_LE with some b_i < 0 in FP32 mode), LP_ERR_OOM,
+ * LP_ERR_CUDA. */
 lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b,
                const double *c, lp_sense sense);
 

@@ -47,6 +47,10 @@ def _bind(lib):
     llp = ctypes.POINTER(ctypes.c_longlong)
     lib.oracle_build.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int, dp, ip]
     lib.oracle_build.restype = None
+    lib.oracle_build_phase1.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ip]
+    lib.oracle_build_phase1.restype = None
+    lib.oracle_phase2_objective.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp]
+    lib.oracle_phase2_objective.restype = None
     lib.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                ctypes.c_longlong, llp, ip, ip, ip, ctypes.c_longlong]
@@ -111,7 +115,15 @@ class OracleResult:
 
 
 class OracleTableau:
-    """Step 1 (Sec. 2) once, then any number of resumable pivot runs."""
+    """Step 1 (Sec. 2) once, then any number of resumable pivot runs.
+
+    The primal form with some b_i < 0 (not covered by the paper's Sec. 2)
+    goes through Phase I: Phase 1 prices with c' = min(c, 0), whose slack
+    basis is dual feasible, and runs the dual simplex until every rhs is
+    >= -eps_r (or the LP proves infeasible); Phase 2 rebuilds the objective
+    row for c in that basis (oracle_phase2_objective), restarts the
+    degenerate-pivot count and runs the primal simplex.  Pivots are counted
+    and traced across both phases."""
 
     def __init__(self, A, b, c, sense=MAX_LE, eps_d=None, eps_p=None, eps_r=None,
                  bland_after=32, trace_cap=0):
@@ -120,8 +132,6 @@ class OracleTableau:
         c = np.ascontiguousarray(c, dtype=np.float64)
         m, n = A.shape
         assert b.shape == (m,) and c.shape == (n,)
-        if sense == MAX_LE and np.any(b < 0):
-            raise ValueError("primal form needs b >= 0 (slack basis feasible, Sec. 2)")
         if sense == MIN_GE and np.any(c < 0):
             raise ValueError("dual form needs c >= 0 (slack basis dual feasible)")
         d, p, r = default_eps(A, b, c)
@@ -132,7 +142,13 @@ class OracleTableau:
         self.bland_after = int(bland_after)
         self.T = np.empty((m + 1, n + m + 1), dtype=np.float64)
         self.basis = np.empty(m, dtype=np.int32)
-        _load().oracle_build(m, n, _dp(A), _dp(b), _dp(c), sense, _dp(self.T), _ip(self.basis))
+        self.c = c
+        # 0: no Phase I; 1: Phase 1 (dual simplex on c' = min(c, 0)); 2: Phase 2
+        self.phase = 1 if sense == MAX_LE and np.any(b < 0) else 0
+        if self.phase:
+            _load().oracle_build_phase1(m, n, _dp(A), _dp(b), _dp(c), _dp(self.T), _ip(self.basis))
+        else:
+            _load().oracle_build(m, n, _dp(A), _dp(b), _dp(c), sense, _dp(self.T), _ip(self.basis))
         self.iters = ctypes.c_longlong(0)
         self.deg = ctypes.c_int(0)
         self.trace_cap = int(trace_cap)
@@ -140,16 +156,29 @@ class OracleTableau:
         self.trace_q = np.full(max(self.trace_cap, 1), -1, dtype=np.int32)
         self.status = None
 
-    def run(self, max_iters: int = 10 ** 12) -> int:
-        """Pivot until a terminal status or until `max_iters` pivots in total."""
+    def _run_rule(self, rule, max_iters):
         tp = _ip(self.trace_p) if self.trace_cap else None
         tq = _ip(self.trace_q) if self.trace_cap else None
-        st = _load().oracle_run(self.m, self.n, self.sense, _dp(self.T), _ip(self.basis),
+        st = _load().oracle_run(self.m, self.n, rule, _dp(self.T), _ip(self.basis),
                                 self.eps_d, self.eps_p, self.eps_r, self.bland_after,
                                 int(max_iters), ctypes.byref(self.iters), ctypes.byref(self.deg),
                                 tp, tq, self.trace_cap)
         if st < 0:
             raise MemoryError("oracle scratch allocation failed")
+        return st
+
+    def run(self, max_iters: int = 10 ** 12) -> int:
+        """Pivot until a terminal status or until `max_iters` pivots in total."""
+        if self.phase == 1:
+            st = self._run_rule(MIN_GE, max_iters)  # the dual simplex rule
+            if st != OPTIMAL:  # INFEASIBLE, or ITER_LIMIT (resumable in Phase 1)
+                self.status = st
+                return st
+            _load().oracle_phase2_objective(self.m, self.n, _dp(self.T), _ip(self.basis),
+                                            _dp(self.c))
+            self.phase = 2
+            self.deg.value = 0
+        st = self._run_rule(MAX_LE if self.phase else self.sense, max_iters)
         self.status = st
         return st
 

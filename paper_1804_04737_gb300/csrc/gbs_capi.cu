@@ -52,6 +52,7 @@ struct lp_handle {
     bool loaded = false;
     bool solved = false;
     int m = 0, n = 0, M = 0, N = 0, sense = 0, prec = PREC_FP64;
+    int phase = 0;  // Phase I (primal form, some b_i < 0): 1 in Phase 1, 2 after it; 0 without
     long long P = 0;
     double eps_d = 0, eps_p = 0, eps_r = 0;
 
@@ -282,6 +283,35 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
+    // the inputs, and what they allow: a primal form with some b_i < 0 goes
+    // through Phase I (FP64 single solves; not in the paper)
+    CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
+    CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
+    CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
+    InputStats st;
+    {
+        cudaStream_t s0 = h->stream;
+        CUDA_TRY(h, cudaMemcpyAsync(h->dA, A, sizeof(double) * (size_t)m * n, cudaMemcpyDefault, s0));
+        CUDA_TRY(h, cudaMemcpyAsync(h->db, b, sizeof(double) * (size_t)m, cudaMemcpyDefault, s0));
+        CUDA_TRY(h, cudaMemcpyAsync(h->dc, c, sizeof(double) * (size_t)n, cudaMemcpyDefault, s0));
+        CUDA_TRY(h, launch_inspect(h->dA, h->db, h->dc, m, n, h->dstats, s0));
+        CUDA_TRY(h, cudaMemcpyAsync(&st, h->dstats, sizeof st, cudaMemcpyDeviceToHost, s0));
+        CUDA_TRY(h, cudaStreamSynchronize(s0));
+    }
+    if (st.flags & 4) {
+        set_err(h, "lp_load: A, b or c holds a NaN or infinity");
+        return LP_ERR_INVALID_ARG;
+    }
+    const bool phase1 = sense == LP_MAX_LE && (st.flags & 1);
+    if (phase1 && h->prec != PREC_FP64) {
+        set_err(h, "lp_load: max form with some b < 0 needs Phase I, which the FP64 mode has "
+                   "(the FP32 mode needs b >= 0)");
+        return LP_ERR_INFEASIBLE_START;
+    }
+    if (sense == LP_MIN_GE && (st.flags & 2)) {
+        set_err(h, "lp_load: min form needs c >= 0 (the slack basis must be dual feasible)");
+        return LP_ERR_INFEASIBLE_START;
+    }
     // the pipelined kernels where they can take the LP: the primal rule in
     // place for small tableaus and two pivots per pass above, the dual rule
     // double-buffered (the rule runs for its sense, and in FP32 mode for both)
@@ -290,7 +320,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         return LP_ERR_INVALID_ARG;
     }
     const bool primal = sense == LP_MAX_LE || h->prec == PREC_FP32;
-    const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32;
+    const bool dualr = sense == LP_MIN_GE || h->prec == PREC_FP32 || phase1;
     int pmode = primal ? h->opt.pipeline : 0;
     const bool force_dist = pmode == 5;  // 5: as 4, the ratio test always distributed
     if (pmode == 5) pmode = 4;
@@ -343,18 +373,16 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         return choose_shape(h->prec, rule, M, N, P, h->sms, h->opt.threads, h->opt.ctas);
     };
     const PivotShape sh = shape_for((int)sense);
-    // the other rule (FP32 recovery)
+    // the other rule (FP32 recovery, Phase 1 of Phase I)
     const PivotShape sh_alt = shape_for(1 - (int)sense);
-    const int ctas_max = h->prec == PREC_FP32 ? std::max(sh.ctas, sh_alt.ctas) : sh.ctas;
+    const bool two_rules = h->prec == PREC_FP32 || phase1;
+    const int ctas_max = two_rules ? std::max(sh.ctas, sh_alt.ctas) : sh.ctas;
 
-    CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
-    CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
-    CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
     CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
     CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
     {
         size_t need = sh.use_smem ? 0 : (size_t)sh.ctas * (size_t)sh.scratch_stride;
-        if (h->prec == PREC_FP32 && !sh_alt.use_smem)
+        if (two_rules && !sh_alt.use_smem)
             need = std::max(need, (size_t)sh_alt.ctas * (size_t)sh_alt.scratch_stride);
         if (need) CUDA_TRY(h, grow_bytes(&h->dscratch, &h->cap_scratch, need));
     }
@@ -379,25 +407,6 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     CUDA_TRY(h, grow(&h->dy, &h->cap_y, (size_t)m));
 
     cudaStream_t s = h->stream;
-    CUDA_TRY(h, cudaMemcpyAsync(h->dA, A, sizeof(double) * (size_t)m * n, cudaMemcpyDefault, s));
-    CUDA_TRY(h, cudaMemcpyAsync(h->db, b, sizeof(double) * (size_t)m, cudaMemcpyDefault, s));
-    CUDA_TRY(h, cudaMemcpyAsync(h->dc, c, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
-    CUDA_TRY(h, launch_inspect(h->dA, h->db, h->dc, m, n, h->dstats, s));
-    InputStats st;
-    CUDA_TRY(h, cudaMemcpyAsync(&st, h->dstats, sizeof st, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(h, cudaStreamSynchronize(s));
-    if (st.flags & 4) {
-        set_err(h, "lp_load: A, b or c holds a NaN or infinity");
-        return LP_ERR_INVALID_ARG;
-    }
-    if (sense == LP_MAX_LE && (st.flags & 1)) {
-        set_err(h, "lp_load: max form needs b >= 0 (the slack basis must be feasible)");
-        return LP_ERR_INFEASIBLE_START;
-    }
-    if (sense == LP_MIN_GE && (st.flags & 2)) {
-        set_err(h, "lp_load: min form needs c >= 0 (the slack basis must be dual feasible)");
-        return LP_ERR_INFEASIBLE_START;
-    }
     const double amax = bits_to_double(st.amax_bits), bmax = bits_to_double(st.bmax_bits),
                  cmax = bits_to_double(st.cmax_bits);
     h->eps_d = h->opt.eps_d > 0 ? h->opt.eps_d : 1e-9 * std::max(1.0, cmax);
@@ -433,7 +442,8 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         h->cap_rb = cap;
     }
 
-    CUDA_TRY(h, launch_build(h->prec, h->dA, h->db, h->dc, m, n, (int)sense, h->dT, P, h->dbasis, s));
+    CUDA_TRY(h, launch_build(h->prec, h->dA, h->db, h->dc, m, n, phase1 ? 2 : (int)sense, h->dT, P,
+                             h->dbasis, s));
 
     LpDesc d{};
     d.T = h->dT;
@@ -474,6 +484,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     h->N = N;
     h->P = P;
     h->sense = (int)sense;
+    h->phase = phase1 ? 1 : 0;
     h->loaded = true;
     return LP_OK;
 }
@@ -656,10 +667,40 @@ lp_err lp_solve_async(lp_handle *h) {
     cudaStream_t s = h->stream;
     // The pivot state (iterations, degeneracy counter) lives in the device
     // descriptor, so consecutive calls resume without a host round trip.
-    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, kBarWords * sizeof(unsigned), s));
+    long long budget = h->opt.max_iters;
     CUDA_TRY(h, cudaEventRecord(h->ev0, s));
-    CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape, h->opt.spin_timeout_cycles,
-                             h->opt.max_iters, s));
+    if (h->phase == 1) {
+        // Phase I, Phase 1: the dual simplex rule on the tableau whose
+        // objective row is max(-c, 0), until no rhs is below -eps_r.  The
+        // host waits for its end to choose what follows.
+        const long long before = h->pdesc->iters;
+        CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, kBarWords * sizeof(unsigned), s));
+        CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape_alt, h->opt.spin_timeout_cycles,
+                                 budget, s));
+        CUDA_TRY(h, cudaMemcpyAsync(h->pdesc, h->ddesc, sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        adopt_tableau(h);
+        if (h->pdesc->status == ST_OPTIMAL) {
+            // Phase 2 from this basis: the objective row of c, the
+            // degenerate-pivot count restarted
+            CUDA_TRY(h, launch_phase2_objective(h->ddesc, h->dc, h->N, s));
+            const int zero = 0;
+            CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, deg), &zero, sizeof zero,
+                                        cudaMemcpyHostToDevice, s));
+            h->phase = 2;
+            budget -= h->pdesc->iters - before;
+        } else {
+            // infeasible (or stopped: iteration limit, timeout; resumable in Phase 1)
+            CUDA_TRY(h, cudaEventRecord(h->ev1, s));
+            CUDA_TRY(h, launch_extract(h->prec, h->ddesc, h->dT, h->dbasis, h->m, h->n, h->P,
+                                       h->sense, h->dx, h->dy, h->dobj, s));
+            CUDA_TRY(h, cudaMemcpyAsync(h->pobj, h->dobj, sizeof(double), cudaMemcpyDeviceToHost, s));
+            h->solved = true;
+            return LP_OK;
+        }
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->dbar, 0, kBarWords * sizeof(unsigned), s));
+    CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape, h->opt.spin_timeout_cycles, budget, s));
     CUDA_TRY(h, cudaEventRecord(h->ev1, s));
     CUDA_TRY(h, launch_extract(h->prec, h->ddesc, h->dT, h->dbasis, h->m, h->n, h->P, h->sense,
                                h->dx, h->dy, h->dobj, s));

@@ -105,8 +105,13 @@ inline long long pitch_for(int N) { return ((long long)N + 31) / 32 * 32; }
 // status.
 cudaError_t launch_inspect(const double *A, const double *b, const double *c, int m, int n,
                            InputStats *out, cudaStream_t s);
+// sense 0 primal form, 1 dual form, 2 Phase 1 of Phase I (primal rows,
+// objective row max(-c, 0))
 cudaError_t launch_build(int prec, const double *A, const double *b, const double *c, int m,
                          int n, int sense, void *T, long long P, int *basis, cudaStream_t s);
+// Phase I, the start of Phase 2 (FP64): the objective row of max c'x in the
+// current basis, over the N columns of the tableau the descriptor names.
+cudaError_t launch_phase2_objective(const LpDesc *d_desc, const double *c, int N, cudaStream_t s);
 PivotShape choose_shape(int prec, int sense, int M, int N, long long P, int sms, int threads,
                         int ctas);
 cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long long spin_limit,

@@ -708,14 +708,16 @@ __global__ void __launch_bounds__(256) inspect_kernel(const double *__restrict__
 
 // Sec. 2 Step 1: the initial tableau (rows [A | I | b], objective row
 // [-c | 0 | 0]; dual form [-A | I | -b] and [c | 0 | 0]), padded with zeros
-// to the pitch P.
+// to the pitch P.  sense 2 is Phase 1 of Phase I (not in the paper): the
+// rows of the primal form with the objective row [max(-c, 0) | 0 | 0], whose
+// slack basis is dual feasible although some b_i < 0.
 template <typename T>
 __global__ void build_kernel(const double *__restrict__ A, const double *__restrict__ b,
                              const double *__restrict__ c, int m, int n, int sense,
                              T *__restrict__ Tab, long long P, int *__restrict__ basis) {
     const int N = n + m + 1;
     const long long total = (long long)(m + 1) * P;
-    const double sg = sense == 0 ? 1.0 : -1.0;
+    const double sg = sense == 1 ? -1.0 : 1.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += stride) {
         const int i = (int)(k / P);
@@ -726,12 +728,32 @@ __global__ void build_kernel(const double *__restrict__ A, const double *__restr
             else if (j == n + i) v = 1.0;
             else if (j == N - 1) v = sg * b[i];
         } else if (j < n) {
-            v = -sg * c[j];
+            v = sense == 2 ? (c[j] < 0.0 ? -c[j] : 0.0) : -sg * c[j];
         }
         Tab[k] = (T)v;
     }
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += stride)
         basis[k] = n + (int)k;
+}
+
+// Phase I, the start of Phase 2: the objective row of max c'x in the basis
+// Phase 1 ended with, z_j = -c_j + sum_i c_B(i) T[i][j] (c_j = 0 for slack
+// columns; the rhs column gives the objective value), summed over the rows
+// in increasing order with one fma per row whose basic variable is
+// structural (slack-basic rows cost 0).  One thread per column; FP64.
+__global__ void phase2_objective_kernel(const LpDesc *__restrict__ d, const double *__restrict__ c) {
+    double *Tab = reinterpret_cast<double *>(d->T);  // the buffer Phase 1 left current
+    const int m = d->m, n = d->n, N = d->N;
+    const long long P = d->P;
+    const int *basis = d->basis;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        double z = j < n ? -c[j] : 0.0;
+        for (int i = 0; i < m; ++i) {
+            const int bi = basis[i];
+            if (bi < n) z = fma(c[bi], Tab[(long long)i * P + j], z);
+        }
+        Tab[(long long)m * P + j] = z;
+    }
 }
 
 // Solution read-off, part 1: zero x, duals from the objective row, objective.
@@ -791,6 +813,11 @@ cudaError_t launch_inspect(const double *A, const double *b, const double *c, in
     if (e != cudaSuccess) return e;
     const long long work = (long long)m * n / 8;  // ~8 elements per thread
     inspect_kernel<<<grid_for(work, 256), 256, 0, s>>>(A, b, c, m, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase2_objective(const LpDesc *d_desc, const double *c, int N, cudaStream_t s) {
+    phase2_objective_kernel<<<(N + 255) / 256, 256, 0, s>>>(d_desc, c);
     return cudaGetLastError();
 }
 

@@ -56,6 +56,27 @@ def paper_lp(m: int, n: int, seed: int = 0, density: float = 0.9):
             return (np.ascontiguousarray(A), np.ascontiguousarray(b), np.ascontiguousarray(c))
 
 
+def with_ge_rows(A, b, frac: float = 0.1, seed: int = 0):
+    """(A', b') with a fraction of the rows of a positive LP turned into >=
+    rows that the origin violates, so that the primal form needs Phase I.
+
+    With x0 = t * 1 for t = min_i b_i / sum_j A_ij / 2 (so A x0 <= b / 2 on
+    every row), each chosen row i (``numpy.random.default_rng(seed)``,
+    without replacement) becomes a_i x >= a_i x0 / 2, stored as
+    -a_i x <= -(a_i x0) / 2.  x0 satisfies every row, so the LP is feasible,
+    and the rows left as <= rows keep it bounded when A > 0."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    b = np.array(b, dtype=np.float64, copy=True)
+    m = A.shape[0]
+    rs = A.sum(axis=1)
+    t = 0.5 * float(np.min(b / rs))
+    k = max(1, int(round(frac * m)))
+    rows = np.random.default_rng(seed).choice(m, size=min(k, m), replace=False)
+    b[rows] = -0.5 * t * rs[rows]
+    A[rows] = -A[rows]
+    return A, b
+
+
 def dual_of(A, b, c):
     """Data of the dual LP  min b'y  s.t.  A'y >= c, y >= 0  as (A', c, b).
 

@@ -279,8 +279,6 @@ def test_resume_and_threads_bitwise():
 
 def test_input_validation():
     with pytest.raises(ValueError):
-        oracle.solve(np.ones((2, 2)), np.array([1.0, -1.0]), np.ones(2))
-    with pytest.raises(ValueError):
         oracle.solve(np.ones((2, 2)), np.ones(2), np.array([1.0, -1.0]), sense=oracle.MIN_GE)
 
 
@@ -299,3 +297,105 @@ def test_paper_family_generator():
     assert res <= 1e-9 * float(np.linalg.norm(b))
     A2, b2, c2 = lpgen.paper_lp(300, 400, seed=7)
     assert np.array_equal(A, A2) and np.array_equal(b, b2) and np.array_equal(c, c2)
+
+
+# ---- Phase I (the primal form with some b_i < 0; not in the paper) ----
+
+def _small_mixed(rng, lo=1, hi=7):
+    m, n = (int(v) for v in rng.integers(lo, hi, size=2))
+    A = rng.integers(-5, 6, size=(m, n)).astype(float)
+    b = rng.integers(-6, 10, size=m).astype(float)
+    c = rng.integers(-3, 6, size=n).astype(float)
+    return A, b, c
+
+
+def test_phase1_vs_highs():
+    """Random small LPs with negative right-hand sides: status and optimum
+    agree with HiGHS (its presolve's "infeasible or unbounded" is settled by
+    a feasibility solve)."""
+    sp = pytest.importorskip("scipy.optimize")
+    rng = np.random.default_rng(11)
+    seen = set()
+    for _ in range(600):
+        A, b, c = _small_mixed(rng)
+        r = oracle.solve(A, b, c)
+        res = sp.linprog(-c, A_ub=A, b_ub=b, bounds=(0, None), method="highs")
+        if res.status not in (0, 2, 3):
+            continue  # HiGHS gave no answer (numerical difficulties)
+        if res.status == 2:
+            feas = sp.linprog(np.zeros(len(c)), A_ub=A, b_ub=b, bounds=(0, None),
+                              method="highs").status == 0
+            want = oracle.UNBOUNDED if feas else oracle.INFEASIBLE
+        else:
+            want = {0: oracle.OPTIMAL, 3: oracle.UNBOUNDED}[res.status]
+        assert r.status == want, (A, b, c, r.status, res.status)
+        if want == oracle.OPTIMAL:
+            assert _rel(r.obj, -res.fun) <= 1e-9
+            assert np.all(A @ r.x <= b + 1e-9) and np.all(r.x >= -1e-12)
+        seen.add(want)
+    assert seen == {oracle.OPTIMAL, oracle.UNBOUNDED, oracle.INFEASIBLE}
+
+
+def test_phase1_brute_force():
+    """Bounded LPs with some b_i < 0: the optimum equals the best vertex."""
+    rng = np.random.default_rng(12)
+    done = 0
+    for _ in range(400):
+        m, n = (int(v) for v in rng.integers(2, 6, size=2))
+        A = rng.integers(-4, 6, size=(m, n)).astype(float)
+        b = rng.integers(-5, 12, size=m).astype(float)
+        A[0] = rng.integers(1, 5, size=n)   # a row that bounds every x_j
+        b[0] = abs(b[0]) + 5.0
+        if not np.any(b < 0):
+            continue
+        c = rng.integers(-3, 6, size=n).astype(float)
+        r = oracle.solve(A, b, c)
+        z, _ = oracle.brute_force(A, b, c)
+        if z is None:
+            assert r.status == oracle.INFEASIBLE
+        else:
+            assert r.status == oracle.OPTIMAL and abs(r.obj - z) <= 1e-9 * max(1.0, abs(z))
+            done += 1
+    assert done > 100
+
+
+def test_phase1_textbook():
+    """max 2x1 + 3x2 s.t. x1 + x2 <= 4, x1 + x2 >= 2, x1 <= 3: the optimum is
+    x = (0, 4), z = 12, and the origin is infeasible, so Phase 1 pivots first."""
+    A = np.array([[1.0, 1.0], [-1.0, -1.0], [1.0, 0.0]])
+    b = np.array([4.0, -2.0, 3.0])
+    c = np.array([2.0, 3.0])
+    r = oracle.solve(A, b, c, trace_cap=10)
+    assert r.status == oracle.OPTIMAL and r.obj == 12.0
+    assert np.array_equal(r.x, [0.0, 4.0])
+    assert r.trace_p[0] == 1  # Phase 1 leaves the violated row first
+
+
+def test_phase1_infeasible():
+    """x1 + x2 <= -1 has no x >= 0: Phase 1 finds no entering column."""
+    r = oracle.solve(np.array([[1.0, 1.0], [1.0, 0.0]]), np.array([-1.0, 3.0]),
+                     np.array([1.0, 1.0]))
+    assert r.status == oracle.INFEASIBLE and r.iters == 0
+
+
+def test_phase1_resume_in_chunks():
+    """Stopping every few pivots (across the switch to Phase 2) and resuming
+    gives the bits of one run."""
+    rng = np.random.default_rng(13)
+    A = rng.integers(1, 20, size=(30, 40)).astype(float)
+    b = rng.integers(50, 200, size=30).astype(float)
+    A[:6] = -A[:6]
+    b[:6] = -0.2 * b[:6]
+    c = rng.integers(1, 30, size=40).astype(float)
+    one = oracle.solve(A, b, c, trace_cap=500, keep_tableau=True)
+    assert one.status == oracle.OPTIMAL and one.iters > 10
+    t = oracle.OracleTableau(A, b, c, trace_cap=500)
+    k = 0
+    while True:
+        k += 3
+        if t.run(k) != oracle.ITER_LIMIT:
+            break
+    r = t.result(keep_tableau=True)
+    assert r.status == one.status and r.iters == one.iters
+    assert np.array_equal(r.trace_p, one.trace_p) and np.array_equal(r.trace_q, one.trace_q)
+    assert np.array_equal(r.T.view(np.uint64), one.T.view(np.uint64))
