@@ -37,6 +37,9 @@ MUTANTS = {
     "dual_ratio_sign": ("const double t = zj / (-a);", "const double t = zj / a;"),
     "bland_tiebreak": ("const int key = bland ? basis[i] : i;", "const int key = i;"),
     "never_bland": ("*deg = (rmin == 0.0) ? *deg + 1 : 0;", "*deg = 0;"),
+    "phase2_term_sign": ("z[j] = fma(cb, row[j], z[j]);", "z[j] = fma(-cb, row[j], z[j]);"),
+    "phase2_objective_value_skipped": ("for (long j = 0; j < N; ++j) z[j] = fma(cb, row[j], z[j]);",
+                                       "for (long j = 0; j < N - 1; ++j) z[j] = fma(cb, row[j], z[j]);"),
     "primal_objective_sign": ("*obj = (sense == OR_MAX_LE) ? z[N - 1] : -z[N - 1];",
                               "*obj = (sense == OR_MAX_LE) ? z[N - 1] : z[N - 1];"),
 }
@@ -80,6 +83,29 @@ def _pins():
     rd = oracle.solve(*lpgen.dual_of(A, b, c), sense=oracle.MIN_GE, max_iters=CAP)
     assert rp.status == rd.status == oracle.OPTIMAL
     assert rel(rd.obj, rp.obj) <= 1e-12 and rp.iters == rd.iters
+    # Phase I (some b_i < 0): brute force on bounded LPs, a hand-solved case
+    done = 0
+    for seed in range(200):
+        rng = np.random.default_rng(1000 + seed)
+        m, n = (int(v) for v in rng.integers(2, 5, size=2))
+        A = rng.integers(-4, 6, size=(m, n)).astype(float)
+        b = rng.integers(-5, 12, size=m).astype(float)
+        A[0] = rng.integers(1, 5, size=n)
+        b[0] = abs(b[0]) + 5.0
+        if not np.any(b < 0):
+            continue
+        c = rng.integers(-3, 6, size=n).astype(float)
+        r = oracle.solve(A, b, c, max_iters=CAP)
+        z, _ = oracle.brute_force(A, b, c)
+        if z is None:
+            assert r.status == oracle.INFEASIBLE
+        else:
+            assert r.status == oracle.OPTIMAL and rel(r.obj, z) <= 1e-9
+            done += 1
+    assert done > 30
+    r = oracle.solve(np.array([[1.0, 1.0], [-1.0, -1.0], [1.0, 0.0]]), np.array([4.0, -2.0, 3.0]),
+                     np.array([2.0, 3.0]), max_iters=CAP)
+    assert r.status == oracle.OPTIMAL and r.obj == 12.0 and np.array_equal(r.x, [0.0, 4.0])
 
 
 def _build_mutant(tmp_path, old, new):
