@@ -235,7 +235,15 @@ lp_err lp_batch_autotune(int count, const int *m, const int *n, const double *co
  * and read off by a persistent kernel that takes new LPs while others are
  * running, so their work overlaps on the GPU.  Each LP runs on a group of
  * CTAs with the single-LP pivot code, so its result equals solving it alone
- * bit for bit.  FP64; m, n <= 4096; inputs and outputs in host memory.
+ * bit for bit.  m, n <= 4096; inputs and outputs in host memory.
+ * With opt->precision == LP_FP32_REINV the tableaus are FP32 and the server
+ * works in rounds: one batched launch in which every admitted LP pivots up
+ * to reinv_k times, then each LP's FP64 reinversion and the decisions of the
+ * FP32 mode (results: the FP64 x, y and objective of the last reinversion);
+ * requests are admitted between rounds and pivot in the same launches as the
+ * LPs already there.  An LP's rounds do not depend on the others, so its
+ * result is the same alone and in the mix, bit for bit.  The FP32 server,
+ * like the FP32 mode, needs b >= 0 (max form) and c >= 0 (min form).
  * submit copies the inputs and returns a ticket at once; poll / wait return
  * the result and the submit-to-completion latency in milliseconds (wait
  * returns LP_ERR_BUSY on timeout).  A request whose inputs fail the checks of

@@ -230,13 +230,6 @@ namespace {
 
 // ------------------------------------------------- FP32 batches (A9 + A11) --
 
-double key_to_double(unsigned long long k) {
-    const unsigned long long bits = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
-    double d;
-    memcpy(&d, &bits, sizeof d);
-    return d;
-}
-
 // What the FP32 rounds need of lp_solve_batch's layout.
 struct BatchFp32 {
     int count;
@@ -253,42 +246,6 @@ struct BatchFp32 {
     size_t smem;
     const lp_options *opt;
     cudaStream_t s;
-};
-
-// Device buffers of one FP64 reinversion, sized for the largest LP and reused
-// LP by LP.
-struct ReinvPool {
-    ReinvBufs rb{};
-    size_t cap_W = 0;
-    int *h_counts = nullptr;
-    ReinvCheck *h_chk = nullptr;
-    ~ReinvPool() {
-        void *bufs[] = {rb.Lflag, rb.S, rb.R, rb.posS, rb.posR, rb.counts, rb.pivrow, rb.W,
-                        rb.xS, rb.yR, rb.zrow, rb.rhs, rb.chk, rb.bar};
-        for (void *p : bufs)
-            if (p) cudaFree(p);
-        if (h_counts) cudaFreeHost(h_counts);
-        if (h_chk) cudaFreeHost(h_chk);
-    }
-    cudaError_t init(size_t cap) {
-        void **ints[] = {(void **)&rb.Lflag, (void **)&rb.S, (void **)&rb.R, (void **)&rb.posS,
-                         (void **)&rb.posR, (void **)&rb.pivrow};
-        for (void **q : ints) {
-            cudaError_t e = cudaMalloc(q, cap * sizeof(int));
-            if (e != cudaSuccess) return e;
-        }
-        void **dbl[] = {(void **)&rb.xS, (void **)&rb.yR, (void **)&rb.zrow, (void **)&rb.rhs};
-        for (void **q : dbl) {
-            cudaError_t e = cudaMalloc(q, cap * sizeof(double));
-            if (e != cudaSuccess) return e;
-        }
-        cudaError_t e = cudaMalloc(&rb.counts, 4 * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&rb.chk, sizeof(ReinvCheck));
-        if (e == cudaSuccess) e = cudaMalloc(&rb.bar, 128 * sizeof(unsigned));
-        if (e == cudaSuccess) e = cudaMallocHost(&h_counts, 4 * sizeof(int));
-        if (e == cudaSuccess) e = cudaMallocHost(&h_chk, sizeof(ReinvCheck));
-        return e;
-    }
 };
 
 // FP32 batch: rounds of one batched launch (every unfinished LP pivots up to

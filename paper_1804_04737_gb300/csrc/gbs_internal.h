@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace gbs {
 
@@ -152,6 +153,51 @@ struct ReinvBufs {
 
 cudaError_t launch_reinv_lists(const int *basis, int m, int n, const ReinvBufs &rb,
                                cudaStream_t s);
+
+// The double whose order-preserving key is k (the reinversion's check minima).
+inline double key_to_double(unsigned long long k) {
+    const unsigned long long bits = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
+    double d;
+    memcpy(&d, &bits, sizeof d);
+    return d;
+}
+
+// Device buffers of one FP64 reinversion, sized for the largest LP and reused
+// LP by LP.
+struct ReinvPool {
+    ReinvBufs rb{};
+    size_t cap_W = 0;
+    int *h_counts = nullptr;
+    ReinvCheck *h_chk = nullptr;
+    ~ReinvPool() {
+        void *bufs[] = {rb.Lflag, rb.S, rb.R, rb.posS, rb.posR, rb.counts, rb.pivrow, rb.W,
+                        rb.xS, rb.yR, rb.zrow, rb.rhs, rb.chk, rb.bar};
+        for (void *p : bufs)
+            if (p) cudaFree(p);
+        if (h_counts) cudaFreeHost(h_counts);
+        if (h_chk) cudaFreeHost(h_chk);
+    }
+    cudaError_t init(size_t cap) {
+        void **ints[] = {(void **)&rb.Lflag, (void **)&rb.S, (void **)&rb.R, (void **)&rb.posS,
+                         (void **)&rb.posR, (void **)&rb.pivrow};
+        for (void **q : ints) {
+            cudaError_t e = cudaMalloc(q, cap * sizeof(int));
+            if (e != cudaSuccess) return e;
+        }
+        void **dbl[] = {(void **)&rb.xS, (void **)&rb.yR, (void **)&rb.zrow, (void **)&rb.rhs};
+        for (void **q : dbl) {
+            cudaError_t e = cudaMalloc(q, cap * sizeof(double));
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaMalloc(&rb.counts, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&rb.chk, sizeof(ReinvCheck));
+        if (e == cudaSuccess) e = cudaMalloc(&rb.bar, 128 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMallocHost(&h_counts, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost(&h_chk, sizeof(ReinvCheck));
+        return e;
+    }
+};
+
 // Everything after the lists, for ns structural basics (W sized for ns).
 // Writes the FP64 solution (x, y, obj), the refreshed rhs column and
 // objective row of T and the check minima.

@@ -137,6 +137,21 @@ struct lp_server {
     long long launches = 0, completed = 0;
     lp_err fatal = LP_OK;
     char fatal_msg[256] = {0};
+    // FP32 tableaus with FP64 reinversion (precision LP_FP32_REINV): a round
+    // engine instead of the persistent kernel.  Each round is one batched
+    // launch in which every admitted LP pivots up to reinv_k times, then the
+    // FP64 reinversion and decision of each LP; requests are admitted
+    // between rounds, so new LPs pivot in the same launches as older ones.
+    bool fp32 = false;
+    LpDesc *d_desc32 = nullptr, *h_desc32 = nullptr;  // one per slot (host copy pinned)
+    int2 *d_items = nullptr, *h_items = nullptr;        // a round's work items
+    unsigned *d_queue = nullptr;
+    int ctas32 = 0;
+    size_t smem32 = 0;
+    std::vector<int> active;  // slots being pivoted
+    std::vector<int> rule, failed;
+    std::vector<long long> remaining, guard, before;
+    ReinvPool *rp = nullptr;
 };
 
 namespace {
@@ -155,11 +170,11 @@ struct SlotLayout {
     size_t T, in, basis, part, bar, out, stats, total;
 };
 
-SlotLayout slot_layout(int m, int n, long long P, int G) {
+SlotLayout slot_layout(int m, int n, long long P, int G, size_t esz = sizeof(double)) {
     SlotLayout L;
     size_t off = 0;
     auto take = [&](size_t b) { const size_t at = off; off += up256(b); return at; };
-    L.T = take((size_t)(m + 1) * (size_t)P * sizeof(double));
+    L.T = take((size_t)(m + 1) * (size_t)P * esz);
     L.in = take(((size_t)m * n + m + n) * sizeof(double));
     L.basis = take((size_t)m * sizeof(int));
     L.part = take(2 * (size_t)G * sizeof(Cand));
@@ -179,6 +194,21 @@ void group_shape(const lp_server *sv, int m, int n, int *G, int *W) {
     g = std::max<long long>(g, gmin);
     long long w = (P + g - 1) / g;
     w = (w + 3) / 4 * 4;
+    *W = (int)w;
+    *G = (int)((P + w - 1) / w);
+}
+
+// The FP32 engine's group of CTAs and strip width for one LP (FP32 vectors of
+// four, strips of whole 32-byte sectors), as the FP32 batch path sizes them.
+void group_shape32(const lp_server *sv, int m, int n, int *G, int *W) {
+    const long long M = m + 1, P = pitch_for(n + m + 1);
+    const long long ge = sv->opt.group_elems > 0 ? sv->opt.group_elems : 262144;
+    const long long gmin = (P + (long long)sv->threads * 4 - 1) / ((long long)sv->threads * 4);
+    long long g = (M * P + ge - 1) / ge;
+    g = std::min<long long>(g, std::min<long long>(sv->ctas32, P / 8));
+    g = std::max<long long>(g, gmin);
+    long long w = (P + g - 1) / g;
+    w = (w + 7) / 8 * 8;
     *W = (int)w;
     *G = (int)((P + w - 1) / w);
 }
@@ -345,6 +375,292 @@ void engine_kernel(lp_server *sv) {
     ++sv->launches;
 }
 
+// bits of a double (the input statistics hold the bits of max |.|)
+double bits_double(unsigned long long b) {
+    double v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+// ---- FP32 engine ----
+
+// Finish the request in `slot`: its FP64 results (those of the last
+// reinversion), its status, and the slot's memory back to the budget.
+void finish32(lp_server *sv, int slot, int status, lp_err err) {
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r = &sv->reqs[sv->slot_ticket[slot]];
+    }
+    const LpDesc &d = sv->h_desc32[slot];
+    // sized in every case: the results are copied out of these on completion
+    r->x.assign(r->n, 0.0);
+    r->y.assign(r->m, 0.0);
+    if (err == LP_OK) {
+        const long long P = pitch_for(r->n + r->m + 1);
+        const SlotLayout L = slot_layout(r->m, r->n, P, r->group, sizeof(float));
+        const double *out = reinterpret_cast<const double *>(sv->arena_dev + r->off + L.out);
+        cudaMemcpyAsync(r->x.data(), out, sizeof(double) * r->n, cudaMemcpyDeviceToHost, sv->kstream);
+        cudaMemcpyAsync(r->y.data(), out + r->n, sizeof(double) * r->m, cudaMemcpyDeviceToHost,
+                        sv->kstream);
+        cudaMemcpyAsync(&r->obj, out + r->n + r->m, sizeof(double), cudaMemcpyDeviceToHost,
+                        sv->kstream);
+        cudaStreamSynchronize(sv->kstream);
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->iters = err == LP_OK ? d.iters : 0;
+    r->err = err;
+    r->status = err == LP_OK ? status : LP_NOT_SOLVED;
+    r->state = DONE;
+    r->t_done = now_ms();
+    sv->arena.release(r->off, r->bytes);
+    sv->slot_ticket[slot] = 0;
+    sv->free_slots.push_back(slot);
+    ++sv->completed;
+    sv->cv.notify_all();
+}
+
+// Admit waiting requests (FIFO, while a slot and the budget allow): copy the
+// inputs, check them, build the FP32 tableau and the slot's descriptor.
+bool admit32(lp_server *sv) {
+    std::vector<std::pair<int, Request *>> adm;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        while (!sv->queue.empty() && !sv->free_slots.empty()) {
+            const unsigned long long t = sv->queue.front();
+            Request &r = sv->reqs[t];
+            group_shape32(sv, r.m, r.n, &r.group, &r.strip);
+            const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group, sizeof(float));
+            size_t off;
+            if (!sv->arena.alloc(L.total, &off)) break;
+            r.off = off;
+            r.bytes = L.total;
+            r.slot = sv->free_slots.back();
+            sv->free_slots.pop_back();
+            sv->slot_ticket[r.slot] = t;
+            r.state = ADMITTED;
+            r.t_admit = now_ms();
+            sv->queue.pop_front();
+            adm.push_back({r.slot, &r});
+        }
+    }
+    if (adm.empty()) return false;
+    cudaStream_t s = sv->kstream;
+    std::vector<InputStats> st(adm.size());
+    for (size_t k = 0; k < adm.size(); ++k) {
+        Request &r = *adm[k].second;
+        const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group, sizeof(float));
+        unsigned char *base = sv->arena_dev + r.off;
+        const double *A = reinterpret_cast<const double *>(base + L.in);
+        cudaMemcpyAsync(base + L.in, r.in.data(), r.in.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(base + L.bar, 0, 512, s);
+        launch_inspect(A, A + (size_t)r.m * r.n, A + (size_t)r.m * r.n + r.m, r.m, r.n,
+                       reinterpret_cast<InputStats *>(base + L.stats), s);
+        cudaMemcpyAsync(&st[k], base + L.stats, sizeof(InputStats), cudaMemcpyDeviceToHost, s);
+    }
+    cudaStreamSynchronize(s);
+    for (size_t k = 0; k < adm.size(); ++k) {
+        const int slot = adm[k].first;
+        Request &r = *adm[k].second;
+        const int m = r.m, n = r.n;
+        const long long P = pitch_for(n + m + 1);
+        const SlotLayout L = slot_layout(m, n, P, r.group, sizeof(float));
+        unsigned char *base = sv->arena_dev + r.off;
+        lp_err err = LP_OK;
+        if (st[k].flags & 4) err = LP_ERR_INVALID_ARG;
+        else if (r.sense == LP_MAX_LE && (st[k].flags & 1)) err = LP_ERR_INFEASIBLE_START;
+        else if (r.sense == LP_MIN_GE && (st[k].flags & 2)) err = LP_ERR_INFEASIBLE_START;
+        if (err != LP_OK) {
+            finish32(sv, slot, LP_NOT_SOLVED, err);
+            continue;
+        }
+        const double *A = reinterpret_cast<const double *>(base + L.in);
+        LpDesc d{};
+        d.T = base + L.T;
+        d.basis = reinterpret_cast<int *>(base + L.basis);
+        d.part_sel = reinterpret_cast<Cand *>(base + L.part);
+        d.bar = reinterpret_cast<unsigned *>(base + L.bar);
+        d.err = reinterpret_cast<int *>(d.bar + 96);
+        d.P = P;
+        d.m = m;
+        d.n = n;
+        d.M = m + 1;
+        d.N = n + m + 1;
+        d.sense = r.sense;
+        d.bland_after = sv->opt.bland_after;
+        // the FP32 tableau pivots with the FP64 tolerances (as lp_load's FP32 mode)
+        d.eps_d = sv->opt.eps_d > 0 ? sv->opt.eps_d : 1e-9 * std::max(1.0, bits_double(st[k].cmax_bits));
+        d.eps_p = sv->opt.eps_p > 0 ? sv->opt.eps_p : 1e-9 * std::max(1.0, bits_double(st[k].amax_bits));
+        d.eps_r = sv->opt.eps_r > 0 ? sv->opt.eps_r : 1e-9 * std::max(1.0, bits_double(st[k].bmax_bits));
+        d.status = -1;
+        d.last_p = d.last_q = -1;
+        d.group = r.group;
+        d.strip = r.strip;
+        launch_build(PREC_FP32, A, A + (size_t)m * n, A + (size_t)m * n + m, m, n, r.sense, d.T, P,
+                     d.basis, s);
+        sv->h_desc32[slot] = d;
+        sv->rule[slot] = r.sense;
+        sv->failed[slot] = 0;
+        sv->remaining[slot] = sv->opt.max_iters;
+        sv->guard[slot] = 20ll * (m + n) + 1000;
+        sv->active.push_back(slot);
+    }
+    return true;
+}
+
+// One round: every admitted LP pivots up to reinv_k times in one batched
+// FP32 launch, then, LP by LP, the FP64 reinversion of its basis and the
+// decisions of the FP32 batch path (accept an FP32 optimum only when the
+// FP64 values are primal and dual feasible; otherwise continue with the rule
+// whose invariant holds).
+void round32(lp_server *sv) {
+    cudaStream_t s = sv->kstream;
+    std::vector<int> order = sv->active;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)sv->h_desc32[a].M * sv->h_desc32[a].P >
+               (long long)sv->h_desc32[b].M * sv->h_desc32[b].P;
+    });
+    long long budget = sv->opt.reinv_k;
+    int nitems = 0;
+    for (int slot : order) {
+        LpDesc &d = sv->h_desc32[slot];
+        budget = std::min(budget, sv->remaining[slot]);
+        for (int r = 0; r < d.group; ++r) sv->h_items[nitems++] = make_int2(slot, r);
+        d.sense = sv->rule[slot];
+        sv->before[slot] = d.iters;
+        cudaMemsetAsync(d.bar, 0, 512, s);
+    }
+    cudaMemcpyAsync(sv->d_items, sv->h_items, nitems * sizeof(int2), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sv->d_desc32, sv->h_desc32, sv->max_slots * sizeof(LpDesc),
+                    cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(sv->d_queue, 0, sizeof(unsigned), s);
+    cudaError_t e = launch_batch(PREC_FP32, sv->d_desc32, sv->d_items, nitems, sv->d_queue,
+                                 sv->ctas32, sv->threads, sv->smem32, 1,
+                                 sv->opt.spin_timeout_cycles, budget, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv->h_desc32, sv->d_desc32, sv->max_slots * sizeof(LpDesc),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->fatal = LP_ERR_CUDA;
+        snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "FP32 round: %s", cudaGetErrorString(e));
+        sv->cv.notify_all();
+        return;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        ++sv->launches;
+    }
+    std::vector<int> still;
+    for (int slot : sv->active) {
+        LpDesc &d = sv->h_desc32[slot];
+        Request *r;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r = &sv->reqs[sv->slot_ticket[slot]];
+        }
+        const long long made = d.iters - sv->before[slot];
+        sv->remaining[slot] -= made;
+        sv->guard[slot] -= made;
+        const int st = d.status;
+        if (st == LP_TIMEOUT) {
+            finish32(sv, slot, LP_TIMEOUT, LP_OK);
+            continue;
+        }
+        // the FP64 reinversion of the basis reached
+        const int m = r->m, n = r->n;
+        const long long P = pitch_for(n + m + 1);
+        const SlotLayout L = slot_layout(m, n, P, r->group, sizeof(float));
+        unsigned char *base = sv->arena_dev + r->off;
+        const double *A = reinterpret_cast<const double *>(base + L.in), *b = A + (size_t)m * n,
+                     *c = b + m;
+        double *out = reinterpret_cast<double *>(base + L.out);
+        ReinvPool &rp = *sv->rp;
+        e = launch_reinv_lists(d.basis, m, n, rp.rb, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rp.h_counts, rp.rb.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        const int ns = rp.h_counts[0];
+        const size_t needW = (size_t)ns * (((size_t)2 * ns + 1 + 31) / 32 * 32);
+        if (e == cudaSuccess && needW > rp.cap_W) {
+            if (rp.rb.W) cudaFree(rp.rb.W);
+            rp.rb.W = nullptr;
+            rp.cap_W = 0;
+            e = cudaMalloc(&rp.rb.W, needW * sizeof(double));
+            if (e == cudaSuccess) rp.cap_W = needW;
+        }
+        if (e == cudaSuccess) {
+            rp.rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
+            e = launch_reinv_solve(PREC_FP32, A, b, c, r->sense, m, n, d.basis, rp.rb, ns, d.T, P,
+                                   out, out + n, out + n + m, sv->sms, sv->opt.spin_timeout_cycles, s);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(rp.h_chk, rp.rb.chk, sizeof(ReinvCheck), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || rp.h_counts[1] != ns) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->fatal = LP_ERR_CUDA;
+            snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "FP32 reinversion: %s",
+                     e != cudaSuccess ? cudaGetErrorString(e) : "inconsistent basis");
+            sv->cv.notify_all();
+            return;
+        }
+        if (rp.h_chk->singular) {
+            finish32(sv, slot, LP_NUMERICAL, LP_OK);
+            continue;
+        }
+        const bool pfeas = key_to_double(rp.h_chk->rhsmin_key) >= -d.eps_r;
+        const bool dfeas = key_to_double(rp.h_chk->zmin_key) >= -d.eps_d;
+        if (st == LP_OPTIMAL) {
+            if (pfeas && dfeas) {
+                finish32(sv, slot, LP_OPTIMAL, LP_OK);
+            } else if ((!pfeas && !dfeas) || ++sv->failed[slot] > 4) {
+                finish32(sv, slot, LP_NUMERICAL, LP_OK);
+            } else {
+                sv->rule[slot] = pfeas ? 0 : 1;
+                still.push_back(slot);
+            }
+            continue;
+        }
+        if (st == LP_UNBOUNDED || st == LP_INFEASIBLE) {
+            finish32(sv, slot, st, LP_OK);
+            continue;
+        }
+        if (sv->remaining[slot] <= 0) {
+            finish32(sv, slot, LP_ITER_LIMIT, LP_OK);
+            continue;
+        }
+        if (sv->guard[slot] <= 0) {
+            finish32(sv, slot, LP_NUMERICAL, LP_OK);
+            continue;
+        }
+        if (sv->rule[slot] == 0 && !pfeas && dfeas) sv->rule[slot] = 1;
+        else if (sv->rule[slot] == 1 && !dfeas && pfeas) sv->rule[slot] = 0;
+        still.push_back(slot);
+    }
+    sv->active.swap(still);
+}
+
+void engine32_main(lp_server *sv) {
+    cudaSetDevice(sv->device);
+    while (!sv->stop.load()) {
+        bool fatal;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            fatal = sv->fatal != LP_OK;
+        }
+        const bool admitted = !fatal && admit32(sv);
+        if (!fatal && !sv->active.empty()) {
+            round32(sv);
+        } else if (!admitted) {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
 void engine_main(lp_server *sv) {
     cudaSetDevice(sv->device);
     while (!sv->stop.load()) {
@@ -368,8 +684,10 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     *out = nullptr;
     lp_options o;
     if (opt) o = *opt; else lp_options_default(&o);
-    if (o.precision != LP_FP64)
-        return sfail(LP_ERR_INVALID_ARG, "lp_server_create: FP64 only");
+    if (o.precision != LP_FP64 && o.precision != LP_FP32_REINV)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_create: unknown precision %d", o.precision);
+    if (o.precision == LP_FP32_REINV && o.reinv_k < 1)
+        return sfail(LP_ERR_INVALID_ARG, "lp_server_create: reinv_k must be >= 1");
     if (max_slots < 1 || max_slots > kServeMaxSlots || hbm_budget_bytes < (1u << 20))
         return sfail(LP_ERR_INVALID_ARG, "lp_server_create: need 1 <= max_slots <= %d and a "
                      "budget of at least 1 MiB", kServeMaxSlots);
@@ -380,6 +698,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->opt = o;
     sv->device = o.device;
     sv->max_slots = max_slots;
+    sv->fp32 = o.precision == LP_FP32_REINV;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
     const int M = lp_server::kMaxDim + 1, N = 2 * lp_server::kMaxDim + 1;
@@ -398,6 +717,31 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     if (e == cudaSuccess) e = cudaMalloc(&sv->d_ctl, sizeof(ServeCtl));
     if (e == cudaSuccess) e = cudaHostAlloc(&sv->h_ring, sizeof(ServeRing), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&sv->d_ring, sv->h_ring, 0);
+    if (e == cudaSuccess && sv->fp32) {
+        // the batched FP32 launches: a strip of up to threads * 4 floats, the
+        // pivot column (FP32) and an FP64 row of the LP's width per CTA
+        sv->smem32 = (size_t)sv->threads * 4 * sizeof(float) +
+                     (((size_t)M * sizeof(float) + 15) & ~(size_t)15) + (size_t)N * sizeof(double);
+        sv->ctas32 = max_coresident_batch_ctas(PREC_FP32, sv->threads, sv->smem32, 1, sv->sms);
+        if (sv->ctas32 < 1) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) e = cudaMalloc(&sv->d_desc32, sizeof(LpDesc) * max_slots);
+        if (e == cudaSuccess) e = cudaMallocHost(&sv->h_desc32, sizeof(LpDesc) * max_slots);
+        if (e == cudaSuccess) e = cudaMalloc(&sv->d_items, sizeof(int2) * max_slots * sv->ctas32);
+        if (e == cudaSuccess) e = cudaMallocHost(&sv->h_items, sizeof(int2) * max_slots * sv->ctas32);
+        if (e == cudaSuccess) e = cudaMalloc(&sv->d_queue, sizeof(unsigned));
+        if (e == cudaSuccess) {
+            sv->rp = new (std::nothrow) ReinvPool();
+            e = sv->rp ? sv->rp->init((size_t)2 * lp_server::kMaxDim) : cudaErrorMemoryAllocation;
+        }
+        if (e == cudaSuccess) {
+            memset(sv->h_desc32, 0, sizeof(LpDesc) * max_slots);
+            sv->rule.assign(max_slots, 0);
+            sv->failed.assign(max_slots, 0);
+            sv->remaining.assign(max_slots, 0);
+            sv->guard.assign(max_slots, 0);
+            sv->before.assign(max_slots, 0);
+        }
+    }
     if (e != cudaSuccess) {
         sfail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA, "lp_server_create: %s",
               cudaGetErrorString(e));
@@ -408,7 +752,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->arena.reset(hbm_budget_bytes);
     sv->slot_ticket.assign(max_slots, 0);
     for (int s = max_slots - 1; s >= 0; --s) sv->free_slots.push_back(s);
-    sv->engine = std::thread(engine_main, sv);
+    sv->engine = std::thread(sv->fp32 ? engine32_main : engine_main, sv);
     *out = sv;
     return LP_OK;
 }
@@ -431,8 +775,10 @@ lp_err lp_server_submit(lp_server *sv, int m, int n, const double *A, const doub
     memcpy(r.in.data() + (size_t)m * n, b, sizeof(double) * m);
     memcpy(r.in.data() + (size_t)m * n + m, c, sizeof(double) * n);
     int G, W;
-    group_shape(sv, m, n, &G, &W);
-    if (slot_layout(m, n, pitch_for(n + m + 1), G).total > sv->arena.size())
+    if (sv->fp32) group_shape32(sv, m, n, &G, &W);
+    else group_shape(sv, m, n, &G, &W);
+    if (slot_layout(m, n, pitch_for(n + m + 1), G, sv->fp32 ? sizeof(float) : sizeof(double)).total >
+        sv->arena.size())
         return sfail(LP_ERR_OOM, "lp_server_submit: an LP of %d x %d exceeds the HBM budget", m, n);
     r.t_submit = now_ms();
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -524,6 +870,12 @@ void lp_server_destroy(lp_server *sv) {
     if (sv->kdone) cudaEventDestroy(sv->kdone);
     if (sv->kstream) cudaStreamDestroy(sv->kstream);
     if (sv->cstream) cudaStreamDestroy(sv->cstream);
+    if (sv->d_desc32) cudaFree(sv->d_desc32);
+    if (sv->h_desc32) cudaFreeHost(sv->h_desc32);
+    if (sv->d_items) cudaFree(sv->d_items);
+    if (sv->h_items) cudaFreeHost(sv->h_items);
+    if (sv->d_queue) cudaFree(sv->d_queue);
+    delete sv->rp;
     delete sv;
 }
 

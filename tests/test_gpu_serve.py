@@ -109,3 +109,75 @@ def test_serve_idle_relaunch_and_rejected_request():
         assert capi.lp_server_stats(srv)[1] >= 2  # relaunched after the idle exit
     finally:
         capi.lp_server_destroy(srv)
+
+
+# ---- FP32 tableaus with FP64 reinversion ----
+
+OBJ_TOL32 = 1e-6
+
+
+def _serve32(lps, budget=2 << 30, slots=64, k=50, stagger=True):
+    opt = capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=k)
+    srv = capi.lp_server_create(opt, hbm_budget_bytes=budget, max_slots=slots)
+    try:
+        tickets = []
+        for i, lp in enumerate(lps):
+            tickets.append(capi.lp_server_submit(srv, *lp))
+            if stagger and i % 7 == 0:
+                time.sleep(0.002)
+        res = [capi.lp_server_wait(srv, t, lp[0].shape[0], lp[0].shape[1])
+               for lp, t in zip(lps, tickets)]
+        return res, capi.lp_server_stats(srv)
+    finally:
+        capi.lp_server_destroy(srv)
+
+
+def test_serve_fp32_objective_and_mix_invariance():
+    """FP32 serving: requests join running rounds; every result reaches the
+    FP64 optimum within the FP32 mode's tolerance with an FP64 certificate,
+    and each result is the same, bit for bit, served alone or in the mix."""
+    lps = _mix(40, 8, 600, seed=3)
+    res, stats = _serve32(lps)
+    assert stats[0] == len(lps) and stats[1] >= 1
+    for lp, r in zip(lps, res):
+        A, b, c, sense = lp
+        obj, st, it, x, y, lat = r
+        o = oracle.solve(A, b, c, sense=sense)
+        assert st == capi.LP_OPTIMAL and lat > 0.0
+        assert abs(obj - o.obj) / max(1.0, abs(o.obj)) <= OBJ_TOL32, (obj, o.obj)
+        cert = oracle.certificate(A, b, c, x, y, obj, sense=sense)
+        scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
+        assert max(cert.values()) <= 1e-9 * scale * 1e3, cert
+    for i in (0, 7, 19, 33):
+        (alone,), _ = _serve32([lps[i]], stagger=False)
+        assert _bits([alone[0]])[0] == _bits([res[i][0]])[0]
+        assert alone[1] == res[i][1] and alone[2] == res[i][2]
+        assert np.array_equal(_bits(alone[3]), _bits(res[i][3]))
+        assert np.array_equal(_bits(alone[4]), _bits(res[i][4]))
+
+
+def test_serve_fp32_small_budget_and_rejects():
+    """A budget that holds a few LPs at a time (requests wait for memory
+    between rounds), reinv_k = 200, and a request the FP32 mode refuses."""
+    lps = _mix(12, 100, 400, seed=4)
+    res, stats = _serve32(lps, budget=24 << 20, slots=8, k=200)
+    assert stats[0] == len(lps)
+    for lp, r in zip(lps, res):
+        o = oracle.solve(lp[0], lp[1], lp[2], sense=lp[3])
+        assert r[1] == capi.LP_OPTIMAL
+        assert abs(r[0] - o.obj) / max(1.0, abs(o.obj)) <= OBJ_TOL32
+    A, b, c = lpgen.dense_lp(30, 40, seed=9)
+    bad = b.copy()
+    bad[3] = -1.0
+    opt = capi.lp_options_default(precision=capi.LP_FP32_REINV)
+    srv = capi.lp_server_create(opt, hbm_budget_bytes=64 << 20, max_slots=4)
+    try:
+        t = capi.lp_server_submit(srv, A, bad, c)
+        t2 = capi.lp_server_submit(srv, A, b, c)
+        with pytest.raises(capi.LpError) as e:
+            capi.lp_server_wait(srv, t, 30, 40)
+        assert e.value.code == capi.LP_ERR_INFEASIBLE_START
+        r = capi.lp_server_wait(srv, t2, 30, 40)
+        assert r[1] == capi.LP_OPTIMAL
+    finally:
+        capi.lp_server_destroy(srv)
