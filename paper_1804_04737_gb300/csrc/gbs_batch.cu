@@ -268,6 +268,7 @@ lp_err solve_batch_fp32(const BatchFp32 &f, lp_status *fin, double *kernel_ms) {
     B_TRY(rp.init(cap));
     B_TRY(cudaMalloc(&rp.rb.W, std::max<size_t>(capW, 1) * sizeof(double)));
     rp.cap_W = capW;
+    BatchReinv ws;
 
     std::vector<int> active(count, 1), rule(count), failed(count, 0);
     std::vector<long long> remaining(count), guard(count), before(count);
@@ -306,43 +307,47 @@ lp_err solve_batch_fp32(const BatchFp32 &f, lp_status *fin, double *kernel_ms) {
         float t = 0.0f;
         cudaEventElapsedTime(&t, e0, e1);
         *kernel_ms += t;
+        // the FP64 reinversion of every unfinished LP's basis, batched
+        std::vector<int> idx;
+        std::vector<ReinvJob> jobs;
         for (int k = 0; k < count; ++k) {
             if (!active[k]) continue;
             LpDesc &d = f.h_desc[k];
             const long long made = d.iters - before[k];
             remaining[k] -= made;
             guard[k] -= made;
+            if (d.status == LP_TIMEOUT) {
+                fin[k] = LP_TIMEOUT;
+                active[k] = 0;
+                continue;
+            }
+            const int m = f.m[k], n = f.n[k];
+            const double *A = f.d_in + f.in_off[k], *b = A + (long long)m * n, *c = b + m;
+            double *x = f.d_xy + f.xy_off[k];
+            jobs.push_back(ReinvJob{A, b, c, m, n, f.sv[k], d.basis, f.d_T + f.t_off[k], f.P[k], x,
+                                    x + n, f.d_obj + k});
+            idx.push_back(k);
+        }
+        int badj = -1;
+        B_TRY(reinvert_many(PREC_FP32, jobs.data(), (int)jobs.size(), ws, rp, f.sms,
+                            f.opt->spin_timeout_cycles, s, &badj));
+        if (badj >= 0)
+            return bfail(LP_ERR_STATE, "lp_solve_batch: LP %d: inconsistent basis", idx[badj]);
+        for (size_t q = 0; q < idx.size(); ++q) {
+            const int k = idx[q];
+            LpDesc &d = f.h_desc[k];
             const int st = d.status;
+            const ReinvCheck *chk = ws.h_chk + q;
             auto finish = [&](lp_status v) {
                 fin[k] = v;
                 active[k] = 0;
             };
-            if (st == LP_TIMEOUT) {
-                finish(LP_TIMEOUT);
-                continue;
-            }
-            // FP64 reinversion of the basis reached
-            const int m = f.m[k], n = f.n[k];
-            const double *A = f.d_in + f.in_off[k], *b = A + (long long)m * n, *c = b + m;
-            B_TRY(launch_reinv_lists(d.basis, m, n, rp.rb, s));
-            B_TRY(cudaMemcpyAsync(rp.h_counts, rp.rb.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-            B_TRY(cudaStreamSynchronize(s));
-            const int ns = rp.h_counts[0];
-            if (rp.h_counts[1] != ns)
-                return bfail(LP_ERR_STATE, "lp_solve_batch: LP %d: inconsistent basis", k);
-            rp.rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
-            double *x = f.d_xy + f.xy_off[k];
-            B_TRY(launch_reinv_solve(PREC_FP32, A, b, c, f.sv[k], m, n, d.basis, rp.rb, ns,
-                                     f.d_T + f.t_off[k], f.P[k], x, x + n, f.d_obj + k, f.sms,
-                                     f.opt->spin_timeout_cycles, s));
-            B_TRY(cudaMemcpyAsync(rp.h_chk, rp.rb.chk, sizeof(ReinvCheck), cudaMemcpyDeviceToHost, s));
-            B_TRY(cudaStreamSynchronize(s));
-            if (rp.h_chk->singular) {
+            if (chk->singular) {
                 finish(LP_NUMERICAL);
                 continue;
             }
-            const bool pfeas = key_to_double(rp.h_chk->rhsmin_key) >= -d.eps_r;
-            const bool dfeas = key_to_double(rp.h_chk->zmin_key) >= -d.eps_d;
+            const bool pfeas = key_to_double(chk->rhsmin_key) >= -d.eps_r;
+            const bool dfeas = key_to_double(chk->zmin_key) >= -d.eps_d;
             if (st == LP_OPTIMAL) {
                 if (pfeas && dfeas) {
                     finish(LP_OPTIMAL);

@@ -154,6 +154,54 @@ struct ReinvBufs {
 cudaError_t launch_reinv_lists(const int *basis, int m, int n, const ReinvBufs &rb,
                                cudaStream_t s);
 
+// One LP of a batched FP64 reinversion (gbs_reinv.cu): its data, tableau,
+// outputs and slices of workspace.  The batched solve takes LPs with at most
+// kReinvCtaMax structural basic variables, one CTA (1024 threads) each, with
+// the arithmetic of the multi-CTA kernels, so the results are the same bits.
+constexpr int kReinvCtaMax = 128;
+struct ReinvItem {
+    const double *A, *b, *c;
+    int m, n, sense, ns;  // ns: structural basic variables (the lists pass's counts[0])
+    const int *basis;
+    void *T;
+    long long P;
+    double *x, *y, *obj;
+    int *Lflag, *S, *R, *posS, *posR, *counts;
+    double *W;
+    long long Wp;
+    double *xS, *yR, *zrow, *rhs;
+    ReinvCheck *chk;
+};
+cudaError_t launch_reinv_lists_batch(const ReinvItem *d_items, int count, cudaStream_t s);
+cudaError_t launch_reinv_solve_batch(int prec, const ReinvItem *d_items, int count, cudaStream_t s);
+
+// One LP to reinvert: original FP64 data, its sense, basis, tableau and outputs.
+struct ReinvJob {
+    const double *A, *b, *c;
+    int m, n, sense;
+    const int *basis;
+    void *T;
+    long long P;
+    double *x, *y, *obj;
+};
+struct ReinvPool;
+// Grow-only workspace of reinvert_many (device slices per LP, pinned mirrors).
+struct BatchReinv {
+    int *d_int = nullptr, *d_counts = nullptr, *h_counts = nullptr;
+    double *d_dbl = nullptr, *d_W = nullptr;
+    ReinvItem *d_items = nullptr, *h_items = nullptr;
+    ReinvCheck *d_chk = nullptr, *h_chk = nullptr;
+    size_t cap_int = 0, cap_dbl = 0, cap_W = 0, cap_n = 0;
+    ~BatchReinv();
+};
+// The FP64 reinversion of many LPs (gbs_reinv.cu): the lists of all in one
+// launch, then every LP with at most kReinvCtaMax structural basics in one
+// launch of a CTA each, the others one by one with the multi-CTA kernels
+// (rp), the same bits either way.  On return ws.h_chk[k] is job k's check;
+// *bad is the first job with an inconsistent basis, or -1.
+cudaError_t reinvert_many(int prec, const ReinvJob *jobs, int count, BatchReinv &ws,
+                          ReinvPool &rp, int sms, long long spin_limit, cudaStream_t s, int *bad);
+
 // The double whose order-preserving key is k (the reinversion's check minima).
 inline double key_to_double(unsigned long long k) {
     const unsigned long long bits = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;

@@ -26,6 +26,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "gbs_device.cuh"
 #include "gbs_internal.h"
 
@@ -38,9 +41,8 @@ using namespace dev;
 // S = structural basic variables (in row order), R = rows whose slack is not
 // basic (ascending); posS[j] = k with S[k] = j or -1; posR[l] = r with R[r] = l
 // or -1; counts[0] = |S|, counts[1] = |R|.
-__global__ void __launch_bounds__(1024) reinv_lists_kernel(const int *__restrict__ basis, int m,
-                                                           int n, int *Lflag, int *S, int *R,
-                                                           int *posS, int *posR, int *counts) {
+__device__ __forceinline__ void lists_cta(const int *__restrict__ basis, int m, int n, int *Lflag,
+                                          int *S, int *R, int *posS, int *posR, int *counts) {
     __shared__ int scanS[1024], scanR[1024];
     const int tid = threadIdx.x, B = blockDim.x;
     for (int l = tid; l < m; l += B) Lflag[l] = 0;
@@ -89,6 +91,18 @@ __global__ void __launch_bounds__(1024) reinv_lists_kernel(const int *__restrict
         counts[0] = scanS[tid];
         counts[1] = scanR[tid];
     }
+}
+
+__global__ void __launch_bounds__(1024) reinv_lists_kernel(const int *__restrict__ basis, int m,
+                                                           int n, int *Lflag, int *S, int *R,
+                                                           int *posS, int *posR, int *counts) {
+    lists_cta(basis, m, n, Lflag, S, R, posS, posR, counts);
+}
+
+// The lists of many LPs, one CTA each.
+__global__ void __launch_bounds__(1024) reinv_lists_batch_kernel(const ReinvItem *__restrict__ it) {
+    const ReinvItem &r = it[blockIdx.x];
+    lists_cta(r.basis, r.m, r.n, r.Lflag, r.S, r.R, r.posS, r.posR, r.counts);
 }
 
 // W = [A_RS | b_R | I_s] (signed data), s rows, pitch Wp >= 2s + 1.
@@ -170,7 +184,8 @@ __global__ void __launch_bounds__(1024) gj_kernel(double *__restrict__ W, long l
 __global__ void reinv_solve_kernel(const double *__restrict__ W, long long Wp, int s,
                                    const int *__restrict__ pivrow, const int *__restrict__ S,
                                    const double *__restrict__ c, double sg, double *xS,
-                                   double *yR) {
+                                   double *yR, const int *__restrict__ singular) {
+    if (*singular) return;  // pivrow holds only the steps made; the host reports the LP numerical
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < s; r += stride) {
         xS[r] = W[(long long)pivrow[r] * Wp + s];
@@ -270,12 +285,173 @@ __global__ void __launch_bounds__(1024) reinv_apply_kernel(
     atomicMin(&chk->rhsmin_key, rmin);
 }
 
+
+// The whole reinversion of one LP in one CTA of 1024 threads (LPs with at
+// most kReinvCtaMax structural basics, lists already made): W, Gauss-Jordan,
+// x_S and y_R, objective row, rhs, and the apply step, each element with the
+// operations and in the order of the multi-CTA kernels above (the objective
+// sum uses the same 1024-thread tree), so the results are the same bits.
+template <typename T>
+__global__ void __launch_bounds__(1024) reinv_cta_kernel(const ReinvItem *__restrict__ items) {
+    __shared__ double colk[kReinvCtaMax], prow[2 * kReinvCtaMax + 1], part[1024];
+    __shared__ unsigned used[(kReinvCtaMax + 31) / 32];
+    __shared__ int piv_row[kReinvCtaMax];
+    __shared__ Cand rbuf[32];
+    __shared__ int s_sing;
+    const ReinvItem &it = items[blockIdx.x];
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int m = it.m, n = it.n, ns = it.ns, ncols = 2 * ns + 1;
+    const double sg = it.sense == 0 ? 1.0 : -1.0;
+    const double *A = it.A, *b = it.b, *c = it.c;
+    const int *S = it.S, *R = it.R, *posS = it.posS, *posR = it.posR;
+    const long long Wp = it.Wp;
+    double *W = it.W;
+    if (tid == 0) {
+        s_sing = 0;
+        it.chk->zmin_key = ~0ull;
+        it.chk->rhsmin_key = ~0ull;
+        it.chk->singular = 0;
+    }
+    for (long long k = tid; k < (long long)ns * Wp; k += B) {
+        const int r = (int)(k / Wp);
+        const int j = (int)(k - (long long)r * Wp);
+        double v = 0.0;
+        if (j < ns) v = sg * A[(long long)R[r] * n + S[j]];
+        else if (j == ns) v = sg * b[R[r]];
+        else if (j - ns - 1 == r) v = 1.0;
+        W[k] = v;
+    }
+    for (int k = tid; k < (ns + 31) / 32; k += B) used[k] = 0u;
+    __syncthreads();
+    for (int k = 0; k < ns; ++k) {
+        Cand cd = cand_empty();
+        for (int i = tid; i < ns; i += B) {
+            const double x = W[(long long)i * Wp + k];
+            colk[i] = x;
+            if (!((used[i >> 5] >> (i & 31)) & 1u)) {
+                const unsigned long long ak =
+                    ((unsigned long long)__double_as_longlong(x) & ~kSign) | kSign;
+                cand_take(cd, ~ak, i, i);
+            }
+        }
+        cd = block_min_c(cd, rbuf);
+        const int p = cd.idx;
+        if (p < 0 || (((unsigned long long)__double_as_longlong(colk[p])) & ~kSign) == 0ull) {
+            if (tid == 0) s_sing = 1;
+            break;  // every thread sees the same column
+        }
+        const double piv = colk[p];
+        for (int j = tid; j < ncols; j += B) prow[j] = W[(long long)p * Wp + j] / piv;
+        if (tid == 0) {
+            used[p >> 5] |= 1u << (p & 31);
+            piv_row[k] = p;
+        }
+        __syncthreads();
+        for (long long e = tid; e < (long long)ns * ncols; e += B) {
+            const int i = (int)(e / ncols);
+            const int j = (int)(e - (long long)i * ncols);
+            double *q = W + (long long)i * Wp + j;
+            *q = i == p ? prow[j] : fma(-colk[i], prow[j], *q);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (s_sing) {  // the host reports the LP numerical; nothing else is read
+        if (tid == 0) it.chk->singular = 1;
+        return;
+    }
+    double *xS = it.xS, *yR = it.yR, *zrow = it.zrow, *rhs = it.rhs;
+    for (int r = tid; r < ns; r += B) {
+        xS[r] = W[(long long)piv_row[r] * Wp + ns];
+        double acc = 0.0;
+        for (int k = 0; k < ns; ++k)
+            acc = fma(W[(long long)piv_row[k] * Wp + ns + 1 + r], sg * c[S[k]], acc);
+        yR[r] = acc;
+    }
+    __syncthreads();
+    for (int j = tid; j < n + m; j += B) {
+        double z = 0.0;
+        if (j < n) {
+            if (posS[j] < 0) {
+                double acc = 0.0;
+                for (int r = 0; r < ns; ++r) acc = fma(sg * A[(long long)R[r] * n + j], yR[r], acc);
+                z = acc - sg * c[j];
+            }
+        } else {
+            const int r = posR[j - n];
+            z = r >= 0 ? yR[r] : 0.0;
+        }
+        zrow[j] = z;
+    }
+    for (int i = tid; i < m; i += B) {
+        const int v = it.basis[i];
+        double r;
+        if (v < n) {
+            r = xS[posS[v]];
+        } else {
+            const int l = v - n;
+            double acc = sg * b[l];
+            for (int k = 0; k < ns; ++k) acc = fma(-(sg * A[(long long)l * n + S[k]]), xS[k], acc);
+            r = acc;
+        }
+        rhs[i] = r;
+    }
+    __syncthreads();
+    // the apply step (reinv_apply_kernel with 1024 threads)
+    T *Tab = reinterpret_cast<T *>(it.T);
+    const long long P = it.P;
+    const int N = n + m + 1;
+    double acc = 0.0;
+    for (int k = tid; k < ns; k += B) acc = fma(sg * c[S[k]], xS[k], acc);
+    part[tid] = acc;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (tid < o && tid + o < B) part[tid] += part[tid + o];
+        __syncthreads();
+    }
+    const double z = part[0];
+    unsigned long long zmin = ~0ull, rmin = ~0ull;
+    for (int j = tid; j < n + m; j += B) {
+        const double v = zrow[j];
+        Tab[(long long)m * P + j] = (T)v;
+        const unsigned long long k = okey(v);
+        zmin = k < zmin ? k : zmin;
+        if (j < n) it.x[j] = posS[j] >= 0 ? xS[posS[j]] : 0.0;
+        else it.y[j - n] = v;
+    }
+    for (int i = tid; i < m; i += B) {
+        const double v = rhs[i];
+        Tab[(long long)i * P + (N - 1)] = (T)v;
+        const unsigned long long k = okey(v);
+        rmin = k < rmin ? k : rmin;
+    }
+    if (tid == 0) {
+        Tab[(long long)m * P + (N - 1)] = (T)z;
+        *it.obj = sg > 0 ? z : -z;
+    }
+    atomicMin(&it.chk->zmin_key, zmin);
+    atomicMin(&it.chk->rhsmin_key, rmin);
+}
+
 int grid_of(long long work) {
     long long g = (work + 255) / 256;
     return (int)(g < 1 ? 1 : (g > 2432 ? 2432 : g));
 }
 
 }  // namespace
+
+cudaError_t launch_reinv_lists_batch(const ReinvItem *d_items, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    reinv_lists_batch_kernel<<<count, 1024, 0, s>>>(d_items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reinv_solve_batch(int prec, const ReinvItem *d_items, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (prec == PREC_FP64) reinv_cta_kernel<double><<<count, 1024, 0, s>>>(d_items);
+    else reinv_cta_kernel<float><<<count, 1024, 0, s>>>(d_items);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_reinv_lists(const int *basis, int m, int n, const ReinvBufs &rb,
                                cudaStream_t s) {
@@ -320,7 +496,7 @@ cudaError_t launch_reinv_solve(int prec, const double *A, const double *b, const
         e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, s);
         if (e != cudaSuccess) return e;
         reinv_solve_kernel<<<grid_of(ns), 256, 0, s>>>(W, Wp, ns, pivrow, rb.S, c, sg, rb.xS,
-                                                       rb.yR);
+                                                       rb.yR, singular);
     }
     reinv_objrow_kernel<<<grid_of(n + m), 256, 0, s>>>(A, c, sg, m, n, rb.R, rb.posS, rb.posR, ns,
                                                        rb.yR, rb.zrow);
@@ -335,6 +511,169 @@ cudaError_t launch_reinv_solve(int prec, const double *A, const double *b, const
                                                      rb.zrow, rb.rhs, (float *)T, P, x, y, obj,
                                                      rb.chk);
     return cudaGetLastError();
+}
+
+namespace {
+template <typename X>
+cudaError_t grow_dev(X **p, size_t *cap, size_t need) {
+    if (need <= *cap) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(p, need * sizeof(X));
+    if (e == cudaSuccess) *cap = need;
+    return e;
+}
+}  // namespace
+
+BatchReinv::~BatchReinv() {
+    if (d_int) cudaFree(d_int);
+    if (d_counts) cudaFree(d_counts);
+    if (h_counts) cudaFreeHost(h_counts);
+    if (d_dbl) cudaFree(d_dbl);
+    if (d_W) cudaFree(d_W);
+    if (d_items) cudaFree(d_items);
+    if (h_items) cudaFreeHost(h_items);
+    if (d_chk) cudaFree(d_chk);
+    if (h_chk) cudaFreeHost(h_chk);
+}
+
+cudaError_t reinvert_many(int prec, const ReinvJob *jobs, int count, BatchReinv &ws,
+                          ReinvPool &rp, int sms, long long spin_limit, cudaStream_t s, int *bad) {
+    *bad = -1;
+    if (count <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if ((size_t)count > ws.cap_n) {
+        if (ws.d_counts) cudaFree(ws.d_counts);
+        if (ws.h_counts) cudaFreeHost(ws.h_counts);
+        if (ws.d_items) cudaFree(ws.d_items);
+        if (ws.h_items) cudaFreeHost(ws.h_items);
+        if (ws.d_chk) cudaFree(ws.d_chk);
+        if (ws.h_chk) cudaFreeHost(ws.h_chk);
+        ws.d_counts = ws.h_counts = nullptr;
+        ws.d_items = ws.h_items = nullptr;
+        ws.d_chk = ws.h_chk = nullptr;
+        ws.cap_n = 0;
+        e = cudaMalloc(&ws.d_counts, 2 * (size_t)count * sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost(&ws.h_counts, 2 * (size_t)count * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&ws.d_items, (size_t)count * sizeof(ReinvItem));
+        if (e == cudaSuccess) e = cudaMallocHost(&ws.h_items, (size_t)count * sizeof(ReinvItem));
+        if (e == cudaSuccess) e = cudaMalloc(&ws.d_chk, (size_t)count * sizeof(ReinvCheck));
+        if (e == cudaSuccess) e = cudaMallocHost(&ws.h_chk, (size_t)count * sizeof(ReinvCheck));
+        if (e != cudaSuccess) return e;
+        ws.cap_n = count;
+    }
+    // slices: ints Lflag (m), S (n), R (m), posS (n), posR (m); doubles xS, yR
+    // (min(m, n) + 1 each), zrow (n + m), rhs (m)
+    size_t ni = 0, nd = 0;
+    for (int k = 0; k < count; ++k) {
+        const size_t m = jobs[k].m, n = jobs[k].n, mn = std::min(m, n) + 1;
+        ni += (3 * m + 2 * n + 63) / 64 * 64;
+        nd += (2 * mn + n + 2 * m + 31) / 32 * 32;
+    }
+    e = grow_dev(&ws.d_int, &ws.cap_int, ni);
+    if (e == cudaSuccess) e = grow_dev(&ws.d_dbl, &ws.cap_dbl, nd);
+    if (e != cudaSuccess) return e;
+    size_t oi = 0, od = 0;
+    for (int k = 0; k < count; ++k) {
+        const ReinvJob &j = jobs[k];
+        const size_t m = j.m, n = j.n, mn = std::min(m, n) + 1;
+        ReinvItem it{};
+        it.A = j.A;
+        it.b = j.b;
+        it.c = j.c;
+        it.m = j.m;
+        it.n = j.n;
+        it.sense = j.sense;
+        it.basis = j.basis;
+        it.T = j.T;
+        it.P = j.P;
+        it.x = j.x;
+        it.y = j.y;
+        it.obj = j.obj;
+        int *ib = ws.d_int + oi;
+        it.Lflag = ib;
+        it.S = ib + m;
+        it.R = ib + m + n;
+        it.posS = ib + 2 * m + n;
+        it.posR = ib + 2 * m + 2 * n;
+        it.counts = ws.d_counts + 2 * (size_t)k;
+        double *db = ws.d_dbl + od;
+        it.xS = db;
+        it.yR = db + mn;
+        it.zrow = db + 2 * mn;
+        it.rhs = db + 2 * mn + n + m;
+        it.chk = ws.d_chk + k;
+        ws.h_items[k] = it;
+        oi += (3 * m + 2 * n + 63) / 64 * 64;
+        od += (2 * mn + n + 2 * m + 31) / 32 * 32;
+    }
+    // the lists of all LPs, and their counts
+    e = cudaMemcpyAsync(ws.d_items, ws.h_items, count * sizeof(ReinvItem), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_reinv_lists_batch(ws.d_items, count, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.h_counts, ws.d_counts, 2 * (size_t)count * sizeof(int),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    // W of the LPs the one-CTA kernel takes
+    size_t nw = 0;
+    for (int k = 0; k < count; ++k) {
+        const int ns = ws.h_counts[2 * k];
+        if (ws.h_counts[2 * k + 1] != ns) {
+            *bad = k;
+            return cudaSuccess;
+        }
+        if (ns <= kReinvCtaMax) nw += (size_t)ns * (((size_t)2 * ns + 1 + 31) / 32 * 32);
+    }
+    e = grow_dev(&ws.d_W, &ws.cap_W, std::max<size_t>(nw, 1));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    size_t ow = 0;
+    std::vector<int> big;
+    std::vector<ReinvItem> small;
+    for (int k = 0; k < count; ++k) {
+        ReinvItem it = ws.h_items[k];
+        it.ns = ws.h_counts[2 * k];
+        if (it.ns <= kReinvCtaMax) {
+            it.Wp = ((long long)2 * it.ns + 1 + 31) / 32 * 32;
+            it.W = ws.d_W + ow;
+            ow += (size_t)it.ns * it.Wp;
+            small.push_back(it);
+            ++nb;
+        } else {
+            big.push_back(k);
+        }
+    }
+    for (int k = 0; k < nb; ++k) ws.h_items[k] = small[k];
+    e = cudaMemcpyAsync(ws.d_items, ws.h_items, nb * sizeof(ReinvItem), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_reinv_solve_batch(prec, ws.d_items, nb, s);
+    // the others LP by LP with the multi-CTA kernels and the pool's buffers
+    for (int k : big) {
+        if (e != cudaSuccess) break;
+        const ReinvJob &j = jobs[k];
+        const int ns = ws.h_counts[2 * k];
+        const size_t needW = (size_t)ns * (((size_t)2 * ns + 1 + 31) / 32 * 32);
+        if (needW > rp.cap_W) {
+            if (rp.rb.W) cudaFree(rp.rb.W);
+            rp.rb.W = nullptr;
+            rp.cap_W = 0;
+            e = cudaMalloc(&rp.rb.W, needW * sizeof(double));
+            if (e != cudaSuccess) break;
+            rp.cap_W = needW;
+        }
+        e = launch_reinv_lists(j.basis, j.m, j.n, rp.rb, s);
+        if (e != cudaSuccess) break;
+        rp.rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
+        e = launch_reinv_solve(prec, j.A, j.b, j.c, j.sense, j.m, j.n, j.basis, rp.rb, ns, j.T, j.P,
+                               j.x, j.y, j.obj, sms, spin_limit, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws.d_chk + k, rp.rb.chk, sizeof(ReinvCheck), cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.h_chk, ws.d_chk, count * sizeof(ReinvCheck), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
 }
 
 }  // namespace gbs

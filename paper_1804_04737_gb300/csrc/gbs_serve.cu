@@ -152,6 +152,7 @@ struct lp_server {
     std::vector<int> rule, failed;
     std::vector<long long> remaining, guard, before;
     ReinvPool *rp = nullptr;
+    BatchReinv ws32;
 };
 
 namespace {
@@ -553,7 +554,9 @@ void round32(lp_server *sv) {
         std::lock_guard<std::mutex> lk(sv->mu);
         ++sv->launches;
     }
-    std::vector<int> still;
+    // the FP64 reinversion of every active LP's basis, batched
+    std::vector<int> idx;
+    std::vector<ReinvJob> jobs;
     for (int slot : sv->active) {
         LpDesc &d = sv->h_desc32[slot];
         Request *r;
@@ -564,12 +567,10 @@ void round32(lp_server *sv) {
         const long long made = d.iters - sv->before[slot];
         sv->remaining[slot] -= made;
         sv->guard[slot] -= made;
-        const int st = d.status;
-        if (st == LP_TIMEOUT) {
+        if (d.status == LP_TIMEOUT) {
             finish32(sv, slot, LP_TIMEOUT, LP_OK);
             continue;
         }
-        // the FP64 reinversion of the basis reached
         const int m = r->m, n = r->n;
         const long long P = pitch_for(n + m + 1);
         const SlotLayout L = slot_layout(m, n, P, r->group, sizeof(float));
@@ -577,42 +578,32 @@ void round32(lp_server *sv) {
         const double *A = reinterpret_cast<const double *>(base + L.in), *b = A + (size_t)m * n,
                      *c = b + m;
         double *out = reinterpret_cast<double *>(base + L.out);
-        ReinvPool &rp = *sv->rp;
-        e = launch_reinv_lists(d.basis, m, n, rp.rb, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(rp.h_counts, rp.rb.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        const int ns = rp.h_counts[0];
-        const size_t needW = (size_t)ns * (((size_t)2 * ns + 1 + 31) / 32 * 32);
-        if (e == cudaSuccess && needW > rp.cap_W) {
-            if (rp.rb.W) cudaFree(rp.rb.W);
-            rp.rb.W = nullptr;
-            rp.cap_W = 0;
-            e = cudaMalloc(&rp.rb.W, needW * sizeof(double));
-            if (e == cudaSuccess) rp.cap_W = needW;
-        }
-        if (e == cudaSuccess) {
-            rp.rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
-            e = launch_reinv_solve(PREC_FP32, A, b, c, r->sense, m, n, d.basis, rp.rb, ns, d.T, P,
-                                   out, out + n, out + n + m, sv->sms, sv->opt.spin_timeout_cycles, s);
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(rp.h_chk, rp.rb.chk, sizeof(ReinvCheck), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess || rp.h_counts[1] != ns) {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            sv->fatal = LP_ERR_CUDA;
-            snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "FP32 reinversion: %s",
-                     e != cudaSuccess ? cudaGetErrorString(e) : "inconsistent basis");
-            sv->cv.notify_all();
-            return;
-        }
-        if (rp.h_chk->singular) {
+        jobs.push_back(ReinvJob{A, b, c, m, n, r->sense, d.basis, d.T, P, out, out + n, out + n + m});
+        idx.push_back(slot);
+    }
+    int badj = -1;
+    e = reinvert_many(PREC_FP32, jobs.data(), (int)jobs.size(), sv->ws32, *sv->rp, sv->sms,
+                      sv->opt.spin_timeout_cycles, s, &badj);
+    if (e != cudaSuccess || badj >= 0) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->fatal = LP_ERR_CUDA;
+        snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "FP32 reinversion: %s",
+                 e != cudaSuccess ? cudaGetErrorString(e) : "inconsistent basis");
+        sv->cv.notify_all();
+        return;
+    }
+    std::vector<int> still;
+    for (size_t q = 0; q < idx.size(); ++q) {
+        const int slot = idx[q];
+        LpDesc &d = sv->h_desc32[slot];
+        const int st = d.status;
+        const ReinvCheck *chk = sv->ws32.h_chk + q;
+        if (chk->singular) {
             finish32(sv, slot, LP_NUMERICAL, LP_OK);
             continue;
         }
-        const bool pfeas = key_to_double(rp.h_chk->rhsmin_key) >= -d.eps_r;
-        const bool dfeas = key_to_double(rp.h_chk->zmin_key) >= -d.eps_d;
+        const bool pfeas = key_to_double(chk->rhsmin_key) >= -d.eps_r;
+        const bool dfeas = key_to_double(chk->zmin_key) >= -d.eps_d;
         if (st == LP_OPTIMAL) {
             if (pfeas && dfeas) {
                 finish32(sv, slot, LP_OPTIMAL, LP_OK);
