@@ -146,6 +146,11 @@ typedef struct {
                                 always runs double-buffered: one pivot per pass
                                 for 2 and 3, two for 1, 4 and 5.
                                 Same pivots and bits in every mode.              */
+    long long solo_elems;    /* FP64 server: an LP of at least this many tableau
+                                elements ((m+1) x row pitch) runs alone, on the
+                                single-LP kernels that `pipeline` picks, once
+                                it reaches the head of the queue; 0 = 2^24,
+                                < 0 = never.  Ignored elsewhere.                */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances

@@ -47,6 +47,7 @@ class lp_options(ctypes.Structure):
         ("trace_cap", ctypes.c_longlong),
         ("group_elems", ctypes.c_longlong),
         ("pipeline", ctypes.c_int),
+        ("solo_elems", ctypes.c_longlong),
     ]
 
 

@@ -78,6 +78,11 @@ struct lp_handle {
     InputStats *dstats = nullptr;
     double *dx = nullptr, *dy = nullptr, *dobj = nullptr;
     size_t cap_x = 0, cap_y = 0;
+    // a caller's device range that the buffers above (from dA to dy, not the
+    // descriptor, statistics, barrier and objective words) are carved from
+    // instead of cudaMalloc: bump-allocated, never freed (handle_bind_region)
+    unsigned char *region = nullptr;
+    size_t region_size = 0, region_used = 0;
 
     // descriptor as written by lp_load, and a pinned mirror of the device copy
     // read back after each solve
@@ -117,23 +122,38 @@ void set_err(lp_handle *h, const char *fmt, ...) {
         }                                                                           \
     } while (0)
 
+// A device buffer from cudaMalloc, or on a handle bound to a device range,
+// the next 256-byte-aligned piece of that range.
+cudaError_t dev_alloc(lp_handle *h, void **ptr, size_t bytes) {
+    if (!h->region) return cudaMalloc(ptr, bytes);
+    const size_t at = (h->region_used + 255) & ~(size_t)255;
+    if (at > h->region_size || bytes > h->region_size - at) return cudaErrorMemoryAllocation;
+    *ptr = h->region + at;
+    h->region_used = at + bytes;
+    return cudaSuccess;
+}
+
+void dev_free(lp_handle *h, void *p) {
+    if (p && !h->region) cudaFree(p);
+}
+
 template <typename P>
-cudaError_t grow(P **ptr, size_t *cap, size_t need_elems) {
+cudaError_t grow(lp_handle *h, P **ptr, size_t *cap, size_t need_elems) {
     if (*ptr && *cap >= need_elems) return cudaSuccess;
-    if (*ptr) cudaFree(*ptr);
+    dev_free(h, *ptr);
     *ptr = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc((void **)ptr, std::max<size_t>(need_elems, 1) * sizeof(P));
+    cudaError_t e = dev_alloc(h, (void **)ptr, std::max<size_t>(need_elems, 1) * sizeof(P));
     if (e == cudaSuccess) *cap = need_elems;
     return e;
 }
 
-cudaError_t grow_bytes(void **ptr, size_t *cap, size_t bytes) {
+cudaError_t grow_bytes(lp_handle *h, void **ptr, size_t *cap, size_t bytes) {
     if (*ptr && *cap >= bytes) return cudaSuccess;
-    if (*ptr) cudaFree(*ptr);
+    dev_free(h, *ptr);
     *ptr = nullptr;
     *cap = 0;
-    cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    cudaError_t e = dev_alloc(h, ptr, std::max<size_t>(bytes, 16));
     if (e == cudaSuccess) *cap = bytes;
     return e;
 }
@@ -249,8 +269,10 @@ void lp_destroy(lp_handle *h) {
                      h->rb.bar};
     for (void *p : rbufs)
         if (p) cudaFree(p);
-    void *bufs[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dcolx, h->dbasis, h->dscratch, h->dpart,
-                    h->dbar, h->dtrace, h->ddesc, h->dstats, h->dx, h->dy, h->dobj};
+    void *grown[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dcolx, h->dbasis, h->dscratch,
+                     h->dpart, h->dtrace, h->dx, h->dy};
+    for (void *p : grown) dev_free(h, p);
+    void *bufs[] = {h->dbar, h->ddesc, h->dstats, h->dobj};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->pdesc) cudaFreeHost(h->pdesc);
@@ -285,9 +307,9 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
     // the inputs, and what they allow: a primal form with some b_i < 0 goes
     // through Phase I (FP64 single solves; not in the paper)
-    CUDA_TRY(h, grow(&h->dA, &h->cap_A, (size_t)m * n));
-    CUDA_TRY(h, grow(&h->db, &h->cap_b, (size_t)m));
-    CUDA_TRY(h, grow(&h->dc, &h->cap_c, (size_t)n));
+    CUDA_TRY(h, grow(h, &h->dA, &h->cap_A, (size_t)m * n));
+    CUDA_TRY(h, grow(h, &h->db, &h->cap_b, (size_t)m));
+    CUDA_TRY(h, grow(h, &h->dc, &h->cap_c, (size_t)n));
     InputStats st;
     {
         cudaStream_t s0 = h->stream;
@@ -329,7 +351,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const bool dwant = dualr && h->opt.pipeline != 0;
     bool have_t2 = false;
     if (pmode >= 3 || dwant) {
-        have_t2 = grow_bytes(&h->dT2, &h->cap_T2, (size_t)M * P * esz) == cudaSuccess;
+        have_t2 = grow_bytes(h, &h->dT2, &h->cap_T2, (size_t)M * P * esz) == cudaSuccess;
         if (!have_t2) cudaGetLastError();
     }
     if (pmode >= 3 && !have_t2) {
@@ -340,7 +362,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         pmode = 2;  // automatic mode without room for a second buffer: in place
     }
     if (pmode == 4)  // the two-pivot kernel's pivot-column slots
-        CUDA_TRY(h, grow_bytes(&h->dcolx, &h->cap_colx, 4 * (((size_t)M * esz + 15) & ~(size_t)15)));
+        CUDA_TRY(h, grow_bytes(h, &h->dcolx, &h->cap_colx, 4 * (((size_t)M * esz + 15) & ~(size_t)15)));
     const bool dpipe = dwant && have_t2;
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
@@ -378,33 +400,33 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const bool two_rules = h->prec == PREC_FP32 || phase1;
     const int ctas_max = two_rules ? std::max(sh.ctas, sh_alt.ctas) : sh.ctas;
 
-    CUDA_TRY(h, grow_bytes(&h->dT, &h->cap_T, (size_t)M * P * esz));
-    CUDA_TRY(h, grow(&h->dbasis, &h->cap_basis, (size_t)m));
+    CUDA_TRY(h, grow_bytes(h, &h->dT, &h->cap_T, (size_t)M * P * esz));
+    CUDA_TRY(h, grow(h, &h->dbasis, &h->cap_basis, (size_t)m));
     {
         size_t need = sh.use_smem ? 0 : (size_t)sh.ctas * (size_t)sh.scratch_stride;
         if (two_rules && !sh_alt.use_smem)
             need = std::max(need, (size_t)sh_alt.ctas * (size_t)sh_alt.scratch_stride);
-        if (need) CUDA_TRY(h, grow_bytes(&h->dscratch, &h->cap_scratch, need));
+        if (need) CUDA_TRY(h, grow_bytes(h, &h->dscratch, &h->cap_scratch, need));
     }
     if (h->max_ctas < ctas_max) {
-        if (h->dpart) cudaFree(h->dpart);
+        dev_free(h, h->dpart);
         h->dpart = nullptr;
         h->max_ctas = 0;
         // records: 4 x G pricing candidates, then (in 8-byte words) 32 x G
         // record values, 16 x G ratio records, 4 x G exact candidates and
         // 16 x G exact values
-        CUDA_TRY(h, cudaMalloc(&h->dpart, 38 * (size_t)ctas_max * sizeof(Cand)));
+        CUDA_TRY(h, dev_alloc(h, (void **)&h->dpart, 38 * (size_t)ctas_max * sizeof(Cand)));
         h->max_ctas = ctas_max;
     }
     if (h->opt.trace_cap > 0 && h->cap_trace < h->opt.trace_cap) {
-        if (h->dtrace) cudaFree(h->dtrace);
+        dev_free(h, h->dtrace);
         h->dtrace = nullptr;
         h->cap_trace = 0;
-        CUDA_TRY(h, cudaMalloc(&h->dtrace, 2 * (size_t)h->opt.trace_cap * sizeof(int)));
+        CUDA_TRY(h, dev_alloc(h, (void **)&h->dtrace, 2 * (size_t)h->opt.trace_cap * sizeof(int)));
         h->cap_trace = h->opt.trace_cap;
     }
-    CUDA_TRY(h, grow(&h->dx, &h->cap_x, (size_t)n));
-    CUDA_TRY(h, grow(&h->dy, &h->cap_y, (size_t)m));
+    CUDA_TRY(h, grow(h, &h->dx, &h->cap_x, (size_t)n));
+    CUDA_TRY(h, grow(h, &h->dy, &h->cap_y, (size_t)m));
 
     cudaStream_t s = h->stream;
     const double amax = bits_to_double(st.amax_bits), bmax = bits_to_double(st.bmax_bits),
@@ -825,3 +847,34 @@ lp_err lp_get_tableau(lp_handle *h, double *T) {
 }
 
 }  // extern "C"
+
+namespace gbs {
+
+lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes) {
+    if (!h || h->prec != PREC_FP64) {
+        set_err(h, "handle_bind_region: FP64 handles only");
+        return LP_ERR_INVALID_ARG;
+    }
+    cudaSetDevice(h->device);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    void **bufs[] = {(void **)&h->dA, (void **)&h->db, (void **)&h->dc, &h->dT, &h->dT2,
+                     &h->dcolx, (void **)&h->dbasis, &h->dscratch, (void **)&h->dpart,
+                     (void **)&h->dtrace, (void **)&h->dx, (void **)&h->dy};
+    for (void **p : bufs) {
+        dev_free(h, *p);
+        *p = nullptr;
+    }
+    h->cap_A = h->cap_b = h->cap_c = h->cap_T = h->cap_T2 = h->cap_colx = 0;
+    h->cap_basis = h->cap_scratch = h->cap_x = h->cap_y = 0;
+    h->max_ctas = 0;
+    h->cap_trace = 0;
+    h->loaded = h->solved = false;
+    h->region = static_cast<unsigned char *>(base);
+    h->region_size = base ? bytes : 0;
+    h->region_used = 0;
+    return LP_OK;
+}
+
+size_t handle_region_used(const lp_handle *h) { return h ? h->region_used : 0; }
+
+}  // namespace gbs

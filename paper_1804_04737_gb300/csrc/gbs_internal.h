@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "gbsimplex.h"
+
 namespace gbs {
 
 enum : int {
@@ -291,6 +293,17 @@ int max_coresident_server_ctas(int threads, size_t smem, int sms);
 
 // Record the message returned by lp_last_error(NULL) (gbs_capi.cu).
 void set_last_error_global(const char *msg);
+
+// Make an FP64 handle take the device buffers that lp_load sizes (inputs,
+// tableaus, pivot-column slots, basis, scratch, records, trace, results)
+// from [base, base + bytes) instead of cudaMalloc: the FP64 server's solves
+// of large LPs run on a handle bound to its HBM arena.  Waits for the
+// handle's stream, drops its buffers (a cudaFree unless they came from a
+// range) and marks it unloaded; base NULL unbinds.  The next lp_load carves
+// from the start of the range and fails with LP_ERR_OOM when it is too
+// small; handle_region_used reports the bytes taken so far.
+lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes);
+size_t handle_region_used(const lp_handle *h);
 
 cudaError_t launch_to_fp64(const float *T, long long P, int M, int N, double *out,
                            cudaStream_t s);

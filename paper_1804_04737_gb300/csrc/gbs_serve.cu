@@ -14,6 +14,7 @@
 // managed by a first-fit allocator with coalescing.
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -100,6 +101,7 @@ struct Request {
     int slot = -1;
     size_t off = 0, bytes = 0;
     int group = 1, strip = 0;
+    bool solo_oom = false;  // too large to run alone in the arena: served by the kernel
     // results
     std::vector<double> x, y;
     double obj = 0.0;
@@ -135,6 +137,12 @@ struct lp_server {
     bool kernel_running = false;
     cudaEvent_t kdone = nullptr;
     long long launches = 0, completed = 0;
+    // FP64: an LP of at least solo_elems tableau elements is solved alone, on
+    // a library handle whose buffers are the arena, by the single-LP kernels
+    // (two pivots per pass over the tableau on every SM), once the persistent
+    // kernel has finished the LPs admitted before it and exited
+    long long solo_elems = -1;
+    lp_handle *solo = nullptr;
     lp_err fatal = LP_OK;
     char fatal_msg[256] = {0};
     // FP32 tableaus with FP64 reinversion (precision LP_FP32_REINV): a round
@@ -214,6 +222,11 @@ void group_shape32(const lp_server *sv, int m, int n, int *G, int *W) {
     *G = (int)((P + w - 1) / w);
 }
 
+bool is_solo(const lp_server *sv, const Request &r) {
+    return sv->solo_elems >= 0 && !r.solo_oom &&
+           (long long)(r.m + 1) * pitch_for(r.n + r.m + 1) >= sv->solo_elems;
+}
+
 // Copy results of finished slots back and release their resources.
 bool engine_complete(lp_server *sv) {
     std::vector<int> fin;
@@ -269,6 +282,7 @@ bool engine_admit(lp_server *sv) {
         while (!sv->queue.empty() && !sv->free_slots.empty()) {
             const unsigned long long t = sv->queue.front();
             Request &r = sv->reqs[t];
+            if (is_solo(sv, r)) break;
             group_shape(sv, r.m, r.n, &r.group, &r.strip);
             const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group);
             size_t off;
@@ -652,12 +666,103 @@ void engine32_main(lp_server *sv) {
     }
 }
 
+// A large LP at the head of the queue.  While the persistent kernel runs, ask
+// it to exit once the LPs already admitted are done (admission stops at this
+// LP); then solve the LP on the library handle, its buffers carved from the
+// whole (now empty) arena, and return to the kernel for the LPs behind it.
+// The verdicts match the kernel's: non-finite inputs are LP_ERR_INVALID_ARG,
+// some b_i < 0 in the max form or some c_j < 0 in the min form
+// LP_ERR_INFEASIBLE_START (no Phase I in the server).  An LP the arena cannot
+// hold this way goes back to the queue head for the kernel.
+bool engine_solo(lp_server *sv) {
+    Request *r;
+    size_t off = 0, bytes = 0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->fatal != LP_OK || sv->queue.empty()) return false;
+        r = &sv->reqs[sv->queue.front()];
+        if (!is_solo(sv, *r)) return false;
+        bool busy = sv->kernel_running;
+        for (int s = 0; !busy && s < sv->max_slots; ++s) busy = sv->slot_ticket[s] != 0;
+        if (busy) {
+            *(volatile int *)&sv->h_ring->shutdown = 1;
+            return false;
+        }
+        bytes = sv->arena.size();
+        if (!sv->arena.alloc(bytes, &off)) return false;
+        sv->queue.pop_front();
+        r->state = ADMITTED;
+        r->t_admit = now_ms();
+        r->off = off;
+        r->bytes = bytes;
+    }
+    const int m = r->m, n = r->n;
+    const double *A = r->in.data(), *b = A + (size_t)m * n, *c = b + m;
+    bool bneg = false;
+    for (int i = 0; i < m; ++i) bneg |= b[i] < 0.0;
+    if (bneg && r->sense == LP_MAX_LE)
+        for (double v : r->in)
+            if (!isfinite(v)) { bneg = false; break; }  // lp_load reports the non-finite input
+    r->x.assign(n, 0.0);
+    r->y.assign(m, 0.0);
+    double obj = 0.0;
+    lp_status st = LP_NOT_SOLVED;
+    long long iters = 0;
+    lp_err verdict = LP_OK, e = LP_OK;
+    if (bneg && r->sense == LP_MAX_LE) {
+        verdict = LP_ERR_INFEASIBLE_START;
+    } else {
+        if (!sv->solo) {
+            lp_options o = sv->opt;
+            o.trace_cap = 0;
+            o.cuda_stream = nullptr;
+            e = lp_create(&sv->solo, &o);
+        }
+        if (e == LP_OK) e = handle_bind_region(sv->solo, sv->arena_dev + off, bytes);
+        if (e == LP_OK) e = lp_load(sv->solo, m, n, A, b, c, (lp_sense)r->sense);
+        if (e == LP_OK) {
+            e = lp_solve(sv->solo);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            ++sv->launches;
+        }
+        if (e == LP_OK) e = lp_result(sv->solo, r->x.data(), r->y.data(), &obj, &st, &iters);
+        if (e == LP_ERR_INVALID_ARG || e == LP_ERR_INFEASIBLE_START) {
+            verdict = e;
+            e = LP_OK;
+        }
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->arena.release(off, bytes);
+    if (e == LP_ERR_OOM) {
+        r->solo_oom = true;
+        r->state = QUEUED;
+        for (auto &t : sv->reqs)
+            if (&t.second == r) { sv->queue.push_front(t.first); break; }
+    } else if (e != LP_OK) {
+        sv->fatal = e;
+        snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "server solve of a large LP: %s",
+                 lp_last_error(sv->solo));
+    } else {
+        r->err = verdict;
+        r->status = verdict == LP_OK ? (int)st : LP_NOT_SOLVED;
+        r->obj = obj;
+        r->iters = iters;
+        r->state = DONE;
+        r->t_done = now_ms();
+        ++sv->completed;
+    }
+    *(volatile int *)&sv->h_ring->shutdown = 0;
+    sv->cv.notify_all();
+    return true;
+}
+
 void engine_main(lp_server *sv) {
     cudaSetDevice(sv->device);
     while (!sv->stop.load()) {
         bool progress = engine_complete(sv);
         progress |= engine_admit(sv);
         engine_kernel(sv);
+        progress |= engine_solo(sv);
         if (!progress) {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv.wait_for(lk, std::chrono::microseconds(20));
@@ -690,6 +795,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->device = o.device;
     sv->max_slots = max_slots;
     sv->fp32 = o.precision == LP_FP32_REINV;
+    sv->solo_elems = sv->fp32 || o.solo_elems < 0 ? -1 : o.solo_elems > 0 ? o.solo_elems : 1ll << 24;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
     const int M = lp_server::kMaxDim + 1, N = 2 * lp_server::kMaxDim + 1;
@@ -866,6 +972,7 @@ void lp_server_destroy(lp_server *sv) {
     if (sv->d_items) cudaFree(sv->d_items);
     if (sv->h_items) cudaFreeHost(sv->h_items);
     if (sv->d_queue) cudaFree(sv->d_queue);
+    lp_destroy(sv->solo);  // its buffers are the arena's: nothing of it to free
     delete sv->rp;
     delete sv;
 }

@@ -111,6 +111,45 @@ def test_serve_idle_relaunch_and_rejected_request():
         capi.lp_server_destroy(srv)
 
 
+def test_serve_large_lps_alone_in_the_mix():
+    """LPs of at least solo_elems tableau elements run alone on the single-LP
+    kernels, between busy periods of the persistent kernel; with a low
+    threshold about half of a mixed stream does.  Every result is still the
+    oracle's, bit for bit, and rejected large requests get the kernel's
+    verdicts."""
+    lps = _mix(40, 8, 300, seed=6)
+    opt = capi.lp_options_default(solo_elems=20000)
+    solo = sum((lp[0].shape[0] + 1) * (-(-(sum(lp[0].shape) + 1) // 32) * 32) >= 20000
+               for lp in lps)
+    assert 5 <= solo <= 35
+    srv = capi.lp_server_create(opt, hbm_budget_bytes=1 << 30, max_slots=32)
+    try:
+        A, b, c, _ = _mix(1, 150, 160, seed=8)[0]
+        bad = b.copy()
+        bad[3] = -1.0
+        nan = c.copy()
+        nan[0] = np.nan
+        tickets = []
+        for k, lp in enumerate(lps):
+            tickets.append(capi.lp_server_submit(srv, *lp))
+            if k == 10:
+                tb = capi.lp_server_submit(srv, A, bad, c)
+                tn = capi.lp_server_submit(srv, A, b, nan)
+            if k % 5 == 0:
+                time.sleep(0.002)
+        for lp, t in zip(lps, tickets):
+            _check(lp, capi.lp_server_wait(srv, t, lp[0].shape[0], lp[0].shape[1]))
+        for t, code in ((tb, capi.LP_ERR_INFEASIBLE_START), (tn, capi.LP_ERR_INVALID_ARG)):
+            with pytest.raises(capi.LpError) as e:
+                capi.lp_server_wait(srv, t, A.shape[0], A.shape[1])
+            assert e.value.code == code
+        done, launches, used, queued = capi.lp_server_stats(srv)
+        assert done == len(lps) + 2 and used == 0 and queued == 0
+        assert launches >= solo + 1
+    finally:
+        capi.lp_server_destroy(srv)
+
+
 # ---- FP32 tableaus with FP64 reinversion ----
 
 OBJ_TOL32 = 1e-6
