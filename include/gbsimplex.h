@@ -146,11 +146,13 @@ typedef struct {
                                 always runs double-buffered: one pivot per pass
                                 for 2 and 3, two for 1, 4 and 5.
                                 Same pivots and bits in every mode.              */
-    long long solo_elems;    /* FP64 server: an LP of at least this many tableau
-                                elements ((m+1) x row pitch) runs alone, on the
-                                single-LP kernels that `pipeline` picks, once
-                                it reaches the head of the queue; 0 = 2^24,
-                                < 0 = never.  Ignored elsewhere.                */
+    long long solo_elems;    /* servers: an LP of at least this many tableau
+                                elements ((m+1) x row pitch) runs alone, as
+                                lp_load + lp_solve would run it (the kernels
+                                `pipeline` picks; FP32: with its reinversions),
+                                once it reaches the head of the queue and the
+                                LPs ahead of it are done; 0 = 2^24, < 0 =
+                                never.  Ignored elsewhere.                      */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
@@ -240,7 +242,10 @@ lp_err lp_batch_autotune(int count, const int *m, const int *n, const double *co
  * and read off by a persistent kernel that takes new LPs while others are
  * running, so their work overlaps on the GPU.  Each LP runs on a group of
  * CTAs with the single-LP pivot code, so its result equals solving it alone
- * bit for bit.  m, n <= 4096; inputs and outputs in host memory.
+ * bit for bit.  An LP of at least opt->solo_elems tableau elements instead
+ * runs alone, as lp_load + lp_solve run it, once the LPs ahead of it are
+ * done (its buffers come from the same arena).  m, n <= 4096; inputs and
+ * outputs in host memory.
  * With opt->precision == LP_FP32_REINV the tableaus are FP32 and the server
  * works in rounds: one batched launch in which every admitted LP pivots up
  * to reinv_k times, then each LP's FP64 reinversion and the decisions of the

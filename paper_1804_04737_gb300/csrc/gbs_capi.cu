@@ -79,8 +79,9 @@ struct lp_handle {
     double *dx = nullptr, *dy = nullptr, *dobj = nullptr;
     size_t cap_x = 0, cap_y = 0;
     // a caller's device range that the buffers above (from dA to dy, not the
-    // descriptor, statistics, barrier and objective words) are carved from
-    // instead of cudaMalloc: bump-allocated, never freed (handle_bind_region)
+    // descriptor, statistics, barrier and objective words) and the FP64
+    // reinversion buffers below are carved from instead of cudaMalloc:
+    // bump-allocated, never freed (handle_bind_region)
     unsigned char *region = nullptr;
     size_t region_size = 0, region_used = 0;
 
@@ -267,8 +268,7 @@ void lp_destroy(lp_handle *h) {
     void *rbufs[] = {h->rb.Lflag, h->rb.S, h->rb.R, h->rb.posS, h->rb.posR, h->rb.counts,
                      h->rb.pivrow, h->rb.W, h->rb.xS, h->rb.yR, h->rb.zrow, h->rb.rhs, h->rb.chk,
                      h->rb.bar};
-    for (void *p : rbufs)
-        if (p) cudaFree(p);
+    for (void *p : rbufs) dev_free(h, p);
     void *grown[] = {h->dA, h->db, h->dc, h->dT, h->dT2, h->dcolx, h->dbasis, h->dscratch,
                      h->dpart, h->dtrace, h->dx, h->dy};
     for (void *p : grown) dev_free(h, p);
@@ -447,20 +447,20 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         void **ints[] = {(void **)&h->rb.Lflag, (void **)&h->rb.S, (void **)&h->rb.R,
                          (void **)&h->rb.posS, (void **)&h->rb.posR, (void **)&h->rb.pivrow};
         for (void **q : ints) {
-            if (*q) cudaFree(*q);
+            dev_free(h, *q);
             *q = nullptr;
-            CUDA_TRY(h, cudaMalloc(q, cap * sizeof(int)));
+            CUDA_TRY(h, dev_alloc(h, q, cap * sizeof(int)));
         }
         void **dbl[] = {(void **)&h->rb.xS, (void **)&h->rb.yR, (void **)&h->rb.zrow,
                         (void **)&h->rb.rhs};
         for (void **q : dbl) {
-            if (*q) cudaFree(*q);
+            dev_free(h, *q);
             *q = nullptr;
-            CUDA_TRY(h, cudaMalloc(q, cap * sizeof(double)));
+            CUDA_TRY(h, dev_alloc(h, q, cap * sizeof(double)));
         }
-        if (!h->rb.counts) CUDA_TRY(h, cudaMalloc(&h->rb.counts, 4 * sizeof(int)));
-        if (!h->rb.chk) CUDA_TRY(h, cudaMalloc(&h->rb.chk, sizeof(ReinvCheck)));
-        if (!h->rb.bar) CUDA_TRY(h, cudaMalloc(&h->rb.bar, 128 * sizeof(unsigned)));
+        if (!h->rb.counts) CUDA_TRY(h, dev_alloc(h, (void **)&h->rb.counts, 4 * sizeof(int)));
+        if (!h->rb.chk) CUDA_TRY(h, dev_alloc(h, (void **)&h->rb.chk, sizeof(ReinvCheck)));
+        if (!h->rb.bar) CUDA_TRY(h, dev_alloc(h, (void **)&h->rb.bar, 128 * sizeof(unsigned)));
         h->cap_rb = cap;
     }
 
@@ -553,11 +553,14 @@ lp_err reinvert(lp_handle *h, bool *singular, double *zmin, double *rmin) {
     h->rb.Wp = ((long long)2 * ns + 1 + 31) / 32 * 32;
     const size_t need = (size_t)ns * (size_t)h->rb.Wp;
     if (need > h->cap_W) {
-        if (h->rb.W) cudaFree(h->rb.W);
+        dev_free(h, h->rb.W);
         h->rb.W = nullptr;
         h->cap_W = 0;
-        CUDA_TRY(h, cudaMalloc(&h->rb.W, std::max<size_t>(need, 1) * sizeof(double)));
-        h->cap_W = need;
+        // from a range (never freed), the largest this LP can need, at once
+        const size_t nsx = (size_t)std::min(m, n);
+        const size_t want = h->region ? std::max(need, nsx * ((2 * nsx + 1 + 31) / 32 * 32)) : need;
+        CUDA_TRY(h, dev_alloc(h, (void **)&h->rb.W, std::max<size_t>(want, 1) * sizeof(double)));
+        h->cap_W = want;
     }
     CUDA_TRY(h, launch_reinv_solve(h->prec, h->dA, h->db, h->dc, h->sense, m, n, h->dbasis, h->rb,
                                    ns, h->dT, h->P, h->dx, h->dy, h->dobj, h->sms,
@@ -851,15 +854,20 @@ lp_err lp_get_tableau(lp_handle *h, double *T) {
 namespace gbs {
 
 lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes) {
-    if (!h || h->prec != PREC_FP64) {
-        set_err(h, "handle_bind_region: FP64 handles only");
+    if (!h) {
+        set_err(h, "handle_bind_region: NULL handle");
         return LP_ERR_INVALID_ARG;
     }
     cudaSetDevice(h->device);
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     void **bufs[] = {(void **)&h->dA, (void **)&h->db, (void **)&h->dc, &h->dT, &h->dT2,
                      &h->dcolx, (void **)&h->dbasis, &h->dscratch, (void **)&h->dpart,
-                     (void **)&h->dtrace, (void **)&h->dx, (void **)&h->dy};
+                     (void **)&h->dtrace, (void **)&h->dx, (void **)&h->dy,
+                     (void **)&h->rb.Lflag, (void **)&h->rb.S, (void **)&h->rb.R,
+                     (void **)&h->rb.posS, (void **)&h->rb.posR, (void **)&h->rb.counts,
+                     (void **)&h->rb.pivrow, (void **)&h->rb.W, (void **)&h->rb.xS,
+                     (void **)&h->rb.yR, (void **)&h->rb.zrow, (void **)&h->rb.rhs,
+                     (void **)&h->rb.chk, (void **)&h->rb.bar};
     for (void **p : bufs) {
         dev_free(h, *p);
         *p = nullptr;
@@ -868,6 +876,7 @@ lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes) {
     h->cap_basis = h->cap_scratch = h->cap_x = h->cap_y = 0;
     h->max_ctas = 0;
     h->cap_trace = 0;
+    h->cap_W = h->cap_rb = 0;
     h->loaded = h->solved = false;
     h->region = static_cast<unsigned char *>(base);
     h->region_size = base ? bytes : 0;

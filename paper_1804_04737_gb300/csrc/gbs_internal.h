@@ -294,10 +294,11 @@ int max_coresident_server_ctas(int threads, size_t smem, int sms);
 // Record the message returned by lp_last_error(NULL) (gbs_capi.cu).
 void set_last_error_global(const char *msg);
 
-// Make an FP64 handle take the device buffers that lp_load sizes (inputs,
-// tableaus, pivot-column slots, basis, scratch, records, trace, results)
-// from [base, base + bytes) instead of cudaMalloc: the FP64 server's solves
-// of large LPs run on a handle bound to its HBM arena.  Waits for the
+// Make a handle take the device buffers that lp_load and the FP32 mode's
+// reinversions size (inputs, tableaus, pivot-column slots, basis, scratch,
+// records, trace, results, reinversion lists and matrix) from
+// [base, base + bytes) instead of cudaMalloc: the server's solves of large
+// LPs run on a handle bound to its HBM arena.  Waits for the
 // handle's stream, drops its buffers (a cudaFree unless they came from a
 // range) and marks it unloaded; base NULL unbinds.  The next lp_load carves
 // from the start of the range and fails with LP_ERR_OOM when it is too

@@ -137,10 +137,11 @@ struct lp_server {
     bool kernel_running = false;
     cudaEvent_t kdone = nullptr;
     long long launches = 0, completed = 0;
-    // FP64: an LP of at least solo_elems tableau elements is solved alone, on
-    // a library handle whose buffers are the arena, by the single-LP kernels
-    // (two pivots per pass over the tableau on every SM), once the persistent
-    // kernel has finished the LPs admitted before it and exited
+    // an LP of at least solo_elems tableau elements is solved alone, on a
+    // library handle whose buffers are the arena, by the single-LP kernels
+    // (two pivots per pass over the tableau on every SM; in FP32 mode with its
+    // FP64 reinversions), once the LPs admitted before it are done (FP64: the
+    // persistent kernel has finished them and exited; FP32: no LP is in a round)
     long long solo_elems = -1;
     lp_handle *solo = nullptr;
     lp_err fatal = LP_OK;
@@ -444,6 +445,7 @@ bool admit32(lp_server *sv) {
         while (!sv->queue.empty() && !sv->free_slots.empty()) {
             const unsigned long long t = sv->queue.front();
             Request &r = sv->reqs[t];
+            if (is_solo(sv, r)) break;
             group_shape32(sv, r.m, r.n, &r.group, &r.strip);
             const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group, sizeof(float));
             size_t off;
@@ -648,6 +650,8 @@ void round32(lp_server *sv) {
     sv->active.swap(still);
 }
 
+bool engine_solo(lp_server *sv);
+
 void engine32_main(lp_server *sv) {
     cudaSetDevice(sv->device);
     while (!sv->stop.load()) {
@@ -659,21 +663,22 @@ void engine32_main(lp_server *sv) {
         const bool admitted = !fatal && admit32(sv);
         if (!fatal && !sv->active.empty()) {
             round32(sv);
-        } else if (!admitted) {
+        } else if (!admitted && (fatal || !engine_solo(sv))) {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv.wait_for(lk, std::chrono::microseconds(20));
         }
     }
 }
 
-// A large LP at the head of the queue.  While the persistent kernel runs, ask
-// it to exit once the LPs already admitted are done (admission stops at this
-// LP); then solve the LP on the library handle, its buffers carved from the
-// whole (now empty) arena, and return to the kernel for the LPs behind it.
-// The verdicts match the kernel's: non-finite inputs are LP_ERR_INVALID_ARG,
-// some b_i < 0 in the max form or some c_j < 0 in the min form
+// A large LP at the head of the queue.  While LPs admitted before it are in
+// flight (admission stops at this LP), ask the FP64 persistent kernel to exit
+// once they are done, or let the FP32 rounds finish them; then solve the LP on
+// the library handle, its buffers carved from the whole (now empty) arena,
+// and return to the kernel or the rounds for the LPs behind it.  The verdicts
+// match the other path's: non-finite inputs are LP_ERR_INVALID_ARG, some
+// b_i < 0 in the max form or some c_j < 0 in the min form
 // LP_ERR_INFEASIBLE_START (no Phase I in the server).  An LP the arena cannot
-// hold this way goes back to the queue head for the kernel.
+// hold this way goes back to the queue head for the other path.
 bool engine_solo(lp_server *sv) {
     Request *r;
     size_t off = 0, bytes = 0;
@@ -682,7 +687,7 @@ bool engine_solo(lp_server *sv) {
         if (sv->fatal != LP_OK || sv->queue.empty()) return false;
         r = &sv->reqs[sv->queue.front()];
         if (!is_solo(sv, *r)) return false;
-        bool busy = sv->kernel_running;
+        bool busy = sv->kernel_running || !sv->active.empty();
         for (int s = 0; !busy && s < sv->max_slots; ++s) busy = sv->slot_ticket[s] != 0;
         if (busy) {
             *(volatile int *)&sv->h_ring->shutdown = 1;
@@ -795,7 +800,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->device = o.device;
     sv->max_slots = max_slots;
     sv->fp32 = o.precision == LP_FP32_REINV;
-    sv->solo_elems = sv->fp32 || o.solo_elems < 0 ? -1 : o.solo_elems > 0 ? o.solo_elems : 1ll << 24;
+    sv->solo_elems = o.solo_elems < 0 ? -1 : o.solo_elems > 0 ? o.solo_elems : 1ll << 24;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
     const int M = lp_server::kMaxDim + 1, N = 2 * lp_server::kMaxDim + 1;

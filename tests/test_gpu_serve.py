@@ -195,6 +195,43 @@ def test_serve_fp32_objective_and_mix_invariance():
         assert np.array_equal(_bits(alone[4]), _bits(res[i][4]))
 
 
+def test_serve_fp32_large_lps_alone():
+    """FP32 serving with a low solo_elems: the large LPs leave the rounds and
+    run alone as lp_load + lp_solve run them, bit for bit, between rounds;
+    every result still reaches the FP64 optimum within the FP32 tolerance."""
+    lps = _mix(24, 8, 300, seed=6)
+    opt = capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50, solo_elems=20000)
+    srv = capi.lp_server_create(opt, hbm_budget_bytes=1 << 30, max_slots=32)
+    try:
+        tickets = [capi.lp_server_submit(srv, *lp) for lp in lps]
+        res = [capi.lp_server_wait(srv, t, lp[0].shape[0], lp[0].shape[1])
+               for lp, t in zip(lps, tickets)]
+        assert capi.lp_server_stats(srv)[2] == 0
+    finally:
+        capi.lp_server_destroy(srv)
+    alone = 0
+    h = capi.lp_create(capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50))
+    try:
+        for lp, r in zip(lps, res):
+            A, b, c, sense = lp
+            o = oracle.solve(A, b, c, sense=sense)
+            assert r[1] == capi.LP_OPTIMAL
+            assert abs(r[0] - o.obj) / max(1.0, abs(o.obj)) <= OBJ_TOL32, (r[0], o.obj)
+            m, n = A.shape
+            if (m + 1) * (-(-(m + n + 1) // 32) * 32) < 20000:
+                continue
+            alone += 1
+            capi.lp_load(h, A, b, c, sense)
+            capi.lp_solve(h)
+            x, y = np.empty(n), np.empty(m)
+            obj, st, it = capi.lp_result(h, x, y)
+            assert _bits([obj])[0] == _bits([r[0]])[0] and st == r[1] and it == r[2]
+            assert np.array_equal(_bits(x), _bits(r[3])) and np.array_equal(_bits(y), _bits(r[4]))
+    finally:
+        capi.lp_destroy(h)
+    assert alone >= 3
+
+
 def test_serve_fp32_small_budget_and_rejects():
     """A budget that holds a few LPs at a time (requests wait for memory
     between rounds), reinv_k = 200, and a request the FP32 mode refuses."""
