@@ -121,11 +121,21 @@ class Clocks:
         self.path = os.path.join("/tmp", "gbs_clocks_%d_%d.csv" % (os.getpid(), index))
 
     def __enter__(self):
+        self.skip = 0
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a while to start: wait for its first sample, so
+            # that the samples kept (those after it) fall inside the timed region
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.proc.poll() is None:
+                with open(self.path) as g:
+                    self.skip = sum(1 for _ in g)
+                if self.skip:
+                    break
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -147,6 +157,8 @@ class Clocks:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
                 rows.append(parts)
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]  # the samples taken while the region ran
         if not rows:
             return {"error": "no samples"}
         sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
