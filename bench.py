@@ -392,6 +392,7 @@ def run_serve(args, capi, torch):
     err = max(abs(a - b) / max(1.0, abs(b)) for a, b in zip(obj32[:n], obj64[:n]))
     print(json.dumps({"workload": "serving: Poisson stream of dense LPs, m,n log-uniform "
                       "[64,4096], 60 GB HBM budget", "requests_per_point": per_point,
+                      "alone_from_tableau_elems": 1 << 24,  # lp_options.solo_elems default
                       "one_lp_per_launch_fp64_lps_per_s": round(one, 1),
                       "fp64": {"saturation": max(fp64, key=lambda p: p["lps_per_s"]), "sweep": fp64},
                       "fp32_reinv_k50": {"saturation": max(fp32, key=lambda p: p["lps_per_s"]),
