@@ -129,3 +129,44 @@ def test_mutant_is_caught(name, tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", _build_mutant(tmp_path, old, new))
     with pytest.raises(AssertionError):
         _pins()
+
+
+# Planted mistakes in copies of oracle.certificate (the checker behind every
+# FP32, batch and serving assertion); the hand-computed battery of
+# test_oracle_certificate.py must fail each one.
+CERT_MUTANTS = {
+    "dropped_max": ("primal = max(0.0, float(np.max(Ax - b)) if len(b) else 0.0)",
+                    "primal = float(np.max(Ax - b)) if len(b) else 0.0"),
+    "dual_sign_swapped": ("dual = max(0.0, float(np.max(c - Aty)) if len(c) else 0.0)",
+                          "dual = max(0.0, float(np.max(Aty - c)) if len(c) else 0.0)"),
+    "min_form_primal_sign": ("primal = max(0.0, float(np.max(b - Ax)) if len(b) else 0.0)",
+                             "primal = max(0.0, float(np.max(Ax - b)) if len(b) else 0.0)"),
+    "x_neg_from_max": ('"x_neg": max(0.0, float(-np.min(x)) if len(x) else 0.0)',
+                       '"x_neg": max(0.0, float(-np.max(x)) if len(x) else 0.0)'),
+    "gap_against_obj": ('"gap": abs(float(c @ x) - float(b @ y))',
+                        '"gap": abs(obj - float(b @ y))'),
+    "compl_rows_self": ('np.abs(y * (b - Ax))', 'np.abs(y * (Ax - Ax))'),
+    "compl_cols_transposed": ("Aty = A.T @ y", "Aty = A.T @ y[::-1]"),
+}
+
+
+def _mutant_certificate(old, new):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(oracle.certificate))
+    assert src.count(old) == 1, old
+    ns = {"np": np, "MAX_LE": oracle.MAX_LE}
+    exec(compile(src.replace(old, new), "<mutant certificate>", "exec"), ns)
+    return ns["certificate"]
+
+
+def test_unmutated_certificate_passes():
+    from test_oracle_certificate import certificate_pins
+    certificate_pins(_mutant_certificate("Aty = A.T @ y", "Aty = A.T @ y"))
+
+
+@pytest.mark.parametrize("name", sorted(CERT_MUTANTS))
+def test_certificate_mutant_is_caught(name):
+    from test_oracle_certificate import certificate_pins
+    with pytest.raises(AssertionError):
+        certificate_pins(_mutant_certificate(*CERT_MUTANTS[name]))
