@@ -100,7 +100,10 @@ typedef enum {
     LP_ITER_LIMIT = 2,  /* max_iters pivots made in this call; lp_solve resumes */
     LP_INFEASIBLE = 3,  /* dual simplex: violated row with no T[r][j] < -eps_p */
     LP_NUMERICAL = 4,   /* FP32 mode: FP64 check still fails after reinversions */
-    LP_TIMEOUT = 5,     /* a device-side wait exceeded spin_timeout_cycles     */
+    LP_TIMEOUT = 5,     /* a device-side wait exceeded spin_timeout_cycles, or
+                           the solve ran past time_limit_s; the tableau is then
+                           undefined and lp_solve refuses to resume
+                           (LP_ERR_STATE) until the next lp_load               */
     LP_NOT_SOLVED = 6
 } lp_status;
 
@@ -153,11 +156,20 @@ typedef struct {
                                 once it reaches the head of the queue and the
                                 LPs ahead of it are done; 0 = 2^24, < 0 =
                                 never.  Ignored elsewhere.                      */
+    double time_limit_s;     /* single-LP solves: wall-clock limit in seconds of
+                                one lp_solve call (or of lp_solve_async and the
+                                wait that completes it), 0 = none.  Past it the
+                                host raises an abort word in mapped host memory
+                                that every pivot kernel reads once per pass; the
+                                kernel stops within a pass and the solve ends in
+                                LP_TIMEOUT.  Ignored by batches, servers and
+                                lp_solve_noalloc.                               */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
  * by formula, bland_after 32, auto launch shape, spin timeout 4e9 cycles,
- * library stream, device 0, no trace, pipelined primal kernel. */
+ * library stream, device 0, no trace, pipelined primal kernel, no wall-clock
+ * limit. */
 void lp_options_default(lp_options *opt);
 
 /* Create a handle on opt->device (opt may be NULL for the defaults).
@@ -178,7 +190,9 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b,
 
 /* Pivot until optimal, unbounded / infeasible, or max_iters pivots in this
  * call; blocking.  After LP_ITER_LIMIT another call continues from the same
- * tableau.  Errors: LP_ERR_STATE (nothing loaded), LP_ERR_CUDA. */
+ * tableau.  With opt->time_limit_s > 0 the call ends in LP_TIMEOUT once that
+ * much wall time has passed.  Errors: LP_ERR_STATE (nothing loaded, or the
+ * last solve ended in LP_TIMEOUT), LP_ERR_CUDA. */
 lp_err lp_solve(lp_handle *h);
 
 /* Enqueue the same work on the handle's stream and return without waiting;
@@ -216,8 +230,12 @@ lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches);
  * queue, largest LPs first.  Per-LP arithmetic is the single-LP path's, so
  * each result equals solving that LP alone bit for bit.  Outputs per LP:
  * obj[k], status[k], iters[k] and, when x / y and x[k] / y[k] are non-NULL,
- * the primal and dual vectors (host memory).  FP64 only; opt->threads caps
- * the CTA size at 512; device memory is pooled per device between calls.
+ * the primal and dual vectors (host memory).  With opt->precision ==
+ * LP_FP32_REINV the tableaus are FP32 and every LP is reinverted in FP64
+ * (batched) every reinv_k pivots and at termination, as in the single-LP FP32
+ * mode (b >= 0 and c >= 0 required); each result then equals that LP's solo
+ * FP32 solve.  opt->threads caps the CTA size at 512; device memory is pooled
+ * per device between calls.
  * Blocking.  Errors as lp_load (the message names the LP), in
  * lp_last_error(NULL). */
 lp_err lp_solve_batch(int count, const int *m, const int *n, const double *const *A,
@@ -292,8 +310,14 @@ lp_err lp_batch_stats(double *kernel_ms, long long *pivots, int *ctas, int *thre
  * device allocator, loops that must not pay an allocation's latency.
  *   - A (m x n, row-major), b, c: host or device memory; x (n), y (m): host or
  *     device memory or NULL; obj, status, iters: host pointers or NULL.
- *   - opt: NULL for the defaults; FP64 only, opt->trace_cap is ignored, runs
- *     on opt->cuda_stream (NULL: the legacy default stream) and opt->device.
+ *   - opt: NULL for the defaults; FP64 only, opt->trace_cap, opt->pipeline
+ *     and opt->time_limit_s are ignored, runs on opt->cuda_stream (NULL: the
+ *     legacy default stream) and opt->device; the caller's current device is
+ *     restored on return.
+ *   - It always runs the one-pivot in-place kernel (pipeline 0: selection,
+ *     then the update, one grid barrier per pivot), whose results are bit for
+ *     bit those of the other kernels; the pipelined kernels need a second
+ *     tableau and more record space than the array holds.
  *   - Blocking: returns after the results are written.
  *   - LPs whose working memory exceeds 64 MiB (about 1500 x 1500) are
  *     rejected with LP_ERR_INVALID_ARG before any GPU work.

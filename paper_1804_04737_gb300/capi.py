@@ -48,6 +48,7 @@ class lp_options(ctypes.Structure):
         ("group_elems", ctypes.c_longlong),
         ("pipeline", ctypes.c_int),
         ("solo_elems", ctypes.c_longlong),
+        ("time_limit_s", ctypes.c_double),
     ]
 
 
@@ -231,10 +232,19 @@ def lp_kernel_time(h):
     return ms.value, n.value
 
 
+def _check_shape(a, shape, name):
+    if a is not None and tuple(a.shape) != shape:
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(a.shape), shape))
+
+
 def lp_solve_noalloc(A, b, c, sense=LP_MAX_LE, opt: Optional[lp_options] = None, x=None,
                      y=None):
     """Allocation-free solve; returns (obj, status, iters) and fills x, y."""
+    if len(A.shape) != 2:
+        raise ValueError("A must be a matrix, got shape %s" % (tuple(A.shape),))
     m, n = int(A.shape[0]), int(A.shape[1])
+    for a, shape, name in ((b, (m,), "b"), (c, (n,), "c"), (x, (n,), "x"), (y, (m,), "y")):
+        _check_shape(a, shape, name)
     obj = ctypes.c_double()
     st = ctypes.c_int()
     it = ctypes.c_longlong()

@@ -405,6 +405,7 @@ extern "C" lp_err lp_solve_batch(int count, const int *m, const int *n, const do
         if ((long long)n[k] + m[k] + 1 > 0x7fffffffll - 64)
             return bfail(LP_ERR_INVALID_ARG, "lp_solve_batch: LP %d too large", k);
     }
+    DeviceRestore restore_;
     B_TRY(cudaSetDevice(o.device));
     int sms = 0;
     B_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device));

@@ -13,7 +13,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <new>
+#include <thread>
 
 #include "gbs_internal.h"
 #include "gbsimplex.h"
@@ -101,6 +103,14 @@ struct lp_handle {
     double fp32_kernel_ms = 0.0, reinv_ms = 0.0;
     int fp32_launches = 0, reinversions = 0;
     double eps32_d = 0, eps32_p = 0, eps32_r = 0;
+
+    // wall-clock limit (opt.time_limit_s): the abort word the pivot kernels
+    // poll, in mapped pinned host memory, and the deadline of the solve in
+    // flight
+    int *habort = nullptr;        // host view
+    int *dabort = nullptr;        // device view of the same word
+    std::chrono::steady_clock::time_point deadline{};
+    bool timed_out = false;       // the last solve ended in LP_TIMEOUT: reload first
 };
 
 namespace {
@@ -234,6 +244,7 @@ lp_err lp_create(lp_handle **out, const lp_options *opt) {
     h->opt = o;
     h->device = o.device;
     h->prec = o.precision == LP_FP64 ? PREC_FP64 : PREC_FP32;
+    DeviceRestore restore_;
     e = cudaSetDevice(h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) {
@@ -252,6 +263,11 @@ lp_err lp_create(lp_handle **out, const lp_options *opt) {
     if (e == cudaSuccess) e = cudaMallocHost(&h->pobj, sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+    if (e == cudaSuccess) e = cudaHostAlloc(&h->habort, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *h->habort = 0;
+        e = cudaHostGetDevicePointer((void **)&h->dabort, h->habort, 0);
+    }
     if (e != cudaSuccess) {
         set_err(nullptr, "lp_create: %s", cudaGetErrorString(e));
         lp_destroy(h);
@@ -263,6 +279,7 @@ lp_err lp_create(lp_handle **out, const lp_options *opt) {
 
 void lp_destroy(lp_handle *h) {
     if (!h) return;
+    DeviceRestore restore_;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     void *rbufs[] = {h->rb.Lflag, h->rb.S, h->rb.R, h->rb.posS, h->rb.posR, h->rb.counts,
@@ -277,6 +294,7 @@ void lp_destroy(lp_handle *h) {
         if (p) cudaFree(p);
     if (h->pdesc) cudaFreeHost(h->pdesc);
     if (h->pobj) cudaFreeHost(h->pobj);
+    if (h->habort) cudaFreeHost(h->habort);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -299,9 +317,11 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
         set_err(h, "lp_load: n + m too large");
         return LP_ERR_INVALID_ARG;
     }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
     h->loaded = false;
     h->solved = false;
+    h->timed_out = false;
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const size_t esz = h->prec == PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -476,6 +496,7 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.part_vals = reinterpret_cast<unsigned long long *>(h->dpart + 4 * (size_t)h->max_ctas);
     d.T2 = have_t2 ? h->dT2 : nullptr;
     d.colx = h->dcolx;
+    d.abort = h->dabort;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;
@@ -514,6 +535,39 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
 }  // extern "C"
 
 namespace {
+
+// Start the wall-clock limit of a solve: lower the abort word (no kernel of
+// this handle is running: the previous solve was waited for) and set the
+// deadline.
+void arm_deadline(lp_handle *h) {
+    __atomic_store_n(h->habort, 0, __ATOMIC_SEQ_CST);
+    if (h->opt.time_limit_s > 0.0)
+        h->deadline = std::chrono::steady_clock::now() +
+                      std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                          std::chrono::duration<double>(h->opt.time_limit_s));
+}
+
+bool past_deadline(const lp_handle *h) {
+    return h->opt.time_limit_s > 0.0 && std::chrono::steady_clock::now() >= h->deadline;
+}
+
+// Wait for the handle's stream.  Under a wall-clock limit the host polls the
+// stream and, once the deadline has passed, raises the abort word, which
+// every pivot kernel reads once per pass: the kernel stops within a pass
+// with status LP_TIMEOUT and the wait ends.
+cudaError_t wait_stream(lp_handle *h) {
+    if (h->opt.time_limit_s <= 0.0) return cudaStreamSynchronize(h->stream);
+    bool raised = false;
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(h->stream);
+        if (e != cudaErrorNotReady) return e;
+        if (!raised && past_deadline(h)) {
+            __atomic_store_n(h->habort, 1, __ATOMIC_SEQ_CST);
+            raised = true;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
 
 // The double-buffered kernel leaves its last tableau in either buffer and
 // names it in the descriptor; once the descriptor is read back, make it h->dT.
@@ -609,7 +663,7 @@ lp_err solve_fp32(lp_handle *h) {
         CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, sh, h->opt.spin_timeout_cycles, budget, s));
         CUDA_TRY(h, cudaEventRecord(h->ev1, s));
         CUDA_TRY(h, cudaMemcpyAsync(h->pdesc, h->ddesc, sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(h, cudaStreamSynchronize(s));
+        CUDA_TRY(h, wait_stream(h));
         adopt_tableau(h);
         float t = 0.0f;
         cudaEventElapsedTime(&t, h->ev0, h->ev1);
@@ -618,7 +672,7 @@ lp_err solve_fp32(lp_handle *h) {
         remaining -= h->pdesc->iters - before;
         guard -= h->pdesc->iters - before;
         const int st = h->pdesc->status;
-        if (st == LP_TIMEOUT) {
+        if (st == LP_TIMEOUT || past_deadline(h)) {
             final = LP_TIMEOUT;
             break;
         }
@@ -671,6 +725,7 @@ lp_err solve_fp32(lp_handle *h) {
         else if (rule == 1 && !dfeas && pfeas) rule = 0;
     }
     h->pdesc->status = final;
+    if (final == LP_TIMEOUT) h->timed_out = true;
     CUDA_TRY(h, cudaMemcpyAsync(h->pobj, h->dobj, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->solved = true;
@@ -687,7 +742,14 @@ lp_err lp_solve_async(lp_handle *h) {
         set_err(h, "lp_solve: no LP loaded");
         return LP_ERR_STATE;
     }
+    if (h->timed_out) {
+        set_err(h, "lp_solve: the last solve ended in LP_TIMEOUT and left the tableau "
+                   "undefined; load the LP again");
+        return LP_ERR_STATE;
+    }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
+    arm_deadline(h);
     if (h->prec == PREC_FP32) return solve_fp32(h);
     cudaStream_t s = h->stream;
     // The pivot state (iterations, degeneracy counter) lives in the device
@@ -703,9 +765,9 @@ lp_err lp_solve_async(lp_handle *h) {
         CUDA_TRY(h, launch_pivot(h->prec, h->ddesc, h->shape_alt, h->opt.spin_timeout_cycles,
                                  budget, s));
         CUDA_TRY(h, cudaMemcpyAsync(h->pdesc, h->ddesc, sizeof(LpDesc), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(h, cudaStreamSynchronize(s));
+        CUDA_TRY(h, wait_stream(h));
         adopt_tableau(h);
-        if (h->pdesc->status == ST_OPTIMAL) {
+        if (h->pdesc->status == ST_OPTIMAL && !past_deadline(h)) {
             // Phase 2 from this basis: the objective row of c, the
             // degenerate-pivot count restarted
             CUDA_TRY(h, launch_phase2_objective(h->ddesc, h->dc, h->N, s));
@@ -715,7 +777,14 @@ lp_err lp_solve_async(lp_handle *h) {
             h->phase = 2;
             budget -= h->pdesc->iters - before;
         } else {
-            // infeasible (or stopped: iteration limit, timeout; resumable in Phase 1)
+            // infeasible (or stopped: iteration limit, timeout; resumable in
+            // Phase 1 after the iteration limit)
+            if (h->pdesc->status == ST_OPTIMAL) {  // Phase 1 done, but past the deadline
+                h->pdesc->status = LP_TIMEOUT;
+                const int st = LP_TIMEOUT;
+                CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, status), &st,
+                                            sizeof st, cudaMemcpyHostToDevice, s));
+            }
             CUDA_TRY(h, cudaEventRecord(h->ev1, s));
             CUDA_TRY(h, launch_extract(h->prec, h->ddesc, h->dT, h->dbasis, h->m, h->n, h->P,
                                        h->sense, h->dx, h->dy, h->dobj, s));
@@ -738,7 +807,8 @@ lp_err lp_solve_async(lp_handle *h) {
 lp_err lp_solve(lp_handle *h) {
     lp_err e = lp_solve_async(h);
     if (e != LP_OK) return e;
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    CUDA_TRY(h, wait_stream(h));
+    if (h->pdesc->status == LP_TIMEOUT) h->timed_out = true;
     return LP_OK;
 }
 
@@ -749,8 +819,11 @@ lp_err lp_result(lp_handle *h, double *x, double *y, double *obj, lp_status *sta
         set_err(h, "lp_result: nothing solved");
         return LP_ERR_STATE;
     }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
+    CUDA_TRY(h, wait_stream(h));
+    if (h->pdesc->status == LP_TIMEOUT) h->timed_out = true;
     if (x) CUDA_TRY(h, cudaMemcpyAsync(x, h->dx, sizeof(double) * h->n, cudaMemcpyDefault, s));
     if (y) CUDA_TRY(h, cudaMemcpyAsync(y, h->dy, sizeof(double) * h->m, cudaMemcpyDefault, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -766,13 +839,14 @@ lp_err lp_kernel_time(lp_handle *h, double *ms, int *launches) {
         set_err(h, "lp_kernel_time: nothing solved");
         return LP_ERR_STATE;
     }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
     if (h->prec == PREC_FP32) {
         if (ms) *ms = h->fp32_kernel_ms;
         if (launches) *launches = h->fp32_launches;
         return LP_OK;
     }
-    CUDA_TRY(h, cudaEventSynchronize(h->ev1));
+    CUDA_TRY(h, wait_stream(h));
     float t = 0.0f;
     CUDA_TRY(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
     if (ms) *ms = (double)t;
@@ -786,6 +860,7 @@ lp_err lp_get_trace(lp_handle *h, int *rows, int *cols, long long cap, long long
         set_err(h, "lp_get_trace: no LP loaded");
         return LP_ERR_STATE;
     }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     long long k = std::min(std::min(h->pdesc->iters, h->pdesc->trace_cap), cap);
@@ -813,6 +888,7 @@ lp_err lp_get_basis(lp_handle *h, int *basis) {
         set_err(h, "lp_get_basis: no LP loaded");
         return LP_ERR_STATE;
     }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
     CUDA_TRY(h, cudaMemcpyAsync(basis, h->dbasis, sizeof(int) * h->m, cudaMemcpyDefault, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -825,6 +901,7 @@ lp_err lp_get_tableau(lp_handle *h, double *T) {
         set_err(h, "lp_get_tableau: no LP loaded");
         return LP_ERR_STATE;
     }
+    DeviceRestore restore_;
     CUDA_TRY(h, cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -858,6 +935,7 @@ lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes) {
         set_err(h, "handle_bind_region: NULL handle");
         return LP_ERR_INVALID_ARG;
     }
+    DeviceRestore restore_;
     cudaSetDevice(h->device);
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     void **bufs[] = {(void **)&h->dA, (void **)&h->db, (void **)&h->dc, &h->dT, &h->dT2,

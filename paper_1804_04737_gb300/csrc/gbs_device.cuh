@@ -157,7 +157,7 @@ static __device__ bool grid_sync(unsigned *bar, int *err, int G, long long spin_
             } else {
                 const long long t0 = clock64();
                 while (ld_acquire(gen) == g0) {
-                    if (clock64() - t0 > spin_limit) {
+                    if (clock64() - t0 > spin_limit || *(volatile int *)err) {
                         atomicExch(err, 1);
                         ok = 0;
                         break;
@@ -205,6 +205,15 @@ struct Vec<float> {
     typedef float4 type;
     static constexpr int W = 4;
 };
+
+// The host's abort word (mapped host memory; nullptr: none).  The load is
+// issued where this is called and its value used later, so its latency (a
+// round trip to host memory) overlaps the work in between.
+__device__ __forceinline__ int abort_peek(const int *a) {
+    int v = 0;
+    if (a) asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ double2 ldv(const double2 *p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ldv(const float4 *p) { return __ldcg(p); }

@@ -65,6 +65,10 @@ struct LpDesc {
     // (4 x the column bytes rounded up to 16; the distributed ratio test
     // assembles each new column there)
     void *colx;
+    // single-LP solves: the host's abort word (mapped host memory), nonzero
+    // once the solve is past its wall-clock limit; nullptr elsewhere.  Each
+    // pivot kernel reads it once per pass and ends in ST_TIMEOUT.
+    const int *abort;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
@@ -308,5 +312,19 @@ size_t handle_region_used(const lp_handle *h);
 
 cudaError_t launch_to_fp64(const float *T, long long P, int M, int N, double *out,
                            cudaStream_t s);
+
+// Host side: restores the caller's current device when an entry point that
+// switched to its own device returns.
+struct DeviceRestore {
+    int dev = -1;
+    DeviceRestore() {
+        if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    }
+    ~DeviceRestore() {
+        if (dev >= 0) cudaSetDevice(dev);
+    }
+    DeviceRestore(const DeviceRestore &) = delete;
+    DeviceRestore &operator=(const DeviceRestore &) = delete;
+};
 
 }  // namespace gbs

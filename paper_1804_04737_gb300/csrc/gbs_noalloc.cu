@@ -20,6 +20,11 @@
 // array's device address with cudaGetSymbolAddress (in host code the array's
 // name is only a host-side stand-in) and caches it per device.  Make that first
 // call before any stream capture.
+//
+// The solve runs the one-pivot in-place kernel (pivot_kernel: selection, then
+// the update, one grid barrier per pivot), whose per-launch state is the
+// 2 x CTAs pricing partials and the barrier block; the pipelined kernels need
+// more record space and a second tableau, which this array does not hold.
 
 #include <cuda_runtime.h>
 #include <stdarg.h>
@@ -72,8 +77,8 @@ Layout layout_for(int m, int n, long long P, const PivotShape &sh) {
     const int M = m + 1;
     L.desc = take(sizeof(LpDesc));
     L.stats = take(sizeof(InputStats));
-    L.bar = take(128 * sizeof(unsigned));
-    L.part = take(2 * (size_t)sh.ctas * sizeof(Cand));
+    L.bar = take(kBarWords * sizeof(unsigned));
+    L.part = take(2 * (size_t)sh.ctas * sizeof(Cand));  // pivot_kernel's partials (sh.pipe == 0)
     L.basis = take((size_t)m * sizeof(int));
     L.A = take((size_t)m * n * sizeof(double));
     L.b = take((size_t)m * sizeof(double));
@@ -86,6 +91,19 @@ Layout layout_for(int m, int n, long long P, const PivotShape &sh) {
     L.total = off;
     return L;
 }
+
+// Waits for the caller's stream on every return once this call has queued
+// work there, so that the lock on the shared array is released only when no
+// copy or kernel of this call can still touch it (declared after the lock,
+// so it runs first).
+struct DrainStream {
+    cudaStream_t s;
+    bool armed = false;
+    explicit DrainStream(cudaStream_t st) : s(st) {}
+    ~DrainStream() {
+        if (armed) cudaStreamSynchronize(s);
+    }
+};
 
 }  // namespace
 
@@ -116,12 +134,15 @@ extern "C" lp_err lp_solve_noalloc(int m, int n, const double *A, const double *
     if (o.device < 0 || o.device >= kMaxDevices)
         return fail(LP_ERR_INVALID_ARG, "lp_solve_noalloc: device %d out of range", o.device);
 
+    DeviceRestore restore;
     NA_TRY(cudaSetDevice(o.device));
     int sms = 0;
     NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device));
     const int M = m + 1, N = n + m + 1;
     const long long P = pitch_for(N);
     const PivotShape sh = choose_shape(PREC_FP64, (int)sense, M, N, P, sms, o.threads, o.ctas);
+    if (sh.pipe != 0)  // the layout holds pivot_kernel's state only
+        return fail(LP_ERR_INVALID_ARG, "lp_solve_noalloc: internal: pipelined shape");
     const Layout L = layout_for(m, n, P, sh);
     if (L.total > kNoAllocBytes)
         return fail(LP_ERR_INVALID_ARG,
@@ -147,6 +168,8 @@ extern "C" lp_err lp_solve_noalloc(int m, int n, const double *A, const double *
     int *dbasis = reinterpret_cast<int *>(base + L.basis);
     void *dT = base + L.T;
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
+    DrainStream drain(s);
+    drain.armed = true;
 
     NA_TRY(cudaMemcpyAsync(dA, A, sizeof(double) * (size_t)m * n, cudaMemcpyDefault, s));
     NA_TRY(cudaMemcpyAsync(db, b, sizeof(double) * (size_t)m, cudaMemcpyDefault, s));
@@ -193,7 +216,7 @@ extern "C" lp_err lp_solve_noalloc(int m, int n, const double *A, const double *
     d.last_p = d.last_q = -1;
     NA_TRY(cudaMemcpyAsync(d_desc, &d, sizeof d, cudaMemcpyHostToDevice, s));
     // The barrier words and the timeout flag must start at zero.
-    NA_TRY(cudaMemsetAsync(d_bar, 0, 128 * sizeof(unsigned), s));
+    NA_TRY(cudaMemsetAsync(d_bar, 0, kBarWords * sizeof(unsigned), s));
     NA_TRY(launch_pivot(PREC_FP64, d_desc, sh, o.spin_timeout_cycles, o.max_iters, s));
     NA_TRY(launch_extract(PREC_FP64, d_desc, dT, dbasis, m, n, P, (int)sense, dx, dy, dobj, s));
     LpDesc out;

@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand selc[SW];
     __shared__ unsigned long long selq[SW];
     __shared__ unsigned sela[SW], selb[SW];
-    __shared__ int s_flag, s_p, s_q, s_status, s_jv, s_uok, s_rzero, s_sok;
+    __shared__ int s_flag, s_p, s_q, s_status, s_jv, s_uok, s_rzero, s_sok, s_abort;
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     // update threads; the last SW warps select (the launch reserves
@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     int lk = 0;  // pivots made in this launch (parity of records and pivot-column buffers)
     const int rowner = (N - 1) / W;  // the CTA whose strip holds the rhs column
     while (status == ST_RUNNING) {
+        const int ab = tid == 0 ? abort_peek(d->abort) : 0;  // used at the pass's end
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
         const T *col = scol[lk & 1];
@@ -554,10 +555,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
         }
         // the CTA's update of pivot k and its selection of pivot k+1 are done
+        if (tid == 0) {
+            s_abort = ab;  // past the host's deadline: stop, and end every CTA's waits
+            if (ab) atomicExch(d->err, 1);
+        }
         __syncthreads();
         ++iters;
         ++lk;
-        status = s_status;
+        status = s_abort ? ST_TIMEOUT : s_status;
         if (!s_uok) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
             p = s_p;
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand rbuf[2][32];
     __shared__ Cand selc[SW];
     __shared__ unsigned long long selq[SW];
-    __shared__ int s_flag, s_p, s_q, s_status, s_rzero, s_sok;
+    __shared__ int s_flag, s_p, s_q, s_status, s_rzero, s_sok, s_abort;
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     const int NU = B - kSelThreads;  // update threads; the last SW warps select
@@ -701,6 +706,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
     int lk = 0;  // pivots made in this launch (parity of records and pivot columns)
     while (status == ST_RUNNING) {
+        const int ab = tid == 0 ? abort_peek(d->abort) : 0;  // used at the pass's end
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
         const T *col = scol[lk & 1];
@@ -867,10 +873,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
         }
         // the CTA's update of pivot k and its selection of pivot k+1 are done
+        if (tid == 0) {
+            s_abort = ab;  // past the host's deadline: stop, and end every CTA's waits
+            if (ab) atomicExch(d->err, 1);
+        }
         __syncthreads();
         ++iters;
         ++lk;
-        status = s_status;
+        status = s_abort ? ST_TIMEOUT : s_status;
         if (status == ST_RUNNING) {
             p = s_p;
             q = s_q;
@@ -1144,7 +1154,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand selc[SW];
     __shared__ unsigned long long selq[SW];
     __shared__ unsigned sela[SW], selb[SW];
-    __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend;
+    __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend, s_abort;
     __shared__ volatile int s_zready;  // passes whose objective-row strip is in sz
     __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
     __shared__ unsigned long long s_tab[kMaxRecs * (kBlk + 1)];  // the records' values
@@ -1284,6 +1294,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __syncthreads();
     if (tid == 0 && status != ST_TIMEOUT) red_add_release(scnt, 1u);  // the first selection
     while (status == ST_RUNNING) {
+        const int ab = tid == 0 ? abort_peek(d->abort) : 0;  // used at the pass's end
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
         const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
@@ -1772,10 +1783,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
         }
         // the CTA's pass and its selection of the next pass are done
+        if (tid == 0) {
+            s_abort = ab;  // past the host's deadline: stop, and end every CTA's waits
+            if (ab) atomicExch(d->err, 1);
+        }
         __syncthreads();
         iters += np;
         ++lk;
-        status = s_status;
+        status = s_abort ? ST_TIMEOUT : s_status;
         if (!s_uok) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
             np = s_np;
@@ -1829,7 +1844,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ Cand rbuf[2][32];
     __shared__ Cand selc[SW];
     __shared__ unsigned long long selq[SW];
-    __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend;
+    __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend, s_abort;
     __shared__ volatile int s_zready;
     __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
     __shared__ unsigned long long s_tab[kMaxRecs * (kBlk + 1)];  // the records' values
@@ -1925,6 +1940,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     int np = 1, pend = ST_RUNNING;
     int pp[kBlk] = {p, -1}, qq[kBlk] = {q, -1};
+    int npv = 0, ppv[kBlk] = {-1, -1}, qqv[kBlk] = {-1, -1};  // the previous pass's pivots
     int cb = 0;
     unsigned lk = 0;
     if (tid == 0) s_zready = 0;
@@ -1932,6 +1948,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (tid == 0 && status != ST_TIMEOUT) red_add_release(scnt, 1u);  // the first selection
 
     while (status == ST_RUNNING) {
+        const int ab = tid == 0 ? abort_peek(d->abort) : 0;  // used at the pass's end
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
         const T *pc[kBlk] = {scol[cb], scol[(cb + 1) & 3]};
@@ -2048,28 +2065,40 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             // selection of the next pass's pivots a and b (dual simplex)
             int st = ST_RUNNING, nnp = 0, npend = ST_RUNNING;
             int pa = -1, qa = -1, pb = -1, qb = -1, rza = 0, rzb = 0;
-            auto bkey = [&](int i) -> int {  // the basic variable of row i after the pass
+            // The basic variable of row i after the pass.  CTA 0 writes the
+            // basis entries of a pass's pivots during that pass, and this
+            // selection runs before any wait of its own pass, so the entries
+            // of the previous pass's pivots may not be in memory yet: they
+            // are taken from ppv / qqv.  Older entries are: this CTA waited
+            // in the previous pass for CTA 0's records, which CTA 0 publishes
+            // only after finishing the pass before it.
+            auto bkey = [&](int i) -> int {
                 if (np > 1 && i == pp[1]) return qq[1];
                 if (i == pp[0]) return qq[0];
+                if (npv > 1 && i == ppv[1]) return qqv[1];
+                if (i == ppv[0]) return qqv[0];
                 return __ldcg(basis + i);
             };
             T *colA = nc[0];
             if (!select) {
                 st = pend;  // the previous pass's selection already ended the solve
             } else {
-                // the pass's pivot-row values at the rhs (the update warps' Step 4 values)
+                // the pass's pivot-row values at the rhs (the update warps' Step 4
+                // values), from this CTA's copy of the source's rhs column: the
+                // tableau's own rhs column belongs to one CTA, which may still be
+                // writing it in the previous pass (no grid barrier separates the
+                // passes)
                 T pvr[kBlk];
                 {
-                    const T r = lds(A + (long long)pp[0] * P + (N - 1)) / pc[0][pp[0]];
+                    const T r = srhs[pp[0]] / pc[0][pp[0]];
                     pvr[0] = r;
                     pvr[1] = (T)0;
                     if (np > 1) {
-                        const T t = (pp[1] == pp[0])
-                                        ? r
-                                        : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + (N - 1)));
+                        const T t = (pp[1] == pp[0]) ? r : tfma(-pc[0][pp[1]], r, srhs[pp[1]]);
                         pvr[1] = t / pc[1][pp[1]];
                     }
                 }
+                named_sync(2, kSelThreads);  // every thread has read srhs[pp[.]] before it changes
                 // ---- pivot a: the leaving row from the rhs of T2, every row
                 // (from the rhs of T0 kept in scratch, which becomes T2's) ----
                 Cand c = cand_empty();
@@ -2269,15 +2298,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
         }
         // the CTA's pass and its selection of the next pass are done
+        if (tid == 0) {
+            s_abort = ab;  // past the host's deadline: stop, and end every CTA's waits
+            if (ab) atomicExch(d->err, 1);
+        }
         __syncthreads();
         iters += np;
         ++lk;
-        status = s_status;
+        status = s_abort ? ST_TIMEOUT : s_status;
         if (!s_uok) status = ST_TIMEOUT;
         if (status == ST_RUNNING) {
+            npv = np;
             np = s_np;
             pend = s_pend;
             for (int k = 0; k < kBlk; ++k) {
+                ppv[k] = pp[k];
+                qqv[k] = qq[k];
                 pp[k] = s_p[k];
                 qq[k] = s_q[k];
             }

@@ -185,6 +185,7 @@ __device__ __forceinline__ void solve_lp(LpDesc *__restrict__ d, int G, int g, i
     unsigned rd_target = 0;
     int lk = 0;  // pivots made in this launch: selects the partials' parity buffer
     while (status == ST_RUNNING) {
+        const int ab = tid == 0 ? abort_peek(d->abort) : 0;  // used at the pivot's barrier
         // ------------- selection, computed redundantly by every CTA -------------
         const int bland = deg >= bland_after;
         const Cand sel = load_partials_min(d->part_sel + (lk & 1) * G, G, rbuf[0]);
@@ -354,6 +355,8 @@ __device__ __forceinline__ void solve_lp(LpDesc *__restrict__ d, int G, int g, i
         }
         watch = block_min_c(watch, rbuf[2]);
         if (tid == 0) d->part_sel[((lk + 1) & 1) * G + g] = watch;
+        // past the host's deadline: the flag ends every CTA's barrier below
+        if (ab) atomicExch(d->err, 1);
         ++iters;
         ++lk;
         if (!grid_sync(d->bar, d->err, G, spin_limit, &s_flag)) {

@@ -801,6 +801,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->max_slots = max_slots;
     sv->fp32 = o.precision == LP_FP32_REINV;
     sv->solo_elems = o.solo_elems < 0 ? -1 : o.solo_elems > 0 ? o.solo_elems : 1ll << 24;
+    DeviceRestore restore_;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
     const int M = lp_server::kMaxDim + 1, N = 2 * lp_server::kMaxDim + 1;
@@ -961,6 +962,7 @@ void lp_server_destroy(lp_server *sv) {
         sv->cv.notify_all();
         sv->engine.join();
     }
+    DeviceRestore restore_;
     cudaSetDevice(sv->device);
     if (sv->h_ring) *(volatile int *)&sv->h_ring->shutdown = 1;
     if (sv->kstream) cudaStreamSynchronize(sv->kstream);  // the kernel exits once idle

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1804_04737_gb300 import capi
@@ -62,3 +63,14 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(capi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         capi.load_library(str(tmp_path / "nope.so"))
+
+
+def test_noalloc_binding_checks_shapes():
+    """The binding rejects inconsistent shapes before calling the library (a
+    short b or c would be read past its end, a short x or y written past it)."""
+    A = np.ones((3, 4))
+    for kw in ({"b": np.ones(2)}, {"c": np.ones(5)}, {"x": np.ones(3)}, {"y": np.ones(4)}):
+        args = {"b": np.ones(3), "c": np.ones(4), **kw}
+        x, y = args.pop("x", None), args.pop("y", None)
+        with pytest.raises(ValueError):
+            capi.lp_solve_noalloc(A, args["b"], args["c"], x=x, y=y)
