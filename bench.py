@@ -1,20 +1,30 @@
 #!/usr/bin/env python3
 """Throughput of the dense tableau simplex on GB300: pivots/s and tableau GB/s.
 
-Workload (one step): four seeded synthetic dense LPs shaped like the paper's
-Sec. 4 problems, all FP64 and solved to optimality --
-  2048 x 2048 primal form (max c'x, Ax <= b),
-  2048 x 2048 dual form (min b'y, A'y >= c, by the dual simplex),
-  512 x 4096 and 4096 x 512 primal form (more variables than constraints and
-  the reverse).
-A entries uniform integers in [1, 1000], b in [1000, 100000], c in [1, 100].
+Default workload (one step): the 8192 x 8192 dense LP (tableau 8193 x 16385,
+1.07 GB in FP64), primal form max c'x s.t. Ax <= b, x >= 0, solved to
+optimality in FP64 (Sec. 2 Steps 1-5, Dantzig pricing): lp_load from device
+buffers (the tableau is built inside the timed region) and lp_solve.  A
+entries uniform integers in [1, 1000], b in [1000, 100000], c in [1, 100],
+seed 0.  Beside it, on the same LP: the FP32 tableau with FP64 reinversion
+every k in {50, 200} pivots, with its objective error against the FP64
+oracle.
 
 `value` is pivots per second over the whole job, device-timed with CUDA
-events on the library's stream, inputs resident in HBM before the timed
-region (lp_load copies them device to device and builds the tableau inside
-it).  L2 is flushed (256 MiB write) between steps, outside the step's events.
-`e2e` is the same metric through the C ABI from pinned host buffers:
-lp_load from host memory, lp_solve, lp_result into host memory, wall clock.
+events on the library's stream, inputs resident in HBM.  The tableau (1.07 GB,
+two buffers) is larger than L2, so nothing survives in L2 from one step to
+the next.  `e2e` is the same metric through the C ABI with host buffers:
+lp_load from pinned host memory, lp_solve, lp_result into pinned host memory,
+wall clock.  `roofline` is that of the pivot kernel (one launch per solve):
+the FP64 FMA rate (one fma per tableau element and pivot) and the DRAM bytes
+it moves (from an ncu record of the same launch), the larger fraction
+leading; pivot-equivalent GB/s (2 x tableau bytes per pivot) is reported
+beside them, not as a bound, because two pivots share one pass over the
+tableau.
+
+Other workloads (--workload): lp2048set (2048^2 primal and dual form,
+512 x 4096, 4096 x 512), paperset (the same shapes from the paper's random
+family), batch1024, serve.
 """
 import argparse
 import json
@@ -27,23 +37,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD_NAME = ("dense LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + 4096x512, "
-                 "FP64, Dantzig pricing")
-# the same shapes from the paper's own random family (Sec. 4): density 0.9,
-# real-valued data, about 25 times the pivots of the integer family
-PAPER_WORKLOAD_NAME = ("paper-family LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + "
-                       "4096x512, density 0.9, FP64, Dantzig pricing")
-FP64_DFMA_PER_CLK_SM = 2          # GB300 FP64 rate: 1.25 TFLOP/s nominal = 2 DFMA/clk/SM
-SMS, SM_MAX_MHZ = 152, 2070.0
-HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal
-ALU_PEAK_TFLOPS = 2 * FP64_DFMA_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
 MAX_LE, MIN_GE = 0, 1
+HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal
+FP64_DFMA_PER_CLK_SM = 2          # GB300 FP64: 1.25 TFLOP/s nominal = 2 DFMA per clock per SM
 KERNEL_SRC = os.path.join(ROOT, "paper_1804_04737_gb300", "csrc", "gbs_pipe.cu")
 
+WORKLOADS = {
+    "lp8192": ("dense LP 8192x8192 (tableau 8193x16385, 1.07 GB FP64), primal form, FP64, Dantzig "
+               "pricing; FP32 tableau + FP64 reinversion every 50 and 200 pivots beside it"),
+    "lp2048set": ("dense LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + 4096x512, "
+                  "FP64, Dantzig pricing"),
+    # the same shapes from the paper's own random family (Sec. 4): density 0.9,
+    # real-valued data, about 25 times the pivots of the integer family
+    "paperset": ("paper-family LP set: 2048x2048 primal + 2048x2048 dual form + 512x4096 + "
+                 "4096x512, density 0.9, FP64, Dantzig pricing"),
+}
+# what the reference arm times per step: the oracle's first REF_PIVOTS pivots
+# of each LP (8192^2: a full solve is several seconds of host time)
+REF_PIVOTS = {"lp8192": 20, "lp2048set": None, "paperset": 200}
 
-def workload(seed, family="dense"):
+
+def workload(name, seed=0):
     from paper_1804_04737_gb300 import lpgen
-    gen = lpgen.dense_lp if family == "dense" else lpgen.paper_lp
+    if name == "lp8192":
+        return [("8192x8192 primal", *lpgen.dense_lp(8192, 8192, seed), MAX_LE)]
+    gen = lpgen.dense_lp if name == "lp2048set" else lpgen.paper_lp
     out = []
     A, b, c = gen(2048, 2048, seed)
     out.append(("2048x2048 primal", A, b, c, MAX_LE))
@@ -53,10 +71,27 @@ def workload(seed, family="dense"):
     return out
 
 
+def bench_config(name, world):
+    """The `config` of both arms' lines (identical, so the driver can pair them)."""
+    cfg = {"workload": WORKLOADS[name], "seed": 0,
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    if name == "lp8192":
+        cfg.update({"m": 8192, "n": 8192, "l2": "inputs larger than L2 (1.07 GB tableau, "
+                                                 "two buffers)"})
+    else:
+        cfg["l2"] = "flushed between steps (256 MiB write), outside the step events"
+    return cfg
+
+
 def tableau_bytes(m, n, w=8):
     """Algorithmic bytes of one pivot: the rank-1 update reads and writes the
     whole (m+1) x (n+m+1) tableau once (Sec. 2 Step 5)."""
     return 2 * (m + 1) * (n + m + 1) * w
+
+
+def tableau_flops(m, n):
+    """One fma (2 flops) per tableau element and pivot (Sec. 2 Step 5)."""
+    return 2 * (m + 1) * (n + m + 1)
 
 
 def peaks():
@@ -68,17 +103,40 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# The kernel each LP of the set runs on (default options): primal LPs below
-# 2^19 tableau elements on the pipelined primal kernel in place, larger ones
-# on the two-pivots-per-pass kernel (double-buffered), the dual form on the
+def device_fp64_peak(index):
+    """(TFLOP/s, how): 2 FP64 FMA per clock per SM x the device's SM count x its
+    maximum SM clock (nvidia-smi), the derived FP64 FMA peak."""
+    import torch
+    sms = torch.cuda.get_device_properties(index).multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=30).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except Exception:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f)["sm_max_mhz"])
+        except Exception:
+            mhz = 2070.0
+    tf = 2 * FP64_DFMA_PER_CLK_SM * sms * mhz * 1e6 / 1e12
+    return tf, "derived: %d FP64 FMA/clk/SM x %d SMs x %.0f MHz" % (FP64_DFMA_PER_CLK_SM, sms, mhz)
+
+
+# The kernel each LP runs on (default options): primal LPs below 2^19 tableau
+# elements on the pipelined primal kernel in place, larger ones on the
+# two-pivots-per-pass kernel (double-buffered), the dual form on the
 # two-pivots-per-pass dual simplex kernel (double-buffered).
 INPLACE_KERNEL = "pivot_pipe_kernel<double> (in place)"
 BLOCK_KERNEL = "pivot_block_kernel<double> (two pivots per pass)"
 DUAL_KERNEL = "pivot_block_dual_kernel<double> (dual simplex, two pivots per pass)"
-# (the in-place kernel runs no LP of the default set, so it has no record)
+# DRAM records (ncu) per kernel and workload; the in-place kernel runs no LP of
+# these sets, so it has none
 TRAFFIC_FILES = {
-    BLOCK_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_kernel_fp64_traffic.txt"),
-    DUAL_KERNEL: os.path.join(ROOT, "profiles", "pivot_block_dual_kernel_fp64_traffic.txt"),
+    ("lp8192", BLOCK_KERNEL): "pivot_block_kernel_fp64_8192_traffic.txt",
+    ("lp2048set", BLOCK_KERNEL): "pivot_block_kernel_fp64_traffic.txt",
+    ("lp2048set", DUAL_KERNEL): "pivot_block_dual_kernel_fp64_traffic.txt",
 }
 
 
@@ -89,14 +147,14 @@ def kernel_of(m, n, sense):
     return INPLACE_KERNEL if (m + 1) * pitch < 2 ** 19 else BLOCK_KERNEL
 
 
-def kernel_traffic(name):
-    """Mean DRAM bytes per launch of one kernel in one bench step, from the
-    committed ncu summary, or None when there is none or the kernel source
-    changed since that capture."""
+def kernel_traffic(wname, kernel):
+    """Mean DRAM bytes (read + write) per launch of one kernel in one step of
+    the workload, from the committed ncu record, or None when there is none
+    or the kernel source changed since that capture."""
     import hashlib
     try:
         rec = {}
-        with open(TRAFFIC_FILES[name]) as f:
+        with open(os.path.join(ROOT, "profiles", TRAFFIC_FILES[(wname, kernel)])) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
@@ -182,93 +240,6 @@ def reduce_over_ranks(dist, maxes, sums, device="cpu"):
     dist.all_reduce(a, op=dist.ReduceOp.MAX)
     dist.all_reduce(b, op=dist.ReduceOp.SUM)
     return a.tolist(), b.tolist()
-
-
-def cpu_oracle_run(lps, threads, cap=None):
-    """Pivots and seconds of the oracle on the whole workload, each LP stopped
-    after `cap` pivots when given."""
-    import oracle
-    oracle.set_threads(threads)
-    pivots = 0
-    t0 = time.perf_counter()
-    for _, A, b, c, sense in lps:
-        r = oracle.solve(A, b, c, sense=sense, max_iters=cap if cap else 10 ** 12)
-        assert r.status == (oracle.ITER_LIMIT if cap and r.iters == cap else oracle.OPTIMAL)
-        pivots += r.iters
-    return pivots, time.perf_counter() - t0
-
-
-def run_reference(args, rank, world):
-    """The FP64 oracle (the paper's method as plain C, OpenMP over the rows of
-    Step 5) on the host cores, same workload, metric and units."""
-    if rank != 0:
-        return
-    cores = len(os.sched_getaffinity(0))
-    lps = workload(0)
-    for _ in range(args.warmup):
-        cpu_oracle_run(lps, cores)
-    piv = 0
-    sec = 0.0
-    for _ in range(args.steps):
-        p, t = cpu_oracle_run(lps, cores)
-        piv += p
-        sec += t
-    v = piv / sec
-    line = {"impl": "reference", "metric": "pivots/s", "value": v, "unit": "pivots/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "seed": 0},
-            "cpu_baseline": {"value": v, "unit": "pivots/s", "cores": cores, "kind": "oracle",
-                             "sample": "the whole workload (4 LPs) per step"},
-            "e2e": {"value": v, "unit": "pivots/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def run_lp8192(args, capi, torch):
-    """8192 x 8192 dense LP: FP64 against the FP32 tableau with FP64
-    reinversion every k in {50, 200} pivots.  The FP64 path is bit-identical
-    to the FP64 oracle at this size (tests/test_gpu_parity.py), so FP32
-    objective errors are measured against it."""
-    from paper_1804_04737_gb300 import lpgen
-    A, b, c = lpgen.dense_lp(8192, 8192, 0)
-    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
-    torch.cuda.synchronize()
-    out = []
-    ref = None
-    for prec, k in ((capi.LP_FP64, 0), (capi.LP_FP32_REINV, 50), (capi.LP_FP32_REINV, 200)):
-        h = capi.lp_create(capi.lp_options_default(precision=prec, reinv_k=max(k, 1)))
-        best = None
-        for rep in range(1 + max(1, args.steps // 5)):
-            t0 = time.perf_counter()
-            capi.lp_load(h, dA, db, dc)
-            capi.lp_solve(h)
-            obj, st, it = capi.lp_result(h)
-            wall = time.perf_counter() - t0
-            kms, launches = capi.lp_kernel_time(h)
-            if rep and (best is None or wall < best[0]):
-                best = (wall, kms, launches, obj, st, it)
-        capi.lp_destroy(h)
-        wall, kms, launches, obj, st, it = best
-        w = 8 if prec == capi.LP_FP64 else 4
-        if ref is None:
-            ref = obj
-        out.append({"mode": "fp64" if prec == capi.LP_FP64 else "fp32+reinv k=%d" % k,
-                    "status": capi.STATUS_NAMES[st], "pivots": it,
-                    "solve_ms": round(1e3 * wall, 2), "pivot_kernel_ms": round(kms, 2),
-                    "pivot_kernel_launches": launches,
-                    "pivots_per_s": round(it / wall, 1),
-                    "tableau_gbs_kernel": round(it * tableau_bytes(8192, 8192, w) / kms / 1e6, 1),
-                    # two pivots per pass over the tableau at this size: the
-                    # tableau traffic is half the algorithmic bytes, and FP64 is
-                    # bound by the FMA rate (one FMA per element and pivot)
-                    "tflops_kernel": round(it * 2 * 8193 * 16385 / kms / 1e9, 4),
-                    "fp64_alu_frac": (round(it * 2 * 8193 * 16385 / kms / 1e9 / ALU_PEAK_TFLOPS, 4)
-                                      if prec == capi.LP_FP64 else None),
-                    "obj": obj, "obj_rel_err_vs_fp64": abs(obj - ref) / abs(ref)})
-    print(json.dumps({"workload": "dense LP 8192x8192, FP64 vs FP32 tableau + FP64 reinversion",
-                      "results": out, "hbm_peak_gbs": peaks()[0]}), flush=True)
 
 
 def run_batch(args, capi, torch):
@@ -400,51 +371,151 @@ def run_serve(args, capi, torch):
                                          "max_obj_rel_err_vs_fp64_server": err}}), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="lp2048set",
-                    choices=["lp2048set", "paperset", "lp8192", "batch1024", "serve"],
-                    help="lp2048set is the headline line; the others report their own figures")
-    args = ap.parse_args()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
+def cpu_oracle_run(lps, threads, cap=None):
+    """Pivots and seconds of the oracle's pivoting on the workload (the Step 1
+    build excluded), each LP stopped after `cap` pivots when given."""
+    import oracle
+    oracle.set_threads(threads)
+    pivots, sec = 0, 0.0
+    for _, A, b, c, sense in lps:
+        t = oracle.OracleTableau(A, b, c, sense)
+        t0 = time.perf_counter()
+        st = t.run(cap if cap else 10 ** 12)
+        sec += time.perf_counter() - t0
+        assert st == (oracle.ITER_LIMIT if cap and t.iters.value == cap else oracle.OPTIMAL)
+        pivots += t.iters.value
+    return pivots, sec
 
+
+def run_reference(args, rank, world):
+    """The FP64 oracle (the paper's method as plain C, OpenMP over the rows of
+    Step 5) on the host cores: same workload, config, metric and units; each
+    step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm covers the single-LP workloads only"}), flush=True)
+        return
+    cores = len(os.sched_getaffinity(0))
+    lps = workload(args.workload, 0)
+    cap = REF_PIVOTS[args.workload]
+    for _ in range(args.warmup):
+        cpu_oracle_run(lps, cores, cap)
+    piv, sec = 0, 0.0
+    for _ in range(args.steps):
+        p, t = cpu_oracle_run(lps, cores, cap)
+        piv += p
+        sec += t
+    v = piv / sec
+    what = ("the first %d pivots of each LP" % cap if cap else "the whole workload") + \
+        " per step, Step 1 build excluded"
+    line = {"impl": "reference", "metric": "pivots/s", "value": v, "unit": "pivots/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": bench_config(args.workload, world),
+            "cpu_baseline": {"value": v, "unit": "pivots/s", "cores": cores, "kind": "oracle",
+                             "sample": what},
+            "e2e": {"value": v, "unit": "pivots/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def lp8192_extras(args, capi, torch, lps, dev_in, g_obj, g_iters, local):
+    """Beside the FP64 line of the 8192^2 LP: the oracle's first 200 pivots on
+    all host cores and its first 10 on one (cpu_baseline), the rest of its
+    solve (parity of the FP64 pivots and objective), and the FP32 tableau with
+    FP64 reinversion every 50 and 200 pivots, with objective errors against
+    the oracle."""
     import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1804_04737_gb300 import capi
+    import oracle
+    _, A, b, c, sense = lps[0]
+    _, dA, db, dc, _ = dev_in[0]
+    out = {}
+    ores = None
+    if not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        oracle.set_threads(cores)
+        t = oracle.OracleTableau(A, b, c, sense)
+        t0 = time.perf_counter()
+        t.run(200)
+        t200, p200 = time.perf_counter() - t0, t.iters.value
+        t.run()  # on to the optimum, untimed
+        ores = t.result()
+        del t
+        oracle.set_threads(1)
+        t1 = oracle.OracleTableau(A, b, c, sense)
+        t0 = time.perf_counter()
+        t1.run(10)
+        ts, ps = time.perf_counter() - t0, t1.iters.value
+        del t1
+        oracle.set_threads(cores)
+        out["cpu_baseline"] = {
+            "value": p200 / t200, "unit": "pivots/s", "cores": cores, "kind": "oracle",
+            "sample": "the first %d pivots of the 8192x8192 LP, Step 1 build excluded, %.1f s"
+                      % (p200, t200),
+            "single_thread": {"value": ps / ts, "unit": "pivots/s",
+                              "sample": "the first %d pivots, %.1f s" % (ps, ts)}}
+        out["parity"] = {"oracle_status": oracle.STATUS_NAMES[ores.status],
+                         "oracle_pivots": ores.iters,
+                         "fp64_pivots_equal": g_iters == ores.iters,
+                         "fp64_obj_bitwise_equal": bool(np.float64(g_obj).view(np.uint64) ==
+                                                        np.float64(ores.obj).view(np.uint64))}
+    fp32 = []
+    for k in (50, 200):
+        h = capi.lp_create(capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=k,
+                                                   device=local))
+        runs = []
+        try:
+            for rep in range(1 + max(2, args.steps // 5)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                capi.lp_load(h, dA, db, dc, sense)
+                capi.lp_solve(h)
+                obj, st, it = capi.lp_result(h)
+                wall = time.perf_counter() - t0
+                kms, launches = capi.lp_kernel_time(h)
+                if rep:
+                    runs.append((wall, kms, launches, obj, st, it))
+        finally:
+            capi.lp_destroy(h)
+        runs.sort()
+        wall, kms, launches, obj, st, it = runs[len(runs) // 2]
+        fp32.append({"reinv_k": k, "status": capi.STATUS_NAMES[st], "pivots": it,
+                     "pivots_per_s": round(it / wall, 1), "solve_ms": round(1e3 * wall, 2),
+                     "pivot_kernel_ms": round(kms, 2), "pivot_kernel_launches": launches,
+                     "pivot_equivalent_gbs_kernel":
+                         round(it * tableau_bytes(8192, 8192, 4) / (kms * 1e-3) / 1e9, 1),
+                     "obj": obj,
+                     "obj_rel_err_vs_oracle": (abs(obj - ores.obj) / abs(ores.obj)
+                                               if ores is not None else None),
+                     "timing": "wall clock of lp_load + lp_solve + lp_result, inputs in HBM, "
+                               "median of %d" % len(runs)})
+    out["fp32_reinv"] = fp32
+    return out
 
-    torch.cuda.set_device(local)
-    family = "paper" if args.workload == "paperset" else "dense"
-    wname = PAPER_WORKLOAD_NAME if family == "paper" else WORKLOAD_NAME
-    if args.workload not in ("lp2048set", "paperset"):
-        return {"lp8192": run_lp8192, "batch1024": run_batch,
-                "serve": run_serve}[args.workload](args, capi, torch)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+def run_lpset(args, capi, torch, rank, world, local, dist):
+    """Single-LP workloads: each step loads and solves every LP of the set
+    once on the device, device-timed; then the same through host buffers."""
+    import numpy as np
+    wname = args.workload
     stream = torch.cuda.Stream()
-    lps = workload(rank, family)
+    lps = workload(wname, 0)
     dev_in = [(name, *(torch.from_numpy(v).cuda() for v in (A, b, c)), sense)
               for name, A, b, c, sense in lps]
     handles = [capi.lp_create(capi.lp_options_default(cuda_stream=stream, device=local))
                for _ in lps]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    # the 8192^2 tableau is larger than L2; the smaller sets flush it
+    flush = None if wname == "lp8192" else torch.empty(64 * 1024 * 1024, dtype=torch.float32,
+                                                       device="cuda")
     torch.cuda.synchronize()
 
     def device_step():
         with torch.cuda.stream(stream):
-            flush.fill_(1.0)
+            if flush is not None:
+                flush.fill_(1.0)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -468,22 +539,25 @@ def main():
     if dist:
         dist.barrier()
     step_ms, pivots, kernel_ms, alg_bytes = [], 0, 0.0, 0.0
-    per_kernel = {}  # name -> [launches, ms, algorithmic bytes, pivots]
+    per_kernel = {}  # name -> [launches, ms, algorithmic bytes, pivots, flops]
+    last = None
     with Clocks(local) as clk:
         for _ in range(args.steps):
             ms, stats = device_step()
             step_ms.append(ms)
+            last = stats
             for (it, kms, _), (_, A, _b, _c, sense) in zip(stats, lps):
+                m, n = A.shape
                 pivots += it
                 kernel_ms += kms
-                by = it * tableau_bytes(A.shape[0], A.shape[1])
+                by = it * tableau_bytes(m, n)
                 alg_bytes += by
-                rec = per_kernel.setdefault(kernel_of(A.shape[0], A.shape[1], sense),
-                                            [0, 0.0, 0.0, 0])
+                rec = per_kernel.setdefault(kernel_of(m, n, sense), [0, 0.0, 0.0, 0, 0.0])
                 rec[0] += 1
                 rec[1] += kms
                 rec[2] += by
                 rec[3] += it
+                rec[4] += it * tableau_flops(m, n)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -523,69 +597,66 @@ def main():
     for h in handles:
         capi.lp_destroy(h)
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
         return
 
     hbm_peak, peak_kind = peaks()
-    gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    fp64_peak, fp64_how = device_fp64_peak(local)
 
     def roofline_of(name):
-        """HBM and FP64-ALU rooflines of one kernel: algorithmic bytes (or
-        flops) per launch over its mean CUDA-event launch duration."""
-        launches, ms, by, piv = per_kernel[name]
+        """The pivot kernel's two real rooflines, per launch over its mean
+        CUDA-event duration: FP64 FMA (one fma per element and pivot) and the
+        DRAM bytes it moves (ncu record); the larger fraction leads.
+        Pivot-equivalent GB/s (2 x tableau bytes per pivot) is reported too;
+        it is not a bound, since two pivots share one pass over the tableau."""
+        launches, ms, by, piv, flops = per_kernel[name]
         sec = ms * 1e-3
-        flops = by / 16 * 2  # one FMA (2 flops) per 16 bytes of FP64 read + write
-        hbm = {"bound": "hbm", "achieved": round(by / sec / 1e9, 1), "peak": hbm_peak,
-               "unit": "GB/s", "frac": round(by / sec / 1e9 / hbm_peak, 4),
-               "peak_kind": peak_kind,
-               "frac_of_nominal": round(by / sec / 1e9 / HBM_NOMINAL_GBS, 4)}
-        alu = {"bound": "alu", "achieved": round(flops / sec / 1e12, 4),
-               "peak": round(ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-               "frac": round(flops / sec / 1e12 / ALU_PEAK_TFLOPS, 4),
-               "peak_kind": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
-        r = dict(max((hbm, alu), key=lambda x: x["frac"]))
-        r["secondary"] = alu if r["bound"] == "hbm" else hbm
-        r["kernel"] = name
-        r["launches_per_step"] = launches // args.steps
-        r["mean_launch_ms"] = round(ms / launches, 4)
-        r["algorithmic_bytes_per_launch"] = round(by / launches)
-        r["share_of_pivot_kernel_time"] = round(ms / kernel_ms, 4)
-        return r
+        traffic = kernel_traffic(wname, name)
+        fma = {"achieved": round(flops / sec / 1e12, 4), "peak": round(fp64_peak, 4),
+               "unit": "TFLOP/s", "frac": round(flops / sec / 1e12 / fp64_peak, 4),
+               "peak_kind": fp64_how}
+        hbm = None
+        if traffic:
+            gbs = traffic * launches / sec / 1e9
+            hbm = {"achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                   "frac": round(gbs / hbm_peak, 4), "peak_kind": peak_kind,
+                   "frac_of_nominal": round(gbs / HBM_NOMINAL_GBS, 4)}
+        lead = hbm if hbm is not None and hbm["frac"] > fma["frac"] else fma
+        return {"bound": "hbm" if lead is hbm else "alu", "achieved": lead["achieved"],
+                "peak": lead["peak"], "unit": lead["unit"], "frac": lead["frac"],
+                "traffic": traffic, "kernel": name,
+                "launches_per_step": launches // args.steps,
+                "mean_launch_ms": round(ms / launches, 4),
+                "algorithmic_bytes_per_launch": round(by / launches),
+                "flops_per_launch": round(flops / launches),
+                "fp64_fma": fma, "hbm_moved": hbm,
+                "pivot_equivalent_gbs": round(by / sec / 1e9, 1),
+                "share_of_pivot_kernel_time": round(ms / kernel_ms, 4)}
 
     dominant = max(per_kernel, key=lambda k: per_kernel[k][1])
     roof = roofline_of(dominant)
-    # (the DRAM records are of the integer family's step)
-    roof["traffic"] = kernel_traffic(dominant) if family == "dense" else None
-    others = []
-    for k in per_kernel:
-        if k != dominant:
-            r = roofline_of(k)
-            r["traffic"] = kernel_traffic(k) if family == "dense" else None
-            others.append(r)
-    roof["others"] = others
+    roof["others"] = [roofline_of(k) for k in per_kernel if k != dominant]
     line = {
         "metric": "pivots/s", "value": all_pivots / (total_ms * 1e-3), "unit": "pivots/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wname, "seed": "rank", "lps": [n for n, *_ in lps],
-                   "pivots_per_step": pivots // args.steps,
-                   "l2": "flushed between steps (256 MiB write), outside the step events",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "tableau_gbs": round(gbs, 1),
+        "config": bench_config(wname, world),
+        "lps": [n for n, *_ in lps], "pivots_per_step": pivots // args.steps,
+        "tableau_gbs": round(alg_bytes / (kernel_ms * 1e-3) / 1e9, 1),
         "e2e": {"value": e2e_val, "unit": "pivots/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "gpu_launches": 5 * len(lps) * args.steps,
         "clocks": clk.summary(),
     }
-    if world == 1 and not args.no_cpu_baseline:
-        # the whole workload, repeated until about 10 s of oracle time
+    if wname == "lp8192":
+        line.update(lp8192_extras(args, capi, torch, lps, dev_in, last[0][2], last[0][0], local))
+    elif world == 1 and not args.no_cpu_baseline:
+        # the whole workload, repeated until about 10 s of oracle time; the
+        # paper family's LPs take thousands of pivots, so there the sample
+        # stops each LP after a fixed number of them
         cores = len(os.sched_getaffinity(0))
-        # the paper family's LPs take thousands of pivots: the sample stops
-        # each LP after a fixed number of them
-        cap, cap1 = (200, 20) if family == "paper" else (None, None)
+        cap, cap1 = (200, 20) if wname == "paperset" else (None, None)
         p, t, reps = 0, 0.0, 0
         while t < 10.0 and reps < 1000:
             dp, dt = cpu_oracle_run(lps, cores, cap)
@@ -595,12 +666,47 @@ def main():
         what1 = "the whole workload" if cap1 is None else "the first %d pivots of each LP" % cap1
         line["cpu_baseline"] = {"value": p / t, "unit": "pivots/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": "%s %d times, %.1f s" % (what, reps, t),
+                                "sample": "%s %d times, Step 1 build excluded, %.1f s"
+                                          % (what, reps, t),
                                 "single_thread": {"value": p1 / t1, "unit": "pivots/s",
                                                   "sample": "%s once, %.1f s" % (what1, t1)}}
     print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=15)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="lp8192",
+                    choices=["lp8192", "lp2048set", "paperset", "batch1024", "serve"],
+                    help="lp8192 is the headline line; the others report their own figures")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_04737_gb300 import capi
+
+    torch.cuda.set_device(local)
+    if args.workload in ("batch1024", "serve"):
+        return {"batch1024": run_batch, "serve": run_serve}[args.workload](args, capi, torch)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        run_lpset(args, capi, torch, rank, world, local, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":
