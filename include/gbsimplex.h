@@ -54,8 +54,11 @@
  * primal and dual feasible within the FP64 tolerances; otherwise pivoting
  * continues (dual simplex from a dual-feasible basis, primal simplex from a
  * primal-feasible one), and LP_NUMERICAL ends a run that does not converge.
- * The body B^-1 A of the tableau stays FP32; its pivot sequence need not
- * equal the FP64 one.
+ * With lp_options.reinv_body (the default) each reinversion also recomputes
+ * the tableau's constraint rows B^-1 [A I] in emulated FP64 and rounds them
+ * into the FP32 tableau, so pivoting resumes from the correctly rounded
+ * tableau of the current basis.  The FP32 pivot sequence need not equal the
+ * FP64 one.
  *
  * Conventions
  *   - Every call returns an lp_err; nothing throws across the ABI.  The
@@ -164,6 +167,16 @@ typedef struct {
                                 kernel stops within a pass and the solve ends in
                                 LP_TIMEOUT.  Ignored by batches, servers and
                                 lp_solve_noalloc.                               */
+    int reinv_body;          /* FP32 mode, single LPs through lp_solve (not the
+                                servers, whose HBM budget has no room for the
+                                products' workspace): 1 (default) = every reinversion
+                                also recomputes the tableau's constraint rows
+                                B^-1 [A I] from the original FP64 data, with
+                                emulated-FP64 products on the tensor cores (see
+                                lp_dgemm_emulated), so the rounding error of the
+                                FP32 body does not build up; 0 = only the rhs,
+                                the duals and the objective row.  Batches do
+                                the latter.                                     */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
@@ -330,6 +343,30 @@ lp_err lp_batch_stats(double *kernel_ms, long long *pivots, int *ctas, int *thre
 lp_err lp_solve_noalloc(int m, int n, const double *A, const double *b, const double *c,
                         lp_sense sense, const lp_options *opt, double *x, double *y,
                         double *obj, lp_status *status, long long *iters);
+
+/* Reinversions of the last FP32 solve, their device time in milliseconds,
+ * and the part of it spent recomputing the tableau body (0 with reinv_body
+ * off).  Any output may be NULL. */
+lp_err lp_fp32_stats(lp_handle *h, int *reinversions, double *reinv_ms, double *body_ms);
+
+/* Emulated-FP64 matrix product on the tensor cores (the paper has no
+ * counterpart; it is the engine of the FP32 mode's body refresh):
+ * C = A B for FP64 A (M x K, row-major, row pitch lda >= K), B (K x N,
+ * row-major, ldb >= N) and C (M x N, row-major, ldc >= N), all device memory.
+ * Each row of A and each column of B is scaled by a power of two and split
+ * into seven signed 7-bit digits held exactly in bf16; the 28 digit products
+ * that carry the leading 49 bits are summed exactly in FP32 on the tensor
+ * cores (tcgen05, operands staged by TMA) and combined into FP64.  The error
+ * of C_ij is below about K 2^-48 max_k|A_ik| max_k|B_kj| (FP64 itself: K
+ * 2^-53 sum_k |A_ik B_kj|); integer data whose products and sums are exact in
+ * FP64 and that need at most 14 bits per row or column of scaled magnitude
+ * give exact results.  opt: NULL for the defaults; uses opt->device,
+ * opt->cuda_stream and opt->spin_timeout_cycles.  Allocates and frees its own
+ * workspace (about 14 (M + N) K bytes); blocking.  Errors:
+ * LP_ERR_INVALID_ARG (sizes, NULL or host pointers), LP_ERR_CUDA (a CUDA call
+ * failed or a device wait ran out); the message is lp_last_error(NULL). */
+lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long long lda, const double *B,
+                         long long ldb, double *C, long long ldc, const lp_options *opt);
 
 /* Free the handle and its device memory.  NULL is allowed. */
 void lp_destroy(lp_handle *h);

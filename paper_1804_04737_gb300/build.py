@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgbsimplex.so")
 SOURCES = ["gbs_pivot.cu", "gbs_pipe.cu", "gbs_reinv.cu", "gbs_batch.cu", "gbs_serve.cu",
-           "gbs_capi.cu", "gbs_noalloc.cu"]
+           "gbs_capi.cu", "gbs_noalloc.cu", "gbs_ozaki.cu"]
 HEADERS = ["gbs_internal.h", "gbs_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -49,6 +49,7 @@ class lp_options(ctypes.Structure):
         ("pipeline", ctypes.c_int),
         ("solo_elems", ctypes.c_longlong),
         ("time_limit_s", ctypes.c_double),
+        ("reinv_body", ctypes.c_int),
     ]
 
 
@@ -114,6 +115,12 @@ _SIGS = [
                                        ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(ctypes.c_int)]),
     ("lp_server_destroy", None, [ctypes.c_void_p]),
+    ("lp_fp32_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), _c_double_p,
+                                     _c_double_p]),
+    ("lp_dgemm_emulated", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                         ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong,
+                                         ctypes.POINTER(lp_options)]),
     ("lp_destroy", None, [ctypes.c_void_p]),
     ("lp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lp_version", ctypes.c_char_p, []),
@@ -253,6 +260,33 @@ def lp_solve_noalloc(A, b, c, sense=LP_MAX_LE, opt: Optional[lp_options] = None,
                                            ctypes.byref(obj), ctypes.byref(st),
                                            ctypes.byref(it)))
     return obj.value, st.value, it.value
+
+
+def lp_fp32_stats(h):
+    """(reinversions, reinversion ms, body-refresh ms) of the last FP32 solve."""
+    n = ctypes.c_int()
+    ms = ctypes.c_double()
+    body = ctypes.c_double()
+    _check(load_library().lp_fp32_stats(h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(body)),
+           h)
+    return n.value, ms.value, body.value
+
+
+def lp_dgemm_emulated(A, B, C, opt: Optional[lp_options] = None) -> None:
+    """C = A B (FP64 device tensors, row-major) by emulated-FP64 tensor-core
+    products; C must be an M x N float64 tensor on the device."""
+    if len(A.shape) != 2 or len(B.shape) != 2 or len(C.shape) != 2:
+        raise ValueError("A, B and C must be matrices")
+    M, K = int(A.shape[0]), int(A.shape[1])
+    if int(B.shape[0]) != K or tuple(C.shape) != (M, int(B.shape[1])):
+        raise ValueError("shapes: A %s, B %s, C %s" % (tuple(A.shape), tuple(B.shape),
+                                                       tuple(C.shape)))
+    N = int(B.shape[1])
+    for t in (A, B, C):
+        if not hasattr(t, "is_cuda") or not t.is_cuda:
+            raise ValueError("A, B and C must be device tensors")
+    _check(load_library().lp_dgemm_emulated(M, N, K, _ptr(A), K, _ptr(B), N, _ptr(C), N,
+                                            ctypes.byref(opt) if opt else None))
 
 
 def lp_solve_batch(lps, opt: Optional[lp_options] = None, want_xy=False):

@@ -111,6 +111,10 @@ struct lp_handle {
     int *dabort = nullptr;        // device view of the same word
     std::chrono::steady_clock::time_point deadline{};
     bool timed_out = false;       // the last solve ended in LP_TIMEOUT: reload first
+
+    // FP32 mode: emulated-FP64 products of the body refresh, and its time
+    OzWork oz{};
+    double body_ms = 0.0;
 };
 
 namespace {
@@ -201,6 +205,7 @@ void lp_options_default(lp_options *o) {
     o->trace_cap = 0;
     o->group_elems = 0;
     o->pipeline = 1;
+    o->reinv_body = 1;
 }
 
 const char *lp_version(void) { return "gbsimplex 0.1 (sm_103a)"; }
@@ -295,6 +300,7 @@ void lp_destroy(lp_handle *h) {
     if (h->pdesc) cudaFreeHost(h->pdesc);
     if (h->pobj) cudaFreeHost(h->pobj);
     if (h->habort) cudaFreeHost(h->habort);
+    oz_work_free(h->oz);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -623,11 +629,30 @@ lp_err reinvert(lp_handle *h, bool *singular, double *zmin, double *rmin) {
     CUDA_TRY(h, cudaMemcpyAsync(&chk, h->rb.chk, sizeof chk, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaEventRecord(e1, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    float t = 0.0f;
+    float t = 0.0f, tb = 0.0f;
     cudaEventElapsedTime(&t, e0, e1);
+    if (h->prec == PREC_FP32 && h->opt.reinv_body && !h->region && chk.singular == 0) {
+        // the body B^-1 [A I] of the basis just reinverted, from the FP64 data
+        CUDA_TRY(h, cudaEventRecord(e0, s));
+        CUDA_TRY(h, oz_refresh_body(h->dA, h->db, h->sense, m, n, h->dbasis, h->rb, ns,
+                                    static_cast<float *>(h->dT), h->P, h->oz, h->sms,
+                                    h->opt.spin_timeout_cycles, s));
+        int oerr = 0;
+        CUDA_TRY(h, cudaMemcpyAsync(&oerr, h->oz.err, sizeof oerr, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaEventRecord(e1, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        cudaEventElapsedTime(&tb, e0, e1);
+        if (oerr) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            set_err(h, "reinversion: a wait of the body refresh ran out");
+            return LP_ERR_CUDA;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->reinv_ms += t;
+    h->reinv_ms += t + tb;
+    h->body_ms += tb;
     h->reinversions += 1;
     *singular = chk.singular != 0;
     *zmin = okey_to_double(chk.zmin_key);
@@ -650,6 +675,7 @@ lp_err solve_fp32(lp_handle *h) {
     h->fp32_kernel_ms = 0.0;
     h->fp32_launches = 0;
     h->reinv_ms = 0.0;
+    h->body_ms = 0.0;
     h->reinversions = 0;
     for (;;) {
         const PivotShape &sh = rule == h->sense ? h->shape : h->shape_alt;
@@ -830,6 +856,14 @@ lp_err lp_result(lp_handle *h, double *x, double *y, double *obj, lp_status *sta
     if (obj) *obj = *h->pobj;
     if (status) *status = (lp_status)h->pdesc->status;
     if (iters) *iters = h->pdesc->iters;
+    return LP_OK;
+}
+
+lp_err lp_fp32_stats(lp_handle *h, int *reinversions, double *reinv_ms, double *body_ms) {
+    if (!h) return LP_ERR_INVALID_ARG;
+    if (reinversions) *reinversions = h->reinversions;
+    if (reinv_ms) *reinv_ms = h->reinv_ms;
+    if (body_ms) *body_ms = h->body_ms;
     return LP_OK;
 }
 

@@ -313,6 +313,36 @@ size_t handle_region_used(const lp_handle *h);
 cudaError_t launch_to_fp64(const float *T, long long P, int M, int N, double *out,
                            cudaStream_t s);
 
+// Emulated-FP64 products on the tensor cores (gbs_ozaki.cu): device
+// workspace, grown on demand and kept between calls.
+struct OzWork {
+    void *asl = nullptr, *bsl = nullptr;       // bf16 digit planes of A and B
+    int *rowexp = nullptr, *colexp = nullptr;  // row / column exponents
+    int *kx = nullptr;                         // inner exponents and balancing shifts
+    size_t cap_asl = 0, cap_bsl = 0, cap_rowexp = 0, cap_colexp = 0, cap_kx = 0;
+    // body refresh
+    double *X = nullptr, *Ainv = nullptr, *Z = nullptr;
+    int *basic_row = nullptr, *L = nullptr, *Lrow = nullptr;
+    size_t cap_X = 0, cap_Ainv = 0, cap_Z = 0, cap_basic = 0, cap_L = 0, cap_Lrow = 0;
+    int *err = nullptr;  // the product kernel's error flag (one int)
+};
+void oz_work_free(OzWork &w);
+
+// C (M x N, ldc) = A (M x K, lda) B (K x N, ldb), FP64 in and out, all device
+// memory, through bf16 digit products on the tensor cores.  *d_err (device)
+// is set when a wait of the kernel ran out.
+cudaError_t oz_dgemm(const double *A, long long lda, const double *B, long long ldb, double *C,
+                     long long ldc, int M, int N, int K, OzWork &w, int *d_err, int sms,
+                     long long spin_limit, cudaStream_t s);
+
+// The FP32 tableau's constraint rows B^-1 [A I] (every column but the rhs),
+// recomputed from the original data for the current basis, after the
+// reinversion's lists and Gauss-Jordan step (rb, ns structural basics).
+cudaError_t oz_refresh_body(const double *A, const double *b, int sense, int m, int n,
+                            const int *basis, const ReinvBufs &rb, int ns, float *T32,
+                            long long P, OzWork &w, int sms, long long spin_limit,
+                            cudaStream_t s);
+
 // Host side: restores the caller's current device when an entry point that
 // switched to its own device returns.
 struct DeviceRestore {

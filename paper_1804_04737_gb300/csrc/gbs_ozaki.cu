@@ -1,0 +1,977 @@
+// Emulated-FP64 matrix products on the tcgen05 tensor cores (an Ozaki-type
+// splitting), and the FP32 tableau's body refresh built on them.
+//
+// GB300 runs FP64 at 2 FMA per clock per SM (1.26 TFLOP/s), but bf16 products
+// on the tensor cores at about 2 PFLOP/s.  A product C = A B of FP64 matrices
+// is formed from bf16 ones: every row i of A is scaled by sigma_i = 2^e_i
+// (|A_ik| < sigma_i) and written as a sum of S = 7 signed 7-bit integer
+// digits, A_ik = sigma_i sum_p a_ik^(p) 2^(-7(p+1)) (plus a residual below
+// 2^-49 sigma_i); likewise every column j of B with tau_j.  The digits are
+// exact in bf16 (|digit| <= 128).  Then
+//   C_ij ~= sigma_i tau_j sum_{g=0}^{S-1} 2^(-7(g+2)) G_g,
+//   G_g = sum_{p+q=g} sum_k a_ik^(p) b_kj^(q),
+// dropping the pairs p + q >= S (below 2^-49 of the scale).  Each G_g is a
+// sum of integer products below 2^24 in magnitude for K <= 448 terms, so the
+// tensor cores' FP32 accumulation forms it exactly; longer sums are split into
+// chunks of 448 whose FP64 results add up.  The epilogue combines the S
+// groups in single-single (two-float) arithmetic and scales once in FP64, so
+// the FP64 pipe does a few operations per output, not one per group.
+//
+// Kernel (persistent, 192 threads, one CTA per SM): warp 0 issues the TMA
+// loads (cp.async.bulk.tensor, 128-byte swizzle) of the A digit planes (a ring
+// of 4 stages of 128 x 64) and of all S B digit planes of a 64-column block
+// (two stages); warp 1 issues tcgen05.mma (M 128, N 64, K 16, bf16 in, FP32
+// accumulate) for the 28 digit pairs into S accumulators in tensor memory
+// (S x 64 of its 512 columns); warps 2-5 read the accumulators (tcgen05.ld) and
+// write C.  Every wait is bounded: past the limit a role sets the error flag,
+// the others stop at their next wait, the loads in flight are waited for, and
+// tensor memory is freed before the CTA exits.
+//
+// The body refresh (FP32 mode, not in the paper; Sec. 2 Steps 4-5 produce the
+// tableau B^-1 [A I b] that it recomputes): with S the structural basic
+// variables, R the s rows whose slack is not basic, L the others, and
+// Ainv = A_RS^-1 from the Gauss-Jordan step of the reinversion,
+//   X = Ainv [A_R | I_R | b_R]            (rows of the structural basics),
+//   Y = [A_L | I_L | b_L] - A_LS X        (rows of the slack basics),
+// both with the tableau's signs (the dual form enters as -A, -b), rounded into
+// the FP32 tableau (basic columns set to exact unit vectors; the rhs column
+// and the objective row come from the reinversion's own FP64 values).
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "gbs_device.cuh"
+#include "gbs_internal.h"
+#include "gbsimplex.h"
+
+namespace gbs {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kOzS = 7;                 // digits per operand
+constexpr int kOzT = 7;                 // bits per digit
+constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 64;
+constexpr int kOzChunkKB = 7;           // K blocks per exact group sum (448 terms)
+constexpr int kOzAStages = 4;
+constexpr int kOzABytes = kOzBM * kOzBK * 2;            // 16 KB: one A digit plane block
+constexpr int kOzBBytes = kOzBN * kOzBK * 2;            // 8 KB: one B digit plane block
+constexpr int kOzBStageBytes = kOzS * kOzBBytes;        // 56 KB: all digit planes of a B block
+constexpr int kOzTmemCols = 512;                        // S x 64 = 448 used
+constexpr int kOzThreads = 192;
+constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + 256;
+
+static_assert(kOzS * kOzBN <= kOzTmemCols, "accumulators must fit tensor memory");
+static_assert(kOzT * kOzS == 49, "the digit extraction below assumes 49 bits");
+
+// ---- PTX wrappers ----
+__device__ __forceinline__ uint32_t su32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false when the limit ran out
+// or another CTA or role flagged an error.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(volatile int *)err) return false;
+        if (clock64() - t0 > limit) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand block in the 128-byte
+// swizzled layout TMA writes (rows of 128 bytes, 8-row groups 1024 bytes
+// apart): start address, stride byte offset 1024, descriptor version 1,
+// layout 128-byte swizzle.  The leading byte offset is not used by this
+// layout.  Advancing the start address by 32 bytes selects the next 16
+// elements of K within the 128-byte row.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, N = 64, M = 128.
+constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                              ((uint32_t)(kOzBN >> 3) << 17) | ((uint32_t)(kOzBM >> 4) << 24);
+
+// ---- the digits ----
+//
+// Exponents are biased FP64 exponents shifted by the inner balancing below;
+// kNoExp marks a row or column without nonzero entries.  For x = m 2^(ex -
+// 1075) (m the 53-bit significand) taken as x 2^sh with |x 2^sh| < 2^(E -
+// 1022) (E: the largest shifted exponent of its row or column),
+// N = round(x 2^sh 2^(49 - (E - 1022))) is an integer below 2^49 in magnitude,
+// and its balanced base-128 digits d_0 .. d_6 (d_0 most significant,
+// |d_0| <= 128, the others in [-64, 63]) satisfy
+// x 2^sh ~= 2^(E - 1022) sum_p d_p 2^(-7(p+1)).
+constexpr int kNoExp = -(1 << 20);
+
+__device__ __forceinline__ int exp_of(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+__device__ __forceinline__ void digits_of(double x, int E, int shift, int (&d)[kOzS]) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+#pragma unroll
+    for (int p = 0; p < kOzS; ++p) d[p] = 0;
+    if (ex == 0 || E == kNoExp) return;  // zero (or subnormal, below 2^-1022: dropped)
+    const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - (ex + shift) + 4;  // >= 4
+    long long N = 0;
+    if (sh < 63) N = (long long)((mant + (1ull << (sh - 1))) >> sh);
+    if (b < 0) N = -N;
+#pragma unroll
+    for (int p = kOzS - 1; p > 0; --p) {
+        const long long r = ((N + 64) & 127) - 64;
+        d[p] = (int)r;
+        N = (N - r) >> 7;
+    }
+    d[0] = (int)N;
+}
+
+// Sources of operand elements.
+struct SrcDense {  // p[i * ld + k]
+    const double *p;
+    long long ld;
+    __device__ double at(int i, int k) const { return p[(long long)i * ld + k]; }
+};
+struct SrcGather {  // sg * A[rows[i]][cols[k]] (A row-major with n columns)
+    const double *A;
+    int n;
+    const int *rows, *cols;
+    double sg;
+    __device__ double at(int i, int k) const { return sg * A[(long long)rows[i] * n + cols[k]]; }
+};
+struct SrcRefreshB {  // row r: [sg A_l | e_l | sg b_l], l = R[r]
+    const double *A, *b;
+    const int *R;
+    int n, m;
+    double sg;
+    __device__ double at(int r, int j) const {
+        const int l = R[r];
+        if (j < n) return sg * A[(long long)l * n + j];
+        if (j < n + m) return (j - n == l) ? 1.0 : 0.0;
+        return sg * b[l];
+    }
+};
+
+// Inner balancing: A B = (A D)(D^-1 B) for D = diag(2^shift_k), exact.  The
+// digits keep 49 bits of each row of A and each column of B; when the terms
+// of a sum have balanced magnitudes but column k of A and row k of B scale in
+// opposite directions (A_RS^-1 times rows of A, with rows of A scaled apart),
+// per-row and per-column scales alone would drop whole terms.  shift_k =
+// floor((eB_k - eA_k) / 2), with eA_k the largest exponent of column k of A
+// and eB_k that of row k of B, brings both to the geometric middle.
+
+// eA_k: largest exponent of column k of A (M x K), one thread per k.
+template <class Src>
+__global__ void oz_kexpA_kernel(Src src, int M, int K, int *kA) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int mx = kNoExp;
+    for (int i = 0; i < M; ++i) {
+        const int ex = exp_of(src.at(i, k));
+        if (ex) mx = max(mx, ex);
+    }
+    kA[k] = mx;
+}
+
+// eB_k: largest exponent of row k of B (K x N), one warp per k; then shift_k.
+template <class Src>
+__global__ void oz_kexpB_kernel(Src src, int K, int N, const int *kA, int *shift) {
+    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (k >= K) return;
+    int mx = kNoExp;
+    for (int j = lane; j < N; j += 32) {
+        const int ex = exp_of(src.at(k, j));
+        if (ex) mx = max(mx, ex);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) shift[k] = (mx != kNoExp && kA[k] != kNoExp) ? (mx - kA[k]) >> 1 : 0;
+}
+
+// Largest shifted exponent of each row i < M of A over k < K (kNoExp: none).
+template <class Src>
+__global__ void oz_rowexp_kernel(Src src, int M, int K, const int *shift, int *rowexp) {
+    const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= M) return;
+    int mx = kNoExp;
+    for (int k = lane; k < K; k += 32) {
+        const int ex = exp_of(src.at(w, k));
+        if (ex) mx = max(mx, ex + shift[k]);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) rowexp[w] = mx;
+}
+
+// Largest shifted exponent of each column j < N of B over k < K.
+template <class Src>
+__global__ void oz_colexp_kernel(Src src, int K, int N, const int *shift, int *colexp) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    int mx = kNoExp;
+    for (int k = 0; k < K; ++k) {
+        const int ex = exp_of(src.at(k, j));
+        if (ex) mx = max(mx, ex - shift[k]);
+    }
+    colexp[j] = mx;
+}
+
+// A digit planes: out[p][i][k] (Mp x Kp per plane), zero in the padding.
+template <class Src>
+__global__ void oz_split_rows_kernel(Src src, int M, int K, int Mp, int Kp, const int *rowexp,
+                                     const int *shift, __nv_bfloat16 *out) {
+    const long long total = (long long)Mp * Kp;
+    const long long plane = total;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / Kp), k = (int)(e - (long long)i * Kp);
+        int d[kOzS];
+        if (i < M && k < K) {
+            digits_of(src.at(i, k), rowexp[i], shift[k], d);
+        } else {
+#pragma unroll
+            for (int p = 0; p < kOzS; ++p) d[p] = 0;
+        }
+#pragma unroll
+        for (int p = 0; p < kOzS; ++p) out[p * plane + e] = __float2bfloat16_rn((float)d[p]);
+    }
+}
+
+// B digit planes, transposed: out[p][j][k] (Np x Kp per plane) for B (K x N),
+// through a 32 x 32 tile in shared memory (reads along j, writes along k).
+template <class Src>
+__global__ void oz_split_cols_kernel(Src src, int K, int N, int Kp, int Np, const int *colexp,
+                                     const int *shift, __nv_bfloat16 *out) {
+    __shared__ __nv_bfloat16 tile[kOzS][32][33];
+    const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int k = k0 + r, j = j0 + tx;
+        int d[kOzS];
+        if (k < K && j < N) {
+            digits_of(src.at(k, j), colexp[j], -shift[k], d);
+        } else {
+#pragma unroll
+            for (int p = 0; p < kOzS; ++p) d[p] = 0;
+        }
+#pragma unroll
+        for (int p = 0; p < kOzS; ++p) tile[p][r][tx] = __float2bfloat16_rn((float)d[p]);
+    }
+    __syncthreads();
+    const size_t plane = (size_t)Np * Kp;
+    for (int r = ty; r < 32; r += 8) {
+        const int j = j0 + r, k = k0 + tx;
+        if (j < Np && k < Kp) {
+#pragma unroll
+            for (int p = 0; p < kOzS; ++p) out[p * plane + (size_t)j * Kp + k] = tile[p][tx][r];
+        }
+    }
+}
+
+// ---- the product kernel ----
+struct OzParams {
+    int M, N, K, Mp, Np, Kp;
+    const int *rowexp, *colexp;
+    int mode;  // 0: C = A B (FP64, rows < M, cols < N); 1: refresh rows into the FP32 tableau
+    double *C;
+    long long ldc;
+    // mode 1: output row r is tableau row rowmap[r], constraint rowk[r]; the
+    // value written is sg [A_k | e_k](j) - (A B)_rj for j < N, with the
+    // basic columns set to unit vectors (basic_row[j]: the row where column j
+    // is basic, or -1)
+    float *T32;
+    long long P;
+    const int *rowmap, *rowk, *basic_row;
+    const double *Aorig;
+    int n, m;
+    double sg;
+    int *err;
+    long long spin_limit;
+};
+
+__device__ __forceinline__ double pow2d(int e) {  // 2^e, e in [-1022, 1023]
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+__device__ __forceinline__ float pow2f(int e) {  // 2^e, e in [-126, 127]
+    return __int_as_float((e + 127) << 23);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const OzParams p) {
+    extern __shared__ unsigned char oz_smem[];
+    __shared__ uint32_t s_tmem;
+    const uint32_t raw = su32(oz_smem);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sB = base;                                  // [2][S][64][128 B]
+    const uint32_t sA = base + 2 * kOzBStageBytes;             // [4][128][128 B]
+    const uint32_t sBar = sA + kOzAStages * kOzABytes;         // barriers, 8 bytes each
+    auto full_a = [&](int s) { return sBar + 8u * s; };
+    auto empty_a = [&](int s) { return sBar + 8u * (kOzAStages + s); };
+    auto full_b = [&](int s) { return sBar + 8u * (2 * kOzAStages + s); };
+    auto empty_b = [&](int s) { return sBar + 8u * (2 * kOzAStages + 2 + s); };
+    const uint32_t tmem_full = sBar + 8u * (2 * kOzAStages + 4);
+    const uint32_t tmem_empty = sBar + 8u * (2 * kOzAStages + 5);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzAStages; ++s) {
+            mbar_init(full_a(s), 1);
+            mbar_init(empty_a(s), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(full_b(s), 1);
+            mbar_init(empty_b(s), 1);
+        }
+        mbar_init(tmem_full, 1);
+        mbar_init(tmem_empty, 4);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                     "r"(kOzTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    const int nmb = p.Mp / kOzBM, nnb = p.Np / kOzBN, tiles = nmb * nnb;
+    const int nkb = p.Kp / kOzBK;
+    const int nch = (nkb + kOzChunkKB - 1) / kOzChunkKB;
+    const long long lim = p.spin_limit;
+
+    if (warp == 0) {
+        // ---- TMA producer ----
+        if (lane == 0) {
+            int as = 0, bs = 0;
+            uint32_t aph = 0, bph = 0;
+            // loads issued and not yet seen complete, per stage, for the drain
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int m0 = (t % nmb) * kOzBM, n0 = (t / nmb) * kOzBN;
+                for (int kb = 0; kb < nkb && ok; ++kb) {
+                    if (!(ok = mbar_wait(empty_b(bs), bph ^ 1u, p.err, lim))) break;
+                    mbar_expect_tx(full_b(bs), kOzBStageBytes);
+                    for (int q = 0; q < kOzS; ++q)
+                        tma_load_2d(sB + bs * kOzBStageBytes + q * kOzBBytes, &tmB, kb * kOzBK,
+                                    q * p.Np + n0, full_b(bs));
+                    if (++bs == 2) {
+                        bs = 0;
+                        bph ^= 1u;
+                    }
+                    for (int pp = 0; pp < kOzS; ++pp) {
+                        if (!(ok = mbar_wait(empty_a(as), aph ^ 1u, p.err, lim))) break;
+                        mbar_expect_tx(full_a(as), kOzABytes);
+                        tma_load_2d(sA + as * kOzABytes, &tmA, kb * kOzBK, pp * p.Mp + m0, full_a(as));
+                        if (++as == kOzAStages) {
+                            as = 0;
+                            aph ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                // Drain: every load issued completes on its stage's full
+                // barrier; wait (bounded) for the phase each stage is in, so
+                // that no copy still writes shared memory when the CTA ends.
+                for (int s = 0; s < kOzAStages; ++s) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(full_a(s), ((s < as) ? aph : aph ^ 1u)) && clock64() - t0 < lim) {}
+                }
+                for (int s = 0; s < 2; ++s) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(full_b(s), ((s < bs) ? bph : bph ^ 1u)) && clock64() - t0 < lim) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int as = 0, bs = 0;
+            uint32_t aph = 0, bph = 0, use = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nch && ok; ++c) {
+                    // the epilogue has drained the accumulators of the last use
+                    if (!(ok = mbar_wait(tmem_empty, (use & 1u) ^ 1u, p.err, lim))) break;
+                    tc_fence_after();
+                    const int kb0 = c * kOzChunkKB, kb1 = min(nkb, kb0 + kOzChunkKB);
+                    for (int kb = kb0; kb < kb1 && ok; ++kb) {
+                        if (!(ok = mbar_wait(full_b(bs), bph, p.err, lim))) break;
+                        tc_fence_after();
+                        for (int pp = 0; pp < kOzS; ++pp) {
+                            if (!(ok = mbar_wait(full_a(as), aph, p.err, lim))) break;
+                            tc_fence_after();
+                            const uint32_t a0 = sA + as * kOzABytes;
+                            for (int q = 0; q < kOzS - pp; ++q) {
+                                const uint32_t b0 = sB + bs * kOzBStageBytes + q * kOzBBytes;
+                                const uint32_t d = tmem + (uint32_t)((pp + q) * kOzBN);
+#pragma unroll
+                                for (int k = 0; k < kOzBK / 16; ++k) {
+                                    const uint32_t acc = (kb == kb0 && pp == 0 && k == 0) ? 0u : 1u;
+                                    tc_mma(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k),
+                                           kOzIdesc, acc);
+                                }
+                            }
+                            tc_commit(empty_a(as));  // the stage frees when these MMAs complete
+                            if (++as == kOzAStages) {
+                                as = 0;
+                                aph ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        tc_commit(empty_b(bs));
+                        if (++bs == 2) {
+                            bs = 0;
+                            bph ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(tmem_full);
+                    ++use;
+                }
+            }
+            // every MMA issued is complete before tensor memory is freed
+            // (a commit arrives after all of them)
+            if (!ok) {
+                tc_commit(tmem_full);
+                const long long t0 = clock64();
+                while (!mbar_try_wait(tmem_full, use & 1u) && clock64() - t0 < lim) {}
+            }
+        }
+    } else {
+        // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) .. + 31 ----
+        const int lg = warp & 3;
+        uint32_t use = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            const int m0 = (t % nmb) * kOzBM, n0 = (t / nmb) * kOzBN;
+            const int r = m0 + lg * 32 + lane;  // this thread's output row
+            for (int c = 0; c < nch && ok; ++c) {
+                if (!(ok = mbar_wait(tmem_full, use & 1u, p.err, lim))) break;
+                tc_fence_after();
+                const int Er = r < p.M ? p.rowexp[r] : kNoExp;
+                for (int h = 0; h < kOzBN / 32; ++h) {
+                    float hi[32], lo[32];
+                    for (int g = 0; g < kOzS; ++g) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(g * kOzBN + h * 32), v);
+                        tmem_ld_wait();
+                        const float sc = pow2f(-kOzT * g);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float x = __fmul_rn(__uint_as_float(v[j]), sc);  // exact
+                            if (g == 0) {
+                                hi[j] = x;
+                                lo[j] = 0.0f;
+                            } else {
+                                float s, e;
+                                two_sum(hi[j], x, s, e);
+                                hi[j] = s;
+                                lo[j] = __fadd_rn(lo[j], e);
+                            }
+                        }
+                    }
+                    if (r < p.M) {
+                        const int j0 = n0 + h * 32;
+                        if (p.mode == 0) {
+                            double *crow = p.C + (long long)r * p.ldc;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int col = j0 + j;
+                                if (col < p.N) {
+                                    const int Fc = p.colexp[col];
+                                    double v = 0.0;
+                                    if (Er != kNoExp && Fc != kNoExp) {
+                                        // scale 2^(Er - 1022 + Fc - 1022 - 14)
+                                        const int e = Er + Fc - 2058;
+                                        if (e >= -1022 && e <= 1023) {
+                                            const double sc = pow2d(e);
+                                            v = fma((double)lo[j], sc, (double)hi[j] * sc);
+                                        } else {
+                                            v = ldexp((double)hi[j] + (double)lo[j], e);
+                                        }
+                                    }
+                                    if (c == 0) crow[col] = v;
+                                    else crow[col] += v;
+                                }
+                            }
+                        } else {
+                            const int ti = p.rowmap[r], k = p.rowk[r];
+                            float *trow = p.T32 + (long long)ti * p.P;
+                            const double *arow = p.Aorig + (long long)k * p.n;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int col = j0 + j;
+                                if (col < p.N - 1) {  // the rhs column comes from the reinversion
+                                    const int br = p.basic_row[col];
+                                    float out;
+                                    if (br >= 0) {
+                                        out = br == ti ? 1.0f : 0.0f;
+                                    } else {
+                                        const double dv = col < p.n ? p.sg * arow[col]
+                                                                    : (col - p.n == k ? 1.0 : 0.0);
+                                        const int Fc = p.colexp[col];
+                                        double prod = 0.0;
+                                        if (Er != kNoExp && Fc != kNoExp) {
+                                            const int e = Er + Fc - 2058;
+                                            if (e >= -1022 && e <= 1023) {
+                                                const double sc = pow2d(e);
+                                                prod = fma((double)lo[j], sc, (double)hi[j] * sc);
+                                            } else {
+                                                prod = ldexp((double)hi[j] + (double)lo[j], e);
+                                            }
+                                        }
+                                        out = (float)(dv - prod);
+                                    }
+                                    trow[col] = out;
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tmem_empty);
+                ++use;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kOzTmemCols)
+                     : "memory");
+    }
+}
+
+// ---- host side ----
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// A 2D map over `rows` rows of `Kp` bf16 (row pitch Kp * 2 bytes), boxes of
+// 64 x box_rows, 128-byte swizzle.
+cudaError_t make_map(CUtensorMap *map, void *ptr, long long rows, int Kp, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Grow a workspace buffer to hold n elements of T (contents not kept).
+template <class T>
+cudaError_t grow_buf(T **p, size_t *cap, size_t n) {
+    if (*cap >= n && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+cudaError_t grow_planes(void **p, size_t *cap, size_t n) {
+    __nv_bfloat16 *q = static_cast<__nv_bfloat16 *>(*p);
+    const cudaError_t e = grow_buf(&q, cap, n);
+    *p = q;
+    return e;
+}
+
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Grow the digit planes and exponent arrays for an M x K by K x N product.
+cudaError_t oz_reserve(OzWork &w, int M, int N, int K) {
+    const int Mp = round_up(std::max(M, 1), kOzBM), Np = round_up(std::max(N, 1), kOzBN),
+              Kp = round_up(std::max(K, 1), kOzBK);
+    cudaError_t e;
+    if ((e = grow_planes(&w.asl, &w.cap_asl, (size_t)kOzS * Mp * Kp)) != cudaSuccess) return e;
+    if ((e = grow_planes(&w.bsl, &w.cap_bsl, (size_t)kOzS * Np * Kp)) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.rowexp, &w.cap_rowexp, (size_t)std::max(M, 1))) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.colexp, &w.cap_colexp, (size_t)std::max(N, 1))) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.kx, &w.cap_kx, (size_t)2 * std::max(K, 1))) != cudaSuccess) return e;
+    if (!w.err && (e = cudaMalloc((void **)&w.err, sizeof(int))) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Digits of A (M x K from srcA) and B (K x N from srcB), then the product.
+// The workspace must already hold this size (oz_reserve): growing it here
+// could free a buffer that queued work still reads.
+template <class SA, class SB>
+cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork &w, int sms,
+                       cudaStream_t s) {
+    const int Mp = round_up(std::max(M, 1), kOzBM), Np = round_up(std::max(N, 1), kOzBN),
+              Kp = round_up(std::max(K, 1), kOzBK);
+    cudaError_t e;
+    if (w.cap_asl < (size_t)kOzS * Mp * Kp || w.cap_bsl < (size_t)kOzS * Np * Kp ||
+        w.cap_rowexp < (size_t)M || w.cap_colexp < (size_t)N || w.cap_kx < (size_t)2 * K || !w.err)
+        return cudaErrorInvalidValue;
+    int *kA = w.kx, *shift = w.kx + K;
+    if (K > 0) {
+        oz_kexpA_kernel<SA><<<(K + 255) / 256, 256, 0, s>>>(srcA, M, K, kA);
+        oz_kexpB_kernel<SB><<<(K + 7) / 8, 256, 0, s>>>(srcB, K, N, kA, shift);
+    }
+    oz_rowexp_kernel<SA><<<(M + 7) / 8, 256, 0, s>>>(srcA, M, K, shift, w.rowexp);
+    oz_colexp_kernel<SB><<<(N + 255) / 256, 256, 0, s>>>(srcB, K, N, shift, w.colexp);
+    {
+        const long long total = (long long)Mp * Kp;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * sms * 8);
+        oz_split_rows_kernel<SA><<<blocks, 256, 0, s>>>(srcA, M, K, Mp, Kp, w.rowexp, shift,
+                                                         static_cast<__nv_bfloat16 *>(w.asl));
+    }
+    oz_split_cols_kernel<SB><<<dim3(Np / 32, Kp / 32), 256, 0, s>>>(
+        srcB, K, N, Kp, Np, w.colexp, shift, static_cast<__nv_bfloat16 *>(w.bsl));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    CUtensorMap ma, mb;
+    if ((e = make_map(&ma, w.asl, (long long)kOzS * Mp, Kp, kOzBM)) != cudaSuccess) return e;
+    if ((e = make_map(&mb, w.bsl, (long long)kOzS * Np, Kp, kOzBN)) != cudaSuccess) return e;
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.Mp = Mp;
+    p.Np = Np;
+    p.Kp = Kp;
+    p.rowexp = w.rowexp;
+    p.colexp = w.colexp;
+    if (!p.err) p.err = w.err;
+    if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if (p.mode == 1 && Kp > kOzChunkKB * kOzBK) return cudaErrorInvalidValue;  // one chunk only
+    if ((e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kOzSmem)) != cudaSuccess)
+        return e;
+    const int tiles = (Mp / kOzBM) * (Np / kOzBN);
+    oz_gemm_kernel<<<std::min(tiles, sms), kOzThreads, kOzSmem, s>>>(ma, mb, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void oz_work_free(OzWork &w) {
+    void *ps[] = {w.asl, w.bsl, w.rowexp, w.colexp, w.kx, w.X, w.Ainv, w.Z, w.basic_row, w.L, w.Lrow, w.err};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    w = OzWork{};
+}
+
+cudaError_t oz_dgemm(const double *A, long long lda, const double *B, long long ldb, double *C,
+                     long long ldc, int M, int N, int K, OzWork &w, int *d_err, int sms,
+                     long long spin_limit, cudaStream_t s) {
+    cudaError_t e = oz_reserve(w, M, N, K);
+    if (e != cudaSuccess) return e;
+    OzParams p{};
+    p.mode = 0;
+    p.C = C;
+    p.ldc = ldc;
+    p.err = d_err;
+    p.spin_limit = spin_limit;
+    return oz_product(SrcDense{A, lda}, SrcDense{B, ldb}, M, N, K, p, w, sms, s);
+}
+
+namespace {
+
+// Ainv[k][r] = row k of A_RS^-1, which the Gauss-Jordan step leaves in row
+// pivrow[k] of the right block of W = [A_RS | b_R | I].
+__global__ void oz_ainv_kernel(const double *__restrict__ W, long long Wp, int ns,
+                               const int *__restrict__ pivrow, double *__restrict__ Ainv) {
+    const long long total = (long long)ns * ns;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / ns), r = (int)(e - (long long)k * ns);
+        Ainv[e] = W[(long long)pivrow[k] * Wp + ns + 1 + r];
+    }
+}
+
+// basic_row[v] = the row where variable v is basic (the array starts at -1).
+__global__ void oz_basic_kernel(const int *__restrict__ basis, int m, int *__restrict__ basic_row) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) basic_row[basis[i]] = i;
+}
+
+// L = the constraints whose slack is basic, ascending; Lrow[r] = the row
+// where the slack of L[r] is basic (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) oz_llist_kernel(const int *__restrict__ basic_row, int m,
+                                                        int n, int *__restrict__ L,
+                                                        int *__restrict__ Lrow) {
+    __shared__ int scan[1024];
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int chunk = (m + B - 1) / B;
+    const int l0 = min(m, tid * chunk), l1 = min(m, l0 + chunk);
+    int cnt = 0;
+    for (int l = l0; l < l1; ++l) cnt += basic_row[n + l] >= 0;
+    scan[tid] = cnt;
+    __syncthreads();
+    for (int o = 1; o < B; o <<= 1) {
+        const int a = tid >= o ? scan[tid - o] : 0;
+        __syncthreads();
+        scan[tid] += a;
+        __syncthreads();
+    }
+    int k = scan[tid] - cnt;
+    for (int l = l0; l < l1; ++l) {
+        const int r = basic_row[n + l];
+        if (r >= 0) {
+            L[k] = l;
+            Lrow[k] = r;
+            ++k;
+        }
+    }
+}
+
+// The rows of the structural basics: tableau row basic_row[S[k]] = X[k] in
+// FP32, basic columns as unit vectors, every column but the rhs.
+__global__ void oz_xrows_kernel(const double *__restrict__ X, int N, int ns, const int *__restrict__ S,
+                                const int *__restrict__ basic_row, float *__restrict__ T32, long long P) {
+    const long long total = (long long)ns * (N - 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / (N - 1)), j = (int)(e - (long long)k * (N - 1));
+        const int ti = basic_row[S[k]], br = basic_row[j];
+        T32[(long long)ti * P + j] = br >= 0 ? (br == ti ? 1.0f : 0.0f) : (float)X[(long long)k * N + j];
+    }
+}
+
+// The rows of the slack basics from Z = A_LS X (when the product took more
+// than one K chunk): sg [A_l | e_l](j) - Z[r][j].
+__global__ void oz_yrows_kernel(const double *__restrict__ Z, int N, int mL, const int *__restrict__ L,
+                                const int *__restrict__ Lrow, const double *__restrict__ A, int n,
+                                double sg, const int *__restrict__ basic_row, float *__restrict__ T32,
+                                long long P) {
+    const long long total = (long long)mL * (N - 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / (N - 1)), j = (int)(e - (long long)r * (N - 1));
+        const int ti = Lrow[r], l = L[r], br = basic_row[j];
+        float v;
+        if (br >= 0) {
+            v = br == ti ? 1.0f : 0.0f;
+        } else {
+            const double d = j < n ? sg * A[(long long)l * n + j] : (j - n == l ? 1.0 : 0.0);
+            v = (float)(d - Z[(long long)r * N + j]);
+        }
+        T32[(long long)ti * P + j] = v;
+    }
+}
+
+int grid_for(long long total) {
+    return (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 4096));
+}
+
+}  // namespace
+
+cudaError_t oz_refresh_body(const double *A, const double *b, int sense, int m, int n,
+                            const int *basis, const ReinvBufs &rb, int ns, float *T32,
+                            long long P, OzWork &w, int sms, long long spin_limit,
+                            cudaStream_t s) {
+    const double sg = sense == 0 ? 1.0 : -1.0;
+    const int N = n + m + 1, mL = m - ns;
+    const bool one_chunk = round_up(std::max(ns, 1), kOzBK) <= kOzChunkKB * kOzBK;
+    cudaError_t e;
+    // every buffer at its final size before any work is queued
+    if ((e = grow_buf(&w.basic_row, &w.cap_basic, (size_t)(n + m))) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.L, &w.cap_L, (size_t)m)) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.Lrow, &w.cap_Lrow, (size_t)m)) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.X, &w.cap_X, (size_t)ns * N)) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.Ainv, &w.cap_Ainv, (size_t)ns * ns)) != cudaSuccess) return e;
+    if (!one_chunk && (e = grow_buf(&w.Z, &w.cap_Z, (size_t)mL * N)) != cudaSuccess) return e;
+    if ((e = oz_reserve(w, ns, N, ns)) != cudaSuccess) return e;
+    if ((e = oz_reserve(w, mL, N, ns)) != cudaSuccess) return e;
+
+    if ((e = cudaMemsetAsync(w.basic_row, 0xff, sizeof(int) * (size_t)(n + m), s)) != cudaSuccess)
+        return e;
+    oz_basic_kernel<<<(m + 255) / 256, 256, 0, s>>>(basis, m, w.basic_row);
+    oz_llist_kernel<<<1, 1024, 0, s>>>(w.basic_row, m, n, w.L, w.Lrow);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ns > 0) {
+        oz_ainv_kernel<<<grid_for((long long)ns * ns), 256, 0, s>>>(rb.W, rb.Wp, ns, rb.pivrow, w.Ainv);
+        OzParams p{};
+        p.mode = 0;
+        p.C = w.X;
+        p.ldc = N;
+        p.spin_limit = spin_limit;
+        e = oz_product(SrcDense{w.Ainv, ns}, SrcRefreshB{A, b, rb.R, n, m, sg}, ns, N, ns, p, w,
+                       sms, s);
+        if (e != cudaSuccess) return e;
+        oz_xrows_kernel<<<grid_for((long long)ns * (N - 1)), 256, 0, s>>>(w.X, N, ns, rb.S,
+                                                                           w.basic_row, T32, P);
+    }
+    if (mL > 0) {
+        OzParams p{};
+        p.spin_limit = spin_limit;
+        const SrcGather a2{A, n, w.L, rb.S, sg};
+        if (one_chunk) {
+            p.mode = 1;
+            p.T32 = T32;
+            p.P = P;
+            p.rowmap = w.Lrow;
+            p.rowk = w.L;
+            p.basic_row = w.basic_row;
+            p.Aorig = A;
+            p.n = n;
+            p.m = m;
+            p.sg = sg;
+            e = oz_product(a2, SrcDense{w.X, N}, mL, N, ns, p, w, sms, s);
+        } else {
+            p.mode = 0;
+            p.C = w.Z;
+            p.ldc = N;
+            e = oz_product(a2, SrcDense{w.X, N}, mL, N, ns, p, w, sms, s);
+            if (e == cudaSuccess)
+                oz_yrows_kernel<<<grid_for((long long)mL * (N - 1)), 256, 0, s>>>(
+                    w.Z, N, mL, w.L, w.Lrow, A, n, sg, w.basic_row, T32, P);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gbs
+
+extern "C" lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long long lda,
+                                    const double *B, long long ldb, double *C, long long ldc,
+                                    const lp_options *opt) {
+    using namespace gbs;
+    char msg[256];
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || lda < K || ldb < N || ldc < N) {
+        set_last_error_global("lp_dgemm_emulated: need M, N, K >= 1, non-NULL A, B, C and "
+                              "lda >= K, ldb >= N, ldc >= N");
+        return LP_ERR_INVALID_ARG;
+    }
+    lp_options o;
+    if (opt) o = *opt; else lp_options_default(&o);
+    const void *ptrs[] = {A, B, C};
+    for (const void *q : ptrs) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            set_last_error_global("lp_dgemm_emulated: A, B and C must be device memory");
+            return LP_ERR_INVALID_ARG;
+        }
+    }
+    DeviceRestore restore_;
+    cudaError_t e = cudaSetDevice(o.device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
+    cudaStream_t s = (cudaStream_t)o.cuda_stream;
+    OzWork w;
+    int herr = 0;
+    if (e == cudaSuccess)
+        e = oz_dgemm(A, lda, B, ldb, C, ldc, M, N, K, w, nullptr, sms, o.spin_timeout_cycles, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, w.err, sizeof herr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    oz_work_free(w);
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "lp_dgemm_emulated: %s", cudaGetErrorString(e));
+        set_last_error_global(msg);
+        return LP_ERR_CUDA;
+    }
+    if (herr) {
+        set_last_error_global("lp_dgemm_emulated: a device wait ran out (spin_timeout_cycles)");
+        return LP_ERR_CUDA;
+    }
+    return LP_OK;
+}

@@ -137,3 +137,28 @@ def test_fp32_paper_family_objective(m, n, sense):
     cert = oracle.certificate(A, b, c, x, y, obj, sense=sense)
     scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
     assert max(cert.values()) <= 1e-9 * scale * 1e3, cert
+
+
+@pytest.mark.parametrize("k", [50, 200])
+def test_fp32_8192_objective_vs_oracle(k):
+    """The 8192^2 dense LP of the bench: FP32 tableau with FP64 reinversion
+    every k pivots, objective within 1e-6 of the FP64 oracle's, with an FP64
+    certificate of the reported x and y."""
+    A, b, c = lpgen.dense_lp(8192, 8192, seed=0)
+    o = _oracle_8192()
+    obj, st, it, x, y, _ = _fp32(A, b, c, reinv_k=k)
+    assert st == capi.LP_OPTIMAL
+    assert _rel(obj, o.obj) <= OBJ_TOL, (obj, o.obj)
+    cert = oracle.certificate(A, b, c, x, y, obj)
+    scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
+    assert max(cert.values()) <= 1e-9 * scale * 1e3, cert
+
+
+_O8192 = []
+
+
+def _oracle_8192():
+    if not _O8192:
+        A, b, c = lpgen.dense_lp(8192, 8192, seed=0)
+        _O8192.append(oracle.solve(A, b, c))
+    return _O8192[0]
