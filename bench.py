@@ -476,15 +476,18 @@ def lp8192_extras(args, capi, torch, lps, dev_in, g_obj, g_iters, local):
                 obj, st, it = capi.lp_result(h)
                 wall = time.perf_counter() - t0
                 kms, launches = capi.lp_kernel_time(h)
+                nre, rms, bms = capi.lp_fp32_stats(h)
                 if rep:
-                    runs.append((wall, kms, launches, obj, st, it))
+                    runs.append((wall, kms, launches, obj, st, it, nre, rms, bms))
         finally:
             capi.lp_destroy(h)
         runs.sort()
-        wall, kms, launches, obj, st, it = runs[len(runs) // 2]
+        wall, kms, launches, obj, st, it, nre, rms, bms = runs[len(runs) // 2]
         fp32.append({"reinv_k": k, "status": capi.STATUS_NAMES[st], "pivots": it,
                      "pivots_per_s": round(it / wall, 1), "solve_ms": round(1e3 * wall, 2),
                      "pivot_kernel_ms": round(kms, 2), "pivot_kernel_launches": launches,
+                     "reinversions": nre, "reinversion_ms": round(rms, 2),
+                     "body_refresh_ms": round(bms, 2),
                      "pivot_equivalent_gbs_kernel":
                          round(it * tableau_bytes(8192, 8192, 4) / (kms * 1e-3) / 1e9, 1),
                      "obj": obj,
@@ -493,7 +496,50 @@ def lp8192_extras(args, capi, torch, lps, dev_in, g_obj, g_iters, local):
                      "timing": "wall clock of lp_load + lp_solve + lp_result, inputs in HBM, "
                                "median of %d" % len(runs)})
     out["fp32_reinv"] = fp32
+    out["emulated_fp64_product"] = product_bench(capi, torch, local)
     return out
+
+
+def product_bench(capi, torch, local, m=8192, n=8192, s=334):
+    """The body refresh's big product at the 8192^2 LP's final basis: the
+    (m - s) x s rows of A times the s x (n + m + 1) block, emulated FP64 on the
+    tensor cores (lp_dgemm_emulated), timed with CUDA events on its stream
+    (digit split, product and epilogue).  tensor TFLOP/s counts the 28 bf16
+    digit products; fp64-equivalent TFLOP/s the 2 M N K flops they stand for."""
+    import numpy as np
+    M, N, K = m - s, n + m + 1, s
+    rng = np.random.default_rng(0)
+    A = torch.from_numpy(rng.integers(1, 1001, size=(M, K)).astype(np.float64)).cuda()
+    B = torch.from_numpy(rng.standard_normal((K, N))).cuda()
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    opt = capi.lp_options_default(cuda_stream=stream, device=local)
+    capi.lp_dgemm_emulated(A, B, C, opt)  # grows the workspace
+    times = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        capi.lp_dgemm_emulated(A, B, C, opt)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    ref = (A.cpu().numpy() @ B[:, :256].cpu().numpy())
+    err = float(np.max(np.abs(C[:, :256].cpu().numpy() - ref) / np.maximum(1.0, np.abs(ref))))
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        kind = "measured"
+    except Exception:
+        bf16, kind = 1900.0, "fallback"
+    flops = 2.0 * M * N * K
+    return {"shape": {"M": M, "N": N, "K": K}, "ms": round(ms, 3),
+            "fp64_equivalent_tflops": round(flops / ms / 1e9, 2),
+            "tensor_tflops": round(28 * flops / ms / 1e9, 1),
+            "tensor_frac": round(28 * flops / ms / 1e9 / bf16, 4), "bf16_peak_tflops": bf16,
+            "peak_kind": kind, "fp64_alu_ms_for_the_same_product": round(flops / 1.2586e12 * 1e3, 1),
+            "max_rel_err_vs_numpy_fp64_first_256_columns": err}
 
 
 def run_lpset(args, capi, torch, rank, world, local, dist):

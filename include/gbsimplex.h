@@ -54,10 +54,11 @@
  * primal and dual feasible within the FP64 tolerances; otherwise pivoting
  * continues (dual simplex from a dual-feasible basis, primal simplex from a
  * primal-feasible one), and LP_NUMERICAL ends a run that does not converge.
- * With lp_options.reinv_body (the default) each reinversion also recomputes
- * the tableau's constraint rows B^-1 [A I] in emulated FP64 and rounds them
- * into the FP32 tableau, so pivoting resumes from the correctly rounded
- * tableau of the current basis.  The FP32 pivot sequence need not equal the
+ * With lp_options.reinv_body (the default) each reinversion after which the
+ * tableau is pivoted again also recomputes its constraint rows B^-1 [A I] in
+ * emulated FP64 and rounds them into the FP32 tableau, so pivoting resumes
+ * from the correctly rounded tableau of the current basis (an accepted
+ * optimum's body, never read again, is left as the FP32 pivots made it).  The FP32 pivot sequence need not equal the
  * FP64 one.
  *
  * Conventions
@@ -170,8 +171,12 @@ typedef struct {
     int reinv_body;          /* FP32 mode, single LPs through lp_solve (not the
                                 servers, whose HBM budget has no room for the
                                 products' workspace): 1 (default) = every reinversion
-                                also recomputes the tableau's constraint rows
-                                B^-1 [A I] from the original FP64 data, with
+                                after which the tableau is pivoted again (the
+                                periodic ones, one that sends an FP32 optimum
+                                back to pivoting, and one that ends a call at
+                                the iteration limit) also recomputes the
+                                tableau's constraint rows B^-1 [A I] from the
+                                original FP64 data, with
                                 emulated-FP64 products on the tensor cores (see
                                 lp_dgemm_emulated), so the rounding error of the
                                 FP32 body does not build up; 0 = only the rhs,
@@ -361,8 +366,10 @@ lp_err lp_fp32_stats(lp_handle *h, int *reinversions, double *reinv_ms, double *
  * 2^-53 sum_k |A_ik B_kj|); integer data whose products and sums are exact in
  * FP64 and that need at most 14 bits per row or column of scaled magnitude
  * give exact results.  opt: NULL for the defaults; uses opt->device,
- * opt->cuda_stream and opt->spin_timeout_cycles.  Allocates and frees its own
- * workspace (about 14 (M + N) K bytes); blocking.  Errors:
+ * opt->cuda_stream and opt->spin_timeout_cycles.  Its workspace (about
+ * 14 (M + N) K bytes of digit planes) is kept per device between calls, grown
+ * when a larger product needs it and held until the process exits; calls are
+ * serialised by a lock.  Blocking.  Errors:
  * LP_ERR_INVALID_ARG (sizes, NULL or host pointers), LP_ERR_CUDA (a CUDA call
  * failed or a device wait ran out); the message is lp_last_error(NULL). */
 lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long long lda, const double *B,

@@ -115,6 +115,7 @@ struct lp_handle {
     // FP32 mode: emulated-FP64 products of the body refresh, and its time
     OzWork oz{};
     double body_ms = 0.0;
+    int last_ns = 0;  // structural basics of the last reinversion
 };
 
 namespace {
@@ -629,34 +630,46 @@ lp_err reinvert(lp_handle *h, bool *singular, double *zmin, double *rmin) {
     CUDA_TRY(h, cudaMemcpyAsync(&chk, h->rb.chk, sizeof chk, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaEventRecord(e1, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    float t = 0.0f, tb = 0.0f;
+    float t = 0.0f;
     cudaEventElapsedTime(&t, e0, e1);
-    if (h->prec == PREC_FP32 && h->opt.reinv_body && !h->region && chk.singular == 0) {
-        // the body B^-1 [A I] of the basis just reinverted, from the FP64 data
-        CUDA_TRY(h, cudaEventRecord(e0, s));
-        CUDA_TRY(h, oz_refresh_body(h->dA, h->db, h->sense, m, n, h->dbasis, h->rb, ns,
-                                    static_cast<float *>(h->dT), h->P, h->oz, h->sms,
-                                    h->opt.spin_timeout_cycles, s));
-        int oerr = 0;
-        CUDA_TRY(h, cudaMemcpyAsync(&oerr, h->oz.err, sizeof oerr, cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(h, cudaEventRecord(e1, s));
-        CUDA_TRY(h, cudaStreamSynchronize(s));
-        cudaEventElapsedTime(&tb, e0, e1);
-        if (oerr) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            set_err(h, "reinversion: a wait of the body refresh ran out");
-            return LP_ERR_CUDA;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->reinv_ms += t + tb;
-    h->body_ms += tb;
+    h->reinv_ms += t;
+    h->last_ns = ns;
     h->reinversions += 1;
     *singular = chk.singular != 0;
     *zmin = okey_to_double(chk.zmin_key);
     *rmin = okey_to_double(chk.rhsmin_key);
+    return LP_OK;
+}
+
+// The FP32 tableau's constraint rows B^-1 [A I] recomputed from the FP64 data
+// for the basis of the last reinversion (lp_options.reinv_body), before the
+// tableau is pivoted again.
+lp_err refresh_body(lp_handle *h) {
+    if (h->prec != PREC_FP32 || !h->opt.reinv_body || h->region) return LP_OK;
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    CUDA_TRY(h, cudaEventRecord(e0, s));
+    CUDA_TRY(h, oz_refresh_body(h->dA, h->db, h->sense, h->m, h->n, h->dbasis, h->rb, h->last_ns,
+                                static_cast<float *>(h->dT), h->P, h->oz, h->sms,
+                                h->opt.spin_timeout_cycles, s));
+    int oerr = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&oerr, h->oz.err, sizeof oerr, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaEventRecord(e1, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    float tb = 0.0f;
+    cudaEventElapsedTime(&tb, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->reinv_ms += tb;
+    h->body_ms += tb;
+    if (oerr) {
+        set_err(h, "reinversion: a wait of the body refresh ran out");
+        return LP_ERR_CUDA;
+    }
     return LP_OK;
 }
 
@@ -729,13 +742,15 @@ lp_err solve_fp32(lp_handle *h) {
             const double eps[3] = {h->eps_d, h->eps_p, h->eps_r};
             CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, eps_d), eps,
                                         sizeof eps, cudaMemcpyHostToDevice, s));
+            if ((e = refresh_body(h)) != LP_OK) return e;
             continue;
         }
         if (st == LP_UNBOUNDED || st == LP_INFEASIBLE) {
             final = (lp_status)st;
             break;
         }
-        if (remaining <= 0) {  // ITER_LIMIT
+        if (remaining <= 0) {  // ITER_LIMIT: a later lp_solve pivots on from here
+            if ((e = refresh_body(h)) != LP_OK) return e;
             final = LP_ITER_LIMIT;
             break;
         }
@@ -749,6 +764,7 @@ lp_err solve_fp32(lp_handle *h) {
         // continue with the other rule
         if (rule == 0 && !pfeas && dfeas) rule = 1;
         else if (rule == 1 && !dfeas && pfeas) rule = 0;
+        if ((e = refresh_body(h)) != LP_OK) return e;
     }
     h->pdesc->status = final;
     if (final == LP_TIMEOUT) h->timed_out = true;

@@ -46,6 +46,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "gbs_device.cuh"
 #include "gbs_internal.h"
@@ -61,7 +62,7 @@ constexpr int kOzS = 7;                 // digits per operand
 constexpr int kOzT = 7;                 // bits per digit
 constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 64;
 constexpr int kOzChunkKB = 7;           // K blocks per exact group sum (448 terms)
-constexpr int kOzAStages = 4;
+constexpr int kOzAStages = 7;  // a whole K block of A digit planes in flight
 constexpr int kOzABytes = kOzBM * kOzBK * 2;            // 16 KB: one A digit plane block
 constexpr int kOzBBytes = kOzBN * kOzBK * 2;            // 8 KB: one B digit plane block
 constexpr int kOzBStageBytes = kOzS * kOzBBytes;        // 56 KB: all digit planes of a B block
@@ -236,17 +237,25 @@ struct SrcRefreshB {  // row r: [sg A_l | e_l | sg b_l], l = R[r]
 // floor((eB_k - eA_k) / 2), with eA_k the largest exponent of column k of A
 // and eB_k that of row k of B, brings both to the geometric middle.
 
-// eA_k: largest exponent of column k of A (M x K), one thread per k.
+// eA_k: largest biased exponent of column k of A (M x K), 0 when the column
+// is zero.  A block of 32 x 8 threads takes 32 columns and 64 rows; kA starts
+// at 0 and takes each block's maximum by atomicMax.
 template <class Src>
 __global__ void oz_kexpA_kernel(Src src, int M, int K, int *kA) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    int mx = kNoExp;
-    for (int i = 0; i < M; ++i) {
-        const int ex = exp_of(src.at(i, k));
-        if (ex) mx = max(mx, ex);
+    __shared__ int red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + tx;
+    int mx = 0;
+    if (k < K) {
+        const int i0 = blockIdx.y * 64;
+        for (int i = i0 + ty; i < min(M, i0 + 64); i += 8) mx = max(mx, exp_of(src.at(i, k)));
     }
-    kA[k] = mx;
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && k < K) {
+        for (int r = 1; r < 8; ++r) mx = max(mx, red[r][tx]);
+        if (mx) atomicMax(kA + k, mx);
+    }
 }
 
 // eB_k: largest exponent of row k of B (K x N), one warp per k; then shift_k.
@@ -260,7 +269,7 @@ __global__ void oz_kexpB_kernel(Src src, int K, int N, const int *kA, int *shift
         if (ex) mx = max(mx, ex);
     }
     mx = __reduce_max_sync(0xffffffffu, mx);
-    if (lane == 0) shift[k] = (mx != kNoExp && kA[k] != kNoExp) ? (mx - kA[k]) >> 1 : 0;
+    if (lane == 0) shift[k] = (mx != kNoExp && kA[k] != 0) ? (mx - kA[k]) >> 1 : 0;
 }
 
 // Largest shifted exponent of each row i < M of A over k < K (kNoExp: none).
@@ -342,6 +351,22 @@ __global__ void oz_split_cols_kernel(Src src, int K, int N, int Kp, int Np, cons
     }
 }
 
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// A named barrier that also ANDs a flag over its threads, so that they all
+// take the same branch after it.
+__device__ __forceinline__ bool named_bar_and(int id, int nthreads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\n"
+        "bar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 // ---- the product kernel ----
 struct OzParams {
     int M, N, K, Mp, Np, Kp;
@@ -363,12 +388,33 @@ struct OzParams {
     long long spin_limit;
 };
 
-__device__ __forceinline__ double pow2d(int e) {  // 2^e, e in [-1022, 1023]
-    return __longlong_as_double((long long)(e + 1023) << 52);
-}
 __device__ __forceinline__ float pow2f(int e) {  // 2^e, e in [-126, 127]
     return __int_as_float((e + 127) << 23);
 }
+// f 2^e as a double, assembled from the bits (exact; no FP64 instruction);
+// false when f is subnormal or the result leaves the normal FP64 range.
+__device__ __forceinline__ bool f2d_scaled(float f, int e, double &out) {
+    const unsigned u = __float_as_uint(f);
+    const int fe = (int)((u >> 23) & 0xffu);
+    if (fe == 0) {
+        out = 0.0;
+        return (u & 0x7fffffu) == 0u;
+    }
+    const int de = fe - 127 + 1023 + e;
+    if (de < 1 || de > 2046) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                           ((unsigned long long)de << 52) |
+                                           ((unsigned long long)(u & 0x7fffffu) << 29)));
+    return true;
+}
+
+// sigma_r tau_j 2^-14 (hi + lo): two exact conversions and one FP64 add.
+__device__ __forceinline__ double scaled_sum(float hi, float lo, int e) {
+    double dh, dl;
+    if (f2d_scaled(hi, e, dh) && f2d_scaled(lo, e, dl)) return dh + dl;
+    return ldexp((double)hi + (double)lo, e);
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
@@ -380,6 +426,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                    const OzParams p) {
     extern __shared__ unsigned char oz_smem[];
     __shared__ uint32_t s_tmem;
+    __shared__ int s_colexp[kOzBN], s_brow[kOzBN];
     const uint32_t raw = su32(oz_smem);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t sB = base;                                  // [2][S][64][128 B]
@@ -480,20 +527,26 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     tc_fence_after();
                     const int kb0 = c * kOzChunkKB, kb1 = min(nkb, kb0 + kOzChunkKB);
                     for (int kb = kb0; kb < kb1 && ok; ++kb) {
+                        // (TMA-written shared memory is read by the MMAs, both
+                        // async-proxy operations: the barrier wait orders them)
                         if (!(ok = mbar_wait(full_b(bs), bph, p.err, lim))) break;
-                        tc_fence_after();
+                        // descriptors: B digit plane q of this stage is 8 KB
+                        // (512 descriptor units) after plane 0; each K step of 16
+                        // elements advances a descriptor by 32 bytes (2 units)
+                        const uint64_t bd0 = sw128_desc(sB + bs * kOzBStageBytes);
                         for (int pp = 0; pp < kOzS; ++pp) {
                             if (!(ok = mbar_wait(full_a(as), aph, p.err, lim))) break;
-                            tc_fence_after();
-                            const uint32_t a0 = sA + as * kOzABytes;
-                            for (int q = 0; q < kOzS - pp; ++q) {
-                                const uint32_t b0 = sB + bs * kOzBStageBytes + q * kOzBBytes;
-                                const uint32_t d = tmem + (uint32_t)((pp + q) * kOzBN);
+                            const uint64_t ad = sw128_desc(sA + as * kOzABytes);
+                            const uint32_t first = (kb == kb0 && pp == 0) ? 1u : 0u;
 #pragma unroll
-                                for (int k = 0; k < kOzBK / 16; ++k) {
-                                    const uint32_t acc = (kb == kb0 && pp == 0 && k == 0) ? 0u : 1u;
-                                    tc_mma(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k),
-                                           kOzIdesc, acc);
+                            for (int q = 0; q < kOzS; ++q) {
+                                if (q < kOzS - pp) {
+                                    const uint32_t d = tmem + (uint32_t)((pp + q) * kOzBN);
+                                    const uint64_t bd = bd0 + (uint64_t)(q * (kOzBBytes >> 4));
+                                    tc_mma(d, ad, bd, kOzIdesc, first ^ 1u);
+                                    tc_mma(d, ad + 2, bd + 2, kOzIdesc, 1u);
+                                    tc_mma(d, ad + 4, bd + 4, kOzIdesc, 1u);
+                                    tc_mma(d, ad + 6, bd + 6, kOzIdesc, 1u);
                                 }
                             }
                             tc_commit(empty_a(as));  // the stage frees when these MMAs complete
@@ -524,26 +577,42 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
     } else {
         // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) .. + 31 ----
-        const int lg = warp & 3;
+        const int lg = warp & 3, et = threadIdx.x - 64;
         uint32_t use = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
             const int m0 = (t % nmb) * kOzBM, n0 = (t / nmb) * kOzBN;
             const int r = m0 + lg * 32 + lane;  // this thread's output row
             for (int c = 0; c < nch && ok; ++c) {
-                if (!(ok = mbar_wait(tmem_full, use & 1u, p.err, lim))) break;
+                // all four epilogue warps leave together or go on together
+                // (this barrier also follows the previous tile's reads of
+                // the shared column data)
+                ok = named_bar_and(1, 128, mbar_wait(tmem_full, use & 1u, p.err, lim));
+                if (!ok) break;
                 tc_fence_after();
                 const int Er = r < p.M ? p.rowexp[r] : kNoExp;
+                // the tile's column exponents (and basic rows) in shared
+                // memory, read by every lane at once (a broadcast)
+                if (et < kOzBN) {
+                    const int col = n0 + et;
+                    s_colexp[et] = col < p.N ? p.colexp[col] : kNoExp;
+                    if (p.mode == 1) s_brow[et] = col < p.N - 1 ? p.basic_row[col] : -1;
+                }
+                named_bar(1, 128);
+                const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
                 for (int h = 0; h < kOzBN / 32; ++h) {
                     float hi[32], lo[32];
+                    uint32_t v[2][32];
+                    // the load of group g + 1 is in flight while group g is added
+                    tmem_ld32(tbase + (uint32_t)(h * 32), v[0]);
+                    tmem_ld_wait();
+#pragma unroll
                     for (int g = 0; g < kOzS; ++g) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(g * kOzBN + h * 32), v);
-                        tmem_ld_wait();
+                        if (g + 1 < kOzS) tmem_ld32(tbase + (uint32_t)((g + 1) * kOzBN + h * 32), v[(g + 1) & 1]);
                         const float sc = pow2f(-kOzT * g);
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const float x = __fmul_rn(__uint_as_float(v[j]), sc);  // exact
+                            const float x = __fmul_rn(__uint_as_float(v[g & 1][j]), sc);  // exact
                             if (g == 0) {
                                 hi[j] = x;
                                 lo[j] = 0.0f;
@@ -554,6 +623,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                 lo[j] = __fadd_rn(lo[j], e);
                             }
                         }
+                        tmem_ld_wait();
                     }
                     if (r < p.M) {
                         const int j0 = n0 + h * 32;
@@ -563,49 +633,39 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                             for (int j = 0; j < 32; ++j) {
                                 const int col = j0 + j;
                                 if (col < p.N) {
-                                    const int Fc = p.colexp[col];
+                                    const int Fc = s_colexp[col - n0];
                                     double v = 0.0;
-                                    if (Er != kNoExp && Fc != kNoExp) {
-                                        // scale 2^(Er - 1022 + Fc - 1022 - 14)
-                                        const int e = Er + Fc - 2058;
-                                        if (e >= -1022 && e <= 1023) {
-                                            const double sc = pow2d(e);
-                                            v = fma((double)lo[j], sc, (double)hi[j] * sc);
-                                        } else {
-                                            v = ldexp((double)hi[j] + (double)lo[j], e);
-                                        }
-                                    }
+                                    // scale 2^(Er - 1022 + Fc - 1022 - 14)
+                                    if (Er != kNoExp && Fc != kNoExp)
+                                        v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
                                     if (c == 0) crow[col] = v;
                                     else crow[col] += v;
                                 }
                             }
                         } else {
                             const int ti = p.rowmap[r], k = p.rowk[r];
+                            const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
                             float *trow = p.T32 + (long long)ti * p.P;
                             const double *arow = p.Aorig + (long long)k * p.n;
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const int col = j0 + j;
                                 if (col < p.N - 1) {  // the rhs column comes from the reinversion
-                                    const int br = p.basic_row[col];
+                                    const int br = s_brow[col - n0];
                                     float out;
                                     if (br >= 0) {
                                         out = br == ti ? 1.0f : 0.0f;
                                     } else {
-                                        const double dv = col < p.n ? p.sg * arow[col]
-                                                                    : (col - p.n == k ? 1.0 : 0.0);
-                                        const int Fc = p.colexp[col];
+                                        // sg A_kj by its sign bit (no FP64 multiply)
+                                        const double dv =
+                                            col < p.n ? __longlong_as_double(
+                                                            __double_as_longlong(arow[col]) ^ sgbit)
+                                                      : (col - p.n == k ? 1.0 : 0.0);
+                                        const int Fc = s_colexp[col - n0];
                                         double prod = 0.0;
-                                        if (Er != kNoExp && Fc != kNoExp) {
-                                            const int e = Er + Fc - 2058;
-                                            if (e >= -1022 && e <= 1023) {
-                                                const double sc = pow2d(e);
-                                                prod = fma((double)lo[j], sc, (double)hi[j] * sc);
-                                            } else {
-                                                prod = ldexp((double)hi[j] + (double)lo[j], e);
-                                            }
-                                        }
-                                        out = (float)(dv - prod);
+                                        if (Er != kNoExp && Fc != kNoExp)
+                                            prod = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
+                                        out = __double2float_rn(dv - prod);
                                     }
                                     trow[col] = out;
                                 }
@@ -712,7 +772,8 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
         return cudaErrorInvalidValue;
     int *kA = w.kx, *shift = w.kx + K;
     if (K > 0) {
-        oz_kexpA_kernel<SA><<<(K + 255) / 256, 256, 0, s>>>(srcA, M, K, kA);
+        if ((e = cudaMemsetAsync(kA, 0, sizeof(int) * (size_t)K, s)) != cudaSuccess) return e;
+        oz_kexpA_kernel<SA><<<dim3((K + 31) / 32, (M + 63) / 64), 256, 0, s>>>(srcA, M, K, kA);
         oz_kexpB_kernel<SB><<<(K + 7) / 8, 256, 0, s>>>(srcB, K, N, kA, shift);
     }
     oz_rowexp_kernel<SA><<<(M + 7) / 8, 256, 0, s>>>(srcA, M, K, shift, w.rowexp);
@@ -930,6 +991,12 @@ cudaError_t oz_refresh_body(const double *A, const double *b, int sense, int m, 
 
 }  // namespace gbs
 
+namespace {
+constexpr int kOzMaxDevices = 64;
+std::mutex g_oz_mutex;
+gbs::OzWork g_oz_work[kOzMaxDevices];
+}  // namespace
+
 extern "C" lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long long lda,
                                     const double *B, long long ldb, double *C, long long ldc,
                                     const lp_options *opt) {
@@ -957,13 +1024,19 @@ extern "C" lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long l
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
     cudaStream_t s = (cudaStream_t)o.cuda_stream;
-    OzWork w;
+    if (o.device < 0 || o.device >= kOzMaxDevices) {
+        set_last_error_global("lp_dgemm_emulated: device out of range");
+        return LP_ERR_INVALID_ARG;
+    }
+    // one workspace per device, kept between calls (it only grows), so that
+    // repeated products allocate nothing; calls are serialised
+    std::lock_guard<std::mutex> lock(g_oz_mutex);
+    OzWork &w = g_oz_work[o.device];
     int herr = 0;
     if (e == cudaSuccess)
         e = oz_dgemm(A, lda, B, ldb, C, ldc, M, N, K, w, nullptr, sms, o.spin_timeout_cycles, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, w.err, sizeof herr, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    oz_work_free(w);
     if (e != cudaSuccess) {
         snprintf(msg, sizeof msg, "lp_dgemm_emulated: %s", cudaGetErrorString(e));
         set_last_error_global(msg);

@@ -56,6 +56,24 @@ def paper_lp(m: int, n: int, seed: int = 0, density: float = 0.9):
             return (np.ascontiguousarray(A), np.ascontiguousarray(b), np.ascontiguousarray(c))
 
 
+def nearly_dependent_lp(m: int, n: int, eps: float = 1e-4, seed: int = 0, group: int = 4):
+    """(A, b, c) of an ill-conditioned dense LP: its rows come in groups of
+    `group` that are relative perturbations of size `eps` of one common row,
+    so bases holding several rows of a group have condition numbers near
+    1 / eps.  Feasible and bounded: A > 0 (for eps well below 1), c > 0, and
+    b = A x0 + a small positive slack for x0 >= 0.
+
+    Draw order (``numpy.random.default_rng(seed)``): the common rows (uniform
+    on [1, 100)), the perturbations (standard normal), x0 (uniform on
+    [0, 1)), the slack (uniform on [0, 0.01)), c (uniform on [1, 100))."""
+    rng = np.random.default_rng(seed)
+    base = rng.uniform(1.0, 100.0, size=(m // group + 1, n))
+    A = base[np.arange(m) // group] * (1.0 + eps * rng.standard_normal((m, n)))
+    b = A @ rng.uniform(0.0, 1.0, size=n) + rng.uniform(0.0, 1e-2, size=m)
+    c = rng.uniform(1.0, 100.0, size=n)
+    return (np.ascontiguousarray(A), np.ascontiguousarray(b), np.ascontiguousarray(c))
+
+
 def with_ge_rows(A, b, frac: float = 0.1, seed: int = 0):
     """(A', b') with a fraction of the rows of a positive LP turned into >=
     rows that the origin violates, so that the primal form needs Phase I.

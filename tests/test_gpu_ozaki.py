@@ -133,3 +133,36 @@ def test_body_refresh_matches_definition(family, m, n, sense):
         for i, v in enumerate(basis):
             col = T[:mm, v]
             assert col[i] == 1.0 and np.count_nonzero(col) == 1
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ill_conditioned_family_needs_the_body_refresh(seed):
+    """Rows in groups of four that differ by relative 1e-4 (bases with
+    condition numbers near 1e4): FP32 pivoting whose body is never refreshed
+    drifts until the FP64 checks give up (LP_NUMERICAL, or an objective off by
+    more than 1e-6); with the body recomputed at every reinversion the FP32
+    mode ends at the FP64 oracle's optimum within 1e-6, with an FP64
+    certificate."""
+    A, b, c = lpgen.nearly_dependent_lp(400, 600, eps=1e-4, seed=seed)
+    o = oracle.solve(A, b, c)
+    assert o.status == oracle.OPTIMAL
+    m, n = A.shape
+    out = {}
+    for body in (0, 1):
+        h = capi.lp_create(capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50,
+                                                   reinv_body=body))
+        try:
+            capi.lp_load(h, A, b, c)
+            capi.lp_solve(h)
+            x, y = np.empty(n), np.empty(m)
+            obj, st, it = capi.lp_result(h, x, y)
+        finally:
+            capi.lp_destroy(h)
+        out[body] = (st, obj, x, y)
+    st0, obj0, _, _ = out[0]
+    assert st0 != capi.LP_OPTIMAL or abs(obj0 - o.obj) > 1e-6 * abs(o.obj)
+    st1, obj1, x1, y1 = out[1]
+    assert st1 == capi.LP_OPTIMAL and abs(obj1 - o.obj) <= 1e-6 * abs(o.obj), (st1, obj1, o.obj)
+    cert = oracle.certificate(A, b, c, x1, y1, obj1)
+    scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
+    assert max(cert.values()) <= 1e-9 * scale * 1e3, cert
