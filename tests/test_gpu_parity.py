@@ -366,3 +366,24 @@ def test_paper_family_2048_bitwise(sense):
     A, b, c, o = _paper_case(2048, 2048, sense)
     assert o.status == oracle.OPTIMAL and o.iters > 2000
     assert_same(Run(A, b, c, sense), o)
+
+
+@pytest.mark.parametrize("negzero", [False, True])
+@pytest.mark.parametrize("pipeline", [1, 4, 5])
+def test_zero_pivot_rows_and_signed_zeros(negzero, pipeline):
+    """A sparse primal LP (half of A zero, so pivot rows have long zero runs),
+    with its zeros stored as +0 or, in a second run, as -0 (the update turns
+    some -0 entries into +0, fma(-c, +0, -0) = +0 for c < 0): every pivot and
+    bit as the oracle, signed zeros included."""
+    rng = np.random.default_rng(31)
+    m, n = 700, 900
+    A = rng.integers(1, 100, size=(m, n)).astype(np.float64)
+    A[rng.random((m, n)) < 0.5] = -0.0 if negzero else 0.0
+    for j in range(n):
+        if not np.any(A[:, j] > 0):
+            A[rng.integers(0, m), j] = 1.0
+    b = rng.integers(100, 10000, size=m).astype(np.float64)
+    c = rng.integers(1, 50, size=n).astype(np.float64)
+    o = _oracle(A, b, c)
+    assert o.status == oracle.OPTIMAL
+    assert_same(Run(A, b, c, pipeline=pipeline), o)
