@@ -504,8 +504,11 @@ def product_bench(capi, torch, local, m=8192, n=8192, s=334):
     """The body refresh's big product at the 8192^2 LP's final basis: the
     (m - s) x s rows of A times the s x (n + m + 1) block, emulated FP64 on the
     tensor cores (lp_dgemm_emulated), timed with CUDA events on its stream
-    (digit split, product and epilogue).  tensor TFLOP/s counts the 28 bf16
-    digit products; fp64-equivalent TFLOP/s the 2 M N K flops they stand for."""
+    (digit split, product and epilogue): the 2 M N K FP64 flops it stands
+    for per second, against the FP64 pipe's derived peak.  (How many of the 28
+    bf16 digit products run depends on the data: digit planes that are zero
+    for a whole row or column block are skipped; the tensor-pipe share is in
+    the ncu record under profiles/.)"""
     import numpy as np
     M, N, K = m - s, n + m + 1, s
     rng = np.random.default_rng(0)
@@ -527,18 +530,13 @@ def product_bench(capi, torch, local, m=8192, n=8192, s=334):
     ms = float(np.median(times))
     ref = (A.cpu().numpy() @ B[:, :256].cpu().numpy())
     err = float(np.max(np.abs(C[:, :256].cpu().numpy() - ref) / np.maximum(1.0, np.abs(ref))))
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16 = float(json.load(f)["bf16_tflops"])
-        kind = "measured"
-    except Exception:
-        bf16, kind = 1900.0, "fallback"
+    fp64_peak, how = device_fp64_peak(local)
     flops = 2.0 * M * N * K
-    return {"shape": {"M": M, "N": N, "K": K}, "ms": round(ms, 3),
+    return {"shape": {"M": M, "N": N, "K": K},
+            "data": "A integers in [1, 1000] (the LP's own data), B standard normal", "ms": round(ms, 3),
             "fp64_equivalent_tflops": round(flops / ms / 1e9, 2),
-            "tensor_tflops": round(28 * flops / ms / 1e9, 1),
-            "tensor_frac": round(28 * flops / ms / 1e9 / bf16, 4), "bf16_peak_tflops": bf16,
-            "peak_kind": kind, "fp64_alu_ms_for_the_same_product": round(flops / 1.2586e12 * 1e3, 1),
+            "vs_fp64_pipe_peak": round(flops / ms / 1e9 / fp64_peak, 2), "fp64_peak_kind": how,
+            "fp64_pipe_ms_for_the_same_product": round(flops / (fp64_peak * 1e12) * 1e3, 1),
             "max_rel_err_vs_numpy_fp64_first_256_columns": err}
 
 

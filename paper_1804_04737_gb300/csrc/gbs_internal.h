@@ -319,7 +319,8 @@ struct OzWork {
     void *asl = nullptr, *bsl = nullptr;       // bf16 digit planes of A and B
     int *rowexp = nullptr, *colexp = nullptr;  // row / column exponents
     int *kx = nullptr;                         // inner exponents and balancing shifts
-    size_t cap_asl = 0, cap_bsl = 0, cap_rowexp = 0, cap_colexp = 0, cap_kx = 0;
+    int *pmask = nullptr;                      // nonzero digit planes per block
+    size_t cap_asl = 0, cap_bsl = 0, cap_rowexp = 0, cap_colexp = 0, cap_kx = 0, cap_pmask = 0;
     // body refresh
     double *X = nullptr, *Ainv = nullptr, *Z = nullptr;
     int *basic_row = nullptr, *L = nullptr, *Lrow = nullptr;

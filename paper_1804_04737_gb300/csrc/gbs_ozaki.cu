@@ -302,9 +302,11 @@ __global__ void oz_colexp_kernel(Src src, int K, int N, const int *shift, int *c
 // A digit planes: out[p][i][k] (Mp x Kp per plane), zero in the padding.
 template <class Src>
 __global__ void oz_split_rows_kernel(Src src, int M, int K, int Mp, int Kp, const int *rowexp,
-                                     const int *shift, __nv_bfloat16 *out) {
+                                     const int *shift, __nv_bfloat16 *out, int *pmask) {
     const long long total = (long long)Mp * Kp;
     const long long plane = total;
+    // (total is a multiple of 32 and Kp of 64: the lanes of a warp stay
+    // together and take one row of one 128-row block)
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(e / Kp), k = (int)(e - (long long)i * Kp);
@@ -315,8 +317,14 @@ __global__ void oz_split_rows_kernel(Src src, int M, int K, int Mp, int Kp, cons
 #pragma unroll
             for (int p = 0; p < kOzS; ++p) d[p] = 0;
         }
+        unsigned nz = 1u;  // plane 0 always counts (it initialises the accumulators)
 #pragma unroll
-        for (int p = 0; p < kOzS; ++p) out[p * plane + e] = __float2bfloat16_rn((float)d[p]);
+        for (int p = 0; p < kOzS; ++p) {
+            out[p * plane + e] = __float2bfloat16_rn((float)d[p]);
+            nz |= d[p] != 0 ? 1u << p : 0u;
+        }
+        nz = __reduce_or_sync(0xffffffffu, nz);
+        if ((threadIdx.x & 31) == 0) atomicOr(pmask + i / kOzBM, (int)nz);
     }
 }
 
@@ -324,10 +332,14 @@ __global__ void oz_split_rows_kernel(Src src, int M, int K, int Mp, int Kp, cons
 // through a 32 x 32 tile in shared memory (reads along j, writes along k).
 template <class Src>
 __global__ void oz_split_cols_kernel(Src src, int K, int N, int Kp, int Np, const int *colexp,
-                                     const int *shift, __nv_bfloat16 *out) {
+                                     const int *shift, __nv_bfloat16 *out, int *pmask) {
     __shared__ __nv_bfloat16 tile[kOzS][32][33];
+    __shared__ int s_nz;
     const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    if (threadIdx.x == 0) s_nz = 1;  // plane 0 always counts
+    __syncthreads();
+    unsigned nz = 0u;
     for (int r = ty; r < 32; r += 8) {
         const int k = k0 + r, j = j0 + tx;
         int d[kOzS];
@@ -338,9 +350,16 @@ __global__ void oz_split_cols_kernel(Src src, int K, int N, int Kp, int Np, cons
             for (int p = 0; p < kOzS; ++p) d[p] = 0;
         }
 #pragma unroll
-        for (int p = 0; p < kOzS; ++p) tile[p][r][tx] = __float2bfloat16_rn((float)d[p]);
+        for (int p = 0; p < kOzS; ++p) {
+            tile[p][r][tx] = __float2bfloat16_rn((float)d[p]);
+            nz |= d[p] != 0 ? 1u << p : 0u;
+        }
     }
+    nz = __reduce_or_sync(0xffffffffu, nz);
+    if (tx == 0 && nz) atomicOr(&s_nz, (int)nz);
     __syncthreads();
+    // the 32 columns of this block lie in one 64-column block of B
+    if (threadIdx.x == 0) atomicOr(pmask + j0 / kOzBN, s_nz);
     const size_t plane = (size_t)Np * Kp;
     for (int r = ty; r < 32; r += 8) {
         const int j = j0 + r, k = k0 + tx;
@@ -371,6 +390,9 @@ __device__ __forceinline__ bool named_bar_and(int id, int nthreads, bool v) {
 struct OzParams {
     int M, N, K, Mp, Np, Kp;
     const int *rowexp, *colexp;
+    // digit planes with a nonzero digit, per 128-row block of A and per
+    // 64-column block of B (bit p: plane p; plane 0 always set)
+    const int *amask, *bmask;
     int mode;  // 0: C = A B (FP64, rows < M, cols < N); 1: refresh rows into the FP32 tableau
     double *C;
     long long ldc;
@@ -479,17 +501,22 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 const int m0 = (t % nmb) * kOzBM, n0 = (t / nmb) * kOzBN;
+                // planes that are zero for the whole row (column) block are
+                // neither loaded nor multiplied
+                const int ma = p.amask[m0 / kOzBM], mb = p.bmask[n0 / kOzBN];
                 for (int kb = 0; kb < nkb && ok; ++kb) {
                     if (!(ok = mbar_wait(empty_b(bs), bph ^ 1u, p.err, lim))) break;
-                    mbar_expect_tx(full_b(bs), kOzBStageBytes);
+                    mbar_expect_tx(full_b(bs), (uint32_t)(__popc(mb) * kOzBBytes));
                     for (int q = 0; q < kOzS; ++q)
-                        tma_load_2d(sB + bs * kOzBStageBytes + q * kOzBBytes, &tmB, kb * kOzBK,
-                                    q * p.Np + n0, full_b(bs));
+                        if ((mb >> q) & 1)
+                            tma_load_2d(sB + bs * kOzBStageBytes + q * kOzBBytes, &tmB, kb * kOzBK,
+                                        q * p.Np + n0, full_b(bs));
                     if (++bs == 2) {
                         bs = 0;
                         bph ^= 1u;
                     }
                     for (int pp = 0; pp < kOzS; ++pp) {
+                        if (!((ma >> pp) & 1)) continue;
                         if (!(ok = mbar_wait(empty_a(as), aph ^ 1u, p.err, lim))) break;
                         mbar_expect_tx(full_a(as), kOzABytes);
                         tma_load_2d(sA + as * kOzABytes, &tmA, kb * kOzBK, pp * p.Mp + m0, full_a(as));
@@ -521,11 +548,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             uint32_t aph = 0, bph = 0, use = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int ma = p.amask[(t % nmb)], mb = p.bmask[(t / nmb)];
                 for (int c = 0; c < nch && ok; ++c) {
                     // the epilogue has drained the accumulators of the last use
                     if (!(ok = mbar_wait(tmem_empty, (use & 1u) ^ 1u, p.err, lim))) break;
                     tc_fence_after();
                     const int kb0 = c * kOzChunkKB, kb1 = min(nkb, kb0 + kOzChunkKB);
+                    uint32_t inited = 0u;  // accumulator groups written in this chunk
                     for (int kb = kb0; kb < kb1 && ok; ++kb) {
                         // (TMA-written shared memory is read by the MMAs, both
                         // async-proxy operations: the barrier wait orders them)
@@ -535,15 +564,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         // elements advances a descriptor by 32 bytes (2 units)
                         const uint64_t bd0 = sw128_desc(sB + bs * kOzBStageBytes);
                         for (int pp = 0; pp < kOzS; ++pp) {
+                            if (!((ma >> pp) & 1)) continue;
                             if (!(ok = mbar_wait(full_a(as), aph, p.err, lim))) break;
                             const uint64_t ad = sw128_desc(sA + as * kOzABytes);
-                            const uint32_t first = (kb == kb0 && pp == 0) ? 1u : 0u;
 #pragma unroll
                             for (int q = 0; q < kOzS; ++q) {
-                                if (q < kOzS - pp) {
+                                if (q < kOzS - pp && ((mb >> q) & 1)) {
+                                    // the first product into a group of this chunk
+                                    // overwrites it
+                                    const uint32_t acc0 = (inited >> (pp + q)) & 1u;
+                                    inited |= 1u << (pp + q);
                                     const uint32_t d = tmem + (uint32_t)((pp + q) * kOzBN);
                                     const uint64_t bd = bd0 + (uint64_t)(q * (kOzBBytes >> 4));
-                                    tc_mma(d, ad, bd, kOzIdesc, first ^ 1u);
+                                    tc_mma(d, ad, bd, kOzIdesc, acc0);
                                     tc_mma(d, ad + 2, bd + 2, kOzIdesc, 1u);
                                     tc_mma(d, ad + 4, bd + 4, kOzIdesc, 1u);
                                     tc_mma(d, ad + 6, bd + 6, kOzIdesc, 1u);
@@ -600,6 +633,15 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 }
                 named_bar(1, 128);
                 const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
+                // the accumulator groups the MMA issuer wrote for this tile
+                uint32_t gm = 0u;
+                {
+                    const int ma = p.amask[m0 / kOzBM], mb = p.bmask[n0 / kOzBN];
+                    for (int pa = 0; pa < kOzS; ++pa)
+                        if ((ma >> pa) & 1)
+                            for (int qb = 0; qb < kOzS - pa; ++qb)
+                                if ((mb >> qb) & 1) gm |= 1u << (pa + qb);
+                }
                 for (int h = 0; h < kOzBN / 32; ++h) {
                     float hi[32], lo[32];
                     uint32_t v[2][32];
@@ -612,7 +654,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         const float sc = pow2f(-kOzT * g);
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const float x = __fmul_rn(__uint_as_float(v[g & 1][j]), sc);  // exact
+                            // (a group no digit pair wrote holds stale columns: zero)
+                            const float x = ((gm >> g) & 1u)
+                                                ? __fmul_rn(__uint_as_float(v[g & 1][j]), sc)  // exact
+                                                : 0.0f;
                             if (g == 0) {
                                 hi[j] = x;
                                 lo[j] = 0.0f;
@@ -754,6 +799,8 @@ cudaError_t oz_reserve(OzWork &w, int M, int N, int K) {
     if ((e = grow_buf(&w.rowexp, &w.cap_rowexp, (size_t)std::max(M, 1))) != cudaSuccess) return e;
     if ((e = grow_buf(&w.colexp, &w.cap_colexp, (size_t)std::max(N, 1))) != cudaSuccess) return e;
     if ((e = grow_buf(&w.kx, &w.cap_kx, (size_t)2 * std::max(K, 1))) != cudaSuccess) return e;
+    if ((e = grow_buf(&w.pmask, &w.cap_pmask, (size_t)(Mp / kOzBM + Np / kOzBN))) != cudaSuccess)
+        return e;
     if (!w.err && (e = cudaMalloc((void **)&w.err, sizeof(int))) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -768,9 +815,14 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
               Kp = round_up(std::max(K, 1), kOzBK);
     cudaError_t e;
     if (w.cap_asl < (size_t)kOzS * Mp * Kp || w.cap_bsl < (size_t)kOzS * Np * Kp ||
-        w.cap_rowexp < (size_t)M || w.cap_colexp < (size_t)N || w.cap_kx < (size_t)2 * K || !w.err)
+        w.cap_rowexp < (size_t)M || w.cap_colexp < (size_t)N || w.cap_kx < (size_t)2 * K ||
+        w.cap_pmask < (size_t)(Mp / kOzBM + Np / kOzBN) || !w.err)
         return cudaErrorInvalidValue;
     int *kA = w.kx, *shift = w.kx + K;
+    int *amask = w.pmask, *bmask = w.pmask + Mp / kOzBM;
+    if ((e = cudaMemsetAsync(w.pmask, 0, sizeof(int) * (size_t)(Mp / kOzBM + Np / kOzBN), s)) !=
+        cudaSuccess)
+        return e;
     if (K > 0) {
         if ((e = cudaMemsetAsync(kA, 0, sizeof(int) * (size_t)K, s)) != cudaSuccess) return e;
         oz_kexpA_kernel<SA><<<dim3((K + 31) / 32, (M + 63) / 64), 256, 0, s>>>(srcA, M, K, kA);
@@ -782,10 +834,10 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
         const long long total = (long long)Mp * Kp;
         const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * sms * 8);
         oz_split_rows_kernel<SA><<<blocks, 256, 0, s>>>(srcA, M, K, Mp, Kp, w.rowexp, shift,
-                                                         static_cast<__nv_bfloat16 *>(w.asl));
+                                                         static_cast<__nv_bfloat16 *>(w.asl), amask);
     }
     oz_split_cols_kernel<SB><<<dim3(Np / 32, Kp / 32), 256, 0, s>>>(
-        srcB, K, N, Kp, Np, w.colexp, shift, static_cast<__nv_bfloat16 *>(w.bsl));
+        srcB, K, N, Kp, Np, w.colexp, shift, static_cast<__nv_bfloat16 *>(w.bsl), bmask);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     CUtensorMap ma, mb;
     if ((e = make_map(&ma, w.asl, (long long)kOzS * Mp, Kp, kOzBM)) != cudaSuccess) return e;
@@ -798,6 +850,8 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
     p.Kp = Kp;
     p.rowexp = w.rowexp;
     p.colexp = w.colexp;
+    p.amask = amask;
+    p.bmask = bmask;
     if (!p.err) p.err = w.err;
     if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), s)) != cudaSuccess) return e;
     if (p.mode == 1 && Kp > kOzChunkKB * kOzBK) return cudaErrorInvalidValue;  // one chunk only
@@ -812,7 +866,7 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
 }  // namespace
 
 void oz_work_free(OzWork &w) {
-    void *ps[] = {w.asl, w.bsl, w.rowexp, w.colexp, w.kx, w.X, w.Ainv, w.Z, w.basic_row, w.L, w.Lrow, w.err};
+    void *ps[] = {w.asl, w.bsl, w.rowexp, w.colexp, w.kx, w.pmask, w.X, w.Ainv, w.Z, w.basic_row, w.L, w.Lrow, w.err};
     for (void *q : ps)
         if (q) cudaFree(q);
     w = OzWork{};
