@@ -62,13 +62,15 @@ constexpr int kOzS = 7;                 // digits per operand
 constexpr int kOzT = 7;                 // bits per digit
 constexpr int kOzBM = 128, kOzBN = 64, kOzBK = 64;
 constexpr int kOzChunkKB = 7;           // K blocks per exact group sum (448 terms)
-constexpr int kOzAStages = 7;  // a whole K block of A digit planes in flight
+constexpr int kOzAStages = 4;
 constexpr int kOzABytes = kOzBM * kOzBK * 2;            // 16 KB: one A digit plane block
 constexpr int kOzBBytes = kOzBN * kOzBK * 2;            // 8 KB: one B digit plane block
 constexpr int kOzBStageBytes = kOzS * kOzBBytes;        // 56 KB: all digit planes of a B block
 constexpr int kOzTmemCols = 512;                        // S x 64 = 448 used
 constexpr int kOzThreads = 192;
-constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + 256;
+constexpr int kOzStg = 33;                              // staging row pitch (doubles)
+constexpr int kOzStgBytes = 4 * 32 * kOzStg * 8;        // 32 rows per epilogue warp, FP64
+constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + kOzStgBytes + 256;
 
 static_assert(kOzS * kOzBN <= kOzTmemCols, "accumulators must fit tensor memory");
 static_assert(kOzT * kOzS == 49, "the digit extraction below assumes 49 bits");
@@ -430,11 +432,15 @@ __device__ __forceinline__ bool f2d_scaled(float f, int e, double &out) {
     return true;
 }
 
+// (hi + lo) 2^e outside the normal range (rare; kept out of line)
+__device__ __noinline__ double scaled_sum_slow(float hi, float lo, int e) {
+    return ldexp((double)hi + (double)lo, e);
+}
 // sigma_r tau_j 2^-14 (hi + lo): two exact conversions and one FP64 add.
 __device__ __forceinline__ double scaled_sum(float hi, float lo, int e) {
     double dh, dl;
     if (f2d_scaled(hi, e, dh) && f2d_scaled(lo, e, dl)) return dh + dl;
-    return ldexp((double)hi + (double)lo, e);
+    return scaled_sum_slow(hi, lo, e);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -453,7 +459,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t sB = base;                                  // [2][S][64][128 B]
     const uint32_t sA = base + 2 * kOzBStageBytes;             // [4][128][128 B]
-    const uint32_t sBar = sA + kOzAStages * kOzABytes;         // barriers, 8 bytes each
+    const uint32_t sStg = sA + kOzAStages * kOzABytes;         // epilogue staging
+    const uint32_t sBar = sStg + kOzStgBytes;                  // barriers, 8 bytes each
     auto full_a = [&](int s) { return sBar + 8u * s; };
     auto empty_a = [&](int s) { return sBar + 8u * (kOzAStages + s); };
     auto full_b = [&](int s) { return sBar + 8u * (2 * kOzAStages + s); };
@@ -611,6 +618,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     } else {
         // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) .. + 31 ----
         const int lg = warp & 3, et = threadIdx.x - 64;
+        double *stg = reinterpret_cast<double *>(oz_smem + (sStg - raw)) + lg * 32 * kOzStg;
         uint32_t use = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
@@ -644,19 +652,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 }
                 for (int h = 0; h < kOzBN / 32; ++h) {
                     float hi[32], lo[32];
-                    uint32_t v[2][32];
-                    // the load of group g + 1 is in flight while group g is added
-                    tmem_ld32(tbase + (uint32_t)(h * 32), v[0]);
-                    tmem_ld_wait();
 #pragma unroll
                     for (int g = 0; g < kOzS; ++g) {
-                        if (g + 1 < kOzS) tmem_ld32(tbase + (uint32_t)((g + 1) * kOzBN + h * 32), v[(g + 1) & 1]);
+                        uint32_t v[32];
+                        tmem_ld32(tbase + (uint32_t)(g * kOzBN + h * 32), v);
+                        tmem_ld_wait();
                         const float sc = pow2f(-kOzT * g);
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             // (a group no digit pair wrote holds stale columns: zero)
                             const float x = ((gm >> g) & 1u)
-                                                ? __fmul_rn(__uint_as_float(v[g & 1][j]), sc)  // exact
+                                                ? __fmul_rn(__uint_as_float(v[j]), sc)  // exact
                                                 : 0.0f;
                             if (g == 0) {
                                 hi[j] = x;
@@ -668,55 +674,75 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                 lo[j] = __fadd_rn(lo[j], e);
                             }
                         }
-                        tmem_ld_wait();
                     }
-                    if (r < p.M) {
-                        const int j0 = n0 + h * 32;
-                        if (p.mode == 0) {
-                            double *crow = p.C + (long long)r * p.ldc;
+                    // The products of this thread's row go to the warp's slice
+                    // of the staging buffer (row = lane); the warp then walks its
+                    // 32 rows with lane = column, so that the data it reads (C,
+                    // or the original row of A) and the results it writes are
+                    // whole coalesced row segments.
+                    const int j0 = n0 + h * 32;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int col = j0 + j;
-                                if (col < p.N) {
-                                    const int Fc = s_colexp[col - n0];
-                                    double v = 0.0;
-                                    // scale 2^(Er - 1022 + Fc - 1022 - 14)
-                                    if (Er != kNoExp && Fc != kNoExp)
-                                        v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
-                                    if (c == 0) crow[col] = v;
-                                    else crow[col] += v;
-                                }
+                    for (int j = 0; j < 32; ++j) {
+                        const int Fc = s_colexp[h * 32 + j];
+                        double v = 0.0;
+                        // scale 2^(Er - 1022 + Fc - 1022 - 14)
+                        if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
+                        stg[lane * kOzStg + j] = v;
+                    }
+                    __syncwarp();
+                    const int col = j0 + lane;
+                    if (p.mode == 0) {
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int row = m0 + lg * 32 + rr;
+                            if (row >= p.M) break;
+                            if (col < p.N) {
+                                double *q = p.C + (long long)row * p.ldc + col;
+                                const double v = stg[rr * kOzStg + lane];
+                                *q = c == 0 ? v : *q + v;
                             }
-                        } else {
-                            const int ti = p.rowmap[r], k = p.rowk[r];
-                            const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
-                            float *trow = p.T32 + (long long)ti * p.P;
-                            const double *arow = p.Aorig + (long long)k * p.n;
+                        }
+                    } else {
+                        const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
+                        const int br = s_brow[h * 32 + lane];
+                        // the tableau row and the constraint of each of the warp's
+                        // rows, one per lane, passed round by shuffles; the original
+                        // rows of A are read eight rows at a time
+                        const int myrow = m0 + lg * 32 + lane;
+                        const int my_ti = myrow < p.M ? p.rowmap[myrow] : 0;
+                        const int my_k = myrow < p.M ? p.rowk[myrow] : 0;
+                        for (int rr0 = 0; rr0 < 32; rr0 += 8) {
+                            double dv[8];
+                            int tiv[8], kv[8];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int col = j0 + j;
-                                if (col < p.N - 1) {  // the rhs column comes from the reinversion
-                                    const int br = s_brow[col - n0];
+                            for (int u = 0; u < 8; ++u) {
+                                tiv[u] = __shfl_sync(0xffffffffu, my_ti, rr0 + u);
+                                kv[u] = __shfl_sync(0xffffffffu, my_k, rr0 + u);
+                                const int row = m0 + lg * 32 + rr0 + u;
+                                dv[u] = (row < p.M && col < p.n)
+                                            ? __ldg(p.Aorig + (long long)kv[u] * p.n + col)
+                                            : 0.0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int row = m0 + lg * 32 + rr0 + u;
+                                // the rhs column comes from the reinversion
+                                if (row < p.M && col < p.N - 1) {
                                     float out;
                                     if (br >= 0) {
-                                        out = br == ti ? 1.0f : 0.0f;
+                                        out = br == tiv[u] ? 1.0f : 0.0f;
                                     } else {
                                         // sg A_kj by its sign bit (no FP64 multiply)
-                                        const double dv =
-                                            col < p.n ? __longlong_as_double(
-                                                            __double_as_longlong(arow[col]) ^ sgbit)
-                                                      : (col - p.n == k ? 1.0 : 0.0);
-                                        const int Fc = s_colexp[col - n0];
-                                        double prod = 0.0;
-                                        if (Er != kNoExp && Fc != kNoExp)
-                                            prod = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
-                                        out = __double2float_rn(dv - prod);
+                                        const double d =
+                                            col < p.n ? __longlong_as_double(__double_as_longlong(dv[u]) ^ sgbit)
+                                                      : (col - p.n == kv[u] ? 1.0 : 0.0);
+                                        out = __double2float_rn(d - stg[(rr0 + u) * kOzStg + lane]);
                                     }
-                                    trow[col] = out;
+                                    p.T32[(long long)tiv[u] * p.P + col] = out;
                                 }
                             }
                         }
                     }
+                    __syncwarp();  // the slice is free again
                 }
                 tc_fence_before();
                 __syncwarp();

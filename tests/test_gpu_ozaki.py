@@ -166,3 +166,21 @@ def test_ill_conditioned_family_needs_the_body_refresh(seed):
     cert = oracle.certificate(A, b, c, x1, y1, obj1)
     scale = max(1.0, abs(o.obj), float(np.max(np.abs(b))), float(np.max(np.abs(c))))
     assert max(cert.values()) <= 1e-9 * scale * 1e3, cert
+
+
+def test_digit_planes_skipped_per_block():
+    """Row blocks of A and column blocks of B of integer data need two of the
+    seven digit planes, real-valued ones all seven; the product skips the
+    planes a block does not need.  Integer block times integer block is
+    exact, every entry within the digit bound."""
+    rng = np.random.default_rng(77)
+    M, N, K = 300, 200, 250
+    A = rng.standard_normal((M, K))
+    A[:128] = rng.integers(-1000, 1001, size=(128, K))   # the first row block
+    B = rng.standard_normal((K, N))
+    B[:, 64:128] = rng.integers(-1000, 1001, size=(K, 64))  # the second column block
+    C = _emulated(A, B)
+    ref = A @ B
+    assert np.array_equal(C[:128, 64:128], ref[:128, 64:128])
+    bound = 2.0 ** -44 * K * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :]
+    assert np.all(np.abs(C - ref) <= bound)
