@@ -16,11 +16,13 @@ two buffers) is larger than L2, so nothing survives in L2 from one step to
 the next.  `e2e` is the same metric through the C ABI with host buffers:
 lp_load from pinned host memory, lp_solve, lp_result into pinned host memory,
 wall clock.  `roofline` is that of the pivot kernel (one launch per solve):
-the FP64 FMA rate (one fma per tableau element and pivot) and the DRAM bytes
-it moves (from an ncu record of the same launch), the larger fraction
-leading; pivot-equivalent GB/s (2 x tableau bytes per pivot) is reported
-beside them, not as a bound, because two pivots share one pass over the
-tableau.
+the FP64 FMA rate of the fmas it executes (one per updated tableau element
+and pivot; the two-pivot primal kernel leaves in place the column vectors
+whose entries in both pivot rows of a pass are zero, and counts what it
+updates) and the DRAM bytes it moves (from an ncu record of the same
+launch), the larger fraction leading; pivot-equivalent GB/s (2 x tableau
+bytes per pivot) is reported beside them, not as a bound: two pivots share
+one pass over the tableau, and vectors left in place are not moved.
 
 Other workloads (--workload): lp2048set (2048^2 primal and dual form,
 512 x 4096, 4096 x 512), paperset (the same shapes from the paper's random
@@ -590,7 +592,7 @@ def run_lpset(args, capi, torch, rank, world, local, dist):
             if st != capi.LP_OPTIMAL:
                 raise RuntimeError("solve ended with status %s" % capi.STATUS_NAMES[st])
             kms, _ = capi.lp_kernel_time(h)
-            stats.append((it, kms, obj))
+            stats.append((it, kms, obj, capi.lp_update_counts(h)))
         ev1.synchronize()
         return ev0.elapsed_time(ev1), stats
 
@@ -600,25 +602,34 @@ def run_lpset(args, capi, torch, rank, world, local, dist):
     if dist:
         dist.barrier()
     step_ms, pivots, kernel_ms, alg_bytes = [], 0, 0.0, 0.0
-    per_kernel = {}  # name -> [launches, ms, algorithmic bytes, pivots, flops]
+    # name -> [launches, ms, algorithmic bytes, pivots, flops, executed flops,
+    #          constraint-row entries updated, left in place]
+    per_kernel = {}
     last = None
     with Clocks(local) as clk:
         for _ in range(args.steps):
             ms, stats = device_step()
             step_ms.append(ms)
             last = stats
-            for (it, kms, _), (_, A, _b, _c, sense) in zip(stats, lps):
+            for (it, kms, _, (upd, kept)), (_, A, _b, _c, sense) in zip(stats, lps):
                 m, n = A.shape
                 pivots += it
                 kernel_ms += kms
                 by = it * tableau_bytes(m, n)
                 alg_bytes += by
-                rec = per_kernel.setdefault(kernel_of(m, n, sense), [0, 0.0, 0.0, 0, 0.0])
+                rec = per_kernel.setdefault(kernel_of(m, n, sense),
+                                            [0, 0.0, 0.0, 0, 0.0, 0.0, 0, 0])
                 rec[0] += 1
                 rec[1] += kms
                 rec[2] += by
                 rec[3] += it
                 rec[4] += it * tableau_flops(m, n)
+                # the fmas executed: the updated constraint-row entries (the
+                # two-pivot primal kernel counts them) and the objective row
+                pitch = (n + m + 1 + 31) // 32 * 32
+                rec[5] += 2 * (upd + it * pitch) if upd + kept else it * tableau_flops(m, n)
+                rec[6] += upd
+                rec[7] += kept
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -665,15 +676,16 @@ def run_lpset(args, capi, torch, rank, world, local, dist):
 
     def roofline_of(name):
         """The pivot kernel's two real rooflines, per launch over its mean
-        CUDA-event duration: FP64 FMA (one fma per element and pivot) and the
-        DRAM bytes it moves (ncu record); the larger fraction leads.
-        Pivot-equivalent GB/s (2 x tableau bytes per pivot) is reported too;
-        it is not a bound, since two pivots share one pass over the tableau."""
-        launches, ms, by, piv, flops = per_kernel[name]
+        CUDA-event duration: FP64 FMA (the fmas it executes: one per updated
+        element and pivot) and the DRAM bytes it moves (ncu record); the
+        larger fraction leads.  Pivot-equivalent GB/s (2 x tableau bytes per
+        pivot) is reported too; it is not a bound, since two pivots share one
+        pass over the tableau and vectors left in place are not moved."""
+        launches, ms, by, piv, flops, xflops, upd, kept = per_kernel[name]
         sec = ms * 1e-3
         traffic = kernel_traffic(wname, name)
-        fma = {"achieved": round(flops / sec / 1e12, 4), "peak": round(fp64_peak, 4),
-               "unit": "TFLOP/s", "frac": round(flops / sec / 1e12 / fp64_peak, 4),
+        fma = {"achieved": round(xflops / sec / 1e12, 4), "peak": round(fp64_peak, 4),
+               "unit": "TFLOP/s", "frac": round(xflops / sec / 1e12 / fp64_peak, 4),
                "peak_kind": fp64_how}
         hbm = None
         if traffic:
@@ -689,6 +701,8 @@ def run_lpset(args, capi, torch, rank, world, local, dist):
                 "mean_launch_ms": round(ms / launches, 4),
                 "algorithmic_bytes_per_launch": round(by / launches),
                 "flops_per_launch": round(flops / launches),
+                "executed_flops_per_launch": round(xflops / launches),
+                "updated_fraction": round(upd / (upd + kept), 4) if upd + kept else 1.0,
                 "fp64_fma": fma, "hbm_moved": hbm,
                 "pivot_equivalent_gbs": round(by / sec / 1e9, 1),
                 "share_of_pivot_kernel_time": round(ms / kernel_ms, 4)}

@@ -182,6 +182,23 @@ typedef struct {
                                 FP32 body does not build up; 0 = only the rhs,
                                 the duals and the objective row.  Batches do
                                 the latter.                                     */
+    int zero_skip;           /* FP64 two-pivot primal kernel (pipeline 1, 4, 5 on
+                                tableaus of at least 2^19 elements, LP_MAX_LE
+                                without Phase I, m >= n / 4): 1 (default) = each CTA owns a
+                                run of the structural columns and one of the
+                                slack and rhs columns, and a pass leaves in
+                                place the 16-byte column vectors whose entries
+                                in both its pivot rows are zeros (the slack
+                                columns of rows whose slack is still basic):
+                                Step 5 leaves them bit for bit as they are
+                                while no constraint row holds a -0 and the
+                                pivot columns are finite, which the kernel
+                                tracks (a -0 in A or b turns it off).  Each
+                                vector's rows live in one of the two tableau
+                                buffers; the launch ends with one buffer
+                                holding all of them.  0 = every vector
+                                updated in every pass.  Same pivots and bits
+                                either way.                                     */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
@@ -348,6 +365,13 @@ lp_err lp_batch_stats(double *kernel_ms, long long *pivots, int *ctas, int *thre
 lp_err lp_solve_noalloc(int m, int n, const double *A, const double *b, const double *c,
                         lp_sense sense, const lp_options *opt, double *x, double *y,
                         double *obj, lp_status *status, long long *iters);
+
+/* Constraint-row entries the two-pivot primal kernel updated (*updated,
+ * each read, updated and written) and left in place (*in_place, see
+ * lp_options.zero_skip), in 16-byte vectors times pivots, summed over the
+ * solves since lp_load (the objective row, always updated, not counted).
+ * Both are 0 for the other kernels.  Either output may be NULL. */
+lp_err lp_update_counts(lp_handle *h, long long *updated, long long *in_place);
 
 /* Reinversions of the last FP32 solve, their device time in milliseconds,
  * and the part of it spent recomputing the tableau body (0 with reinv_body

@@ -50,6 +50,7 @@ class lp_options(ctypes.Structure):
         ("solo_elems", ctypes.c_longlong),
         ("time_limit_s", ctypes.c_double),
         ("reinv_body", ctypes.c_int),
+        ("zero_skip", ctypes.c_int),
     ]
 
 
@@ -117,6 +118,8 @@ _SIGS = [
     ("lp_server_destroy", None, [ctypes.c_void_p]),
     ("lp_fp32_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), _c_double_p,
                                      _c_double_p]),
+    ("lp_update_counts", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_longlong)]),
     ("lp_dgemm_emulated", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                          ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong,
@@ -270,6 +273,15 @@ def lp_fp32_stats(h):
     _check(load_library().lp_fp32_stats(h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(body)),
            h)
     return n.value, ms.value, body.value
+
+
+def lp_update_counts(h):
+    """(updated, left in place): constraint-row entries the two-pivot primal
+    kernel updated and left in place, summed over the pivots since lp_load."""
+    f = ctypes.c_longlong()
+    z = ctypes.c_longlong()
+    _check(load_library().lp_update_counts(h, ctypes.byref(f), ctypes.byref(z)), h)
+    return f.value, z.value
 
 
 def lp_dgemm_emulated(A, B, C, opt: Optional[lp_options] = None) -> None:

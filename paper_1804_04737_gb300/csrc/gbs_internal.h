@@ -69,6 +69,13 @@ struct LpDesc {
     // once the solve is past its wall-clock limit; nullptr elsewhere.  Each
     // pivot kernel reads it once per pass and ends in ST_TIMEOUT.
     const int *abort;
+    // two-pivot primal kernel: vectors x pivots updated ([0]) and left in
+    // place because both pivot rows are zero on them ([1]), added up over the
+    // passes; nullptr: not counted
+    unsigned long long *work;
+    // nonzero when a constraint row may hold a -0 (from the data, Phase I,
+    // FP32 mode, or a -0 an update produced): no vector is left in place
+    int negz;
 };
 
 // Launch shape of the persistent pivot kernel for one LP.
@@ -81,6 +88,8 @@ struct PivotShape {
     int pipe = 0;                  // pipelined kernel: 1 in place, 2 double-buffered, 3 two pivots per pass
     int sel_warps = 4;             // two pivots per pass: selection warps per CTA (4 or 8)
     int dist = 0;                  // two pivots per pass, primal: ratio test distributed over the CTAs
+    int split = 0;                 // two pivots per pass, primal: first column of every CTA's second
+                                   // run (0: one contiguous strip, every vector updated)
     size_t smem_bytes = 0;         // dynamic shared memory per CTA
     long long scratch_stride = 0;  // global scratch bytes per CTA when !use_smem
 };
@@ -96,7 +105,7 @@ constexpr int kBarWords = 256;
 
 struct InputStats {
     unsigned long long amax_bits, bmax_bits, cmax_bits;  // bit patterns of max |.|
-    int flags;  // 1: some b < 0, 2: some c < 0, 4: a non-finite value
+    int flags;  // 1: some b < 0, 2: some c < 0, 4: a non-finite value, 8: a -0 in A or b
     int pad_;
 };
 
@@ -134,8 +143,11 @@ int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, 
 // else a global slice of scratch_stride bytes per CTA.
 // dual: 1 the dual simplex kernel, 2 the two-pivot primal kernel (both
 // double-buffered only), 0 the primal kernel.
+// split (two-pivot kernels, dual >= 2): the column where each CTA's second
+// segment of columns starts, or 0; the shape keeps it only when every CTA's
+// two segments fit its update threads.
 PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas,
-                             int dual);
+                             int dual, int split = 0);
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s);
 cudaError_t launch_extract(int prec, const LpDesc *d_desc, const void *T, const int *basis,

@@ -940,8 +940,87 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // without waiting for the slowest CTA of pass k.
 
 constexpr int kBlk = 2;       // pivots per pass
-constexpr int kBlkVals = 8;   // values per record: 3 at the record's column, 3 at the rhs, 2 unused
+constexpr int kBlkVals = 8;   // values per record: [0, 3) at the record's column, [4, 7) at the rhs
+                              // (two-pivot primal kernel: [3] the buffer of the column's rows)
+constexpr int kRecTab = 4;    // values of a record the selection keeps in shared memory
 constexpr int kMaxRecs = 256; // CTAs of a two-pivot launch (records copied to shared memory)
+
+// ---- the columns of one CTA of the two-pivot primal kernel ----
+//
+// Run A [a0, a0 + wa) and run B [b0, b0 + wb); local column l in [0, wa + wb),
+// A first.  Without a split (split == 0) CTA g owns the contiguous strip
+// [g W, g W + W), cut at P.  With a split column (a multiple of the sector,
+// where the structural columns end), [0, split) and [split, P) are each cut
+// into G near-equal runs of whole sectors, one of each per CTA.  The slack
+// column of a row whose slack is still basic holds a unit vector: zero in
+// every pivot row but its own, so the update leaves it in place (see the
+// kernel); split runs give every CTA the same share of the columns that are
+// updated.
+struct Strip {
+    int a0, wa, b0, wb;
+    __host__ __device__ int w() const { return wa + wb; }
+    __host__ __device__ int gcol(int l) const { return l < wa ? a0 + l : b0 + (l - wa); }
+    __host__ __device__ int lcol(int j) const {
+        if ((unsigned)(j - a0) < (unsigned)wa) return j - a0;
+        if ((unsigned)(j - b0) < (unsigned)wb) return wa + (j - b0);
+        return -1;
+    }
+};
+__host__ __device__ inline Strip make_strip(int g, int G, int W, int split, long long P, int sector) {
+    Strip s;
+    if (split <= 0) {
+        const long long a0 = (long long)g * W;
+        s.a0 = (int)a0;
+        s.wa = (int)(a0 >= P ? 0 : (a0 + W <= P ? W : P - a0));
+        s.b0 = 0;
+        s.wb = 0;
+        return s;
+    }
+    const long long nb = P - split;
+    const long long ea0 = (long long)split * g / G / sector * sector;
+    const long long ea1 = (long long)split * (g + 1) / G / sector * sector;
+    const long long eb0 = nb * g / G / sector * sector, eb1 = nb * (g + 1) / G / sector * sector;
+    s.a0 = (int)ea0;
+    s.wa = (int)(ea1 - ea0);
+    s.b0 = (int)(split + eb0);
+    s.wb = (int)(eb1 - eb0);
+    return s;
+}
+
+// OR of a flag over the nthreads threads of named barrier id (which it is).
+__device__ __forceinline__ int named_bar_or(int id, int nthreads, int v) {
+    unsigned r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\n"
+        "bar.red.or.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((unsigned)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return (int)r;
+}
+__device__ __forceinline__ bool not_finite(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool not_finite(float x) {
+    return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u;
+}
+// a component of v is -0
+__device__ __forceinline__ bool has_negzero(const double2 &v) {
+    return (unsigned long long)__double_as_longlong(v.x) == kSign ||
+           (unsigned long long)__double_as_longlong(v.y) == kSign;
+}
+__device__ __forceinline__ bool has_negzero(const float4 &v) {
+    return __float_as_uint(v.x) == 0x80000000u || __float_as_uint(v.y) == 0x80000000u ||
+           __float_as_uint(v.z) == 0x80000000u || __float_as_uint(v.w) == 0x80000000u;
+}
+__device__ __forceinline__ bool zero_vec(const double2 &v) {
+    return (((unsigned long long)__double_as_longlong(v.x) |
+             (unsigned long long)__double_as_longlong(v.y)) << 1) == 0ull;
+}
+__device__ __forceinline__ bool zero_vec(const float4 &v) {
+    return ((__float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) |
+             __float_as_uint(v.w)) << 1) == 0u;
+}
 
 // scan_records over one round of two-pivot records, which also copies the
 // first NV values of every record (vals + k * kBlkVals) to tab[k * NV + v] in
@@ -1143,7 +1222,8 @@ __device__ __forceinline__ T blk_apply(T x, int i, int np, const int *pp, const 
 
 template <typename T, int SW, bool DIST>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-    pivot_block_kernel(LpDesc *__restrict__ d, int W, long long spin_limit, long long budget) {
+    pivot_block_kernel(LpDesc *__restrict__ d, int W, int split, long long spin_limit,
+                       long long budget) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
     constexpr int kSelThreads = 32 * SW;
@@ -1157,7 +1237,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ int s_flag, s_status, s_sok, s_uok, s_np, s_pend, s_abort;
     __shared__ volatile int s_zready;  // passes whose objective-row strip is in sz
     __shared__ int s_p[kBlk], s_q[kBlk], s_rz[kBlk];
-    __shared__ unsigned long long s_tab[kMaxRecs * (kBlk + 1)];  // the records' values
+    __shared__ unsigned long long s_tab[kMaxRecs * kRecTab];  // the records' values
+    __shared__ unsigned short s_vl[kMaxThreads];     // the vectors updated this pass, in order
+    __shared__ unsigned char s_res[2][kMaxThreads];  // buffer holding each vector's rows, by pass parity
+    __shared__ unsigned char s_nz[kMaxThreads];      // the vector's rows may hold a -0
+    __shared__ int s_cf[32], s_rowner;
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     const int NU = B - kSelThreads;
@@ -1183,16 +1267,42 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // pass's source tableau
     unsigned *pcnt = d->bar + 64, *scnt = d->bar + 160;
 
-    // strip and thread map of the update threads
-    const int c0 = g * W;
-    const int c1 = (int)min((long long)c0 + W, P);
-    const int vpr = (c1 - c0) / VW;
-    const int rpp = NU / vpr;
-    const int lr = tid / vpr, lv = tid - lr * vpr;
-    const bool active = !selw && lr < rpp;
-    const int col0 = c0 + lv * VW;
-    const int rv = (N - 1 >= c0 && N - 1 < c1) ? (N - 1 - c0) / VW : -1;
-    const int rowner = (N - 1) / W;
+    // The CTA's columns (local l <-> global S.gcol(l)), vpr vectors of VW
+    // columns; the rhs column's local index here (or -1) and its CTA.
+    //
+    // Vectors left in place (skip): the constraint rows of a vector live in
+    // one of the two buffers, s_res[parity of the pass][vector].  A pass
+    // updates a vector from that buffer into the other one, except a vector
+    // whose entries in both pivot rows of the pass are zeros: Step 5 leaves
+    // it as it is, bit for bit (fma(-c, +-0, t) = t for finite c and t not
+    // -0, and the pivot row's entry pr = +0 / positive pivot = +0 is the one
+    // there), so its rows stay where they are.  That holds while no
+    // constraint row holds a -0 (the primal form's pivots are positive, so a
+    // -0 comes only from the data or from an update rounding to -0, which
+    // marks the vector in s_nz and the LP in d->negz) and the pass's pivot
+    // columns are finite.  Readers of a column take its buffer from s_res
+    // (this CTA's columns) or from the record that named the column.  The
+    // objective row follows the pass parity.
+    constexpr int kSector = 32 / (int)sizeof(T);
+    const Strip S = make_strip(g, G, W, split, P, kSector);
+    const int ws = S.w();
+    const int vpr = ws / VW;
+    const int rl = S.lcol(N - 1);
+    const bool skip = split > 0;
+    for (int v = tid; v < vpr; v += B) {
+        s_res[0][v] = 0;
+        s_res[1][v] = 0;
+        s_nz[v] = (skip && !d->negz) ? 0 : 1;
+    }
+    if (tid == 0) {
+        int o = 0;
+        for (int k = 0; k < G; ++k)
+            if (make_strip(k, G, W, split, P, kSector).lcol(N - 1) >= 0) {
+                o = k;
+                break;
+            }
+        s_rowner = o;
+    }
     // shared memory: the pass's pivot rows on the strip, the objective row of
     // T2 on the strip, pivot a's row on the strip; scratch (shared or this
     // CTA's global slice): four pivot columns (this pass's two, the next
@@ -1237,7 +1347,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int bland = deg >= bland_after;
         Cand c = cand_empty();
         const T *z = Tab + (long long)m * P;
-        for (int j = c0 + tid; j < c1 && j < N - 1; j += B) {
+        for (int l = tid; l < ws; l += B) {
+            const int j = S.gcol(l);
+            if (j >= N - 1) continue;
             const unsigned long long zk = okey(lds(z + j));
             if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
         }
@@ -1310,18 +1422,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (!selw) {
             // the strip of the objective row is loaded with the pivot rows'
             V zt;
-            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + c0 + tid * VW));
+            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + S.gcol(tid * VW)));
             // Step 4 for the pass's pivots on this CTA's strip
-            for (int j = c0 + tid; j < c1; j += NU) {
-                const T r = lds(A + (long long)pp[0] * P + j) / pc[0][pp[0]];
-                sprow[0][j - c0] = r;
+            for (int l = tid; l < ws; l += NU) {
+                const int j = S.gcol(l);
+                const T *Ar = bufs[s_res[par][l / VW]];
+                const T r = lds(Ar + (long long)pp[0] * P + j) / pc[0][pp[0]];
+                sprow[0][l] = r;
                 if (np > 1) {
                     const T t = (pp[1] == pp[0]) ? r
-                                                 : tfma(-pc[0][pp[1]], r, lds(A + (long long)pp[1] * P + j));
-                    sprow[1][j - c0] = t / pc[1][pp[1]];
+                                                 : tfma(-pc[0][pp[1]], r, lds(Ar + (long long)pp[1] * P + j));
+                    sprow[1][l] = t / pc[1][pp[1]];
                 }
             }
-            named_sync(1, NU);
+            // a non-finite entry in a pivot column: update every vector
+            int bad = 0;
+            if (skip)
+                for (int i = tid; i < m; i += NU)
+                    bad |= (int)not_finite(pc[0][i]) | (int)(np > 1 && not_finite(pc[1][i]));
+            bad = named_bar_or(1, NU, bad);
             // the new strip of the objective row of T2, and the CTA's pricing record a
             Cand c = cand_empty();
             if (tid < vpr) {
@@ -1331,14 +1450,35 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 *reinterpret_cast<V *>(sz + tid * VW) = zt;
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
-                    const int j = c0 + tid * VW + k;
+                    const int j = S.gcol(tid * VW) + k;
                     const unsigned long long zk = okey(getc(zt, k));
                     if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
                 }
             }
+            // vector tid is updated this pass (else both pivot rows are zero on it)
+            bool fv = false;
+            if (tid < vpr)
+                fv = !skip || bad || s_nz[tid] ||
+                     !(zero_vec(*reinterpret_cast<const V *>(sprow[0] + tid * VW)) &&
+                       (np < 2 || zero_vec(*reinterpret_cast<const V *>(sprow[1] + tid * VW))));
+            const unsigned bfv = __ballot_sync(0xffffffffu, fv);
             c = warp_min(c);
-            if (lane == 0) wpart[tid >> 5] = c;
+            if (lane == 0) {
+                wpart[tid >> 5] = c;
+                s_cf[tid >> 5] = __popc(bfv);
+            }
             named_sync(1, NU);
+            // the updated vectors in order, nF of them
+            int nF = 0;
+            {
+                int of = 0;
+                for (int w = 0; w < (NU >> 5); ++w) {
+                    const int f = s_cf[w];
+                    of += w < (tid >> 5) ? f : 0;
+                    nF += f;
+                }
+                if (fv) s_vl[of + __popc(bfv & ((1u << lane) - 1u))] = (unsigned short)tid;
+            }
             if (tid < 32) {
                 const Cand e = tid < NU / 32 ? wpart[tid] : cand_empty();
                 const Cand r = warp_min(e);
@@ -1347,9 +1487,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         recA[g] = r;
                         unsigned long long *v = valA + (size_t)g * kBlkVals;
                         for (int k = 0; k < np; ++k) {
-                            v[k] = r.idx >= 0 ? tbits(sprow[k][r.idx - c0]) : 0ull;
-                            v[3 + k] = rv >= 0 ? tbits(sprow[k][N - 1 - c0]) : 0ull;
+                            v[k] = r.idx >= 0 ? tbits(sprow[k][S.lcol(r.idx)]) : 0ull;
+                            v[4 + k] = rl >= 0 ? tbits(sprow[k][rl]) : 0ull;
                         }
+                        v[3] = r.idx >= 0 ? s_res[par][S.lcol(r.idx) / VW] : 0ull;
                         red_add_release(pcnt, 1u);
                     }
                     __threadfence_block();
@@ -1377,59 +1518,82 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 }
             }
             named_sync(1, NU);
-            const bool upd = active && s_uok;
-            if (s_uok && tid < vpr) *reinterpret_cast<V *>(Bn + (long long)m * P + c0 + tid * VW) = zt;
-            // Step 5 for the pass's pivots on the constraint rows of the strip
-            if (upd && np == 2) {
-                const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
-                const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
-                const int p0 = pp[0], p1 = pp[1];
-                const T *__restrict__ c0p = pc[0];
-                const T *__restrict__ c1p = pc[1];
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
-                int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
-                    t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
-                    t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p1, c1p[i1], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p1, c1p[i2], pr1);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p1, c1p[i3], pr1);
-                }
-                for (; i < m; i += rpp) {
-                    V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p1, c1p[i], pr1);
-                }
-            } else if (upd) {
+            if (s_uok && tid < vpr) {
+                *reinterpret_cast<V *>(Bn + (long long)m * P + S.gcol(tid * VW)) = zt;
+                s_res[par ^ 1][tid] = s_res[par][tid] ^ (fv ? 1 : 0);
+            }
+            if (s_uok && tid == 0 && d->work) {  // vectors x pivots updated and left in place
+                atomicAdd(d->work, (unsigned long long)(nF * np));
+                atomicAdd(d->work + 1, (unsigned long long)((vpr - nF) * np));
+            }
+            // Step 5 for the pass's pivots on the constraint rows of the
+            // updated vectors, every update thread on one of them
+            const int rpp = nF > 0 ? NU / nF : 0;
+            const int lr = nF > 0 ? tid / nF : 0;
+            if (s_uok && lr < rpp) {
+                const int lv = s_vl[tid - lr * nF];
+                const int rs = s_res[par][lv];
+                const int col0 = S.gcol(lv * VW);
+                const T *abase = bufs[rs] + col0;
+                T *bbase = bufs[rs ^ 1] + col0;
                 const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
                 const int p0 = pp[0];
                 const T *__restrict__ c0p = pc[0];
-                const T *abase = A + col0;
-                T *bbase = Bn + col0;
+                bool nz = false;
                 int i = lr;
-                for (; i + 3 * rpp < m; i += 4 * rpp) {
-                    const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    const V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
-                    const V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
-                    const V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i1 * P) = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i2 * P) = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
-                    *reinterpret_cast<V *>(bbase + (long long)i3 * P) = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
+                if (np == 2) {
+                    const V pr1 = *reinterpret_cast<const V *>(sprow[1] + lv * VW);
+                    const int p1 = pp[1];
+                    const T *__restrict__ c1p = pc[1];
+                    for (; i + 3 * rpp < m; i += 4 * rpp) {
+                        const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                        V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                        V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                        V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                        V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                        t0 = pivot_vec<T>(pivot_vec<T>(t0, i, p0, c0p[i], pr0), i, p1, c1p[i], pr1);
+                        t1 = pivot_vec<T>(pivot_vec<T>(t1, i1, p0, c0p[i1], pr0), i1, p1, c1p[i1], pr1);
+                        t2 = pivot_vec<T>(pivot_vec<T>(t2, i2, p0, c0p[i2], pr0), i2, p1, c1p[i2], pr1);
+                        t3 = pivot_vec<T>(pivot_vec<T>(t3, i3, p0, c0p[i3], pr0), i3, p1, c1p[i3], pr1);
+                        nz |= has_negzero(t0) | has_negzero(t1) | has_negzero(t2) | has_negzero(t3);
+                        *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
+                        *reinterpret_cast<V *>(bbase + (long long)i1 * P) = t1;
+                        *reinterpret_cast<V *>(bbase + (long long)i2 * P) = t2;
+                        *reinterpret_cast<V *>(bbase + (long long)i3 * P) = t3;
+                    }
+                    for (; i < m; i += rpp) {
+                        V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                        t0 = pivot_vec<T>(pivot_vec<T>(t0, i, p0, c0p[i], pr0), i, p1, c1p[i], pr1);
+                        nz |= has_negzero(t0);
+                        *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
+                    }
+                } else {
+                    for (; i + 3 * rpp < m; i += 4 * rpp) {
+                        const int i1 = i + rpp, i2 = i + 2 * rpp, i3 = i + 3 * rpp;
+                        V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                        V t1 = ldv(reinterpret_cast<const V *>(abase + (long long)i1 * P));
+                        V t2 = ldv(reinterpret_cast<const V *>(abase + (long long)i2 * P));
+                        V t3 = ldv(reinterpret_cast<const V *>(abase + (long long)i3 * P));
+                        t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                        t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
+                        t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
+                        t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
+                        nz |= has_negzero(t0) | has_negzero(t1) | has_negzero(t2) | has_negzero(t3);
+                        *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
+                        *reinterpret_cast<V *>(bbase + (long long)i1 * P) = t1;
+                        *reinterpret_cast<V *>(bbase + (long long)i2 * P) = t2;
+                        *reinterpret_cast<V *>(bbase + (long long)i3 * P) = t3;
+                    }
+                    for (; i < m; i += rpp) {
+                        V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
+                        t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                        nz |= has_negzero(t0);
+                        *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
+                    }
                 }
-                for (; i < m; i += rpp) {
-                    const V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
-                    *reinterpret_cast<V *>(bbase + (long long)i * P) = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
+                if (nz && skip) {  // this vector is never left in place again, nor any later
+                    s_nz[lv] = 1;
+                    d->negz = 1;
                 }
             }
         } else {
@@ -1456,8 +1620,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     st = ST_TIMEOUT;
                 } else {
 #pragma unroll
-                    for (int k = 0; k < kBlk; ++k) rvb[k] = __ldcg(valA + (size_t)rowner * kBlkVals + 3 + k);
-                    const Cand e = scan_records_tab<kSelThreads, kBlk>(recA, valA, G, stid, &ka, s_tab);
+                    for (int k = 0; k < kBlk; ++k) rvb[k] = __ldcg(valA + (size_t)s_rowner * kBlkVals + 4 + k);
+                    const Cand e = scan_records_tab<kSelThreads, kRecTab>(recA, valA, G, stid, &ka, s_tab);
                     const Cand sel = sel_min<SW>(e, ka, selc, selq, &ka);
                     if (sel.idx < 0) st = ST_OPTIMAL;
                     else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
@@ -1470,9 +1634,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     T pvq[kBlk], pvr[kBlk];
 #pragma unroll
                     for (int k = 0; k < kBlk; ++k) {
-                        pvq[k] = tfrom<T>(s_tab[ka * kBlk + k]);
+                        pvq[k] = tfrom<T>(s_tab[ka * kRecTab + k]);
                         pvr[k] = tfrom<T>(rvb[k]);
                     }
+                    const T *Aq = bufs[s_tab[ka * kRecTab + 3] & 1];  // the buffer of column q_a's rows
                     // column q_a and rhs of T2 on this CTA's rows (Step 3,
                     // distributed); the rhs from the one of T0 kept in scratch,
                     // which becomes T2's
@@ -1485,7 +1650,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
                             const int i = i0 + u * kSelThreads;
-                            av[u] = i < ra1 ? lds(A + (long long)i * P + qa) : (T)0;
+                            av[u] = i < ra1 ? lds(Aq + (long long)i * P + qa) : (T)0;
                         }
 #pragma unroll
                         for (int u = 0; u < kColRows; ++u) {
@@ -1601,16 +1766,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         st = ST_TIMEOUT;
                     } else {
                         Cand e = cand_empty();
-                        for (int j = c0 + stid; j < c1; j += kSelThreads) {
-                            T r = lds(A + (long long)pa * P + j);
+                        for (int l = stid; l < ws; l += kSelThreads) {
+                            const int j = S.gcol(l);
+                            T r = lds(bufs[s_res[par][l / VW]] + (long long)pa * P + j);
 #pragma unroll
                             for (int k = 0; k < kBlk; ++k)
                                 if (k < np)
-                                    r = (pa == pp[k]) ? sprow[k][j - c0]
-                                                      : tfma(-pc[k][pa], sprow[k][j - c0], r);
+                                    r = (pa == pp[k]) ? sprow[k][l] : tfma(-pc[k][pa], sprow[k][l], r);
                             const T pra = r / piva;
-                            spa[j - c0] = pra;
-                            const unsigned long long zk = okey(tfma(-colA[m], pra, sz[j - c0]));
+                            spa[l] = pra;
+                            const unsigned long long zk = okey(tfma(-colA[m], pra, sz[l]));
                             if (j < N - 1 && zk < lim_d) cand_take(e, nblandb ? zero_k : zk, j, j);
                         }
                         e = sel_min<SW>(e, 0ull, selc, selq, nullptr);
@@ -1619,9 +1784,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             unsigned long long *v = valB + (size_t)g * kBlkVals;
                             for (int k = 0; k <= np; ++k) {
                                 const T *row = k < np ? sprow[k] : spa;
-                                v[k] = e.idx >= 0 ? tbits(row[e.idx - c0]) : 0ull;
-                                v[3 + k] = rv >= 0 ? tbits(row[N - 1 - c0]) : 0ull;
+                                v[k] = e.idx >= 0 ? tbits(row[S.lcol(e.idx)]) : 0ull;
+                                v[4 + k] = rl >= 0 ? tbits(row[rl]) : 0ull;
                             }
+                            v[3] = e.idx >= 0 ? s_res[par][S.lcol(e.idx) / VW] : 0ull;
                             red_add_release(pcnt, 1u);
                         }
                         // ---- pivot b (Step 2): the pricing records ----
@@ -1634,8 +1800,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         } else {
 #pragma unroll
                             for (int k = 0; k <= kBlk; ++k)
-                                rvb[k] = __ldcg(valB + (size_t)rowner * kBlkVals + 3 + k);
-                            const Cand f = scan_records_tab<kSelThreads, kBlk + 1>(recB, valB, G, stid, &kb, s_tab);
+                                rvb[k] = __ldcg(valB + (size_t)s_rowner * kBlkVals + 4 + k);
+                            const Cand f = scan_records_tab<kSelThreads, kRecTab>(recB, valB, G, stid, &kb, s_tab);
                             const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
                             nnp = 1;
                             if (sel.idx < 0) npend = ST_OPTIMAL;
@@ -1648,9 +1814,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             T pvq[kBlk + 1], pvr[kBlk + 1];
 #pragma unroll
                             for (int k = 0; k <= kBlk; ++k) {
-                                pvq[k] = tfrom<T>(s_tab[kb * (kBlk + 1) + k]);
+                                pvq[k] = tfrom<T>(s_tab[kb * kRecTab + k]);
                                 pvr[k] = tfrom<T>(rvb[k]);
                             }
+                            const T *Aq = bufs[s_tab[kb * kRecTab + 3] & 1];  // column q_b's rows
                             // column q_b and rhs after pivot a on this CTA's rows
                             // (Step 3, distributed); scratch keeps T2's rhs for the
                             // next pass
@@ -1662,7 +1829,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
                                     const int i = i0 + u * kSelThreads;
-                                    av[u] = i < ra1 ? lds(A + (long long)i * P + qb) : (T)0;
+                                    av[u] = i < ra1 ? lds(Aq + (long long)i * P + qb) : (T)0;
                                 }
 #pragma unroll
                                 for (int u = 0; u < kColRows; ++u) {
@@ -1808,6 +1975,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         // done; the counters order everything that crosses CTAs
     }
 
+    // Hand over one buffer: the rows of the vectors last left in the other
+    // one are copied into it (the objective row is there already).  No
+    // reader of the passes reads a vector from the buffer it is not in.
+    {
+        const unsigned char *res = s_res[lk & 1];
+        for (int v = 0; v < vpr; ++v) {
+            if (res[v] == cur) continue;
+            const T *src = bufs[res[v]] + S.gcol(v * VW);
+            T *dst = bufs[cur] + S.gcol(v * VW);
+            for (int i = tid; i < m; i += B)
+                *reinterpret_cast<V *>(dst + (long long)i * P) = ldv(reinterpret_cast<const V *>(src + (long long)i * P));
+        }
+    }
     if (g == 0 && tid == 0) {
         // every CTA's last selection is done, and with it its last wait
         wait_ctr(scnt, (unsigned)G * (lk + 1u), d->err, spin_limit);
@@ -2345,7 +2525,9 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
     int dbm = sh.pipe == 2 ? 1 : 0;
     void *args[] = {&d_desc, &W, &spin_limit, &budget, &dbm};
     if (sh.pipe == 3) {  // two pivots per pass
+        int split = sh.split;
         void *bargs[] = {&d_desc, &W, &spin_limit, &budget};
+        void *pargs[] = {&d_desc, &W, &split, &spin_limit, &budget};
         const bool w8 = sh.sel_warps == 8;
         const void *fn = sh.dual ? (prec == PREC_FP64
                                         ? (w8 ? (const void *)pivot_block_dual_kernel<double, 8>
@@ -2366,8 +2548,8 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                                  (int)sh.smem_bytes);
             if (e != cudaSuccess) return e;
         }
-        return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), bargs,
-                                           sh.smem_bytes, s);
+        return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads),
+                                           sh.dual ? bargs : pargs, sh.smem_bytes, s);
     }
     if (sh.dual) {
         const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_dual_kernel<double, 4>
@@ -2397,7 +2579,7 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
 // (all but the last warp), shared memory for the strip and the selection
 // warp's block of rows.
 PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads, int ctas,
-                             int dual) {
+                             int dual, int split) {
     PivotShape sh;
     const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
     const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -2418,6 +2600,23 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     if (w > (long long)nu * vw) w = (long long)nu * vw / sector * sector;
     sh.strip = (int)w;
     sh.ctas = (int)((P + w - 1) / w);
+    // two runs per CTA (the two-pivot primal kernel): the widest CTA sizes
+    // the shared memory; every CTA needs columns and at most a pass of the
+    // update threads
+    if (dual == 2 && split > 0 && split % sector == 0 && split < P) {
+        int wmax = 0;
+        bool fits = true;
+        for (int k = 0; k < sh.ctas && fits; ++k) {
+            const Strip st = make_strip(k, sh.ctas, sh.strip, split, P, sector);
+            fits = st.w() > 0 && st.w() <= nu * vw;
+            wmax = std::max(wmax, st.w());
+        }
+        if (fits) {
+            sh.split = split;
+            sh.strip = wmax;
+            w = wmax;
+        }
+    }
     // the pivot columns of two pivots and the ratio numerators and screening
     // keys (primal), or the strip of the new objective row (dual)
     const size_t cbytes = ((size_t)M * esz + 15) & ~(size_t)15;

@@ -683,12 +683,14 @@ __global__ void __launch_bounds__(256) inspect_kernel(const double *__restrict__
         const double v = A[k];
         if (!isfinite(v)) flags |= 4;
         else amax = fmax(amax, fabs(v));
+        if ((unsigned long long)__double_as_longlong(v) == 0x8000000000000000ull) flags |= 8;
     }
     for (long long k = t0; k < m; k += stride) {
         const double v = b[k];
         if (!isfinite(v)) flags |= 4;
         else bmax = fmax(bmax, fabs(v));
         if (v < 0.0) flags |= 1;
+        if ((unsigned long long)__double_as_longlong(v) == 0x8000000000000000ull) flags |= 8;
     }
     for (long long k = t0; k < n; k += stride) {
         const double v = c[k];

@@ -44,9 +44,12 @@ def _strips(P, ctas, vw=2, sector=4, nu=768):
     return G, w, P - (G - 1) * w
 
 
+@pytest.mark.parametrize("zero_skip", [0, 1])
 @pytest.mark.parametrize("ctas", [5, 13, 29, 57, 100, 120, 150])
 @pytest.mark.parametrize("sense,pipeline", [(MIN_GE, 4), (MIN_GE, 1), (MAX_LE, 4), (MAX_LE, 5)])
-def test_two_pivot_kernels_at_partial_last_strips(ctas, sense, pipeline):
+def test_two_pivot_kernels_at_partial_last_strips(ctas, sense, pipeline, zero_skip):
+    """zero_skip=0: contiguous strips, the last one partial; zero_skip=1: two
+    runs per CTA, uneven by up to a sector."""
     A, b, c = lpgen.dense_lp(300, 500, seed=ctas)
     if sense == MIN_GE:
         A, b, c = lpgen.dual_of(A, b, c)
@@ -54,7 +57,8 @@ def test_two_pivot_kernels_at_partial_last_strips(ctas, sense, pipeline):
     P = -(-(n + m + 1) // 32) * 32
     G, w, last = _strips(P, ctas)
     assert 0 < last <= w
-    assert_same(Run(A, b, c, sense, ctas=ctas, pipeline=pipeline, time_limit_s=60.0),
+    assert_same(Run(A, b, c, sense, ctas=ctas, pipeline=pipeline, zero_skip=zero_skip,
+                    time_limit_s=60.0),
                 _oracle(A, b, c, sense))
 
 

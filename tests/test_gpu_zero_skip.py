@@ -1,0 +1,153 @@
+"""GPU: split runs and vectors left in place in the two-pivot primal kernel.
+
+With lp_options.zero_skip (the default) every CTA of the FP64 two-pivot primal
+kernel owns a run of the structural columns and a run of the slack and rhs
+columns, and a pass leaves in place the column vectors whose entries in both
+its pivot rows are zeros, their rows staying in whichever tableau buffer holds
+them.  Sec. 2 Step 5 updates every entry with one fma per pivot; with a zero
+multiplier that fma returns the entry itself unless the entry is -0, so the
+kernel must leave every pivot and every bit of the tableau (signed zeros
+included) as the oracle's: at grids whose runs are uneven, with -0 in the data
+(where nothing may be left in place), with entries that round to -0 during the
+solve, in both forms and with the option off.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_04737_gb300 import capi, lpgen
+from paper_1804_04737_gb300.build import build_library
+from test_gpu_parity import Run, _bits, _oracle, assert_same
+
+pytestmark = pytest.mark.gpu
+
+MAX_LE, MIN_GE = capi.LP_MAX_LE, capi.LP_MIN_GE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_library()
+    capi.load_library()
+    oracle.set_threads(os.cpu_count() or 1)
+    yield
+    oracle.set_threads(1)
+
+
+@pytest.mark.parametrize("zero_skip", [0, 1])
+@pytest.mark.parametrize("sense,pipeline", [(MAX_LE, 4), (MAX_LE, 5), (MIN_GE, 4)])
+@pytest.mark.parametrize("m,n,ctas", [(300, 500, 0), (500, 300, 0), (300, 500, 37),
+                                      (257, 1000, 150), (1000, 257, 7), (64, 2048, 0),
+                                      (2048, 64, 0)])
+def test_split_strips_bitwise(m, n, ctas, sense, pipeline, zero_skip):
+    A, b, c = lpgen.dense_lp(m, n, seed=m + 7 * n)
+    if sense == MIN_GE:
+        A, b, c = lpgen.dual_of(A, b, c)
+    assert_same(Run(A, b, c, sense, ctas=ctas, pipeline=pipeline, zero_skip=zero_skip,
+                    time_limit_s=60.0),
+                _oracle(A, b, c, sense))
+
+
+def _sparse_signed(m, n, negzero, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.integers(1, 100, size=(m, n)).astype(np.float64)
+    A[rng.random((m, n)) < 0.5] = -0.0 if negzero else 0.0
+    for j in range(n):
+        if not np.any(A[:, j] > 0):
+            A[rng.integers(0, m), j] = 1.0
+    b = rng.integers(100, 10000, size=m).astype(np.float64)
+    c = rng.integers(1, 50, size=n).astype(np.float64)
+    return A, b, c
+
+
+@pytest.mark.parametrize("negzero", [False, True])
+@pytest.mark.parametrize("sense", [MAX_LE, MIN_GE])
+def test_signed_zeros_both_forms(negzero, sense):
+    """Half of A zero, stored as +0 or as -0: long zero runs in the pivot rows
+    of both forms; with -0 in the data nothing may be left in place (an fma
+    with a zero multiplier turns some -0 entries into +0)."""
+    A, b, c = _sparse_signed(600, 800, negzero, seed=5)
+    if sense == MIN_GE:
+        A, b, c = lpgen.dual_of(A, b, c)
+    o = _oracle(A, b, c, sense)
+    assert o.status in (oracle.OPTIMAL, oracle.UNBOUNDED, oracle.INFEASIBLE)
+    for pipeline in (1, 4):
+        assert_same(Run(A, b, c, sense, pipeline=pipeline), o)
+
+
+def _solve_counts(A, b, c, sense, **opts):
+    h = capi.lp_create(capi.lp_options_default(**opts))
+    try:
+        capi.lp_load(h, A, b, c, sense)
+        capi.lp_solve(h)
+        obj, st, it = capi.lp_result(h)
+        f, z = capi.lp_update_counts(h)
+    finally:
+        capi.lp_destroy(h)
+    return obj, st, it, f, z
+
+
+def test_update_counts_cover_the_tableau():
+    """Every pivot either updates or leaves in place each vector of the m
+    constraint rows over the whole row pitch; with the option off every one
+    is updated.  A dense LP with few pivots relative to m keeps most slack
+    columns at their unit vectors, so most of them stay in place."""
+    sense = MAX_LE
+    A, b, c = lpgen.dense_lp(1024, 1024, seed=3)
+    m, n = A.shape
+    P = (n + m + 1 + 31) // 32 * 32
+    obj1, st1, it1, f1, z1 = _solve_counts(A, b, c, sense, pipeline=4)
+    obj0, st0, it0, f0, z0 = _solve_counts(A, b, c, sense, pipeline=4, zero_skip=0)
+    assert st1 == st0 == capi.LP_OPTIMAL
+    assert it1 == it0 and obj1 == obj0
+    assert f1 + z1 == it1 * P * m
+    assert f0 == it0 * P * m and z0 == 0
+    assert z1 > 0.3 * (f1 + z1), (f1, z1)
+
+
+def test_fp32_same_bits_with_and_without():
+    """FP32 mode (which leaves nothing in place: its refreshes rewrite the
+    rows) gives the same bits with the option on and off."""
+    A, b, c = lpgen.dense_lp(1024, 1536, seed=11)
+    out = []
+    for zs in (1, 0):
+        h = capi.lp_create(capi.lp_options_default(precision=capi.LP_FP32_REINV, zero_skip=zs))
+        try:
+            capi.lp_load(h, A, b, c)
+            capi.lp_solve(h)
+            x = np.empty(A.shape[1])
+            y = np.empty(A.shape[0])
+            obj, st, it = capi.lp_result(h, x, y)
+        finally:
+            capi.lp_destroy(h)
+        out.append((obj, st, it, _bits(x), _bits(y)))
+    (o1, s1, i1, x1, y1), (o0, s0, i0, x0, y0) = out
+    assert s1 == s0 == capi.LP_OPTIMAL and i1 == i0
+    assert _bits([o1])[0] == _bits([o0])[0]
+    assert np.array_equal(x1, x0) and np.array_equal(y1, y0)
+
+
+def test_entries_rounding_to_negative_zero():
+    """Entries of -2^-1074 (the smallest subnormal, negated) in A: the first
+    pivot row holds one, and dividing it by the pivot rounds it to -0 (the
+    oracle's tableau after one pivot shows it), so from then on the kernel
+    may not leave that vector in place.  Every bit as the oracle's after the
+    first pivot and at the end."""
+    A, b, c = lpgen.dense_lp(700, 900, seed=21)
+    rng = np.random.default_rng(4)
+    A[rng.integers(0, 700, 400), rng.integers(0, 900, 400)] = -5e-324
+    o1 = _oracle(A, b, c, max_iters=1)
+    assert (_bits(o1.T[:-1].ravel()) == 0x8000000000000000).any()
+    assert_same(Run(A, b, c, pipeline=4, max_iters=1), o1)
+    assert_same(Run(A, b, c, pipeline=4), _oracle(A, b, c))
+
+
+def test_wide_lp_keeps_one_strip():
+    """Below one slack column per four structural ones the runs are not split
+    (few vectors would stay in place); same bits either way."""
+    A, b, c = lpgen.dense_lp(128, 1024, seed=2)
+    o = _oracle(A, b, c)
+    _, st, it, f, z = _solve_counts(A, b, c, MAX_LE, pipeline=4)
+    assert st == o.status and it == o.iters and z == 0
+    assert_same(Run(A, b, c, pipeline=4), o)
