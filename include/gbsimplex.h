@@ -182,9 +182,10 @@ typedef struct {
                                 FP32 body does not build up; 0 = only the rhs,
                                 the duals and the objective row.  Batches do
                                 the latter.                                     */
-    int zero_skip;           /* FP64 two-pivot primal kernel (pipeline 1, 4, 5 on
-                                tableaus of at least 2^19 elements, LP_MAX_LE
-                                without Phase I, m >= n / 4): 1 (default) = each CTA owns a
+    int zero_skip;           /* FP64 two-pivot primal kernel (pipeline 1, 4, 5),
+                                on tableaus of at least 2^25 elements
+                                ((m+1) x row pitch), LP_MAX_LE without Phase I,
+                                m >= n / 4: 1 (default) = each CTA owns a
                                 run of the structural columns and one of the
                                 slack and rhs columns, and a pass leaves in
                                 place the 16-byte column vectors whose entries
@@ -197,8 +198,10 @@ typedef struct {
                                 vector's rows live in one of the two tableau
                                 buffers; the launch ends with one buffer
                                 holding all of them.  0 = every vector
-                                updated in every pass.  Same pivots and bits
-                                either way.                                     */
+                                updated in every pass; 2 = as 1 at any size
+                                and shape (slower where the selection chain
+                                bounds the pass).  Same pivots and bits in
+                                every mode.                                     */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances

@@ -41,6 +41,9 @@ constexpr size_t kBlockBytes = 384ull << 20;
 // (2 rows a thread) 11.4 / 13.5 us, 2048^2 (8) 24.3 / 23.7, 4096 x 512 (16)
 // 46.6 / 40.5, 8192^2 (64) 243 / 239).
 constexpr int kDistRows = 4;
+// smallest tableau (elements) on which the two-pivot primal kernel leaves
+// vectors in place (lp_options.zero_skip)
+constexpr long long kSkipElems = 1ll << 25;
 
 struct lp_handle {
     lp_options opt;
@@ -395,11 +398,16 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     const bool dpipe = dwant && have_t2;
     // the two-pivot primal kernel's second run of columns (FP64, with
     // zero_skip): the slack and rhs columns, from the last whole sector of
-    // the structural columns; not below one slack column per four
-    // structural ones, where too few vectors stay in place to pay for the
-    // split (512 x 4096: 14.1 against 13.0 us per pivot)
-    const int split =
-        h->opt.zero_skip && h->prec == PREC_FP64 && 4ll * m >= n ? n / 4 * 4 : 0;
+    // the structural columns.  Only where the update bounds the pass: on
+    // tableaus of at least kSkipElems elements with at least one slack
+    // column per four structural ones.  On the smaller tableaus the
+    // selection chain bounds the pass and an update that finishes early only
+    // crowds the chain's loads (4096 x 512 of the paper's family: 63 against
+    // 42 us per pivot; 2048^2: 27 against 25).  zero_skip 2: at any size.
+    const bool skip = h->prec == PREC_FP64 &&
+                      (h->opt.zero_skip == 2 ||
+                       (h->opt.zero_skip == 1 && 4ll * m >= n && (long long)M * P >= kSkipElems));
+    const int split = skip ? n / 4 * 4 : 0;
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
             PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas,

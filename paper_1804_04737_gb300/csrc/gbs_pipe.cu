@@ -1220,13 +1220,16 @@ __device__ __forceinline__ T blk_apply(T x, int i, int np, const int *pp, const 
     return x;
 }
 
-template <typename T, int SW, bool DIST>
+template <typename T, int SW, bool DIST, bool SKIP>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pivot_block_kernel(LpDesc *__restrict__ d, int W, int split, long long spin_limit,
                        long long budget) {
     typedef typename Vec<T>::type V;
     constexpr int VW = Vec<T>::W;
     constexpr int kSelThreads = 32 * SW;
+    // values of a pricing record kept in shared memory: the pivot-row values
+    // (np for record a, np + 1 for record b) and, with SKIP, the buffer bit
+    constexpr int NVA = SKIP ? kRecTab : kBlk, NVB = SKIP ? kRecTab : kBlk + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Cand rbuf[2][32];
     __shared__ unsigned long long ubuf[32];
@@ -1267,10 +1270,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // pass's source tableau
     unsigned *pcnt = d->bar + 64, *scnt = d->bar + 160;
 
-    // The CTA's columns (local l <-> global S.gcol(l)), vpr vectors of VW
+    // The CTA's columns (local l <-> global gcol(l)), vpr vectors of VW
     // columns; the rhs column's local index here (or -1) and its CTA.
     //
-    // Vectors left in place (skip): the constraint rows of a vector live in
+    // Vectors left in place (SKIP, with split runs): the constraint rows of a vector live in
     // one of the two buffers, s_res[parity of the pass][vector].  A pass
     // updates a vector from that buffer into the other one, except a vector
     // whose entries in both pivot rows of the pass are zeros: Step 5 leaves
@@ -1288,11 +1291,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     const int ws = S.w();
     const int vpr = ws / VW;
     const int rl = S.lcol(N - 1);
-    const bool skip = split > 0;
-    for (int v = tid; v < vpr; v += B) {
-        s_res[0][v] = 0;
-        s_res[1][v] = 0;
-        s_nz[v] = (skip && !d->negz) ? 0 : 1;
+    // without SKIP the strip is the contiguous one: the mappings simplify
+    auto gcol = [&](int l) { return SKIP ? S.gcol(l) : S.a0 + l; };
+    auto lcol = [&](int j) { return SKIP ? S.lcol(j) : j - S.a0; };
+    if constexpr (SKIP) {
+        for (int v = tid; v < vpr; v += B) {
+            s_res[0][v] = 0;
+            s_res[1][v] = 0;
+            s_nz[v] = d->negz ? 1 : 0;
+        }
     }
     if (tid == 0) {
         int o = 0;
@@ -1348,7 +1355,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         Cand c = cand_empty();
         const T *z = Tab + (long long)m * P;
         for (int l = tid; l < ws; l += B) {
-            const int j = S.gcol(l);
+            const int j = gcol(l);
             if (j >= N - 1) continue;
             const unsigned long long zk = okey(lds(z + j));
             if (zk < lim_d) cand_take(c, bland ? zero_k : zk, j, j);
@@ -1422,11 +1429,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         if (!selw) {
             // the strip of the objective row is loaded with the pivot rows'
             V zt;
-            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + S.gcol(tid * VW)));
+            if (tid < vpr) zt = ldv(reinterpret_cast<const V *>(A + (long long)m * P + gcol(tid * VW)));
             // Step 4 for the pass's pivots on this CTA's strip
             for (int l = tid; l < ws; l += NU) {
-                const int j = S.gcol(l);
-                const T *Ar = bufs[s_res[par][l / VW]];
+                const int j = gcol(l);
+                const T *Ar = SKIP ? bufs[s_res[par][l / VW]] : A;
                 const T r = lds(Ar + (long long)pp[0] * P + j) / pc[0][pp[0]];
                 sprow[0][l] = r;
                 if (np > 1) {
@@ -1437,10 +1444,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
             // a non-finite entry in a pivot column: update every vector
             int bad = 0;
-            if (skip)
+            if constexpr (SKIP) {
                 for (int i = tid; i < m; i += NU)
                     bad |= (int)not_finite(pc[0][i]) | (int)(np > 1 && not_finite(pc[1][i]));
-            bad = named_bar_or(1, NU, bad);
+                bad = named_bar_or(1, NU, bad);
+            } else {
+                named_sync(1, NU);
+            }
             // the new strip of the objective row of T2, and the CTA's pricing record a
             Cand c = cand_empty();
             if (tid < vpr) {
@@ -1450,35 +1460,29 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 *reinterpret_cast<V *>(sz + tid * VW) = zt;
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
-                    const int j = S.gcol(tid * VW) + k;
+                    const int j = gcol(tid * VW) + k;
                     const unsigned long long zk = okey(getc(zt, k));
                     if (j < N - 1 && zk < lim_d) cand_take(c, nbland ? zero_k : zk, j, j);
                 }
             }
             // vector tid is updated this pass (else both pivot rows are zero on it)
-            bool fv = false;
-            if (tid < vpr)
-                fv = !skip || bad || s_nz[tid] ||
-                     !(zero_vec(*reinterpret_cast<const V *>(sprow[0] + tid * VW)) &&
-                       (np < 2 || zero_vec(*reinterpret_cast<const V *>(sprow[1] + tid * VW))));
-            const unsigned bfv = __ballot_sync(0xffffffffu, fv);
+            bool fv = true;
+            unsigned bfv = 0u;
+            if constexpr (SKIP) {
+                if (tid < vpr)
+                    fv = bad || s_nz[tid] ||
+                         !(zero_vec(*reinterpret_cast<const V *>(sprow[0] + tid * VW)) &&
+                           (np < 2 || zero_vec(*reinterpret_cast<const V *>(sprow[1] + tid * VW))));
+                else
+                    fv = false;
+                bfv = __ballot_sync(0xffffffffu, fv);
+            }
             c = warp_min(c);
             if (lane == 0) {
                 wpart[tid >> 5] = c;
-                s_cf[tid >> 5] = __popc(bfv);
+                if constexpr (SKIP) s_cf[tid >> 5] = __popc(bfv);
             }
             named_sync(1, NU);
-            // the updated vectors in order, nF of them
-            int nF = 0;
-            {
-                int of = 0;
-                for (int w = 0; w < (NU >> 5); ++w) {
-                    const int f = s_cf[w];
-                    of += w < (tid >> 5) ? f : 0;
-                    nF += f;
-                }
-                if (fv) s_vl[of + __popc(bfv & ((1u << lane) - 1u))] = (unsigned short)tid;
-            }
             if (tid < 32) {
                 const Cand e = tid < NU / 32 ? wpart[tid] : cand_empty();
                 const Cand r = warp_min(e);
@@ -1487,10 +1491,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         recA[g] = r;
                         unsigned long long *v = valA + (size_t)g * kBlkVals;
                         for (int k = 0; k < np; ++k) {
-                            v[k] = r.idx >= 0 ? tbits(sprow[k][S.lcol(r.idx)]) : 0ull;
+                            v[k] = r.idx >= 0 ? tbits(sprow[k][lcol(r.idx)]) : 0ull;
                             v[4 + k] = rl >= 0 ? tbits(sprow[k][rl]) : 0ull;
                         }
-                        v[3] = r.idx >= 0 ? s_res[par][S.lcol(r.idx) / VW] : 0ull;
+                        if constexpr (SKIP) v[3] = r.idx >= 0 ? s_res[par][S.lcol(r.idx) / VW] : 0ull;
                         red_add_release(pcnt, 1u);
                     }
                     __threadfence_block();
@@ -1517,10 +1521,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     s_uok = ok;
                 }
             }
+            // the updated vectors in order, nF of them (after the record: it
+            // is on the selection's path, this is not)
+            int nF = vpr;
+            if constexpr (SKIP) {
+                int of = 0;
+                nF = 0;
+                for (int w = 0; w < (NU >> 5); ++w) {
+                    const int f = s_cf[w];
+                    of += w < (tid >> 5) ? f : 0;
+                    nF += f;
+                }
+                if (fv) s_vl[of + __popc(bfv & ((1u << lane) - 1u))] = (unsigned short)tid;
+            }
             named_sync(1, NU);
             if (s_uok && tid < vpr) {
-                *reinterpret_cast<V *>(Bn + (long long)m * P + S.gcol(tid * VW)) = zt;
-                s_res[par ^ 1][tid] = s_res[par][tid] ^ (fv ? 1 : 0);
+                *reinterpret_cast<V *>(Bn + (long long)m * P + gcol(tid * VW)) = zt;
+                if constexpr (SKIP) s_res[par ^ 1][tid] = s_res[par][tid] ^ (fv ? 1 : 0);
             }
             if (s_uok && tid == 0 && d->work) {  // vectors x pivots updated and left in place
                 atomicAdd(d->work, (unsigned long long)(nF * np));
@@ -1531,9 +1548,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             const int rpp = nF > 0 ? NU / nF : 0;
             const int lr = nF > 0 ? tid / nF : 0;
             if (s_uok && lr < rpp) {
-                const int lv = s_vl[tid - lr * nF];
-                const int rs = s_res[par][lv];
-                const int col0 = S.gcol(lv * VW);
+                const int lv = SKIP ? (int)s_vl[tid - lr * nF] : tid - lr * nF;
+                const int rs = SKIP ? (int)s_res[par][lv] : cur;
+                const int col0 = gcol(lv * VW);
                 const T *abase = bufs[rs] + col0;
                 T *bbase = bufs[rs ^ 1] + col0;
                 const V pr0 = *reinterpret_cast<const V *>(sprow[0] + lv * VW);
@@ -1555,7 +1572,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         t1 = pivot_vec<T>(pivot_vec<T>(t1, i1, p0, c0p[i1], pr0), i1, p1, c1p[i1], pr1);
                         t2 = pivot_vec<T>(pivot_vec<T>(t2, i2, p0, c0p[i2], pr0), i2, p1, c1p[i2], pr1);
                         t3 = pivot_vec<T>(pivot_vec<T>(t3, i3, p0, c0p[i3], pr0), i3, p1, c1p[i3], pr1);
-                        nz |= has_negzero(t0) | has_negzero(t1) | has_negzero(t2) | has_negzero(t3);
+                        if constexpr (SKIP) nz |= has_negzero(t0) | has_negzero(t1) | has_negzero(t2) | has_negzero(t3);
                         *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
                         *reinterpret_cast<V *>(bbase + (long long)i1 * P) = t1;
                         *reinterpret_cast<V *>(bbase + (long long)i2 * P) = t2;
@@ -1564,7 +1581,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     for (; i < m; i += rpp) {
                         V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
                         t0 = pivot_vec<T>(pivot_vec<T>(t0, i, p0, c0p[i], pr0), i, p1, c1p[i], pr1);
-                        nz |= has_negzero(t0);
+                        if constexpr (SKIP) nz |= has_negzero(t0);
                         *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
                     }
                 } else {
@@ -1578,7 +1595,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                         t1 = pivot_vec<T>(t1, i1, p0, c0p[i1], pr0);
                         t2 = pivot_vec<T>(t2, i2, p0, c0p[i2], pr0);
                         t3 = pivot_vec<T>(t3, i3, p0, c0p[i3], pr0);
-                        nz |= has_negzero(t0) | has_negzero(t1) | has_negzero(t2) | has_negzero(t3);
+                        if constexpr (SKIP) nz |= has_negzero(t0) | has_negzero(t1) | has_negzero(t2) | has_negzero(t3);
                         *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
                         *reinterpret_cast<V *>(bbase + (long long)i1 * P) = t1;
                         *reinterpret_cast<V *>(bbase + (long long)i2 * P) = t2;
@@ -1587,11 +1604,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     for (; i < m; i += rpp) {
                         V t0 = ldv(reinterpret_cast<const V *>(abase + (long long)i * P));
                         t0 = pivot_vec<T>(t0, i, p0, c0p[i], pr0);
-                        nz |= has_negzero(t0);
+                        if constexpr (SKIP) nz |= has_negzero(t0);
                         *reinterpret_cast<V *>(bbase + (long long)i * P) = t0;
                     }
                 }
-                if (nz && skip) {  // this vector is never left in place again, nor any later
+                if (SKIP && nz) {  // this vector is never left in place again, nor any later
                     s_nz[lv] = 1;
                     d->negz = 1;
                 }
@@ -1621,7 +1638,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 } else {
 #pragma unroll
                     for (int k = 0; k < kBlk; ++k) rvb[k] = __ldcg(valA + (size_t)s_rowner * kBlkVals + 4 + k);
-                    const Cand e = scan_records_tab<kSelThreads, kRecTab>(recA, valA, G, stid, &ka, s_tab);
+                    const Cand e = scan_records_tab<kSelThreads, NVA>(recA, valA, G, stid, &ka, s_tab);
                     const Cand sel = sel_min<SW>(e, ka, selc, selq, &ka);
                     if (sel.idx < 0) st = ST_OPTIMAL;
                     else if (iters + np >= iter_limit) st = ST_ITER_LIMIT;
@@ -1634,10 +1651,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     T pvq[kBlk], pvr[kBlk];
 #pragma unroll
                     for (int k = 0; k < kBlk; ++k) {
-                        pvq[k] = tfrom<T>(s_tab[ka * kRecTab + k]);
+                        pvq[k] = tfrom<T>(s_tab[ka * NVA + k]);
                         pvr[k] = tfrom<T>(rvb[k]);
                     }
-                    const T *Aq = bufs[s_tab[ka * kRecTab + 3] & 1];  // the buffer of column q_a's rows
+                    const T *Aq = SKIP ? bufs[s_tab[ka * NVA + 3] & 1] : A;  // column q_a's rows
                     // column q_a and rhs of T2 on this CTA's rows (Step 3,
                     // distributed); the rhs from the one of T0 kept in scratch,
                     // which becomes T2's
@@ -1767,8 +1784,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     } else {
                         Cand e = cand_empty();
                         for (int l = stid; l < ws; l += kSelThreads) {
-                            const int j = S.gcol(l);
-                            T r = lds(bufs[s_res[par][l / VW]] + (long long)pa * P + j);
+                            const int j = gcol(l);
+                            T r = lds((SKIP ? bufs[s_res[par][l / VW]] : A) + (long long)pa * P + j);
 #pragma unroll
                             for (int k = 0; k < kBlk; ++k)
                                 if (k < np)
@@ -1784,10 +1801,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             unsigned long long *v = valB + (size_t)g * kBlkVals;
                             for (int k = 0; k <= np; ++k) {
                                 const T *row = k < np ? sprow[k] : spa;
-                                v[k] = e.idx >= 0 ? tbits(row[S.lcol(e.idx)]) : 0ull;
+                                v[k] = e.idx >= 0 ? tbits(row[lcol(e.idx)]) : 0ull;
                                 v[4 + k] = rl >= 0 ? tbits(row[rl]) : 0ull;
                             }
-                            v[3] = e.idx >= 0 ? s_res[par][S.lcol(e.idx) / VW] : 0ull;
+                            if constexpr (SKIP) v[3] = e.idx >= 0 ? s_res[par][S.lcol(e.idx) / VW] : 0ull;
                             red_add_release(pcnt, 1u);
                         }
                         // ---- pivot b (Step 2): the pricing records ----
@@ -1801,7 +1818,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
                             for (int k = 0; k <= kBlk; ++k)
                                 rvb[k] = __ldcg(valB + (size_t)s_rowner * kBlkVals + 4 + k);
-                            const Cand f = scan_records_tab<kSelThreads, kRecTab>(recB, valB, G, stid, &kb, s_tab);
+                            const Cand f = scan_records_tab<kSelThreads, NVB>(recB, valB, G, stid, &kb, s_tab);
                             const Cand sel = sel_min<SW>(f, kb, selc, selq, &kb);
                             nnp = 1;
                             if (sel.idx < 0) npend = ST_OPTIMAL;
@@ -1814,10 +1831,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             T pvq[kBlk + 1], pvr[kBlk + 1];
 #pragma unroll
                             for (int k = 0; k <= kBlk; ++k) {
-                                pvq[k] = tfrom<T>(s_tab[kb * kRecTab + k]);
+                                pvq[k] = tfrom<T>(s_tab[kb * NVB + k]);
                                 pvr[k] = tfrom<T>(rvb[k]);
                             }
-                            const T *Aq = bufs[s_tab[kb * kRecTab + 3] & 1];  // column q_b's rows
+                            const T *Aq = SKIP ? bufs[s_tab[kb * NVB + 3] & 1] : A;  // column q_b's rows
                             // column q_b and rhs after pivot a on this CTA's rows
                             // (Step 3, distributed); scratch keeps T2's rhs for the
                             // next pass
@@ -1978,7 +1995,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // Hand over one buffer: the rows of the vectors last left in the other
     // one are copied into it (the objective row is there already).  No
     // reader of the passes reads a vector from the buffer it is not in.
-    {
+    if constexpr (SKIP) {
         const unsigned char *res = s_res[lk & 1];
         for (int v = 0; v < vpr; ++v) {
             if (res[v] == cur) continue;
@@ -2535,14 +2552,19 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                         : (w8 ? (const void *)pivot_block_dual_kernel<float, 8>
                                               : (const void *)pivot_block_dual_kernel<float, 4>))
                          : prec == PREC_FP64
-                             ? (w8 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true>
-                                              : (const void *)pivot_block_kernel<double, 8, false>)
-                                   : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true>
-                                              : (const void *)pivot_block_kernel<double, 4, false>))
-                             : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<float, 8, true>
-                                              : (const void *)pivot_block_kernel<float, 8, false>)
-                                   : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true>
-                                              : (const void *)pivot_block_kernel<float, 4, false>));
+                             ? (sh.split > 0
+                                    ? (w8 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, true>
+                                                     : (const void *)pivot_block_kernel<double, 8, false, true>)
+                                          : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true, true>
+                                                     : (const void *)pivot_block_kernel<double, 4, false, true>))
+                                    : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false>
+                                                     : (const void *)pivot_block_kernel<double, 8, false, false>)
+                                          : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true, false>
+                                                     : (const void *)pivot_block_kernel<double, 4, false, false>)))
+                             : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<float, 8, true, false>
+                                              : (const void *)pivot_block_kernel<float, 8, false, false>)
+                                   : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true, false>
+                                              : (const void *)pivot_block_kernel<float, 4, false, false>));
         if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sh.smem_bytes);

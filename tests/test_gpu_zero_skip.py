@@ -35,7 +35,7 @@ def _lib():
     oracle.set_threads(1)
 
 
-@pytest.mark.parametrize("zero_skip", [0, 1])
+@pytest.mark.parametrize("zero_skip", [0, 2])
 @pytest.mark.parametrize("sense,pipeline", [(MAX_LE, 4), (MAX_LE, 5), (MIN_GE, 4)])
 @pytest.mark.parametrize("m,n,ctas", [(300, 500, 0), (500, 300, 0), (300, 500, 37),
                                       (257, 1000, 150), (1000, 257, 7), (64, 2048, 0),
@@ -73,7 +73,7 @@ def test_signed_zeros_both_forms(negzero, sense):
     o = _oracle(A, b, c, sense)
     assert o.status in (oracle.OPTIMAL, oracle.UNBOUNDED, oracle.INFEASIBLE)
     for pipeline in (1, 4):
-        assert_same(Run(A, b, c, sense, pipeline=pipeline), o)
+        assert_same(Run(A, b, c, sense, pipeline=pipeline, zero_skip=2), o)
 
 
 def _solve_counts(A, b, c, sense, **opts):
@@ -97,7 +97,7 @@ def test_update_counts_cover_the_tableau():
     A, b, c = lpgen.dense_lp(1024, 1024, seed=3)
     m, n = A.shape
     P = (n + m + 1 + 31) // 32 * 32
-    obj1, st1, it1, f1, z1 = _solve_counts(A, b, c, sense, pipeline=4)
+    obj1, st1, it1, f1, z1 = _solve_counts(A, b, c, sense, pipeline=4, zero_skip=2)
     obj0, st0, it0, f0, z0 = _solve_counts(A, b, c, sense, pipeline=4, zero_skip=0)
     assert st1 == st0 == capi.LP_OPTIMAL
     assert it1 == it0 and obj1 == obj0
@@ -139,15 +139,30 @@ def test_entries_rounding_to_negative_zero():
     A[rng.integers(0, 700, 400), rng.integers(0, 900, 400)] = -5e-324
     o1 = _oracle(A, b, c, max_iters=1)
     assert (_bits(o1.T[:-1].ravel()) == 0x8000000000000000).any()
-    assert_same(Run(A, b, c, pipeline=4, max_iters=1), o1)
-    assert_same(Run(A, b, c, pipeline=4), _oracle(A, b, c))
+    assert_same(Run(A, b, c, pipeline=4, max_iters=1, zero_skip=2), o1)
+    assert_same(Run(A, b, c, pipeline=4, zero_skip=2), _oracle(A, b, c))
+
+
+def test_default_size_rule():
+    """By default (zero_skip 1) vectors stay in place only on tableaus of at
+    least 2^25 elements: 4096^2 (4097 x 8224) does, 1024^2 does not; every
+    bit as the oracle's at 4096^2."""
+    A, b, c = lpgen.dense_lp(4096, 4096, seed=7)
+    o = _oracle(A, b, c)
+    g = Run(A, b, c)
+    assert_same(g, o)
+    _, st, it, f, z = _solve_counts(A, b, c, MAX_LE)
+    assert st == o.status and it == o.iters and z > 0.3 * (f + z)
+    A, b, c = lpgen.dense_lp(1024, 1024, seed=3)
+    assert _solve_counts(A, b, c, MAX_LE, pipeline=4)[4] == 0
 
 
 def test_wide_lp_keeps_one_strip():
-    """Below one slack column per four structural ones the runs are not split
-    (few vectors would stay in place); same bits either way."""
-    A, b, c = lpgen.dense_lp(128, 1024, seed=2)
+    """By default, below one slack column per four structural ones the runs
+    are not split (few vectors would stay in place), even above the size
+    threshold: 2048 x 16384 (2049 x 18464 elements); the oracle's bits."""
+    A, b, c = lpgen.dense_lp(2048, 16384, seed=2)
     o = _oracle(A, b, c)
-    _, st, it, f, z = _solve_counts(A, b, c, MAX_LE, pipeline=4)
+    _, st, it, f, z = _solve_counts(A, b, c, MAX_LE)
     assert st == o.status and it == o.iters and z == 0
-    assert_same(Run(A, b, c, pipeline=4), o)
+    assert_same(Run(A, b, c), o)
