@@ -182,10 +182,10 @@ typedef struct {
                                 FP32 body does not build up; 0 = only the rhs,
                                 the duals and the objective row.  Batches do
                                 the latter.                                     */
-    int zero_skip;           /* FP64 two-pivot primal kernel (pipeline 1, 4, 5),
-                                on tableaus of at least 2^25 elements
-                                ((m+1) x row pitch), LP_MAX_LE without Phase I,
-                                m >= n / 4: 1 (default) = each CTA owns a
+    int zero_skip;           /* two-pivot primal kernel (pipeline 1, 4, 5: the
+                                primal rule, FP64 or the FP32 tableau), on
+                                tableaus of at least 2^25 elements ((m+1) x row
+                                pitch) with m >= n / 4: 1 (default) = each CTA owns a
                                 run of the structural columns and one of the
                                 slack and rhs columns, and a pass leaves in
                                 place the 16-byte column vectors whose entries
@@ -194,7 +194,9 @@ typedef struct {
                                 Step 5 leaves them bit for bit as they are
                                 while no constraint row holds a -0 and the
                                 pivot columns are finite, which the kernel
-                                tracks (a -0 in A or b turns it off).  Each
+                                tracks (where a -0 may be present, from the
+                                data, Phase I or FP32 refreshes, a launch
+                                first finds the vectors that hold one).  Each
                                 vector's rows live in one of the two tableau
                                 buffers; the launch ends with one buffer
                                 holding all of them.  0 = every vector

@@ -396,18 +396,18 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     if (pmode == 4)  // the two-pivot kernel's pivot-column slots
         CUDA_TRY(h, grow_bytes(h, &h->dcolx, &h->cap_colx, 4 * (((size_t)M * esz + 15) & ~(size_t)15)));
     const bool dpipe = dwant && have_t2;
-    // the two-pivot primal kernel's second run of columns (FP64, with
-    // zero_skip): the slack and rhs columns, from the last whole sector of
+    // the two-pivot primal kernel's second run of columns (with zero_skip):
+    // the slack and rhs columns, from the last whole sector of
     // the structural columns.  Only where the update bounds the pass: on
     // tableaus of at least kSkipElems elements with at least one slack
     // column per four structural ones.  On the smaller tableaus the
     // selection chain bounds the pass and an update that finishes early only
     // crowds the chain's loads (4096 x 512 of the paper's family: 63 against
     // 42 us per pivot; 2048^2: 27 against 25).  zero_skip 2: at any size.
-    const bool skip = h->prec == PREC_FP64 &&
-                      (h->opt.zero_skip == 2 ||
-                       (h->opt.zero_skip == 1 && 4ll * m >= n && (long long)M * P >= kSkipElems));
-    const int split = skip ? n / 4 * 4 : 0;
+    const bool skip = h->opt.zero_skip == 2 ||
+                      (h->opt.zero_skip == 1 && 4ll * m >= n && (long long)M * P >= kSkipElems);
+    const int sector = h->prec == PREC_FP64 ? 4 : 8;
+    const int split = skip ? n / sector * sector : 0;
     auto shape_for = [&](int rule) {
         if (rule == 0 && pmode) {
             PivotShape ps = choose_pipe_shape(h->prec, M, P, h->sms, h->opt.threads, h->opt.ctas,
@@ -524,7 +524,9 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.work = reinterpret_cast<unsigned long long *>(h->dbar + kBarWords);
     CUDA_TRY(h, cudaMemsetAsync(d.work, 0, 2 * sizeof(unsigned long long), s));
     // a constraint row may hold a -0: from the data, after Phase 1 (dual
-    // pivots are negative), or in FP32 mode (its refreshes rewrite the rows)
+    // pivots are negative), or in FP32 mode (its refreshes and its dual-rule
+    // recovery rewrite the rows); the two-pivot primal kernel then starts
+    // each launch by finding the vectors that do
     d.negz = (st.flags & 8) || phase1 || h->prec == PREC_FP32 ? 1 : 0;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);

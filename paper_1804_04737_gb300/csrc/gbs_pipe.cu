@@ -1282,8 +1282,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // there), so its rows stay where they are.  That holds while no
     // constraint row holds a -0 (the primal form's pivots are positive, so a
     // -0 comes only from the data or from an update rounding to -0, which
-    // marks the vector in s_nz and the LP in d->negz) and the pass's pivot
-    // columns are finite.  Readers of a column take its buffer from s_res
+    // marks the vector in s_nz and the LP in d->negz; with d->negz set, the
+    // launch starts by marking the vectors that hold one) and the pass's
+    // pivot columns are finite.  Readers of a column take its buffer from s_res
     // (this CTA's columns) or from the record that named the column.  The
     // objective row follows the pass parity.
     constexpr int kSector = 32 / (int)sizeof(T);
@@ -1298,7 +1299,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         for (int v = tid; v < vpr; v += B) {
             s_res[0][v] = 0;
             s_res[1][v] = 0;
-            s_nz[v] = d->negz ? 1 : 0;
+            s_nz[v] = 0;
+        }
+        if (d->negz) {
+            // a constraint row may hold a -0 (from the data, Phase I, an FP32
+            // refresh or an earlier launch): mark the vectors that do, one
+            // read of the CTA's columns
+            __syncthreads();
+            const int rows = B / vpr, v = tid % vpr, r0 = tid / vpr;
+            if (r0 < rows) {
+                const T *col = bufs[0] + gcol(v * VW);
+                bool f = false;
+                for (int i = r0; i < m; i += rows) f |= has_negzero(ldv(reinterpret_cast<const V *>(col + (long long)i * P)));
+                if (f) s_nz[v] = 1;
+            }
         }
     }
     if (tid == 0) {
@@ -2561,10 +2575,15 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                                      : (const void *)pivot_block_kernel<double, 8, false, false>)
                                           : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true, false>
                                                      : (const void *)pivot_block_kernel<double, 4, false, false>)))
-                             : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<float, 8, true, false>
-                                              : (const void *)pivot_block_kernel<float, 8, false, false>)
-                                   : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true, false>
-                                              : (const void *)pivot_block_kernel<float, 4, false, false>));
+                             : (sh.split > 0
+                                    ? (w8 ? (sh.dist ? (const void *)pivot_block_kernel<float, 8, true, true>
+                                                     : (const void *)pivot_block_kernel<float, 8, false, true>)
+                                          : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true, true>
+                                                     : (const void *)pivot_block_kernel<float, 4, false, true>))
+                                    : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<float, 8, true, false>
+                                                     : (const void *)pivot_block_kernel<float, 8, false, false>)
+                                          : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true, false>
+                                                     : (const void *)pivot_block_kernel<float, 4, false, false>)));
         if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sh.smem_bytes);
