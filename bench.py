@@ -26,7 +26,7 @@ one pass over the tableau, and vectors left in place are not moved.
 
 Other workloads (--workload): lp2048set (2048^2 primal and dual form,
 512 x 4096, 4096 x 512), paperset (the same shapes from the paper's random
-family), batch1024, serve.
+family), batch1024, serve, product (the emulated-FP64 product alone).
 """
 import argparse
 import json
@@ -559,6 +559,14 @@ def product_bench(capi, torch, local, m=8192, n=8192, s=334):
             "max_rel_err_vs_numpy_fp64_first_256_columns": err}
 
 
+def run_product(args, capi, torch):
+    """The emulated-FP64 product alone, at the body refresh's largest size
+    (one workspace-growing call, then five timed)."""
+    print(json.dumps({"workload": "emulated-FP64 product of the 8192^2 LP's body refresh "
+                                  "(tcgen05, bf16 digit planes)",
+                      **product_bench(capi, torch, 0)}), flush=True)
+
+
 def run_lpset(args, capi, torch, rank, world, local, dist):
     """Single-LP workloads: each step loads and solves every LP of the set
     once on the device, device-timed; then the same through host buffers."""
@@ -756,7 +764,7 @@ def main():
     ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="lp8192",
-                    choices=["lp8192", "lp2048set", "paperset", "batch1024", "serve"],
+                    choices=["lp8192", "lp2048set", "paperset", "batch1024", "serve", "product"],
                     help="lp8192 is the headline line; the others report their own figures")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -771,8 +779,9 @@ def main():
     from paper_1804_04737_gb300 import capi
 
     torch.cuda.set_device(local)
-    if args.workload in ("batch1024", "serve"):
-        return {"batch1024": run_batch, "serve": run_serve}[args.workload](args, capi, torch)
+    if args.workload in ("batch1024", "serve", "product"):
+        return {"batch1024": run_batch, "serve": run_serve,
+                "product": run_product}[args.workload](args, capi, torch)
     dist = None
     if world > 1:
         import torch.distributed as dist
