@@ -2624,7 +2624,16 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     PivotShape sh;
     const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
     const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    sh.threads = threads > 0 ? threads : kMaxThreads;
+    // Default CTA size: 1024 threads; 768 for the two-pivot kernels below 2^24
+    // tableau elements, where the selection chain bounds the pass and fewer
+    // update threads leave it more of the memory system (pivot-kernel us per
+    // pivot at 512 / 640 / 768 / 896 / 1024 threads: 2048^2 primal 35.6 /
+    // 26.3 / 23.0 / 23.7 / 24.5, dual form 35.1 / 28.3 / 25.7 / 26.1 / 27.2,
+    // 512 x 4096 11.3 / 11.6 / 12.1 / 12.1 / 12.2; above it the update
+    // bounds: 4096 x 512 70.0 / 52.6 / 43.8 / 41.3 / 41.0, 8192^2 201 / 160 /
+    // 150 / 147 / 147)
+    sh.threads = threads > 0 ? threads
+                             : (dual >= 2 && (long long)M * P < (1ll << 24) ? 768 : kMaxThreads);
     sh.threads = std::min(kMaxThreads, std::max(2 * kSelThreadsMax, (sh.threads + 31) / 32 * 32));
     const int nu = sh.threads - kSelThreadsMax;
     // Default grid: every SM.  A pivot costs the selection chain plus the
