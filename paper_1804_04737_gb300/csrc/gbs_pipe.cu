@@ -2624,16 +2624,35 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
     PivotShape sh;
     const int vw = prec == PREC_FP64 ? 2 : 4, sector = prec == PREC_FP64 ? 4 : 8;
     const size_t esz = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-    // Default CTA size: 1024 threads; 768 for the two-pivot kernels below 2^24
-    // tableau elements, where the selection chain bounds the pass and fewer
-    // update threads leave it more of the memory system (pivot-kernel us per
-    // pivot at 512 / 640 / 768 / 896 / 1024 threads: 2048^2 primal 35.6 /
-    // 26.3 / 23.0 / 23.7 / 24.5, dual form 35.1 / 28.3 / 25.7 / 26.1 / 27.2,
-    // 512 x 4096 11.3 / 11.6 / 12.1 / 12.1 / 12.2; above it the update
-    // bounds: 4096 x 512 70.0 / 52.6 / 43.8 / 41.3 / 41.0, 8192^2 201 / 160 /
-    // 150 / 147 / 147)
-    sh.threads = threads > 0 ? threads
-                             : (dual >= 2 && (long long)M * P < (1ll << 24) ? 768 : kMaxThreads);
+    // Default CTA size.  The one-pivot kernels take 1024 threads.  The
+    // two-pivot kernels size their update threads so that each forms about
+    // 25 + m / 68 rows of its vector column per pass: where the selection
+    // chain bounds the pass, fewer update threads leave it more of the memory
+    // system, and a longer chain (more rows) hides a longer update.  Measured
+    // pivot-kernel us per pivot at 512 / 640 / 768 / 1024 threads (rule's
+    // choice marked *): 512 x 4096 11.3* / 11.6 / 12.1 / 12.2, 256 x 8192
+    // 10.6* / 11.0 / 11.2 / 11.5, 1024^2 13.3* / 13.2 / 13.7 / 14.1, 1536^2
+    // 17.6 / 16.9* / 17.9 / 19.4, 1024 x 4096 19.5 / 17.0 / 17.2* (704) /
+    // 18.8, 2048^2 35.6 / 26.3 / 23.0* / 24.5 (dual form 35.1 / 28.3 / 25.7* /
+    // 27.2), 3072^2 73.1 / 53.5 / 45.3 / 42.5*, 4096 x 512 70.0 / 52.6 / 43.8
+    // / 41.0*, 8192^2 201 / 160 / 150 / 147*.  With vectors
+    // left in place only the structural share of the columns counts.
+    if (threads > 0) {
+        sh.threads = threads;
+    } else if (dual >= 2) {
+        const long long g0 = (long long)M * P >= (1ll << 19) ? sms : (sms + 1) / 2;
+        long long w0 = (P + g0 - 1) / g0;
+        w0 = (w0 + sector - 1) / sector * sector;
+        double vpr = (double)w0 / vw;
+        if (split > 0) vpr *= (double)split / (double)P;
+        const int m = M - 1;
+        const double rows = 25.0 + m / 68.0;
+        const int sel = (long long)M * P * (long long)esz < (384ll << 20) ? 256 : 128;
+        const double nu_want = m * vpr / rows;
+        sh.threads = (int)((nu_want + sel) / 32.0 + 0.5) * 32;
+    } else {
+        sh.threads = kMaxThreads;
+    }
     sh.threads = std::min(kMaxThreads, std::max(2 * kSelThreadsMax, (sh.threads + 31) / 32 * 32));
     const int nu = sh.threads - kSelThreadsMax;
     // Default grid: every SM.  A pivot costs the selection chain plus the
