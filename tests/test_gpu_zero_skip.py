@@ -167,3 +167,73 @@ def test_wide_lp_keeps_one_strip():
     _, st, it, f, z = _solve_counts(A, b, c, MAX_LE)
     assert st == o.status and it == o.iters and z == 0
     assert_same(Run(A, b, c), o)
+
+
+def test_phase1_then_vectors_in_place():
+    """Phase I (some b_i < 0): Phase 1 runs the dual rule (negative pivots
+    write -0 entries), Phase 2 the primal kernel, which first finds the
+    vectors holding a -0 and leaves only the others in place; the oracle's
+    pivots and bits."""
+    A, b, c = lpgen.dense_lp(300, 200, seed=1)
+    A, b = lpgen.with_ge_rows(A, b, 0.1, seed=2)
+    o = _oracle(A, b, c)
+    assert o.status == oracle.OPTIMAL
+    for pipeline in (1, 4, 5):
+        assert_same(Run(A, b, c, pipeline=pipeline, zero_skip=2), o)
+
+
+@pytest.mark.parametrize("e", [70, 130])
+def test_scaled_lps_in_place(e):
+    """Rows and columns scaled by 2^+-e (quotients outside the screening
+    window, entries near the ends of the FP64 range): the oracle's bits."""
+    from test_gpu_scaled import scaled_lp
+    (A, b, c), eps, _ = scaled_lp(120, 150, e, seed=e)
+    o = _oracle(A, b, c, **eps)
+    assert o.status == oracle.OPTIMAL
+    assert_same(Run(A, b, c, pipeline=4, zero_skip=2, **eps), o)
+
+
+@pytest.mark.parametrize("chunk", [1, 7, 64])
+def test_resumed_in_chunks(chunk):
+    """Solves of a few pivots per call: each launch starts from one buffer,
+    leaves vectors in the other and hands one buffer back; the oracle's
+    pivots and bits after every call's worth, at the end."""
+    A, b, c = lpgen.dense_lp(700, 900, seed=13)
+    o = _oracle(A, b, c)
+    m, n = A.shape
+    h = capi.lp_create(capi.lp_options_default(pipeline=4, zero_skip=2, max_iters=chunk,
+                                               trace_cap=4096))
+    try:
+        capi.lp_load(h, A, b, c)
+        for _ in range(100000):
+            capi.lp_solve(h)
+            x, y = np.empty(n), np.empty(m)
+            obj, st, it = capi.lp_result(h, x, y)
+            if st != capi.LP_ITER_LIMIT:
+                break
+        assert st == o.status and it == o.iters
+        assert _bits([obj])[0] == _bits([o.obj])[0]
+        assert np.array_equal(_bits(x), _bits(o.x)) and np.array_equal(_bits(y), _bits(o.y))
+        assert np.array_equal(_bits(capi.lp_get_tableau(h, m, n)), _bits(o.T))
+    finally:
+        capi.lp_destroy(h)
+
+
+def test_fp32_nearly_dependent_same_bits():
+    """The nearly-dependent-rows family in FP32 mode (body refreshes and
+    dual-rule recovery between the primal launches): the same bits with
+    vectors left in place as without."""
+    A, b, c = lpgen.nearly_dependent_lp(600, 600, seed=3)
+    out = []
+    for zs in (2, 0):
+        h = capi.lp_create(capi.lp_options_default(precision=capi.LP_FP32_REINV, zero_skip=zs,
+                                                   reinv_k=7))
+        try:
+            capi.lp_load(h, A, b, c)
+            capi.lp_solve(h)
+            x = np.empty(A.shape[1])
+            obj, st, it = capi.lp_result(h, x)
+        finally:
+            capi.lp_destroy(h)
+        out.append((_bits([obj])[0], st, it, _bits(x)))
+    assert out[0][:3] == out[1][:3] and np.array_equal(out[0][3], out[1][3])
