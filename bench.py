@@ -26,7 +26,8 @@ one pass over the tableau, and vectors left in place are not moved.
 
 Other workloads (--workload): lp2048set (2048^2 primal and dual form,
 512 x 4096, 4096 x 512), paperset (the same shapes from the paper's random
-family), batch1024, serve, product (the emulated-FP64 product alone).
+family), batch1024, serve, servespill (servers that spill idle LPs to host
+memory, off and on), product (the emulated-FP64 product alone).
 """
 import argparse
 import json
@@ -395,6 +396,93 @@ def run_serve(args, capi, torch):
                       "fp64": {"stream_at_saturation": fp64_stream, "sweep": fp64_pts},
                       "fp32_reinv_k50": {"stream_at_saturation": fp32_stream, "sweep": fp32_pts,
                                          "max_obj_rel_err_vs_fp64_server": err}}), flush=True)
+
+def run_serve_spill(args, capi, torch):
+    """Spilling idle LPs to host memory (lp_options.spill_pivots), with it off
+    and on, on two streams where some LPs hold the device for long:
+    - FP64: a Poisson stream (100 requests/s) of small dense LPs (m, n
+      log-uniform in [64, 512]) with one LP of the paper's family at 2048^2
+      (seeds 1 and 2 in turn; seed 1 takes 24734 pivots, 0.55 s alone) in
+      every 100 requests; LPs of at least 2^22 tableau elements run alone,
+      and with spilling on they run 400 pivots at a time and are spilled
+      while others wait;
+    - FP32 + FP64 reinversion every 50 pivots: a Poisson stream (100/s) of
+      LPs of the paper's family, m and n log-uniform in [256, 1024] (tens to
+      thousands of pivots), under a 64 MB budget (a few LPs at a time); with
+      spilling on, LPs that made 100 pivots since their admission are spilled
+      between rounds when the queue head does not fit.
+    Latency percentiles of the small and of the large LPs (FP64) or of all of
+    them (FP32), served rate, spills; the results are the same bits with
+    spilling off and on (checked)."""
+    import numpy as np
+    from paper_1804_04737_gb300 import lpgen
+    count = 250 if args.steps <= 5 else 500
+
+    def stream(opt, budget, lps, rate, seed):
+        srv = capi.lp_server_create(opt, hbm_budget_bytes=budget, max_slots=256)
+        try:
+            arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=len(lps)))
+            tickets = []
+            t0 = time.perf_counter()
+            for (A, b, c), ta in zip(lps, arrivals):
+                d = t0 + ta - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(capi.lp_server_submit(srv, A, b, c))
+            res = [capi.lp_server_wait(srv, t, A.shape[0], A.shape[1], timeout_s=600)
+                   for t, (A, _, _) in zip(tickets, lps)]
+            span = time.perf_counter() - t0
+            sp, rs, host = capi.lp_server_spill_stats(srv)
+        finally:
+            capi.lp_server_destroy(srv)
+        return res, span, {"spills": sp, "restores": rs, "pinned_host_mb": round(host / 2 ** 20, 1)}
+
+    def pct(v):
+        return {"p50_ms": round(float(np.percentile(v, 50)), 2),
+                "p99_ms": round(float(np.percentile(v, 99)), 2)}
+
+    def same(ra, rb):
+        return all(a[1] == b[1] and a[2] == b[2] and
+                   np.array_equal(np.asarray(a[3]).view(np.uint64), np.asarray(b[3]).view(np.uint64))
+                   for a, b in zip(ra, rb))
+
+    out = {"workload": "serving with spilling of idle LPs to host memory", "requests": count}
+    # FP64: small LPs and large ones that run alone
+    smalls = [lpgen.dense_lp(m, n, seed=k) for k, (m, n) in
+              enumerate(lpgen.log_uniform_shapes(96, 64, 512, seed=3))]
+    bigs = [lpgen.paper_lp(2048, 2048, seed=s) for s in (1, 2)]
+    lps, big = [], []
+    for k in range(count):
+        big.append(k % 100 == 12)
+        lps.append(bigs[(k // 100) % 2] if big[-1] else smalls[k % len(smalls)])
+    fp64 = {}
+    runs = {}
+    for spill in (0, 400):
+        opt = capi.lp_options_default(solo_elems=1 << 22, spill_pivots=spill)
+        res, span, st = stream(opt, 8 << 30, lps, 100.0, 5)
+        lat = np.array([r[5] for r in res])
+        isbig = np.array(big)
+        fp64["spill_pivots_%d" % spill] = {
+            "lps_per_s": round(len(lps) / span, 1), "small": pct(lat[~isbig]),
+            "large": pct(lat[isbig]), **st}
+        runs[spill] = res
+    fp64["same_results"] = same(runs[0], runs[400])
+    out["fp64_small_lps_and_2048sq_alone_100_per_s"] = fp64
+    # FP32 rounds under a small budget
+    lps32 = [lpgen.paper_lp(m, n, seed=100 + k) for k, (m, n) in
+             enumerate(lpgen.log_uniform_shapes(count // 2, 256, 1024, seed=4))]
+    fp32 = {}
+    runs = {}
+    for spill in (0, 100):
+        opt = capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50, spill_pivots=spill)
+        res, span, st = stream(opt, 64 << 20, lps32, 100.0, 6)
+        lat = np.array([r[5] for r in res])
+        fp32["spill_pivots_%d" % spill] = {"lps_per_s": round(len(lps32) / span, 1), **pct(lat), **st}
+        runs[spill] = res
+    fp32["same_results"] = same(runs[0], runs[100])
+    out["fp32_reinv_k50_paper_family_256_1024_budget_64mb_100_per_s"] = fp32
+    print(json.dumps(out), flush=True)
+
 
 def cpu_oracle_run(lps, threads, cap=None):
     """Pivots and seconds of the oracle's pivoting on the workload (the Step 1
@@ -770,7 +858,8 @@ def main():
     ap.add_argument("--impl", default="gbsimplex", choices=["gbsimplex", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="lp8192",
-                    choices=["lp8192", "lp2048set", "paperset", "batch1024", "serve", "product"],
+                    choices=["lp8192", "lp2048set", "paperset", "batch1024", "serve", "servespill",
+                             "product"],
                     help="lp8192 is the headline line; the others report their own figures")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -785,8 +874,8 @@ def main():
     from paper_1804_04737_gb300 import capi
 
     torch.cuda.set_device(local)
-    if args.workload in ("batch1024", "serve", "product"):
-        return {"batch1024": run_batch, "serve": run_serve,
+    if args.workload in ("batch1024", "serve", "servespill", "product"):
+        return {"batch1024": run_batch, "serve": run_serve, "servespill": run_serve_spill,
                 "product": run_product}[args.workload](args, capi, torch)
     dist = None
     if world > 1:

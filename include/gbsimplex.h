@@ -204,6 +204,26 @@ typedef struct {
                                 and shape (slower where the selection chain
                                 bounds the pass).  Same pivots and bits in
                                 every mode.                                     */
+    long long spill_pivots;  /* servers: 0 (default) = an admitted LP keeps its
+                                HBM until it ends.  > 0 = an LP idle on the
+                                device that has made at least this many pivots
+                                since it was last admitted may be spilled when
+                                the request at the head of the queue cannot be
+                                admitted (no slot, not enough of the budget,
+                                or, for an LP that runs alone, any LP in
+                                flight): its tableau and solver state are
+                                copied to pinned host memory, its HBM and slot
+                                are returned, and it goes to the back of the
+                                queue; readmitted, it pivots on from where it
+                                stopped, bit for bit as if never spilled.  Idle
+                                LPs: those of the FP32 server between its
+                                rounds, and an FP64 LP that runs alone
+                                (solo_elems), which pivots spill_pivots at a
+                                time and is spilled at the end of a slice when
+                                any request is waiting.  The FP64 server
+                                kernel's LPs and FP32 LPs that run alone
+                                (whose reinversion schedule restarts with each
+                                call) run to their end.  Ignored elsewhere.     */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
@@ -331,6 +351,11 @@ lp_err lp_server_wait(lp_server *srv, unsigned long long ticket, double timeout_
  * waiting for admission. */
 lp_err lp_server_stats(lp_server *srv, long long *completed, long long *launches,
                        size_t *hbm_used, int *queued);
+/* Spilling (lp_options.spill_pivots): LPs spilled to host memory and
+ * readmitted so far, and the pinned host bytes the server holds for spills
+ * (buffers are reused; freed by lp_server_destroy).  NULL outputs skipped. */
+lp_err lp_server_spill_stats(lp_server *srv, long long *spills, long long *restores,
+                             size_t *host_bytes);
 /* Finishes the requests in flight, then frees everything.  NULL allowed. */
 void lp_server_destroy(lp_server *srv);
 

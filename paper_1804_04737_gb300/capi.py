@@ -51,6 +51,7 @@ class lp_options(ctypes.Structure):
         ("time_limit_s", ctypes.c_double),
         ("reinv_body", ctypes.c_int),
         ("zero_skip", ctypes.c_int),
+        ("spill_pivots", ctypes.c_longlong),
     ]
 
 
@@ -115,6 +116,9 @@ _SIGS = [
                                        ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(ctypes.c_int)]),
+    ("lp_server_spill_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_size_t)]),
     ("lp_server_destroy", None, [ctypes.c_void_p]),
     ("lp_fp32_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), _c_double_p,
                                      _c_double_p]),
@@ -406,6 +410,14 @@ def lp_server_stats(srv):
     _check(load_library().lp_server_stats(srv, ctypes.byref(c), ctypes.byref(l), ctypes.byref(u),
                                           ctypes.byref(q)))
     return c.value, l.value, u.value, q.value
+
+
+def lp_server_spill_stats(srv):
+    """(LPs spilled to host memory, LPs readmitted, pinned host bytes held)."""
+    sp, rs, hb = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()
+    _check(load_library().lp_server_spill_stats(srv, ctypes.byref(sp), ctypes.byref(rs),
+                                                ctypes.byref(hb)))
+    return sp.value, rs.value, hb.value
 
 
 def lp_server_destroy(srv) -> None:

@@ -211,6 +211,7 @@ void lp_options_default(lp_options *o) {
     o->pipeline = 1;
     o->reinv_body = 1;
     o->zero_skip = 1;
+    o->spill_pivots = 0;
 }
 
 const char *lp_version(void) { return "gbsimplex 0.1 (sm_103a)"; }
@@ -1056,5 +1057,9 @@ lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes) {
 }
 
 size_t handle_region_used(const lp_handle *h) { return h ? h->region_used : 0; }
+
+void handle_set_max_iters(lp_handle *h, long long n) {
+    if (h) h->opt.max_iters = n;
+}
 
 }  // namespace gbs

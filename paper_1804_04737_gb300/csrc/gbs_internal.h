@@ -321,6 +321,9 @@ void set_last_error_global(const char *msg);
 // small; handle_region_used reports the bytes taken so far.
 lp_err handle_bind_region(lp_handle *h, void *base, size_t bytes);
 size_t handle_region_used(const lp_handle *h);
+// Pivots per lp_solve call of a handle (its lp_options.max_iters): the
+// servers cut the solve of an LP that runs alone into slices with it.
+void handle_set_max_iters(lp_handle *h, long long n);
 
 cudaError_t launch_to_fp64(const float *T, long long P, int M, int N, double *out,
                            cudaStream_t s);

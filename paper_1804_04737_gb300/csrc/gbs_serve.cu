@@ -109,6 +109,19 @@ struct Request {
     long long iters = 0;
     lp_err err = LP_OK;
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    // spilled to pinned host memory (lp_options.spill_pivots): FP32 rounds,
+    // the slot's bytes and the engine's state of the LP; an LP run alone,
+    // the bytes of its handle's range of the arena (the handle keeps the
+    // host-side state)
+    bool spilled = false;
+    unsigned char *host = nullptr;
+    size_t host_cap = 0;            // bytes of the pinned buffer
+    size_t host_used = 0;           // bytes copied into it
+    long long resident_from = 0;    // pivots made when last (re)admitted
+    LpDesc d32{};
+    int rule32 = 0, failed32 = 0;
+    long long remaining32 = 0, guard32 = 0;
+    lp_handle *solo_h = nullptr;
 };
 
 }  // namespace
@@ -162,6 +175,13 @@ struct lp_server {
     std::vector<long long> remaining, guard, before;
     ReinvPool *rp = nullptr;
     BatchReinv ws32;
+    // spilling (lp_options.spill_pivots): pinned host buffers not in use, by
+    // size, every pinned buffer allocated, and the counts
+    long long spill_pivots = 0;
+    std::multimap<size_t, unsigned char *> host_free;
+    std::vector<std::pair<unsigned char *, size_t>> host_all;
+    size_t host_total = 0;
+    long long spills = 0, restores = 0;
 };
 
 namespace {
@@ -227,6 +247,39 @@ bool is_solo(const lp_server *sv, const Request &r) {
     return sv->solo_elems >= 0 && !r.solo_oom &&
            (long long)(r.m + 1) * pitch_for(r.n + r.m + 1) >= sv->solo_elems;
 }
+
+// A server-wide failure: every waiting call returns `code` from now on.
+void set_fatal(lp_server *sv, lp_err code, const char *what, cudaError_t e) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->fatal = code;
+    snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "%s: %s", what, cudaGetErrorString(e));
+    sv->cv.notify_all();
+}
+
+// A pinned host buffer of at least `bytes` for a spill: the smallest free
+// one of at most twice the size, else a new one (nullptr when the host
+// cannot pin more; the LP then stays).
+unsigned char *host_take(lp_server *sv, size_t bytes, size_t *cap) {
+    auto it = sv->host_free.lower_bound(bytes);
+    if (it != sv->host_free.end() && it->first / 2 <= bytes) {
+        unsigned char *p = it->second;
+        *cap = it->first;
+        sv->host_free.erase(it);
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, std::max<size_t>(bytes, 1), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    sv->host_all.push_back({static_cast<unsigned char *>(p), bytes});
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->host_total += bytes;
+    *cap = bytes;
+    return static_cast<unsigned char *>(p);
+}
+
+void host_give(lp_server *sv, unsigned char *p, size_t cap) { sv->host_free.emplace(cap, p); }
 
 // Copy results of finished slots back and release their resources.
 bool engine_complete(lp_server *sv) {
@@ -446,7 +499,7 @@ bool admit32(lp_server *sv) {
             const unsigned long long t = sv->queue.front();
             Request &r = sv->reqs[t];
             if (is_solo(sv, r)) break;
-            group_shape32(sv, r.m, r.n, &r.group, &r.strip);
+            if (!r.spilled) group_shape32(sv, r.m, r.n, &r.group, &r.strip);
             const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group, sizeof(float));
             size_t off;
             if (!sv->arena.alloc(L.total, &off)) break;
@@ -468,6 +521,10 @@ bool admit32(lp_server *sv) {
         Request &r = *adm[k].second;
         const SlotLayout L = slot_layout(r.m, r.n, pitch_for(r.n + r.m + 1), r.group, sizeof(float));
         unsigned char *base = sv->arena_dev + r.off;
+        if (r.spilled) {  // the slot's bytes as they were spilled
+            cudaMemcpyAsync(base, r.host, r.host_used, cudaMemcpyHostToDevice, s);
+            continue;
+        }
         const double *A = reinterpret_cast<const double *>(base + L.in);
         cudaMemcpyAsync(base + L.in, r.in.data(), r.in.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s);
@@ -476,7 +533,11 @@ bool admit32(lp_server *sv) {
                        reinterpret_cast<InputStats *>(base + L.stats), s);
         cudaMemcpyAsync(&st[k], base + L.stats, sizeof(InputStats), cudaMemcpyDeviceToHost, s);
     }
-    cudaStreamSynchronize(s);
+    const cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+        set_fatal(sv, LP_ERR_CUDA, "FP32 admission", ce);
+        return true;
+    }
     for (size_t k = 0; k < adm.size(); ++k) {
         const int slot = adm[k].first;
         Request &r = *adm[k].second;
@@ -484,6 +545,29 @@ bool admit32(lp_server *sv) {
         const long long P = pitch_for(n + m + 1);
         const SlotLayout L = slot_layout(m, n, P, r.group, sizeof(float));
         unsigned char *base = sv->arena_dev + r.off;
+        if (r.spilled) {
+            // readmitted: the descriptor's pointers into the slot's new
+            // place, the engine's state as it was
+            LpDesc d = r.d32;
+            d.T = base + L.T;
+            d.basis = reinterpret_cast<int *>(base + L.basis);
+            d.part_sel = reinterpret_cast<Cand *>(base + L.part);
+            d.bar = reinterpret_cast<unsigned *>(base + L.bar);
+            d.err = reinterpret_cast<int *>(d.bar + 96);
+            sv->h_desc32[slot] = d;
+            sv->rule[slot] = r.rule32;
+            sv->failed[slot] = r.failed32;
+            sv->remaining[slot] = r.remaining32;
+            sv->guard[slot] = r.guard32;
+            sv->active.push_back(slot);
+            host_give(sv, r.host, r.host_cap);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r.host = nullptr;
+            r.spilled = false;
+            r.resident_from = d.iters;
+            ++sv->restores;
+            continue;
+        }
         lp_err err = LP_OK;
         if (st[k].flags & 4) err = LP_ERR_INVALID_ARG;
         else if (r.sense == LP_MAX_LE && (st[k].flags & 1)) err = LP_ERR_INFEASIBLE_START;
@@ -522,8 +606,108 @@ bool admit32(lp_server *sv) {
         sv->remaining[slot] = sv->opt.max_iters;
         sv->guard[slot] = 20ll * (m + n) + 1000;
         sv->active.push_back(slot);
+        r.resident_from = 0;
     }
     return true;
+}
+
+// Spill the FP32 LP in `slot`, idle between rounds: the slot's bytes to a
+// pinned host buffer, the descriptor and the engine's state of the LP to the
+// request; the slot and its HBM are returned and the request goes to the back
+// of the queue.  False (the LP stays) when no host buffer can be had.
+bool spill32(lp_server *sv, int slot) {
+    unsigned long long t;
+    Request *r;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        t = sv->slot_ticket[slot];
+        r = &sv->reqs[t];
+    }
+    size_t cap = 0;
+    unsigned char *hp = host_take(sv, r->bytes, &cap);
+    if (!hp) return false;
+    cudaError_t e = cudaMemcpyAsync(hp, sv->arena_dev + r->off, r->bytes, cudaMemcpyDeviceToHost,
+                                    sv->kstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sv->kstream);
+    if (e != cudaSuccess) {
+        host_give(sv, hp, cap);
+        set_fatal(sv, LP_ERR_CUDA, "FP32 spill", e);
+        return false;
+    }
+    r->d32 = sv->h_desc32[slot];
+    r->rule32 = sv->rule[slot];
+    r->failed32 = sv->failed[slot];
+    r->remaining32 = sv->remaining[slot];
+    r->guard32 = sv->guard[slot];
+    sv->active.erase(std::find(sv->active.begin(), sv->active.end(), slot));
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->host = hp;
+    r->host_cap = cap;
+    r->host_used = r->bytes;
+    r->spilled = true;
+    sv->arena.release(r->off, r->bytes);
+    sv->slot_ticket[slot] = 0;
+    sv->free_slots.push_back(slot);
+    r->slot = -1;
+    r->state = QUEUED;
+    sv->queue.push_back(t);
+    ++sv->spills;
+    return true;
+}
+
+// Between rounds, with spill_pivots > 0: when the request at the head of the
+// queue cannot be admitted (no free slot or not enough of the budget), spill
+// the LPs in the rounds that have pivoted at least spill_pivots times since
+// they were last admitted, longest-running first, until it can; for an LP
+// that runs alone (which needs the whole arena) only once every LP in the
+// rounds may go.  Nothing is spilled when the eligible LPs could not make
+// room.
+void evict32(lp_server *sv) {
+    if (sv->spill_pivots <= 0 || sv->active.empty()) return;
+    std::vector<std::pair<long long, int>> cand;  // (pivots since admission, slot)
+    bool solo = false;
+    size_t need = 0, freeable = 0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->fatal != LP_OK || sv->queue.empty()) return;
+        for (int slot : sv->active) {
+            const Request &r = sv->reqs[sv->slot_ticket[slot]];
+            const long long run = sv->h_desc32[slot].iters - r.resident_from;
+            if (run >= sv->spill_pivots) {
+                cand.push_back({run, slot});
+                freeable += up256(r.bytes);
+            }
+        }
+        if (cand.empty()) return;
+        Request &h = sv->reqs[sv->queue.front()];
+        solo = is_solo(sv, h);
+        if (!solo) {
+            if (!h.spilled) group_shape32(sv, h.m, h.n, &h.group, &h.strip);
+            need = up256(slot_layout(h.m, h.n, pitch_for(h.n + h.m + 1), h.group, sizeof(float)).total);
+            if (sv->arena.size() - sv->arena.used() + freeable < need) return;
+        }
+    }
+    std::stable_sort(cand.begin(), cand.end(),
+                     [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) {
+                         return a.first > b.first;
+                     });
+    if (solo) {
+        if (cand.size() != sv->active.size()) return;
+        for (const auto &c : cand)
+            if (!spill32(sv, c.second)) return;
+        return;
+    }
+    auto admissible = [&]() {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        size_t off;
+        if (sv->free_slots.empty() || !sv->arena.alloc(need, &off)) return false;
+        sv->arena.release(off, need);
+        return true;
+    };
+    for (const auto &c : cand) {
+        if (admissible()) return;
+        if (!spill32(sv, c.second)) return;
+    }
 }
 
 // One round: every admitted LP pivots up to reinv_k times in one batched
@@ -660,6 +844,7 @@ void engine32_main(lp_server *sv) {
             std::lock_guard<std::mutex> lk(sv->mu);
             fatal = sv->fatal != LP_OK;
         }
+        if (!fatal) evict32(sv);
         const bool admitted = !fatal && admit32(sv);
         if (!fatal && !sv->active.empty()) {
             round32(sv);
@@ -703,8 +888,9 @@ bool engine_solo(lp_server *sv) {
     }
     const int m = r->m, n = r->n;
     const double *A = r->in.data(), *b = A + (size_t)m * n, *c = b + m;
+    const bool resume = r->spilled;
     bool bneg = false;
-    for (int i = 0; i < m; ++i) bneg |= b[i] < 0.0;
+    for (int i = 0; !resume && i < m; ++i) bneg |= b[i] < 0.0;
     if (bneg && r->sense == LP_MAX_LE)
         for (double v : r->in)
             if (!isfinite(v)) { bneg = false; break; }  // lp_load reports the non-finite input
@@ -714,8 +900,30 @@ bool engine_solo(lp_server *sv) {
     lp_status st = LP_NOT_SOLVED;
     long long iters = 0;
     lp_err verdict = LP_OK, e = LP_OK;
+    lp_handle *h = nullptr;
+    bool spilled = false;
+    char why[160] = {0};
     if (bneg && r->sense == LP_MAX_LE) {
         verdict = LP_ERR_INFEASIBLE_START;
+    } else if (resume) {
+        // A spilled LP: its handle's range of the arena back in place (the
+        // range starts at the arena's base, where every LP that runs alone
+        // starts), then the handle pivots on from where it stopped.
+        h = r->solo_h;
+        iters = r->iters;  // pivots made before the spill
+        cudaError_t ce = cudaMemcpyAsync(sv->arena_dev + off, r->host, r->host_used,
+                                         cudaMemcpyHostToDevice, sv->kstream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(sv->kstream);
+        host_give(sv, r->host, r->host_cap);
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->host = nullptr;
+        r->spilled = false;
+        r->solo_h = nullptr;
+        ++sv->restores;
+        if (ce != cudaSuccess) {
+            e = LP_ERR_CUDA;
+            snprintf(why, sizeof why, "restoring a spilled LP: %s", cudaGetErrorString(ce));
+        }
     } else {
         if (!sv->solo) {
             lp_options o = sv->opt;
@@ -723,30 +931,76 @@ bool engine_solo(lp_server *sv) {
             o.cuda_stream = nullptr;
             e = lp_create(&sv->solo, &o);
         }
-        if (e == LP_OK) e = handle_bind_region(sv->solo, sv->arena_dev + off, bytes);
-        if (e == LP_OK) e = lp_load(sv->solo, m, n, A, b, c, (lp_sense)r->sense);
-        if (e == LP_OK) {
-            e = lp_solve(sv->solo);
+        h = sv->solo;
+        if (e == LP_OK) e = handle_bind_region(h, sv->arena_dev + off, bytes);
+        if (e == LP_OK) e = lp_load(h, m, n, A, b, c, (lp_sense)r->sense);
+        if (e == LP_OK) r->resident_from = 0;
+    }
+    // FP64 with spill_pivots: slices of spill_pivots pivots (an FP64 solve
+    // cut into calls makes the same pivots, bit for bit); after a slice, when
+    // any request is waiting, the LP is spilled and goes to the back of the
+    // queue
+    const bool sliced = sv->spill_pivots > 0 && !sv->fp32;
+    while (h && e == LP_OK && verdict == LP_OK) {
+        if (sliced) handle_set_max_iters(h, std::min(sv->spill_pivots, sv->opt.max_iters - iters));
+        e = lp_solve(h);
+        {
             std::lock_guard<std::mutex> lk(sv->mu);
             ++sv->launches;
         }
-        if (e == LP_OK) e = lp_result(sv->solo, r->x.data(), r->y.data(), &obj, &st, &iters);
-        if (e == LP_ERR_INVALID_ARG || e == LP_ERR_INFEASIBLE_START) {
-            verdict = e;
-            e = LP_OK;
+        if (e == LP_OK) e = lp_result(h, r->x.data(), r->y.data(), &obj, &st, &iters);
+        if (e != LP_OK || !sliced || st != LP_ITER_LIMIT || iters >= sv->opt.max_iters) break;
+        bool waiting;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            waiting = !sv->queue.empty();
         }
+        if (!waiting) continue;
+        const size_t used = handle_region_used(h);
+        size_t cap = 0;
+        unsigned char *hp = host_take(sv, used, &cap);
+        if (!hp) continue;  // no host memory to spill to: pivot on
+        cudaError_t ce = cudaMemcpyAsync(hp, sv->arena_dev + off, used, cudaMemcpyDeviceToHost,
+                                         sv->kstream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(sv->kstream);
+        if (ce != cudaSuccess) {
+            host_give(sv, hp, cap);
+            e = LP_ERR_CUDA;
+            snprintf(why, sizeof why, "spilling an LP: %s", cudaGetErrorString(ce));
+            break;
+        }
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->iters = iters;
+        r->host = hp;
+        r->host_cap = cap;
+        r->host_used = used;
+        r->solo_h = h;
+        if (h == sv->solo) sv->solo = nullptr;  // the next LP that runs alone takes a new handle
+        r->spilled = true;
+        ++sv->spills;
+        spilled = true;
+        break;
+    }
+    if (e == LP_ERR_INVALID_ARG || e == LP_ERR_INFEASIBLE_START) {
+        verdict = e;
+        e = LP_OK;
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->arena.release(off, bytes);
-    if (e == LP_ERR_OOM) {
+    unsigned long long tk = 0;
+    for (auto &t : sv->reqs)
+        if (&t.second == r) { tk = t.first; break; }
+    if (spilled) {
+        r->state = QUEUED;
+        sv->queue.push_back(tk);
+    } else if (e == LP_ERR_OOM) {
         r->solo_oom = true;
         r->state = QUEUED;
-        for (auto &t : sv->reqs)
-            if (&t.second == r) { sv->queue.push_front(t.first); break; }
+        sv->queue.push_front(tk);
     } else if (e != LP_OK) {
         sv->fatal = e;
         snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "server solve of a large LP: %s",
-                 lp_last_error(sv->solo));
+                 why[0] ? why : lp_last_error(h));
     } else {
         r->err = verdict;
         r->status = verdict == LP_OK ? (int)st : LP_NOT_SOLVED;
@@ -755,6 +1009,12 @@ bool engine_solo(lp_server *sv) {
         r->state = DONE;
         r->t_done = now_ms();
         ++sv->completed;
+    }
+    // a handle that carried a spilled LP to its end serves the next LP that
+    // runs alone, or goes
+    if (!spilled && h && h != sv->solo) {
+        if (!sv->solo) sv->solo = h;
+        else lp_destroy(h);
     }
     *(volatile int *)&sv->h_ring->shutdown = 0;
     sv->cv.notify_all();
@@ -792,7 +1052,8 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     if (max_slots < 1 || max_slots > kServeMaxSlots || hbm_budget_bytes < (1u << 20))
         return sfail(LP_ERR_INVALID_ARG, "lp_server_create: need 1 <= max_slots <= %d and a "
                      "budget of at least 1 MiB", kServeMaxSlots);
-    if (o.max_iters < 0 || o.bland_after < 0 || o.spin_timeout_cycles <= 0 || o.device < 0)
+    if (o.max_iters < 0 || o.bland_after < 0 || o.spin_timeout_cycles <= 0 || o.device < 0 ||
+        o.spill_pivots < 0)
         return sfail(LP_ERR_INVALID_ARG, "lp_server_create: option out of range");
     lp_server *sv = new (std::nothrow) lp_server();
     if (!sv) return sfail(LP_ERR_OOM, "lp_server_create: host allocation failed");
@@ -801,6 +1062,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->max_slots = max_slots;
     sv->fp32 = o.precision == LP_FP32_REINV;
     sv->solo_elems = o.solo_elems < 0 ? -1 : o.solo_elems > 0 ? o.solo_elems : 1ll << 24;
+    sv->spill_pivots = o.spill_pivots;
     DeviceRestore restore_;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
@@ -955,6 +1217,16 @@ lp_err lp_server_stats(lp_server *sv, long long *completed, long long *launches,
     return LP_OK;
 }
 
+lp_err lp_server_spill_stats(lp_server *sv, long long *spills, long long *restores,
+                             size_t *host_bytes) {
+    if (!sv) return sfail(LP_ERR_INVALID_ARG, "lp_server_spill_stats: NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (spills) *spills = sv->spills;
+    if (restores) *restores = sv->restores;
+    if (host_bytes) *host_bytes = sv->host_total;
+    return LP_OK;
+}
+
 void lp_server_destroy(lp_server *sv) {
     if (!sv) return;
     if (sv->engine.joinable()) {
@@ -980,6 +1252,8 @@ void lp_server_destroy(lp_server *sv) {
     if (sv->h_items) cudaFreeHost(sv->h_items);
     if (sv->d_queue) cudaFree(sv->d_queue);
     lp_destroy(sv->solo);  // its buffers are the arena's: nothing of it to free
+    for (auto &t : sv->reqs) lp_destroy(t.second.solo_h);  // LPs still spilled
+    for (auto &p : sv->host_all) cudaFreeHost(p.first);
     delete sv->rp;
     delete sv;
 }

@@ -77,7 +77,7 @@ def test_dual_2048_at_narrow_grids(ctas):
     (capi.LP_FP64, MAX_LE, 4), (capi.LP_FP64, MAX_LE, 5), (capi.LP_FP64, MIN_GE, 1),
     (capi.LP_FP64, MIN_GE, 2), (capi.LP_FP32_REINV, MAX_LE, 1)])
 def test_time_limit_ends_in_timeout_and_reload_solves(precision, sense, pipeline):
-    # the paper's own random family at 1024^2: 1445 pivots, tens of ms
+    # the paper's own random family at 1024^2, seed 1: 365 pivots, milliseconds
     A, b, c = lpgen.paper_lp(1024, 1024, seed=1)
     if sense == MIN_GE:
         A, b, c = lpgen.dual_of(A, b, c)
@@ -110,7 +110,7 @@ def test_time_limit_ends_in_timeout_and_reload_solves(precision, sense, pipeline
 
 
 def test_time_limit_same_handle_reload():
-    # the paper's family at 2048^2 takes 2172 pivots, tens of milliseconds
+    # the paper's family at 2048^2, seed 1: 24734 pivots, about half a second
     A, b, c = lpgen.paper_lp(2048, 2048, seed=1)
     h = capi.lp_create(capi.lp_options_default(time_limit_s=2e-3))
     try:
