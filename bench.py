@@ -314,7 +314,8 @@ def run_serve(args, capi, torch):
     the FP64 server and for FP32 tableaus with FP64 reinversion every 50
     pivots.  Then the stated stream: 20000 requests at each server's
     saturating rate, and one LP per launch (lp_load + lp_solve + lp_result,
-    FP64, one handle) over the same 20000 requests.  The requests cycle
+    FP64, one handle) over the same 20000 requests.  The FP64 server runs
+    twice: with its persistent kernel (lanes 0) and with three lanes.  The requests cycle
     through a pool of 512 distinct seeded LPs (20000 distinct ones would take
     about 150 GB of host memory and more generator time than the stream)."""
     import numpy as np
@@ -365,26 +366,31 @@ def run_serve(args, capi, torch):
             capi.lp_server_destroy(srv)
         return points, best, stream, objs
 
-    fp64_pts, fp64_best, fp64_stream, obj64 = sweep(capi.lp_options_default())
+    def one_per_launch():
+        # one LP per launch on the same 20000 requests (after one untimed pass
+        # over the pool, in which the handle's buffers grow)
+        h = capi.lp_create(capi.lp_options_default())
+        try:
+            for A, b, c in pool:
+                capi.lp_load(h, A, b, c)
+                capi.lp_solve(h)
+                capi.lp_result(h)
+            t0 = time.perf_counter()
+            for k in range(stream_len):
+                A, b, c = pool[k % len(pool)]
+                capi.lp_load(h, A, b, c)
+                capi.lp_solve(h)
+                capi.lp_result(h)
+            return stream_len / (time.perf_counter() - t0)
+        finally:
+            capi.lp_destroy(h)
+
+    one = one_per_launch()
+    fp64_pts, fp64_best, fp64_stream, obj64 = sweep(capi.lp_options_default(lanes=0))
+    lane_pts, lane_best, lane_stream, objl = sweep(capi.lp_options_default(lanes=3))
     fp32_pts, fp32_best, fp32_stream, obj32 = sweep(
         capi.lp_options_default(precision=capi.LP_FP32_REINV, reinv_k=50))
-    # one LP per launch on the same 20000 requests (after one untimed pass over
-    # the pool, in which the handle's buffers grow)
-    h = capi.lp_create(capi.lp_options_default())
-    try:
-        for A, b, c in pool:
-            capi.lp_load(h, A, b, c)
-            capi.lp_solve(h)
-            capi.lp_result(h)
-        t0 = time.perf_counter()
-        for k in range(stream_len):
-            A, b, c = pool[k % len(pool)]
-            capi.lp_load(h, A, b, c)
-            capi.lp_solve(h)
-            capi.lp_result(h)
-        one = stream_len / (time.perf_counter() - t0)
-    finally:
-        capi.lp_destroy(h)
+    one_after = one_per_launch()
     # the two streams hold the same LPs in the same order: FP32 against FP64
     err = max(abs(a - b) / max(1.0, abs(b)) for a, b in zip(obj32, obj64))
     print(json.dumps({"workload": "serving: Poisson stream of dense LPs, m,n log-uniform "
@@ -393,7 +399,10 @@ def run_serve(args, capi, torch):
                       "alone_from_tableau_elems": 1 << 24,  # lp_options.solo_elems default
                       "stream_requests": stream_len,
                       "one_lp_per_launch_fp64_lps_per_s": round(one, 1),
+                      "one_lp_per_launch_again_after_the_servers": round(one_after, 1),
                       "fp64": {"stream_at_saturation": fp64_stream, "sweep": fp64_pts},
+                      "fp64_3_lanes": {"stream_at_saturation": lane_stream, "sweep": lane_pts,
+                                       "same_objectives_as_server_kernel": objl == obj64},
                       "fp32_reinv_k50": {"stream_at_saturation": fp32_stream, "sweep": fp32_pts,
                                          "max_obj_rel_err_vs_fp64_server": err}}), flush=True)
 

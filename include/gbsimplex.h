@@ -224,12 +224,24 @@ typedef struct {
                                 kernel's LPs and FP32 LPs that run alone
                                 (whose reinversion schedule restarts with each
                                 call) run to their end.  Ignored elsewhere.     */
+    int lanes;               /* FP64 servers: L in 1..16 (default 3) = L lanes,
+                                each solving one LP at a time as lp_load +
+                                lp_solve + lp_result would (the kernels
+                                `pipeline` picks) on SMs / L CTAs and a 1 / L
+                                slice of the budget, the lanes' kernels sharing
+                                the GPU; an LP a slice cannot hold runs alone
+                                like one of solo_elems elements.  0 = the LPs
+                                below solo_elems run in the persistent server
+                                kernel instead, each on a group of CTAs with
+                                the one-pivot code.  Same bits either way.
+                                Ignored elsewhere.                              */
 } lp_options;
 
 /* Fill *opt with the defaults: FP64, reinv_k 50, max_iters 1e12, tolerances
  * by formula, bland_after 32, auto launch shape, spin timeout 4e9 cycles,
  * library stream, device 0, no trace, pipelined primal kernel, no wall-clock
- * limit. */
+ * limit, body refresh on, vectors left in place from 2^25 elements, no
+ * spilling, three FP64 server lanes. */
 void lp_options_default(lp_options *opt);
 
 /* Create a handle on opt->device (opt may be NULL for the defaults).
@@ -314,16 +326,19 @@ lp_err lp_batch_autotune(int count, const int *m, const int *n, const double *co
                          const lp_options *opt, const char *cache_path, lp_options *best);
 
 /* Serving with continuous batching (a library service; the paper solves one
- * LP at a time).  A server owns an HBM budget (one arena, first-fit
- * allocation) and up to max_slots LPs in flight.  Requests are admitted in
- * arrival order as slots and memory free up; admitted LPs are built, pivoted
- * and read off by a persistent kernel that takes new LPs while others are
- * running, so their work overlaps on the GPU.  Each LP runs on a group of
- * CTAs with the single-LP pivot code, so its result equals solving it alone
- * bit for bit.  An LP of at least opt->solo_elems tableau elements instead
- * runs alone, as lp_load + lp_solve run it, once the LPs ahead of it are
- * done (its buffers come from the same arena).  m, n <= 4096; inputs and
- * outputs in host memory.
+ * LP at a time).  A server owns an HBM budget (one arena) and takes requests
+ * in arrival order as memory (and, for its kernel, slots) free up.  FP64: by
+ * default (opt->lanes) a few lanes each solve one LP at a time as lp_load +
+ * lp_solve + lp_result would, on a share of the SMs and a slice of the
+ * budget, so the LPs' kernels overlap on the GPU; with opt->lanes 0 a
+ * persistent kernel builds, pivots and reads off the admitted LPs (up to
+ * max_slots in flight), taking new ones while others run, each on a group of
+ * CTAs with the single-LP pivot code.  Either way the result equals solving
+ * the LP alone, bit for bit.  An LP of at least opt->solo_elems tableau
+ * elements instead runs alone, as lp_load + lp_solve run it, once the LPs
+ * ahead of it are done (its buffers come from the same arena).  Inputs are
+ * staged in pinned host memory at submit.  m, n <= 4096; inputs and outputs
+ * in host memory.
  * With opt->precision == LP_FP32_REINV the tableaus are FP32 and the server
  * works in rounds: one batched launch in which every admitted LP pivots up
  * to reinv_k times, then each LP's FP64 reinversion and the decisions of the

@@ -52,6 +52,7 @@ class lp_options(ctypes.Structure):
         ("reinv_body", ctypes.c_int),
         ("zero_skip", ctypes.c_int),
         ("spill_pivots", ctypes.c_longlong),
+        ("lanes", ctypes.c_int),
     ]
 
 

@@ -212,6 +212,7 @@ void lp_options_default(lp_options *o) {
     o->reinv_body = 1;
     o->zero_skip = 1;
     o->spill_pivots = 0;
+    o->lanes = 3;
 }
 
 const char *lp_version(void) { return "gbsimplex 0.1 (sm_103a)"; }

@@ -359,6 +359,15 @@ cudaError_t oz_refresh_body(const double *A, const double *b, int sense, int m, 
                             long long P, OzWork &w, int sms, long long spin_limit,
                             cudaStream_t s);
 
+// Raise a kernel's dynamic shared memory limit (cudaFuncAttributeMax-
+// DynamicSharedMemorySize, a per-function setting shared by every host
+// thread) to the most the current device allows beside the kernel's static
+// shared memory.  Every launch site sets this same value, so host threads
+// that launch one kernel at once with different sizes (handles on different
+// threads) never lower the limit under one another's launch.  The value per
+// kernel and device is looked up once.
+cudaError_t allow_dyn_smem(const void *fn);
+
 // Host side: restores the caller's current device when an entry point that
 // switched to its own device returns.
 struct DeviceRestore {

@@ -2585,8 +2585,7 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                           : (sh.dist ? (const void *)pivot_block_kernel<float, 4, true, false>
                                                      : (const void *)pivot_block_kernel<float, 4, false, false>)));
         if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sh.smem_bytes);
+            cudaError_t e = allow_dyn_smem(fn);
             if (e != cudaSuccess) return e;
         }
         return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads),
@@ -2596,8 +2595,7 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
         const void *fn = prec == PREC_FP64 ? (const void *)pivot_pipe_dual_kernel<double, 4>
                                            : (const void *)pivot_pipe_dual_kernel<float, 4>;
         if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sh.smem_bytes);
+            cudaError_t e = allow_dyn_smem(fn);
             if (e != cudaSuccess) return e;
         }
         return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args,
@@ -2609,8 +2607,7 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                          : (sh.pipe == 2 ? (const void *)pivot_pipe_kernel<float, 2>
                                          : (const void *)pivot_pipe_kernel<float, 4>);
     if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sh.smem_bytes);
+        cudaError_t e = allow_dyn_smem(fn);
         if (e != cudaSuccess) return e;
     }
     return cudaLaunchCooperativeKernel(fn, dim3(sh.ctas), dim3(sh.threads), args, sh.smem_bytes, s);

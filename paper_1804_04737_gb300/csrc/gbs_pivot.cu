@@ -43,13 +43,42 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <stddef.h>
 #include <stdint.h>
+#include <utility>
 
 #include "gbs_device.cuh"
 #include "gbs_internal.h"
 
 namespace gbs {
+
+cudaError_t allow_dyn_smem(const void *fn) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int bytes;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = limit.find({fn, dev});
+        if (it != limit.end()) {
+            bytes = it->second;
+        } else {
+            cudaFuncAttributes fa;
+            int optin = 0;
+            if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+                cudaSuccess)
+                return e;
+            bytes = optin - (int)fa.sharedSizeBytes;
+            limit[{fn, dev}] = bytes;
+        }
+    }
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 namespace {
 
@@ -902,8 +931,7 @@ cudaError_t launch_pivot(int prec, LpDesc *d_desc, const PivotShape &sh, long lo
                              : (const void *)pivot_kernel<float, false, false>;
     }
     if (sh.smem_bytes > 0) {  // static shared memory counts against the 48 KB default too
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sh.smem_bytes);
+        cudaError_t e = allow_dyn_smem(fn);
         if (e != cudaSuccess) return e;
     }
     // A cooperative launch fails instead of running when the grid cannot be
@@ -917,8 +945,7 @@ cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing
     void *args[] = {&slots, &nslots, &ctl, &ring_dev, &spin_limit, &idle_limit};
     const void *fn = (const void *)server_kernel;
     if (smem > 0) {  // static shared memory counts against the 48 KB default too
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = allow_dyn_smem(fn);
         if (e != cudaSuccess) return e;
     }
     return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
@@ -926,7 +953,7 @@ cudaError_t launch_server(ServeSlot *slots, int nslots, ServeCtl *ctl, ServeRing
 
 int max_coresident_server_ctas(int threads, size_t smem, int sms) {
     const void *fn = (const void *)server_kernel;
-    if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 0) allow_dyn_smem(fn);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
         return 0;
@@ -943,8 +970,7 @@ cudaError_t launch_batch(int prec, LpDesc *descs, const int2 *items, int nitems,
     else
         fn = use_smem ? (const void *)batch_kernel<float, true> : (const void *)batch_kernel<float, false>;
     if (smem > 0) {  // static shared memory counts against the 48 KB default too
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = allow_dyn_smem(fn);
         if (e != cudaSuccess) return e;
     }
     return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
@@ -956,7 +982,7 @@ int max_coresident_batch_ctas(int prec, int threads, size_t smem, int use_smem, 
         fn = use_smem ? (const void *)batch_kernel<double, true> : (const void *)batch_kernel<double, false>;
     else
         fn = use_smem ? (const void *)batch_kernel<float, true> : (const void *)batch_kernel<float, false>;
-    if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 0) allow_dyn_smem(fn);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
         return 0;

@@ -480,7 +480,7 @@ cudaError_t launch_reinv_solve(int prec, const double *A, const double *b, const
         const size_t smem = sizeof(double) * ((size_t)ns + strip) + 4 * (((size_t)ns + 31) / 32);
         const void *fn = (const void *)gj_kernel;
         if (smem > 0) {  // static shared memory counts against the 48 KB default too
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = allow_dyn_smem(fn);
             if (e != cudaSuccess) return e;
         }
         e = cudaMemsetAsync(rb.bar, 0, 128 * sizeof(unsigned), s);

@@ -96,12 +96,20 @@ enum TicketState { QUEUED, ADMITTED, DONE };
 
 struct Request {
     int m = 0, n = 0, sense = 0;
-    std::vector<double> in;  // A, b, c packed
+    // A, b, c packed (nin doubles): in a pinned buffer of the server's pool
+    // (class pin_cls) until the admission copy to the device is done, or in
+    // pageable memory when the pool had none to give
+    size_t nin = 0;
+    double *pin = nullptr;
+    int pin_cls = -1;
+    std::vector<double> in;
+    const double *input() const { return pin ? pin : in.data(); }
     TicketState state = QUEUED;
     int slot = -1;
     size_t off = 0, bytes = 0;
     int group = 1, strip = 0;
     bool solo_oom = false;  // too large to run alone in the arena: served by the kernel
+    bool alone = false;     // lanes: too large for a lane's slice of the arena, runs alone
     // results
     std::vector<double> x, y;
     double obj = 0.0;
@@ -178,6 +186,21 @@ struct lp_server {
     // spilling (lp_options.spill_pivots): pinned host buffers not in use, by
     // size, every pinned buffer allocated, and the counts
     long long spill_pivots = 0;
+    // FP64 lanes (lp_options.lanes > 0) instead of the persistent kernel: the
+    // lane threads, their handles' CTA count and arena slice, the lanes that
+    // are solving an LP; alone_wait: an LP that runs alone is at the head of
+    // the queue (lanes start no new LP), alone_busy: it is running
+    int lanes = 0, lane_ctas = 0;
+    size_t lane_bytes = 0;
+    std::vector<std::thread> lane_threads;
+    int busy_lanes = 0;
+    bool alone_wait = false, alone_busy = false;
+    // pinned buffers for request inputs, by size class (2^k bytes), and
+    // every one allocated (pin_mu: submit runs on the callers' threads)
+    std::mutex pin_mu;
+    std::vector<std::vector<double *>> pin_free;
+    std::vector<void *> pin_all;
+    size_t pin_total = 0;
     std::multimap<size_t, unsigned char *> host_free;
     std::vector<std::pair<unsigned char *, size_t>> host_all;
     size_t host_total = 0;
@@ -244,8 +267,22 @@ void group_shape32(const lp_server *sv, int m, int n, int *G, int *W) {
 }
 
 bool is_solo(const lp_server *sv, const Request &r) {
-    return sv->solo_elems >= 0 && !r.solo_oom &&
-           (long long)(r.m + 1) * pitch_for(r.n + r.m + 1) >= sv->solo_elems;
+    return r.alone || (sv->solo_elems >= 0 && !r.solo_oom &&
+                       (long long)(r.m + 1) * pitch_for(r.n + r.m + 1) >= sv->solo_elems);
+}
+
+// A max-form request with some b_i < 0 (and every input finite; lp_load
+// reports a non-finite one): the server has no Phase I, so it is rejected
+// with LP_ERR_INFEASIBLE_START, as the server kernel rejects it.
+bool needs_phase1(const Request &r) {
+    if (r.sense != LP_MAX_LE) return false;
+    const double *A = r.input(), *b = A + (size_t)r.m * r.n;
+    bool neg = false;
+    for (int i = 0; i < r.m; ++i) neg |= b[i] < 0.0;
+    if (!neg) return false;
+    for (size_t k = 0; k < r.nin; ++k)
+        if (!isfinite(A[k])) return false;
+    return true;
 }
 
 // A server-wide failure: every waiting call returns `code` from now on.
@@ -280,6 +317,49 @@ unsigned char *host_take(lp_server *sv, size_t bytes, size_t *cap) {
 }
 
 void host_give(lp_server *sv, unsigned char *p, size_t cap) { sv->host_free.emplace(cap, p); }
+
+// Pinned host memory for a request's inputs, so that admission copies them to
+// the device by DMA at the link's rate instead of through the driver's
+// staging of pageable memory (measured: 0.68 ms of each lp_load's 1.4 ms on
+// the serving stream's LPs, 7.5 MB of inputs on average).  Buffers of 2^k
+// bytes, reused; at most kPinInputCap bytes in all, beyond which requests
+// keep their inputs in pageable memory.
+constexpr size_t kPinInputCap = 8ull << 30;
+
+double *pin_take(lp_server *sv, size_t bytes, int *cls) {
+    int k = 12;
+    while (((size_t)1 << k) < bytes) ++k;
+    std::lock_guard<std::mutex> lk(sv->pin_mu);
+    if ((int)sv->pin_free.size() <= k) sv->pin_free.resize(k + 1);
+    if (!sv->pin_free[k].empty()) {
+        double *p = sv->pin_free[k].back();
+        sv->pin_free[k].pop_back();
+        *cls = k;
+        return p;
+    }
+    if (sv->pin_total + ((size_t)1 << k) > kPinInputCap) return nullptr;
+    DeviceRestore restore_;
+    void *p = nullptr;
+    if (cudaSetDevice(sv->device) != cudaSuccess ||
+        cudaHostAlloc(&p, (size_t)1 << k, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    sv->pin_all.push_back(p);
+    sv->pin_total += (size_t)1 << k;
+    *cls = k;
+    return static_cast<double *>(p);
+}
+
+// The request's pinned inputs back to the pool (their copy to the device is
+// complete, or they are not needed any more).
+void pin_give(lp_server *sv, Request &r) {
+    if (!r.pin) return;
+    std::lock_guard<std::mutex> lk(sv->pin_mu);
+    sv->pin_free[r.pin_cls].push_back(r.pin);
+    r.pin = nullptr;
+    r.pin_cls = -1;
+}
 
 // Copy results of finished slots back and release their resources.
 bool engine_complete(lp_server *sv) {
@@ -360,8 +440,8 @@ bool engine_admit(lp_server *sv) {
         const long long P = pitch_for(n + m + 1);
         const SlotLayout L = slot_layout(m, n, P, r.group);
         unsigned char *base = sv->arena_dev + r.off;
-        cudaMemcpyAsync(base + L.in, r.in.data(), r.in.size() * sizeof(double),
-                        cudaMemcpyHostToDevice, sv->cstream);
+        cudaMemcpyAsync(base + L.in, r.input(), r.nin * sizeof(double), cudaMemcpyHostToDevice,
+                        sv->cstream);
         cudaMemsetAsync(base + L.bar, 0, 512, sv->cstream);
         cudaMemsetAsync(base + L.stats, 0, sizeof(InputStats), sv->cstream);
         ServeSlot &S = hs[k];
@@ -399,6 +479,7 @@ bool engine_admit(lp_server *sv) {
         cudaMemcpyAsync(&sv->d_slots[adm[k].s], &S, sizeof S, cudaMemcpyHostToDevice, sv->cstream);
     }
     cudaStreamSynchronize(sv->cstream);
+    for (const Adm &a : adm) pin_give(sv, *a.r);
     int tail = *(volatile int *)&sv->h_ring->rq_tail;
     for (const Adm &a : adm) sv->h_ring->rq[tail++ % kServeMaxSlots] = a.s;
     std::atomic_thread_fence(std::memory_order_release);
@@ -526,8 +607,7 @@ bool admit32(lp_server *sv) {
             continue;
         }
         const double *A = reinterpret_cast<const double *>(base + L.in);
-        cudaMemcpyAsync(base + L.in, r.in.data(), r.in.size() * sizeof(double),
-                        cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(base + L.in, r.input(), r.nin * sizeof(double), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(base + L.bar, 0, 512, s);
         launch_inspect(A, A + (size_t)r.m * r.n, A + (size_t)r.m * r.n + r.m, r.m, r.n,
                        reinterpret_cast<InputStats *>(base + L.stats), s);
@@ -538,6 +618,7 @@ bool admit32(lp_server *sv) {
         set_fatal(sv, LP_ERR_CUDA, "FP32 admission", ce);
         return true;
     }
+    for (auto &a : adm) pin_give(sv, *a.second);
     for (size_t k = 0; k < adm.size(); ++k) {
         const int slot = adm[k].first;
         Request &r = *adm[k].second;
@@ -872,10 +953,10 @@ bool engine_solo(lp_server *sv) {
         if (sv->fatal != LP_OK || sv->queue.empty()) return false;
         r = &sv->reqs[sv->queue.front()];
         if (!is_solo(sv, *r)) return false;
-        bool busy = sv->kernel_running || !sv->active.empty();
+        bool busy = sv->kernel_running || !sv->active.empty() || sv->busy_lanes > 0;
         for (int s = 0; !busy && s < sv->max_slots; ++s) busy = sv->slot_ticket[s] != 0;
         if (busy) {
-            *(volatile int *)&sv->h_ring->shutdown = 1;
+            if (!sv->lanes) *(volatile int *)&sv->h_ring->shutdown = 1;
             return false;
         }
         bytes = sv->arena.size();
@@ -887,13 +968,9 @@ bool engine_solo(lp_server *sv) {
         r->bytes = bytes;
     }
     const int m = r->m, n = r->n;
-    const double *A = r->in.data(), *b = A + (size_t)m * n, *c = b + m;
+    const double *A = r->input(), *b = A + (size_t)m * n, *c = b + m;
     const bool resume = r->spilled;
-    bool bneg = false;
-    for (int i = 0; !resume && i < m; ++i) bneg |= b[i] < 0.0;
-    if (bneg && r->sense == LP_MAX_LE)
-        for (double v : r->in)
-            if (!isfinite(v)) { bneg = false; break; }  // lp_load reports the non-finite input
+    const bool bneg = !resume && needs_phase1(*r);
     r->x.assign(n, 0.0);
     r->y.assign(m, 0.0);
     double obj = 0.0;
@@ -903,7 +980,7 @@ bool engine_solo(lp_server *sv) {
     lp_handle *h = nullptr;
     bool spilled = false;
     char why[160] = {0};
-    if (bneg && r->sense == LP_MAX_LE) {
+    if (bneg) {
         verdict = LP_ERR_INFEASIBLE_START;
     } else if (resume) {
         // A spilled LP: its handle's range of the arena back in place (the
@@ -929,6 +1006,7 @@ bool engine_solo(lp_server *sv) {
             lp_options o = sv->opt;
             o.trace_cap = 0;
             o.cuda_stream = nullptr;
+            o.time_limit_s = 0.0;
             e = lp_create(&sv->solo, &o);
         }
         h = sv->solo;
@@ -993,10 +1071,16 @@ bool engine_solo(lp_server *sv) {
     if (spilled) {
         r->state = QUEUED;
         sv->queue.push_back(tk);
-    } else if (e == LP_ERR_OOM) {
-        r->solo_oom = true;
+    } else if (e == LP_ERR_OOM && !sv->lanes) {
+        r->solo_oom = true;  // the server kernel's slot layout may still hold it
         r->state = QUEUED;
         sv->queue.push_front(tk);
+    } else if (e == LP_ERR_OOM) {  // lanes: nothing holds more than the whole arena
+        r->err = LP_ERR_OOM;
+        r->status = LP_NOT_SOLVED;
+        r->state = DONE;
+        r->t_done = now_ms();
+        ++sv->completed;
     } else if (e != LP_OK) {
         sv->fatal = e;
         snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "server solve of a large LP: %s",
@@ -1010,6 +1094,9 @@ bool engine_solo(lp_server *sv) {
         r->t_done = now_ms();
         ++sv->completed;
     }
+    // inputs loaded (every lp_solve and lp_result waits for the handle's
+    // stream) or not needed any more
+    if (spilled || r->state == DONE) pin_give(sv, *r);
     // a handle that carried a spilled LP to its end serves the next LP that
     // runs alone, or goes
     if (!spilled && h && h != sv->solo) {
@@ -1019,6 +1106,123 @@ bool engine_solo(lp_server *sv) {
     *(volatile int *)&sv->h_ring->shutdown = 0;
     sv->cv.notify_all();
     return true;
+}
+
+// FP64 lanes (lp_options.lanes > 0): lane k solves one LP at a time, as
+// lp_load + lp_solve + lp_result solve it, on its own handle (its own stream,
+// SMs / lanes CTAs, its buffers carved from a slice of budget / lanes bytes of
+// the arena taken for the LP); the lanes' kernels share the GPU, so the
+// chain-bound selection of one LP overlaps the others' updates.  An LP that
+// runs alone (solo_elems, or one a slice cannot hold) waits at the head of
+// the queue until every lane is idle, the lanes taking no new LP meanwhile,
+// then runs on the whole arena and every SM (engine_solo, with its slices and
+// spills under spill_pivots).
+void lane_main(lp_server *sv, int k) {
+    (void)k;
+    cudaSetDevice(sv->device);
+    lp_handle *h = nullptr;
+    {
+        lp_options o = sv->opt;
+        o.trace_cap = 0;
+        o.cuda_stream = nullptr;
+        o.ctas = sv->lane_ctas;
+        o.time_limit_s = 0.0;
+        if (lp_create(&h, &o) != LP_OK) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->fatal = LP_ERR_CUDA;
+            snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "lane handle: %s", lp_last_error(nullptr));
+            sv->cv.notify_all();
+            return;
+        }
+    }
+    while (!sv->stop.load()) {
+        Request *r = nullptr;
+        unsigned long long tk = 0;
+        size_t off = 0;
+        bool alone = false;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            if (sv->fatal != LP_OK || sv->queue.empty() || sv->alone_busy) {
+                sv->cv.wait_for(lk, std::chrono::microseconds(200));
+                continue;
+            }
+            tk = sv->queue.front();
+            Request &q = sv->reqs[tk];
+            if (is_solo(sv, q)) {
+                if (sv->busy_lanes > 0) {
+                    sv->alone_wait = true;
+                    sv->cv.wait_for(lk, std::chrono::microseconds(20));
+                    continue;
+                }
+                sv->alone_wait = false;
+                sv->alone_busy = true;
+                alone = true;
+            } else if (sv->alone_wait || !sv->arena.alloc(sv->lane_bytes, &off)) {
+                sv->cv.wait_for(lk, std::chrono::microseconds(20));
+                continue;
+            } else {
+                sv->queue.pop_front();
+                r = &q;
+                r->state = ADMITTED;
+                r->t_admit = now_ms();
+                ++sv->busy_lanes;
+            }
+        }
+        if (alone) {
+            engine_solo(sv);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->alone_busy = false;
+            sv->cv.notify_all();
+            continue;
+        }
+        const int m = r->m, n = r->n;
+        const double *A = r->input(), *b = A + (size_t)m * n, *c = b + m;
+        r->x.assign(n, 0.0);
+        r->y.assign(m, 0.0);
+        double obj = 0.0;
+        lp_status st = LP_NOT_SOLVED;
+        long long iters = 0;
+        lp_err e = LP_OK, verdict = LP_OK;
+        bool solved = false;
+        if (needs_phase1(*r)) {
+            verdict = LP_ERR_INFEASIBLE_START;
+        } else {
+            e = handle_bind_region(h, sv->arena_dev + off, sv->lane_bytes);
+            if (e == LP_OK) e = lp_load(h, m, n, A, b, c, (lp_sense)r->sense);
+            if (e == LP_OK) {
+                e = lp_solve(h);
+                solved = true;
+            }
+            if (e == LP_OK) e = lp_result(h, r->x.data(), r->y.data(), &obj, &st, &iters);
+            if (e == LP_ERR_INVALID_ARG || e == LP_ERR_INFEASIBLE_START) {
+                verdict = e;
+                e = LP_OK;
+            }
+        }
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->arena.release(off, sv->lane_bytes);
+        --sv->busy_lanes;
+        if (solved) ++sv->launches;
+        if (e == LP_ERR_OOM) {
+            r->alone = true;  // a slice cannot hold it: it runs alone
+            r->state = QUEUED;
+            sv->queue.push_front(tk);
+        } else if (e != LP_OK) {
+            sv->fatal = e;
+            snprintf(sv->fatal_msg, sizeof sv->fatal_msg, "lane solve: %s", lp_last_error(h));
+        } else {
+            pin_give(sv, *r);
+            r->err = verdict;
+            r->status = verdict == LP_OK ? (int)st : LP_NOT_SOLVED;
+            r->obj = obj;
+            r->iters = iters;
+            r->state = DONE;
+            r->t_done = now_ms();
+            ++sv->completed;
+        }
+        sv->cv.notify_all();
+    }
+    lp_destroy(h);  // its buffers are the arena's
 }
 
 void engine_main(lp_server *sv) {
@@ -1053,7 +1257,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
         return sfail(LP_ERR_INVALID_ARG, "lp_server_create: need 1 <= max_slots <= %d and a "
                      "budget of at least 1 MiB", kServeMaxSlots);
     if (o.max_iters < 0 || o.bland_after < 0 || o.spin_timeout_cycles <= 0 || o.device < 0 ||
-        o.spill_pivots < 0)
+        o.spill_pivots < 0 || o.lanes < 0 || o.lanes > 16)
         return sfail(LP_ERR_INVALID_ARG, "lp_server_create: option out of range");
     lp_server *sv = new (std::nothrow) lp_server();
     if (!sv) return sfail(LP_ERR_OOM, "lp_server_create: host allocation failed");
@@ -1063,6 +1267,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->fp32 = o.precision == LP_FP32_REINV;
     sv->solo_elems = o.solo_elems < 0 ? -1 : o.solo_elems > 0 ? o.solo_elems : 1ll << 24;
     sv->spill_pivots = o.spill_pivots;
+    sv->lanes = sv->fp32 ? 0 : o.lanes;
     DeviceRestore restore_;
     cudaError_t e = cudaSetDevice(o.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv->sms, cudaDevAttrMultiProcessorCount, o.device);
@@ -1117,7 +1322,13 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     sv->arena.reset(hbm_budget_bytes);
     sv->slot_ticket.assign(max_slots, 0);
     for (int s = max_slots - 1; s >= 0; --s) sv->free_slots.push_back(s);
-    sv->engine = std::thread(sv->fp32 ? engine32_main : engine_main, sv);
+    if (sv->lanes > 0) {
+        sv->lane_ctas = std::max(1, sv->sms / sv->lanes);
+        sv->lane_bytes = hbm_budget_bytes / sv->lanes / 256 * 256;
+        for (int k = 0; k < sv->lanes; ++k) sv->lane_threads.emplace_back(lane_main, sv, k);
+    } else {
+        sv->engine = std::thread(sv->fp32 ? engine32_main : engine_main, sv);
+    }
     *out = sv;
     return LP_OK;
 }
@@ -1135,19 +1346,28 @@ lp_err lp_server_submit(lp_server *sv, int m, int n, const double *A, const doub
     r.m = m;
     r.n = n;
     r.sense = (int)sense;
-    r.in.resize((size_t)m * n + m + n);
-    memcpy(r.in.data(), A, sizeof(double) * (size_t)m * n);
-    memcpy(r.in.data() + (size_t)m * n, b, sizeof(double) * m);
-    memcpy(r.in.data() + (size_t)m * n + m, c, sizeof(double) * n);
     int G, W;
     if (sv->fp32) group_shape32(sv, m, n, &G, &W);
     else group_shape(sv, m, n, &G, &W);
     if (slot_layout(m, n, pitch_for(n + m + 1), G, sv->fp32 ? sizeof(float) : sizeof(double)).total >
         sv->arena.size())
         return sfail(LP_ERR_OOM, "lp_server_submit: an LP of %d x %d exceeds the HBM budget", m, n);
+    r.nin = (size_t)m * n + m + n;
+    double *dst = pin_take(sv, r.nin * sizeof(double), &r.pin_cls);
+    r.pin = dst;
+    if (!dst) {
+        r.in.resize(r.nin);
+        dst = r.in.data();
+    }
+    memcpy(dst, A, sizeof(double) * (size_t)m * n);
+    memcpy(dst + (size_t)m * n, b, sizeof(double) * m);
+    memcpy(dst + (size_t)m * n + m, c, sizeof(double) * n);
     r.t_submit = now_ms();
     std::lock_guard<std::mutex> lk(sv->mu);
-    if (sv->fatal != LP_OK) return sfail(sv->fatal, "lp_server_submit: %s", sv->fatal_msg);
+    if (sv->fatal != LP_OK) {
+        pin_give(sv, r);
+        return sfail(sv->fatal, "lp_server_submit: %s", sv->fatal_msg);
+    }
     const unsigned long long t = sv->next_ticket++;
     sv->reqs.emplace(t, std::move(r));
     sv->queue.push_back(t);
@@ -1229,11 +1449,11 @@ lp_err lp_server_spill_stats(lp_server *sv, long long *spills, long long *restor
 
 void lp_server_destroy(lp_server *sv) {
     if (!sv) return;
-    if (sv->engine.joinable()) {
-        sv->stop.store(true);
-        sv->cv.notify_all();
-        sv->engine.join();
-    }
+    sv->stop.store(true);
+    sv->cv.notify_all();
+    if (sv->engine.joinable()) sv->engine.join();
+    for (auto &t : sv->lane_threads)
+        if (t.joinable()) t.join();
     DeviceRestore restore_;
     cudaSetDevice(sv->device);
     if (sv->h_ring) *(volatile int *)&sv->h_ring->shutdown = 1;
@@ -1254,6 +1474,7 @@ void lp_server_destroy(lp_server *sv) {
     lp_destroy(sv->solo);  // its buffers are the arena's: nothing of it to free
     for (auto &t : sv->reqs) lp_destroy(t.second.solo_h);  // LPs still spilled
     for (auto &p : sv->host_all) cudaFreeHost(p.first);
+    for (void *p : sv->pin_all) cudaFreeHost(p);
     delete sv->rp;
     delete sv;
 }

@@ -51,9 +51,14 @@ def _check(lp, res):
     assert lat > 0.0
 
 
-def test_serve_stream_matches_oracle():
+LANES = pytest.mark.parametrize("lanes", [0, 3])  # the server kernel, or three lanes
+
+
+@LANES
+def test_serve_stream_matches_oracle(lanes):
     lps = _mix(60, 8, 600, seed=1)
-    srv = capi.lp_server_create(hbm_budget_bytes=2 << 30, max_slots=64)
+    srv = capi.lp_server_create(capi.lp_options_default(lanes=lanes), hbm_budget_bytes=2 << 30,
+                                max_slots=64)
     try:
         tickets = []
         for k, lp in enumerate(lps):  # staggered arrivals: new requests join running ones
@@ -67,10 +72,13 @@ def test_serve_stream_matches_oracle():
         capi.lp_server_destroy(srv)
 
 
-def test_serve_small_budget_admission_and_threads():
-    """A budget that holds only a few tableaus: requests wait for memory."""
+@LANES
+def test_serve_small_budget_admission_and_threads(lanes):
+    """A budget that holds only a few tableaus: requests wait for memory (with
+    lanes, LPs a 4 MB slice cannot hold run alone on the whole 12 MB)."""
     lps = _mix(24, 100, 400, seed=2)
-    srv = capi.lp_server_create(hbm_budget_bytes=12 << 20, max_slots=8)
+    srv = capi.lp_server_create(capi.lp_options_default(lanes=lanes), hbm_budget_bytes=12 << 20,
+                                max_slots=8)
     results = {}
     try:
         def client(idx):
@@ -90,8 +98,10 @@ def test_serve_small_budget_admission_and_threads():
         capi.lp_server_destroy(srv)
 
 
-def test_serve_idle_relaunch_and_rejected_request():
-    srv = capi.lp_server_create(hbm_budget_bytes=1 << 30, max_slots=16)
+@LANES
+def test_serve_idle_relaunch_and_rejected_request(lanes):
+    srv = capi.lp_server_create(capi.lp_options_default(lanes=lanes), hbm_budget_bytes=1 << 30,
+                                max_slots=16)
     try:
         lp = _mix(1, 50, 60, seed=3)[0]
         _check(lp, capi.lp_server_wait(srv, capi.lp_server_submit(srv, *lp), lp[0].shape[0], lp[0].shape[1]))
@@ -111,14 +121,15 @@ def test_serve_idle_relaunch_and_rejected_request():
         capi.lp_server_destroy(srv)
 
 
-def test_serve_large_lps_alone_in_the_mix():
+@LANES
+def test_serve_large_lps_alone_in_the_mix(lanes):
     """LPs of at least solo_elems tableau elements run alone on the single-LP
     kernels, between busy periods of the persistent kernel; with a low
     threshold about half of a mixed stream does.  Every result is still the
     oracle's, bit for bit, and rejected large requests get the kernel's
     verdicts."""
     lps = _mix(40, 8, 300, seed=6)
-    opt = capi.lp_options_default(solo_elems=20000)
+    opt = capi.lp_options_default(solo_elems=20000, lanes=lanes)
     solo = sum((lp[0].shape[0] + 1) * (-(-(sum(lp[0].shape) + 1) // 32) * 32) >= 20000
                for lp in lps)
     assert 5 <= solo <= 35

@@ -69,13 +69,15 @@ def _run(srv, lps):
     return res, done
 
 
-def test_fp64_large_lp_sliced_and_spilled():
+@pytest.mark.parametrize("lanes", [0, 3])
+def test_fp64_large_lp_sliced_and_spilled(lanes):
     """A large LP (alone, in slices of 40 pivots) submitted just before 24
     small ones: it is spilled while they wait, they finish before it, and
-    every result is the oracle's, bit for bit."""
+    every result is the oracle's, bit for bit; with the server kernel or
+    with three lanes serving the small ones."""
     big = (*lpgen.paper_lp(600, 800, seed=1), capi.LP_MAX_LE)  # 657 pivots
     lps = [big] + _small(24, seed=2)
-    opt = capi.lp_options_default(solo_elems=200000, spill_pivots=40)
+    opt = capi.lp_options_default(solo_elems=200000, spill_pivots=40, lanes=lanes)
     srv = capi.lp_server_create(opt, hbm_budget_bytes=256 << 20, max_slots=32)
     try:
         res, done = _run(srv, lps)
