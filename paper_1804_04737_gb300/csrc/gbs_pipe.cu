@@ -959,7 +959,6 @@ constexpr int kMaxRecs = 256; // CTAs of a two-pivot launch (records copied to s
 struct Strip {
     int a0, wa, b0, wb;
     __host__ __device__ int w() const { return wa + wb; }
-    __host__ __device__ int gcol(int l) const { return l < wa ? a0 + l : b0 + (l - wa); }
     __host__ __device__ int lcol(int j) const {
         if ((unsigned)(j - a0) < (unsigned)wa) return j - a0;
         if ((unsigned)(j - b0) < (unsigned)wb) return wa + (j - b0);
@@ -1245,6 +1244,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     __shared__ unsigned char s_res[2][kMaxThreads];  // buffer holding each vector's rows, by pass parity
     __shared__ unsigned char s_nz[kMaxThreads];      // the vector's rows may hold a -0
     __shared__ int s_cf[32], s_rowner;
+    // balanced ownership (below): the slack vectors no CTA owns yet (a bit
+    // each), every CTA's vector count, this CTA's slack-run vectors (global
+    // vector indices) in the order it took them, and the leaving variables of
+    // the next pass's pivots
+    constexpr int kDynWords = SKIP ? 512 : 1, kDynG = SKIP ? 256 : 1;
+    __shared__ unsigned s_unown[kDynWords];
+    __shared__ unsigned short s_load[kDynG];
+    __shared__ unsigned short s_ov[SKIP ? kMaxThreads : 1];
+    __shared__ int s_nown, s_unc, s_lv[kBlk];
 
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, B = blockDim.x;
     const int NU = B - kSelThreads;
@@ -1287,19 +1295,105 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     // pivot columns are finite.  Readers of a column take its buffer from s_res
     // (this CTA's columns) or from the record that named the column.  The
     // objective row follows the pass parity.
+    //
+    // Balanced ownership (SKIP, on a launch from the slack basis with no -0
+    // anywhere: d->iters == 0 and !d->negz).  A slack column whose variable
+    // is basic is an exact unit vector e_r with a zero objective entry, and a
+    // pivot leaves it as it is unless its row r is the pivot row, that is
+    // unless its variable leaves; so a vector of VW slack columns that are all
+    // basic is left in place until one of them leaves.  Those vectors belong
+    // to no CTA at first; when one of its variables leaves (every CTA knows
+    // the leaving variables, from the selection), the vector goes to the CTA
+    // with the fewest vectors (ties: the lowest index) for the rest of the
+    // launch, so no vector changes hands and the CTAs' update work stays
+    // within a vector of each other, where fixed runs give each CTA the
+    // leaving slacks that happen to fall in its run.  Each CTA keeps its run
+    // of structural columns; the other vectors of the slack run (structural,
+    // rhs and padding columns) are dealt out the same way at the start.  All
+    // CTAs make the same choices from the same data.  A pass with a
+    // non-finite pivot-column entry gives out every vector left.
     constexpr int kSector = 32 / (int)sizeof(T);
     const Strip S = make_strip(g, G, W, split, P, kSector);
-    const int ws = S.w();
-    const int vpr = ws / VW;
-    const int rl = S.lcol(N - 1);
+    const int vpa = S.wa / VW;  // the CTA's structural vectors
+    // the slack vectors that may start unowned: [dv0, dv1)
+    const int nst = N - 1 - m;  // structural columns
+    const int dv0 = (nst + VW - 1) / VW, dv1 = (nst + m) / VW, vtot = (int)(P / VW);
+    const int capv = W / VW;  // most vectors a CTA may own (its shared memory holds W columns)
+    const bool dyn = SKIP && split > 0 && d->iters == 0 && !d->negz && G <= kDynG &&
+                     dv1 - dv0 <= 32 * kDynWords && vtot < 65536 && capv <= kMaxThreads;
+    int ws = S.w();
+    int vpr = ws / VW;
+    int rl = S.lcol(N - 1);
     // without SKIP the strip is the contiguous one: the mappings simplify
-    auto gcol = [&](int l) { return SKIP ? S.gcol(l) : S.a0 + l; };
-    auto lcol = [&](int j) { return SKIP ? S.lcol(j) : j - S.a0; };
+    auto gcol = [&](int l) -> int {
+        if (!SKIP || l < S.wa) return S.a0 + l;
+        if (!dyn) return S.b0 + (l - S.wa);
+        const int k = l - S.wa;
+        return (int)s_ov[k / VW] * VW + k % VW;
+    };
+    // (this CTA's columns only; -1 elsewhere)
+    auto lcol = [&](int j) -> int {
+        if (!SKIP) return j - S.a0;
+        if (!dyn) return S.lcol(j);
+        if ((unsigned)(j - S.a0) < (unsigned)S.wa) return j - S.a0;
+        for (int k = 0; k < vpr - vpa; ++k)
+            if ((int)s_ov[k] == j / VW) return S.wa + k * VW + j % VW;
+        return -1;
+    };
+    // warp 0: vector v to the CTA with the fewest vectors below capv
+    auto assign = [&](int v) {
+        unsigned best = 0xffffffffu;
+        for (int c = lane; c < G; c += 32) {
+            const unsigned l = s_load[c];
+            if (l < (unsigned)capv) best = min(best, (l << 16) | (unsigned)c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) {
+            if (best == 0xffffffffu) {  // never: the host leaves every CTA room
+                atomicExch(d->err, 1);
+            } else {
+                const int c = (int)(best & 0xffffu);
+                s_load[c] = (unsigned short)(s_load[c] + 1);
+                if (c == g) {
+                    s_ov[s_nown++] = (unsigned short)v;
+                    // the objective row follows the pass parity for the CTA's
+                    // vectors; this one's entries are still in the first buffer
+                    if (cur != 0)
+                        for (int k = 0; k < VW; ++k)
+                            bufs[cur][(long long)m * P + (long long)v * VW + k] =
+                                bufs[0][(long long)m * P + (long long)v * VW + k];
+                }
+                if (v == (N - 1) / VW) s_rowner = c;
+            }
+        }
+        __syncwarp();
+    };
     if constexpr (SKIP) {
-        for (int v = tid; v < vpr; v += B) {
+        for (int v = tid; v < (dyn ? capv : vpr); v += B) {
             s_res[0][v] = 0;
             s_res[1][v] = 0;
             s_nz[v] = 0;
+        }
+        if (dyn) {
+            for (int c = tid; c < G; c += B) s_load[c] = (unsigned short)(make_strip(c, G, W, split, P, kSector).wa / VW);
+            for (int w = tid; w < kDynWords; w += B) {
+                const int b0 = 32 * w, nb = dv1 - dv0 - b0;
+                s_unown[w] = nb >= 32 ? 0xffffffffu : nb > 0 ? (1u << nb) - 1u : 0u;
+            }
+            if (tid == 0) {
+                s_nown = 0;
+                s_unc = dv1 - dv0;
+                s_lv[0] = s_lv[1] = -1;
+            }
+            __syncthreads();
+            if (tid < 32)  // the slack run's vectors that are not all slack columns
+                for (int v = split / VW; v < vtot; ++v)
+                    if (v < dv0 || v >= dv1) assign(v);
+            __syncthreads();
+            vpr = vpa + s_nown;
+            ws = vpr * VW;
+            rl = lcol(N - 1);
         }
         if (d->negz) {
             // a constraint row may hold a -0 (from the data, Phase I, an FP32
@@ -1315,7 +1409,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
         }
     }
-    if (tid == 0) {
+    if (tid == 0 && !dyn) {
         int o = 0;
         for (int k = 0; k < G; ++k)
             if (make_strip(k, G, W, split, P, kSector).lcol(N - 1) >= 0) {
@@ -1424,9 +1518,57 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     int cb = 0;          // the pass's pivot columns are scol[cb], scol[cb + 1] (mod 4)
     unsigned lk = 0;     // passes made in this launch
     if (tid == 0) s_zready = 0;
+    if (tid == 0 && dyn && p >= 0) s_lv[0] = __ldcg(basis + p);  // the first pivot's leaving variable
     __syncthreads();
     if (tid == 0 && status != ST_TIMEOUT) red_add_release(scnt, 1u);  // the first selection
     while (status == ST_RUNNING) {
+        if constexpr (SKIP) {
+            if (dyn) {
+                // the pass's leaving slack vectors go to their owners (with a
+                // non-finite pivot-column entry, every vector still unowned:
+                // the pass updates them all)
+                const T *c0 = scol[cb], *c1 = scol[(cb + 1) & 3];
+                int nf = 0;
+                for (int i = tid; i < m; i += B)
+                    nf |= (int)not_finite(c0[i]) | (int)(np > 1 && not_finite(c1[i]));
+                nf = __syncthreads_or(nf);
+                if (tid < 32) {
+                    if (nf) {
+                        for (int w = 0; w < kDynWords; ++w) {
+                            unsigned bits = s_unown[w];
+                            while (bits) {
+                                const int b = __ffs(bits) - 1;
+                                bits &= bits - 1u;
+                                assign(dv0 + 32 * w + b);
+                            }
+                            __syncwarp();
+                            if (lane == 0) s_unown[w] = 0u;
+                        }
+                        if (lane == 0) s_unc = 0;
+                    } else {
+                        for (int k = 0; k < np; ++k) {
+                            const int lv = s_lv[k];
+                            const int v = lv >= nst && lv < nst + m ? lv / VW : -1;
+                            if (v >= dv0 && v < dv1) {
+                                const int b = v - dv0;
+                                if ((s_unown[b >> 5] >> (b & 31)) & 1u) {
+                                    __syncwarp();
+                                    if (lane == 0) {
+                                        s_unown[b >> 5] &= ~(1u << (b & 31));
+                                        --s_unc;
+                                    }
+                                    __syncwarp();
+                                    assign(v);
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                vpr = vpa + s_nown;
+                ws = vpr * VW;
+            }
+        }
         const int ab = tid == 0 ? abort_peek(d->abort) : 0;  // used at the pass's end
         const T *A = bufs[cur];
         T *Bn = bufs[cur ^ 1];
@@ -1508,7 +1650,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                             v[k] = r.idx >= 0 ? tbits(sprow[k][lcol(r.idx)]) : 0ull;
                             v[4 + k] = rl >= 0 ? tbits(sprow[k][rl]) : 0ull;
                         }
-                        if constexpr (SKIP) v[3] = r.idx >= 0 ? s_res[par][S.lcol(r.idx) / VW] : 0ull;
+                        if constexpr (SKIP) v[3] = r.idx >= 0 ? s_res[par][lcol(r.idx) / VW] : 0ull;
                         red_add_release(pcnt, 1u);
                     }
                     __threadfence_block();
@@ -1555,7 +1697,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
             if (s_uok && tid == 0 && d->work) {  // vectors x pivots updated and left in place
                 atomicAdd(d->work, (unsigned long long)(nF * np));
-                atomicAdd(d->work + 1, (unsigned long long)((vpr - nF) * np));
+                atomicAdd(d->work + 1, (unsigned long long)((vpr - nF + (dyn && g == 0 ? s_unc : 0)) * np));
             }
             // Step 5 for the pass's pivots on the constraint rows of the
             // updated vectors, every update thread on one of them
@@ -1818,7 +1960,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                                 v[k] = e.idx >= 0 ? tbits(row[lcol(e.idx)]) : 0ull;
                                 v[4 + k] = rl >= 0 ? tbits(row[rl]) : 0ull;
                             }
-                            if constexpr (SKIP) v[3] = e.idx >= 0 ? s_res[par][S.lcol(e.idx) / VW] : 0ull;
+                            if constexpr (SKIP) v[3] = e.idx >= 0 ? s_res[par][lcol(e.idx) / VW] : 0ull;
                             red_add_release(pcnt, 1u);
                         }
                         // ---- pivot b (Step 2): the pricing records ----
@@ -1978,6 +2120,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 s_q[1] = qb;
                 s_rz[0] = rza;
                 s_rz[1] = rzb;
+                if constexpr (SKIP) {  // the leaving variables of the next pass's pivots
+                    s_lv[0] = pa >= 0 ? bkey(pa) : -1;
+                    s_lv[1] = pb >= 0 ? (pb == pa ? qa : bkey(pb)) : -1;
+                }
             }
         }
         // the CTA's pass and its selection of the next pass are done
@@ -2013,10 +2159,27 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const unsigned char *res = s_res[lk & 1];
         for (int v = 0; v < vpr; ++v) {
             if (res[v] == cur) continue;
-            const T *src = bufs[res[v]] + S.gcol(v * VW);
-            T *dst = bufs[cur] + S.gcol(v * VW);
+            const T *src = bufs[res[v]] + gcol(v * VW);
+            T *dst = bufs[cur] + gcol(v * VW);
             for (int i = tid; i < m; i += B)
                 *reinterpret_cast<V *>(dst + (long long)i * P) = ldv(reinterpret_cast<const V *>(src + (long long)i * P));
+        }
+        if (dyn && cur != 0) {
+            // the vectors no CTA took are in the first buffer, objective
+            // entries included: CTA u mod G copies the u-th of them
+            for (int w = 0; w < kDynWords; ++w) {
+                unsigned bits = s_unown[w];
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const int u = 32 * w + b;
+                    if (u % G != g) continue;
+                    const long long col = (long long)(dv0 + u) * VW;
+                    for (int i = tid; i < M; i += B)
+                        *reinterpret_cast<V *>(bufs[1] + (long long)i * P + col) =
+                            ldv(reinterpret_cast<const V *>(bufs[0] + (long long)i * P + col));
+                }
+            }
         }
     }
     if (g == 0 && tid == 0) {
@@ -2678,9 +2841,11 @@ PivotShape choose_pipe_shape(int prec, int M, long long P, int sms, int threads,
             wmax = std::max(wmax, st.w());
         }
         if (fits) {
+            // (two sectors more: the kernel may deal the slack vectors out
+            // by load, one CTA getting up to a few vectors above its run)
             sh.split = split;
-            sh.strip = wmax;
-            w = wmax;
+            sh.strip = std::max(wmax, std::min(wmax + 2 * sector, nu * vw / sector * sector));
+            w = sh.strip;
         }
     }
     // the pivot columns of two pivots and the ratio numerators and screening
