@@ -526,10 +526,11 @@ lp_err lp_load(lp_handle *h, int m, int n, const double *A, const double *b, con
     d.work = reinterpret_cast<unsigned long long *>(h->dbar + kBarWords);
     CUDA_TRY(h, cudaMemsetAsync(d.work, 0, 2 * sizeof(unsigned long long), s));
     // a constraint row may hold a -0: from the data, after Phase 1 (dual
-    // pivots are negative), or in FP32 mode (its refreshes and its dual-rule
-    // recovery rewrite the rows); the two-pivot primal kernel then starts
-    // each launch by finding the vectors that do
-    d.negz = (st.flags & 8) || phase1 || h->prec == PREC_FP32 ? 1 : 0;
+    // pivots are negative), or in FP32 mode once a reinversion has rewritten
+    // the rows (its refreshes and its dual-rule recovery; reinvert marks the
+    // LP); the two-pivot primal kernel then starts each launch by finding the
+    // vectors that do
+    d.negz = (st.flags & 8) || phase1 ? 1 : 0;
     d.bar = h->dbar;
     d.err = (int *)(h->dbar + 96);
     d.trace = h->dtrace;
@@ -652,6 +653,11 @@ lp_err reinvert(lp_handle *h, bool *singular, double *zmin, double *rmin) {
     CUDA_TRY(h, launch_reinv_solve(h->prec, h->dA, h->db, h->dc, h->sense, m, n, h->dbasis, h->rb,
                                    ns, h->dT, h->P, h->dx, h->dy, h->dobj, h->sms,
                                    h->opt.spin_timeout_cycles, s));
+    // the rows are rewritten from here on (rhs, objective row, the body's
+    // refresh, the dual rule's recovery): a -0 may be present
+    const int negz = 1;
+    CUDA_TRY(h, cudaMemcpyAsync((char *)h->ddesc + offsetof(LpDesc, negz), &negz, sizeof negz,
+                                cudaMemcpyHostToDevice, s));
     ReinvCheck chk;
     CUDA_TRY(h, cudaMemcpyAsync(&chk, h->rb.chk, sizeof chk, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaEventRecord(e1, s));
