@@ -1219,8 +1219,8 @@ __device__ __forceinline__ T blk_apply(T x, int i, int np, const int *pp, const 
     return x;
 }
 
-template <typename T, int SW, bool DIST, bool SKIP>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+template <typename T, int SW, bool DIST, bool SKIP, int MAXT = kMaxThreads>
+__global__ void __launch_bounds__(MAXT, 1)
     pivot_block_kernel(LpDesc *__restrict__ d, int W, int split, long long spin_limit,
                        long long budget) {
     typedef typename Vec<T>::type V;
@@ -2713,6 +2713,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
 }  // namespace
 
+// CTAs of up to this many threads launch the FP64 two-pivot primal kernel
+// compiled for it: up to 80 registers a thread instead of 64, so the
+// selection chain and the update keep their values in registers (the
+// 1024-thread build spills)
+constexpr int kMidThreads = 768;
+
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s) {
     int W = sh.strip;
@@ -2734,8 +2740,11 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                                      : (const void *)pivot_block_kernel<double, 8, false, true>)
                                           : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true, true>
                                                      : (const void *)pivot_block_kernel<double, 4, false, true>))
-                                    : (w8 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false>
-                                                     : (const void *)pivot_block_kernel<double, 8, false, false>)
+                                    : (w8 ? (sh.threads <= kMidThreads
+                                                 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false, kMidThreads>
+                                                            : (const void *)pivot_block_kernel<double, 8, false, false, kMidThreads>)
+                                                 : (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false>
+                                                            : (const void *)pivot_block_kernel<double, 8, false, false>))
                                           : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true, false>
                                                      : (const void *)pivot_block_kernel<double, 4, false, false>)))
                              : (sh.split > 0
