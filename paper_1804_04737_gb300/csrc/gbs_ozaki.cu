@@ -68,9 +68,7 @@ constexpr int kOzBBytes = kOzBN * kOzBK * 2;            // 8 KB: one B digit pla
 constexpr int kOzBStageBytes = kOzS * kOzBBytes;        // 56 KB: all digit planes of a B block
 constexpr int kOzTmemCols = 512;                        // S x 64 = 448 used
 constexpr int kOzThreads = 192;
-constexpr int kOzStg = 33;                              // staging row pitch (doubles)
-constexpr int kOzStgBytes = 4 * 32 * kOzStg * 8;        // 32 rows per epilogue warp, FP64
-constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + kOzStgBytes + 256;
+constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + 256;
 
 static_assert(kOzS * kOzBN <= kOzTmemCols, "accumulators must fit tensor memory");
 static_assert(kOzT * kOzS == 49, "the digit extraction below assumes 49 bits");
@@ -459,8 +457,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t sB = base;                                  // [2][S][64][128 B]
     const uint32_t sA = base + 2 * kOzBStageBytes;             // [4][128][128 B]
-    const uint32_t sStg = sA + kOzAStages * kOzABytes;         // epilogue staging
-    const uint32_t sBar = sStg + kOzStgBytes;                  // barriers, 8 bytes each
+    const uint32_t sBar = sA + kOzAStages * kOzABytes;         // barriers, 8 bytes each
     auto full_a = [&](int s) { return sBar + 8u * s; };
     auto empty_a = [&](int s) { return sBar + 8u * (kOzAStages + s); };
     auto full_b = [&](int s) { return sBar + 8u * (2 * kOzAStages + s); };
@@ -618,7 +615,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     } else {
         // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) .. + 31 ----
         const int lg = warp & 3, et = threadIdx.x - 64;
-        double *stg = reinterpret_cast<double *>(oz_smem + (sStg - raw)) + lg * 32 * kOzStg;
         uint32_t use = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
@@ -675,78 +671,64 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                             }
                         }
                     }
-                    // The products of this thread's row go to the warp's slice
-                    // of the staging buffer (row = lane); the warp then walks its
-                    // 32 rows with lane = column, so that the data it reads (C,
-                    // or the original row of A) and the results it writes are
-                    // whole coalesced row segments.
-                    const int j0 = n0 + h * 32;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int Fc = s_colexp[h * 32 + j];
-                        double v = 0.0;
-                        // scale 2^(Er - 1022 + Fc - 1022 - 14)
-                        if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
-                        stg[lane * kOzStg + j] = v;
+                    if (h == kOzBN / 32 - 1) {
+                        // every accumulator of the tile is in registers: the
+                        // MMAs of the next tile may start while this half's
+                        // results are written
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tmem_empty);
                     }
-                    __syncwarp();
-                    const int col = j0 + lane;
+                    // Each thread writes its own row's 32 results (the row its
+                    // tensor-memory lane holds): one contiguous row segment per
+                    // thread, read (C, or the original row of A) and written with
+                    // independent accesses, no shared-memory transposition.
+                    const int j0 = n0 + h * 32;
                     if (p.mode == 0) {
-                        for (int rr = 0; rr < 32; ++rr) {
-                            const int row = m0 + lg * 32 + rr;
-                            if (row >= p.M) break;
-                            if (col < p.N) {
-                                double *q = p.C + (long long)row * p.ldc + col;
-                                const double v = stg[rr * kOzStg + lane];
-                                *q = c == 0 ? v : *q + v;
+                        if (r < p.M) {
+                            double *crow = p.C + (long long)r * p.ldc + j0;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int Fc = s_colexp[h * 32 + j];
+                                double v = 0.0;
+                                // scale 2^(Er - 1022 + Fc - 1022 - 14)
+                                if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
+                                if (j0 + j < p.N) crow[j] = c == 0 ? v : crow[j] + v;
                             }
                         }
-                    } else {
+                    } else if (r < p.M) {
                         const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
-                        const int br = s_brow[h * 32 + lane];
-                        // the tableau row and the constraint of each of the warp's
-                        // rows, one per lane, passed round by shuffles; the original
-                        // rows of A are read eight rows at a time
-                        const int myrow = m0 + lg * 32 + lane;
-                        const int my_ti = myrow < p.M ? p.rowmap[myrow] : 0;
-                        const int my_k = myrow < p.M ? p.rowk[myrow] : 0;
-                        for (int rr0 = 0; rr0 < 32; rr0 += 8) {
-                            double dv[8];
-                            int tiv[8], kv[8];
+                        // this row's place in the tableau and its constraint
+                        const int ti = p.rowmap[r], kr = p.rowk[r];
+                        const double *arow = p.Aorig + (long long)kr * p.n;
+                        float *trow = p.T32 + (long long)ti * p.P;
+                        double av[32];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                tiv[u] = __shfl_sync(0xffffffffu, my_ti, rr0 + u);
-                                kv[u] = __shfl_sync(0xffffffffu, my_k, rr0 + u);
-                                const int row = m0 + lg * 32 + rr0 + u;
-                                dv[u] = (row < p.M && col < p.n)
-                                            ? __ldg(p.Aorig + (long long)kv[u] * p.n + col)
-                                            : 0.0;
-                            }
+                        for (int j = 0; j < 32; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const int row = m0 + lg * 32 + rr0 + u;
-                                // the rhs column comes from the reinversion
-                                if (row < p.M && col < p.N - 1) {
-                                    float out;
-                                    if (br >= 0) {
-                                        out = br == tiv[u] ? 1.0f : 0.0f;
-                                    } else {
-                                        // sg A_kj by its sign bit (no FP64 multiply)
-                                        const double d =
-                                            col < p.n ? __longlong_as_double(__double_as_longlong(dv[u]) ^ sgbit)
-                                                      : (col - p.n == kv[u] ? 1.0 : 0.0);
-                                        out = __double2float_rn(d - stg[(rr0 + u) * kOzStg + lane]);
-                                    }
-                                    p.T32[(long long)tiv[u] * p.P + col] = out;
+                        for (int j = 0; j < 32; ++j) {
+                            const int col = j0 + j;
+                            // the rhs column comes from the reinversion
+                            if (col < p.N - 1) {
+                                const int br = s_brow[h * 32 + j];
+                                float out;
+                                if (br >= 0) {
+                                    out = br == ti ? 1.0f : 0.0f;
+                                } else {
+                                    const int Fc = s_colexp[h * 32 + j];
+                                    double v = 0.0;
+                                    if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
+                                    // sg A_kj by its sign bit (no FP64 multiply)
+                                    const double d = col < p.n ? __longlong_as_double(__double_as_longlong(av[j]) ^ sgbit)
+                                                               : (col - p.n == kr ? 1.0 : 0.0);
+                                    out = __double2float_rn(d - v);
                                 }
+                                trow[col] = out;
                             }
                         }
                     }
                     __syncwarp();  // the slice is free again
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tmem_empty);
                 ++use;
             }
         }
