@@ -647,6 +647,20 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                 if ((mb >> qb) & 1) gm |= 1u << (pa + qb);
                 }
                 for (int h = 0; h < kOzBN / 32; ++h) {
+                    const int j0 = n0 + h * 32;
+                    // mode 1: this row's place in the tableau, its constraint and
+                    // its original entries at the half's columns, read before the
+                    // accumulators so that their latency overlaps the reads of
+                    // tensor memory
+                    int ti = 0, kr = 0;
+                    double av[32];
+                    if (p.mode == 1 && r < p.M) {
+                        ti = p.rowmap[r];
+                        kr = p.rowk[r];
+                        const double *arow = p.Aorig + (long long)kr * p.n;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
+                    }
                     float hi[32], lo[32];
 #pragma unroll
                     for (int g = 0; g < kOzS; ++g) {
@@ -683,7 +697,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     // tensor-memory lane holds): one contiguous row segment per
                     // thread, read (C, or the original row of A) and written with
                     // independent accesses, no shared-memory transposition.
-                    const int j0 = n0 + h * 32;
                     if (p.mode == 0) {
                         if (r < p.M) {
                             double *crow = p.C + (long long)r * p.ldc + j0;
@@ -698,13 +711,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         }
                     } else if (r < p.M) {
                         const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
-                        // this row's place in the tableau and its constraint
-                        const int ti = p.rowmap[r], kr = p.rowk[r];
-                        const double *arow = p.Aorig + (long long)kr * p.n;
                         float *trow = p.T32 + (long long)ti * p.P;
-                        double av[32];
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
                             const int col = j0 + j;
