@@ -67,7 +67,8 @@ constexpr int kOzABytes = kOzBM * kOzBK * 2;            // 16 KB: one A digit pl
 constexpr int kOzBBytes = kOzBN * kOzBK * 2;            // 8 KB: one B digit plane block
 constexpr int kOzBStageBytes = kOzS * kOzBBytes;        // 56 KB: all digit planes of a B block
 constexpr int kOzTmemCols = 512;                        // S x 64 = 448 used
-constexpr int kOzThreads = 192;
+constexpr int kOzEpiWarps = 8;          // epilogue warps: two per tensor-memory lane quarter
+constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + 256;
 
 static_assert(kOzS * kOzBN <= kOzTmemCols, "accumulators must fit tensor memory");
@@ -146,6 +147,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
           "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() {
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             mbar_init(empty_b(s), 1);
         }
         mbar_init(tmem_full, 1);
-        mbar_init(tmem_empty, 4);
+        mbar_init(tmem_empty, kOzEpiWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -613,18 +623,19 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             }
         }
     } else {
-        // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) .. + 31 ----
-        const int lg = warp & 3, et = threadIdx.x - 64;
+        // ---- epilogue: warps 2..9, TMEM lanes 32 (warp % 4) .. + 31; warps
+        // 2..5 take the tile's first 32 columns, warps 6..9 the last 32 ----
+        const int lg = warp & 3, et = threadIdx.x - 64, hsel = (warp - 2) >> 2;
         uint32_t use = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
             const int m0 = (t % nmb) * kOzBM, n0 = (t / nmb) * kOzBN;
             const int r = m0 + lg * 32 + lane;  // this thread's output row
             for (int c = 0; c < nch && ok; ++c) {
-                // all four epilogue warps leave together or go on together
+                // all the epilogue warps leave together or go on together
                 // (this barrier also follows the previous tile's reads of
                 // the shared column data)
-                ok = named_bar_and(1, 128, mbar_wait(tmem_full, use & 1u, p.err, lim));
+                ok = named_bar_and(1, 32 * kOzEpiWarps, mbar_wait(tmem_full, use & 1u, p.err, lim));
                 if (!ok) break;
                 tc_fence_after();
                 const int Er = r < p.M ? p.rowexp[r] : kNoExp;
@@ -635,7 +646,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     s_colexp[et] = col < p.N ? p.colexp[col] : kNoExp;
                     if (p.mode == 1) s_brow[et] = col < p.N - 1 ? p.basic_row[col] : -1;
                 }
-                named_bar(1, 128);
+                named_bar(1, 32 * kOzEpiWarps);
                 const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
                 // the accumulator groups the MMA issuer wrote for this tile
                 uint32_t gm = 0u;
@@ -646,95 +657,102 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                             for (int qb = 0; qb < kOzS - pa; ++qb)
                                 if ((mb >> qb) & 1) gm |= 1u << (pa + qb);
                 }
-                for (int h = 0; h < kOzBN / 32; ++h) {
-                    const int j0 = n0 + h * 32;
-                    // mode 1: this row's place in the tableau, its constraint and
-                    // its original entries at the half's columns, read before the
-                    // accumulators so that their latency overlaps the reads of
-                    // tensor memory
-                    int ti = 0, kr = 0;
-                    double av[32];
+                {
+                    // the warp's 32 columns in two blocks of 16 (few enough
+                    // registers for two epilogue warps per lane quarter)
+                    int ti = 0, kr = 0;  // mode 1: this row's place in the tableau, its constraint
                     if (p.mode == 1 && r < p.M) {
                         ti = p.rowmap[r];
                         kr = p.rowk[r];
-                        const double *arow = p.Aorig + (long long)kr * p.n;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
                     }
-                    float hi[32], lo[32];
+                    const double *arow = p.Aorig + (long long)kr * p.n;
+#pragma unroll 1
+                    for (int sb = 0; sb < 2; ++sb) {
+                        const int cb = hsel * 32 + sb * 16;  // the block's first column in the tile
+                        const int j0 = n0 + cb;
+                        // mode 1: the row's original entries at the block's
+                        // columns, read before the accumulators so that their
+                        // latency overlaps the reads of tensor memory
+                        double av[16];
+                        if (p.mode == 1 && r < p.M) {
 #pragma unroll
-                    for (int g = 0; g < kOzS; ++g) {
-                        uint32_t v[32];
-                        tmem_ld32(tbase + (uint32_t)(g * kOzBN + h * 32), v);
-                        tmem_ld_wait();
-                        const float sc = pow2f(-kOzT * g);
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            // (a group no digit pair wrote holds stale columns: zero)
-                            const float x = ((gm >> g) & 1u)
-                                                ? __fmul_rn(__uint_as_float(v[j]), sc)  // exact
-                                                : 0.0f;
-                            if (g == 0) {
-                                hi[j] = x;
-                                lo[j] = 0.0f;
-                            } else {
-                                float s, e;
-                                two_sum(hi[j], x, s, e);
-                                hi[j] = s;
-                                lo[j] = __fadd_rn(lo[j], e);
-                            }
+                            for (int j = 0; j < 16; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
                         }
-                    }
-                    if (h == kOzBN / 32 - 1) {
-                        // every accumulator of the tile is in registers: the
-                        // MMAs of the next tile may start while this half's
-                        // results are written
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(tmem_empty);
-                    }
-                    // Each thread writes its own row's 32 results (the row its
-                    // tensor-memory lane holds): one contiguous row segment per
-                    // thread, read (C, or the original row of A) and written with
-                    // independent accesses, no shared-memory transposition.
-                    if (p.mode == 0) {
-                        if (r < p.M) {
-                            double *crow = p.C + (long long)r * p.ldc + j0;
+                        float hi[16], lo[16];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int Fc = s_colexp[h * 32 + j];
-                                double v = 0.0;
-                                // scale 2^(Er - 1022 + Fc - 1022 - 14)
-                                if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
-                                if (j0 + j < p.N) crow[j] = c == 0 ? v : crow[j] + v;
-                            }
-                        }
-                    } else if (r < p.M) {
-                        const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
-                        float *trow = p.T32 + (long long)ti * p.P;
+                        for (int g = 0; g < kOzS; ++g) {
+                            uint32_t v[16];
+                            tmem_ld16(tbase + (uint32_t)(g * kOzBN + cb), v);
+                            tmem_ld_wait();
+                            const float sc = pow2f(-kOzT * g);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int col = j0 + j;
-                            // the rhs column comes from the reinversion
-                            if (col < p.N - 1) {
-                                const int br = s_brow[h * 32 + j];
-                                float out;
-                                if (br >= 0) {
-                                    out = br == ti ? 1.0f : 0.0f;
+                            for (int j = 0; j < 16; ++j) {
+                                // (a group no digit pair wrote holds stale columns: zero)
+                                const float x = ((gm >> g) & 1u)
+                                                    ? __fmul_rn(__uint_as_float(v[j]), sc)  // exact
+                                                    : 0.0f;
+                                if (g == 0) {
+                                    hi[j] = x;
+                                    lo[j] = 0.0f;
                                 } else {
-                                    const int Fc = s_colexp[h * 32 + j];
-                                    double v = 0.0;
-                                    if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
-                                    // sg A_kj by its sign bit (no FP64 multiply)
-                                    const double d = col < p.n ? __longlong_as_double(__double_as_longlong(av[j]) ^ sgbit)
-                                                               : (col - p.n == kr ? 1.0 : 0.0);
-                                    out = __double2float_rn(d - v);
+                                    float s, e;
+                                    two_sum(hi[j], x, s, e);
+                                    hi[j] = s;
+                                    lo[j] = __fadd_rn(lo[j], e);
                                 }
-                                trow[col] = out;
+                            }
+                        }
+                        if (sb == 1) {
+                            // this warp's accumulators are in registers: once every
+                            // epilogue warp's are, the MMAs of the next tile may
+                            // start while the results are written
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(tmem_empty);
+                        }
+                        // Each thread writes its own row's results (the row its
+                        // tensor-memory lane holds): one contiguous row segment per
+                        // thread, read (C, or the original row of A) and written with
+                        // independent accesses, no shared-memory transposition.
+                        if (p.mode == 0) {
+                            if (r < p.M) {
+                                double *crow = p.C + (long long)r * p.ldc + j0;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const int Fc = s_colexp[cb + j];
+                                    double v = 0.0;
+                                    // scale 2^(Er - 1022 + Fc - 1022 - 14)
+                                    if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
+                                    if (j0 + j < p.N) crow[j] = c == 0 ? v : crow[j] + v;
+                                }
+                            }
+                        } else if (r < p.M) {
+                            const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
+                            float *trow = p.T32 + (long long)ti * p.P;
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int col = j0 + j;
+                                // the rhs column comes from the reinversion
+                                if (col < p.N - 1) {
+                                    const int br = s_brow[cb + j];
+                                    float out;
+                                    if (br >= 0) {
+                                        out = br == ti ? 1.0f : 0.0f;
+                                    } else {
+                                        const int Fc = s_colexp[cb + j];
+                                        double v = 0.0;
+                                        if (Er != kNoExp && Fc != kNoExp) v = scaled_sum(hi[j], lo[j], Er + Fc - 2058);
+                                        // sg A_kj by its sign bit (no FP64 multiply)
+                                        const double d = col < p.n ? __longlong_as_double(__double_as_longlong(av[j]) ^ sgbit)
+                                                                   : (col - p.n == kr ? 1.0 : 0.0);
+                                        out = __double2float_rn(d - v);
+                                    }
+                                    trow[col] = out;
+                                }
                             }
                         }
                     }
-                    __syncwarp();  // the slice is free again
+                    __syncwarp();
                 }
                 ++use;
             }
