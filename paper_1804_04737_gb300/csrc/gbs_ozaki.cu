@@ -67,7 +67,7 @@ constexpr int kOzABytes = kOzBM * kOzBK * 2;            // 16 KB: one A digit pl
 constexpr int kOzBBytes = kOzBN * kOzBK * 2;            // 8 KB: one B digit plane block
 constexpr int kOzBStageBytes = kOzS * kOzBBytes;        // 56 KB: all digit planes of a B block
 constexpr int kOzTmemCols = 512;                        // S x 64 = 448 used
-constexpr int kOzEpiWarps = 8;          // epilogue warps: two per tensor-memory lane quarter
+constexpr int kOzEpiWarps = 16;         // epilogue warps: four per tensor-memory lane quarter
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr size_t kOzSmem = 1024 + 2 * kOzBStageBytes + kOzAStages * kOzABytes + 256;
 
@@ -157,6 +157,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -623,8 +629,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             }
         }
     } else {
-        // ---- epilogue: warps 2..9, TMEM lanes 32 (warp % 4) .. + 31; warps
-        // 2..5 take the tile's first 32 columns, warps 6..9 the last 32 ----
+        // ---- epilogue: warps 2..17, TMEM lanes 32 (warp % 4) .. + 31; warps
+        // 2..5 take the tile's columns 0..15, warps 6..9 columns 16..31, and so on ----
         const int lg = warp & 3, et = threadIdx.x - 64, hsel = (warp - 2) >> 2;
         uint32_t use = 0;
         bool ok = true;
@@ -658,8 +664,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                 if ((mb >> qb) & 1) gm |= 1u << (pa + qb);
                 }
                 {
-                    // the warp's 32 columns in two blocks of 16 (few enough
-                    // registers for two epilogue warps per lane quarter)
+                    // the warp's 16 columns in two blocks of 8 (few enough
+                    // registers for four epilogue warps per lane quarter)
                     int ti = 0, kr = 0;  // mode 1: this row's place in the tableau, its constraint
                     if (p.mode == 1 && r < p.M) {
                         ti = p.rowmap[r];
@@ -668,25 +674,25 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     const double *arow = p.Aorig + (long long)kr * p.n;
 #pragma unroll 1
                     for (int sb = 0; sb < 2; ++sb) {
-                        const int cb = hsel * 32 + sb * 16;  // the block's first column in the tile
+                        const int cb = hsel * 16 + sb * 8;  // the block's first column in the tile
                         const int j0 = n0 + cb;
                         // mode 1: the row's original entries at the block's
                         // columns, read before the accumulators so that their
                         // latency overlaps the reads of tensor memory
-                        double av[16];
+                        double av[8];
                         if (p.mode == 1 && r < p.M) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
+                            for (int j = 0; j < 8; ++j) av[j] = j0 + j < p.n ? __ldg(arow + j0 + j) : 0.0;
                         }
-                        float hi[16], lo[16];
+                        float hi[8], lo[8];
 #pragma unroll
                         for (int g = 0; g < kOzS; ++g) {
-                            uint32_t v[16];
-                            tmem_ld16(tbase + (uint32_t)(g * kOzBN + cb), v);
+                            uint32_t v[8];
+                            tmem_ld8(tbase + (uint32_t)(g * kOzBN + cb), v);
                             tmem_ld_wait();
                             const float sc = pow2f(-kOzT * g);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < 8; ++j) {
                                 // (a group no digit pair wrote holds stale columns: zero)
                                 const float x = ((gm >> g) & 1u)
                                                     ? __fmul_rn(__uint_as_float(v[j]), sc)  // exact
@@ -718,7 +724,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                             if (r < p.M) {
                                 double *crow = p.C + (long long)r * p.ldc + j0;
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) {
+                                for (int j = 0; j < 8; ++j) {
                                     const int Fc = s_colexp[cb + j];
                                     double v = 0.0;
                                     // scale 2^(Er - 1022 + Fc - 1022 - 14)
@@ -730,7 +736,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                             const long long sgbit = p.sg < 0.0 ? (long long)kSign : 0ll;
                             float *trow = p.T32 + (long long)ti * p.P;
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < 8; ++j) {
                                 const int col = j0 + j;
                                 // the rhs column comes from the reinversion
                                 if (col < p.N - 1) {
