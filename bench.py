@@ -106,6 +106,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """(TFLOP/s, how): the measured dense bf16 rate (burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def device_fp64_peak(index):
     """(TFLOP/s, how): 2 FP64 FMA per clock per SM x the device's SM count x its
     maximum SM clock (nvidia-smi), the derived FP64 FMA peak."""
@@ -650,6 +659,9 @@ def product_bench(capi, torch, local, m=8192, n=8192, s=334):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = float(np.median(times))
+    # the bf16 digit products the tensor cores ran (128 x 64 x 16 per MMA)
+    tensor_flops = capi.lp_dgemm_stats() * 2.0 * 128 * 64 * 16
+    bf16, bf16_how = bf16_peak()
     ref = (A.cpu().numpy() @ B[:, :256].cpu().numpy())
     err = float(np.max(np.abs(C[:, :256].cpu().numpy() - ref) / np.maximum(1.0, np.abs(ref))))
     fp64_peak, how = device_fp64_peak(local)
@@ -659,6 +671,11 @@ def product_bench(capi, torch, local, m=8192, n=8192, s=334):
             "fp64_equivalent_tflops": round(flops / ms / 1e9, 2),
             "vs_fp64_pipe_peak": round(flops / ms / 1e9 / fp64_peak, 2), "fp64_peak_kind": how,
             "fp64_pipe_ms_for_the_same_product": round(flops / (fp64_peak * 1e12) * 1e3, 1),
+            "tensor": {"bf16_tflops_executed": round(tensor_flops / ms / 1e9, 1),
+                       "digit_products_run_of_28": round(tensor_flops / flops, 2),
+                       "peak": bf16, "peak_kind": bf16_how,
+                       "frac": round(tensor_flops / ms / 1e9 / bf16, 4),
+                       "note": "the whole call: digit split, products and epilogue"},
             "max_rel_err_vs_numpy_fp64_first_256_columns": err}
 
 

@@ -443,6 +443,12 @@ lp_err lp_fp32_stats(lp_handle *h, int *reinversions, double *reinv_ms, double *
  * failed or a device wait ran out); the message is lp_last_error(NULL). */
 lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long long lda, const double *B,
                          long long ldb, double *C, long long ldc, const lp_options *opt);
+/* The tensor-core MMA instructions (tcgen05.mma kind::f16, 128 x 64 x 16 bf16,
+ * 2 x 128 x 64 x 16 flops each) the last lp_dgemm_emulated in this process
+ * issued: the digit products it ran, which depend on the data (digit planes
+ * that are zero over a whole 128-row or 64-column block are skipped).  0 before
+ * the first call or after a failed one. */
+lp_err lp_dgemm_stats(long long *tensor_mmas);
 
 /* Free the handle and its device memory.  NULL is allowed. */
 void lp_destroy(lp_handle *h);

@@ -129,6 +129,7 @@ _SIGS = [
                                          ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                          ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong,
                                          ctypes.POINTER(lp_options)]),
+    ("lp_dgemm_stats", ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong)]),
     ("lp_destroy", None, [ctypes.c_void_p]),
     ("lp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("lp_version", ctypes.c_char_p, []),
@@ -472,3 +473,11 @@ def solve(A, b, c, sense=LP_MAX_LE, trace_cap=0, **opts) -> Result:
         return Result(st, obj, x, y, it, tp, tq)
     finally:
         lp_destroy(h)
+
+
+def lp_dgemm_stats():
+    """Tensor-core MMA instructions (128 x 64 x 16 bf16) the last
+    lp_dgemm_emulated issued."""
+    n = ctypes.c_longlong()
+    _check(load_library().lp_dgemm_stats(ctypes.byref(n)))
+    return n.value

@@ -341,6 +341,7 @@ struct OzWork {
     int *basic_row = nullptr, *L = nullptr, *Lrow = nullptr;
     size_t cap_X = 0, cap_Ainv = 0, cap_Z = 0, cap_basic = 0, cap_L = 0, cap_Lrow = 0;
     int *err = nullptr;  // the product kernel's error flag (one int)
+    unsigned long long *mmas = nullptr;  // tensor-core MMAs the last product issued
 };
 void oz_work_free(OzWork &w);
 

@@ -423,6 +423,7 @@ struct OzParams {
     int n, m;
     double sg;
     int *err;
+    unsigned long long *mmas;  // += the tcgen05.mma instructions issued (128 x 64 x 16 each)
     long long spin_limit;
 };
 
@@ -566,6 +567,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (lane == 0) {
             int as = 0, bs = 0;
             uint32_t aph = 0, bph = 0, use = 0;
+            unsigned long long nmma = 0;  // MMA instructions issued
             bool ok = true;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 const int ma = p.amask[(t % nmb)], mb = p.bmask[(t / nmb)];
@@ -600,6 +602,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                     tc_mma(d, ad + 2, bd + 2, kOzIdesc, 1u);
                                     tc_mma(d, ad + 4, bd + 4, kOzIdesc, 1u);
                                     tc_mma(d, ad + 6, bd + 6, kOzIdesc, 1u);
+                                    nmma += 4;
                                 }
                             }
                             tc_commit(empty_a(as));  // the stage frees when these MMAs complete
@@ -620,6 +623,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     ++use;
                 }
             }
+            if (p.mmas) atomicAdd(p.mmas, nmma);
             // every MMA issued is complete before tensor memory is freed
             // (a commit arrives after all of them)
             if (!ok) {
@@ -841,6 +845,8 @@ cudaError_t oz_reserve(OzWork &w, int M, int N, int K) {
     if ((e = grow_buf(&w.pmask, &w.cap_pmask, (size_t)(Mp / kOzBM + Np / kOzBN))) != cudaSuccess)
         return e;
     if (!w.err && (e = cudaMalloc((void **)&w.err, sizeof(int))) != cudaSuccess) return e;
+    if (!w.mmas && (e = cudaMalloc((void **)&w.mmas, sizeof(unsigned long long))) != cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 
@@ -855,7 +861,7 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
     cudaError_t e;
     if (w.cap_asl < (size_t)kOzS * Mp * Kp || w.cap_bsl < (size_t)kOzS * Np * Kp ||
         w.cap_rowexp < (size_t)M || w.cap_colexp < (size_t)N || w.cap_kx < (size_t)2 * K ||
-        w.cap_pmask < (size_t)(Mp / kOzBM + Np / kOzBN) || !w.err)
+        w.cap_pmask < (size_t)(Mp / kOzBM + Np / kOzBN) || !w.err || !w.mmas)
         return cudaErrorInvalidValue;
     int *kA = w.kx, *shift = w.kx + K;
     int *amask = w.pmask, *bmask = w.pmask + Mp / kOzBM;
@@ -892,7 +898,9 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
     p.amask = amask;
     p.bmask = bmask;
     if (!p.err) p.err = w.err;
+    p.mmas = w.mmas;
     if ((e = cudaMemsetAsync(p.err, 0, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.mmas, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if (p.mode == 1 && Kp > kOzChunkKB * kOzBK) return cudaErrorInvalidValue;  // one chunk only
     if ((e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kOzSmem)) != cudaSuccess)
@@ -905,7 +913,8 @@ cudaError_t oz_product(SA srcA, SB srcB, int M, int N, int K, OzParams p, OzWork
 }  // namespace
 
 void oz_work_free(OzWork &w) {
-    void *ps[] = {w.asl, w.bsl, w.rowexp, w.colexp, w.kx, w.pmask, w.X, w.Ainv, w.Z, w.basic_row, w.L, w.Lrow, w.err};
+    void *ps[] = {w.asl, w.bsl, w.rowexp, w.colexp, w.kx, w.pmask, w.X, w.Ainv, w.Z, w.basic_row, w.L, w.Lrow, w.err,
+                  w.mmas};
     for (void *q : ps)
         if (q) cudaFree(q);
     w = OzWork{};
@@ -1088,6 +1097,7 @@ namespace {
 constexpr int kOzMaxDevices = 64;
 std::mutex g_oz_mutex;
 gbs::OzWork g_oz_work[kOzMaxDevices];
+long long g_oz_last_mmas = 0;  // MMAs of the last lp_dgemm_emulated (under g_oz_mutex)
 }  // namespace
 
 extern "C" lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long long lda,
@@ -1126,10 +1136,13 @@ extern "C" lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long l
     std::lock_guard<std::mutex> lock(g_oz_mutex);
     OzWork &w = g_oz_work[o.device];
     int herr = 0;
+    unsigned long long nmma = 0;
     if (e == cudaSuccess)
         e = oz_dgemm(A, lda, B, ldb, C, ldc, M, N, K, w, nullptr, sms, o.spin_timeout_cycles, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, w.err, sizeof herr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nmma, w.mmas, sizeof nmma, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    g_oz_last_mmas = e == cudaSuccess ? (long long)nmma : 0;
     if (e != cudaSuccess) {
         snprintf(msg, sizeof msg, "lp_dgemm_emulated: %s", cudaGetErrorString(e));
         set_last_error_global(msg);
@@ -1139,5 +1152,15 @@ extern "C" lp_err lp_dgemm_emulated(int M, int N, int K, const double *A, long l
         set_last_error_global("lp_dgemm_emulated: a device wait ran out (spin_timeout_cycles)");
         return LP_ERR_CUDA;
     }
+    return LP_OK;
+}
+
+extern "C" lp_err lp_dgemm_stats(long long *tensor_mmas) {
+    if (!tensor_mmas) {
+        gbs::set_last_error_global("lp_dgemm_stats: NULL output");
+        return LP_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_oz_mutex);
+    *tensor_mmas = g_oz_last_mmas;
     return LP_OK;
 }

@@ -184,3 +184,22 @@ def test_digit_planes_skipped_per_block():
     assert np.array_equal(C[:128, 64:128], ref[:128, 64:128])
     bound = 2.0 ** -44 * K * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :]
     assert np.all(np.abs(C - ref) <= bound)
+
+
+def test_mma_count_of_the_digit_products():
+    """lp_dgemm_stats: real-valued blocks need all seven digit planes, so
+    every output tile runs the 28 digit pairs (p + q < 7) for every 64-deep
+    K block, 4 MMAs of K = 16 each; with integer blocks (two planes) the
+    product runs fewer, and never none."""
+    rng = np.random.default_rng(5)
+    M, N, K = 256, 128, 128  # 2 x 2 tiles of 128 x 64, 2 K blocks
+    _emulated(rng.standard_normal((M, K)), rng.standard_normal((K, N)))
+    assert capi.lp_dgemm_stats() == 2 * 2 * 2 * 28 * 4
+    M, N, K = 300, 200, 250  # 3 x 4 tiles, 4 K blocks
+    A = rng.standard_normal((M, K))
+    A[:128] = rng.integers(-1000, 1001, size=(128, K))
+    B = rng.standard_normal((K, N))
+    B[:, 64:128] = rng.integers(-1000, 1001, size=(K, 64))
+    _emulated(A, B)
+    full = 3 * 4 * 4 * 28 * 4
+    assert 3 * 4 * 4 * 4 <= capi.lp_dgemm_stats() < full
