@@ -672,10 +672,10 @@ def product_bench(capi, torch, local, m=8192, n=8192, s=334):
             "vs_fp64_pipe_peak": round(flops / ms / 1e9 / fp64_peak, 2), "fp64_peak_kind": how,
             "fp64_pipe_ms_for_the_same_product": round(flops / (fp64_peak * 1e12) * 1e3, 1),
             "tensor": {"bf16_tflops_executed": round(tensor_flops / ms / 1e9, 1),
-                       "digit_products_run_of_28": round(tensor_flops / flops, 2),
+                       "bf16_flops_per_fp64_flop": round(tensor_flops / flops, 2),
                        "peak": bf16, "peak_kind": bf16_how,
                        "frac": round(tensor_flops / ms / 1e9 / bf16, 4),
-                       "note": "the whole call: digit split, products and epilogue"},
+                       "note": "digit products run (of 28 pairs, K padded to 64): the whole call, digit split, products and epilogue"},
             "max_rel_err_vs_numpy_fp64_first_256_columns": err}
 
 

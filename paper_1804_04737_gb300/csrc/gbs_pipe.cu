@@ -2718,6 +2718,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 // selection chain and the update keep their values in registers (the
 // 1024-thread build spills)
 constexpr int kMidThreads = 768;
+// and of up to this many: 96 registers
+constexpr int kSmallThreads = 640;
 
 cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                               long long spin_limit, long long budget, cudaStream_t s) {
@@ -2740,7 +2742,10 @@ cudaError_t launch_pivot_pipe(int prec, LpDesc *d_desc, const PivotShape &sh,
                                                      : (const void *)pivot_block_kernel<double, 8, false, true>)
                                           : (sh.dist ? (const void *)pivot_block_kernel<double, 4, true, true>
                                                      : (const void *)pivot_block_kernel<double, 4, false, true>))
-                                    : (w8 ? (sh.threads <= kMidThreads
+                                    : (w8 ? (sh.threads <= kSmallThreads
+                                                 ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false, kSmallThreads>
+                                                            : (const void *)pivot_block_kernel<double, 8, false, false, kSmallThreads>)
+                                             : sh.threads <= kMidThreads
                                                  ? (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false, kMidThreads>
                                                             : (const void *)pivot_block_kernel<double, 8, false, false, kMidThreads>)
                                                  : (sh.dist ? (const void *)pivot_block_kernel<double, 8, true, false>
