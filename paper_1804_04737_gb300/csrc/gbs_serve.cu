@@ -988,8 +988,10 @@ bool engine_solo(lp_server *sv) {
         // starts), then the handle pivots on from where it stopped.
         h = r->solo_h;
         iters = r->iters;  // pivots made before the spill
-        cudaError_t ce = cudaMemcpyAsync(sv->arena_dev + off, r->host, r->host_used,
-                                         cudaMemcpyHostToDevice, sv->kstream);
+        // (the whole arena, allocated from empty, starts at offset 0)
+        cudaError_t ce = off == 0 ? cudaMemcpyAsync(sv->arena_dev + off, r->host, r->host_used,
+                                                    cudaMemcpyHostToDevice, sv->kstream)
+                                  : cudaErrorInvalidValue;
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(sv->kstream);
         host_give(sv, r->host, r->host_cap);
         std::lock_guard<std::mutex> lk(sv->mu);
