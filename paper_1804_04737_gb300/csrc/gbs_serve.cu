@@ -1110,7 +1110,7 @@ bool engine_solo(lp_server *sv) {
     return true;
 }
 
-// FP64 lanes (lp_options.lanes > 0): lane k solves one LP at a time, as
+// FP64 lanes (lp_options.lanes > 0): each lane solves one LP at a time, as
 // lp_load + lp_solve + lp_result solve it, on its own handle (its own stream,
 // SMs / lanes CTAs, its buffers carved from a slice of budget / lanes bytes of
 // the arena taken for the LP); the lanes' kernels share the GPU, so the
@@ -1119,8 +1119,7 @@ bool engine_solo(lp_server *sv) {
 // the queue until every lane is idle, the lanes taking no new LP meanwhile,
 // then runs on the whole arena and every SM (engine_solo, with its slices and
 // spills under spill_pivots).
-void lane_main(lp_server *sv, int k) {
-    (void)k;
+void lane_main(lp_server *sv) {
     cudaSetDevice(sv->device);
     lp_handle *h = nullptr;
     {
@@ -1327,7 +1326,7 @@ lp_err lp_server_create(lp_server **out, const lp_options *opt, size_t hbm_budge
     if (sv->lanes > 0) {
         sv->lane_ctas = std::max(1, sv->sms / sv->lanes);
         sv->lane_bytes = hbm_budget_bytes / sv->lanes / 256 * 256;
-        for (int k = 0; k < sv->lanes; ++k) sv->lane_threads.emplace_back(lane_main, sv, k);
+        for (int k = 0; k < sv->lanes; ++k) sv->lane_threads.emplace_back(lane_main, sv);
     } else {
         sv->engine = std::thread(sv->fp32 ? engine32_main : engine_main, sv);
     }
