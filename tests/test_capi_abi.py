@@ -59,6 +59,24 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert "NULL" in capi.lp_last_error(None)
 
 
+def test_server_options_checked_without_gpu(lib):
+    """The server's option checks come before any CUDA call: lanes outside
+    0..16 and a negative spill_pivots are refused; the stats calls refuse
+    NULL; no product has run, so no MMA is counted."""
+    import ctypes
+    srv = ctypes.c_void_p()
+    for bad in ({"lanes": 17}, {"lanes": -1}, {"spill_pivots": -1}):
+        opt = capi.lp_options_default(**bad)
+        assert lib.lp_server_create(ctypes.byref(srv), ctypes.byref(opt), 1 << 30, 8) == \
+            capi.LP_ERR_INVALID_ARG
+        assert not srv.value
+    assert lib.lp_server_spill_stats(None, None, None, None) == capi.LP_ERR_INVALID_ARG
+    assert lib.lp_dgemm_stats(None) == capi.LP_ERR_INVALID_ARG
+    assert capi.lp_dgemm_stats() == 0
+    o = capi.lp_options_default()
+    assert o.lanes == 3 and o.spill_pivots == 0 and o.zero_skip == 1
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(capi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
