@@ -337,8 +337,9 @@ lp_err lp_batch_autotune(int count, const int *m, const int *n, const double *co
  * the LP alone, bit for bit.  An LP of at least opt->solo_elems tableau
  * elements instead runs alone, as lp_load + lp_solve run it, once the LPs
  * ahead of it are done (its buffers come from the same arena).  Inputs are
- * staged in pinned host memory at submit.  m, n <= 4096; inputs and outputs
- * in host memory.
+ * staged in pinned host memory at submit (a pool of reused buffers of up to
+ * 8 GiB in all, pageable memory beyond it, freed by lp_server_destroy).
+ * m, n <= 4096; inputs and outputs in host memory.
  * With opt->precision == LP_FP32_REINV the tableaus are FP32 and the server
  * works in rounds: one batched launch in which every admitted LP pivots up
  * to reinv_k times, then each LP's FP64 reinversion and the decisions of the
