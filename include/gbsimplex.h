@@ -220,10 +220,11 @@ typedef struct {
                                 rounds, and an FP64 LP that runs alone
                                 (solo_elems), which pivots spill_pivots at a
                                 time and is spilled at the end of a slice when
-                                any request is waiting.  The FP64 server
-                                kernel's LPs and FP32 LPs that run alone
-                                (whose reinversion schedule restarts with each
-                                call) run to their end.  Ignored elsewhere.     */
+                                any request is waiting.  The LPs of the FP64
+                                lanes and of the FP64 server kernel, and FP32
+                                LPs that run alone (whose reinversion schedule
+                                restarts with each call), run to their end.
+                                Ignored elsewhere.                              */
     int lanes;               /* FP64 servers: L in 1..16 (default 3) = L lanes,
                                 each solving one LP at a time as lp_load +
                                 lp_solve + lp_result would (the kernels
