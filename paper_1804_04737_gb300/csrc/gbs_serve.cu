@@ -720,7 +720,8 @@ bool spill32(lp_server *sv, int slot) {
     r->failed32 = sv->failed[slot];
     r->remaining32 = sv->remaining[slot];
     r->guard32 = sv->guard[slot];
-    sv->active.erase(std::find(sv->active.begin(), sv->active.end(), slot));
+    const auto at = std::find(sv->active.begin(), sv->active.end(), slot);
+    if (at != sv->active.end()) sv->active.erase(at);
     std::lock_guard<std::mutex> lk(sv->mu);
     r->host = hp;
     r->host_cap = cap;
